@@ -1,0 +1,217 @@
+/*
+ * th.h -- C ABI of the GB300 two-grid Helmholtz library.
+ *
+ * The method (Stolk, "A two-grid method with dispersion matching for
+ * finite-element Helmholtz problems"): the Helmholtz equation
+ *     -Lap u - (k^2 + i eps) u = f              (Section 2, Eq. Helmholtz_eq)
+ * on the unit square with Robin (absorbing) or Neumann sides, discretised with
+ * continuous Q_p elements on a uniform mesh of n x n cells (Section 3.1,
+ * Eq. bilin_form), is solved by flexible GMRES preconditioned with the
+ * two-grid step of Algorithm 1: a complex-shifted overlapping domain-
+ * decomposition smoother (Algorithm 2, Eq. RAS_like_update) and a coarse
+ * correction on a mesh of spacing 2h/p with the dispersion-minimising QSFEM
+ * 9-point operator (Sections 3.2-3.3, Eq. P_QSFEM, Eq. element_wise_qsfem).
+ *
+ * Conventions shared by every entry point
+ *   - Fine vectors hold N = (n p + 1)^2 complex values, lexicographic on the
+ *     global node grid, x fastest; coarse vectors hold Nc = (n p / 2 + 1)^2.
+ *     The nodal basis is the Lagrange basis on the Gauss-Lobatto-Legendre
+ *     points of each cell.
+ *   - Complex numbers are interleaved (re, im) IEEE doubles: a vector is a
+ *     double[2 N].  Several right-hand sides are stored one after another:
+ *     rhs r starts at element 2 N r.
+ *   - Pointers named *_dev are CUDA device pointers (or managed memory);
+ *     pointers named *_host are host pointers (pageable or pinned).
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Calls are asynchronous with respect to the host unless stated.
+ *   - The caller owns every buffer it passes.  The library never frees caller
+ *     memory and allocates no device memory except inside th_setup's caller-
+ *     provided workspace (plus what the CUDA runtime itself reserves).
+ *   - Errors are reported by the return code only (no exceptions, no aborts).
+ *     After an error the outputs are unspecified; the context stays valid for
+ *     th_destroy.  th_status_str gives a static message.
+ *   - One context must not be used from two host threads at once.
+ */
+#ifndef TH_H
+#define TH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TH_OK = 0,
+  TH_ERR_ARG = 1,          /* invalid argument or size */
+  TH_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed */
+  TH_ERR_NOMEM = 3,        /* workspace too small, or host allocation failed */
+  TH_ERR_NOCONV = 4,       /* th_solve reached maxit before tol */
+  TH_ERR_BREAKDOWN = 5,    /* Krylov breakdown (zero new direction before convergence) */
+  TH_ERR_NONFINITE = 6,    /* NaN/Inf met in a residual norm */
+  TH_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
+  TH_ERR_UNSUPPORTED = 8,  /* valid but not implemented (e.g. Dirichlet sides) */
+  TH_ERR_SINGULAR = 9      /* a zero pivot during the FP64 set-up factorisations */
+} th_status;
+
+/* Boundary condition of one side (Section 2). */
+enum { TH_BC_NEUMANN = 0, TH_BC_ROBIN = 1, TH_BC_DIRICHLET = 2 /* not supported */ };
+/* Side index in th_mesh.bc: 0 = x low, 1 = x high, 2 = y low, 3 = y high. */
+
+/* Storage / arithmetic precision of the two-grid cycle.
+ *   TH_PREC_FP64: every step in FP64 (the plain form).
+ *   TH_PREC_FP32, TH_PREC_BF16, TH_PREC_FP16: the cycle (operator applies,
+ *   smoother, transfers, coarse solve) runs in FP32 complex arithmetic; the
+ *   subdomain inverse rows are stored in FP32, BF16 or FP16 respectively and
+ *   accumulated in FP32.  The FGMRES orthogonalisation, residual norms and its
+ *   A z products stay FP64 in all modes; the set-up (inverse rows, QSFEM
+ *   coefficients, coarse factorisation) is always computed in FP64. */
+enum { TH_PREC_FP64 = 0, TH_PREC_FP32 = 1, TH_PREC_BF16 = 2, TH_PREC_FP16 = 3 };
+
+/* Operators for th_apply. */
+enum {
+  TH_OP_A = 0,   /* fine Helmholtz matrix A (Eq. bilin_form) */
+  TH_OP_AS = 1,  /* fine shifted matrix A_s: k^2 -> k^2 (1 + i alpha_s) (Section 4.1) */
+  TH_OP_AQ = 2   /* coarse QSFEM matrix A_q (Section 3.3); x, y are coarse vectors */
+};
+
+typedef struct {
+  int dim;      /* 2 */
+  int n;        /* cells per direction, >= 1 */
+  int p;        /* element order: 2, 4, 6 or 8 */
+  int bc[4];    /* TH_BC_* per side: x low, x high, y low, y high */
+} th_mesh;
+
+typedef struct {
+  double alpha_s;   /* smoother shift (Section 4.1); the paper uses 0.2 */
+  int l_dd;         /* subdomain size U^(i) in cells per direction (Section 4.5) */
+  int n_dd;         /* DD iterations per smoother step (Algorithm 2), >= 1 */
+  int n_s;          /* pre- and post-smoothing steps (Algorithm 1), >= 1 */
+  double omega_c;   /* coarse-correction relaxation (Algorithm 1) */
+  int prec;         /* active cycle precision, TH_PREC_* */
+  unsigned prec_mask; /* additional precisions to prepare (bit 1 << TH_PREC_*),
+                         so th_set_precision can switch without a new set-up */
+  int restart;      /* FGMRES restart length m, >= 1 */
+  int maxit;        /* FGMRES iteration limit */
+  double tol;       /* relative residual target ||f - A u|| / ||f|| */
+  int nrhs_max;     /* largest nrhs any later call will pass */
+} th_params;
+
+typedef struct {
+  int iters;            /* FGMRES iterations (max over right-hand sides) */
+  int converged;        /* number of right-hand sides that met tol */
+  double relres_max;    /* max over rhs of the true ||f - A u|| / ||f|| at exit */
+  double ms_total;      /* wall time of th_solve (host clock, includes syncs) */
+  int iters_per_rhs[64];/* iterations of the first min(nrhs, 64) right-hand sides */
+} th_solve_info;
+
+typedef struct th_ctx th_ctx;
+
+/* ------------------------------------------------------------------ set-up */
+
+/* Bytes of device workspace th_setup needs for this mesh and parameters.
+ * Host-only computation.  Returns TH_ERR_ARG / TH_ERR_UNSUPPORTED for invalid
+ * or unsupported inputs. */
+th_status th_workspace_size(const th_mesh* mesh, const th_params* prm, size_t* bytes);
+
+/* Builds a context: the FP64 set-up of Sections 3-4 (GLL reference matrices,
+ * QSFEM cell coefficients, partition, subdomain inverse rows, coarse block
+ * factorisation) on the host, then copies everything into `workspace_dev`.
+ *   k_host, eps_host: double[n*n] per cell, row-major [cy][cx]; eps_host may
+ *     be NULL (eps = 0).  Copied; the caller may free them after return.
+ *   workspace_dev: device buffer of at least th_workspace_size bytes, 256-byte
+ *     aligned, owned by the caller and kept alive until th_destroy.
+ * Synchronous: returns after the copies have completed on `stream`. */
+th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_host,
+                   const th_params* prm, void* workspace_dev, size_t bytes,
+                   void* stream, th_ctx** out);
+
+/* Selects the active cycle precision (must have been prepared at set-up). */
+th_status th_set_precision(th_ctx* ctx, int prec);
+
+/* Releases host-side state.  Does not touch the caller's workspace. */
+void th_destroy(th_ctx* ctx);
+
+const char* th_status_str(th_status s);
+
+/* --------------------------------------------------------- hot-path steps */
+
+/* y = OP x for nrhs right-hand sides (OP = A, A_s: fine vectors; A_q: coarse).
+ * prec: TH_PREC_FP64 applies in FP64; TH_PREC_FP32 rounds x to FP32, applies
+ * in FP32 and widens the result.  x and y must not overlap. */
+th_status th_apply(th_ctx* ctx, int op, const double* x_dev, double* y_dev,
+                   int nrhs, int prec, void* stream);
+
+/* r = f - A u (the residual, fused with the apply), FP64. */
+th_status th_residual(th_ctx* ctx, const double* f_dev, const double* u_dev,
+                      double* r_dev, int nrhs, void* stream);
+
+/* One CSDDSmoother(u, f) step of Algorithm 2 in the active precision:
+ * r = f - A u; v = 0; n_dd times DDStep(v, r; A_s); u += v.  Updates u. */
+th_status th_smooth(th_ctx* ctx, const double* f_dev, double* u_dev, int nrhs, void* stream);
+
+/* r_c = I_P^T r (restriction, the adjoint of the prolongation), FP64. */
+th_status th_restrict(th_ctx* ctx, const double* r_dev, double* rc_dev, int nrhs, void* stream);
+
+/* u += omega * I_P u_c (prolongation: degree-p/2 interpolation of the coarse
+ * vertex values in every fine cell, Section 4.2), FP64. */
+th_status th_prolong(th_ctx* ctx, const double* uc_dev, double* u_dev, double omega,
+                     int nrhs, void* stream);
+
+/* u_c = A_q^{-1} r_c: direct coarse solve with the FP64 block factorisation,
+ * applied in the active precision. */
+th_status th_coarse_solve(th_ctx* ctx, const double* rc_dev, double* uc_dev, int nrhs,
+                          void* stream);
+
+/* One TwoGridStep(u, f) of Algorithm 1 in the active precision; updates u.
+ * With u = 0 on input it is the preconditioner of Section 4. */
+th_status th_cycle(th_ctx* ctx, const double* f_dev, double* u_dev, int nrhs, void* stream);
+
+/* Same as th_cycle on host buffers: copies f and u to the device, runs the
+ * cycle, copies u back; synchronous. */
+th_status th_cycle_host(th_ctx* ctx, const double* f_host, double* u_host, int nrhs, void* stream);
+
+/* Right-preconditioned flexible GMRES(restart) with the two-grid
+ * preconditioner, FP64 orthogonalisation.  u holds the initial guess on
+ * input and the solution on output.  Synchronous (the Hessenberg update runs
+ * on the host).  info may be NULL.  Returns TH_ERR_NOCONV if some right-hand
+ * side has not reached tol within maxit (u then holds the last iterate). */
+th_status th_solve(th_ctx* ctx, const double* f_dev, double* u_dev, int nrhs,
+                   th_solve_info* info, void* stream);
+
+/* th_solve on host buffers (copies in and out inside the call). */
+th_status th_solve_host(th_ctx* ctx, const double* f_host, double* u_host, int nrhs,
+                        th_solve_info* info, void* stream);
+
+/* Number of kernel launches the library issued since the context was built
+ * (all entry points), for accounting. */
+th_status th_launch_count(const th_ctx* ctx, long long* launches);
+
+/* ------------------------------------------------- host-side set-up data */
+/* These run on the host only (no GPU needed) and expose the FP64 set-up the
+ * device path is built from, so that it can be checked on its own. */
+
+/* 1-D reference matrices of Q_p on [0,1] with the GLL Lagrange basis:
+ * nodes[p+1], mass[(p+1)^2], stiff[(p+1)^2] (row-major), integrated exactly. */
+th_status th_host_reference_1d(int p, double* nodes, double* mass, double* stiff);
+
+/* QSFEM per-cell coefficients (Section 3.3) of one coarse cell of size hc with
+ * wavenumber k and damping eps: out[6] = (d0, d1, d2) complex interleaved,
+ * d0 = N P0/4 - i eps hc^2/9, d1 = N P1/2 - i eps hc^2/18, d2 = N P2 - i eps hc^2/36. */
+th_status th_host_qsfem_cell(double k, double eps, double hc, double* out);
+
+/* Inverse rows of one subdomain matrix A_s^(i) (Algorithm 2) of the mesh
+ * (as th_setup would build them): subdomain index `sub` in the row-major
+ * block order; out receives rows x cols complex values (interleaved FP64),
+ * row r = U-box dof r (lexicographic in the U box), column c = Omega-box dof
+ * c, scaled by 1/L_j, where the boxes are given as
+ * box[8] = (ox, oy, wx, wy, ux, uy, vx, vy) in global dof coordinates. */
+th_status th_host_inverse_rows(const th_mesh* mesh, const double* k_host, const double* eps_host,
+                               const th_params* prm, int sub, int* box, double* out,
+                               size_t out_len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TH_H */

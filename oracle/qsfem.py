@@ -22,6 +22,7 @@ cell's k and eps (the paper states the coefficients are constant per cell).
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -29,25 +30,64 @@ import scipy.sparse as sp
 
 from . import fem
 
+try:  # extended precision for the QSFEM ratios
+    import mpmath as _mp
+except ImportError:  # numpy long double is used instead
+    _mp = None
+
+
+def _stencil_scalar(eta: float):
+    """(P0, P1, P2, N) at one eta, the formulas as printed, in 50-digit arithmetic.
+
+    The printed ratios lose about eta^-6 units of the working precision (both
+    numerators and the denominator vanish like eta^4, and sigma_P(0) like
+    eta^2), so they are evaluated in extended precision and rounded once.
+    """
+    if _mp is not None:
+        with _mp.workdps(50):
+            e = _mp.mpf(eta)
+            c1 = _mp.cos(e * _mp.cos(_mp.pi / 16))
+            s1 = _mp.cos(e * _mp.sin(_mp.pi / 16))
+            c2 = _mp.cos(e * _mp.cos(3 * _mp.pi / 16))
+            s2 = _mp.cos(e * _mp.sin(3 * _mp.pi / 16))
+            den = c2 * s2 * (c1 + s1) - c1 * s1 * (c2 + s2)
+            P0 = _mp.mpf(4)
+            P1 = 2 * (c1 * s1 - c2 * s2) / den
+            P2 = (c2 + s2 - c1 - s1) / den
+            N = -e * e / (P0 + 4 * P1 + 4 * P2)
+            return float(P0), float(P1), float(P2), float(N)
+    e = np.longdouble(eta)
+    pi = np.longdouble(math.pi)
+    c1, s1 = np.cos(e * np.cos(pi / 16)), np.cos(e * np.sin(pi / 16))
+    c2, s2 = np.cos(e * np.cos(3 * pi / 16)), np.cos(e * np.sin(3 * pi / 16))
+    den = c2 * s2 * (c1 + s1) - c1 * s1 * (c2 + s2)
+    P1 = 2 * (c1 * s1 - c2 * s2) / den
+    P2 = (c2 + s2 - c1 - s1) / den
+    N = -e * e / (4 + 4 * P1 + 4 * P2)
+    return 4.0, float(P1), float(P2), float(N)
+
+
+@functools.lru_cache(maxsize=1 << 16)
+def _stencil_cached(eta: float):
+    return _stencil_scalar(eta)
+
+
+def _stencil(eta):
+    eta = np.asarray(eta, dtype=float)
+    flat = [_stencil_cached(float(v)) for v in eta.reshape(-1)]
+    out = np.array(flat).reshape(eta.shape + (4,)) if flat else np.zeros(eta.shape + (4,))
+    return out[..., 0], out[..., 1], out[..., 2], out[..., 3]
+
 
 def qsfem_stencil(eta):
     """(P0, P1, P2) of Eq. P_QSFEM, elementwise in eta."""
-    eta = np.asarray(eta, dtype=float)
-    c1 = np.cos(eta * math.cos(math.pi / 16))
-    s1 = np.cos(eta * math.sin(math.pi / 16))
-    c2 = np.cos(eta * math.cos(3 * math.pi / 16))
-    s2 = np.cos(eta * math.sin(3 * math.pi / 16))
-    den = c2 * s2 * (c1 + s1) - c1 * s1 * (c2 + s2)
-    P0 = np.full_like(eta, 4.0)
-    P1 = 2.0 * (c1 * s1 - c2 * s2) / den
-    P2 = (c2 + s2 - c1 - s1) / den
+    P0, P1, P2, _ = _stencil(eta)
     return P0, P1, P2
 
 
 def scaling_N(eta):
     """N(eta) = -eta^2 / sigma_P(0) (Eq. scaling_factor_QSFEM)."""
-    P0, P1, P2 = qsfem_stencil(eta)
-    return -np.asarray(eta, dtype=float) ** 2 / (P0 + 4 * P1 + 4 * P2)
+    return _stencil(eta)[3]
 
 
 def symbol(eta, xi1, xi2):

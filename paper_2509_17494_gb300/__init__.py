@@ -1,0 +1,329 @@
+"""GB300 two-grid Helmholtz solver (arXiv 2509.17494): Python binding of include/th.h.
+
+Argument marshalling only: every step of the solver runs in the native
+library libth.so (hand-written sm_103a CUDA kernels plus the FP64 host
+set-up).  PyTorch provides device memory and streams.  If the library is
+missing the binding raises; there is no fallback implementation.
+
+Vectors are torch.complex128 CUDA tensors of shape (N,) or (nrhs, N) with
+N = (n p + 1)^2 (fine) or Nc = (n p / 2 + 1)^2 (coarse), lexicographic node
+order with x fastest.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["TwoGridSolver", "lib", "library_path", "workspace_size", "host_reference_1d",
+           "host_qsfem_cell", "host_inverse_rows", "PREC", "OPS", "ThError"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libth.so")
+_LIB = None
+
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
+OPS = {"A": 0, "As": 1, "Aq": 2}
+BC = {"neumann": 0, "robin": 1, "dirichlet": 2}
+SIDES = ("xlo", "xhi", "ylo", "yhi")
+
+
+class ThError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {lib().th_status_str(code).decode()} (status {code})")
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("p", ctypes.c_int), ("bc", ctypes.c_int * 4)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("alpha_s", ctypes.c_double), ("l_dd", ctypes.c_int), ("n_dd", ctypes.c_int),
+                ("n_s", ctypes.c_int), ("omega_c", ctypes.c_double), ("prec", ctypes.c_int),
+                ("prec_mask", ctypes.c_uint), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("tol", ctypes.c_double), ("nrhs_max", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("relres_max", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("iters_per_rhs", ctypes.c_int * 64)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libth.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(there is no non-native fallback)")
+    L = ctypes.CDLL(_LIB_PATH)
+    P, I, D, U, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint, None
+    sig = {
+        "th_status_str": ([I], ctypes.c_char_p),
+        "th_workspace_size": ([ctypes.POINTER(Mesh), ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)], I),
+        "th_setup": ([ctypes.POINTER(Mesh), P, P, ctypes.POINTER(Params), P, ctypes.c_size_t, P,
+                      ctypes.POINTER(P)], I),
+        "th_set_precision": ([P, I], I),
+        "th_destroy": ([P], V),
+        "th_apply": ([P, I, P, P, I, I, P], I),
+        "th_residual": ([P, P, P, P, I, P], I),
+        "th_smooth": ([P, P, P, I, P], I),
+        "th_restrict": ([P, P, P, I, P], I),
+        "th_prolong": ([P, P, P, D, I, P], I),
+        "th_coarse_solve": ([P, P, P, I, P], I),
+        "th_cycle": ([P, P, P, I, P], I),
+        "th_cycle_host": ([P, P, P, I, P], I),
+        "th_solve": ([P, P, P, I, ctypes.POINTER(SolveInfo), P], I),
+        "th_solve_host": ([P, P, P, I, ctypes.POINTER(SolveInfo), P], I),
+        "th_launch_count": ([P, ctypes.POINTER(ctypes.c_longlong)], I),
+        "th_host_reference_1d": ([I, P, P, P], I),
+        "th_host_qsfem_cell": ([D, D, D, P], I),
+        "th_host_inverse_rows": ([ctypes.POINTER(Mesh), P, P, ctypes.POINTER(Params), I, P, P,
+                                  ctypes.c_size_t], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = L
+    return L
+
+
+def _check(code, what):
+    if code != 0:
+        raise ThError(code, what)
+
+
+def _mesh(n, p, bc):
+    m = Mesh()
+    m.dim, m.n, m.p = 2, int(n), int(p)
+    if isinstance(bc, str):
+        vals = [BC[bc]] * 4
+    else:
+        vals = [BC[bc.get(s, "neumann")] for s in SIDES]
+    for i, v in enumerate(vals):
+        m.bc[i] = v
+    return m
+
+
+def _params(alpha_s=0.5, l_dd=2, n_dd=1, n_s=1, omega_c=1.0, prec="fp64", extra_prec=(), restart=30,
+            maxit=200, tol=1e-8, nrhs_max=1):
+    q = Params()
+    q.alpha_s, q.l_dd, q.n_dd, q.n_s, q.omega_c = float(alpha_s), int(l_dd), int(n_dd), int(n_s), float(omega_c)
+    q.prec = PREC[prec]
+    mask = 0
+    for e in extra_prec:
+        mask |= 1 << PREC[e]
+    q.prec_mask = mask
+    q.restart, q.maxit, q.tol, q.nrhs_max = int(restart), int(maxit), float(tol), int(nrhs_max)
+    return q
+
+
+def workspace_size(n, p, bc="robin", **params) -> int:
+    out = ctypes.c_size_t(0)
+    m, q = _mesh(n, p, bc), _params(**params)
+    _check(lib().th_workspace_size(ctypes.byref(m), ctypes.byref(q), ctypes.byref(out)), "th_workspace_size")
+    return out.value
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def host_reference_1d(p):
+    nodes, M, K = np.zeros(p + 1), np.zeros((p + 1) ** 2), np.zeros((p + 1) ** 2)
+    _check(lib().th_host_reference_1d(p, nodes.ctypes.data, M.ctypes.data, K.ctypes.data), "th_host_reference_1d")
+    return nodes, M.reshape(p + 1, p + 1), K.reshape(p + 1, p + 1)
+
+
+def host_qsfem_cell(k, eps, hc):
+    out = np.zeros(6)
+    _check(lib().th_host_qsfem_cell(float(k), float(eps), float(hc), out.ctypes.data), "th_host_qsfem_cell")
+    return out[0::2] + 1j * out[1::2]
+
+
+def host_inverse_rows(n, p, k_cell, eps_cell, sub, bc="robin", **params):
+    """(box, W) of subdomain `sub` as the set-up computes it on the host."""
+    m, q = _mesh(n, p, bc), _params(**params)
+    k, kp = _f64(k_cell)
+    e, ep = _f64(eps_cell if eps_cell is not None else np.zeros_like(k))
+    l_dd = max(1, min(int(params.get("l_dd", 2)), n))
+    # maximal U / Omega box widths
+    nb = -(-n // l_dd)
+    lmax = -(-n // nb)
+    Lu = lmax * p + 1
+    Lw = min(lmax + 2, n) * p + 1
+    out = np.zeros(2 * Lu * Lu * Lw * Lw)
+    box = (ctypes.c_int * 8)()
+    _check(lib().th_host_inverse_rows(ctypes.byref(m), kp, ep, ctypes.byref(q), int(sub), box, out.ctypes.data,
+                                      out.size), "th_host_inverse_rows")
+    W = (out[0::2] + 1j * out[1::2]).reshape(Lu * Lu, Lw * Lw)
+    return list(box), W, Lu, Lw
+
+
+class TwoGridSolver:
+    """A set-up context of the two-grid preconditioned FGMRES solver on one GPU."""
+
+    def __init__(self, n, p, k_cell, eps_cell=None, bc="robin", alpha_s=0.5, l_dd=2, n_dd=1, n_s=1,
+                 omega_c=1.0, prec="fp64", extra_prec=(), restart=30, maxit=200, tol=1e-8, nrhs_max=1,
+                 device=None):
+        import torch
+
+        self.torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("TwoGridSolver needs a CUDA device (no CPU fallback)")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.n, self.p = int(n), int(p)
+        self.N = (self.n * self.p + 1) ** 2
+        self.Nc = (self.n * self.p // 2 + 1) ** 2
+        self.nrhs_max = int(nrhs_max)
+        self._mesh = _mesh(n, p, bc)
+        self._params = _params(alpha_s, l_dd, n_dd, n_s, omega_c, prec, extra_prec, restart, maxit, tol, nrhs_max)
+        L = lib()
+        nb = ctypes.c_size_t(0)
+        _check(L.th_workspace_size(ctypes.byref(self._mesh), ctypes.byref(self._params), ctypes.byref(nb)),
+               "th_workspace_size")
+        self.workspace_bytes = nb.value
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        self._k, kp = _f64(np.asarray(k_cell, dtype=float).reshape(-1))
+        if eps_cell is None:
+            ep = None
+        else:
+            self._e, ep = _f64(np.asarray(eps_cell, dtype=float).reshape(-1))
+        ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = L.th_setup(ctypes.byref(self._mesh), kp, ep, ctypes.byref(self._params),
+                            ctypes.c_void_p(self.workspace.data_ptr()), nb.value, self._stream(),
+                            ctypes.byref(ctx))
+        _check(st, "th_setup")
+        self._ctx = ctx
+
+    # ------------------------------------------------------------- helpers
+    def _stream(self):
+        return ctypes.c_void_p(self.torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _vec(self, t, length, name):
+        torch = self.torch
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or t.device != self.device:
+            raise TypeError(f"{name} must be a complex128 tensor on {self.device}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() % length != 0:
+            raise ValueError(f"{name} has {t.numel()} entries, not a multiple of {length}")
+        return t.numel() // length
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().th_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, prec):
+        _check(lib().th_set_precision(self._ctx, PREC[prec]), "th_set_precision")
+
+    def launch_count(self) -> int:
+        v = ctypes.c_longlong(0)
+        _check(lib().th_launch_count(self._ctx, ctypes.byref(v)), "th_launch_count")
+        return v.value
+
+    # ------------------------------------------------------------- operators
+    def apply(self, x, op="A", prec="fp64", out=None):
+        length = self.Nc if op == "Aq" else self.N
+        nrhs = self._vec(x, length, "x")
+        y = out if out is not None else self.torch.empty_like(x)
+        _check(lib().th_apply(self._ctx, OPS[op], x.data_ptr(), y.data_ptr(), nrhs, PREC[prec], self._stream()),
+               "th_apply")
+        return y
+
+    def residual(self, f, u, out=None):
+        nrhs = self._vec(f, self.N, "f")
+        self._vec(u, self.N, "u")
+        r = out if out is not None else self.torch.empty_like(f)
+        _check(lib().th_residual(self._ctx, f.data_ptr(), u.data_ptr(), r.data_ptr(), nrhs, self._stream()),
+               "th_residual")
+        return r
+
+    def smooth(self, f, u):
+        """One CSDDSmoother step, in place on u."""
+        nrhs = self._vec(f, self.N, "f")
+        self._vec(u, self.N, "u")
+        _check(lib().th_smooth(self._ctx, f.data_ptr(), u.data_ptr(), nrhs, self._stream()), "th_smooth")
+        return u
+
+    def restrict(self, r, out=None):
+        nrhs = self._vec(r, self.N, "r")
+        rc = out if out is not None else self.torch.empty(r.shape[:-1] + (self.Nc,), dtype=r.dtype,
+                                                           device=self.device)
+        _check(lib().th_restrict(self._ctx, r.data_ptr(), rc.data_ptr(), nrhs, self._stream()), "th_restrict")
+        return rc
+
+    def prolong(self, uc, u, omega=1.0):
+        """u += omega * I_P uc, in place on u."""
+        nrhs = self._vec(uc, self.Nc, "uc")
+        self._vec(u, self.N, "u")
+        _check(lib().th_prolong(self._ctx, uc.data_ptr(), u.data_ptr(), float(omega), nrhs, self._stream()),
+               "th_prolong")
+        return u
+
+    def coarse_solve(self, rc, out=None):
+        nrhs = self._vec(rc, self.Nc, "rc")
+        uc = out if out is not None else self.torch.empty_like(rc)
+        _check(lib().th_coarse_solve(self._ctx, rc.data_ptr(), uc.data_ptr(), nrhs, self._stream()),
+               "th_coarse_solve")
+        return uc
+
+    def cycle(self, f, u):
+        """One TwoGridStep(u, f), in place on u."""
+        nrhs = self._vec(f, self.N, "f")
+        self._vec(u, self.N, "u")
+        _check(lib().th_cycle(self._ctx, f.data_ptr(), u.data_ptr(), nrhs, self._stream()), "th_cycle")
+        return u
+
+    def solve(self, f, u=None, check=True):
+        """FGMRES with the two-grid preconditioner; returns (u, info dict)."""
+        nrhs = self._vec(f, self.N, "f")
+        if u is None:
+            u = self.torch.zeros_like(f)
+        info = SolveInfo()
+        st = lib().th_solve(self._ctx, f.data_ptr(), u.data_ptr(), nrhs, ctypes.byref(info), self._stream())
+        if check and st not in (0,):
+            raise ThError(st, "th_solve")
+        return u, _info(info, nrhs, st)
+
+    # host-buffer variants (copies inside the call)
+    def cycle_host(self, f, u):
+        f = np.ascontiguousarray(f, dtype=np.complex128)
+        assert u.dtype == np.complex128 and u.flags.c_contiguous
+        nrhs = f.size // self.N
+        _check(lib().th_cycle_host(self._ctx, f.ctypes.data, u.ctypes.data, nrhs, self._stream()), "th_cycle_host")
+        return u
+
+    def solve_host(self, f, u=None):
+        f = np.ascontiguousarray(f, dtype=np.complex128)
+        nrhs = f.size // self.N
+        if u is None:
+            u = np.zeros_like(f)
+        info = SolveInfo()
+        st = lib().th_solve_host(self._ctx, f.ctypes.data, u.ctypes.data, nrhs, ctypes.byref(info), self._stream())
+        if st not in (0, 4):
+            raise ThError(st, "th_solve_host")
+        return u, _info(info, nrhs, st)
+
+
+def _info(info, nrhs, st):
+    return dict(iters=info.iters, converged=info.converged, relres_max=info.relres_max,
+                ms_total=info.ms_total, iters_per_rhs=list(info.iters_per_rhs[:min(nrhs, 64)]), status=st)

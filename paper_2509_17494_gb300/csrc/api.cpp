@@ -1,0 +1,998 @@
+// C ABI of the two-grid Helmholtz library: context, workspace, set-up upload,
+// the two-grid cycle (Algorithm 1 with the CSDD smoother of Algorithm 2) and
+// the outer right-preconditioned flexible GMRES.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "kernels.h"
+#include "th_internal.h"
+
+using th::cplx;
+
+namespace {
+
+// Bump allocator over the caller's workspace; with base == nullptr it only
+// measures (th_workspace_size and th_setup carve in the same order).
+struct Carve {
+  char* base = nullptr;
+  size_t cap = 0, used = 0;
+  bool ok = true;
+  template <typename T>
+  T* take(size_t count) {
+    size_t off = (used + 255) & ~(size_t)255;
+    size_t bytes = count * sizeof(T);
+    used = off + bytes;
+    if (!base) return nullptr;
+    if (used > cap) { ok = false; return nullptr; }
+    return reinterpret_cast<T*>(base + off);
+  }
+};
+
+inline bool has_prec(unsigned mask, int p) { return (mask >> p) & 1u; }
+
+}  // namespace
+
+struct th_ctx {
+  th_mesh mesh{};
+  th_params prm{};
+  th::Geometry g;
+  th::Ref1D ref;
+  unsigned avail = 0;  // bitmask of prepared precisions
+  int active = 0;
+  bool mixed = false;  // any FP32-cycle precision prepared
+  long long launches = 0;
+  int cluster = 8, rpc = 0;
+  int nblk = 1;
+  int rmax = 0;
+  int wchunks[4] = {0, 0, 0, 0};
+  int ddG = 4;  // column groups per subdomain in K3
+  // device arrays
+  double *kc64 = nullptr, *ec64 = nullptr;
+  float *kc32 = nullptr, *ec32 = nullptr;
+  int* box = nullptr;
+  int4* ctab = nullptr;
+  void* W[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* wscale16 = nullptr;
+  int *pj0 = nullptr, *ridx = nullptr;
+  double *pw64 = nullptr, *rw64 = nullptr;
+  float *pw32 = nullptr, *rw32 = nullptr;
+  double2 *ccell64 = nullptr, *crho64 = nullptr;
+  float2 *ccell32 = nullptr, *crho32 = nullptr;
+  double2 *G64 = nullptr, *cl64 = nullptr, *cd64 = nullptr, *cu64 = nullptr;
+  float2 *G32 = nullptr, *cl32 = nullptr, *cd32 = nullptr, *cu32 = nullptr;
+  // cycle work vectors
+  double2 *r64 = nullptr, *s64 = nullptr, *v64 = nullptr, *V64 = nullptr, *rc64 = nullptr, *uc64 = nullptr,
+          *zc64 = nullptr, *t64 = nullptr;
+  float2 *f32 = nullptr, *u32 = nullptr, *r32 = nullptr, *s32 = nullptr, *v32 = nullptr, *V32 = nullptr,
+         *rc32 = nullptr, *uc32 = nullptr, *zc32 = nullptr;
+  // FGMRES
+  double2 *Vk = nullptr, *Zk = nullptr, *w = nullptr, *h1 = nullptr, *h2 = nullptr, *ybuf = nullptr,
+          *dpart = nullptr;
+  double *npart = nullptr, *nrm = nullptr, *scal = nullptr;
+  double2 *fin = nullptr, *uin = nullptr;  // device staging for the host-buffer entry points
+};
+
+namespace {
+
+th_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TH_OK : TH_ERR_CUDA; }
+#define TH_CU(expr)                                   \
+  do {                                                \
+    cudaError_t _e = (expr);                          \
+    if (_e != cudaSuccess) return TH_ERR_CUDA;        \
+  } while (0)
+
+// Carves every device array in a fixed order (sizes only when c.base == nullptr).
+void carve_all(th_ctx& x, Carve& c) {
+  const th::Geometry& g = x.g;
+  const th_params& prm = x.prm;
+  const size_t n2 = (size_t)g.n * g.n;
+  const int nr = prm.nrhs_max;
+  x.kc64 = c.take<double>(n2);
+  x.ec64 = c.take<double>(n2);
+  x.box = c.take<int>((size_t)g.nsub * 8);
+  x.ctab = c.take<int4>((size_t)g.m);
+  x.pj0 = c.take<int>(g.m);
+  x.pw64 = c.take<double>((size_t)g.m * (g.q + 1));
+  x.ridx = c.take<int>((size_t)g.mc * x.rmax);
+  x.rw64 = c.take<double>((size_t)g.mc * x.rmax);
+  x.ccell64 = c.take<double2>((size_t)g.nc * g.nc * 3);
+  x.crho64 = c.take<double2>((size_t)4 * g.nc);
+  const size_t mm = (size_t)g.mc * g.mc;
+  x.cl64 = c.take<double2>(mm);
+  x.cd64 = c.take<double2>(mm);
+  x.cu64 = c.take<double2>(mm);
+  const int CPC[4] = {1, 2, 4, 4};
+  for (int k = 0; k < 4; ++k) {
+    x.wchunks[k] = (g.NC + CPC[k] - 1) / CPC[k];
+    x.W[k] = has_prec(x.avail, k) ? (void*)c.take<uint4>((size_t)g.nsub * x.wchunks[k] * g.NR) : nullptr;
+  }
+  x.wscale16 = has_prec(x.avail, TH_PREC_FP16) ? c.take<float>(g.nsub) : nullptr;
+  const bool fp64 = has_prec(x.avail, TH_PREC_FP64);
+  x.G64 = fp64 ? c.take<double2>(mm * g.mc) : nullptr;
+  // FP64 work vectors are always present (residuals, FGMRES, FP64 applies)
+  x.r64 = c.take<double2>((size_t)nr * g.N);
+  x.s64 = c.take<double2>((size_t)nr * g.N);
+  x.v64 = c.take<double2>((size_t)nr * g.N);
+  x.t64 = c.take<double2>((size_t)nr * g.N);
+  x.V64 = fp64 ? c.take<double2>((size_t)nr * g.nsub * g.NR) : nullptr;
+  x.rc64 = c.take<double2>((size_t)nr * g.Nc);
+  x.uc64 = c.take<double2>((size_t)nr * g.Nc);
+  x.zc64 = fp64 ? c.take<double2>((size_t)nr * g.Nc) : nullptr;
+  if (x.mixed) {
+    x.kc32 = c.take<float>(n2);
+    x.ec32 = c.take<float>(n2);
+    x.pw32 = c.take<float>((size_t)g.m * (g.q + 1));
+    x.rw32 = c.take<float>((size_t)g.mc * x.rmax);
+    x.ccell32 = c.take<float2>((size_t)g.nc * g.nc * 3);
+    x.crho32 = c.take<float2>((size_t)4 * g.nc);
+    x.cl32 = c.take<float2>(mm);
+    x.cd32 = c.take<float2>(mm);
+    x.cu32 = c.take<float2>(mm);
+    x.G32 = c.take<float2>(mm * g.mc);
+    x.f32 = c.take<float2>((size_t)nr * g.N);
+    x.u32 = c.take<float2>((size_t)nr * g.N);
+    x.r32 = c.take<float2>((size_t)nr * g.N);
+    x.s32 = c.take<float2>((size_t)nr * g.N);
+    x.v32 = c.take<float2>((size_t)nr * g.N);
+    x.V32 = c.take<float2>((size_t)nr * g.nsub * g.NR);
+    x.rc32 = c.take<float2>((size_t)nr * g.Nc);
+    x.uc32 = c.take<float2>((size_t)nr * g.Nc);
+    x.zc32 = c.take<float2>((size_t)nr * g.Nc);
+  }
+  const int m = prm.restart;
+  x.Vk = c.take<double2>((size_t)(m + 1) * nr * g.N);
+  x.Zk = c.take<double2>((size_t)m * nr * g.N);
+  x.w = c.take<double2>((size_t)nr * g.N);
+  x.h1 = c.take<double2>((size_t)nr * (m + 1));
+  x.h2 = c.take<double2>((size_t)nr * (m + 1));
+  x.ybuf = c.take<double2>((size_t)nr * (m + 1));
+  x.nblk = th::mdot_blocks(g.N);
+  x.dpart = c.take<double2>((size_t)nr * (m + 1) * x.nblk);
+  x.npart = c.take<double>((size_t)nr * x.nblk);
+  x.nrm = c.take<double>((size_t)nr);
+  x.scal = c.take<double>((size_t)nr);
+  x.fin = c.take<double2>((size_t)nr * g.N);
+  x.uin = c.take<double2>((size_t)nr * g.N);
+}
+
+th_status prepare(const th_mesh* mesh, const th_params* prm, th_ctx& x) {
+  if (!mesh || !prm) return TH_ERR_ARG;
+  x.mesh = *mesh;
+  x.prm = *prm;
+  th_status st = th::make_geometry(*mesh, *prm, x.g);
+  if (st != TH_OK) return st;
+  x.avail = (prm->prec_mask & 0xFu) | (1u << prm->prec);
+  x.active = prm->prec;
+  x.mixed = (x.avail & ~1u) != 0;
+  // restriction table width
+  th::Ref1D ref = th::reference_1d(mesh->p);
+  th::TransferTables tt;
+  th::transfer_tables(x.g, ref, tt);
+  x.rmax = tt.rmax;
+  x.ref = ref;
+  x.cluster = 8;
+  x.rpc = (x.g.mc + x.cluster - 1) / x.cluster;
+  return TH_OK;
+}
+
+uint16_t f2bf(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);  // inf / nan
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+template <typename T>
+th::FineArgs<T> fine_args(const th_ctx& x, int op) {
+  th::FineArgs<T> a{};
+  const th::Geometry& g = x.g;
+  a.N = g.N;
+  a.n = g.n;
+  a.m = g.m;
+  a.p = g.p;
+  a.robin = g.robin[0] | (g.robin[1] << 1) | (g.robin[2] << 2) | (g.robin[3] << 3);
+  a.h = (T)g.h;
+  a.h2 = (T)(g.h * g.h);
+  a.alpha = (op == TH_OP_AS) ? (T)x.prm.alpha_s : (T)0;
+  const int np = g.p + 1;
+  for (int i = 0; i < np * np; ++i) {
+    a.M[i] = (T)x.ref.M[i];
+    a.K[i] = (T)x.ref.K[i];
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    a.kc = x.kc64;
+    a.ec = x.ec64;
+  } else {
+    a.kc = x.kc32;
+    a.ec = x.ec32;
+  }
+  return a;
+}
+
+// y = OP u or y = f - OP u, in precision T, on nrhs right-hand sides
+template <typename T>
+th_status fine_apply(th_ctx& x, int op, const typename th::Cx<T>::t* u, const typename th::Cx<T>::t* f,
+                     typename th::Cx<T>::t* y, int nrhs, cudaStream_t s) {
+  th::FineArgs<T> a = fine_args<T>(x, op);
+  a.u = u;
+  a.f = f;
+  a.y = y;
+  a.residual = f ? 1 : 0;
+  x.launches += 1;
+  return cuda_status(th::launch_fine_apply<T>(a, nrhs, s));
+}
+
+template <typename T> struct PrecBufs;
+template <> struct PrecBufs<double> {
+  static double2* r(th_ctx& x) { return x.r64; }
+  static double2* s(th_ctx& x) { return x.s64; }
+  static double2* v(th_ctx& x) { return x.v64; }
+  static double2* V(th_ctx& x) { return x.V64; }
+  static double2* rc(th_ctx& x) { return x.rc64; }
+  static double2* uc(th_ctx& x) { return x.uc64; }
+  static double2* zc(th_ctx& x) { return x.zc64; }
+  static const double* pw(th_ctx& x) { return x.pw64; }
+  static const double* rw(th_ctx& x) { return x.rw64; }
+  static const double2* G(th_ctx& x) { return x.G64; }
+  static const double2* cl(th_ctx& x) { return x.cl64; }
+  static const double2* cd(th_ctx& x) { return x.cd64; }
+  static const double2* cu(th_ctx& x) { return x.cu64; }
+  static const double2* cell(th_ctx& x) { return x.ccell64; }
+  static const double2* rho(th_ctx& x) { return x.crho64; }
+};
+template <> struct PrecBufs<float> {
+  static float2* r(th_ctx& x) { return x.r32; }
+  static float2* s(th_ctx& x) { return x.s32; }
+  static float2* v(th_ctx& x) { return x.v32; }
+  static float2* V(th_ctx& x) { return x.V32; }
+  static float2* rc(th_ctx& x) { return x.rc32; }
+  static float2* uc(th_ctx& x) { return x.uc32; }
+  static float2* zc(th_ctx& x) { return x.zc32; }
+  static const float* pw(th_ctx& x) { return x.pw32; }
+  static const float* rw(th_ctx& x) { return x.rw32; }
+  static const float2* G(th_ctx& x) { return x.G32; }
+  static const float2* cl(th_ctx& x) { return x.cl32; }
+  static const float2* cd(th_ctx& x) { return x.cd32; }
+  static const float2* cu(th_ctx& x) { return x.cu32; }
+  static const float2* cell(th_ctx& x) { return x.ccell32; }
+  static const float2* rho(th_ctx& x) { return x.crho32; }
+};
+
+template <typename T>
+th_status dd_apply(th_ctx& x, int wkind, const typename th::Cx<T>::t* r, int nrhs, cudaStream_t s) {
+  using B = PrecBufs<T>;
+  const th::Geometry& g = x.g;
+  th::DDArgs<T> a{};
+  a.r = r;
+  a.V = B::V(x);
+  a.W = x.W[wkind];
+  a.box = x.box;
+  a.wscale = (wkind == TH_PREC_FP16) ? x.wscale16 : nullptr;
+  a.N = g.N;
+  a.nsub = g.nsub;
+  a.m = g.m;
+  a.Lw = g.Lw;
+  a.NC = g.NC;
+  a.NCH = x.wchunks[wkind];
+  a.NR = g.NR;
+  a.G = std::max(1, std::min(x.ddG, 512 / std::max(1, g.NR)));
+  a.nrhs = nrhs;
+  x.launches += 1;
+  return cuda_status(th::launch_dd_apply<T>(a, wkind, 0, s));
+}
+
+template <typename T>
+th_status dd_combine(th_ctx& x, typename th::Cx<T>::t* u, int accumulate, int nrhs, cudaStream_t s) {
+  const th::Geometry& g = x.g;
+  th::CombineArgs<T> a{};
+  a.V = PrecBufs<T>::V(x);
+  a.u = u;
+  a.ctab = x.ctab;
+  a.N = g.N;
+  a.m = g.m;
+  a.nb = g.nb;
+  a.Lu = g.Lu;
+  a.NR = g.NR;
+  a.nsub = g.nsub;
+  a.accumulate = accumulate;
+  x.launches += 1;
+  return cuda_status(th::launch_dd_combine<T>(a, nrhs, s));
+}
+
+// CSDDSmoother(u, f) of Algorithm 2 in precision T.  u_zero: u is known to be
+// zero on entry (then r = f and u is overwritten).
+template <typename T>
+th_status smooth(th_ctx& x, int wkind, const typename th::Cx<T>::t* f, typename th::Cx<T>::t* u, bool u_zero,
+                 int nrhs, cudaStream_t s) {
+  using B = PrecBufs<T>;
+  using C = typename th::Cx<T>::t;
+  th_status st;
+  const C* r = f;
+  if (!u_zero) {
+    if ((st = fine_apply<T>(x, TH_OP_A, u, f, B::r(x), nrhs, s)) != TH_OK) return st;
+    r = B::r(x);
+  }
+  if ((st = dd_apply<T>(x, wkind, r, nrhs, s)) != TH_OK) return st;
+  if (x.prm.n_dd == 1) return dd_combine<T>(x, u, u_zero ? 0 : 1, nrhs, s);
+  // n_dd >= 2: v = DDStep(0, r); then v <- DDStep(v, r) = v + avg(W R (r - A_s v))
+  C* v = B::v(x);
+  if ((st = dd_combine<T>(x, v, 0, nrhs, s)) != TH_OK) return st;
+  for (int it = 1; it < x.prm.n_dd; ++it) {
+    if ((st = fine_apply<T>(x, TH_OP_AS, v, r, B::s(x), nrhs, s)) != TH_OK) return st;
+    if ((st = dd_apply<T>(x, wkind, B::s(x), nrhs, s)) != TH_OK) return st;
+    if ((st = dd_combine<T>(x, v, 1, nrhs, s)) != TH_OK) return st;
+  }
+  const long long n = x.g.N * (long long)nrhs;
+  x.launches += 1;
+  if (u_zero) return cuda_status(cudaMemcpyAsync(u, v, sizeof(C) * n, cudaMemcpyDeviceToDevice, s));
+  return cuda_status(th::launch_zaxpy<T>(v, u, (T)1, n, s));
+}
+
+template <typename T>
+th_status restrict_(th_ctx& x, const typename th::Cx<T>::t* r, typename th::Cx<T>::t* rc, int nrhs, cudaStream_t s) {
+  using B = PrecBufs<T>;
+  th::TransferArgs<T> a{};
+  a.in = r;
+  a.out = rc;
+  a.ridx = x.ridx;
+  a.rw = B::rw(x);
+  a.rmax = x.rmax;
+  a.N = x.g.N;
+  a.Nc = x.g.Nc;
+  a.m = x.g.m;
+  a.mc = x.g.mc;
+  a.q = x.g.q;
+  x.launches += 1;
+  return cuda_status(th::launch_restrict<T>(a, nrhs, s));
+}
+
+template <typename T>
+th_status prolong_(th_ctx& x, const typename th::Cx<T>::t* uc, typename th::Cx<T>::t* u, T omega, int nrhs,
+                   cudaStream_t s) {
+  using B = PrecBufs<T>;
+  th::TransferArgs<T> a{};
+  a.in = uc;
+  a.out = u;
+  a.pj0 = x.pj0;
+  a.pw = B::pw(x);
+  a.N = x.g.N;
+  a.Nc = x.g.Nc;
+  a.m = x.g.m;
+  a.mc = x.g.mc;
+  a.q = x.g.q;
+  a.omega = omega;
+  x.launches += 1;
+  return cuda_status(th::launch_prolong<T>(a, nrhs, s));
+}
+
+template <typename T>
+th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th::Cx<T>::t* uc, int nrhs,
+                        cudaStream_t s) {
+  using B = PrecBufs<T>;
+  th::CoarseSolveArgs<T> a{};
+  a.rhs = rc;
+  a.x = uc;
+  a.z = B::zc(x);
+  a.G = B::G(x);
+  a.cl = B::cl(x);
+  a.cd = B::cd(x);
+  a.cu = B::cu(x);
+  a.Nc = x.g.Nc;
+  a.mc = x.g.mc;
+  a.rpc = x.rpc;
+  if (!a.G || !a.z) return TH_ERR_UNSUPPORTED;
+  x.launches += 1;
+  return cuda_status(th::launch_coarse_solve<T>(a, nrhs, x.cluster, s));
+}
+
+template <typename T>
+th_status coarse_apply_(th_ctx& x, const typename th::Cx<T>::t* in, typename th::Cx<T>::t* out, int nrhs,
+                        cudaStream_t s) {
+  using B = PrecBufs<T>;
+  th::CoarseApplyArgs<T> a{};
+  a.x = in;
+  a.y = out;
+  a.cell = B::cell(x);
+  a.rho = B::rho(x);
+  a.Nc = x.g.Nc;
+  a.nc = x.g.nc;
+  a.mc = x.g.mc;
+  x.launches += 1;
+  return cuda_status(th::launch_coarse_apply<T>(a, nrhs, s));
+}
+
+// TwoGridStep(u, f) of Algorithm 1 in precision T.
+template <typename T>
+th_status cycle(th_ctx& x, int wkind, const typename th::Cx<T>::t* f, typename th::Cx<T>::t* u, bool u_zero,
+                int nrhs, cudaStream_t s) {
+  using B = PrecBufs<T>;
+  th_status st;
+  for (int i = 0; i < x.prm.n_s; ++i)
+    if ((st = smooth<T>(x, wkind, f, u, u_zero && i == 0, nrhs, s)) != TH_OK) return st;
+  if ((st = fine_apply<T>(x, TH_OP_A, u, f, B::r(x), nrhs, s)) != TH_OK) return st;
+  if ((st = restrict_<T>(x, B::r(x), B::rc(x), nrhs, s)) != TH_OK) return st;
+  if ((st = coarse_solve_<T>(x, B::rc(x), B::uc(x), nrhs, s)) != TH_OK) return st;
+  if ((st = prolong_<T>(x, B::uc(x), u, (T)x.prm.omega_c, nrhs, s)) != TH_OK) return st;
+  for (int i = 0; i < x.prm.n_s; ++i)
+    if ((st = smooth<T>(x, wkind, f, u, false, nrhs, s)) != TH_OK) return st;
+  return TH_OK;
+}
+
+// Widen / narrow helpers (interleaved complex = 2 reals per entry)
+th_status narrow(th_ctx& x, const double2* in, float2* out, long long n, cudaStream_t s) {
+  x.launches += 1;
+  return cuda_status(th::launch_d2f((const double*)in, (float*)out, 2 * n, s));
+}
+th_status widen(th_ctx& x, const float2* in, double2* out, long long n, int acc, cudaStream_t s) {
+  x.launches += 1;
+  return cuda_status(th::launch_f2d((const float*)in, (double*)out, 2 * n, acc, s));
+}
+
+// z = B v: the two-grid preconditioner (TwoGridStep with u = 0) in the active precision.
+th_status precondition(th_ctx& x, const double2* v, double2* z, int nrhs, cudaStream_t s) {
+  const long long n = x.g.N * (long long)nrhs;
+  if (x.active == TH_PREC_FP64) return cycle<double>(x, TH_PREC_FP64, v, z, true, nrhs, s);
+  th_status st;
+  if ((st = narrow(x, v, x.f32, n, s)) != TH_OK) return st;
+  if ((st = cycle<float>(x, x.active, x.f32, x.u32, true, nrhs, s)) != TH_OK) return st;
+  return widen(x, x.u32, z, n, 0, s);
+}
+
+th_status check_nrhs(const th_ctx* x, int nrhs) {
+  if (!x) return TH_ERR_ARG;
+  if (nrhs < 1 || nrhs > x->prm.nrhs_max) return TH_ERR_ARG;
+  return TH_OK;
+}
+
+th_status norms(th_ctx& x, const double2* w, int nrhs, std::vector<double>& out, cudaStream_t s) {
+  x.launches += 2;
+  TH_CU(th::launch_norm2(w, x.g.N, nrhs, x.npart, x.nrm, x.nblk, s));
+  out.resize(nrhs);
+  TH_CU(cudaMemcpyAsync(out.data(), x.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  TH_CU(cudaStreamSynchronize(s));
+  for (auto& v : out) v = std::sqrt(v);
+  return TH_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+const char* th_status_str(th_status s) {
+  switch (s) {
+    case TH_OK: return "ok";
+    case TH_ERR_ARG: return "invalid argument";
+    case TH_ERR_CUDA: return "CUDA error";
+    case TH_ERR_NOMEM: return "workspace too small or host allocation failed";
+    case TH_ERR_NOCONV: return "not converged within maxit";
+    case TH_ERR_BREAKDOWN: return "Krylov breakdown";
+    case TH_ERR_NONFINITE: return "non-finite value in a residual norm";
+    case TH_ERR_TIMEOUT: return "device wait timed out";
+    case TH_ERR_UNSUPPORTED: return "unsupported configuration";
+    case TH_ERR_SINGULAR: return "singular matrix in set-up";
+  }
+  return "unknown status";
+}
+
+th_status th_workspace_size(const th_mesh* mesh, const th_params* prm, size_t* bytes) {
+  if (!bytes) return TH_ERR_ARG;
+  th_ctx x;
+  th_status st = prepare(mesh, prm, x);
+  if (st != TH_OK) return st;
+  Carve c;
+  carve_all(x, c);
+  *bytes = c.used + 256;
+  return TH_OK;
+}
+
+th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_host, const th_params* prm,
+                   void* workspace_dev, size_t bytes, void* stream, th_ctx** out) {
+  if (!out || !k_host || !workspace_dev) return TH_ERR_ARG;
+  *out = nullptr;
+  std::unique_ptr<th_ctx> x(new (std::nothrow) th_ctx());
+  if (!x) return TH_ERR_NOMEM;
+  th_status st = prepare(mesh, prm, *x);
+  if (st != TH_OK) return st;
+  const th::Geometry& g = x->g;
+  const size_t n2 = (size_t)g.n * g.n;
+  for (size_t i = 0; i < n2; ++i) {
+    if (!std::isfinite(k_host[i]) || k_host[i] <= 0.0) return TH_ERR_ARG;
+    if (eps_host && (!std::isfinite(eps_host[i]) || eps_host[i] < 0.0)) return TH_ERR_ARG;
+  }
+  Carve c;
+  c.base = reinterpret_cast<char*>(workspace_dev);
+  c.cap = bytes;
+  if ((reinterpret_cast<uintptr_t>(workspace_dev) & 255u) != 0) return TH_ERR_ARG;
+  carve_all(*x, c);
+  if (!c.ok) return TH_ERR_NOMEM;
+  cudaStream_t s = S(stream);
+  std::vector<double> eps0;
+  const double* eps = eps_host;
+  if (!eps) {
+    eps0.assign(n2, 0.0);
+    eps = eps0.data();
+  }
+
+  // --- host FP64 set-up
+  th::TransferTables tt;
+  th::transfer_tables(g, x->ref, tt);
+  th::CoarseBlocks cb;
+  if ((st = th::coarse_setup(g, k_host, eps, cb)) != TH_OK) return st;
+  std::vector<cplx> Wh;
+  if ((st = th::all_inverse_rows(g, x->ref, k_host, eps, x->prm.alpha_s, Wh)) != TH_OK) return st;
+
+  // --- uploads (synchronous copies from host vectors)
+  auto up = [&](void* dst, const void* src, size_t nb) -> th_status {
+    if (!dst || nb == 0) return TH_OK;
+    return cuda_status(cudaMemcpyAsync(dst, src, nb, cudaMemcpyHostToDevice, s));
+  };
+  std::vector<int4> ctab(g.m);
+  for (int i = 0; i < g.m; ++i)
+    ctab[i] = make_int4(g.ctab[i * 4], g.ctab[i * 4 + 1], g.ctab[i * 4 + 2], g.ctab[i * 4 + 3]);
+  std::vector<float> kf(n2), ef(n2), pwf(tt.pw.size()), rwf(tt.rw.size());
+  for (size_t i = 0; i < n2; ++i) { kf[i] = (float)k_host[i]; ef[i] = (float)eps[i]; }
+  for (size_t i = 0; i < tt.pw.size(); ++i) pwf[i] = (float)tt.pw[i];
+  for (size_t i = 0; i < tt.rw.size(); ++i) rwf[i] = (float)tt.rw[i];
+  std::vector<double2> rho64(4 * (size_t)g.nc);
+  for (int sd = 0; sd < 4; ++sd)
+    for (int t = 0; t < g.nc; ++t) rho64[(size_t)sd * g.nc + t] = make_double2(cb.rho[sd][t].real(), cb.rho[sd][t].imag());
+  const size_t mm = (size_t)g.mc * g.mc;
+  auto to2 = [](const std::vector<cplx>& v) {
+    std::vector<double2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = make_double2(v[i].real(), v[i].imag());
+    return o;
+  };
+  auto to2f = [](const std::vector<cplx>& v) {
+    std::vector<float2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].real(), (float)v[i].imag());
+    return o;
+  };
+  std::vector<double2> cell64 = to2(cb.cell), cl64 = to2(cb.cl), cd64 = to2(cb.cd), cu64 = to2(cb.cu);
+  if ((st = up(x->kc64, k_host, n2 * 8)) != TH_OK) return st;
+  if ((st = up(x->ec64, eps, n2 * 8)) != TH_OK) return st;
+  if ((st = up(x->box, g.box.data(), g.box.size() * 4)) != TH_OK) return st;
+  if ((st = up(x->ctab, ctab.data(), ctab.size() * sizeof(int4))) != TH_OK) return st;
+  if ((st = up(x->pj0, tt.pj0.data(), tt.pj0.size() * 4)) != TH_OK) return st;
+  if ((st = up(x->pw64, tt.pw.data(), tt.pw.size() * 8)) != TH_OK) return st;
+  if ((st = up(x->ridx, tt.ridx.data(), tt.ridx.size() * 4)) != TH_OK) return st;
+  if ((st = up(x->rw64, tt.rw.data(), tt.rw.size() * 8)) != TH_OK) return st;
+  if ((st = up(x->ccell64, cell64.data(), cell64.size() * 16)) != TH_OK) return st;
+  if ((st = up(x->crho64, rho64.data(), rho64.size() * 16)) != TH_OK) return st;
+  if ((st = up(x->cl64, cl64.data(), mm * 16)) != TH_OK) return st;
+  if ((st = up(x->cd64, cd64.data(), mm * 16)) != TH_OK) return st;
+  if ((st = up(x->cu64, cu64.data(), mm * 16)) != TH_OK) return st;
+  std::vector<double2> G64h;
+  if (x->G64) {
+    G64h = to2(cb.G);
+    if ((st = up(x->G64, G64h.data(), G64h.size() * 16)) != TH_OK) return st;
+  }
+  std::vector<float2> cell32, rho32, cl32, cd32, cu32, G32;
+  if (x->mixed) {
+    cell32 = to2f(cb.cell);
+    cl32 = to2f(cb.cl);
+    cd32 = to2f(cb.cd);
+    cu32 = to2f(cb.cu);
+    G32 = to2f(cb.G);
+    rho32.resize(rho64.size());
+    for (size_t i = 0; i < rho64.size(); ++i) rho32[i] = make_float2((float)rho64[i].x, (float)rho64[i].y);
+    if ((st = up(x->kc32, kf.data(), n2 * 4)) != TH_OK) return st;
+    if ((st = up(x->ec32, ef.data(), n2 * 4)) != TH_OK) return st;
+    if ((st = up(x->pw32, pwf.data(), pwf.size() * 4)) != TH_OK) return st;
+    if ((st = up(x->rw32, rwf.data(), rwf.size() * 4)) != TH_OK) return st;
+    if ((st = up(x->ccell32, cell32.data(), cell32.size() * 8)) != TH_OK) return st;
+    if ((st = up(x->crho32, rho32.data(), rho32.size() * 8)) != TH_OK) return st;
+    if ((st = up(x->cl32, cl32.data(), mm * 8)) != TH_OK) return st;
+    if ((st = up(x->cd32, cd32.data(), mm * 8)) != TH_OK) return st;
+    if ((st = up(x->cu32, cu32.data(), mm * 8)) != TH_OK) return st;
+    if ((st = up(x->G32, G32.data(), G32.size() * 8)) != TH_OK) return st;
+  }
+  // inverse rows in the chunk-major layouts
+  const size_t blk = (size_t)g.NR * g.NC;
+  std::vector<uint4> stage;
+  std::vector<float> scale16;
+  for (int kind = 0; kind < 4; ++kind) {
+    if (!x->W[kind]) continue;
+    const int NCH = x->wchunks[kind];
+    stage.assign((size_t)g.nsub * NCH * g.NR, make_uint4(0, 0, 0, 0));
+    if (kind == TH_PREC_FP16) scale16.assign(g.nsub, 1.0f);
+    th::parallel_for(g.nsub, [&](int sub) {
+      const cplx* src = Wh.data() + blk * sub;
+      float sc = 1.0f;
+      if (kind == TH_PREC_FP16) {
+        double mx = 0.0;
+        for (size_t i = 0; i < blk; ++i) mx = std::max(mx, std::max(std::fabs(src[i].real()), std::fabs(src[i].imag())));
+        sc = mx > 0 ? (float)(mx / 4096.0) : 1.0f;
+        scale16[sub] = sc;
+      }
+      for (int ch = 0; ch < NCH; ++ch)
+        for (int r = 0; r < g.NR; ++r) {
+          uint4& o = stage[((size_t)sub * NCH + ch) * g.NR + r];
+          if (kind == TH_PREC_FP64) {
+            const cplx v = src[(size_t)r * g.NC + ch];
+            double2 d = make_double2(v.real(), v.imag());
+            std::memcpy(&o, &d, 16);
+          } else if (kind == TH_PREC_FP32) {
+            float f[4] = {0, 0, 0, 0};
+            for (int j = 0; j < 2; ++j) {
+              const int c = ch * 2 + j;
+              if (c < g.NC) {
+                f[2 * j] = (float)src[(size_t)r * g.NC + c].real();
+                f[2 * j + 1] = (float)src[(size_t)r * g.NC + c].imag();
+              }
+            }
+            std::memcpy(&o, f, 16);
+          } else {
+            uint32_t wv[4] = {0, 0, 0, 0};
+            for (int j = 0; j < 4; ++j) {
+              const int c = ch * 4 + j;
+              if (c >= g.NC) continue;
+              const cplx v = src[(size_t)r * g.NC + c];
+              if (kind == TH_PREC_BF16) {
+                wv[j] = (uint32_t)f2bf((float)v.real()) | ((uint32_t)f2bf((float)v.imag()) << 16);
+              } else {
+                __half hr = __float2half_rn((float)(v.real() / sc));
+                __half hi = __float2half_rn((float)(v.imag() / sc));
+                uint16_t a, b;
+                std::memcpy(&a, &hr, 2);
+                std::memcpy(&b, &hi, 2);
+                wv[j] = (uint32_t)a | ((uint32_t)b << 16);
+              }
+            }
+            std::memcpy(&o, wv, 16);
+          }
+        }
+    });
+    if ((st = up(x->W[kind], stage.data(), stage.size() * 16)) != TH_OK) return st;
+    if (kind == TH_PREC_FP16 && (st = up(x->wscale16, scale16.data(), scale16.size() * 4)) != TH_OK) return st;
+    // copies read host memory asynchronously: finish before the staging buffer is reused
+    TH_CU(cudaStreamSynchronize(s));
+  }
+  TH_CU(cudaStreamSynchronize(s));
+  *out = x.release();
+  return TH_OK;
+}
+
+th_status th_set_precision(th_ctx* x, int prec) {
+  if (!x || prec < 0 || prec > 3) return TH_ERR_ARG;
+  if (!has_prec(x->avail, prec)) return TH_ERR_UNSUPPORTED;
+  x->active = prec;
+  return TH_OK;
+}
+
+void th_destroy(th_ctx* x) { delete x; }
+
+th_status th_launch_count(const th_ctx* x, long long* n) {
+  if (!x || !n) return TH_ERR_ARG;
+  *n = x->launches;
+  return TH_OK;
+}
+
+th_status th_apply(th_ctx* x, int op, const double* xin, double* y, int nrhs, int prec, void* stream) {
+  th_status st = check_nrhs(x, nrhs);
+  if (st != TH_OK) return st;
+  if (!xin || !y || (prec != TH_PREC_FP64 && prec != TH_PREC_FP32)) return TH_ERR_ARG;
+  cudaStream_t s = S(stream);
+  const double2* in = reinterpret_cast<const double2*>(xin);
+  double2* out = reinterpret_cast<double2*>(y);
+  if (op == TH_OP_A || op == TH_OP_AS) {
+    if (prec == TH_PREC_FP64) return fine_apply<double>(*x, op, in, nullptr, out, nrhs, s);
+    if (!x->mixed) return TH_ERR_UNSUPPORTED;
+    const long long n = x->g.N * (long long)nrhs;
+    if ((st = narrow(*x, in, x->f32, n, s)) != TH_OK) return st;
+    if ((st = fine_apply<float>(*x, op, x->f32, nullptr, x->r32, nrhs, s)) != TH_OK) return st;
+    return widen(*x, x->r32, out, n, 0, s);
+  }
+  if (op == TH_OP_AQ) {
+    if (prec == TH_PREC_FP64) return coarse_apply_<double>(*x, in, out, nrhs, s);
+    if (!x->mixed) return TH_ERR_UNSUPPORTED;
+    const long long n = x->g.Nc * (long long)nrhs;
+    if ((st = narrow(*x, in, x->rc32, n, s)) != TH_OK) return st;
+    if ((st = coarse_apply_<float>(*x, x->rc32, x->uc32, nrhs, s)) != TH_OK) return st;
+    return widen(*x, x->uc32, out, n, 0, s);
+  }
+  return TH_ERR_ARG;
+}
+
+th_status th_residual(th_ctx* x, const double* f, const double* u, double* r, int nrhs, void* stream) {
+  th_status st = check_nrhs(x, nrhs);
+  if (st != TH_OK) return st;
+  if (!f || !u || !r) return TH_ERR_ARG;
+  return fine_apply<double>(*x, TH_OP_A, reinterpret_cast<const double2*>(u), reinterpret_cast<const double2*>(f),
+                            reinterpret_cast<double2*>(r), nrhs, S(stream));
+}
+
+th_status th_smooth(th_ctx* x, const double* f, double* u, int nrhs, void* stream) {
+  th_status st = check_nrhs(x, nrhs);
+  if (st != TH_OK) return st;
+  if (!f || !u) return TH_ERR_ARG;
+  cudaStream_t s = S(stream);
+  const double2* f2 = reinterpret_cast<const double2*>(f);
+  double2* u2 = reinterpret_cast<double2*>(u);
+  if (x->active == TH_PREC_FP64) return smooth<double>(*x, TH_PREC_FP64, f2, u2, false, nrhs, s);
+  // mixed: u += S(0, f - A u) in FP32
+  const long long n = x->g.N * (long long)nrhs;
+  if ((st = fine_apply<double>(*x, TH_OP_A, u2, f2, x->r64, nrhs, s)) != TH_OK) return st;
+  if ((st = narrow(*x, x->r64, x->f32, n, s)) != TH_OK) return st;
+  if ((st = smooth<float>(*x, x->active, x->f32, x->u32, true, nrhs, s)) != TH_OK) return st;
+  return widen(*x, x->u32, u2, n, 1, s);
+}
+
+th_status th_restrict(th_ctx* x, const double* r, double* rc, int nrhs, void* stream) {
+  th_status st = check_nrhs(x, nrhs);
+  if (st != TH_OK) return st;
+  if (!r || !rc) return TH_ERR_ARG;
+  return restrict_<double>(*x, reinterpret_cast<const double2*>(r), reinterpret_cast<double2*>(rc), nrhs, S(stream));
+}
+
+th_status th_prolong(th_ctx* x, const double* uc, double* u, double omega, int nrhs, void* stream) {
+  th_status st = check_nrhs(x, nrhs);
+  if (st != TH_OK) return st;
+  if (!uc || !u) return TH_ERR_ARG;
+  return prolong_<double>(*x, reinterpret_cast<const double2*>(uc), reinterpret_cast<double2*>(u), omega, nrhs,
+                          S(stream));
+}
+
+th_status th_coarse_solve(th_ctx* x, const double* rc, double* uc, int nrhs, void* stream) {
+  th_status st = check_nrhs(x, nrhs);
+  if (st != TH_OK) return st;
+  if (!rc || !uc) return TH_ERR_ARG;
+  cudaStream_t s = S(stream);
+  const double2* in = reinterpret_cast<const double2*>(rc);
+  double2* out = reinterpret_cast<double2*>(uc);
+  if (x->active == TH_PREC_FP64) return coarse_solve_<double>(*x, in, out, nrhs, s);
+  const long long n = x->g.Nc * (long long)nrhs;
+  if ((st = narrow(*x, in, x->rc32, n, s)) != TH_OK) return st;
+  if ((st = coarse_solve_<float>(*x, x->rc32, x->uc32, nrhs, s)) != TH_OK) return st;
+  return widen(*x, x->uc32, out, n, 0, s);
+}
+
+th_status th_cycle(th_ctx* x, const double* f, double* u, int nrhs, void* stream) {
+  th_status st = check_nrhs(x, nrhs);
+  if (st != TH_OK) return st;
+  if (!f || !u) return TH_ERR_ARG;
+  cudaStream_t s = S(stream);
+  const double2* f2 = reinterpret_cast<const double2*>(f);
+  double2* u2 = reinterpret_cast<double2*>(u);
+  if (x->active == TH_PREC_FP64) return cycle<double>(*x, TH_PREC_FP64, f2, u2, false, nrhs, s);
+  // mixed: TwoGridStep(u, f) = u + TwoGridStep(0, f - A u) (the step is affine in u and f)
+  const long long n = x->g.N * (long long)nrhs;
+  if ((st = fine_apply<double>(*x, TH_OP_A, u2, f2, x->r64, nrhs, s)) != TH_OK) return st;
+  if ((st = narrow(*x, x->r64, x->f32, n, s)) != TH_OK) return st;
+  if ((st = cycle<float>(*x, x->active, x->f32, x->u32, true, nrhs, s)) != TH_OK) return st;
+  return widen(*x, x->u32, u2, n, 1, s);
+}
+
+th_status th_cycle_host(th_ctx* x, const double* f_host, double* u_host, int nrhs, void* stream) {
+  th_status st = check_nrhs(x, nrhs);
+  if (st != TH_OK) return st;
+  if (!f_host || !u_host) return TH_ERR_ARG;
+  cudaStream_t s = S(stream);
+  const size_t nb = sizeof(double2) * x->g.N * (size_t)nrhs;
+  TH_CU(cudaMemcpyAsync(x->fin, f_host, nb, cudaMemcpyHostToDevice, s));
+  TH_CU(cudaMemcpyAsync(x->uin, u_host, nb, cudaMemcpyHostToDevice, s));
+  if ((st = th_cycle(x, (const double*)x->fin, (double*)x->uin, nrhs, stream)) != TH_OK) return st;
+  TH_CU(cudaMemcpyAsync(u_host, x->uin, nb, cudaMemcpyDeviceToHost, s));
+  TH_CU(cudaStreamSynchronize(s));
+  return TH_OK;
+}
+
+th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_info* info, void* stream) {
+  th_status st = check_nrhs(x, nrhs);
+  if (st != TH_OK) return st;
+  if (!f || !u) return TH_ERR_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = S(stream);
+  const th::Geometry& g = x->g;
+  const long long N = g.N;
+  const int m = x->prm.restart;
+  const long long vstride = N * (long long)nrhs;  // between basis vectors
+  const double2* f2 = reinterpret_cast<const double2*>(f);
+  double2* u2 = reinterpret_cast<double2*>(u);
+  const double tol = x->prm.tol;
+  std::vector<double> fn, beta, hn;
+  if ((st = norms(*x, f2, nrhs, fn, s)) != TH_OK) return st;
+  for (double v : fn)
+    if (!std::isfinite(v)) return TH_ERR_NONFINITE;
+  std::vector<int> done(nrhs, 0), its(nrhs, 0);
+  for (int r = 0; r < nrhs; ++r)
+    if (fn[r] == 0.0) done[r] = 1;
+  std::vector<cplx> H((size_t)nrhs * (m + 1) * m), cs((size_t)nrhs * m), sn((size_t)nrhs * m),
+      gg((size_t)nrhs * (m + 1));
+  std::vector<double2> hh1((size_t)nrhs * (m + 1)), hh2((size_t)nrhs * (m + 1));
+  std::vector<double> scal(nrhs);
+  std::vector<double2> yv;
+  int it = 0;
+  th_status result = TH_OK;
+  for (;;) {
+    // r = f - A x  -> V_0
+    if ((st = fine_apply<double>(*x, TH_OP_A, u2, f2, x->Vk, nrhs, s)) != TH_OK) return st;
+    if ((st = norms(*x, x->Vk, nrhs, beta, s)) != TH_OK) return st;
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) {
+      if (!std::isfinite(beta[r])) return TH_ERR_NONFINITE;
+      if (!done[r] && beta[r] <= tol * fn[r]) done[r] = 1;
+      all = all && done[r];
+    }
+    if (all || it >= x->prm.maxit) break;
+    std::vector<int> active(nrhs), jr(nrhs, 0);
+    for (int r = 0; r < nrhs; ++r) {
+      active[r] = !done[r];
+      scal[r] = active[r] ? 1.0 / beta[r] : 0.0;
+      std::fill(gg.begin() + (size_t)r * (m + 1), gg.begin() + (size_t)(r + 1) * (m + 1), cplx(0.0));
+      gg[(size_t)r * (m + 1)] = beta[r];
+    }
+    TH_CU(cudaMemcpyAsync(x->scal, scal.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    x->launches += 1;
+    TH_CU(th::launch_scale_rhs(x->Vk, x->Vk, x->scal, N, nrhs, s));
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      double2* Vj = x->Vk + (size_t)j * vstride;
+      double2* Zj = x->Zk + (size_t)j * vstride;
+      if ((st = precondition(*x, Vj, Zj, nrhs, s)) != TH_OK) return st;
+      if ((st = fine_apply<double>(*x, TH_OP_A, Zj, nullptr, x->w, nrhs, s)) != TH_OK) return st;
+      // classical Gram-Schmidt, twice
+      x->launches += 6;
+      TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, nrhs, x->dpart, x->h1, x->nblk, s));
+      TH_CU(th::launch_maxpy(x->Vk, vstride, x->h1, j + 1, x->w, N, j + 1, nrhs, -1.0, s));
+      TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, nrhs, x->dpart, x->h2, x->nblk, s));
+      TH_CU(th::launch_maxpy(x->Vk, vstride, x->h2, j + 1, x->w, N, j + 1, nrhs, -1.0, s));
+      TH_CU(cudaMemcpyAsync(hh1.data(), x->h1, sizeof(double2) * (j + 1) * nrhs, cudaMemcpyDeviceToHost, s));
+      TH_CU(cudaMemcpyAsync(hh2.data(), x->h2, sizeof(double2) * (j + 1) * nrhs, cudaMemcpyDeviceToHost, s));
+      if ((st = norms(*x, x->w, nrhs, hn, s)) != TH_OK) return st;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!std::isfinite(hn[r])) return TH_ERR_NONFINITE;
+        scal[r] = (active[r] && hn[r] > 0.0) ? 1.0 / hn[r] : 0.0;
+      }
+      TH_CU(cudaMemcpyAsync(x->scal, scal.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+      x->launches += 1;
+      TH_CU(th::launch_scale_rhs(x->w, x->Vk + (size_t)(j + 1) * vstride, x->scal, N, nrhs, s));
+      ++it;
+      jdone = j + 1;
+      bool any = false;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!active[r]) continue;
+        cplx* Hc = &H[((size_t)r * (m + 1)) * m];  // column-major (m+1) x m: Hc[i + j (m+1)]
+        for (int i = 0; i <= j; ++i) {
+          const double2 a1 = hh1[(size_t)r * (j + 1) + i], a2 = hh2[(size_t)r * (j + 1) + i];
+          Hc[i + (size_t)j * (m + 1)] = cplx(a1.x + a2.x, a1.y + a2.y);
+        }
+        Hc[j + 1 + (size_t)j * (m + 1)] = hn[r];
+        cplx* c_ = &cs[(size_t)r * m];
+        cplx* s_ = &sn[(size_t)r * m];
+        for (int i = 0; i < j; ++i) {
+          const cplx a = Hc[i + (size_t)j * (m + 1)], b = Hc[i + 1 + (size_t)j * (m + 1)];
+          Hc[i + (size_t)j * (m + 1)] = std::conj(c_[i]) * a + std::conj(s_[i]) * b;
+          Hc[i + 1 + (size_t)j * (m + 1)] = -s_[i] * a + c_[i] * b;
+        }
+        const cplx a = Hc[j + (size_t)j * (m + 1)], b = Hc[j + 1 + (size_t)j * (m + 1)];
+        const double den = std::sqrt(std::norm(a) + std::norm(b));
+        c_[j] = den > 0 ? a / den : cplx(1.0);
+        s_[j] = den > 0 ? b / den : cplx(0.0);
+        Hc[j + (size_t)j * (m + 1)] = den;
+        Hc[j + 1 + (size_t)j * (m + 1)] = 0.0;
+        cplx* gr = &gg[(size_t)r * (m + 1)];
+        gr[j + 1] = -s_[j] * gr[j];
+        gr[j] = std::conj(c_[j]) * gr[j];
+        its[r] = it;
+        jr[r] = j + 1;
+        if (std::abs(gr[j + 1]) <= tol * fn[r] || hn[r] == 0.0) {
+          active[r] = 0;
+        } else {
+          any = true;
+        }
+      }
+      if (!any || it >= x->prm.maxit) break;
+    }
+    // x += Z y per right-hand side (y = 0 beyond its own last step)
+    yv.assign((size_t)nrhs * jdone, make_double2(0, 0));
+    for (int r = 0; r < nrhs; ++r) {
+      const int jj = jr[r];
+      if (jj == 0) continue;
+      const cplx* Hc = &H[((size_t)r * (m + 1)) * m];
+      const cplx* gr = &gg[(size_t)r * (m + 1)];
+      std::vector<cplx> y(jj);
+      for (int i = jj - 1; i >= 0; --i) {
+        cplx sacc = gr[i];
+        for (int k = i + 1; k < jj; ++k) sacc -= Hc[i + (size_t)k * (m + 1)] * y[k];
+        const cplx d = Hc[i + (size_t)i * (m + 1)];
+        if (d == 0.0) return TH_ERR_BREAKDOWN;
+        y[i] = sacc / d;
+      }
+      for (int i = 0; i < jj; ++i) yv[(size_t)r * jdone + i] = make_double2(y[i].real(), y[i].imag());
+    }
+    TH_CU(cudaMemcpyAsync(x->ybuf, yv.data(), sizeof(double2) * yv.size(), cudaMemcpyHostToDevice, s));
+    x->launches += 1;
+    TH_CU(th::launch_maxpy(x->Zk, vstride, x->ybuf, jdone, u2, N, jdone, nrhs, 1.0, s));
+    TH_CU(cudaStreamSynchronize(s));
+  }
+  // final true residuals
+  if ((st = fine_apply<double>(*x, TH_OP_A, u2, f2, x->w, nrhs, s)) != TH_OK) return st;
+  std::vector<double> rn;
+  if ((st = norms(*x, x->w, nrhs, rn, s)) != TH_OK) return st;
+  double rmax = 0.0;
+  int nconv = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    const double rel = fn[r] > 0 ? rn[r] / fn[r] : 0.0;
+    rmax = std::max(rmax, rel);
+    if (rel <= tol * 1.0000001 || fn[r] == 0.0) ++nconv;
+  }
+  if (nconv < nrhs) result = TH_ERR_NOCONV;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = it;
+    info->converged = nconv;
+    info->relres_max = rmax;
+    for (int r = 0; r < nrhs && r < 64; ++r) info->iters_per_rhs[r] = its[r];
+    info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return result;
+}
+
+th_status th_solve_host(th_ctx* x, const double* f_host, double* u_host, int nrhs, th_solve_info* info,
+                        void* stream) {
+  th_status st = check_nrhs(x, nrhs);
+  if (st != TH_OK) return st;
+  if (!f_host || !u_host) return TH_ERR_ARG;
+  cudaStream_t s = S(stream);
+  const size_t nb = sizeof(double2) * x->g.N * (size_t)nrhs;
+  TH_CU(cudaMemcpyAsync(x->fin, f_host, nb, cudaMemcpyHostToDevice, s));
+  TH_CU(cudaMemcpyAsync(x->uin, u_host, nb, cudaMemcpyHostToDevice, s));
+  th_status rs = th_solve(x, (const double*)x->fin, (double*)x->uin, nrhs, info, stream);
+  if (rs != TH_OK && rs != TH_ERR_NOCONV) return rs;
+  TH_CU(cudaMemcpyAsync(u_host, x->uin, nb, cudaMemcpyDeviceToHost, s));
+  TH_CU(cudaStreamSynchronize(s));
+  return rs;
+}
+
+// ------------------------------------------------------------ host-only
+th_status th_host_reference_1d(int p, double* nodes, double* mass, double* stiff) {
+  if (p < 1 || p > th::kMaxP || !nodes || !mass || !stiff) return TH_ERR_ARG;
+  if (p % 2 != 0) return TH_ERR_ARG;
+  th::Ref1D r = th::reference_1d(p);
+  std::copy(r.nodes.begin(), r.nodes.end(), nodes);
+  std::copy(r.M.begin(), r.M.end(), mass);
+  std::copy(r.K.begin(), r.K.end(), stiff);
+  return TH_OK;
+}
+
+th_status th_host_qsfem_cell(double k, double eps, double hc, double* out) {
+  if (!out || !(k > 0) || !(hc > 0)) return TH_ERR_ARG;
+  cplx d[3];
+  th::qsfem_cell(k, eps, hc, d);
+  for (int i = 0; i < 3; ++i) {
+    out[2 * i] = d[i].real();
+    out[2 * i + 1] = d[i].imag();
+  }
+  return TH_OK;
+}
+
+th_status th_host_inverse_rows(const th_mesh* mesh, const double* k_host, const double* eps_host,
+                               const th_params* prm, int sub, int* box, double* out, size_t out_len) {
+  if (!mesh || !prm || !k_host || !box || !out) return TH_ERR_ARG;
+  th::Geometry g;
+  th_status st = th::make_geometry(*mesh, *prm, g);
+  if (st != TH_OK) return st;
+  if (sub < 0 || sub >= g.nsub) return TH_ERR_ARG;
+  if (out_len < (size_t)g.NR * g.NC * 2) return TH_ERR_NOMEM;
+  std::copy(&g.box[(size_t)sub * 8], &g.box[(size_t)sub * 8] + 8, box);
+  th::Ref1D ref = th::reference_1d(mesh->p);
+  std::vector<cplx> o((size_t)g.NR * g.NC);
+  if ((st = th::subdomain_inverse_rows(g, ref, k_host, eps_host, prm->alpha_s, sub, o.data())) != TH_OK) return st;
+  std::memcpy(out, o.data(), o.size() * sizeof(cplx));
+  return TH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,220 @@
+// K3/K4: the complex-shifted domain-decomposition smoother (Section 4.1,
+// Algorithm 2, Eq. RAS_like_update) applied with precomputed inverse rows.
+//
+// With v = 0 on entry (the first DDStep of a CSDDSmoother), the local solve
+// of subdomain i reduces to w_i = (A_s^(i))^{-1} R_i r, and only its values on
+// Dofs(U^(i)) are ever used.  The set-up stores exactly those rows, scaled by
+// 1/L_j, as W_i (NR x NC, NR = Lu^2 U-box nodes, NC = Lw^2 Omega-box nodes).
+//
+// K3 (k_dd_apply): per subdomain, gather x = R_i r (the Omega box of r, L2
+// resident) into shared memory and stream W_i from HBM: V_i = W_i x.  W_i is
+// stored chunk-major, [chunk][row] of 16-byte chunks holding CPC consecutive
+// columns of one row (CPC = 1 complex FP64, 2 FP32, 4 BF16/FP16), so a warp
+// reads 512 contiguous bytes per load.  Thread (row, g) accumulates the
+// chunks g, g + G, ... of its row; the G partial sums are added in a fixed
+// order.  Low-precision rows are widened to FP32 and accumulated in FP32.
+//
+// K4 (k_dd_combine): u_j (+)= sum over the (at most four) subdomains whose
+// U box holds j of V_i[j], in a fixed order (bitwise deterministic).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "kernels.h"
+
+namespace th {
+
+template <int KIND> struct WTraits;
+template <> struct WTraits<W_FP64> { static constexpr int CPC = 1; };
+template <> struct WTraits<W_FP32> { static constexpr int CPC = 2; };
+template <> struct WTraits<W_BF16> { static constexpr int CPC = 4; };
+template <> struct WTraits<W_FP16> { static constexpr int CPC = 4; };
+
+template <typename T, int KIND>
+__device__ __forceinline__ void unpack_chunk(const void* base, size_t idx, T* wr, T* wi) {
+  if constexpr (KIND == W_FP64) {
+    const double2 v = __ldcs(reinterpret_cast<const double2*>(base) + idx);
+    wr[0] = (T)v.x;
+    wi[0] = (T)v.y;
+  } else if constexpr (KIND == W_FP32) {
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(base) + idx);
+    wr[0] = v.x; wi[0] = v.y; wr[1] = v.z; wi[1] = v.w;
+  } else if constexpr (KIND == W_BF16) {
+    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(base) + idx);
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      wr[j] = __uint_as_float(w[j] << 16);
+      wi[j] = __uint_as_float(w[j] & 0xffff0000u);
+    }
+  } else {
+    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(base) + idx);
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __half2 h2 = *reinterpret_cast<const __half2*>(&w[j]);
+      float2 f = __half22float2(h2);
+      wr[j] = f.x;
+      wi[j] = f.y;
+    }
+  }
+}
+
+template <typename T, int KIND, int NRHS>
+__global__ void __launch_bounds__(512) k_dd_apply(const DDArgs<T> a) {
+  using C = typename Cx<T>::t;
+  constexpr int CPC = WTraits<KIND>::CPC;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int XL = a.NCH * CPC;
+  C* xs = reinterpret_cast<C*>(smraw);        // [NRHS][XL]
+  C* red = xs + NRHS * XL;                     // [G][NR][NRHS]
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int rr = tid % a.NR, g = tid / a.NR;
+  const int r0 = blockIdx.y * NRHS;
+  const int nr = min(NRHS, a.nrhs - r0);
+  for (int sub = blockIdx.x; sub < a.nsub; sub += gridDim.x) {
+    const int* bb = a.box + (size_t)sub * 8;
+    const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3];
+    for (int i = tid; i < NRHS * XL; i += nth) {
+      const int k = i / XL, c = i - k * XL;
+      const int cy = c / a.Lw, cx = c - cy * a.Lw;
+      C v;
+      v.x = 0;
+      v.y = 0;
+      if (k < nr && c < a.NC && cx < wx && cy < wy)
+        v = a.r[(size_t)(r0 + k) * a.N + (size_t)(oy + cy) * a.m + (ox + cx)];
+      xs[i] = v;
+    }
+    __syncthreads();
+    if (g < a.G) {
+      T acr[NRHS], aci[NRHS];
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) { acr[k] = 0; aci[k] = 0; }
+      const size_t wbase = (size_t)sub * a.NCH * a.NR + rr;
+#pragma unroll 4
+      for (int ch = g; ch < a.NCH; ch += a.G) {
+        T wr[CPC], wi[CPC];
+        unpack_chunk<T, KIND>(a.W, wbase + (size_t)ch * a.NR, wr, wi);
+#pragma unroll
+        for (int j = 0; j < CPC; ++j) {
+#pragma unroll
+          for (int k = 0; k < NRHS; ++k) {
+            const C xv = xs[k * XL + ch * CPC + j];
+            acr[k] += wr[j] * xv.x - wi[j] * xv.y;
+            aci[k] += wr[j] * xv.y + wi[j] * xv.x;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) {
+        C v;
+        v.x = acr[k];
+        v.y = aci[k];
+        red[((size_t)g * a.NR + rr) * NRHS + k] = v;
+      }
+    }
+    __syncthreads();
+    if (tid < a.NR) {
+      const T sc = a.wscale ? (T)a.wscale[sub] : (T)1;
+      for (int k = 0; k < nr; ++k) {
+        T sr = 0, si = 0;
+        for (int gg = 0; gg < a.G; ++gg) {
+          const C v = red[((size_t)gg * a.NR + tid) * NRHS + k];
+          sr += v.x;
+          si += v.y;
+        }
+        C o;
+        o.x = sr * sc;
+        o.y = si * sc;
+        a.V[((size_t)(r0 + k) * a.nsub + sub) * a.NR + tid] = o;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int KIND, int NRHS>
+static cudaError_t launch_dd_k(const DDArgs<T>& a, int grid_cap, cudaStream_t s) {
+  using C = typename Cx<T>::t;
+  constexpr int CPC = WTraits<KIND>::CPC;
+  const int threads = ((a.NR * a.G + 31) / 32) * 32;
+  if (threads > 512) return cudaErrorInvalidConfiguration;
+  const size_t smem = sizeof(C) * ((size_t)NRHS * a.NCH * CPC + (size_t)a.G * a.NR * NRHS);
+  cudaError_t e = cudaFuncSetAttribute(k_dd_apply<T, KIND, NRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int gx = (grid_cap > 0 && grid_cap < a.nsub) ? grid_cap : a.nsub;
+  dim3 grid(gx, (a.nrhs + NRHS - 1) / NRHS);
+  k_dd_apply<T, KIND, NRHS><<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int KIND>
+static cudaError_t launch_dd_kind(const DDArgs<T>& a, int grid_cap, cudaStream_t s) {
+  if (a.nrhs >= 4) return launch_dd_k<T, KIND, 4>(a, grid_cap, s);
+  if (a.nrhs >= 2) return launch_dd_k<T, KIND, 2>(a, grid_cap, s);
+  return launch_dd_k<T, KIND, 1>(a, grid_cap, s);
+}
+
+template <>
+cudaError_t launch_dd_apply<double>(const DDArgs<double>& a, int kind, int grid_cap, cudaStream_t s) {
+  if (kind != W_FP64) return cudaErrorInvalidValue;
+  return launch_dd_kind<double, W_FP64>(a, grid_cap, s);
+}
+
+template <>
+cudaError_t launch_dd_apply<float>(const DDArgs<float>& a, int kind, int grid_cap, cudaStream_t s) {
+  switch (kind) {
+    case W_FP32: return launch_dd_kind<float, W_FP32>(a, grid_cap, s);
+    case W_BF16: return launch_dd_kind<float, W_BF16>(a, grid_cap, s);
+    case W_FP16: return launch_dd_kind<float, W_FP16>(a, grid_cap, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ------------------------------------------------------------------- K4
+template <typename T>
+__global__ void __launch_bounds__(256) k_dd_combine(const CombineArgs<T> a) {
+  using C = typename Cx<T>::t;
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.N) return;
+  const int iy = (int)(j / a.m), ix = (int)(j - (long long)iy * a.m);
+  const int4 tx = a.ctab[ix], ty = a.ctab[iy];
+  const C* V = a.V + (size_t)blockIdx.y * a.nsub * a.NR;
+  T sr = 0, si = 0;
+  const int byl[2] = {ty.x, ty.z}, ryl[2] = {ty.y, ty.w};
+  const int bxl[2] = {tx.x, tx.z}, rxl[2] = {tx.y, tx.w};
+#pragma unroll
+  for (int jy = 0; jy < 2; ++jy) {
+    if (byl[jy] < 0) continue;
+#pragma unroll
+    for (int jx = 0; jx < 2; ++jx) {
+      if (bxl[jx] < 0) continue;
+      const C v = V[((size_t)byl[jy] * a.nb + bxl[jx]) * a.NR + ryl[jy] * a.Lu + rxl[jx]];
+      sr += v.x;
+      si += v.y;
+    }
+  }
+  C* u = a.u + (size_t)blockIdx.y * a.N;
+  C o;
+  if (a.accumulate) {
+    o = u[j];
+    o.x += sr;
+    o.y += si;
+  } else {
+    o.x = sr;
+    o.y = si;
+  }
+  u[j] = o;
+}
+
+template <typename T>
+cudaError_t launch_dd_combine(const CombineArgs<T>& a, int nrhs, cudaStream_t s) {
+  dim3 grid((unsigned)((a.N + 255) / 256), nrhs);
+  k_dd_combine<T><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_dd_combine<double>(const CombineArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_dd_combine<float>(const CombineArgs<float>&, int, cudaStream_t);
+
+}  // namespace th

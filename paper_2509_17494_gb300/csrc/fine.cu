@@ -1,0 +1,218 @@
+// K1/K2: matrix-free, sum-factorised apply of the fine Q_p operators A and A_s
+// (Section 3.1, Eq. bilin_form; the shifted coefficient of Section 4.1), fused
+// with the residual r = f - A u.
+//
+// Per cell e with local nodal values U[ay][ax]:
+//   Y = M T2 + (K + m_e M) T1,   T1 = U M^T,  T2 = U K^T (contractions along x),
+//   m_e = -(k_e^2 (1 + i alpha) + i eps_e) h^2,
+// plus -i k_e h M (1-D) on the nodes of absorbing boundary sides.
+// A CTA owns a TC x TC tile of cells and the nodes [cx0 p, (cx0+TC) p) of it
+// (the last tile also owns the closing node).  It stages the nodal values of
+// its cells and of the halo cell layer below/left of the tile in shared
+// memory, computes every cell matrix-vector product there, and sums the
+// contributions of the 1, 2 or 4 cells around each owned node in a fixed
+// order, so the result is bitwise deterministic.
+#include "kernels.h"
+
+namespace th {
+
+template <typename C, typename T>
+__device__ __forceinline__ C cmul(C a, T br, T bi) {
+  C r;
+  r.x = a.x * br - a.y * bi;
+  r.y = a.x * bi + a.y * br;
+  return r;
+}
+
+template <int P, int TC, typename T>
+__global__ void __launch_bounds__(256) k_fine_apply(const FineArgs<T> a) {
+  using C = typename Cx<T>::t;
+  constexpr int NP = P + 1, E = TC + 1, UT = E * P + 1, CELLS = E * E;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* su = reinterpret_cast<C*>(smraw);
+  C* s1 = su + UT * UT;
+  C* s2 = s1 + CELLS * NP * NP;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int cx0 = blockIdx.x * TC, cy0 = blockIdx.y * TC;
+  const int ex0 = cx0 - 1, ey0 = cy0 - 1;
+  const size_t roff = (size_t)blockIdx.z * a.N;
+  const C* u = a.u + roff;
+
+  for (int i = tid; i < UT * UT; i += nth) {
+    const int iy = i / UT, ix = i - iy * UT;
+    const int gx = ex0 * P + ix, gy = ey0 * P + iy;
+    C v;
+    v.x = 0;
+    v.y = 0;
+    if (gx >= 0 && gx < a.m && gy >= 0 && gy < a.m) v = u[(size_t)gy * a.m + gx];
+    su[i] = v;
+  }
+  __syncthreads();
+
+  // phase 1: x-contractions of every row of every (extended) cell
+  for (int it = tid; it < CELLS * NP; it += nth) {
+    const int e = it / NP, ay = it - e * NP;
+    const int ecy = e / E, ecx = e - ecy * E;
+    const int gcx = ex0 + ecx, gcy = ey0 + ecy;
+    if (gcx < 0 || gcx >= a.n || gcy < 0 || gcy >= a.n) continue;
+    const C* row = su + (ecy * P + ay) * UT + ecx * P;
+    C uv[NP];
+#pragma unroll
+    for (int b = 0; b < NP; ++b) uv[b] = row[b];
+#pragma unroll
+    for (int ax = 0; ax < NP; ++ax) {
+      T mr = 0, mi = 0, kr = 0, ki = 0;
+#pragma unroll
+      for (int b = 0; b < NP; ++b) {
+        const T mm = a.M[ax * NP + b], kk = a.K[ax * NP + b];
+        mr += mm * uv[b].x;
+        mi += mm * uv[b].y;
+        kr += kk * uv[b].x;
+        ki += kk * uv[b].y;
+      }
+      C t1, t2;
+      t1.x = mr; t1.y = mi;
+      t2.x = kr; t2.y = ki;
+      s1[(e * NP + ay) * NP + ax] = t1;
+      s2[(e * NP + ay) * NP + ax] = t2;
+    }
+  }
+  __syncthreads();
+
+  // phase 2: y-contractions, cell coefficient and absorbing boundary terms
+  for (int it = tid; it < CELLS * NP; it += nth) {
+    const int e = it / NP, ax = it - e * NP;
+    const int ecy = e / E, ecx = e - ecy * E;
+    const int gcx = ex0 + ecx, gcy = ey0 + ecy;
+    if (gcx < 0 || gcx >= a.n || gcy < 0 || gcy >= a.n) continue;
+    const size_t cell = (size_t)gcy * a.n + gcx;
+    const T kk = a.kc[cell], ee = a.ec[cell];
+    const T me_r = -kk * kk * a.h2, me_i = -(a.alpha * kk * kk + ee) * a.h2;
+    C t1[NP], z[NP];
+#pragma unroll
+    for (int b = 0; b < NP; ++b) {
+      t1[b] = s1[(e * NP + b) * NP + ax];
+      const C t2 = s2[(e * NP + b) * NP + ax];
+      const C mt = cmul(t1[b], me_r, me_i);
+      z[b].x = t2.x + mt.x;
+      z[b].y = t2.y + mt.y;
+    }
+    C yv[NP];
+#pragma unroll
+    for (int ay = 0; ay < NP; ++ay) {
+      T yr = 0, yi = 0;
+#pragma unroll
+      for (int b = 0; b < NP; ++b) {
+        const T mm = a.M[ay * NP + b], kq = a.K[ay * NP + b];
+        yr += mm * z[b].x + kq * t1[b].x;
+        yi += mm * z[b].y + kq * t1[b].y;
+      }
+      yv[ay].x = yr;
+      yv[ay].y = yi;
+    }
+    // -i k h M on absorbing sides: rho * (x + i y) = k h y - i k h x
+    const T kh = kk * a.h;
+    if (gcy == 0 && (a.robin & 4)) { yv[0].x += kh * t1[0].y; yv[0].y -= kh * t1[0].x; }
+    if (gcy == a.n - 1 && (a.robin & 8)) { yv[P].x += kh * t1[P].y; yv[P].y -= kh * t1[P].x; }
+    if ((ax == 0 && gcx == 0 && (a.robin & 1)) || (ax == P && gcx == a.n - 1 && (a.robin & 2))) {
+      const C* col = su + (ecy * P) * UT + ecx * P + ax;
+#pragma unroll
+      for (int ay = 0; ay < NP; ++ay) {
+        T sr = 0, si = 0;
+#pragma unroll
+        for (int b = 0; b < NP; ++b) {
+          const T mm = a.M[ay * NP + b];
+          sr += mm * col[b * UT].x;
+          si += mm * col[b * UT].y;
+        }
+        yv[ay].x += kh * si;
+        yv[ay].y -= kh * sr;
+      }
+    }
+#pragma unroll
+    for (int ay = 0; ay < NP; ++ay) s2[(e * NP + ay) * NP + ax] = yv[ay];
+  }
+  __syncthreads();
+
+  // phase 3: owned nodes sum their cells in a fixed order
+  const int ncx = min(TC, a.n - cx0), ncy = min(TC, a.n - cy0);
+  const int wx = ncx * P + ((cx0 + ncx == a.n) ? 1 : 0);
+  const int wy = ncy * P + ((cy0 + ncy == a.n) ? 1 : 0);
+  C* y = a.y + roff;
+  const C* f = a.f ? a.f + roff : nullptr;
+  for (int i = tid; i < wx * wy; i += nth) {
+    const int ly = i / wx, lx = i - ly * wx;
+    const int ux = lx + P, uy = ly + P;
+    int exs[2], axs[2], eys[2], ays[2];
+    int nxc = 0, nyc = 0;
+    if (ux % P == 0) {
+      exs[nxc] = ux / P - 1; axs[nxc++] = P;
+      exs[nxc] = ux / P;     axs[nxc++] = 0;
+    } else {
+      exs[nxc] = ux / P; axs[nxc++] = ux % P;
+    }
+    if (uy % P == 0) {
+      eys[nyc] = uy / P - 1; ays[nyc++] = P;
+      eys[nyc] = uy / P;     ays[nyc++] = 0;
+    } else {
+      eys[nyc] = uy / P; ays[nyc++] = uy % P;
+    }
+    T ar = 0, ai = 0;
+    for (int jy = 0; jy < nyc; ++jy) {
+      const int ey = eys[jy], gcy = ey0 + ey;
+      if (ey >= E || gcy < 0 || gcy >= a.n) continue;
+      for (int jx = 0; jx < nxc; ++jx) {
+        const int ex = exs[jx], gcx = ex0 + ex;
+        if (ex >= E || gcx < 0 || gcx >= a.n) continue;
+        const C v = s2[((ey * E + ex) * NP + ays[jy]) * NP + axs[jx]];
+        ar += v.x;
+        ai += v.y;
+      }
+    }
+    const size_t g = (size_t)(cy0 * P + ly) * a.m + (cx0 * P + lx);
+    C out;
+    if (f) {
+      const C fv = f[g];
+      out.x = fv.x - ar;
+      out.y = fv.y - ai;
+    } else {
+      out.x = ar;
+      out.y = ai;
+    }
+    y[g] = out;
+  }
+}
+
+template <int P, int TC, typename T>
+static cudaError_t launch_fine_p(const FineArgs<T>& a, int nrhs, cudaStream_t s) {
+  using C = typename Cx<T>::t;
+  constexpr int NP = P + 1, E = TC + 1, UT = E * P + 1;
+  const size_t smem = sizeof(C) * (size_t)(UT * UT + 2 * E * E * NP * NP);
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_fine_apply<P, TC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int tiles = (a.n + TC - 1) / TC;
+  dim3 grid(tiles, tiles, nrhs);
+  k_fine_apply<P, TC, T><<<grid, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fine_apply(const FineArgs<T>& a, int nrhs, cudaStream_t s) {
+  switch (a.p) {
+    case 2: return launch_fine_p<2, 16, T>(a, nrhs, s);
+    case 4: return launch_fine_p<4, 8, T>(a, nrhs, s);
+    case 6: return launch_fine_p<6, 5, T>(a, nrhs, s);
+    case 8: return launch_fine_p<8, 4, T>(a, nrhs, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_fine_apply<double>(const FineArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_fine_apply<float>(const FineArgs<float>&, int, cudaStream_t);
+
+}  // namespace th

@@ -1,0 +1,129 @@
+// Kernel argument blocks and host launchers (device code lives in the .cu files).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace th {
+
+template <typename T> struct Cx;
+template <> struct Cx<double> { using t = double2; };
+template <> struct Cx<float> { using t = float2; };
+
+// ---------------------------------------------------------------- K1 fine apply
+template <typename T>
+struct FineArgs {
+  const typename Cx<T>::t* u;
+  const typename Cx<T>::t* f;  // used when residual != 0
+  typename Cx<T>::t* y;
+  const T* kc;                 // k per cell
+  const T* ec;                 // eps per cell
+  long long N;                 // stride between right-hand sides
+  int n, m, p;
+  int robin;                   // bit s set = side s absorbing (x lo, x hi, y lo, y hi)
+  int residual;                // 0: y = OP u;  1: y = f - OP u
+  T h, h2, alpha;              // alpha = shift (0 for A)
+  T M[81], K[81];              // 1-D reference mass / stiffness, (p+1)^2
+};
+template <typename T>
+cudaError_t launch_fine_apply(const FineArgs<T>& a, int nrhs, cudaStream_t s);
+
+// ------------------------------------------------------- K3 DD block apply
+enum WKind { W_FP64 = 0, W_FP32 = 1, W_BF16 = 2, W_FP16 = 3 };
+template <typename T>
+struct DDArgs {
+  const typename Cx<T>::t* r;   // residual, [rhs][N]
+  typename Cx<T>::t* V;         // per-subdomain results, [rhs][nsub][NR]
+  const void* W;                // inverse rows, [sub][chunk][NR] 16-byte chunks
+  const int* box;               // 8 ints per subdomain
+  const float* wscale;          // per-subdomain scale (FP16 rows), or null
+  long long N;
+  int nsub, m, Lw, NC, NCH, NR, G, nrhs;
+};
+template <typename T>
+cudaError_t launch_dd_apply(const DDArgs<T>& a, int kind, int grid_cap, cudaStream_t s);
+
+// ------------------------------------------------------- K4 DD combine
+template <typename T>
+struct CombineArgs {
+  const typename Cx<T>::t* V;   // [rhs][nsub][NR]
+  typename Cx<T>::t* u;         // [rhs][N]
+  const int4* ctab;             // per 1-D node: (b0, r0, b1, r1)
+  long long N;
+  int m, nb, Lu, NR, nsub, accumulate;
+};
+template <typename T>
+cudaError_t launch_dd_combine(const CombineArgs<T>& a, int nrhs, cudaStream_t s);
+
+// ------------------------------------------------------- K5/K6 transfers
+template <typename T>
+struct TransferArgs {
+  const typename Cx<T>::t* in;
+  typename Cx<T>::t* out;
+  const int* pj0;  const T* pw;                        // prolongation tables (per fine 1-D node)
+  const int* ridx; const T* rw; int rmax;              // restriction tables (per coarse 1-D node)
+  long long N, Nc;
+  int m, mc, q;
+  T omega;
+};
+template <typename T>
+cudaError_t launch_restrict(const TransferArgs<T>& a, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong(const TransferArgs<T>& a, int nrhs, cudaStream_t s);
+
+// ------------------------------------------------------- K7 coarse apply
+template <typename T>
+struct CoarseApplyArgs {
+  const typename Cx<T>::t* x;
+  typename Cx<T>::t* y;
+  const typename Cx<T>::t* cell;   // nc^2 x 3 (d0, d1, d2)
+  const typename Cx<T>::t* rho;    // 4 x nc (per side), zero where Neumann
+  long long Nc;
+  int nc, mc;
+};
+template <typename T>
+cudaError_t launch_coarse_apply(const CoarseApplyArgs<T>& a, int nrhs, cudaStream_t s);
+
+// ------------------------------------------------------- K8 coarse solve
+template <typename T>
+struct CoarseSolveArgs {
+  const typename Cx<T>::t* rhs;    // [rhs][Nc]
+  typename Cx<T>::t* x;            // [rhs][Nc]
+  typename Cx<T>::t* z;            // scratch [rhs][Nc]
+  const typename Cx<T>::t* G;      // mc blocks of mc x mc
+  const typename Cx<T>::t* cl;     // C_j diagonals, mc x mc
+  const typename Cx<T>::t* cd;
+  const typename Cx<T>::t* cu;
+  long long Nc;
+  int mc, rpc;                     // rows per CTA
+};
+template <typename T>
+cudaError_t launch_coarse_solve(const CoarseSolveArgs<T>& a, int nrhs, int cluster, cudaStream_t s);
+
+// ------------------------------------------------------- vectors (K9/K10)
+cudaError_t launch_d2f(const double* in, float* out, long long n, cudaStream_t s);
+cudaError_t launch_f2d(const float* in, double* out, long long n, int accumulate, cudaStream_t s);
+// y[r] = a * x[r] + b * y[r] (complex a per rhs from device array, b real); generic axpby on complex vectors
+cudaError_t launch_zaxpy_f64(const double2* x, double2* y, double alpha, long long n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_zaxpy(const typename Cx<T>::t* x, typename Cx<T>::t* y, T alpha, long long n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_zero(typename Cx<T>::t* x, long long n, cudaStream_t s);
+
+// multi-dot: h[rhs][i] = sum_n conj(V_i[rhs][n]) w[rhs][n], i = 0..nv-1, V_i at Vbase + i*vstride.
+// partial sums in `part` ([rhs][nv][nblk]) then a fixed-order reduction.
+int mdot_blocks(long long N);
+cudaError_t launch_mdot(const double2* Vbase, long long vstride, const double2* w, long long N,
+                        int nv, int nrhs, double2* part, double2* h, int nblk, cudaStream_t s);
+// w[rhs] -= sum_i h[rhs][i] V_i[rhs]  (sign = -1) or += (sign = +1)
+cudaError_t launch_maxpy(const double2* Vbase, long long vstride, const double2* h, int hstride,
+                         double2* w, long long N, int nv, int nrhs, double sign, cudaStream_t s);
+// nrm2[rhs] = ||w[rhs]||^2 (fixed-order two-pass reduction into part/out)
+cudaError_t launch_norm2(const double2* w, long long N, int nrhs, double* part, double* out,
+                         int nblk, cudaStream_t s);
+// out[rhs] = in[rhs] * scale[rhs] (real scale per rhs from a device array; 0 if scale is not finite)
+cudaError_t launch_scale_rhs(const double2* in, double2* out, const double* inv, long long N, int nrhs,
+                             cudaStream_t s);
+
+}  // namespace th

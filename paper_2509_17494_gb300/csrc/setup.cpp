@@ -1,0 +1,636 @@
+// Host-side FP64 set-up of the two-grid Helmholtz library.
+//
+//  * 1-D reference element (Section 3.1): GLL nodes by Newton iteration on
+//    P_p', exact mass/stiffness with a (p+2)-point Gauss-Legendre rule, the
+//    derivatives through the barycentric differentiation matrix.
+//  * Partition and overlapping subdomains (Section 4.1, Section 4.5).
+//  * Subdomain matrices A_s^(i) (shifted volume coefficient, unshifted -i k
+//    on internal boundaries, inherited conditions elsewhere) and their
+//    inverse rows on the dofs of U^(i), scaled by 1/L_j (Eq. RAS_like_update),
+//    by a banded LU with partial pivoting.
+//  * QSFEM coarse cell coefficients (Eq. P_QSFEM, Eq. scaling_factor_QSFEM,
+//    Eq. element_wise_qsfem) and the block-tridiagonal factorisation of A_q
+//    by coarse grid rows.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+
+#include "th_internal.h"
+
+namespace th {
+
+// ------------------------------------------------------------------ threads
+void parallel_for(int n, const std::function<void(int)>& f) {
+  unsigned hw = std::thread::hardware_concurrency();
+  int nt = (int)std::max(1u, std::min(hw == 0 ? 4u : hw, 64u));
+  nt = std::min(nt, n);
+  if (nt <= 1) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int> next(0);
+  std::vector<std::thread> pool;
+  pool.reserve(nt);
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([&]() {
+      for (;;) {
+        int i = next.fetch_add(1);
+        if (i >= n) break;
+        f(i);
+      }
+    });
+  for (auto& th : pool) th.join();
+}
+
+// ------------------------------------------------------------- 1-D element
+static void legendre_pd(int n, double x, double& P, double& dP) {
+  // P_n(x) and P_n'(x) by the three-term recurrence (|x| < 1 for dP)
+  double p0 = 1.0, p1 = x;
+  if (n == 0) { P = 1.0; dP = 0.0; return; }
+  for (int k = 2; k <= n; ++k) {
+    double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    p0 = p1;
+    p1 = p2;
+  }
+  P = p1;
+  dP = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+static void gauss_rule(int nq, std::vector<double>& x, std::vector<double>& w) {
+  // nq-point Gauss-Legendre on [0,1]
+  x.resize(nq);
+  w.resize(nq);
+  for (int i = 0; i < nq; ++i) {
+    double t = std::cos(M_PI * (i + 0.75) / (nq + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre_pd(nq, t, P, dP);
+      double dt = P / dP;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    double P, dP;
+    legendre_pd(nq, t, P, dP);
+    x[i] = 0.5 * (1.0 - t);
+    w[i] = 1.0 / ((1.0 - t * t) * dP * dP);  // (2 / ((1-t^2) P'^2)) / 2
+  }
+}
+
+static std::vector<double> gll_nodes(int p) {
+  std::vector<double> x(p + 1);
+  x[0] = -1.0;
+  x[p] = 1.0;
+  for (int i = 1; i < p; ++i) {
+    double t = -std::cos(M_PI * i / p);
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre_pd(p, t, P, dP);
+      double d2P = (2.0 * t * dP - p * (p + 1.0) * P) / (1.0 - t * t);
+      double dt = dP / d2P;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    x[i] = t;
+  }
+  std::sort(x.begin(), x.end());
+  for (auto& v : x) v = 0.5 * (v + 1.0);
+  return x;
+}
+
+static double lagrange_value(const std::vector<double>& nodes, int a, double x) {
+  double v = 1.0;
+  for (size_t b = 0; b < nodes.size(); ++b)
+    if ((int)b != a) v *= (x - nodes[b]) / (nodes[a] - nodes[b]);
+  return v;
+}
+
+Ref1D reference_1d(int p) {
+  Ref1D r;
+  r.p = p;
+  r.nodes = gll_nodes(p);
+  const int np = p + 1;
+  // barycentric weights and the nodal differentiation matrix D[i][j] = l_j'(x_i)
+  std::vector<double> lam(np, 1.0);
+  for (int j = 0; j < np; ++j)
+    for (int k = 0; k < np; ++k)
+      if (k != j) lam[j] /= (r.nodes[j] - r.nodes[k]);
+  std::vector<double> D(np * np, 0.0);
+  for (int i = 0; i < np; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < np; ++j)
+      if (j != i) {
+        D[i * np + j] = (lam[j] / lam[i]) / (r.nodes[i] - r.nodes[j]);
+        s += D[i * np + j];
+      }
+    D[i * np + i] = -s;
+  }
+  std::vector<double> xq, wq;
+  gauss_rule(p + 2, xq, wq);  // exact for degree 2p + 3
+  const int nq = (int)xq.size();
+  std::vector<double> V(nq * np), Vd(nq * np, 0.0);
+  for (int q = 0; q < nq; ++q)
+    for (int a = 0; a < np; ++a) V[q * np + a] = lagrange_value(r.nodes, a, xq[q]);
+  // l_a'(x_q) = sum_i l_i(x_q) D[i][a]  (l_a' has degree p-1, interpolated exactly)
+  for (int q = 0; q < nq; ++q)
+    for (int a = 0; a < np; ++a) {
+      double s = 0.0;
+      for (int i = 0; i < np; ++i) s += V[q * np + i] * D[i * np + a];
+      Vd[q * np + a] = s;
+    }
+  r.M.assign(np * np, 0.0);
+  r.K.assign(np * np, 0.0);
+  for (int a = 0; a < np; ++a)
+    for (int b = 0; b < np; ++b) {
+      double sm = 0.0, sk = 0.0;
+      for (int q = 0; q < nq; ++q) {
+        sm += wq[q] * V[q * np + a] * V[q * np + b];
+        sk += wq[q] * Vd[q * np + a] * Vd[q * np + b];
+      }
+      r.M[a * np + b] = sm;
+      r.K[a * np + b] = sk;
+    }
+  // degree-p/2 interpolation through p/2+1 equispaced points, evaluated at the GLL nodes
+  const int q = p / 2;
+  std::vector<double> eq(q + 1);
+  for (int b = 0; b <= q; ++b) eq[b] = (double)b / q;
+  r.Pw.assign(np * (q + 1), 0.0);
+  for (int a = 0; a < np; ++a)
+    for (int b = 0; b <= q; ++b) r.Pw[a * (q + 1) + b] = lagrange_value(eq, b, r.nodes[a]);
+  // exact end-point values (Lagrange property at shared vertices)
+  for (int b = 0; b <= q; ++b) {
+    r.Pw[0 * (q + 1) + b] = (b == 0) ? 1.0 : 0.0;
+    r.Pw[p * (q + 1) + b] = (b == q) ? 1.0 : 0.0;
+  }
+  return r;
+}
+
+// --------------------------------------------------------------- partition
+Block1D partition_1d(int n, int l_dd) {
+  Block1D b;
+  int nb = (n + l_dd - 1) / l_dd;
+  int base = n / nb, rem = n % nb;
+  int s = 0;
+  for (int i = 0; i < nb; ++i) {
+    int z = base + (i < rem ? 1 : 0);
+    b.start.push_back(s);
+    b.size.push_back(z);
+    s += z;
+  }
+  return b;
+}
+
+th_status make_geometry(const th_mesh& mesh, const th_params& prm, Geometry& g) {
+  if (mesh.dim != 2) return TH_ERR_UNSUPPORTED;
+  if (mesh.n < 1 || mesh.n > 4096) return TH_ERR_ARG;
+  if (mesh.p < 2 || mesh.p > kMaxP || (mesh.p % 2) != 0) return TH_ERR_ARG;
+  for (int s = 0; s < 4; ++s) {
+    if (mesh.bc[s] == TH_BC_DIRICHLET) return TH_ERR_UNSUPPORTED;
+    if (mesh.bc[s] != TH_BC_ROBIN && mesh.bc[s] != TH_BC_NEUMANN) return TH_ERR_ARG;
+  }
+  if (prm.l_dd < 1 || prm.n_dd < 1 || prm.n_s < 1) return TH_ERR_ARG;
+  if (prm.restart < 1 || prm.maxit < 0 || prm.nrhs_max < 1 || prm.nrhs_max > 4096) return TH_ERR_ARG;
+  if (prm.prec < TH_PREC_FP64 || prm.prec > TH_PREC_FP16) return TH_ERR_ARG;
+  if (!(prm.tol >= 0.0) || !std::isfinite(prm.alpha_s) || !std::isfinite(prm.omega_c)) return TH_ERR_ARG;
+  g.n = mesh.n;
+  g.p = mesh.p;
+  g.q = mesh.p / 2;
+  g.m = g.n * g.p + 1;
+  g.N = (long long)g.m * g.m;
+  g.nc = g.n * g.q;
+  g.mc = g.nc + 1;
+  g.Nc = (long long)g.mc * g.mc;
+  g.h = 1.0 / g.n;
+  g.hc = 1.0 / g.nc;
+  for (int s = 0; s < 4; ++s) g.robin[s] = (mesh.bc[s] == TH_BC_ROBIN);
+  g.l_dd = std::min(prm.l_dd, g.n);
+  g.blk = partition_1d(g.n, g.l_dd);
+  g.nb = (int)g.blk.start.size();
+  g.nsub = g.nb * g.nb;
+  int lmax = *std::max_element(g.blk.size.begin(), g.blk.size.end());
+  g.Lu = lmax * g.p + 1;
+  g.Lw = std::min(lmax + 2, g.n) * g.p + 1;
+  g.NR = g.Lu * g.Lu;
+  g.NC = g.Lw * g.Lw;
+  // boxes
+  std::vector<int> o0(g.nb), o1(g.nb);
+  for (int b = 0; b < g.nb; ++b) {
+    o0[b] = std::max(g.blk.start[b] - 1, 0);
+    o1[b] = std::min(g.blk.start[b] + g.blk.size[b] + 1, g.n);
+  }
+  g.box.resize((size_t)g.nsub * 8);
+  for (int by = 0; by < g.nb; ++by)
+    for (int bx = 0; bx < g.nb; ++bx) {
+      int* bb = &g.box[((size_t)by * g.nb + bx) * 8];
+      bb[0] = o0[bx] * g.p;
+      bb[1] = o0[by] * g.p;
+      bb[2] = (o1[bx] - o0[bx]) * g.p + 1;
+      bb[3] = (o1[by] - o0[by]) * g.p + 1;
+      bb[4] = g.blk.start[bx] * g.p;
+      bb[5] = g.blk.start[by] * g.p;
+      bb[6] = g.blk.size[bx] * g.p + 1;
+      bb[7] = g.blk.size[by] * g.p + 1;
+    }
+  // 1-D combine table and multiplicity
+  g.ctab.assign((size_t)g.m * 4, -1);
+  g.mult1d.assign(g.m, 0);
+  for (int b = 0; b < g.nb; ++b) {
+    int lo = g.blk.start[b] * g.p, hi = (g.blk.start[b] + g.blk.size[b]) * g.p;
+    for (int i = lo; i <= hi; ++i) {
+      int c = g.mult1d[i]++;
+      g.ctab[(size_t)i * 4 + 2 * c] = b;
+      g.ctab[(size_t)i * 4 + 2 * c + 1] = i - lo;
+    }
+  }
+  return TH_OK;
+}
+
+// ------------------------------------------------------ subdomain matrices
+// Banded LU with partial pivoting on dense row-major storage (LAPACK gbtrf
+// semantics: the interchange of step k is applied to the right-hand side
+// just before the elimination of step k).
+static bool band_lu(cplx* A, int n, int kl, int ku, std::vector<int>& piv) {
+  piv.resize(n);
+  for (int k = 0; k < n; ++k) {
+    int rmax = std::min(n - 1, k + kl);
+    int pr = k;
+    double best = std::abs(A[(size_t)k * n + k]);
+    for (int r = k + 1; r <= rmax; ++r) {
+      double v = std::abs(A[(size_t)r * n + k]);
+      if (v > best) { best = v; pr = r; }
+    }
+    if (best == 0.0) return false;
+    piv[k] = pr;
+    int cmax = std::min(n - 1, k + kl + ku);
+    if (pr != k)
+      for (int c = k; c <= cmax; ++c) std::swap(A[(size_t)k * n + c], A[(size_t)pr * n + c]);
+    cplx inv = 1.0 / A[(size_t)k * n + k];
+    const cplx* rowk = A + (size_t)k * n;
+    for (int r = k + 1; r <= rmax; ++r) {
+      cplx* rowr = A + (size_t)r * n;
+      cplx l = rowr[k] * inv;
+      rowr[k] = l;
+      if (l == 0.0) continue;
+      for (int c = k + 1; c <= cmax; ++c) rowr[c] -= l * rowk[c];
+    }
+  }
+  return true;
+}
+
+static void band_solve(const cplx* A, int n, int kl, int ku, const std::vector<int>& piv, cplx* b) {
+  for (int k = 0; k < n; ++k) {
+    if (piv[k] != k) std::swap(b[k], b[piv[k]]);
+    cplx bk = b[k];
+    if (bk == 0.0) continue;
+    int rmax = std::min(n - 1, k + kl);
+    for (int r = k + 1; r <= rmax; ++r) b[r] -= A[(size_t)r * n + k] * bk;
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    int cmax = std::min(n - 1, k + kl + ku);
+    cplx s = b[k];
+    for (int c = k + 1; c <= cmax; ++c) s -= A[(size_t)k * n + c] * b[c];
+    b[k] = s / A[(size_t)k * n + k];
+  }
+}
+
+th_status subdomain_inverse_rows(const Geometry& g, const Ref1D& ref, const double* k,
+                                 const double* eps, double alpha_s, int sub, cplx* out) {
+  const int* bb = &g.box[(size_t)sub * 8];
+  const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3];
+  const int ux = bb[4], uy = bb[5], vx = bb[6], vy = bb[7];
+  const int p = g.p, np = p + 1;
+  const int ncx = (wx - 1) / p, ncy = (wy - 1) / p;
+  const int c0x = ox / p, c0y = oy / p;
+  const int nd = wx * wy;
+  std::vector<cplx> A((size_t)nd * nd, 0.0);
+  const double h = g.h;
+  // volume terms: stiffness K(x)M(y) + M(x)K(y), shifted mass -(k^2 (1 + i a) + i eps) h^2 M M
+  for (int cy = 0; cy < ncy; ++cy)
+    for (int cx = 0; cx < ncx; ++cx) {
+      const size_t cell = (size_t)(c0y + cy) * g.n + (c0x + cx);
+      const double kk = k[cell], ee = eps ? eps[cell] : 0.0;
+      const cplx me = -cplx(kk * kk, alpha_s * kk * kk + ee) * (h * h);
+      for (int ay = 0; ay < np; ++ay)
+        for (int ax = 0; ax < np; ++ax) {
+          const int row = (cy * p + ay) * wx + cx * p + ax;
+          for (int by = 0; by < np; ++by)
+            for (int bx = 0; bx < np; ++bx) {
+              const int col = (cy * p + by) * wx + cx * p + bx;
+              const double mm = ref.M[ay * np + by] * ref.M[ax * np + bx];
+              const double st = ref.M[ay * np + by] * ref.K[ax * np + bx] + ref.K[ay * np + by] * ref.M[ax * np + bx];
+              A[(size_t)row * nd + col] += st + me * mm;
+            }
+        }
+    }
+  // absorbing sides: internal sides of Omega^(i), and Robin sides of the domain
+  const bool at_lo_x = (c0x == 0), at_hi_x = (c0x + ncx == g.n);
+  const bool at_lo_y = (c0y == 0), at_hi_y = (c0y + ncy == g.n);
+  const bool side_abs[4] = {at_lo_x ? (bool)g.robin[0] : true, at_hi_x ? (bool)g.robin[1] : true,
+                            at_lo_y ? (bool)g.robin[2] : true, at_hi_y ? (bool)g.robin[3] : true};
+  for (int s = 0; s < 4; ++s) {
+    if (!side_abs[s]) continue;
+    const bool xside = (s < 2);
+    const int ncell = xside ? ncy : ncx;
+    for (int c = 0; c < ncell; ++c) {
+      int cx, cy;
+      if (xside) { cy = c; cx = (s == 0) ? 0 : ncx - 1; }
+      else { cx = c; cy = (s == 2) ? 0 : ncy - 1; }
+      const size_t cell = (size_t)(c0y + cy) * g.n + (c0x + cx);
+      const cplx rho(0.0, -k[cell] * h);  // -i k h
+      for (int a = 0; a < np; ++a)
+        for (int b = 0; b < np; ++b) {
+          int ra, rb;
+          if (xside) {
+            const int lx = (s == 0) ? 0 : wx - 1;
+            ra = (cy * p + a) * wx + lx;
+            rb = (cy * p + b) * wx + lx;
+          } else {
+            const int ly = (s == 2) ? 0 : wy - 1;
+            ra = ly * wx + cx * p + a;
+            rb = ly * wx + cx * p + b;
+          }
+          A[(size_t)ra * nd + rb] += rho * ref.M[a * np + b];
+        }
+    }
+  }
+  // banded LU: coupling within a cell reaches p rows and p columns
+  const int bw = p * wx + p;
+  std::vector<int> piv;
+  if (!band_lu(A.data(), nd, bw, bw, piv)) return TH_ERR_SINGULAR;
+  // A_s^(i) is complex symmetric, so row j of its inverse solves A x = e_j.
+  std::vector<cplx> x(nd);
+  const int NR = g.NR, NC = g.NC, Lu = g.Lu, Lw = g.Lw;
+  std::fill(out, out + (size_t)NR * NC, cplx(0.0));
+  for (int ry = 0; ry < vy; ++ry)
+    for (int rx = 0; rx < vx; ++rx) {
+      const int gx = ux + rx, gy = uy + ry;
+      const int lj = (gy - oy) * wx + (gx - ox);
+      std::fill(x.begin(), x.end(), cplx(0.0));
+      x[lj] = 1.0;
+      band_solve(A.data(), nd, bw, bw, piv, x.data());
+      const double Lj = (double)g.mult1d[gx] * g.mult1d[gy];
+      cplx* orow = out + (size_t)(ry * Lu + rx) * NC;
+      for (int cy = 0; cy < wy; ++cy)
+        for (int cx = 0; cx < wx; ++cx) orow[cy * Lw + cx] = x[cy * wx + cx] / Lj;
+    }
+  return TH_OK;
+}
+
+th_status all_inverse_rows(const Geometry& g, const Ref1D& ref, const double* k, const double* eps,
+                           double alpha_s, std::vector<cplx>& out) {
+  const size_t blk = (size_t)g.NR * g.NC;
+  out.assign(blk * g.nsub, cplx(0.0));
+  // identical subdomains (same boxes relative to the boundary, same coefficients,
+  // same multiplicities) give identical rows: compute each distinct one once
+  std::vector<int> rep(g.nsub);
+  std::map<std::string, int> seen;
+  for (int s = 0; s < g.nsub; ++s) {
+    const int* bb = &g.box[(size_t)s * 8];
+    std::string key;
+    auto put = [&](const void* d, size_t nbytes) { key.append((const char*)d, nbytes); };
+    const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3];
+    int rel[8] = {bb[2], bb[3], bb[4] - ox, bb[5] - oy, bb[6], bb[7],
+                  (ox == 0) ? 1 : 0, (oy == 0) ? 1 : 0};
+    put(rel, sizeof(rel));
+    int hi[2] = {(ox + wx - 1 == g.m - 1) ? 1 : 0, (oy + wy - 1 == g.m - 1) ? 1 : 0};
+    put(hi, sizeof(hi));
+    for (int cy = oy / g.p; cy < (oy + wy - 1) / g.p; ++cy)
+      for (int cx = ox / g.p; cx < (ox + wx - 1) / g.p; ++cx) {
+        const size_t c = (size_t)cy * g.n + cx;
+        put(&k[c], sizeof(double));
+        double e = eps ? eps[c] : 0.0;
+        put(&e, sizeof(double));
+      }
+    for (int i = bb[4]; i < bb[4] + bb[6]; ++i) put(&g.mult1d[i], sizeof(int));
+    for (int i = bb[5]; i < bb[5] + bb[7]; ++i) put(&g.mult1d[i], sizeof(int));
+    auto it = seen.find(key);
+    if (it == seen.end()) {
+      seen.emplace(key, s);
+      rep[s] = s;
+    } else {
+      rep[s] = it->second;
+    }
+  }
+  std::vector<int> todo;
+  for (int s = 0; s < g.nsub; ++s)
+    if (rep[s] == s) todo.push_back(s);
+  std::atomic<int> err(0);
+  parallel_for((int)todo.size(), [&](int i) {
+    int s = todo[i];
+    th_status st = subdomain_inverse_rows(g, ref, k, eps, alpha_s, s, out.data() + blk * s);
+    if (st != TH_OK) err.store((int)st);
+  });
+  if (err.load() != 0) return (th_status)err.load();
+  for (int s = 0; s < g.nsub; ++s)
+    if (rep[s] != s) std::copy(out.begin() + blk * rep[s], out.begin() + blk * (rep[s] + 1), out.begin() + blk * s);
+  return TH_OK;
+}
+
+// -------------------------------------------------------------------- QSFEM
+// The printed formulas for P1, P2 and N are ratios of quantities that all
+// vanish as eta -> 0 (numerators and denominator like eta^4, sigma_P(0) den
+// like eta^6), so evaluating them as written loses about eta^-6 ulps.  Each
+// quantity is a signed sum of cosines sum_j w_j cos(eta t_j) (products of
+// cosines turned into sums), and its low Taylor moments sum_j w_j t_j^(2k)
+// vanish exactly (k = 0, 1 for the numerators and the denominator, k = 0, 1, 2
+// for E = 4 den + 8 num1 + 4 num2 = den sigma_P(0)).  The sums are therefore
+// evaluated with the remainders cos x - 1 + x^2/2 (resp. - x^4/24 too), which
+// carry no cancellation.  Then
+//   q00 = N P0/4 = -eta^2 den / E,  q_edge = N P1/2 = -eta^2 num1 / E,
+//   q_diag = N P2 = -eta^2 num2 / E.
+static double cos_rem(double x, int order) {
+  // order 4: cos x - 1 + x^2/2;  order 6: cos x - 1 + x^2/2 - x^4/24
+  const double ax = std::fabs(x);
+  if (ax > 1.5) {
+    double v = std::cos(x) - 1.0 + 0.5 * x * x;
+    if (order == 6) v -= x * x * x * x / 24.0;
+    return v;
+  }
+  const double x2 = x * x;
+  double term = (order == 4) ? x2 * x2 / 24.0 : -x2 * x2 * x2 / 720.0;  // first term
+  int k = (order == 4) ? 2 : 3;
+  double sum = 0.0;
+  for (int it = 0; it < 20; ++it) {
+    sum += term;
+    term *= -x2 / ((2.0 * k + 1.0) * (2.0 * k + 2.0));
+    ++k;
+  }
+  return sum;
+}
+
+void qsfem_cell(double k, double eps, double hc, cplx d[3]) {
+  const double eta = k * hc;
+  const double a = std::cos(M_PI / 16), b = std::sin(M_PI / 16);
+  const double c = std::cos(3 * M_PI / 16), e = std::sin(3 * M_PI / 16);
+  struct Term { double w, t; };
+  // num1 = c1 s1 - c2 s2, num2 = c2 + s2 - c1 - s1, den = c2 s2 (c1 + s1) - c1 s1 (c2 + s2)
+  const Term n1[4] = {{0.5, a + b}, {0.5, a - b}, {-0.5, c + e}, {-0.5, c - e}};
+  const Term n2[4] = {{1, c}, {1, e}, {-1, a}, {-1, b}};
+  Term dn[16];
+  const double trip[4][4] = {{c, e, a, 1}, {c, e, b, 1}, {a, b, c, -1}, {a, b, e, -1}};
+  for (int i = 0; i < 4; ++i) {
+    const double x = trip[i][0], y = trip[i][1], z = trip[i][2], w = 0.25 * trip[i][3];
+    dn[4 * i + 0] = {w, x + y + z};
+    dn[4 * i + 1] = {w, x + y - z};
+    dn[4 * i + 2] = {w, x - y + z};
+    dn[4 * i + 3] = {w, x - y - z};
+  }
+  double num1 = 0, num2 = 0, den = 0, E = 0;
+  for (const Term& t : n1) { num1 += t.w * cos_rem(eta * t.t, 4); E += 8 * t.w * cos_rem(eta * t.t, 6); }
+  for (const Term& t : n2) { num2 += t.w * cos_rem(eta * t.t, 4); E += 4 * t.w * cos_rem(eta * t.t, 6); }
+  for (const Term& t : dn) { den += t.w * cos_rem(eta * t.t, 4); E += 4 * t.w * cos_rem(eta * t.t, 6); }
+  const double s = -eta * eta / E;
+  const double h2 = hc * hc;
+  d[0] = cplx(s * den, -eps * h2 / 9.0);
+  d[1] = cplx(s * num1, -eps * h2 / 18.0);
+  d[2] = cplx(s * num2, -eps * h2 / 36.0);
+}
+
+// Inverse of a dense complex matrix (LU with partial pivoting, then one
+// triangular solve per unit column, columns in parallel).
+static bool dense_inverse(std::vector<cplx>& S, int n, cplx* out) {
+  std::vector<int> piv;
+  if (!band_lu(S.data(), n, n - 1, n - 1, piv)) return false;
+  // column c of the inverse solves S x = e_c; write it as column c of out
+  parallel_for(n, [&](int c) {
+    std::vector<cplx> x(n, cplx(0.0));
+    x[c] = 1.0;
+    band_solve(S.data(), n, n - 1, n - 1, piv, x.data());
+    for (int r = 0; r < n; ++r) out[(size_t)r * n + c] = x[r];
+  });
+  return true;
+}
+
+th_status coarse_setup(const Geometry& g, const double* k, const double* eps, CoarseBlocks& cb) {
+  const int nc = g.nc, mc = g.mc, q = g.q;
+  cb.mc = mc;
+  cb.cell.assign((size_t)nc * nc * 3, cplx(0.0));
+  for (int cy = 0; cy < nc; ++cy)
+    for (int cx = 0; cx < nc; ++cx) {
+      const size_t f = (size_t)(cy / q) * g.n + (cx / q);
+      qsfem_cell(k[f], eps ? eps[f] : 0.0, g.hc, &cb.cell[((size_t)cy * nc + cx) * 3]);
+    }
+  for (int s = 0; s < 4; ++s) {
+    cb.rho[s].assign(nc, cplx(0.0));
+    if (!g.robin[s]) continue;
+    for (int t = 0; t < nc; ++t) {
+      int cx, cy;
+      if (s < 2) { cy = t; cx = (s == 0) ? 0 : nc - 1; }
+      else { cx = t; cy = (s == 2) ? 0 : nc - 1; }
+      const size_t f = (size_t)(cy / q) * g.n + (cx / q);
+      cb.rho[s][t] = cplx(0.0, -k[f] * g.hc);
+    }
+  }
+  const size_t mm = (size_t)mc * mc;
+  cb.dl.assign(mm, 0.0); cb.dd.assign(mm, 0.0); cb.du.assign(mm, 0.0);
+  cb.cl.assign(mm, 0.0); cb.cd.assign(mm, 0.0); cb.cu.assign(mm, 0.0);
+  auto add = [&](int ax, int ay, int bx, int by, cplx v) {
+    // entry A[(ax,ay),(bx,by)] into the block structure (rows ay, lower blocks implied)
+    const size_t r = (size_t)ay * mc + ax;
+    const int dx = bx - ax;
+    if (by == ay) {
+      (dx == -1 ? cb.dl : dx == 0 ? cb.dd : cb.du)[r] += v;
+    } else if (by == ay + 1) {
+      (dx == -1 ? cb.cl : dx == 0 ? cb.cd : cb.cu)[r] += v;
+    }
+  };
+  for (int cy = 0; cy < nc; ++cy)
+    for (int cx = 0; cx < nc; ++cx) {
+      const cplx* d = &cb.cell[((size_t)cy * nc + cx) * 3];
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          const int ax = cx + (a & 1), ay = cy + (a >> 1);
+          const int bx = cx + (b & 1), by = cy + (b >> 1);
+          const int nd = std::abs(ax - bx) + std::abs(ay - by);
+          add(ax, ay, bx, by, d[nd]);
+        }
+    }
+  for (int s = 0; s < 4; ++s) {
+    if (!g.robin[s]) continue;
+    for (int t = 0; t < nc; ++t) {
+      int x0, y0, x1, y1;
+      if (s < 2) { x0 = x1 = (s == 0) ? 0 : nc; y0 = t; y1 = t + 1; }
+      else { y0 = y1 = (s == 2) ? 0 : nc; x0 = t; x1 = t + 1; }
+      const cplx r = cb.rho[s][t];
+      add(x0, y0, x0, y0, r / 3.0);
+      add(x1, y1, x1, y1, r / 3.0);
+      add(x0, y0, x1, y1, r / 6.0);
+      add(x1, y1, x0, y0, r / 6.0);
+    }
+  }
+  // block elimination: S_0 = D_0, S_j = D_j - B_j S_{j-1}^{-1} C_{j-1}, B_j = C_{j-1}^T
+  cb.G.assign((size_t)mc * mm, cplx(0.0));
+  std::vector<cplx> S(mm), T(mm);
+  for (int j = 0; j < mc; ++j) {
+    std::fill(S.begin(), S.end(), cplx(0.0));
+    const size_t o = (size_t)j * mc;
+    for (int a = 0; a < mc; ++a) {
+      if (a > 0) S[(size_t)a * mc + a - 1] = cb.dl[o + a];
+      S[(size_t)a * mc + a] = cb.dd[o + a];
+      if (a + 1 < mc) S[(size_t)a * mc + a + 1] = cb.du[o + a];
+    }
+    if (j > 0) {
+      const cplx* Gp = &cb.G[(size_t)(j - 1) * mm];
+      const size_t op = (size_t)(j - 1) * mc;
+      // T = G_{j-1} C_{j-1}:  T[a][b] = G[a][b-1] cu[b-1] + G[a][b] cd[b] + G[a][b+1] cl[b+1]
+      parallel_for(mc, [&](int a) {
+        for (int b = 0; b < mc; ++b) {
+          cplx s = Gp[(size_t)a * mc + b] * cb.cd[op + b];
+          if (b > 0) s += Gp[(size_t)a * mc + b - 1] * cb.cu[op + b - 1];
+          if (b + 1 < mc) s += Gp[(size_t)a * mc + b + 1] * cb.cl[op + b + 1];
+          T[(size_t)a * mc + b] = s;
+        }
+      });
+      // S -= B_j T with B_j[a][a-1] = cu[a-1], B_j[a][a] = cd[a], B_j[a][a+1] = cl[a+1]
+      parallel_for(mc, [&](int a) {
+        for (int b = 0; b < mc; ++b) {
+          cplx s = cb.cd[op + a] * T[(size_t)a * mc + b];
+          if (a > 0) s += cb.cu[op + a - 1] * T[(size_t)(a - 1) * mc + b];
+          if (a + 1 < mc) s += cb.cl[op + a + 1] * T[(size_t)(a + 1) * mc + b];
+          S[(size_t)a * mc + b] -= s;
+        }
+      });
+    }
+    if (!dense_inverse(S, mc, &cb.G[(size_t)j * mm])) return TH_ERR_SINGULAR;
+  }
+  return TH_OK;
+}
+
+// ---------------------------------------------------------------- transfers
+void transfer_tables(const Geometry& g, const Ref1D& ref, TransferTables& t) {
+  const int p = g.p, q = g.q, m = g.m, mc = g.mc;
+  t.q = q;
+  t.pj0.assign(m, 0);
+  t.pw.assign((size_t)m * (q + 1), 0.0);
+  for (int i = 0; i < m; ++i) {
+    int e = std::min(i / p, g.n - 1);
+    int a = i - e * p;
+    t.pj0[i] = e * q;
+    for (int b = 0; b <= q; ++b) t.pw[(size_t)i * (q + 1) + b] = ref.Pw[a * (q + 1) + b];
+  }
+  // transpose: coarse node J collects every fine node with a nonzero weight on J
+  std::vector<std::vector<std::pair<int, double>>> lists(mc);
+  for (int i = 0; i < m; ++i)
+    for (int b = 0; b <= q; ++b) {
+      double w = t.pw[(size_t)i * (q + 1) + b];
+      if (w != 0.0) lists[t.pj0[i] + b].push_back({i, w});
+    }
+  t.rmax = 0;
+  for (auto& l : lists) t.rmax = std::max(t.rmax, (int)l.size());
+  t.rcnt.assign(mc, 0);
+  t.ridx.assign((size_t)mc * t.rmax, 0);
+  t.rw.assign((size_t)mc * t.rmax, 0.0);
+  for (int J = 0; J < mc; ++J) {
+    t.rcnt[J] = (int)lists[J].size();
+    for (size_t r = 0; r < lists[J].size(); ++r) {
+      t.ridx[(size_t)J * t.rmax + r] = lists[J][r].first;
+      t.rw[(size_t)J * t.rmax + r] = lists[J][r].second;
+    }
+    for (int r = (int)lists[J].size(); r < t.rmax; ++r) t.ridx[(size_t)J * t.rmax + r] = lists[J].empty() ? 0 : lists[J][0].first;
+  }
+}
+
+}  // namespace th

@@ -1,0 +1,382 @@
+// K5/K6 grid transfers, K7 coarse QSFEM apply, K9/K10 vector kernels.
+//
+// K6 prolongation (Section 4.2): I_P u_c is, in every fine cell, the
+// degree-p/2 interpolant of the coarse values at the (p/2+1)^2 coarse nodes of
+// that cell; its fine nodal values are a tensor product of 1-D weights
+// l^eq_b(xi_a).  K5 restriction is the transpose I_P^T (Algorithm 1).
+// K7: A_q of Section 3.3 applied cell by cell: per coarse cell c the
+// coefficients (d0, d1, d2) for same-node, edge-neighbour and diagonal pairs,
+// plus -i k hc times the Q1 edge mass on absorbing sides.
+#include "kernels.h"
+
+namespace th {
+
+// -------------------------------------------------------------------- K5
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict(const TransferArgs<T> a) {
+  using C = typename Cx<T>::t;
+  const long long J = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= a.Nc) return;
+  const int Jy = (int)(J / a.mc), Jx = (int)(J - (long long)Jy * a.mc);
+  const C* r = a.in + (size_t)blockIdx.y * a.N;
+  T sr = 0, si = 0;
+  for (int ky = 0; ky < a.rmax; ++ky) {
+    const T wy = a.rw[(size_t)Jy * a.rmax + ky];
+    if (wy == (T)0) continue;
+    const int iy = a.ridx[(size_t)Jy * a.rmax + ky];
+    T tr = 0, ti = 0;
+    for (int kx = 0; kx < a.rmax; ++kx) {
+      const T wx = a.rw[(size_t)Jx * a.rmax + kx];
+      const C v = r[(size_t)iy * a.m + a.ridx[(size_t)Jx * a.rmax + kx]];
+      tr += wx * v.x;
+      ti += wx * v.y;
+    }
+    sr += wy * tr;
+    si += wy * ti;
+  }
+  C o;
+  o.x = sr;
+  o.y = si;
+  a.out[(size_t)blockIdx.y * a.Nc + J] = o;
+}
+
+// -------------------------------------------------------------------- K6
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong(const TransferArgs<T> a) {
+  using C = typename Cx<T>::t;
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.N) return;
+  const int iy = (int)(j / a.m), ix = (int)(j - (long long)iy * a.m);
+  const C* uc = a.in + (size_t)blockIdx.y * a.Nc;
+  const int jx0 = a.pj0[ix], jy0 = a.pj0[iy];
+  T sr = 0, si = 0;
+  for (int by = 0; by <= a.q; ++by) {
+    const T wy = a.pw[(size_t)iy * (a.q + 1) + by];
+    if (wy == (T)0) continue;
+    T tr = 0, ti = 0;
+    for (int bx = 0; bx <= a.q; ++bx) {
+      const T wx = a.pw[(size_t)ix * (a.q + 1) + bx];
+      const C v = uc[(size_t)(jy0 + by) * a.mc + jx0 + bx];
+      tr += wx * v.x;
+      ti += wx * v.y;
+    }
+    sr += wy * tr;
+    si += wy * ti;
+  }
+  C* u = a.out + (size_t)blockIdx.y * a.N;
+  C o = u[j];
+  o.x += a.omega * sr;
+  o.y += a.omega * si;
+  u[j] = o;
+}
+
+template <typename T>
+cudaError_t launch_restrict(const TransferArgs<T>& a, int nrhs, cudaStream_t s) {
+  dim3 grid((unsigned)((a.Nc + 255) / 256), nrhs);
+  k_restrict<T><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_prolong(const TransferArgs<T>& a, int nrhs, cudaStream_t s) {
+  dim3 grid((unsigned)((a.N + 255) / 256), nrhs);
+  k_prolong<T><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template cudaError_t launch_restrict<double>(const TransferArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_restrict<float>(const TransferArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_prolong<double>(const TransferArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_prolong<float>(const TransferArgs<float>&, int, cudaStream_t);
+
+// -------------------------------------------------------------------- K7
+template <typename C>
+__device__ __forceinline__ void cfma(C& acc, C a, C b) {
+  acc.x += a.x * b.x - a.y * b.y;
+  acc.y += a.x * b.y + a.y * b.x;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_apply(const CoarseApplyArgs<T> a) {
+  using C = typename Cx<T>::t;
+  const long long J = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= a.Nc) return;
+  const int Jy = (int)(J / a.mc), Jx = (int)(J - (long long)Jy * a.mc);
+  const C* x = a.x + (size_t)blockIdx.y * a.Nc;
+  C acc;
+  acc.x = 0;
+  acc.y = 0;
+  // cells (cx, cy) around node (Jx, Jy): cx in {Jx-1, Jx}, cy in {Jy-1, Jy}
+  for (int cy = Jy - 1; cy <= Jy; ++cy) {
+    if (cy < 0 || cy >= a.nc) continue;
+    for (int cx = Jx - 1; cx <= Jx; ++cx) {
+      if (cx < 0 || cx >= a.nc) continue;
+      const C* d = a.cell + ((size_t)cy * a.nc + cx) * 3;
+      const int ox = (cx == Jx) ? 1 : -1, oy = (cy == Jy) ? 1 : -1;  // direction of the other nodes
+      cfma(acc, d[0], x[(size_t)Jy * a.mc + Jx]);
+      cfma(acc, d[1], x[(size_t)Jy * a.mc + Jx + ox]);
+      cfma(acc, d[1], x[(size_t)(Jy + oy) * a.mc + Jx]);
+      cfma(acc, d[2], x[(size_t)(Jy + oy) * a.mc + Jx + ox]);
+    }
+  }
+  // absorbing sides: rho_e (1/3 x_J + 1/6 x_neighbour) per boundary edge at J
+  const T third = (T)(1.0 / 3.0), sixth = (T)(1.0 / 6.0);
+  for (int s = 0; s < 4; ++s) {
+    const bool xside = s < 2;
+    const int fixed = xside ? Jx : Jy;
+    const int along = xside ? Jy : Jx;
+    if (fixed != ((s & 1) ? a.nc : 0)) continue;
+    const C* rho = a.rho + (size_t)s * a.nc;
+    for (int t = along - 1; t <= along; ++t) {
+      if (t < 0 || t >= a.nc) continue;
+      const C r = rho[t];
+      const int other = (t == along) ? along + 1 : along - 1;
+      const size_t jo = xside ? (size_t)other * a.mc + Jx : (size_t)Jy * a.mc + other;
+      C xj = x[J], xo = x[jo];
+      C v;
+      v.x = third * xj.x + sixth * xo.x;
+      v.y = third * xj.y + sixth * xo.y;
+      cfma(acc, r, v);
+    }
+  }
+  a.y[(size_t)blockIdx.y * a.Nc + J] = acc;
+}
+
+template <typename T>
+cudaError_t launch_coarse_apply(const CoarseApplyArgs<T>& a, int nrhs, cudaStream_t s) {
+  dim3 grid((unsigned)((a.Nc + 255) / 256), nrhs);
+  k_coarse_apply<T><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template cudaError_t launch_coarse_apply<double>(const CoarseApplyArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_coarse_apply<float>(const CoarseApplyArgs<float>&, int, cudaStream_t);
+
+// ---------------------------------------------------------------- K10 etc.
+__global__ void k_d2f(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+__global__ void k_f2d(const float* __restrict__ in, double* __restrict__ out, long long n, int acc) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = acc ? out[i] + (double)in[i] : (double)in[i];
+}
+static unsigned vgrid(long long n) {
+  long long b = (n + 255) / 256;
+  return (unsigned)(b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b));
+}
+cudaError_t launch_d2f(const double* in, float* out, long long n, cudaStream_t s) {
+  k_d2f<<<vgrid(n), 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_f2d(const float* in, double* out, long long n, int accumulate, cudaStream_t s) {
+  k_f2d<<<vgrid(n), 256, 0, s>>>(in, out, n, accumulate);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_zaxpy(const typename Cx<T>::t* __restrict__ x, typename Cx<T>::t* __restrict__ y, T alpha,
+                        long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    auto v = y[i];
+    const auto xv = x[i];
+    v.x += alpha * xv.x;
+    v.y += alpha * xv.y;
+    y[i] = v;
+  }
+}
+template <typename T>
+cudaError_t launch_zaxpy(const typename Cx<T>::t* x, typename Cx<T>::t* y, T alpha, long long n, cudaStream_t s) {
+  k_zaxpy<T><<<vgrid(n), 256, 0, s>>>(x, y, alpha, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_zaxpy<double>(const double2*, double2*, double, long long, cudaStream_t);
+template cudaError_t launch_zaxpy<float>(const float2*, float2*, float, long long, cudaStream_t);
+
+template <typename T>
+__global__ void k_zero(typename Cx<T>::t* x, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    typename Cx<T>::t z;
+    z.x = 0;
+    z.y = 0;
+    x[i] = z;
+  }
+}
+template <typename T>
+cudaError_t launch_zero(typename Cx<T>::t* x, long long n, cudaStream_t s) {
+  k_zero<T><<<vgrid(n), 256, 0, s>>>(x, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_zero<double>(double2*, long long, cudaStream_t);
+template cudaError_t launch_zero<float>(float2*, long long, cudaStream_t);
+
+// ---------------------------------------------------------------- K9 Krylov
+constexpr int kDotTile = 8;  // basis vectors per block row
+
+int mdot_blocks(long long N) {
+  long long b = (N + 1023) / 1024;
+  return (int)(b > 256 ? 256 : (b < 1 ? 1 : b));
+}
+
+// part[(rhs * nv + i) * nblk + blk] = sum over this block's range of conj(V_i) w
+__global__ void __launch_bounds__(256) k_mdot_part(const double2* __restrict__ Vb, long long vstride,
+                                                   const double2* __restrict__ w, long long N, int nv,
+                                                   double2* __restrict__ part, int nblk) {
+  const int rhs = blockIdx.z, i0 = blockIdx.y * kDotTile;
+  const int ni = min(kDotTile, nv - i0);
+  const long long chunk = (N + nblk - 1) / nblk;
+  const long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
+  const double2* wr = w + (size_t)rhs * N;
+  double ar[kDotTile], ai[kDotTile];
+#pragma unroll
+  for (int t = 0; t < kDotTile; ++t) { ar[t] = 0; ai[t] = 0; }
+  for (long long n = lo + threadIdx.x; n < hi; n += blockDim.x) {
+    const double2 wv = wr[n];
+#pragma unroll
+    for (int t = 0; t < kDotTile; ++t) {
+      if (t < ni) {
+        const double2 v = Vb[(size_t)(i0 + t) * vstride + (size_t)rhs * N + n];
+        ar[t] += v.x * wv.x + v.y * wv.y;
+        ai[t] += v.x * wv.y - v.y * wv.x;
+      }
+    }
+  }
+  __shared__ double sh[2][kDotTile][256];
+#pragma unroll
+  for (int t = 0; t < kDotTile; ++t) {
+    sh[0][t][threadIdx.x] = ar[t];
+    sh[1][t][threadIdx.x] = ai[t];
+  }
+  __syncthreads();
+  for (int stride = 128; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride) {
+#pragma unroll
+      for (int t = 0; t < kDotTile; ++t) {
+        sh[0][t][threadIdx.x] += sh[0][t][threadIdx.x + stride];
+        sh[1][t][threadIdx.x] += sh[1][t][threadIdx.x + stride];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < (unsigned)ni) {
+    double2 o;
+    o.x = sh[0][threadIdx.x][0];
+    o.y = sh[1][threadIdx.x][0];
+    part[((size_t)rhs * nv + i0 + threadIdx.x) * nblk + blockIdx.x] = o;
+  }
+}
+
+// h[rhs * nv + i] = sum over blocks (fixed order)
+__global__ void k_mdot_final(const double2* __restrict__ part, int nblk, int total, double2* __restrict__ h) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  double sr = 0, si = 0;
+  for (int b = 0; b < nblk; ++b) {
+    const double2 v = part[(size_t)idx * nblk + b];
+    sr += v.x;
+    si += v.y;
+  }
+  double2 o;
+  o.x = sr;
+  o.y = si;
+  h[idx] = o;
+}
+
+cudaError_t launch_mdot(const double2* Vbase, long long vstride, const double2* w, long long N, int nv, int nrhs,
+                        double2* part, double2* h, int nblk, cudaStream_t s) {
+  dim3 grid(nblk, (nv + kDotTile - 1) / kDotTile, nrhs);
+  k_mdot_part<<<grid, 256, 0, s>>>(Vbase, vstride, w, N, nv, part, nblk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int total = nv * nrhs;
+  k_mdot_final<<<(total + 127) / 128, 128, 0, s>>>(part, nblk, total, h);
+  return cudaGetLastError();
+}
+
+// w[rhs] += sign * sum_i h[rhs * hstride + i] V_i[rhs]
+__global__ void __launch_bounds__(256) k_maxpy(const double2* __restrict__ Vb, long long vstride,
+                                               const double2* __restrict__ h, int hstride, double2* __restrict__ w,
+                                               long long N, int nv, double sign) {
+  const int rhs = blockIdx.y;
+  double2* wr = w + (size_t)rhs * N;
+  const double2* hr = h + (size_t)rhs * hstride;
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    double sr = 0, si = 0;
+    for (int i = 0; i < nv; ++i) {
+      const double2 c = hr[i];
+      const double2 v = Vb[(size_t)i * vstride + (size_t)rhs * N + n];
+      sr += c.x * v.x - c.y * v.y;
+      si += c.x * v.y + c.y * v.x;
+    }
+    double2 o = wr[n];
+    o.x += sign * sr;
+    o.y += sign * si;
+    wr[n] = o;
+  }
+}
+
+cudaError_t launch_maxpy(const double2* Vbase, long long vstride, const double2* h, int hstride, double2* w,
+                         long long N, int nv, int nrhs, double sign, cudaStream_t s) {
+  long long b = (N + 255) / 256;
+  dim3 grid((unsigned)(b > 1216 ? 1216 : b), nrhs);
+  k_maxpy<<<grid, 256, 0, s>>>(Vbase, vstride, h, hstride, w, N, nv, sign);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_norm_part(const double2* __restrict__ w, long long N, double* part, int nblk) {
+  const int rhs = blockIdx.y;
+  const long long chunk = (N + nblk - 1) / nblk;
+  const long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
+  const double2* wr = w + (size_t)rhs * N;
+  double s = 0;
+  for (long long n = lo + threadIdx.x; n < hi; n += blockDim.x) {
+    const double2 v = wr[n];
+    s += v.x * v.x + v.y * v.y;
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int stride = 128; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride) sh[threadIdx.x] += sh[threadIdx.x + stride];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(size_t)rhs * nblk + blockIdx.x] = sh[0];
+}
+
+__global__ void k_norm_final(const double* part, int nblk, int nrhs, double* out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  double s = 0;
+  for (int b = 0; b < nblk; ++b) s += part[(size_t)r * nblk + b];
+  out[r] = s;
+}
+
+cudaError_t launch_norm2(const double2* w, long long N, int nrhs, double* part, double* out, int nblk,
+                         cudaStream_t s) {
+  dim3 grid(nblk, nrhs);
+  k_norm_part<<<grid, 256, 0, s>>>(w, N, part, nblk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_norm_final<<<(nrhs + 127) / 128, 128, 0, s>>>(part, nblk, nrhs, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_scale_rhs(const double2* in, double2* out, const double* __restrict__ sc,
+                            long long N) {
+  const int rhs = blockIdx.y;
+  const double c = sc[rhs];
+  const double f = isfinite(c) ? c : 0.0;
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    double2 v = in[(size_t)rhs * N + n];
+    v.x *= f;
+    v.y *= f;
+    out[(size_t)rhs * N + n] = v;
+  }
+}
+
+cudaError_t launch_scale_rhs(const double2* in, double2* out, const double* inv, long long N, int nrhs,
+                             cudaStream_t s) {
+  long long b = (N + 255) / 256;
+  dim3 grid((unsigned)(b > 1216 ? 1216 : b), nrhs);
+  k_scale_rhs<<<grid, 256, 0, s>>>(in, out, inv, N);
+  return cudaGetLastError();
+}
+
+}  // namespace th

@@ -1,0 +1,221 @@
+"""GPU parity: every hot-path step through the C ABI against the FP64 oracle.
+
+Tolerances (relative, max-norm over the output):
+  * FP64 operator applies (A, A_s, A_q), residual, transfers: 1e-12 (the
+    arithmetic differs only in summation order);
+  * FP64 smoother: 1e-11 (inverse rows from a banded LU vs SuperLU solves of
+    subdomain systems with condition numbers below ~1e3);
+  * FP64 coarse solve and two-grid cycle: 1e-9 (explicit block inverses vs
+    banded LU on the coarse Helmholtz matrix, condition numbers up to ~1e6);
+  * FP64 FGMRES: identical iteration count, solutions within 1e-7;
+  * FP32 applies: 2e-6; FP32 / FP16 / BF16 smoothers against the FP64
+    smoother: 1e-5 / 2e-3 / 2e-2 (unit roundoff of the stored rows times the
+    growth of a few-hundred-term sums); mixed-precision solves reach the same
+    1e-8 residual and the oracle's solution within 1e-6.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dd, krylov, twogrid
+from tests.common import ensure_built, oracle_bc, relerr, small_case
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def th():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    import paper_2509_17494_gb300 as th
+    return th
+
+
+DEV = "cuda:0"
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+CASES = [
+    dict(n=6, p=4, l_dd=2, bc="robin"),
+    dict(n=9, p=4, l_dd=2, bc={"xlo": "robin", "yhi": "robin"}),     # ragged tile, mixed sides
+    dict(n=20, p=2, l_dd=3, bc="robin"),                             # p = 2, ragged tiles and blocks
+    dict(n=5, p=6, l_dd=2, bc="neumann"),                            # p = 6, Neumann (layer absorbs)
+    dict(n=5, p=8, l_dd=2, bc={"ylo": "robin", "xhi": "robin"}),     # p = 8
+    dict(n=25, p=4, l_dd=4, bc="robin"),                             # 4/3 block sizes
+]
+
+
+def build(th, c, nrhs=3, **kw):
+    k, eps = small_case(n=c["n"], p=c["p"])
+    S = th.TwoGridSolver(c["n"], c["p"], k, eps, bc=c["bc"], alpha_s=kw.pop("alpha_s", 0.5), l_dd=c["l_dd"],
+                         nrhs_max=nrhs, device=DEV, **kw)
+    P = twogrid.Problem(c["n"], c["p"], k, eps, bc=oracle_bc(c["bc"]), alpha_s=0.5)
+    return S, P
+
+
+@pytest.mark.parametrize("c", CASES)
+def test_fine_applies_fp64(th, c):
+    S, P = build(th, c)
+    x = synth.random_complex((3, P.N), 1)
+    for op, M in (("A", P.A), ("As", P.As)):
+        y = host(S.apply(dev(x), op))
+        want = (M @ x.T).T
+        assert relerr(y, want) < 1e-12, op
+    f = synth.random_complex((3, P.N), 2)
+    r = host(S.residual(dev(f), dev(x)))
+    assert relerr(r, f - (P.A @ x.T).T) < 1e-12
+
+
+@pytest.mark.parametrize("c", CASES)
+def test_coarse_apply_and_transfers_fp64(th, c):
+    S, P = build(th, c)
+    xc = synth.random_complex((3, P.Nc), 3)
+    assert relerr(host(S.apply(dev(xc), "Aq")), (P.Aq @ xc.T).T) < 1e-12
+    r = synth.random_complex((3, P.N), 4)
+    assert relerr(host(S.restrict(dev(r))), (P.IP.T @ r.T).T) < 1e-12
+    u = synth.random_complex((3, P.N), 5)
+    got = host(S.prolong(dev(xc), dev(u.copy()), omega=0.7))
+    assert relerr(got, u + 0.7 * (P.IP @ xc.T).T) < 1e-12
+
+
+@pytest.mark.parametrize("c", CASES)
+@pytest.mark.parametrize("n_dd", [1, 2])
+def test_smoother_fp64(th, c, n_dd):
+    S, P = build(th, c, n_dd=n_dd)
+    sm = dd.DDSmoother(P, c["l_dd"])
+    f = synth.random_complex((3, P.N), 6)
+    u = synth.random_complex((3, P.N), 7)
+    got = host(S.smooth(dev(f), dev(u.copy())))
+    want = np.stack([sm.smooth(u[i], f[i], n_dd) for i in range(3)])
+    assert relerr(got, want) < 1e-11
+
+
+@pytest.mark.parametrize("c", CASES)
+def test_coarse_solve_fp64(th, c):
+    S, P = build(th, c)
+    rc = synth.random_complex((3, P.Nc), 8)
+    got = host(S.coarse_solve(dev(rc)))
+    B = twogrid.BandedSolver(P.Aq)
+    want = np.stack([B.solve(rc[i]) for i in range(3)])
+    assert relerr(got, want) < 1e-9
+
+
+@pytest.mark.parametrize("c", CASES)
+@pytest.mark.parametrize("n_s,omega_c", [(1, 1.0), (2, 0.8)])
+def test_cycle_fp64(th, c, n_s, omega_c):
+    S, P = build(th, c, n_s=n_s, omega_c=omega_c)
+    TG = twogrid.TwoGrid(P, l_dd=c["l_dd"], n_s=n_s, omega_c=omega_c)
+    f = synth.random_complex((3, P.N), 9)
+    u = synth.random_complex((3, P.N), 10)
+    got = host(S.cycle(dev(f), dev(u.copy())))
+    want = np.stack([TG.step(u[i], f[i]) for i in range(3)])
+    assert relerr(got, want) < 1e-9
+
+
+def test_cycle_is_deterministic(th):
+    S, P = build(th, CASES[1])
+    f = dev(synth.random_complex((3, P.N), 11))
+    u1 = dev(synth.random_complex((3, P.N), 12))
+    u2 = u1.clone()
+    S.cycle(f, u1)
+    S.cycle(f, u2)
+    assert torch.equal(u1, u2)
+
+
+@pytest.mark.parametrize("name,alpha_s,l_dd", [("square10_q4_n25", 0.5, 2), ("square10_q4_n25", 0.2, 4)])
+def test_solve_matches_oracle_iterations(th, name, alpha_s, l_dd):
+    w = synth.workload(name)
+    S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=alpha_s, l_dd=l_dd, restart=40, device=DEV)
+    P = twogrid.Problem(w["n"], w["p"], w["k"], w["eps"], alpha_s=alpha_s)
+    TG = twogrid.TwoGrid(P, l_dd=l_dd)
+    xo, it, rr, _ = krylov.fgmres(lambda v: P.A @ v, TG.precondition, w["f"], tol=1e-8, restart=40)
+    x, info = S.solve(dev(w["f"]))
+    assert info["iters"] == it
+    assert info["relres_max"] <= 1e-8
+    assert relerr(host(x), xo) < 1e-7
+
+
+def test_solve_multiple_rhs_and_restart(th):
+    c = CASES[0]
+    S, P = build(th, c, nrhs=4, restart=5, maxit=300)
+    TG = twogrid.TwoGrid(P, l_dd=c["l_dd"])
+    F = synth.random_complex((4, P.N), 13)
+    X, info = S.solve(dev(F))
+    assert info["converged"] == 4 and info["relres_max"] <= 1e-8
+    for i in range(4):
+        xo, it, rr, _ = krylov.fgmres(lambda v: P.A @ v, TG.precondition, F[i], tol=1e-8, restart=5, maxit=300)
+        assert info["iters_per_rhs"][i] == it
+        assert relerr(host(X)[i], xo) < 1e-7
+
+
+def test_host_buffer_entry_points(th):
+    S, P = build(th, CASES[0], nrhs=1)
+    f = synth.random_complex(P.N, 14)
+    u = synth.random_complex(P.N, 15)
+    ud = host(S.cycle(dev(f), dev(u.copy())))
+    uh = u.copy()
+    S.cycle_host(f, uh)
+    assert np.array_equal(uh, ud)
+    xh, info = S.solve_host(f)
+    xd, info2 = S.solve(dev(f))
+    assert info["iters"] == info2["iters"] and np.array_equal(xh, host(xd))
+
+
+# ------------------------------------------------------------ mixed precision
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 2e-3), ("bf16", 2e-2)])
+def test_mixed_smoother_close_to_fp64(th, prec, tol):
+    c = CASES[5]
+    S, P = build(th, c, prec=prec, extra_prec=("fp64",))
+    f = dev(synth.random_complex((3, P.N), 16))
+    u = synth.random_complex((3, P.N), 17)
+    S.set_precision("fp64")
+    ref = S.smooth(f, dev(u.copy())) - dev(u)
+    S.set_precision(prec)
+    got = S.smooth(f, dev(u.copy())) - dev(u)
+    assert relerr(host(got), host(ref)) < tol
+    x = dev(synth.random_complex((3, P.N), 18))
+    assert relerr(host(S.apply(x, "A", prec="fp32")), host(S.apply(x, "A"))) < 2e-6
+    xc = dev(synth.random_complex((3, P.Nc), 19))
+    assert relerr(host(S.apply(xc, "Aq", prec="fp32")), host(S.apply(xc, "Aq"))) < 2e-6
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_mixed_solve_reaches_tolerance(th, prec):
+    w = synth.workload("square10_q4_n25")
+    S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=0.5, l_dd=2, prec=prec,
+                         extra_prec=("fp64",), restart=40, device=DEV)
+    P = twogrid.Problem(w["n"], w["p"], w["k"], w["eps"], alpha_s=0.5)
+    import scipy.sparse.linalg as spla
+    xs = spla.spsolve(P.A.tocsc(), w["f"])
+    x, info = S.solve(dev(w["f"]))
+    S.set_precision("fp64")
+    x64, info64 = S.solve(dev(w["f"]))
+    assert info["relres_max"] <= 1e-8
+    assert info["iters"] <= info64["iters"] + 2
+    assert relerr(host(x), xs) < 1e-6
+
+
+# ------------------------------------------------------------ full-size, sampled
+def test_full_size_apply_and_cycle(th):
+    """40-wavelength 401^2 workload: the apply at full size and one cycle compared on sampled nodes."""
+    w = synth.workload("square40_q4_n100")
+    S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=0.5, l_dd=2, device=DEV)
+    P = twogrid.Problem(w["n"], w["p"], w["k"], w["eps"], alpha_s=0.5)
+    x = synth.random_complex(P.N, 20)
+    assert relerr(host(S.apply(dev(x), "A")), P.A @ x) < 1e-12
+    TG = twogrid.TwoGrid(P, l_dd=2)
+    f = w["f"]
+    got = host(S.cycle(dev(f), dev(np.zeros_like(f))))
+    want = TG.step(np.zeros_like(f), f)
+    idx = synth.rng(21).integers(0, P.N, 4000)
+    assert relerr(got[idx], want[idx]) < 1e-9

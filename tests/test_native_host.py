@@ -1,0 +1,89 @@
+"""CPU checks of the native library: it builds, loads, exports the C ABI, and
+its FP64 host set-up agrees with the oracle (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import dd, fem, qsfem, twogrid
+from tests.common import ensure_built, small_case, oracle_bc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def th():
+    ensure_built()
+    import paper_2509_17494_gb300 as th
+    th.lib()
+    return th
+
+
+def test_exports_every_declared_symbol(th):
+    hdrs = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+    names = set()
+    for h in hdrs:
+        txt = open(h).read()
+        names |= set(re.findall(r"^\s*(?:th_status|void|const char\*)\s+(th_\w+)\s*\(", txt, re.M))
+    assert len(names) >= 19
+    L = ctypes.CDLL(th.library_path())
+    for nm in sorted(names):
+        assert hasattr(L, nm), nm
+
+
+@pytest.mark.parametrize("p", [2, 4, 6, 8])
+def test_reference_matrices_match_oracle(th, p):
+    nodes, M, K = th.host_reference_1d(p)
+    M2, K2 = fem.reference_matrices(p)
+    assert np.abs(nodes - fem.gll_points(p)).max() < 1e-14
+    assert np.abs(M - M2).max() < 1e-14
+    assert np.abs(K - K2).max() < 1e-12 * np.abs(K2).max()
+
+
+@pytest.mark.parametrize("eta", [0.02, 0.05, 0.1, 0.19, 0.4, 1.0, 2 * np.pi / 5, 2.5])
+def test_qsfem_cell_matches_oracle(th, eta):
+    hc, eps = 0.02, 7.0
+    d = th.host_qsfem_cell(eta / hc, eps, hc)
+    q = qsfem.cell_q(eta)
+    want = np.array([q[0] - 1j * eps * hc * hc / 9, q[1] - 1j * eps * hc * hc / 18, q[2] - 1j * eps * hc * hc / 36])
+    assert np.abs(d - want).max() <= 5e-14 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("n,l_dd,bc", [(6, 2, "robin"), (7, 3, "neumann"),
+                                        (5, 2, {"xlo": "robin", "yhi": "robin"})])
+def test_inverse_rows_match_oracle(th, n, l_dd, bc):
+    p = 4
+    k, eps = small_case(n=n, p=p)
+    P = twogrid.Problem(n, p, k, eps, bc=oracle_bc(bc), alpha_s=0.5)
+    S = dd.DDSmoother(P, l_dd)
+    for sub, sd in enumerate(S.subs):
+        box, W, Lu, Lw = th.host_inverse_rows(n, p, k, eps, sub, bc=bc, alpha_s=0.5, l_dd=l_dd)
+        inv = np.linalg.inv(sd.As.toarray())
+        rows = inv[sd.u_local, :] / S.L[sd.u_dofs][:, None]
+        ox, oy, wx, wy, ux, uy, vx, vy = box
+        Wr = np.zeros((vx * vy, wx * wy), complex)
+        for ry in range(vy):
+            for rx in range(vx):
+                Wr[ry * vx + rx] = W[ry * Lu + rx].reshape(Lw, Lw)[:wy, :wx].reshape(-1)
+        assert np.abs(Wr - rows).max() <= 1e-12 * np.abs(rows).max(), sub
+        # padding beyond the boxes is exactly zero
+        Wfull = W.reshape(Lu, Lu, Lw, Lw)
+        assert np.all(Wfull[vy:] == 0) and np.all(Wfull[:, vx:] == 0)
+        assert np.all(Wfull[..., wy:, :] == 0) and np.all(Wfull[..., wx:] == 0)
+
+
+def test_workspace_size_and_argument_errors(th):
+    a = th.workspace_size(25, 4, l_dd=2)
+    b = th.workspace_size(25, 4, l_dd=2, nrhs_max=4)
+    c = th.workspace_size(25, 4, l_dd=2, prec="bf16", extra_prec=("fp64",))
+    assert 0 < a < b and a < c
+    for kw, code in [(dict(n=25, p=3), 1), (dict(n=0, p=4), 1), (dict(n=10, p=4, bc="dirichlet"), 8)]:
+        with pytest.raises(th.ThError) as e:
+            th.workspace_size(**kw)
+        assert e.value.code == code
+    with pytest.raises(th.ThError):
+        th.workspace_size(10, 4, l_dd=0)
+    with pytest.raises(th.ThError):
+        th.workspace_size(10, 4, restart=0)

@@ -138,14 +138,14 @@ def test_robin_sign_gives_outgoing_wave():
 
 
 # ---------------------------------------------------------------------- QSFEM
-@pytest.mark.parametrize("eta", [0.5, 1.0, 2 * math.pi / 5, 2.0])
+@pytest.mark.parametrize("eta", [0.1, 0.3, 0.5, 1.0, 2 * math.pi / 5, 2.0])
 def test_qsfem_exact_zeros_on_pi16_directions(eta):
     for j in (1, 3, 5, 7, 9, 11, 13, 15, 17, 19, 21, 23, 25, 27, 29, 31):
         t = j * math.pi / 16
         s = qsfem.symbol(eta, eta * math.cos(t), eta * math.sin(t))
         assert abs(s) < 1e-12 * eta ** 2 + 1e-13
     # and nonzero elsewhere on the circle (the stencil is not exact everywhere)
-    assert abs(qsfem.symbol(eta, eta, 0.0)) > 1e-9 * eta ** 2
+    assert abs(qsfem.symbol(eta, eta, 0.0)) > 1e-6 * eta ** 8      # error ~ 2.6e-6 eta^8 along theta = 0
     # sigma_{N P}(0) = -eta^2
     assert abs(qsfem.symbol(eta, 0.0, 0.0) + eta ** 2) < 1e-13 * eta ** 2
 
