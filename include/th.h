@@ -188,6 +188,30 @@ th_status th_solve_host(th_ctx* ctx, const double* f_host, double* u_host, int n
  * (all entry points), for accounting. */
 th_status th_launch_count(const th_ctx* ctx, long long* launches);
 
+/* Kernel classes for th_profile_read. */
+enum {
+  TH_K_FINE = 0,        /* fine operator apply / residual (K1, K2) */
+  TH_K_DD = 1,          /* subdomain inverse-row products (K3) */
+  TH_K_COMBINE = 2,     /* interface averaging and update (K4) */
+  TH_K_RESTRICT = 3,    /* restriction (K5) */
+  TH_K_PROLONG = 4,     /* prolongation and correction (K6) */
+  TH_K_COARSE_APPLY = 5,/* coarse QSFEM apply (K7) */
+  TH_K_COARSE_SOLVE = 6,/* coarse block-tridiagonal solve (K8) */
+  TH_K_VECTOR = 7,      /* precision conversions, axpy, zero fill (K10) */
+  TH_K_KRYLOV = 8,      /* FGMRES dots, norms, updates (K9) */
+  TH_K_COUNT = 9
+};
+
+/* Per-kernel timing for measurement: with enable = 1 every later kernel
+ * launch of the context is bracketed by two CUDA events recorded on the
+ * stream it is launched on (previous records are discarded); enable = 0 stops
+ * recording.  Records beyond an internal pool of 65536 launches are dropped. */
+th_status th_profile(th_ctx* ctx, int enable);
+
+/* Sum of the event-timed durations (ms) and the number of launches of kernel
+ * class `kind` since th_profile(ctx, 1).  Synchronises on the recorded events. */
+th_status th_profile_read(th_ctx* ctx, int kind, double* ms, long long* launches);
+
 /* ------------------------------------------------- host-side set-up data */
 /* These run on the host only (no GPU needed) and expose the FP64 set-up the
  * device path is built from, so that it can be checked on its own. */

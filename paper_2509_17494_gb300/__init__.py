@@ -83,6 +83,8 @@ def lib() -> ctypes.CDLL:
         "th_solve": ([P, P, P, I, ctypes.POINTER(SolveInfo), P], I),
         "th_solve_host": ([P, P, P, I, ctypes.POINTER(SolveInfo), P], I),
         "th_launch_count": ([P, ctypes.POINTER(ctypes.c_longlong)], I),
+        "th_profile": ([P, I], I),
+        "th_profile_read": ([P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)], I),
         "th_host_reference_1d": ([I, P, P, P], I),
         "th_host_qsfem_cell": ([D, D, D, P], I),
         "th_host_inverse_rows": ([ctypes.POINTER(Mesh), P, P, ctypes.POINTER(Params), I, P, P,
@@ -239,6 +241,21 @@ class TwoGridSolver:
         v = ctypes.c_longlong(0)
         _check(lib().th_launch_count(self._ctx, ctypes.byref(v)), "th_launch_count")
         return v.value
+
+    KERNELS = ("fine", "dd", "combine", "restrict", "prolong", "coarse_apply", "coarse_solve", "vector", "krylov")
+
+    def profile(self, enable=True):
+        """Start (clearing old records) or stop per-kernel CUDA-event timing."""
+        _check(lib().th_profile(self._ctx, 1 if enable else 0), "th_profile")
+
+    def profile_read(self):
+        """{kernel class: (total ms, launches)} since profile(True)."""
+        out = {}
+        for i, name in enumerate(self.KERNELS):
+            ms, cnt = ctypes.c_double(0), ctypes.c_longlong(0)
+            _check(lib().th_profile_read(self._ctx, i, ctypes.byref(ms), ctypes.byref(cnt)), "th_profile_read")
+            out[name] = (ms.value, cnt.value)
+        return out
 
     # ------------------------------------------------------------- operators
     def apply(self, x, op="A", prec="fp64", out=None):

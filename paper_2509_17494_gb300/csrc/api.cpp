@@ -79,11 +79,42 @@ struct th_ctx {
           *dpart = nullptr;
   double *npart = nullptr, *nrm = nullptr, *scal = nullptr;
   double2 *fin = nullptr, *uin = nullptr;  // device staging for the host-buffer entry points
+  // per-kernel event timing (th_profile)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> prof_rec;  // (kind, first event index)
+  size_t ev_used = 0;
+  ~th_ctx() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
 };
 
 namespace {
 
 th_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TH_OK : TH_ERR_CUDA; }
+// RAII bracket of one kernel launch with two events (only while profiling).
+struct Prof {
+  th_ctx& x;
+  cudaStream_t s;
+  int idx = -1;
+  Prof(th_ctx& x_, int kind, cudaStream_t s_) : x(x_), s(s_) {
+    if (!x.prof_on) return;
+    if (x.ev_used + 2 > 65536) return;
+    while (x.ev_pool.size() < x.ev_used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      x.ev_pool.push_back(e);
+    }
+    idx = (int)x.ev_used;
+    x.ev_used += 2;
+    cudaEventRecord(x.ev_pool[idx], s);
+    x.prof_rec.push_back({kind, idx});
+  }
+  ~Prof() {
+    if (idx >= 0) cudaEventRecord(x.ev_pool[idx + 1], s);
+  }
+};
+
 #define TH_CU(expr)                                   \
   do {                                                \
     cudaError_t _e = (expr);                          \
@@ -231,6 +262,7 @@ th_status fine_apply(th_ctx& x, int op, const typename th::Cx<T>::t* u, const ty
   a.y = y;
   a.residual = f ? 1 : 0;
   x.launches += 1;
+  Prof prof(x, TH_K_FINE, s);
   return cuda_status(th::launch_fine_apply<T>(a, nrhs, s));
 }
 
@@ -290,6 +322,7 @@ th_status dd_apply(th_ctx& x, int wkind, const typename th::Cx<T>::t* r, int nrh
   a.G = std::max(1, std::min(x.ddG, 512 / std::max(1, g.NR)));
   a.nrhs = nrhs;
   x.launches += 1;
+  Prof prof(x, TH_K_DD, s);
   return cuda_status(th::launch_dd_apply<T>(a, wkind, 0, s));
 }
 
@@ -308,6 +341,7 @@ th_status dd_combine(th_ctx& x, typename th::Cx<T>::t* u, int accumulate, int nr
   a.nsub = g.nsub;
   a.accumulate = accumulate;
   x.launches += 1;
+  Prof prof(x, TH_K_COMBINE, s);
   return cuda_status(th::launch_dd_combine<T>(a, nrhs, s));
 }
 
@@ -336,6 +370,7 @@ th_status smooth(th_ctx& x, int wkind, const typename th::Cx<T>::t* f, typename 
   }
   const long long n = x.g.N * (long long)nrhs;
   x.launches += 1;
+  Prof prof(x, TH_K_VECTOR, s);
   if (u_zero) return cuda_status(cudaMemcpyAsync(u, v, sizeof(C) * n, cudaMemcpyDeviceToDevice, s));
   return cuda_status(th::launch_zaxpy<T>(v, u, (T)1, n, s));
 }
@@ -355,6 +390,7 @@ th_status restrict_(th_ctx& x, const typename th::Cx<T>::t* r, typename th::Cx<T
   a.mc = x.g.mc;
   a.q = x.g.q;
   x.launches += 1;
+  Prof prof(x, TH_K_RESTRICT, s);
   return cuda_status(th::launch_restrict<T>(a, nrhs, s));
 }
 
@@ -374,6 +410,7 @@ th_status prolong_(th_ctx& x, const typename th::Cx<T>::t* uc, typename th::Cx<T
   a.q = x.g.q;
   a.omega = omega;
   x.launches += 1;
+  Prof prof(x, TH_K_PROLONG, s);
   return cuda_status(th::launch_prolong<T>(a, nrhs, s));
 }
 
@@ -394,6 +431,7 @@ th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th:
   a.rpc = x.rpc;
   if (!a.G || !a.z) return TH_ERR_UNSUPPORTED;
   x.launches += 1;
+  Prof prof(x, TH_K_COARSE_SOLVE, s);
   return cuda_status(th::launch_coarse_solve<T>(a, nrhs, x.cluster, s));
 }
 
@@ -410,6 +448,7 @@ th_status coarse_apply_(th_ctx& x, const typename th::Cx<T>::t* in, typename th:
   a.nc = x.g.nc;
   a.mc = x.g.mc;
   x.launches += 1;
+  Prof prof(x, TH_K_COARSE_APPLY, s);
   return cuda_status(th::launch_coarse_apply<T>(a, nrhs, s));
 }
 
@@ -433,10 +472,12 @@ th_status cycle(th_ctx& x, int wkind, const typename th::Cx<T>::t* f, typename t
 // Widen / narrow helpers (interleaved complex = 2 reals per entry)
 th_status narrow(th_ctx& x, const double2* in, float2* out, long long n, cudaStream_t s) {
   x.launches += 1;
+  Prof prof(x, TH_K_VECTOR, s);
   return cuda_status(th::launch_d2f((const double*)in, (float*)out, 2 * n, s));
 }
 th_status widen(th_ctx& x, const float2* in, double2* out, long long n, int acc, cudaStream_t s) {
   x.launches += 1;
+  Prof prof(x, TH_K_VECTOR, s);
   return cuda_status(th::launch_f2d((const float*)in, (double*)out, 2 * n, acc, s));
 }
 
@@ -458,7 +499,10 @@ th_status check_nrhs(const th_ctx* x, int nrhs) {
 
 th_status norms(th_ctx& x, const double2* w, int nrhs, std::vector<double>& out, cudaStream_t s) {
   x.launches += 2;
-  TH_CU(th::launch_norm2(w, x.g.N, nrhs, x.npart, x.nrm, x.nblk, s));
+  {
+    Prof prof(x, TH_K_KRYLOV, s);
+    TH_CU(th::launch_norm2(w, x.g.N, nrhs, x.npart, x.nrm, x.nblk, s));
+  }
   out.resize(nrhs);
   TH_CU(cudaMemcpyAsync(out.data(), x.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
   TH_CU(cudaStreamSynchronize(s));
@@ -680,6 +724,33 @@ th_status th_launch_count(const th_ctx* x, long long* n) {
   return TH_OK;
 }
 
+th_status th_profile(th_ctx* x, int enable) {
+  if (!x) return TH_ERR_ARG;
+  if (enable) {
+    x->prof_rec.clear();
+    x->ev_used = 0;
+  }
+  x->prof_on = enable != 0;
+  return TH_OK;
+}
+
+th_status th_profile_read(th_ctx* x, int kind, double* ms, long long* launches) {
+  if (!x || !ms || !launches || kind < 0 || kind >= TH_K_COUNT) return TH_ERR_ARG;
+  double tot = 0.0;
+  long long cnt = 0;
+  for (const auto& r : x->prof_rec) {
+    if (r.first != kind) continue;
+    TH_CU(cudaEventSynchronize(x->ev_pool[r.second + 1]));
+    float t = 0.0f;
+    TH_CU(cudaEventElapsedTime(&t, x->ev_pool[r.second], x->ev_pool[r.second + 1]));
+    tot += t;
+    ++cnt;
+  }
+  *ms = tot;
+  *launches = cnt;
+  return TH_OK;
+}
+
 th_status th_apply(th_ctx* x, int op, const double* xin, double* y, int nrhs, int prec, void* stream) {
   th_status st = check_nrhs(x, nrhs);
   if (st != TH_OK) return st;
@@ -845,10 +916,13 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
       if ((st = fine_apply<double>(*x, TH_OP_A, Zj, nullptr, x->w, nrhs, s)) != TH_OK) return st;
       // classical Gram-Schmidt, twice
       x->launches += 6;
-      TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, nrhs, x->dpart, x->h1, x->nblk, s));
-      TH_CU(th::launch_maxpy(x->Vk, vstride, x->h1, j + 1, x->w, N, j + 1, nrhs, -1.0, s));
-      TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, nrhs, x->dpart, x->h2, x->nblk, s));
-      TH_CU(th::launch_maxpy(x->Vk, vstride, x->h2, j + 1, x->w, N, j + 1, nrhs, -1.0, s));
+      {
+        Prof prof(*x, TH_K_KRYLOV, s);
+        TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, nrhs, x->dpart, x->h1, x->nblk, s));
+        TH_CU(th::launch_maxpy(x->Vk, vstride, x->h1, j + 1, x->w, N, j + 1, nrhs, -1.0, s));
+        TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, nrhs, x->dpart, x->h2, x->nblk, s));
+        TH_CU(th::launch_maxpy(x->Vk, vstride, x->h2, j + 1, x->w, N, j + 1, nrhs, -1.0, s));
+      }
       TH_CU(cudaMemcpyAsync(hh1.data(), x->h1, sizeof(double2) * (j + 1) * nrhs, cudaMemcpyDeviceToHost, s));
       TH_CU(cudaMemcpyAsync(hh2.data(), x->h2, sizeof(double2) * (j + 1) * nrhs, cudaMemcpyDeviceToHost, s));
       if ((st = norms(*x, x->w, nrhs, hn, s)) != TH_OK) return st;
