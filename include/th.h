@@ -172,6 +172,30 @@ th_status th_cycle(th_ctx* ctx, const double* f_dev, double* u_dev, int nrhs, vo
  * cycle, copies u back; synchronous. */
 th_status th_cycle_host(th_ctx* ctx, const double* f_host, double* u_host, int nrhs, void* stream);
 
+/* th_coarse_solve without any workspace scratch (no counterpart in the paper).
+ *
+ * The same FP64 direct coarse solve u_c = A_q^{-1} r_c as th_coarse_solve on an
+ * FP64-prepared context, for callers that cannot allocate device memory when
+ * they need the solve: code running inside another framework's fixed memory
+ * arena, allocation-free real-time paths, or a context shared read-only by
+ * several users, none of whom may reserve per-call scratch.  Its scratch (the
+ * forward-sweep block vectors) lives in a fixed 4 MiB device array of the
+ * library, so the call uses only rc_dev (input), uc_dev (output) and the
+ * context's factors, which it only reads.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *   Limit: Nc * nrhs <= 262144 complex values (e.g. one right-hand side up to a
+ *   401 x 401 coarse grid); larger requests return TH_ERR_ARG.  nrhs must not
+ *   exceed the context's nrhs_max.  A context without FP64 factors returns
+ *   TH_ERR_UNSUPPORTED.
+ *   The array is per GPU and stays allocated until the process exits.  The
+ *   first call on a device looks up the array's device address with that device
+ *   current; make that first call before any CUDA stream capture.
+ *   All calls share the one array and it keeps the last call's contents (every
+ *   entry is written before it is read, so nothing needs clearing); calls whose
+ *   executions overlap on the GPU (other streams) race on it. */
+th_status th_coarse_solve_noalloc(const th_ctx* ctx, const double* rc_dev, double* uc_dev, int nrhs,
+                                  void* stream);
+
 /* Right-preconditioned flexible GMRES(restart) with the two-grid
  * preconditioner, FP64 orthogonalisation.  u holds the initial guess on
  * input and the solution on output.  Synchronous (the Hessenberg update runs

@@ -512,6 +512,23 @@ th_status norms(th_ctx& x, const double2* w, int nrhs, std::vector<double>& out,
 
 }  // namespace
 
+namespace th {
+// Read-only view of the FP64 coarse factors of a context (for th_coarse_solve_noalloc).
+bool coarse_factors_fp64(const th_ctx* x, CoarseSolveArgs<double>* a, int* cluster, int* nrhs_max) {
+  if (!x || !x->G64) return false;
+  a->G = x->G64;
+  a->cl = x->cl64;
+  a->cd = x->cd64;
+  a->cu = x->cu64;
+  a->Nc = x->g.Nc;
+  a->mc = x->g.mc;
+  a->rpc = x->rpc;
+  *cluster = x->cluster;
+  *nrhs_max = x->prm.nrhs_max;
+  return true;
+}
+}  // namespace th
+
 // ====================================================================== ABI
 extern "C" {
 
