@@ -67,8 +67,13 @@ struct th_ctx {
   float *pw32 = nullptr, *rw32 = nullptr;
   double2 *ccell64 = nullptr, *crho64 = nullptr;
   float2 *ccell32 = nullptr, *crho32 = nullptr;
-  double2 *G64 = nullptr, *cl64 = nullptr, *cd64 = nullptr, *cu64 = nullptr;
-  float2 *G32 = nullptr, *cl32 = nullptr, *cd32 = nullptr, *cu32 = nullptr;
+  double2 *G64 = nullptr, *cl64 = nullptr, *cd64 = nullptr, *cu64 = nullptr;  // G64: unpartitioned (no-alloc path)
+  float2 *cl32 = nullptr, *cd32 = nullptr, *cu32 = nullptr;
+  // partitioned coarse factors (both precisions when prepared)
+  int P = 1, mcp = 0, Lmax = 0;
+  int *ca = nullptr, *cb = nullptr, *sep = nullptr, *chunk_of = nullptr;
+  double2 *Gp64 = nullptr, *LR64 = nullptr, *Gh64 = nullptr, *Fh64 = nullptr, *Hh64 = nullptr;
+  float2 *Gp32 = nullptr, *LR32 = nullptr, *Gh32 = nullptr, *Fh32 = nullptr, *Hh32 = nullptr;
   // cycle work vectors
   double2 *r64 = nullptr, *s64 = nullptr, *v64 = nullptr, *V64 = nullptr, *rc64 = nullptr, *uc64 = nullptr,
           *zc64 = nullptr, *t64 = nullptr;
@@ -149,6 +154,19 @@ void carve_all(th_ctx& x, Carve& c) {
   x.wscale16 = has_prec(x.avail, TH_PREC_FP16) ? c.take<float>(g.nsub) : nullptr;
   const bool fp64 = has_prec(x.avail, TH_PREC_FP64);
   x.G64 = fp64 ? c.take<double2>(mm * g.mc) : nullptr;
+  const size_t blk = (size_t)g.mc * x.mcp;  // one padded dense block
+  const int K = std::max(x.P - 1, 1);
+  x.ca = c.take<int>(x.P);
+  x.cb = c.take<int>(x.P);
+  x.sep = c.take<int>(K);
+  x.chunk_of = c.take<int>(g.mc);
+  if (fp64) {
+    x.Gp64 = c.take<double2>(blk * g.mc);
+    x.LR64 = c.take<double2>(2 * blk * g.mc);
+    x.Gh64 = c.take<double2>(blk * K);
+    x.Fh64 = c.take<double2>(blk * K);
+    x.Hh64 = c.take<double2>(blk * K);
+  }
   // FP64 work vectors are always present (residuals, FGMRES, FP64 applies)
   x.r64 = c.take<double2>((size_t)nr * g.N);
   x.s64 = c.take<double2>((size_t)nr * g.N);
@@ -157,7 +175,7 @@ void carve_all(th_ctx& x, Carve& c) {
   x.V64 = fp64 ? c.take<double2>((size_t)nr * g.nsub * g.NR) : nullptr;
   x.rc64 = c.take<double2>((size_t)nr * g.Nc);
   x.uc64 = c.take<double2>((size_t)nr * g.Nc);
-  x.zc64 = fp64 ? c.take<double2>((size_t)nr * g.Nc) : nullptr;
+
   if (x.mixed) {
     x.kc32 = c.take<float>(n2);
     x.ec32 = c.take<float>(n2);
@@ -168,7 +186,11 @@ void carve_all(th_ctx& x, Carve& c) {
     x.cl32 = c.take<float2>(mm);
     x.cd32 = c.take<float2>(mm);
     x.cu32 = c.take<float2>(mm);
-    x.G32 = c.take<float2>(mm * g.mc);
+    x.Gp32 = c.take<float2>(blk * g.mc);
+    x.LR32 = c.take<float2>(2 * blk * g.mc);
+    x.Gh32 = c.take<float2>(blk * K);
+    x.Fh32 = c.take<float2>(blk * K);
+    x.Hh32 = c.take<float2>(blk * K);
     x.f32 = c.take<float2>((size_t)nr * g.N);
     x.u32 = c.take<float2>((size_t)nr * g.N);
     x.r32 = c.take<float2>((size_t)nr * g.N);
@@ -177,7 +199,6 @@ void carve_all(th_ctx& x, Carve& c) {
     x.V32 = c.take<float2>((size_t)nr * g.nsub * g.NR);
     x.rc32 = c.take<float2>((size_t)nr * g.Nc);
     x.uc32 = c.take<float2>((size_t)nr * g.Nc);
-    x.zc32 = c.take<float2>((size_t)nr * g.Nc);
   }
   const int m = prm.restart;
   x.Vk = c.take<double2>((size_t)(m + 1) * nr * g.N);
@@ -201,6 +222,7 @@ th_status prepare(const th_mesh* mesh, const th_params* prm, th_ctx& x) {
   x.prm = *prm;
   th_status st = th::make_geometry(*mesh, *prm, x.g);
   if (st != TH_OK) return st;
+  if (x.g.mc > 1024) return TH_ERR_UNSUPPORTED;  // coarse kernels hold two coarse rows per thread
   x.avail = (prm->prec_mask & 0xFu) | (1u << prm->prec);
   x.active = prm->prec;
   x.mixed = (x.avail & ~1u) != 0;
@@ -212,6 +234,12 @@ th_status prepare(const th_mesh* mesh, const th_params* prm, th_ctx& x) {
   x.ref = ref;
   x.cluster = 8;
   x.rpc = (x.g.mc + x.cluster - 1) / x.cluster;
+  x.P = th::coarse_chunks(x.g.mc);
+  x.mcp = x.g.mc + (x.g.mc & 1);
+  {
+    const int rows = x.g.mc - (x.P - 1);
+    x.Lmax = rows / x.P + ((rows % x.P) ? 1 : 0);
+  }
   return TH_OK;
 }
 
@@ -274,10 +302,13 @@ template <> struct PrecBufs<double> {
   static double2* V(th_ctx& x) { return x.V64; }
   static double2* rc(th_ctx& x) { return x.rc64; }
   static double2* uc(th_ctx& x) { return x.uc64; }
-  static double2* zc(th_ctx& x) { return x.zc64; }
+  static const double2* Gp(th_ctx& x) { return x.Gp64; }
+  static const double2* LR(th_ctx& x) { return x.LR64; }
+  static const double2* Gh(th_ctx& x) { return x.Gh64; }
+  static const double2* Fh(th_ctx& x) { return x.Fh64; }
+  static const double2* Hh(th_ctx& x) { return x.Hh64; }
   static const double* pw(th_ctx& x) { return x.pw64; }
   static const double* rw(th_ctx& x) { return x.rw64; }
-  static const double2* G(th_ctx& x) { return x.G64; }
   static const double2* cl(th_ctx& x) { return x.cl64; }
   static const double2* cd(th_ctx& x) { return x.cd64; }
   static const double2* cu(th_ctx& x) { return x.cu64; }
@@ -291,10 +322,13 @@ template <> struct PrecBufs<float> {
   static float2* V(th_ctx& x) { return x.V32; }
   static float2* rc(th_ctx& x) { return x.rc32; }
   static float2* uc(th_ctx& x) { return x.uc32; }
-  static float2* zc(th_ctx& x) { return x.zc32; }
+  static const float2* Gp(th_ctx& x) { return x.Gp32; }
+  static const float2* LR(th_ctx& x) { return x.LR32; }
+  static const float2* Gh(th_ctx& x) { return x.Gh32; }
+  static const float2* Fh(th_ctx& x) { return x.Fh32; }
+  static const float2* Hh(th_ctx& x) { return x.Hh32; }
   static const float* pw(th_ctx& x) { return x.pw32; }
   static const float* rw(th_ctx& x) { return x.rw32; }
-  static const float2* G(th_ctx& x) { return x.G32; }
   static const float2* cl(th_ctx& x) { return x.cl32; }
   static const float2* cd(th_ctx& x) { return x.cd32; }
   static const float2* cu(th_ctx& x) { return x.cu32; }
@@ -418,21 +452,31 @@ template <typename T>
 th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th::Cx<T>::t* uc, int nrhs,
                         cudaStream_t s) {
   using B = PrecBufs<T>;
-  th::CoarseSolveArgs<T> a{};
-  a.rhs = rc;
+  th::CoarsePartArgs<T> a{};
+  a.b = rc;
   a.x = uc;
-  a.z = B::zc(x);
-  a.G = B::G(x);
+  a.G = B::Gp(x);
+  a.LR = B::LR(x);
+  a.Gh = B::Gh(x);
+  a.Fh = B::Fh(x);
+  a.Hh = B::Hh(x);
   a.cl = B::cl(x);
   a.cd = B::cd(x);
   a.cu = B::cu(x);
+  a.ca = x.ca;
+  a.cb = x.cb;
+  a.sep = x.sep;
+  a.chunk_of = x.chunk_of;
   a.Nc = x.g.Nc;
   a.mc = x.g.mc;
+  a.mcp = x.mcp;
+  a.P = x.P;
   a.rpc = x.rpc;
-  if (!a.G || !a.z) return TH_ERR_UNSUPPORTED;
-  x.launches += 1;
+  a.Lmax = x.Lmax;
+  if (!a.G || !a.LR) return TH_ERR_UNSUPPORTED;
+  x.launches += (x.P > 1) ? 3 : 1;
   Prof prof(x, TH_K_COARSE_SOLVE, s);
-  return cuda_status(th::launch_coarse_solve<T>(a, nrhs, x.cluster, s));
+  return cuda_status(th::launch_coarse_part<T>(a, nrhs, x.cluster, s));
 }
 
 template <typename T>
@@ -592,6 +636,8 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
   th::transfer_tables(g, x->ref, tt);
   th::CoarseBlocks cb;
   if ((st = th::coarse_setup(g, k_host, eps, cb)) != TH_OK) return st;
+  th::CoarsePart cpart;
+  if ((st = th::coarse_partition(g, cb, x->P, cpart)) != TH_OK) return st;
   std::vector<cplx> Wh;
   if ((st = th::all_inverse_rows(g, x->ref, k_host, eps, x->prm.alpha_s, Wh)) != TH_OK) return st;
 
@@ -640,13 +686,47 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     G64h = to2(cb.G);
     if ((st = up(x->G64, G64h.data(), G64h.size() * 16)) != TH_OK) return st;
   }
-  std::vector<float2> cell32, rho32, cl32, cd32, cu32, G32;
+  {
+    std::vector<int> chunk_of(g.mc, -1);
+    for (int c = 0; c < x->P; ++c)
+      for (int j = cpart.ca[c]; j <= cpart.cb[c]; ++j) chunk_of[j] = c;
+    std::vector<int> sep(std::max(x->P - 1, 1), 0);
+    std::copy(cpart.sep.begin(), cpart.sep.end(), sep.begin());
+    if ((st = up(x->ca, cpart.ca.data(), cpart.ca.size() * 4)) != TH_OK) return st;
+    if ((st = up(x->cb, cpart.cb.data(), cpart.cb.size() * 4)) != TH_OK) return st;
+    if ((st = up(x->sep, sep.data(), sep.size() * 4)) != TH_OK) return st;
+    if ((st = up(x->chunk_of, chunk_of.data(), chunk_of.size() * 4)) != TH_OK) return st;
+    TH_CU(cudaStreamSynchronize(s));
+  }
+  // partitioned factors, FP64 and/or FP32 (one staging vector at a time)
+  auto upload_c = [&](double2* d64, float2* d32, const std::vector<cplx>& v) -> th_status {
+    if (d64) {
+      std::vector<double2> t = to2(v);
+      th_status r = up(d64, t.data(), t.size() * 16);
+      if (r != TH_OK) return r;
+      if (cudaStreamSynchronize(s) != cudaSuccess) return TH_ERR_CUDA;
+    }
+    if (d32) {
+      std::vector<float2> t = to2f(v);
+      th_status r = up(d32, t.data(), t.size() * 8);
+      if (r != TH_OK) return r;
+      if (cudaStreamSynchronize(s) != cudaSuccess) return TH_ERR_CUDA;
+    }
+    return TH_OK;
+  };
+  if ((st = upload_c(x->Gp64, x->Gp32, cpart.G)) != TH_OK) return st;
+  if ((st = upload_c(x->LR64, x->LR32, cpart.LR)) != TH_OK) return st;
+  if (x->P > 1) {
+    if ((st = upload_c(x->Gh64, x->Gh32, cpart.Gh)) != TH_OK) return st;
+    if ((st = upload_c(x->Fh64, x->Fh32, cpart.Fh)) != TH_OK) return st;
+    if ((st = upload_c(x->Hh64, x->Hh32, cpart.Hh)) != TH_OK) return st;
+  }
+  std::vector<float2> cell32, rho32, cl32, cd32, cu32;
   if (x->mixed) {
     cell32 = to2f(cb.cell);
     cl32 = to2f(cb.cl);
     cd32 = to2f(cb.cd);
     cu32 = to2f(cb.cu);
-    G32 = to2f(cb.G);
     rho32.resize(rho64.size());
     for (size_t i = 0; i < rho64.size(); ++i) rho32[i] = make_float2((float)rho64[i].x, (float)rho64[i].y);
     if ((st = up(x->kc32, kf.data(), n2 * 4)) != TH_OK) return st;
@@ -658,7 +738,6 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     if ((st = up(x->cl32, cl32.data(), mm * 8)) != TH_OK) return st;
     if ((st = up(x->cd32, cd32.data(), mm * 8)) != TH_OK) return st;
     if ((st = up(x->cu32, cu32.data(), mm * 8)) != TH_OK) return st;
-    if ((st = up(x->G32, G32.data(), G32.size() * 8)) != TH_OK) return st;
   }
   // inverse rows in the chunk-major layouts
   const size_t blk = (size_t)g.NR * g.NC;

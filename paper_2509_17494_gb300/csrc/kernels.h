@@ -101,6 +101,29 @@ struct CoarseSolveArgs {
 template <typename T>
 cudaError_t launch_coarse_solve(const CoarseSolveArgs<T>& a, int nrhs, int cluster, cudaStream_t s);
 
+// ------------------------------------------------------- K8 partitioned coarse solve
+template <typename T>
+struct CoarsePartArgs {
+  const typename Cx<T>::t* b;    // [rhs][Nc]
+  typename Cx<T>::t* x;          // [rhs][Nc]
+  const typename Cx<T>::t* G;    // chunk-row block inverses, mc blocks of mc x mcp
+  const typename Cx<T>::t* LR;   // spikes [L_j | R_j], mc blocks of mc x 2 mcp
+  const typename Cx<T>::t* Gh;   // reduced factors, P - 1 blocks of mc x mcp each
+  const typename Cx<T>::t* Fh;
+  const typename Cx<T>::t* Hh;
+  const typename Cx<T>::t* cl;   // C_j diagonals
+  const typename Cx<T>::t* cd;
+  const typename Cx<T>::t* cu;
+  const int* ca;                 // chunk first rows
+  const int* cb;                 // chunk last rows
+  const int* sep;                // separator rows
+  const int* chunk_of;           // per row: chunk index, or -1 for a separator
+  long long Nc;
+  int mc, mcp, P, rpc, Lmax;
+};
+template <typename T>
+cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster, cudaStream_t s);
+
 // ------------------------------------------------------- vectors (K9/K10)
 cudaError_t launch_d2f(const double* in, float* out, long long n, cudaStream_t s);
 cudaError_t launch_f2d(const float* in, double* out, long long n, int accumulate, cudaStream_t s);

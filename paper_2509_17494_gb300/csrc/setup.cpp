@@ -633,4 +633,245 @@ void transfer_tables(const Geometry& g, const Ref1D& ref, TransferTables& t) {
   }
 }
 
+// ------------------------------------------------ partitioned coarse solve
+// The coarse rows are split into P chunks [a_c, b_c] separated by P - 1
+// separator rows s_c = b_c + 1.  With y = A_cc^{-1} b_c (chunk c alone), the
+// chunk rows of the solution are
+//     x_j = y_j - L_j x_{s_{c-1}} - R_j x_{s_c},
+//     L = A_cc^{-1} E_a B_a (left spike),  R = A_cc^{-1} E_b C_b (right spike),
+// and the separators satisfy a block-tridiagonal system with P - 1 rows:
+//     Shat_k x_k + What_k x_{k-1} + Ehat_k x_{k+1} = b_s - B_s y_{s-1} - C_s y_{s+1},
+//     Shat_k = D_s - B_s R_{s-1} - C_s L_{s+1},  What_k = -B_s L_{s-1},  Ehat_k = -C_s R_{s+1},
+// factorised as Ghat_k = (Shat_k - What_k Ghat_{k-1} Ehat_{k-1})^{-1}, F_k = Ghat_k What_k,
+// H_k = Ghat_k Ehat_k.  Everything in FP64; dense blocks are stored with row stride mcp.
+namespace {
+
+using Mat = std::vector<cplx>;
+
+// C = alpha A B (+ C when acc), n x n dense row-major, serial (i-k-j order)
+void zgemm(int n, const cplx* A, const cplx* B, cplx* C, cplx alpha, bool acc) {
+  if (!acc) std::fill(C, C + (size_t)n * n, cplx(0.0));
+  for (int i = 0; i < n; ++i) {
+    double* ci = reinterpret_cast<double*>(C + (size_t)i * n);
+    for (int k = 0; k < n; ++k) {
+      const cplx a = alpha * A[(size_t)i * n + k];
+      const double ar = a.real(), ai = a.imag();
+      if (ar == 0.0 && ai == 0.0) continue;
+      const double* bk = reinterpret_cast<const double*>(B + (size_t)k * n);
+      for (int j = 0; j < n; ++j) {
+        const double br = bk[2 * j], bi = bk[2 * j + 1];
+        ci[2 * j] += ar * br - ai * bi;
+        ci[2 * j + 1] += ar * bi + ai * br;
+      }
+    }
+  }
+}
+
+// Tridiagonal block helpers over the C_j diagonals (cl, cd, cu at row offset o = j mc):
+// (C_j X)[a][:] = cl[a] X[a-1] + cd[a] X[a] + cu[a] X[a+1]
+void tri_C_left(int n, const cplx* cl, const cplx* cd, const cplx* cu, const cplx* X, cplx* Y) {
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      cplx s = cd[a] * X[(size_t)a * n + b];
+      if (a > 0) s += cl[a] * X[(size_t)(a - 1) * n + b];
+      if (a + 1 < n) s += cu[a] * X[(size_t)(a + 1) * n + b];
+      Y[(size_t)a * n + b] = s;
+    }
+}
+// (B_{j+1} X) with B_{j+1} = C_j^T: row a = cu[a-1] X[a-1] + cd[a] X[a] + cl[a+1] X[a+1]
+void tri_CT_left(int n, const cplx* cl, const cplx* cd, const cplx* cu, const cplx* X, cplx* Y) {
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      cplx s = cd[a] * X[(size_t)a * n + b];
+      if (a > 0) s += cu[a - 1] * X[(size_t)(a - 1) * n + b];
+      if (a + 1 < n) s += cl[a + 1] * X[(size_t)(a + 1) * n + b];
+      Y[(size_t)a * n + b] = s;
+    }
+}
+// Y = X C_j: Y[a][b] = X[a][b-1] cu[b-1] + X[a][b] cd[b] + X[a][b+1] cl[b+1]
+void tri_C_right(int n, const cplx* cl, const cplx* cd, const cplx* cu, const cplx* X, cplx* Y) {
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      cplx s = X[(size_t)a * n + b] * cd[b];
+      if (b > 0) s += X[(size_t)a * n + b - 1] * cu[b - 1];
+      if (b + 1 < n) s += X[(size_t)a * n + b + 1] * cl[b + 1];
+      Y[(size_t)a * n + b] = s;
+    }
+}
+// Y = X C_j^T: Y[a][b] = X[a][b-1] cl[b] + X[a][b] cd[b] + X[a][b+1] cu[b]
+void tri_CT_right(int n, const cplx* cl, const cplx* cd, const cplx* cu, const cplx* X, cplx* Y) {
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      cplx s = X[(size_t)a * n + b] * cd[b];
+      if (b > 0) s += X[(size_t)a * n + b - 1] * cl[b];
+      if (b + 1 < n) s += X[(size_t)a * n + b + 1] * cu[b];
+      Y[(size_t)a * n + b] = s;
+    }
+}
+bool zinverse_serial(int n, Mat& S, cplx* out) {
+  std::vector<int> piv;
+  if (!band_lu(S.data(), n, n - 1, n - 1, piv)) return false;
+  std::vector<cplx> x(n);
+  for (int c = 0; c < n; ++c) {
+    std::fill(x.begin(), x.end(), cplx(0.0));
+    x[c] = 1.0;
+    band_solve(S.data(), n, n - 1, n - 1, piv, x.data());
+    for (int r = 0; r < n; ++r) out[(size_t)r * n + c] = x[r];
+  }
+  return true;
+}
+
+void store_padded(int n, int ld, const cplx* M, cplx* dst) {
+  for (int r = 0; r < n; ++r) std::copy(M + (size_t)r * n, M + (size_t)(r + 1) * n, dst + (size_t)r * ld);
+}
+
+}  // namespace
+
+int coarse_chunks(int mc) {
+  int P = (int)std::lround(std::sqrt((double)mc));
+  P = std::max(1, std::min(P, (mc + 1) / 2));
+  return P;
+}
+
+th_status coarse_partition(const Geometry& g, const CoarseBlocks& cb, int P, CoarsePart& cp) {
+  const int mc = g.mc;
+  const size_t mm = (size_t)mc * mc;
+  if (P < 1 || 2 * P - 1 > mc) return TH_ERR_ARG;
+  cp.P = P;
+  cp.mcp = mc + (mc & 1);
+  const int ld = cp.mcp;
+  // chunk sizes as equal as possible, P - 1 separator rows between them
+  const int rows = mc - (P - 1);
+  const int base = rows / P, rem = rows % P;
+  cp.ca.assign(P, 0);
+  cp.cb.assign(P, 0);
+  cp.sep.assign(std::max(P - 1, 0), 0);
+  int r0 = 0;
+  for (int c = 0; c < P; ++c) {
+    const int L = base + (c < rem ? 1 : 0);
+    cp.ca[c] = r0;
+    cp.cb[c] = r0 + L - 1;
+    if (c < P - 1) cp.sep[c] = r0 + L;
+    r0 += L + 1;
+  }
+  cp.G.assign((size_t)mc * mc * ld, cplx(0.0));
+  cp.LR.assign((size_t)mc * mc * 2 * ld, cplx(0.0));
+  const cplx* cl = cb.cl.data();
+  const cplx* cd = cb.cd.data();
+  const cplx* cu = cb.cu.data();
+  std::vector<Mat> Rend(P), Lend(P), Lbeg(P), Rbeg(P);  // spikes at the chunk ends
+  std::atomic<int> err(0);
+  parallel_for(P, [&](int c) {
+    const int a = cp.ca[c], b = cp.cb[c], L = b - a + 1;
+    std::vector<Mat> G(L, Mat(mm));
+    Mat S(mm), T(mm), U(mm);
+    for (int jj = 0; jj < L; ++jj) {
+      const int j = a + jj;
+      std::fill(S.begin(), S.end(), cplx(0.0));
+      const size_t o = (size_t)j * mc;
+      for (int r = 0; r < mc; ++r) {
+        if (r > 0) S[(size_t)r * mc + r - 1] = cb.dl[o + r];
+        S[(size_t)r * mc + r] = cb.dd[o + r];
+        if (r + 1 < mc) S[(size_t)r * mc + r + 1] = cb.du[o + r];
+      }
+      if (jj > 0) {
+        const size_t op = (size_t)(j - 1) * mc;
+        tri_C_right(mc, cl + op, cd + op, cu + op, G[jj - 1].data(), T.data());  // T = G_{j-1} C_{j-1}
+        tri_CT_left(mc, cl + op, cd + op, cu + op, T.data(), U.data());  // B_j T
+        for (size_t i = 0; i < mm; ++i) S[i] -= U[i];
+      }
+      if (!zinverse_serial(mc, S, G[jj].data())) { err.store(1); return; }
+      store_padded(mc, ld, G[jj].data(), &cp.G[(size_t)j * mc * ld]);
+    }
+    // right spike: R_b = G_b C_b, R_j = -G_j C_j R_{j+1}
+    if (c < P - 1) {
+      Mat R(mm), Rn(mm);
+      const size_t ob = (size_t)b * mc;
+      tri_C_right(mc, cl + ob, cd + ob, cu + ob, G[L - 1].data(), R.data());
+      for (int jj = L - 1; jj >= 0; --jj) {
+        const int j = a + jj;
+        if (jj < L - 1) {
+          const size_t o = (size_t)j * mc;
+          tri_C_left(mc, cl + o, cd + o, cu + o, R.data(), T.data());
+          zgemm(mc, G[jj].data(), T.data(), Rn.data(), -1.0, false);
+          std::swap(R, Rn);
+        }
+        for (int r = 0; r < mc; ++r)
+          std::copy(&R[(size_t)r * mc], &R[(size_t)(r + 1) * mc], &cp.LR[((size_t)j * mc + r) * 2 * ld + ld]);
+        if (jj == L - 1) Rend[c] = R;
+        if (jj == 0) Rbeg[c] = R;
+      }
+    }
+    // left spike: Z_a = G_a B_a, Z_j = -G_j B_j Z_{j-1}; L_b = Z_b, L_j = Z_j - G_j C_j L_{j+1}
+    if (c > 0) {
+      std::vector<Mat> Z(L, Mat(mm));
+      const size_t oa = (size_t)(a - 1) * mc;  // B_a = C_{a-1}^T
+      tri_CT_right(mc, cl + oa, cd + oa, cu + oa, G[0].data(), Z[0].data());
+      for (int jj = 1; jj < L; ++jj) {
+        const size_t op = (size_t)(a + jj - 1) * mc;
+        tri_CT_left(mc, cl + op, cd + op, cu + op, Z[jj - 1].data(), T.data());
+        zgemm(mc, G[jj].data(), T.data(), Z[jj].data(), -1.0, false);
+      }
+      Mat Lc = Z[L - 1];
+      for (int jj = L - 1; jj >= 0; --jj) {
+        const int j = a + jj;
+        if (jj < L - 1) {
+          const size_t o = (size_t)j * mc;
+          tri_C_left(mc, cl + o, cd + o, cu + o, Lc.data(), T.data());
+          Lc = Z[jj];
+          zgemm(mc, G[jj].data(), T.data(), Lc.data(), -1.0, true);
+        }
+        for (int r = 0; r < mc; ++r)
+          std::copy(&Lc[(size_t)r * mc], &Lc[(size_t)(r + 1) * mc], &cp.LR[((size_t)j * mc + r) * 2 * ld]);
+        if (jj == L - 1) Lend[c] = Lc;
+        if (jj == 0) Lbeg[c] = Lc;
+      }
+    }
+  });
+  if (err.load()) return TH_ERR_SINGULAR;
+  // reduced system on the separators
+  const int K = P - 1;
+  cp.Gh.assign((size_t)std::max(K, 0) * mc * ld, cplx(0.0));
+  cp.Fh.assign((size_t)std::max(K, 0) * mc * ld, cplx(0.0));
+  cp.Hh.assign((size_t)std::max(K, 0) * mc * ld, cplx(0.0));
+  Mat Ghp(mm), Eprev(mm), S(mm), T(mm), U(mm), W(mm), E(mm), Gk(mm);
+  for (int k = 0; k < K; ++k) {
+    const int s = cp.sep[k];
+    const size_t os = (size_t)s * mc, op = (size_t)(s - 1) * mc;
+    std::fill(S.begin(), S.end(), cplx(0.0));
+    for (int r = 0; r < mc; ++r) {
+      if (r > 0) S[(size_t)r * mc + r - 1] = cb.dl[os + r];
+      S[(size_t)r * mc + r] = cb.dd[os + r];
+      if (r + 1 < mc) S[(size_t)r * mc + r + 1] = cb.du[os + r];
+    }
+    // - B_s R^{(k)}_{s-1} - C_s L^{(k+1)}_{s+1}
+    tri_CT_left(mc, cl + op, cd + op, cu + op, Rend[k].data(), T.data());
+    tri_C_left(mc, cl + os, cd + os, cu + os, Lbeg[k + 1].data(), U.data());
+    for (size_t i = 0; i < mm; ++i) S[i] -= T[i] + U[i];
+    // What_k = -B_s L^{(k)}_{s-1},  Ehat_k = -C_s R^{(k+1)}_{s+1}
+    if (k > 0) {
+      tri_CT_left(mc, cl + op, cd + op, cu + op, Lend[k].data(), W.data());
+      for (auto& v : W) v = -v;
+      // S -= What_k Ghat_{k-1} Ehat_{k-1}
+      zgemm(mc, Ghp.data(), Eprev.data(), T.data(), 1.0, false);
+      zgemm(mc, W.data(), T.data(), S.data(), -1.0, true);
+    }
+    if (!zinverse_serial(mc, S, Gk.data())) return TH_ERR_SINGULAR;
+    store_padded(mc, ld, Gk.data(), &cp.Gh[(size_t)k * mc * ld]);
+    if (k > 0) {
+      zgemm(mc, Gk.data(), W.data(), T.data(), 1.0, false);
+      store_padded(mc, ld, T.data(), &cp.Fh[(size_t)k * mc * ld]);
+    }
+    if (k < K - 1) {
+      tri_C_left(mc, cl + os, cd + os, cu + os, Rbeg[k + 1].data(), E.data());
+      for (auto& v : E) v = -v;
+      zgemm(mc, Gk.data(), E.data(), T.data(), 1.0, false);
+      store_padded(mc, ld, T.data(), &cp.Hh[(size_t)k * mc * ld]);
+      Eprev = E;
+    }
+    Ghp = Gk;
+  }
+  return TH_OK;
+}
+
 }  // namespace th

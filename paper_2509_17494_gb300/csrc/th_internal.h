@@ -77,6 +77,19 @@ struct CoarseBlocks {
 };
 th_status coarse_setup(const Geometry& g, const double* k, const double* eps, CoarseBlocks& cb);
 
+// Partitioned form of the coarse block-tridiagonal system (see coarse_partition).
+struct CoarsePart {
+  int P = 1;                      // chunks of coarse rows
+  int mcp = 0;                    // padded row stride of dense blocks (even)
+  std::vector<int> ca, cb;        // chunk row ranges [ca, cb]
+  std::vector<int> sep;           // separator rows, P - 1
+  std::vector<cplx> G;            // mc blocks (chunk rows; separator slots zero), mc x mcp each
+  std::vector<cplx> LR;           // mc blocks of mc x (2 mcp): [L_j | R_j] spikes
+  std::vector<cplx> Gh, Fh, Hh;   // P - 1 blocks each, mc x mcp: reduced factors
+};
+th_status coarse_partition(const Geometry& g, const CoarseBlocks& cb, int P, CoarsePart& cp);
+int coarse_chunks(int mc);
+
 // Transfer tables.
 struct TransferTables {
   int q = 0, rmax = 0;
