@@ -39,7 +39,7 @@ HBM_FALLBACK_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_dd_apply (BF16 rows,
 # 1 rhs) launch on this workload, from the ncu capture summarised in
 # profiles/k_dd_apply_bf16_square40_q4_n100.md; None once the kernel changes.
-DD_TRAFFIC_BYTES = 241.1e6
+DD_TRAFFIC_BYTES = {0: 241.1e6, 1: None}
 
 
 def parse():
@@ -221,8 +221,10 @@ def run_native(args):
         return ms, S.launch_count() - l0, prof, ck, u
 
     clocks = ClockSampler(local)
-    ms_mixed, launches, prof, ck, _ = timed_cycles("bf16", args.steps, args.warmup, profile=True, clocks=clocks)
+    ms_mixed, launches, _, ck, _ = timed_cycles("bf16", args.steps, args.warmup, clocks=clocks)
     ms_mixed = max_over_ranks(ms_mixed, world, dev)
+    # a second pass of the same steps with per-kernel CUDA events (library's th_profile)
+    ms_prof, _, prof, _, _ = timed_cycles("bf16", args.steps, 1, profile=True)
     steps64 = max(3, args.steps // 2)
     ms_fp64, _, prof64, _, _ = timed_cycles("fp64", steps64, max(3, args.warmup // 2), profile=True)
     ms_fp64 = max_over_ranks(ms_fp64, world, dev)
@@ -255,21 +257,26 @@ def run_native(args):
     ms_e2e = (time.perf_counter() - te) * 1e3 / e2e_steps
     ms_e2e = max_over_ranks(ms_e2e, world, dev)
 
+    S.device_status()
     gdofs = lambda ms: N * world / (ms * 1e-3) / 1e9
     # roofline of the dominant kernel class (by time) of the mixed cycle
     per_step = {k: (v[0] / args.steps, v[1] / args.steps) for k, v in prof.items()}
     dominant = max(per_step, key=lambda k: per_step[k][0])
     dd_ms, dd_cnt = prof["dd"]
     dd_avg_ms = dd_ms / max(dd_cnt, 1)
+    dd_kernel = "k_dd_stream (TMA bulk)" if S.get_variant("dd", "fp32") else "k_dd_apply"
     alg_bytes, _ = dd_algorithmic_bytes(n, p, w["l_dd"], 4, 8)
     hbm, peak_src = peaks()
     achieved = alg_bytes / (dd_avg_ms * 1e-3) / 1e9
-    roofline = {"kernel": "k_dd_apply (BF16 inverse rows, 1 rhs)", "bound": "hbm", "achieved": round(achieved, 1),
+    roofline = {"kernel": f"{dd_kernel}, BF16 inverse rows, 1 rhs", "bound": "hbm", "achieved": round(achieved, 1),
                 "peak": hbm, "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": DD_TRAFFIC_BYTES, "alg_bytes_per_launch": int(alg_bytes),
+                "traffic": DD_TRAFFIC_BYTES.get(S.get_variant("dd", "fp32")), "alg_bytes_per_launch": int(alg_bytes),
                 "avg_launch_ms": round(dd_avg_ms, 5),
                 "dominant_by_time": dominant,
-                "share_of_step": {k: round(v[0] / ms_mixed, 3) for k, v in per_step.items() if v[1] > 0}}
+                "profiled_ms_per_step": round(ms_prof, 4),
+                "share_of_step": {k: round(v[0] / ms_prof, 3) for k, v in per_step.items() if v[1] > 0},
+                "variants": {"dd_fp32": S.get_variant("dd", "fp32"), "fine_fp32": S.get_variant("fine", "fp32"),
+                             "dd_fp64": S.get_variant("dd", "fp64"), "fine_fp64": S.get_variant("fine", "fp64")}}
 
     line = {
         "metric": METRIC,

@@ -127,6 +127,13 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
                    const th_params* prm, void* workspace_dev, size_t bytes,
                    void* stream, th_ctx** out);
 
+/* Device-side status: synchronises `stream` and returns TH_ERR_TIMEOUT if a
+ * bounded device wait of an earlier kernel gave up (the flag is then cleared),
+ * TH_OK otherwise.  Kernels that wait on mbarriers do so with an iteration
+ * limit; on a timeout they drain their copies in flight and return early, so
+ * the results of that launch are invalid. */
+th_status th_device_status(th_ctx* ctx, void* stream);
+
 /* Selects the active cycle precision (must have been prepared at set-up). */
 th_status th_set_precision(th_ctx* ctx, int prec);
 
@@ -235,6 +242,17 @@ th_status th_profile(th_ctx* ctx, int enable);
 /* Sum of the event-timed durations (ms) and the number of launches of kernel
  * class `kind` since th_profile(ctx, 1).  Synchronises on the recorded events. */
 th_status th_profile_read(th_ctx* ctx, int kind, double* ms, long long* launches);
+
+/* Kernel variants chosen by the set-up autotuner (which times each candidate
+ * on the context's own problem with CUDA events):
+ *   TH_K_FINE: 0 = large cell tile, 1 = small cell tile;
+ *   TH_K_DD:   0 = per-subdomain CTAs with direct loads,
+ *              1 = persistent CTAs streaming the rows through TMA bulk copies.
+ * prec selects the FP64 or the FP32-cycle kernels (TH_PREC_FP64 / TH_PREC_FP32).
+ * Overriding is for testing and measurement; every variant computes the same
+ * result up to summation order. */
+th_status th_set_kernel_variant(th_ctx* ctx, int kernel, int prec, int variant);
+th_status th_get_kernel_variant(const th_ctx* ctx, int kernel, int prec, int* variant);
 
 /* ------------------------------------------------- host-side set-up data */
 /* These run on the host only (no GPU needed) and expose the FP64 set-up the

@@ -71,6 +71,9 @@ def lib() -> ctypes.CDLL:
         "th_setup": ([ctypes.POINTER(Mesh), P, P, ctypes.POINTER(Params), P, ctypes.c_size_t, P,
                       ctypes.POINTER(P)], I),
         "th_set_precision": ([P, I], I),
+        "th_device_status": ([P, P], I),
+        "th_set_kernel_variant": ([P, I, I, I], I),
+        "th_get_kernel_variant": ([P, I, I, ctypes.POINTER(I)], I),
         "th_destroy": ([P], V),
         "th_apply": ([P, I, P, P, I, I, P], I),
         "th_residual": ([P, P, P, P, I, P], I),
@@ -236,6 +239,21 @@ class TwoGridSolver:
 
     def set_precision(self, prec):
         _check(lib().th_set_precision(self._ctx, PREC[prec]), "th_set_precision")
+
+    def set_variant(self, kernel, prec, variant):
+        """kernel: 'fine' | 'dd'; prec: 'fp64' | 'fp32'; variant 0 / 1 (see include/th.h)."""
+        k = {"fine": 0, "dd": 1}[kernel]
+        _check(lib().th_set_kernel_variant(self._ctx, k, PREC[prec], int(variant)), "th_set_kernel_variant")
+
+    def get_variant(self, kernel, prec):
+        k = {"fine": 0, "dd": 1}[kernel]
+        v = ctypes.c_int(0)
+        _check(lib().th_get_kernel_variant(self._ctx, k, PREC[prec], ctypes.byref(v)), "th_get_kernel_variant")
+        return v.value
+
+    def device_status(self):
+        """Raises ThError(TH_ERR_TIMEOUT) if a bounded device wait gave up since the last check."""
+        _check(lib().th_device_status(self._ctx, self._stream()), "th_device_status")
 
     def launch_count(self) -> int:
         v = ctypes.c_longlong(0)

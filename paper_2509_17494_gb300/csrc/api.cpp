@@ -55,6 +55,10 @@ struct th_ctx {
   int rmax = 0;
   int wchunks[4] = {0, 0, 0, 0};
   int ddG = 4;  // column groups per subdomain in K3
+  int tc64 = 0, tc32 = 0;  // fine-apply tile variant per precision (0 large, 1 small), autotuned
+  int dds64 = 0, dds32 = 0;  // DD kernel per precision: 0 k_dd_apply, 1 k_dd_stream (autotuned)
+  int sms = 152;
+  int* derr = nullptr;      // device flag: a bounded device wait gave up
   // device arrays
   double *kc64 = nullptr, *ec64 = nullptr;
   float *kc32 = nullptr, *ec32 = nullptr;
@@ -72,8 +76,9 @@ struct th_ctx {
   // partitioned coarse factors (both precisions when prepared)
   int P = 1, mcp = 0, Lmax = 0;
   int *ca = nullptr, *cb = nullptr, *sep = nullptr, *chunk_of = nullptr;
-  double2 *Gp64 = nullptr, *LR64 = nullptr, *Gh64 = nullptr, *Fh64 = nullptr, *Hh64 = nullptr;
-  float2 *Gp32 = nullptr, *LR32 = nullptr, *Gh32 = nullptr, *Fh32 = nullptr, *Hh32 = nullptr;
+  int nred = 0;  // (P - 1) mc separator unknowns
+  double2 *Gp64 = nullptr, *LR64 = nullptr, *Si64 = nullptr, *rh64 = nullptr;
+  float2 *Gp32 = nullptr, *LR32 = nullptr, *Si32 = nullptr, *rh32 = nullptr;
   // cycle work vectors
   double2 *r64 = nullptr, *s64 = nullptr, *v64 = nullptr, *V64 = nullptr, *rc64 = nullptr, *uc64 = nullptr,
           *zc64 = nullptr, *t64 = nullptr;
@@ -132,6 +137,7 @@ void carve_all(th_ctx& x, Carve& c) {
   const th_params& prm = x.prm;
   const size_t n2 = (size_t)g.n * g.n;
   const int nr = prm.nrhs_max;
+  x.derr = c.take<int>(64);
   x.kc64 = c.take<double>(n2);
   x.ec64 = c.take<double>(n2);
   x.box = c.take<int>((size_t)g.nsub * 8);
@@ -160,12 +166,12 @@ void carve_all(th_ctx& x, Carve& c) {
   x.cb = c.take<int>(x.P);
   x.sep = c.take<int>(K);
   x.chunk_of = c.take<int>(g.mc);
+  const size_t nred = std::max(x.nred, 1);
   if (fp64) {
     x.Gp64 = c.take<double2>(blk * g.mc);
     x.LR64 = c.take<double2>(2 * blk * g.mc);
-    x.Gh64 = c.take<double2>(blk * K);
-    x.Fh64 = c.take<double2>(blk * K);
-    x.Hh64 = c.take<double2>(blk * K);
+    x.Si64 = c.take<double2>(nred * nred);
+    x.rh64 = c.take<double2>(nred * nr);
   }
   // FP64 work vectors are always present (residuals, FGMRES, FP64 applies)
   x.r64 = c.take<double2>((size_t)nr * g.N);
@@ -188,9 +194,8 @@ void carve_all(th_ctx& x, Carve& c) {
     x.cu32 = c.take<float2>(mm);
     x.Gp32 = c.take<float2>(blk * g.mc);
     x.LR32 = c.take<float2>(2 * blk * g.mc);
-    x.Gh32 = c.take<float2>(blk * K);
-    x.Fh32 = c.take<float2>(blk * K);
-    x.Hh32 = c.take<float2>(blk * K);
+    x.Si32 = c.take<float2>(nred * nred);
+    x.rh32 = c.take<float2>(nred * nr);
     x.f32 = c.take<float2>((size_t)nr * g.N);
     x.u32 = c.take<float2>((size_t)nr * g.N);
     x.r32 = c.take<float2>((size_t)nr * g.N);
@@ -239,6 +244,7 @@ th_status prepare(const th_mesh* mesh, const th_params* prm, th_ctx& x) {
   {
     const int rows = x.g.mc - (x.P - 1);
     x.Lmax = rows / x.P + ((rows % x.P) ? 1 : 0);
+    x.nred = (x.P - 1) * x.g.mc;
   }
   return TH_OK;
 }
@@ -265,6 +271,7 @@ th::FineArgs<T> fine_args(const th_ctx& x, int op) {
   a.h = (T)g.h;
   a.h2 = (T)(g.h * g.h);
   a.alpha = (op == TH_OP_AS) ? (T)x.prm.alpha_s : (T)0;
+  a.tc = std::is_same<T, double>::value ? x.tc64 : x.tc32;
   const int np = g.p + 1;
   for (int i = 0; i < np * np; ++i) {
     a.M[i] = (T)x.ref.M[i];
@@ -304,9 +311,8 @@ template <> struct PrecBufs<double> {
   static double2* uc(th_ctx& x) { return x.uc64; }
   static const double2* Gp(th_ctx& x) { return x.Gp64; }
   static const double2* LR(th_ctx& x) { return x.LR64; }
-  static const double2* Gh(th_ctx& x) { return x.Gh64; }
-  static const double2* Fh(th_ctx& x) { return x.Fh64; }
-  static const double2* Hh(th_ctx& x) { return x.Hh64; }
+  static const double2* Si(th_ctx& x) { return x.Si64; }
+  static double2* rh(th_ctx& x) { return x.rh64; }
   static const double* pw(th_ctx& x) { return x.pw64; }
   static const double* rw(th_ctx& x) { return x.rw64; }
   static const double2* cl(th_ctx& x) { return x.cl64; }
@@ -324,9 +330,8 @@ template <> struct PrecBufs<float> {
   static float2* uc(th_ctx& x) { return x.uc32; }
   static const float2* Gp(th_ctx& x) { return x.Gp32; }
   static const float2* LR(th_ctx& x) { return x.LR32; }
-  static const float2* Gh(th_ctx& x) { return x.Gh32; }
-  static const float2* Fh(th_ctx& x) { return x.Fh32; }
-  static const float2* Hh(th_ctx& x) { return x.Hh32; }
+  static const float2* Si(th_ctx& x) { return x.Si32; }
+  static float2* rh(th_ctx& x) { return x.rh32; }
   static const float* pw(th_ctx& x) { return x.pw32; }
   static const float* rw(th_ctx& x) { return x.rw32; }
   static const float2* cl(th_ctx& x) { return x.cl32; }
@@ -357,6 +362,8 @@ th_status dd_apply(th_ctx& x, int wkind, const typename th::Cx<T>::t* r, int nrh
   a.nrhs = nrhs;
   x.launches += 1;
   Prof prof(x, TH_K_DD, s);
+  const int stream = std::is_same<T, double>::value ? x.dds64 : x.dds32;
+  if (stream) return cuda_status(th::launch_dd_stream<T>(a, wkind, x.derr, x.sms, s));
   return cuda_status(th::launch_dd_apply<T>(a, wkind, 0, s));
 }
 
@@ -457,9 +464,9 @@ th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th:
   a.x = uc;
   a.G = B::Gp(x);
   a.LR = B::LR(x);
-  a.Gh = B::Gh(x);
-  a.Fh = B::Fh(x);
-  a.Hh = B::Hh(x);
+  a.Sinv = B::Si(x);
+  a.rhat = B::rh(x);
+  a.nred = x.nred;
   a.cl = B::cl(x);
   a.cd = B::cd(x);
   a.cu = B::cu(x);
@@ -474,7 +481,7 @@ th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th:
   a.rpc = x.rpc;
   a.Lmax = x.Lmax;
   if (!a.G || !a.LR) return TH_ERR_UNSUPPORTED;
-  x.launches += (x.P > 1) ? 3 : 1;
+  x.launches += (x.P > 1) ? 4 : 1;
   Prof prof(x, TH_K_COARSE_SOLVE, s);
   return cuda_status(th::launch_coarse_part<T>(a, nrhs, x.cluster, s));
 }
@@ -551,6 +558,87 @@ th_status norms(th_ctx& x, const double2* w, int nrhs, std::vector<double>& out,
   TH_CU(cudaMemcpyAsync(out.data(), x.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
   TH_CU(cudaStreamSynchronize(s));
   for (auto& v : out) v = std::sqrt(v);
+  return TH_OK;
+}
+
+}  // namespace
+
+namespace {
+// Set-up autotuner: times the fine-apply tile variants on this problem with
+// CUDA events and keeps the faster one per precision.
+template <typename T>
+th_status tune_fine(th_ctx& x, cudaStream_t s, int& choice) {
+  using C = typename th::Cx<T>::t;
+  C* u = nullptr;
+  C* y = nullptr;
+  if constexpr (std::is_same<T, double>::value) {
+    u = x.r64;
+    y = x.t64;
+  } else {
+    u = x.f32;
+    y = x.r32;
+  }
+  if (!u || !y) return TH_OK;
+  TH_CU(cudaMemsetAsync(u, 0, sizeof(C) * x.g.N, s));
+  cudaEvent_t e0, e1;
+  TH_CU(cudaEventCreate(&e0));
+  TH_CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int arg = 0;
+  for (int v = 0; v < 2; ++v) {
+    choice = v;
+    th::FineArgs<T> a = fine_args<T>(x, TH_OP_A);
+    a.u = u;
+    a.y = y;
+    a.f = nullptr;
+    a.residual = 0;
+    for (int w = 0; w < 2; ++w) TH_CU(th::launch_fine_apply<T>(a, 1, s));
+    TH_CU(cudaEventRecord(e0, s));
+    for (int r = 0; r < 5; ++r) TH_CU(th::launch_fine_apply<T>(a, 1, s));
+    TH_CU(cudaEventRecord(e1, s));
+    TH_CU(cudaEventSynchronize(e1));
+    float ms = 0;
+    TH_CU(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) { best = ms; arg = v; }
+  }
+  choice = arg;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return TH_OK;
+}
+
+template <typename T>
+th_status tune_dd(th_ctx& x, int wkind, cudaStream_t s, int& choice) {
+  using C = typename th::Cx<T>::t;
+  C* r = nullptr;
+  if constexpr (std::is_same<T, double>::value) r = x.r64; else r = x.r32;
+  if (!r || !x.W[wkind]) return TH_OK;
+  TH_CU(cudaMemsetAsync(r, 0, sizeof(C) * x.g.N, s));
+  cudaEvent_t e0, e1;
+  TH_CU(cudaEventCreate(&e0));
+  TH_CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int arg = 0;
+  for (int v = 0; v < 2; ++v) {
+    choice = v;
+    bool ok = true;
+    for (int w = 0; w < 2 && ok; ++w) ok = (dd_apply<T>(x, wkind, r, 1, s) == TH_OK);
+    if (!ok) {
+      cudaGetLastError();
+      continue;
+    }
+    TH_CU(cudaEventRecord(e0, s));
+    for (int k = 0; k < 4; ++k)
+      if (dd_apply<T>(x, wkind, r, 1, s) != TH_OK) ok = false;
+    TH_CU(cudaEventRecord(e1, s));
+    TH_CU(cudaEventSynchronize(e1));
+    float ms = 0;
+    TH_CU(cudaEventElapsedTime(&ms, e0, e1));
+    if (ok && ms < best) { best = ms; arg = v; }
+  }
+  choice = arg;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   return TH_OK;
 }
 
@@ -716,11 +804,7 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
   };
   if ((st = upload_c(x->Gp64, x->Gp32, cpart.G)) != TH_OK) return st;
   if ((st = upload_c(x->LR64, x->LR32, cpart.LR)) != TH_OK) return st;
-  if (x->P > 1) {
-    if ((st = upload_c(x->Gh64, x->Gh32, cpart.Gh)) != TH_OK) return st;
-    if ((st = upload_c(x->Fh64, x->Fh32, cpart.Fh)) != TH_OK) return st;
-    if ((st = upload_c(x->Hh64, x->Hh32, cpart.Hh)) != TH_OK) return st;
-  }
+  if (x->P > 1 && (st = upload_c(x->Si64, x->Si32, cpart.Sinv)) != TH_OK) return st;
   std::vector<float2> cell32, rho32, cl32, cd32, cu32;
   if (x->mixed) {
     cell32 = to2f(cb.cell);
@@ -801,8 +885,62 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     TH_CU(cudaStreamSynchronize(s));
   }
   TH_CU(cudaStreamSynchronize(s));
+  {
+    int dev = 0;
+    TH_CU(cudaGetDevice(&dev));
+    TH_CU(cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, dev));
+    TH_CU(cudaMemsetAsync(x->derr, 0, 64 * sizeof(int), s));
+  }
+  if ((st = tune_fine<double>(*x, s, x->tc64)) != TH_OK) return st;
+  if (x->mixed && (st = tune_fine<float>(*x, s, x->tc32)) != TH_OK) return st;
+  if (x->W[TH_PREC_FP64] && (st = tune_dd<double>(*x, TH_PREC_FP64, s, x->dds64)) != TH_OK) return st;
+  if (x->mixed) {
+    const int wk = (x->active != TH_PREC_FP64) ? x->active : (x->W[TH_PREC_BF16] ? TH_PREC_BF16 : TH_PREC_FP32);
+    if (x->W[wk] && (st = tune_dd<float>(*x, wk, s, x->dds32)) != TH_OK) return st;
+  }
+  TH_CU(cudaStreamSynchronize(s));
+  {
+    int flag = 0;
+    TH_CU(cudaMemcpy(&flag, x->derr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return TH_ERR_TIMEOUT;
+  }
+  TH_CU(cudaStreamSynchronize(s));
   *out = x.release();
   return TH_OK;
+}
+
+th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
+  if (!x || variant < 0 || variant > 1 || (prec != TH_PREC_FP64 && prec != TH_PREC_FP32)) return TH_ERR_ARG;
+  const bool d = (prec == TH_PREC_FP64);
+  if (kernel == TH_K_FINE) {
+    (d ? x->tc64 : x->tc32) = variant;
+  } else if (kernel == TH_K_DD) {
+    (d ? x->dds64 : x->dds32) = variant;
+  } else {
+    return TH_ERR_ARG;
+  }
+  return TH_OK;
+}
+
+th_status th_get_kernel_variant(const th_ctx* x, int kernel, int prec, int* variant) {
+  if (!x || !variant || (prec != TH_PREC_FP64 && prec != TH_PREC_FP32)) return TH_ERR_ARG;
+  const bool d = (prec == TH_PREC_FP64);
+  if (kernel == TH_K_FINE) *variant = d ? x->tc64 : x->tc32;
+  else if (kernel == TH_K_DD) *variant = d ? x->dds64 : x->dds32;
+  else return TH_ERR_ARG;
+  return TH_OK;
+}
+
+th_status th_device_status(th_ctx* x, void* stream) {
+  if (!x) return TH_ERR_ARG;
+  cudaStream_t s = S(stream);
+  int flag = 0;
+  TH_CU(cudaMemcpyAsync(&flag, x->derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TH_CU(cudaStreamSynchronize(s));
+  if (!flag) return TH_OK;
+  TH_CU(cudaMemsetAsync(x->derr, 0, sizeof(int), s));
+  TH_CU(cudaStreamSynchronize(s));
+  return TH_ERR_TIMEOUT;
 }
 
 th_status th_set_precision(th_ctx* x, int prec) {

@@ -8,9 +8,10 @@
 //      LU sweep of its chunk alone, y = A_cc^{-1} b_c, writing y into the
 //      output.  The chunks run concurrently, so the dependent chain is the
 //      chunk length (about sqrt(m_c)) instead of m_c.
-//   2. k_reduced_sweep: one cluster per rhs solves the block-tridiagonal
-//      system of the separator rows (dense blocks, P - 1 rows), writing the
-//      separator values into the output.
+//   2. k_reduced_rhs + k_reduced_gemv: the separator rows satisfy a small
+//      dense system (P - 1 block rows); its right-hand side is formed from y
+//      and its FP64-set-up explicit inverse is applied as one row-parallel
+//      GEMV, writing the separator values into the output.
 //   3. k_spike_correct: every chunk row gets x_j = y_j - L_j x_left - R_j x_right
 //      (dense spike blocks, all rows in parallel).
 // Inside a cluster, CTA c owns rows [c rpc, (c+1) rpc) of every block vector.
@@ -191,120 +192,53 @@ __global__ void __launch_bounds__(512, 1) k_chunk_sweep(const CoarsePartArgs<T> 
   }
 }
 
-// ------------------------------------------------------------- reduced sweep
-// Forward values zhat_k = Ghat_k rhat_k - F_k zhat_{k-1}: the products
-// g_k = Ghat_k rhat_k do not depend on the sweep and are formed first for all
-// k; the dependent steps then need one matvec each, with its rows copied in
-// by cp.async two steps ahead, and touch no global memory until the loop ends.
-template <typename T, bool PREFETCH>
-__global__ void __launch_bounds__(512, 1) k_reduced_sweep(const CoarsePartArgs<T> a) {
+// ------------------------------------------------------------- reduced system
+// rhat_k = b_s - C_{s-1}^T y_{s-1} - C_s y_{s+1} for every separator row s = sep[k]
+template <typename T>
+__global__ void __launch_bounds__(256) k_reduced_rhs(const CoarsePartArgs<T> a) {
   using C = typename Cx<T>::t;
-  cg::cluster_group cl = cg::this_cluster();
-  const int crank = (int)cl.block_rank(), csz = (int)cl.num_blocks();
-  const int rhs = blockIdx.x / csz;
-  const int mc = a.mc, mcp = a.mcp, rpc = a.rpc, K = a.P - 1;
-  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
-  const int row0 = crank * rpc, nrow = max(0, min(rpc, mc - row0));
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C* gbuf = reinterpret_cast<C*>(smraw);                    // [2][rpc * mcp] (PREFETCH)
-  C* full = gbuf + (PREFETCH ? (size_t)2 * rpc * mcp : 0);  // [2][mc]
-  C* rh = full + 2 * mc;                                    // [K][mc]
-  C* gs = rh + (size_t)K * mc;                              // [K][rpc]: g, zhat, then xhat
-  const C* b = a.b + (size_t)rhs * a.Nc;
-  C* x = a.x + (size_t)rhs * a.Nc;
-  const int nsteps = 2 * K - 1;
-  // matrix used by step q: forward k = q >= 1 -> F_k; backward k = 2K-2-q -> H_k; none for q = 0
-  auto mat_of = [&](int q) -> const C* {
-    if (q == 0) return nullptr;
-    if (q < K) return a.Fh + (size_t)q * mc * mcp;
-    return a.Hh + (size_t)(2 * K - 2 - q) * mc * mcp;
-  };
-  auto prefetch = [&](int q, int buf) {
-    if (PREFETCH) {
-      const C* m = (q < nsteps) ? mat_of(q) : nullptr;
-      if (m && nrow > 0) {
-        const char* src = reinterpret_cast<const char*>(m + (size_t)row0 * mcp);
-        char* dst = reinterpret_cast<char*>(gbuf + (size_t)buf * rpc * mcp);
-        const int units = (int)((size_t)nrow * mcp * sizeof(C) / 16);
-        for (int u = tid; u < units; u += nth) cp_async16(dst + (size_t)u * 16, src + (size_t)u * 16);
-      }
-      cp_async_commit();
-    }
-  };
-  prefetch(0, 0);
-  prefetch(1, 1);
-  // prologue 1: rhat_k = b_s - C_{s-1}^T y_{s-1} - C_s y_{s+1} for every separator (all of mc)
-  for (int i = tid; i < K * mc; i += nth) {
-    const int k = i / mc, e = i - k * mc;
-    const int s = a.sep[k];
-    const C* ym = x + (size_t)(s - 1) * mc;
-    const C* yp = x + (size_t)(s + 1) * mc;
-    const size_t om = (size_t)(s - 1) * mc, os = (size_t)s * mc;
-    C t = b[os + e];
-    C v;
-    v.x = 0;
-    v.y = 0;
-    cmac(v, a.cd[om + e], ym[e]);
-    if (e > 0) cmac(v, a.cu[om + e - 1], ym[e - 1]);
-    if (e + 1 < mc) cmac(v, a.cl[om + e + 1], ym[e + 1]);
-    cmac(v, a.cd[os + e], yp[e]);
-    if (e > 0) cmac(v, a.cl[os + e], yp[e - 1]);
-    if (e + 1 < mc) cmac(v, a.cu[os + e], yp[e + 1]);
-    t.x -= v.x;
-    t.y -= v.y;
-    rh[i] = t;
-  }
-  __syncthreads();
-  // prologue 2: g_k = Ghat_k rhat_k on this CTA's rows
-  for (int w = warp; w < K * nrow; w += nwarps) {
-    const int k = w / nrow, rr = w - k * nrow;
-    const C* g = a.Gh + ((size_t)k * mc + row0 + rr) * mcp;
-    const C* r = rh + (size_t)k * mc;
-    C acc;
-    acc.x = 0;
-    acc.y = 0;
-    for (int c = lane; c < mc; c += 32) cmac(acc, g[c], r[c]);
-    acc = warp_sum<T>(acc);
-    if (lane == 0) gs[(size_t)k * rpc + rr] = acc;
-  }
-  for (int q = 0; q < nsteps; ++q) {
-    const bool fwd = q < K;
-    const int k = fwd ? q : 2 * K - 2 - q;
-    const C* prev = full + ((q - 1) & 1) * mc;
-    const C* M = mat_of(q);
-    if (PREFETCH) cp_async_wait<1>();
-    __syncthreads();
-    const C* Mr = PREFETCH ? gbuf + (size_t)(q & 1) * rpc * mcp : (M ? M + (size_t)row0 * mcp : nullptr);
-    C* dst = full + (q & 1) * mc;
-    for (int rr = warp; rr < nrow; rr += nwarps) {
-      C acc;
-      acc.x = 0;
-      acc.y = 0;
-      if (M) {
-        const C* m = Mr + (size_t)rr * mcp;
-        for (int c = lane; c < mc; c += 32) cmac(acc, m[c], prev[c]);
-        acc = warp_sum<T>(acc);
-      }
-      const C g = gs[(size_t)k * rpc + rr];
-      C val;
-      val.x = g.x - acc.x;
-      val.y = g.y - acc.y;
-      __syncwarp();
-      if (lane == 0) gs[(size_t)k * rpc + rr] = val;  // zhat_k forward, xhat_k backward
-      if (lane < csz) {
-        C* remote = cl.map_shared_rank(dst, lane);
-        remote[row0 + rr] = val;
-      }
-    }
-    cluster_arrive_release();
-    cluster_wait_acquire();
-    prefetch(q + 2, q & 1);
-  }
-  if (PREFETCH) cp_async_wait<0>();
-  __syncthreads();
-  for (int i = tid; i < K * nrow; i += nth) {
-    const int k = i / nrow, rr = i - k * nrow;
-    x[(size_t)a.sep[k] * mc + row0 + rr] = gs[(size_t)k * rpc + rr];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.nred) return;
+  const int mc = a.mc;
+  const int k = i / mc, e = i - k * mc;
+  const int s = a.sep[k];
+  const C* b = a.b + (size_t)blockIdx.y * a.Nc;
+  const C* x = a.x + (size_t)blockIdx.y * a.Nc;
+  const C* ym = x + (size_t)(s - 1) * mc;
+  const C* yp = x + (size_t)(s + 1) * mc;
+  const size_t om = (size_t)(s - 1) * mc, os = (size_t)s * mc;
+  C t = b[os + e];
+  C v;
+  v.x = 0;
+  v.y = 0;
+  cmac(v, a.cd[om + e], ym[e]);
+  if (e > 0) cmac(v, a.cu[om + e - 1], ym[e - 1]);
+  if (e + 1 < mc) cmac(v, a.cl[om + e + 1], ym[e + 1]);
+  cmac(v, a.cd[os + e], yp[e]);
+  if (e > 0) cmac(v, a.cl[os + e], yp[e - 1]);
+  if (e + 1 < mc) cmac(v, a.cu[os + e], yp[e + 1]);
+  t.x -= v.x;
+  t.y -= v.y;
+  a.rhat[(size_t)blockIdx.y * a.nred + i] = t;
+}
+
+// xhat = Sinv rhat, one warp per row, written into the separator rows of x
+template <typename T>
+__global__ void __launch_bounds__(256) k_reduced_gemv(const CoarsePartArgs<T> a) {
+  using C = typename Cx<T>::t;
+  const int lane = threadIdx.x & 31;
+  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= a.nred) return;
+  const C* srow = a.Sinv + (size_t)row * a.nred;
+  const C* r = a.rhat + (size_t)blockIdx.y * a.nred;
+  C acc;
+  acc.x = 0;
+  acc.y = 0;
+  for (int c = lane; c < a.nred; c += 32) cmac(acc, srow[c], r[c]);
+  acc = warp_sum<T>(acc);
+  if (lane == 0) {
+    const int k = (int)(row / a.mc), e = (int)(row - (long long)k * a.mc);
+    a.x[(size_t)blockIdx.y * a.Nc + (size_t)a.sep[k] * a.mc + e] = acc;
   }
 }
 
@@ -383,14 +317,16 @@ cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster
   cudaError_t e = pf ? launch_cluster(k_chunk_sweep<T, true>, a, cluster * a.P * nrhs, cluster, sm1, s)
                      : launch_cluster(k_chunk_sweep<T, false>, a, cluster * a.P * nrhs, cluster, sm1, s);
   if (e != cudaSuccess || a.P < 2) return e;
-  using C = typename Cx<T>::t;
-  const size_t base2 = sizeof(C) * ((size_t)2 * a.mc + (size_t)(a.P - 1) * (a.mc + a.rpc));
-  const size_t pf2 = sizeof(C) * (size_t)2 * a.rpc * a.mcp;
-  if (base2 + pf2 <= 220 * 1024)
-    e = launch_cluster(k_reduced_sweep<T, true>, a, cluster * nrhs, cluster, base2 + pf2, s);
-  else
-    e = launch_cluster(k_reduced_sweep<T, false>, a, cluster * nrhs, cluster, base2, s);
-  if (e != cudaSuccess) return e;
+  {
+    dim3 g1((unsigned)((a.nred + 255) / 256), nrhs);
+    k_reduced_rhs<T><<<g1, 256, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 g2((unsigned)(((long long)a.nred * 32 + 255) / 256), nrhs);
+    k_reduced_gemv<T><<<g2, 256, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const long long warps = (long long)a.mc * a.mc;
   dim3 grid((unsigned)((warps * 32 + 255) / 256), nrhs);
   k_spike_correct<T><<<grid, 256, 0, s>>>(a);

@@ -19,6 +19,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace th {
@@ -48,6 +50,37 @@ __device__ __forceinline__ void unpack_chunk(const void* base, size_t idx, T* wr
     }
   } else {
     const uint4 v = __ldcs(reinterpret_cast<const uint4*>(base) + idx);
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __half2 h2 = *reinterpret_cast<const __half2*>(&w[j]);
+      float2 f = __half22float2(h2);
+      wr[j] = f.x;
+      wi[j] = f.y;
+    }
+  }
+}
+
+// same unpacking from shared memory (plain loads)
+template <typename T, int KIND>
+__device__ __forceinline__ void unpack_chunk_smem(const void* base, size_t idx, T* wr, T* wi) {
+  if constexpr (KIND == W_FP64) {
+    const double2 v = reinterpret_cast<const double2*>(base)[idx];
+    wr[0] = (T)v.x;
+    wi[0] = (T)v.y;
+  } else if constexpr (KIND == W_FP32) {
+    const float4 v = reinterpret_cast<const float4*>(base)[idx];
+    wr[0] = v.x; wi[0] = v.y; wr[1] = v.z; wi[1] = v.w;
+  } else if constexpr (KIND == W_BF16) {
+    const uint4 v = reinterpret_cast<const uint4*>(base)[idx];
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      wr[j] = __uint_as_float(w[j] << 16);
+      wi[j] = __uint_as_float(w[j] & 0xffff0000u);
+    }
+  } else {
+    const uint4 v = reinterpret_cast<const uint4*>(base)[idx];
     const unsigned w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -216,5 +249,248 @@ cudaError_t launch_dd_combine(const CombineArgs<T>& a, int nrhs, cudaStream_t s)
 
 template cudaError_t launch_dd_combine<double>(const CombineArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_dd_combine<float>(const CombineArgs<float>&, int, cudaStream_t);
+
+
+// ------------------------------------------------------------------- K3 (TMA streamed)
+// Persistent variant of K3: one CTA per SM walks its subdomains; the inverse
+// rows of each subdomain (contiguous, chunk-major) are pulled from HBM in
+// stages of up to 48 KB by one-dimensional bulk copies (cp.async.bulk, the
+// TMA engine) into a ring of D shared-memory slots, each completing on its
+// own mbarrier, D - 1 stages ahead of the consumers.  The next subdomain's
+// gather of r is prefetched with cp.async while the current one computes.
+// Every wait on an mbarrier is bounded: on timeout the CTA records a flag,
+// drains its copies in flight (again bounded) and returns.
+namespace {
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx_arrive(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded wait: false after the iteration limit
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (int it = 0; it < (1 << 20); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+template <typename C>
+__device__ __forceinline__ void cp_async_c(C* smem, const C* gmem) {
+  if constexpr (sizeof(C) == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+}  // namespace
+
+template <typename T, int KIND, int NRHS>
+__global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps, int depth, int* err) {
+  using C = typename Cx<T>::t;
+  constexpr int CPC = WTraits<KIND>::CPC;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int NR = a.NR, NCH = a.NCH, G = a.G;
+  const size_t slot_bytes = (size_t)cps * NR * 16;
+  unsigned char* slots = smraw;                                             // [depth][slot_bytes]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smraw + depth * slot_bytes);  // [depth]
+  const int XL = NCH * CPC;
+  C* xs = reinterpret_cast<C*>(bars + 8);                                   // [2][NRHS][XL]
+  C* red = xs + 2 * NRHS * XL;                                              // [G][NR][NRHS]
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int rr = tid % NR, g = tid / NR;
+  const int r0 = blockIdx.y * NRHS;
+  const int nr = min(NRHS, a.nrhs - r0);
+  const int NS = (NCH + cps - 1) / cps;
+  const int nmine = (a.nsub - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int total = nmine * NS;
+
+  int issued_hi = 0;         // thread 0: one past the last item issued
+  auto issue = [&](int t) {  // thread 0 only
+    if (t >= total) return;
+    issued_hi = t + 1;
+    const int sub = blockIdx.x + (t / NS) * gridDim.x;
+    const int s = t % NS;
+    const int ch0 = s * cps;
+    const int nch = min(cps, NCH - ch0);
+    const unsigned bytes = (unsigned)((size_t)nch * NR * 16);
+    const char* src = reinterpret_cast<const char*>(a.W) + ((size_t)sub * NCH + ch0) * NR * 16;
+    uint64_t* bar = bars + (t % depth);
+    mbar_expect_tx_arrive(bar, bytes);
+    bulk_g2s(slots + (size_t)(t % depth) * slot_bytes, src, bytes, bar);
+  };
+  auto gather = [&](int i, int buf) {
+    if (i < nmine) {
+      const int sub = blockIdx.x + i * gridDim.x;
+      const int* bb = a.box + (size_t)sub * 8;
+      const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3];
+      C* dst = xs + (size_t)buf * NRHS * XL;
+      for (int idx = tid; idx < NRHS * XL; idx += nth) {
+        const int k = idx / XL, c = idx - k * XL;
+        const int cy = c / a.Lw, cx = c - cy * a.Lw;
+        if (k < nr && c < a.NC && cx < wx && cy < wy) {
+          cp_async_c(dst + idx, a.r + (size_t)(r0 + k) * a.N + (size_t)(oy + cy) * a.m + (ox + cx));
+        } else {
+          C z;
+          z.x = 0;
+          z.y = 0;
+          dst[idx] = z;
+        }
+      }
+    }
+    cp_commit();
+  };
+
+  if (tid == 0) {
+    for (int d = 0; d < depth; ++d) mbar_init(bars + d, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int t = 0; t < depth; ++t) issue(t);
+  gather(0, 0);
+  // A wait that gives up marks `failed` (shared); every thread keeps running the
+  // same loop (on possibly stale data) so the barriers stay uniform, no new
+  // copies are issued, and the copies in flight are drained at the end.
+  __shared__ int failed;
+  if (tid == 0) failed = 0;
+  int t = 0;
+  for (int i = 0; i < nmine; ++i) {
+    gather(i + 1, (i + 1) & 1);
+    cp_wait1();
+    __syncthreads();
+    const C* xv = xs + (size_t)(i & 1) * NRHS * XL;
+    T acr[NRHS], aci[NRHS];
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) { acr[k] = 0; aci[k] = 0; }
+    for (int s = 0; s < NS; ++s, ++t) {
+      if (!failed && !mbar_wait_bounded(bars + (t % depth), (unsigned)((t / depth) & 1))) failed = 1;
+      const int ch0 = s * cps, nch = min(cps, NCH - ch0);
+      const unsigned char* slot = slots + (size_t)(t % depth) * slot_bytes;
+      if (g < G) {
+        for (int ch = g; ch < nch; ch += G) {
+          T wr[CPC], wi[CPC];
+          unpack_chunk_smem<T, KIND>(slot, (size_t)ch * NR + rr, wr, wi);
+#pragma unroll
+          for (int j = 0; j < CPC; ++j) {
+            const int c = (ch0 + ch) * CPC + j;
+#pragma unroll
+            for (int k = 0; k < NRHS; ++k) {
+              const C x = xv[k * XL + c];
+              acr[k] += wr[j] * x.x - wi[j] * x.y;
+              aci[k] += wr[j] * x.y + wi[j] * x.x;
+            }
+          }
+        }
+      }
+      __syncthreads();  // every thread is done with this slot
+      if (tid == 0 && !failed) issue(t + depth);
+    }
+    const int sub = blockIdx.x + i * gridDim.x;
+    if (g < G) {
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) {
+        C v;
+        v.x = acr[k];
+        v.y = aci[k];
+        red[((size_t)g * NR + rr) * NRHS + k] = v;
+      }
+    }
+    __syncthreads();
+    if (tid < NR) {
+      const T sc = a.wscale ? (T)a.wscale[sub] : (T)1;
+      for (int k = 0; k < nr; ++k) {
+        T sr = 0, si = 0;
+        for (int gg = 0; gg < G; ++gg) {
+          const C v = red[((size_t)gg * NR + tid) * NRHS + k];
+          sr += v.x;
+          si += v.y;
+        }
+        C o;
+        o.x = sr * sc;
+        o.y = si * sc;
+        a.V[((size_t)(r0 + k) * a.nsub + sub) * NR + tid] = o;
+      }
+    }
+  }
+  cp_wait0();
+  __syncthreads();
+  if (tid == 0 && failed) {
+    // record, then wait (bounded) for the copies that can still be in flight:
+    // no item is issued before the one `depth` places earlier was consumed
+    atomicExch(err, 1);
+    for (int u = max(0, issued_hi - depth); u < issued_hi; ++u)
+      mbar_wait_bounded(bars + (u % depth), (unsigned)((u / depth) & 1));
+  }
+  __syncthreads();
+}
+
+template <typename T, int KIND, int NRHS>
+static cudaError_t launch_dd_stream_k(const DDArgs<T>& a, int* err, int sms, cudaStream_t s) {
+  using C = typename Cx<T>::t;
+  constexpr int CPC = WTraits<KIND>::CPC;
+  const int threads = ((a.NR * a.G + 31) / 32) * 32;
+  if (threads > 512) return cudaErrorInvalidConfiguration;
+  // two CTAs per SM, each with a ring of three stages of up to 32 KB
+  const int cps = std::max(1, (int)((32 * 1024) / ((size_t)a.NR * 16)));
+  const size_t slot_bytes = (size_t)cps * a.NR * 16;
+  const size_t fixed = 8 * sizeof(uint64_t) +
+                       sizeof(C) * ((size_t)2 * NRHS * a.NCH * CPC + (size_t)a.G * a.NR * NRHS);
+  const int depth = 3;
+  const size_t smem = depth * slot_bytes + fixed;
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  const int per_sm = (2 * (smem + 1024) <= 228 * 1024) ? 2 : 1;
+  cudaError_t e = cudaFuncSetAttribute(k_dd_stream<T, KIND, NRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int gx = std::min(a.nsub, per_sm * sms);
+  dim3 grid(gx, (a.nrhs + NRHS - 1) / NRHS);
+  k_dd_stream<T, KIND, NRHS><<<grid, threads, smem, s>>>(a, cps, depth, err);
+  return cudaGetLastError();
+}
+
+template <typename T, int KIND>
+static cudaError_t launch_dd_stream_kind(const DDArgs<T>& a, int* err, int sms, cudaStream_t s) {
+  if (a.nrhs >= 4) return launch_dd_stream_k<T, KIND, 4>(a, err, sms, s);
+  if (a.nrhs >= 2) return launch_dd_stream_k<T, KIND, 2>(a, err, sms, s);
+  return launch_dd_stream_k<T, KIND, 1>(a, err, sms, s);
+}
+
+template <>
+cudaError_t launch_dd_stream<double>(const DDArgs<double>& a, int kind, int* err, int sms, cudaStream_t s) {
+  if (kind != W_FP64) return cudaErrorInvalidValue;
+  return launch_dd_stream_kind<double, W_FP64>(a, err, sms, s);
+}
+template <>
+cudaError_t launch_dd_stream<float>(const DDArgs<float>& a, int kind, int* err, int sms, cudaStream_t s) {
+  switch (kind) {
+    case W_FP32: return launch_dd_stream_kind<float, W_FP32>(a, err, sms, s);
+    case W_BF16: return launch_dd_stream_kind<float, W_BF16>(a, err, sms, s);
+    case W_FP16: return launch_dd_stream_kind<float, W_FP16>(a, err, sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 }  // namespace th

@@ -25,7 +25,7 @@ __device__ __forceinline__ C cmul(C a, T br, T bi) {
 }
 
 template <int P, int TC, typename T>
-__global__ void __launch_bounds__(256) k_fine_apply(const FineArgs<T> a) {
+__global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineArgs<T> a) {
   using C = typename Cx<T>::t;
   constexpr int NP = P + 1, E = TC + 1, UT = E * P + 1, CELLS = E * E;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -197,17 +197,20 @@ static cudaError_t launch_fine_p(const FineArgs<T>& a, int nrhs, cudaStream_t s)
   }
   const int tiles = (a.n + TC - 1) / TC;
   dim3 grid(tiles, tiles, nrhs);
-  k_fine_apply<P, TC, T><<<grid, 256, smem, s>>>(a);
+  k_fine_apply<P, TC, T><<<grid, TC >= 8 ? 256 : 128, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fine_apply(const FineArgs<T>& a, int nrhs, cudaStream_t s) {
+  // two tile shapes per order: the larger recomputes fewer halo cells, the
+  // smaller spreads a small mesh over more SMs (chosen by the set-up autotuner)
+  const bool small = (a.tc != 0);
   switch (a.p) {
-    case 2: return launch_fine_p<2, 16, T>(a, nrhs, s);
-    case 4: return launch_fine_p<4, 8, T>(a, nrhs, s);
-    case 6: return launch_fine_p<6, 5, T>(a, nrhs, s);
-    case 8: return launch_fine_p<8, 4, T>(a, nrhs, s);
+    case 2: return small ? launch_fine_p<2, 8, T>(a, nrhs, s) : launch_fine_p<2, 16, T>(a, nrhs, s);
+    case 4: return small ? launch_fine_p<4, 4, T>(a, nrhs, s) : launch_fine_p<4, 8, T>(a, nrhs, s);
+    case 6: return small ? launch_fine_p<6, 3, T>(a, nrhs, s) : launch_fine_p<6, 5, T>(a, nrhs, s);
+    case 8: return small ? launch_fine_p<8, 2, T>(a, nrhs, s) : launch_fine_p<8, 4, T>(a, nrhs, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -23,6 +23,7 @@ struct FineArgs {
   int n, m, p;
   int robin;                   // bit s set = side s absorbing (x lo, x hi, y lo, y hi)
   int residual;                // 0: y = OP u;  1: y = f - OP u
+  int tc;                      // tile edge in cells (0: default for p)
   T h, h2, alpha;              // alpha = shift (0 for A)
   T M[81], K[81];              // 1-D reference mass / stiffness, (p+1)^2
 };
@@ -43,6 +44,9 @@ struct DDArgs {
 };
 template <typename T>
 cudaError_t launch_dd_apply(const DDArgs<T>& a, int kind, int grid_cap, cudaStream_t s);
+// TMA-streamed variant (persistent, one CTA per SM); *err is set to 1 if a bounded wait gave up
+template <typename T>
+cudaError_t launch_dd_stream(const DDArgs<T>& a, int kind, int* err, int sms, cudaStream_t s);
 
 // ------------------------------------------------------- K4 DD combine
 template <typename T>
@@ -108,9 +112,8 @@ struct CoarsePartArgs {
   typename Cx<T>::t* x;          // [rhs][Nc]
   const typename Cx<T>::t* G;    // chunk-row block inverses, mc blocks of mc x mcp
   const typename Cx<T>::t* LR;   // spikes [L_j | R_j], mc blocks of mc x 2 mcp
-  const typename Cx<T>::t* Gh;   // reduced factors, P - 1 blocks of mc x mcp each
-  const typename Cx<T>::t* Fh;
-  const typename Cx<T>::t* Hh;
+  const typename Cx<T>::t* Sinv; // explicit inverse of the reduced separator system, nred x nred
+  typename Cx<T>::t* rhat;       // scratch: reduced right-hand sides, [rhs][nred]
   const typename Cx<T>::t* cl;   // C_j diagonals
   const typename Cx<T>::t* cd;
   const typename Cx<T>::t* cu;
@@ -119,7 +122,7 @@ struct CoarsePartArgs {
   const int* sep;                // separator rows
   const int* chunk_of;           // per row: chunk index, or -1 for a separator
   long long Nc;
-  int mc, mcp, P, rpc, Lmax;
+  int mc, mcp, P, rpc, Lmax, nred;
 };
 template <typename T>
 cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster, cudaStream_t s);

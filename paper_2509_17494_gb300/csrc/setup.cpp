@@ -871,6 +871,42 @@ th_status coarse_partition(const Geometry& g, const CoarseBlocks& cb, int P, Coa
     }
     Ghp = Gk;
   }
+  // explicit inverse of the reduced system, one column per unit right-hand side
+  // through its block factorisation (forward zhat_k = Ghat_k rhat_k - F_k zhat_{k-1},
+  // backward xhat_k = zhat_k - H_k xhat_{k+1}); columns in parallel
+  if (K > 0) {
+    const size_t nred = (size_t)K * mc;
+    cp.Sinv.assign(nred * nred, cplx(0.0));
+    parallel_for((int)nred, [&](int col) {
+      const int k0 = col / mc, e0 = col % mc;
+      std::vector<cplx> z(nred, cplx(0.0)), xh(nred, cplx(0.0));
+      for (int k = k0; k < K; ++k) {
+        cplx* zk = &z[(size_t)k * mc];
+        if (k == k0) {
+          for (int r = 0; r < mc; ++r) zk[r] = cp.Gh[((size_t)k * mc + r) * ld + e0];
+        } else {
+          const cplx* zp = &z[(size_t)(k - 1) * mc];
+          for (int r = 0; r < mc; ++r) {
+            const cplx* f = &cp.Fh[((size_t)k * mc + r) * ld];
+            cplx acc = 0.0;
+            for (int c2 = 0; c2 < mc; ++c2) acc += f[c2] * zp[c2];
+            zk[r] = -acc;
+          }
+        }
+      }
+      for (int r = 0; r < mc; ++r) xh[(size_t)(K - 1) * mc + r] = z[(size_t)(K - 1) * mc + r];
+      for (int k = K - 2; k >= 0; --k) {
+        const cplx* xn = &xh[(size_t)(k + 1) * mc];
+        for (int r = 0; r < mc; ++r) {
+          const cplx* hrow = &cp.Hh[((size_t)k * mc + r) * ld];
+          cplx acc = 0.0;
+          for (int c2 = 0; c2 < mc; ++c2) acc += hrow[c2] * xn[c2];
+          xh[(size_t)k * mc + r] = z[(size_t)k * mc + r] - acc;
+        }
+      }
+      for (size_t r = 0; r < nred; ++r) cp.Sinv[r * nred + col] = xh[r];
+    });
+  }
   return TH_OK;
 }
 

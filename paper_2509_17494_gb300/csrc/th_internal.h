@@ -86,6 +86,7 @@ struct CoarsePart {
   std::vector<cplx> G;            // mc blocks (chunk rows; separator slots zero), mc x mcp each
   std::vector<cplx> LR;           // mc blocks of mc x (2 mcp): [L_j | R_j] spikes
   std::vector<cplx> Gh, Fh, Hh;   // P - 1 blocks each, mc x mcp: reduced factors
+  std::vector<cplx> Sinv;         // explicit inverse of the reduced system, (P-1) mc square
 };
 th_status coarse_partition(const Geometry& g, const CoarseBlocks& cb, int P, CoarsePart& cp);
 int coarse_chunks(int mc);

@@ -89,15 +89,27 @@ def test_coarse_apply_and_transfers_fp64(th, c):
 
 
 @pytest.mark.parametrize("c", CASES)
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fine_apply_variants_fp64(th, c, variant):
+    S, P = build(th, c)
+    S.set_variant("fine", "fp64", variant)
+    x = synth.random_complex((3, P.N), 31)
+    assert relerr(host(S.apply(dev(x), "As")), (P.As @ x.T).T) < 1e-12
+
+
+@pytest.mark.parametrize("c", CASES)
 @pytest.mark.parametrize("n_dd", [1, 2])
-def test_smoother_fp64(th, c, n_dd):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_smoother_fp64(th, c, n_dd, variant):
     S, P = build(th, c, n_dd=n_dd)
+    S.set_variant("dd", "fp64", variant)
     sm = dd.DDSmoother(P, c["l_dd"])
     f = synth.random_complex((3, P.N), 6)
     u = synth.random_complex((3, P.N), 7)
     got = host(S.smooth(dev(f), dev(u.copy())))
     want = np.stack([sm.smooth(u[i], f[i], n_dd) for i in range(3)])
     assert relerr(got, want) < 1e-11
+    S.device_status()
 
 
 @pytest.mark.parametrize("c", CASES)
@@ -173,9 +185,12 @@ def test_host_buffer_entry_points(th):
 
 # ------------------------------------------------------------ mixed precision
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 2e-3), ("bf16", 2e-2)])
-def test_mixed_smoother_close_to_fp64(th, prec, tol):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_mixed_smoother_close_to_fp64(th, prec, tol, variant):
     c = CASES[5]
     S, P = build(th, c, prec=prec, extra_prec=("fp64",))
+    S.set_variant("dd", "fp32", variant)
+    S.set_variant("fine", "fp32", variant)
     f = dev(synth.random_complex((3, P.N), 16))
     u = synth.random_complex((3, P.N), 17)
     S.set_precision("fp64")
