@@ -230,7 +230,8 @@ enum {
   TH_K_COARSE_SOLVE = 6,/* coarse block-tridiagonal solve (K8) */
   TH_K_VECTOR = 7,      /* precision conversions, axpy, zero fill (K10) */
   TH_K_KRYLOV = 8,      /* FGMRES dots, norms, updates (K9) */
-  TH_K_COUNT = 9
+  TH_K_COUNT = 9,
+  TH_K_DD_BATCH = 9     /* (variants only) batched BF16 subdomain products: 0 CUDA cores, 1 tensor cores */
 };
 
 /* Per-kernel timing for measurement: with enable = 1 every later kernel
@@ -247,7 +248,11 @@ th_status th_profile_read(th_ctx* ctx, int kind, double* ms, long long* launches
  * on the context's own problem with CUDA events):
  *   TH_K_FINE: 0 = large cell tile, 1 = small cell tile;
  *   TH_K_DD:   0 = per-subdomain CTAs with direct loads,
- *              1 = persistent CTAs streaming the rows through TMA bulk copies.
+ *              1 = persistent CTAs streaming the rows through TMA bulk copies;
+ *   TH_K_DD_BATCH: 1 (default when the BF16 rows fit, U box <= 128 nodes) runs
+ *              the products of 8 or more right-hand sides on the tensor cores
+ *              (tcgen05.mma, BF16 operands, FP32 accumulation; the residuals
+ *              are rounded to BF16), 0 keeps them on the CUDA cores.
  * prec selects the FP64 or the FP32-cycle kernels (TH_PREC_FP64 / TH_PREC_FP32).
  * Overriding is for testing and measurement; every variant computes the same
  * result up to summation order. */

@@ -57,6 +57,8 @@ struct th_ctx {
   int ddG = 4;  // column groups per subdomain in K3
   int tc64 = 0, tc32 = 0;  // fine-apply tile variant per precision (0 large, 1 small), autotuned
   int dds64 = 0, dds32 = 0;  // DD kernel per precision: 0 k_dd_apply, 1 k_dd_stream (autotuned)
+  int dd_tc = 1;             // batched BF16 products on tensor cores (k_dd_umma) when available
+  unsigned char* Wu = nullptr;  // BF16 inverse rows in the tcgen05 operand layout (NR <= 128)
   int sms = 152;
   int* derr = nullptr;      // device flag: a bounded device wait gave up
   // device arrays
@@ -158,6 +160,9 @@ void carve_all(th_ctx& x, Carve& c) {
     x.W[k] = has_prec(x.avail, k) ? (void*)c.take<uint4>((size_t)g.nsub * x.wchunks[k] * g.NR) : nullptr;
   }
   x.wscale16 = has_prec(x.avail, TH_PREC_FP16) ? c.take<float>(g.nsub) : nullptr;
+  x.Wu = (has_prec(x.avail, TH_PREC_BF16) && g.NR <= 128)
+             ? c.take<unsigned char>((size_t)g.nsub * th::dd_umma_bytes_per_sub(g.NR, g.NC))
+             : nullptr;
   const bool fp64 = has_prec(x.avail, TH_PREC_FP64);
   x.G64 = fp64 ? c.take<double2>(mm * g.mc) : nullptr;
   const size_t blk = (size_t)g.mc * x.mcp;  // one padded dense block
@@ -362,6 +367,26 @@ th_status dd_apply(th_ctx& x, int wkind, const typename th::Cx<T>::t* r, int nrh
   a.nrhs = nrhs;
   x.launches += 1;
   Prof prof(x, TH_K_DD, s);
+  if constexpr (std::is_same<T, float>::value) {
+    if (wkind == TH_PREC_BF16 && x.Wu && x.dd_tc && nrhs >= 8) {
+      th::DDUmmaArgs u{};
+      u.r = r;
+      u.V = a.V;
+      u.W = x.Wu;
+      u.box = x.box;
+      u.err = x.derr;
+      u.N = g.N;
+      u.nsub = g.nsub;
+      u.m = g.m;
+      u.Lw = g.Lw;
+      u.NC = g.NC;
+      u.NR = g.NR;
+      u.nrhs = nrhs;
+      u.M8 = (g.NR + 7) / 8;
+      u.K8 = 2 * ((g.NC + 15) / 16);
+      return cuda_status(th::launch_dd_umma(u, x.sms, s));
+    }
+  }
   const int stream = std::is_same<T, double>::value ? x.dds64 : x.dds32;
   if (stream) return cuda_status(th::launch_dd_stream<T>(a, wkind, x.derr, x.sms, s));
   return cuda_status(th::launch_dd_apply<T>(a, wkind, 0, s));
@@ -884,6 +909,36 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     // copies read host memory asynchronously: finish before the staging buffer is reused
     TH_CU(cudaStreamSynchronize(s));
   }
+  if (x->Wu) {
+    // per subdomain: K-chunks of 64 columns, each [re | im] x [row/8][k/8 in chunk][8 rows][8 columns] BF16
+    const int M8 = (g.NR + 7) / 8, K8 = 2 * ((g.NC + 15) / 16);
+    const size_t sub_bytes = th::dd_umma_bytes_per_sub(g.NR, g.NC);
+    std::vector<uint16_t> ustage(sub_bytes / 2 * (size_t)g.nsub, 0);
+    th::parallel_for(g.nsub, [&](int sub) {
+      const cplx* src = Wh.data() + blk * sub;
+      uint16_t* base = ustage.data() + (size_t)sub * sub_bytes / 2;
+      for (int kc = 0; kc * 8 < K8; ++kc) {
+        const int kcs = std::min(8, K8 - kc * 8);
+        uint16_t* chunk = base + (size_t)kc * 8 * 2 * M8 * 64;
+        for (int ri = 0; ri < 2; ++ri) {
+          uint16_t* part = chunk + (size_t)ri * M8 * kcs * 64;
+          for (int mrow = 0; mrow < M8 * 8; ++mrow)
+            for (int k8 = 0; k8 < kcs; ++k8)
+              for (int e = 0; e < 8; ++e) {
+                const int col = (kc * 8 + k8) * 8 + e;
+                double v = 0.0;
+                if (mrow < g.NR && col < g.NC) {
+                  const cplx w = src[(size_t)mrow * g.NC + col];
+                  v = ri ? w.imag() : w.real();
+                }
+                part[((size_t)(mrow / 8) * kcs + k8) * 64 + (mrow % 8) * 8 + e] = f2bf((float)v);
+              }
+        }
+      }
+    });
+    if ((st = up(x->Wu, ustage.data(), ustage.size() * 2)) != TH_OK) return st;
+    TH_CU(cudaStreamSynchronize(s));
+  }
   TH_CU(cudaStreamSynchronize(s));
   {
     int dev = 0;
@@ -916,6 +971,8 @@ th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
     (d ? x->tc64 : x->tc32) = variant;
   } else if (kernel == TH_K_DD) {
     (d ? x->dds64 : x->dds32) = variant;
+  } else if (kernel == TH_K_DD_BATCH) {
+    x->dd_tc = variant;
   } else {
     return TH_ERR_ARG;
   }
@@ -927,6 +984,7 @@ th_status th_get_kernel_variant(const th_ctx* x, int kernel, int prec, int* vari
   const bool d = (prec == TH_PREC_FP64);
   if (kernel == TH_K_FINE) *variant = d ? x->tc64 : x->tc32;
   else if (kernel == TH_K_DD) *variant = d ? x->dds64 : x->dds32;
+  else if (kernel == TH_K_DD_BATCH) *variant = (x->Wu && x->dd_tc) ? 1 : 0;
   else return TH_ERR_ARG;
   return TH_OK;
 }

@@ -1,0 +1,300 @@
+// K3b: the subdomain inverse-row products for a batch of right-hand sides on
+// the fifth-generation tensor cores (tcgen05.mma, Section 4.1 / Algorithm 2:
+// V_i = W_i R_i r for every right-hand side at once).
+//
+// Per subdomain the product is a complex GEMM V = W X^T, W: NR x NC rows
+// (NR <= 128), X: NB x NC gathered residuals (NB right-hand sides).  In real
+// arithmetic, with A = W (M = 128 rows, K-major) and B = X (N = NB, K-major):
+//   D_re = W_re X_re^T - W_im X_im^T,   D_im = W_re X_im^T + W_im X_re^T,
+// four MMAs per K-step of 16 (the minus sign through the A-negate bit), with
+// BF16 operands and FP32 accumulators in tensor memory.
+//
+// Operand layout in shared memory: "core matrices" of 8 rows x 16 bytes,
+// arranged [row/8][k/8] with k/8 fastest, no swizzle; the descriptors carry
+// the K step (128 bytes) and the row step (the number of k/8 blocks times 128
+// bytes).  W is stored in global memory already in this layout, split into
+// K-chunks of 64 so each chunk is one contiguous bulk copy (TMA engine) per
+// real/imaginary part; rows 88..127 of the A tile are never loaded (their
+// results are discarded).  X is gathered from the FP32 residual, rounded to
+// BF16 and written in the same layout by producer warps.
+//
+// Roles in a persistent CTA (one per SM): warp 0 lane 0 issues the bulk copies
+// and the MMAs; warps 4-7 move the accumulators from tensor memory to global
+// memory; all other warps gather X.  W chunks go through a ring of 4 slots,
+// X and the accumulators are double-buffered; everything is ordered by
+// mbarriers.  Every wait has an iteration limit; when one gives up the CTA
+// raises `failed`, stops issuing work, drains what it issued (bounded) and
+// frees its tensor memory before returning.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace th {
+namespace {
+
+constexpr int kNB = 32;      // right-hand sides per tile (MMA N)
+constexpr int kKC = 8;       // k/8 blocks per W chunk (64 columns)
+constexpr int kDepth = 4;    // W chunk slots
+constexpr int kSlotBytes = 2 * 16 * kKC * 128;  // re + im, 128 rows, 64 columns
+constexpr int kThreads = 512;
+
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t umma_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version
+  return d;                // no swizzle, base offset 0
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(ok)
+               : "r"(su32(b)), "r"(parity)
+               : "memory");
+  return ok != 0;
+}
+// bounded wait; false when the limit is reached or the CTA already failed
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* failed) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    if (mbar_try(b, parity)) return true;
+    if ((it & 255) == 255 && *failed) return false;
+  }
+  *failed = 1;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void umma_bf16(unsigned d_tmem, uint64_t a, uint64_t b, unsigned idesc, unsigned acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(unsigned addr, unsigned* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+}  // namespace
+
+size_t dd_umma_bytes_per_sub(int NR, int NC) {
+  const int M8 = (NR + 7) / 8;
+  const int K8 = 2 * ((NC + 15) / 16);
+  return (size_t)K8 * 2 * M8 * 128;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_dd_umma(const DDUmmaArgs a) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  const int M8 = a.M8, K8 = a.K8;
+  const int NKC = (K8 + kKC - 1) / kKC;
+  const size_t xbuf_bytes = (size_t)2 * (kNB / 8) * K8 * 128;  // re + im
+  unsigned char* wslot = smraw;                                 // [kDepth][kSlotBytes]
+  unsigned char* xbuf = smraw + (size_t)kDepth * kSlotBytes;    // [2][xbuf_bytes]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(xbuf + 2 * xbuf_bytes);
+  uint64_t* wfull = bars;           // [kDepth]
+  uint64_t* wempty = bars + 4;      // [kDepth]
+  uint64_t* xfull = bars + 8;       // [2]
+  uint64_t* xempty = bars + 10;     // [2]
+  uint64_t* afull = bars + 12;      // [2]
+  uint64_t* aempty = bars + 14;     // [2]
+  uint64_t* done = bars + 16;       // every MMA of this CTA has completed
+  __shared__ unsigned tmem_base;
+  __shared__ volatile int failed;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r0 = blockIdx.y * kNB;
+  const int nmine = (a.nsub - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const bool producer = (warp >= 1 && warp <= 3) || warp >= 8;
+  const int nprod = 11 * 32;
+  const int pidx = (warp <= 3) ? tid - 32 : tid - 32 - 128;  // 0..351 among producers
+
+  if (tid == 0) {
+    failed = 0;
+    for (int i = 0; i < kDepth; ++i) { mbar_init(wfull + i, 1); mbar_init(wempty + i, 1); }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(xfull + i, nprod);
+      mbar_init(xempty + i, 1);
+      mbar_init(afull + i, 1);
+      mbar_init(aempty + i, 128);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                 "r"(4 * kNB)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------ TMA + MMA issuer
+      const int total = nmine * NKC;
+      const size_t sub_bytes = (size_t)K8 * 2 * M8 * 128;
+      int issued = 0;  // W chunks handed to the bulk-copy engine
+      auto issue = [&](int t) {
+        if (t >= total || failed) return;
+        const int i = t / NKC, kc = t - i * NKC;
+        const int sub = blockIdx.x + i * gridDim.x;
+        const int kcs = min(kKC, K8 - kc * kKC);
+        const unsigned part = (unsigned)(M8 * kcs * 128);
+        const int slot = t % kDepth, use = t / kDepth;
+        if (!mbar_wait(wempty + slot, (unsigned)((use & 1) ^ 1), &failed)) return;
+        mbar_expect_tx(wfull + slot, 2 * part);
+        const unsigned char* src = a.W + (size_t)sub * sub_bytes + (size_t)kc * kKC * 2 * M8 * 128;
+        unsigned char* dst = wslot + (size_t)slot * kSlotBytes;
+        bulk_g2s(dst, src, part, wfull + slot);                          // real part
+        bulk_g2s(dst + kSlotBytes / 2, src + part, part, wfull + slot);  // imaginary part
+        issued = t + 1;
+      };
+      // instruction descriptors: D f32, A/B bf16, K-major, N = kNB, M = 128
+      const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kNB >> 3) << 17) | (8u << 24);
+      const unsigned idesc_neg = idesc | (1u << 13);
+      for (int t = 0; t < kDepth - 1; ++t) issue(t);
+      int t = 0;
+      for (int i = 0; i < nmine && !failed; ++i) {
+        const int xb = i & 1, ux = i >> 1, ab = i & 1;
+        if (!mbar_wait(xfull + xb, (unsigned)(ux & 1), &failed)) break;
+        if (!mbar_wait(aempty + ab, (unsigned)((ux & 1) ^ 1), &failed)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned d_re = tmem + (unsigned)(ab * 2 * kNB), d_im = d_re + kNB;
+        const unsigned xre = su32(xbuf + (size_t)xb * xbuf_bytes), xim = xre + (unsigned)(xbuf_bytes / 2);
+        for (int kc = 0; kc < NKC; ++kc, ++t) {
+          const int slot = t % kDepth, use = t / kDepth;
+          if (!mbar_wait(wfull + slot, (unsigned)(use & 1), &failed)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int kcs = min(kKC, K8 - kc * kKC);
+          const unsigned wre = su32(wslot + (size_t)slot * kSlotBytes), wim = wre + kSlotBytes / 2;
+          const unsigned a_sbo = (unsigned)kcs * 128, b_sbo = (unsigned)K8 * 128;
+          for (int j = 0; j < kcs / 2; ++j) {
+            const unsigned ka = (unsigned)j * 256;                    // within the chunk
+            const unsigned kb = (unsigned)(kc * kKC + 2 * j) * 128;   // within X
+            const uint64_t Are = umma_desc(wre + ka, 128, a_sbo), Aim = umma_desc(wim + ka, 128, a_sbo);
+            const uint64_t Bre = umma_desc(xre + kb, 128, b_sbo), Bim = umma_desc(xim + kb, 128, b_sbo);
+            const unsigned acc = (kc > 0 || j > 0) ? 1u : 0u;
+            umma_bf16(d_re, Are, Bre, idesc, acc);
+            umma_bf16(d_re, Aim, Bim, idesc_neg, 1u);
+            umma_bf16(d_im, Are, Bim, idesc, acc);
+            umma_bf16(d_im, Aim, Bre, idesc, 1u);
+          }
+          umma_commit(wempty + slot);
+          issue(t + kDepth - 1);  // refill the slot freed by the previous chunk's MMAs
+        }
+        if (failed) break;
+        umma_commit(afull + ab);
+        umma_commit(xempty + xb);
+      }
+      // every MMA issued above completes before tensor memory is released
+      umma_commit(done);
+      volatile int ignore = 0;
+      mbar_wait(done, 0u, &ignore);
+      // bulk copies issued but not consumed (only after a failure)
+      for (int u = t; u < issued; ++u) mbar_wait(wfull + (u % kDepth), (unsigned)((u / kDepth) & 1), &ignore);
+    }
+  } else if (warp >= 4 && warp <= 7) {
+    // ------------------------------------------------ epilogue: TMEM -> V
+    const int q = warp - 4;  // lanes 32q .. 32q + 31 of tensor memory
+    const int row = q * 32 + lane;
+    for (int i = 0; i < nmine; ++i) {
+      const int ab = i & 1, ua = i >> 1;
+      const int sub = blockIdx.x + i * gridDim.x;
+      if (!failed) mbar_wait(afull + ab, (unsigned)(ua & 1), &failed);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned base = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(ab * 2 * kNB);
+      for (int c0 = 0; c0 < kNB; c0 += 16) {
+        unsigned re[16], im[16];
+        tmem_ld16(base + (unsigned)c0, re);
+        tmem_ld16(base + (unsigned)(kNB + c0), im);
+        if (row < a.NR && !failed) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int rhs = r0 + c0 + j;
+            if (rhs < a.nrhs)
+              a.V[((size_t)rhs * a.nsub + sub) * a.NR + row] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(aempty + ab);
+    }
+  } else if (producer) {
+    // ------------------------------------------------ X producers: gather, round to BF16
+    const int KP = K8 * 8;
+    for (int i = 0; i < nmine; ++i) {
+      const int xb = i & 1, ux = i >> 1;
+      const int sub = blockIdx.x + i * gridDim.x;
+      if (!failed) mbar_wait(xempty + xb, (unsigned)((ux & 1) ^ 1), &failed);
+      const int* bb = a.box + (size_t)sub * 8;
+      const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3];
+      __nv_bfloat16* xr = reinterpret_cast<__nv_bfloat16*>(xbuf + (size_t)xb * xbuf_bytes);
+      __nv_bfloat16* xi = xr + xbuf_bytes / 4;
+      for (int idx = pidx; idx < kNB * KP; idx += nprod) {
+        const int n = idx / KP, c = idx - n * KP;
+        const int cy = c / a.Lw, cx = c - cy * a.Lw;
+        float2 v = make_float2(0.f, 0.f);
+        const int rhs = r0 + n;
+        if (rhs < a.nrhs && c < a.NC && cx < wx && cy < wy)
+          v = a.r[(size_t)rhs * a.N + (size_t)(oy + cy) * a.m + (ox + cx)];
+        const size_t off = ((size_t)(n >> 3) * K8 + (c >> 3)) * 64 + (n & 7) * 8 + (c & 7);
+        xr[off] = __float2bfloat16_rn(v.x);
+        xi[off] = __float2bfloat16_rn(v.y);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(xfull + xb);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid == 0 && failed) atomicExch(a.err, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * kNB) : "memory");
+  }
+}
+
+cudaError_t launch_dd_umma(const DDUmmaArgs& a, int sms, cudaStream_t s) {
+  if (a.NR > 128 || (a.K8 & 1) || a.M8 * 8 > 128) return cudaErrorInvalidValue;
+  const size_t xbuf_bytes = (size_t)2 * (kNB / 8) * a.K8 * 128;
+  const size_t smem = (size_t)kDepth * kSlotBytes + 2 * xbuf_bytes + 17 * sizeof(uint64_t);
+  if (smem > 225 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_dd_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)(a.nsub < sms ? a.nsub : sms), (unsigned)((a.nrhs + kNB - 1) / kNB));
+  k_dd_umma<<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace th

@@ -48,6 +48,22 @@ cudaError_t launch_dd_apply(const DDArgs<T>& a, int kind, int grid_cap, cudaStre
 template <typename T>
 cudaError_t launch_dd_stream(const DDArgs<T>& a, int kind, int* err, int sms, cudaStream_t s);
 
+// ------------------------------------------------------- K3b batched DD on tensor cores
+// V[rhs][sub][row] = W_sub X_sub for a tile of NB right-hand sides with
+// tcgen05.mma (BF16 operands, FP32 accumulators in tensor memory).
+struct DDUmmaArgs {
+  const float2* r;        // residual, [rhs][N], FP32 complex
+  float2* V;              // [rhs][nsub][NR]
+  const unsigned char* W; // BF16 rows in the UMMA core-matrix layout (see setup)
+  const int* box;         // 8 ints per subdomain
+  int* err;               // set to 1 when a bounded wait gives up
+  long long N;
+  int nsub, m, Lw, NC, NR, nrhs;
+  int M8, K8;             // row and column core-matrix counts (rows <= 128, K8 even)
+};
+cudaError_t launch_dd_umma(const DDUmmaArgs& a, int sms, cudaStream_t s);
+size_t dd_umma_bytes_per_sub(int NR, int NC);
+
 // ------------------------------------------------------- K4 DD combine
 template <typename T>
 struct CombineArgs {

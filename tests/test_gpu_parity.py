@@ -234,3 +234,48 @@ def test_full_size_apply_and_cycle(th):
     want = TG.step(np.zeros_like(f), f)
     idx = synth.rng(21).integers(0, P.N, 4000)
     assert relerr(got[idx], want[idx]) < 1e-9
+
+
+# ------------------------------------------------------------ batched, tensor cores
+@pytest.mark.parametrize("nrhs", [8, 40])
+def test_batched_tensor_core_smoother(th, nrhs):
+    """BF16 subdomain products for many right-hand sides on tcgen05: the same
+    rows as the CUDA-core BF16 kernel, with the residuals also rounded to BF16
+    (both tcgen05 operands of the f16 kind share one type).  That rounding is
+    2^-9 relative per entry, the same as the rows' own, so the tensor-core and
+    CUDA-core results agree within the BF16-vs-FP64 smoother tolerance (2e-2)
+    and the tensor-core result stays within 1.5x of it from FP64."""
+    c = CASES[1]
+    S, P = build(th, c, nrhs=nrhs, prec="bf16", extra_prec=("fp64",))
+    f = dev(synth.random_complex((nrhs, P.N), 50))
+    u = synth.random_complex((nrhs, P.N), 51)
+    S.set_precision("fp64")
+    ref = host(S.smooth(f, dev(u.copy()))) - u
+    S.set_precision("bf16")
+    S.set_variant("dd_batch", "fp32", 1)
+    assert S.get_variant("dd_batch", "fp32") == 1
+    tc = host(S.smooth(f, dev(u.copy()))) - u
+    S.device_status()
+    S.set_variant("dd_batch", "fp32", 0)
+    cc = host(S.smooth(f, dev(u.copy()))) - u
+    assert relerr(tc, cc) < 2e-2
+    assert relerr(tc, ref) < 3e-2
+    # deterministic
+    S.set_variant("dd_batch", "fp32", 1)
+    tc2 = host(S.smooth(f, dev(u.copy()))) - u
+    assert np.array_equal(tc, tc2)
+
+
+def test_batched_tensor_core_solve(th):
+    w = synth.workload("square10_q4_n25")
+    nrhs = 16
+    F = synth.random_sources(w["n"], w["p"], 2, nrhs, seed=60)
+    S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=0.5, l_dd=2, prec="bf16",
+                         extra_prec=("fp64",), restart=40, nrhs_max=nrhs, device=DEV)
+    X, info = S.solve(dev(F))
+    S.device_status()
+    assert info["converged"] == nrhs and info["relres_max"] <= 1e-8
+    S.set_precision("fp64")
+    X64, info64 = S.solve(dev(F))
+    assert info["iters"] <= info64["iters"] + 2
+    assert relerr(host(X), host(X64)) < 1e-6
