@@ -191,11 +191,12 @@ def run_native(args):
     f = torch.from_numpy(np.ascontiguousarray(w["f"] if w["f"].ndim == 1 else w["f"][0])).to(dev)
     stream = torch.cuda.current_stream(dev)
 
-    def timed_cycles(prec, steps, warmup, profile=False, clocks=None):
+    def timed_cycles(prec, steps, warmup, profile=False, clocks=None, graph=True):
         S.set_precision(prec)
         u = torch.zeros_like(f)
+        step = S.cycle_graph if graph else S.cycle
         for _ in range(warmup):
-            S.cycle(f, u)
+            step(f, u)
         torch.cuda.synchronize(dev)
         barrier(world)
         torch.cuda.synchronize(dev)
@@ -208,7 +209,7 @@ def run_native(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            S.cycle(f, u)
+            step(f, u)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier(world)
@@ -223,10 +224,12 @@ def run_native(args):
     clocks = ClockSampler(local)
     ms_mixed, launches, _, ck, _ = timed_cycles("bf16", args.steps, args.warmup, clocks=clocks)
     ms_mixed = max_over_ranks(ms_mixed, world, dev)
-    # a second pass of the same steps with per-kernel CUDA events (library's th_profile)
-    ms_prof, _, prof, _, _ = timed_cycles("bf16", args.steps, 1, profile=True)
+    # the same steps launched kernel by kernel (no graph), then with per-kernel CUDA events (th_profile)
+    ms_nograph, _, _, _, _ = timed_cycles("bf16", args.steps, 2, graph=False)
+    ms_prof, _, prof, _, _ = timed_cycles("bf16", args.steps, 1, profile=True, graph=False)
     steps64 = max(3, args.steps // 2)
-    ms_fp64, _, prof64, _, _ = timed_cycles("fp64", steps64, max(3, args.warmup // 2), profile=True)
+    ms_fp64, _, _, _, _ = timed_cycles("fp64", steps64, max(3, args.warmup // 2))
+    _, _, prof64, _, _ = timed_cycles("fp64", steps64, 1, profile=True, graph=False)
     ms_fp64 = max_over_ranks(ms_fp64, world, dev)
 
     # time to 1e-8 (th_solve, synchronous; host clock inside the library)
@@ -278,6 +281,7 @@ def run_native(args):
                 "variants": {"dd_fp32": S.get_variant("dd", "fp32"), "fine_fp32": S.get_variant("fine", "fp32"),
                              "dd_fp64": S.get_variant("dd", "fp64"), "fine_fp64": S.get_variant("fine", "fp64")}}
 
+    fine_ms = sum(v[0] for k, v in per_step.items() if k != "coarse_solve")
     line = {
         "metric": METRIC,
         "value": round(gdofs(ms_mixed), 4),
@@ -295,11 +299,14 @@ def run_native(args):
                    "coarse_dofs": S.Nc, "wavelengths": 40, "alpha_s": w["alpha_s"], "l_dd": w["l_dd"],
                    "n_s": 1, "n_dd": 1, "omega_c": 1.0, "nrhs": 1,
                    "precision": "FP32 cycle, BF16 inverse rows (FP32 accumulate), FP64 FGMRES",
-                   "step": "one TwoGridStep u <- TwoGridStep(u, f): 3 fine applies, 2 DD smoothers, "
-                           "restriction, coarse block solve, prolongation",
+                   "step": "one TwoGridStep u <- TwoGridStep(u, f) replayed from a CUDA graph: FP64 residual, "
+                           "2 DD smoothers, FP32 residual, restriction, coarse block solve, prolongation",
                    "l2": "inputs larger than L2: the BF16 inverse rows streamed every smoother step are "
                          f"{alg_bytes / 1e6:.0f} MB > 129 MB",
                    "setup_s": round(setup_s, 2), "parallelism": f"replicas x{world}"},
+        "cycle_launch": {"graph_ms_per_step": round(ms_mixed, 4), "no_graph_ms_per_step": round(ms_nograph, 4)},
+        "fine_level": {"value": round(gdofs(fine_ms), 4), "unit": "GDOF/s", "ms_per_step": round(fine_ms, 4),
+                       "what": "sum of the per-kernel event times of every cycle kernel except the coarse solve"},
         "time_to_tol_ms": round(tt_mixed, 3),
         "iters": info_mixed["iters"],
         "relres": info_mixed["relres_max"],

@@ -175,8 +175,28 @@ th_status th_coarse_solve(th_ctx* ctx, const double* rc_dev, double* uc_dev, int
  * With u = 0 on input it is the preconditioner of Section 4. */
 th_status th_cycle(th_ctx* ctx, const double* f_dev, double* u_dev, int nrhs, void* stream);
 
+/* th_cycle replayed from a CUDA graph (no counterpart in the paper; the
+ * arithmetic is th_cycle's, bit for bit).  The first call for a given
+ * (f_dev, u_dev, nrhs, active precision) captures th_cycle's kernel sequence
+ * on a private stream of the context and instantiates it; that call and every
+ * later call with the same arguments launch the graph on `stream`, so a cycle
+ * costs one host call instead of about twenty kernel launches.  Captured
+ * graphs hold the pointers they were captured with: the caller must keep
+ * f_dev and u_dev valid (or stop calling with them).  th_set_precision and
+ * th_set_kernel_variant invalidate the cache; at most 256 graphs are kept per
+ * context (all are dropped when the cache is full).  While th_profile is on,
+ * or after th_set_graphs(ctx, 0), it runs th_cycle directly.
+ * Errors: those of th_cycle; TH_ERR_CUDA if capture or instantiation fails. */
+th_status th_cycle_graph(th_ctx* ctx, const double* f_dev, double* u_dev, int nrhs, void* stream);
+
+/* enable = 1 (default): th_cycle_graph and the preconditioner applications
+ * inside th_solve replay captured graphs; enable = 0: they launch kernel by
+ * kernel and the cached graphs are destroyed.  TH_ERR_ARG for other values. */
+th_status th_set_graphs(th_ctx* ctx, int enable);
+
 /* Same as th_cycle on host buffers: copies f and u to the device, runs the
- * cycle, copies u back; synchronous. */
+ * cycle (as th_cycle_graph: replayed from a captured graph unless graphs are
+ * off or profiling is on), copies u back; synchronous. */
 th_status th_cycle_host(th_ctx* ctx, const double* f_host, double* u_host, int nrhs, void* stream);
 
 /* th_coarse_solve without any workspace scratch (no counterpart in the paper).

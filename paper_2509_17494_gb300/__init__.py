@@ -82,6 +82,8 @@ def lib() -> ctypes.CDLL:
         "th_prolong": ([P, P, P, D, I, P], I),
         "th_coarse_solve": ([P, P, P, I, P], I),
         "th_cycle": ([P, P, P, I, P], I),
+        "th_cycle_graph": ([P, P, P, I, P], I),
+        "th_set_graphs": ([P, I], I),
         "th_cycle_host": ([P, P, P, I, P], I),
         "th_solve": ([P, P, P, I, ctypes.POINTER(SolveInfo), P], I),
         "th_solve_host": ([P, P, P, I, ctypes.POINTER(SolveInfo), P], I),
@@ -327,6 +329,17 @@ class TwoGridSolver:
         self._vec(u, self.N, "u")
         _check(lib().th_cycle(self._ctx, f.data_ptr(), u.data_ptr(), nrhs, self._stream()), "th_cycle")
         return u
+
+    def cycle_graph(self, f, u):
+        """One TwoGridStep(u, f), in place on u, replayed from a captured CUDA graph."""
+        nrhs = self._vec(f, self.N, "f")
+        self._vec(u, self.N, "u")
+        _check(lib().th_cycle_graph(self._ctx, f.data_ptr(), u.data_ptr(), nrhs, self._stream()),
+               "th_cycle_graph")
+        return u
+
+    def set_graphs(self, enable=True):
+        _check(lib().th_set_graphs(self._ctx, 1 if enable else 0), "th_set_graphs")
 
     def solve(self, f, u=None, check=True):
         """FGMRES with the two-grid preconditioner; returns (u, info dict)."""

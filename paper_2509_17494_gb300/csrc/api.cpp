@@ -81,6 +81,10 @@ struct th_ctx {
   int nred = 0;  // (P - 1) mc separator unknowns
   double2 *Gp64 = nullptr, *LR64 = nullptr, *Si64 = nullptr, *rh64 = nullptr;
   float2 *Gp32 = nullptr, *LR32 = nullptr, *Si32 = nullptr, *rh32 = nullptr;
+  // G_j transposed with rows padded to mcr, for the many-right-hand-side sweep (nrhs_max >= 2)
+  int rpcm = 0, mcr = 0;
+  double2* Gt64 = nullptr;
+  float2* Gt32 = nullptr;
   // cycle work vectors
   double2 *r64 = nullptr, *s64 = nullptr, *v64 = nullptr, *V64 = nullptr, *rc64 = nullptr, *uc64 = nullptr,
           *zc64 = nullptr, *t64 = nullptr;
@@ -96,7 +100,25 @@ struct th_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> prof_rec;  // (kind, first event index)
   size_t ev_used = 0;
+  // captured launch sequences (th_cycle_graph, the FGMRES preconditioner)
+  struct Graph {
+    int kind, nrhs, active;
+    const void* a;
+    const void* b;
+    long long epoch, launches;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t gstream = nullptr;  // private capture stream (the legacy stream cannot be captured)
+  bool use_graphs = true;
+  long long epoch = 0;  // bumped whenever a setting that changes the launch sequence changes
+  void drop_graphs() {
+    for (Graph& gr : graphs) cudaGraphExecDestroy(gr.exec);
+    graphs.clear();
+  }
   ~th_ctx() {
+    drop_graphs();
+    if (gstream) cudaStreamDestroy(gstream);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   }
 };
@@ -175,8 +197,9 @@ void carve_all(th_ctx& x, Carve& c) {
   if (fp64) {
     x.Gp64 = c.take<double2>(blk * g.mc);
     x.LR64 = c.take<double2>(2 * blk * g.mc);
-    x.Si64 = c.take<double2>(nred * nred);
+    x.Si64 = c.take<double2>(nred * (nred + (nred & 1)));
     x.rh64 = c.take<double2>(nred * nr);
+    if (nr >= 2) x.Gt64 = c.take<double2>(mm * x.mcr);
   }
   // FP64 work vectors are always present (residuals, FGMRES, FP64 applies)
   x.r64 = c.take<double2>((size_t)nr * g.N);
@@ -199,8 +222,9 @@ void carve_all(th_ctx& x, Carve& c) {
     x.cu32 = c.take<float2>(mm);
     x.Gp32 = c.take<float2>(blk * g.mc);
     x.LR32 = c.take<float2>(2 * blk * g.mc);
-    x.Si32 = c.take<float2>(nred * nred);
+    x.Si32 = c.take<float2>(nred * (nred + (nred & 1)));
     x.rh32 = c.take<float2>(nred * nr);
+    if (nr >= 2) x.Gt32 = c.take<float2>(mm * x.mcr);
     x.f32 = c.take<float2>((size_t)nr * g.N);
     x.u32 = c.take<float2>((size_t)nr * g.N);
     x.r32 = c.take<float2>((size_t)nr * g.N);
@@ -246,6 +270,8 @@ th_status prepare(const th_mesh* mesh, const th_params* prm, th_ctx& x) {
   x.rpc = (x.g.mc + x.cluster - 1) / x.cluster;
   x.P = th::coarse_chunks(x.g.mc);
   x.mcp = x.g.mc + (x.g.mc & 1);
+  x.rpcm = x.rpc + (x.rpc & 1);
+  x.mcr = x.cluster * x.rpcm;
   {
     const int rows = x.g.mc - (x.P - 1);
     x.Lmax = rows / x.P + ((rows % x.P) ? 1 : 0);
@@ -315,6 +341,7 @@ template <> struct PrecBufs<double> {
   static double2* rc(th_ctx& x) { return x.rc64; }
   static double2* uc(th_ctx& x) { return x.uc64; }
   static const double2* Gp(th_ctx& x) { return x.Gp64; }
+  static const double2* Gt(th_ctx& x) { return x.Gt64; }
   static const double2* LR(th_ctx& x) { return x.LR64; }
   static const double2* Si(th_ctx& x) { return x.Si64; }
   static double2* rh(th_ctx& x) { return x.rh64; }
@@ -334,6 +361,7 @@ template <> struct PrecBufs<float> {
   static float2* rc(th_ctx& x) { return x.rc32; }
   static float2* uc(th_ctx& x) { return x.uc32; }
   static const float2* Gp(th_ctx& x) { return x.Gp32; }
+  static const float2* Gt(th_ctx& x) { return x.Gt32; }
   static const float2* LR(th_ctx& x) { return x.LR32; }
   static const float2* Si(th_ctx& x) { return x.Si32; }
   static float2* rh(th_ctx& x) { return x.rh32; }
@@ -492,6 +520,7 @@ th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th:
   a.Sinv = B::Si(x);
   a.rhat = B::rh(x);
   a.nred = x.nred;
+  a.ldS = x.nred + (x.nred & 1);
   a.cl = B::cl(x);
   a.cd = B::cd(x);
   a.cu = B::cu(x);
@@ -505,6 +534,10 @@ th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th:
   a.P = x.P;
   a.rpc = x.rpc;
   a.Lmax = x.Lmax;
+  a.Gt = B::Gt(x);
+  a.mcr = x.mcr;
+  a.rpcm = x.rpcm;
+  a.nrhs = nrhs;
   if (!a.G || !a.LR) return TH_ERR_UNSUPPORTED;
   x.launches += (x.P > 1) ? 4 : 1;
   Prof prof(x, TH_K_COARSE_SOLVE, s);
@@ -565,6 +598,44 @@ th_status precondition(th_ctx& x, const double2* v, double2* z, int nrhs, cudaSt
   if ((st = narrow(x, v, x.f32, n, s)) != TH_OK) return st;
   if ((st = cycle<float>(x, x.active, x.f32, x.u32, true, nrhs, s)) != TH_OK) return st;
   return widen(x, x.u32, z, n, 0, s);
+}
+
+// Runs body(stream) from a CUDA graph: the first call for a key (kind, a, b,
+// nrhs, active precision, settings epoch) captures body's launches on the
+// private capture stream and instantiates them; every call then launches the
+// graph on s, so a cycle costs one host call instead of one per kernel.
+constexpr size_t kMaxGraphs = 256;
+template <typename F>
+th_status graph_run(th_ctx& x, int kind, const void* a, const void* b, int nrhs, cudaStream_t s, F&& body) {
+  for (const th_ctx::Graph& gr : x.graphs)
+    if (gr.kind == kind && gr.a == a && gr.b == b && gr.nrhs == nrhs && gr.active == x.active &&
+        gr.epoch == x.epoch) {
+      TH_CU(cudaGraphLaunch(gr.exec, s));
+      x.launches += gr.launches;
+      return TH_OK;
+    }
+  if (x.graphs.size() >= kMaxGraphs) x.drop_graphs();
+  if (!x.gstream) TH_CU(cudaStreamCreateWithFlags(&x.gstream, cudaStreamNonBlocking));
+  const long long l0 = x.launches;
+  TH_CU(cudaStreamBeginCapture(x.gstream, cudaStreamCaptureModeThreadLocal));
+  const th_status st = body(x.gstream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(x.gstream, &graph);
+  const long long nl = x.launches - l0;
+  x.launches = l0;  // nothing ran during the capture
+  if (st != TH_OK || ce != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return st != TH_OK ? st : TH_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return TH_ERR_CUDA;
+  x.graphs.push_back({kind, nrhs, x.active, a, b, x.epoch, nl, exec});
+  TH_CU(cudaGraphLaunch(exec, s));
+  x.launches += nl;
+  return TH_OK;
 }
 
 th_status check_nrhs(const th_ctx* x, int nrhs) {
@@ -828,8 +899,25 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     return TH_OK;
   };
   if ((st = upload_c(x->Gp64, x->Gp32, cpart.G)) != TH_OK) return st;
+  if (x->Gt64 || x->Gt32) {
+    // G_j^T with rows padded to mcr: Gt[j][c][row] = G[j][row][c]
+    const size_t mcr = (size_t)x->mcr, mcp = (size_t)x->mcp;
+    std::vector<cplx> gt((size_t)g.mc * g.mc * mcr, cplx(0.0));
+    th::parallel_for(g.mc, [&](int j) {
+      for (int row = 0; row < g.mc; ++row)
+        for (int c = 0; c < g.mc; ++c)
+          gt[((size_t)j * g.mc + c) * mcr + row] = cpart.G[((size_t)j * g.mc + row) * mcp + c];
+    });
+    if ((st = upload_c(x->Gt64, x->Gt32, gt)) != TH_OK) return st;
+  }
   if ((st = upload_c(x->LR64, x->LR32, cpart.LR)) != TH_OK) return st;
-  if (x->P > 1 && (st = upload_c(x->Si64, x->Si32, cpart.Sinv)) != TH_OK) return st;
+  if (x->P > 1) {
+    // rows padded to an even length (pairs of complex values per load)
+    const size_t nr_ = (size_t)x->nred, ld = nr_ + (nr_ & 1);
+    std::vector<cplx> sp(nr_ * ld, cplx(0.0));
+    for (size_t r = 0; r < nr_; ++r) std::copy(&cpart.Sinv[r * nr_], &cpart.Sinv[r * nr_] + nr_, &sp[r * ld]);
+    if ((st = upload_c(x->Si64, x->Si32, sp)) != TH_OK) return st;
+  }
   std::vector<float2> cell32, rho32, cl32, cd32, cu32;
   if (x->mixed) {
     cell32 = to2f(cb.cell);
@@ -976,6 +1064,7 @@ th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
   } else {
     return TH_ERR_ARG;
   }
+  ++x->epoch;
   return TH_OK;
 }
 
@@ -1005,6 +1094,7 @@ th_status th_set_precision(th_ctx* x, int prec) {
   if (!x || prec < 0 || prec > 3) return TH_ERR_ARG;
   if (!has_prec(x->avail, prec)) return TH_ERR_UNSUPPORTED;
   x->active = prec;
+  ++x->epoch;
   return TH_OK;
 }
 
@@ -1138,6 +1228,22 @@ th_status th_cycle(th_ctx* x, const double* f, double* u, int nrhs, void* stream
   return widen(*x, x->u32, u2, n, 1, s);
 }
 
+th_status th_cycle_graph(th_ctx* x, const double* f, double* u, int nrhs, void* stream) {
+  th_status st = check_nrhs(x, nrhs);
+  if (st != TH_OK) return st;
+  if (!f || !u) return TH_ERR_ARG;
+  if (!x->use_graphs || x->prof_on) return th_cycle(x, f, u, nrhs, stream);
+  return graph_run(*x, 0, f, u, nrhs, S(stream),
+                   [&](cudaStream_t gs) { return th_cycle(x, f, u, nrhs, (void*)gs); });
+}
+
+th_status th_set_graphs(th_ctx* x, int enable) {
+  if (!x || (enable != 0 && enable != 1)) return TH_ERR_ARG;
+  x->use_graphs = enable != 0;
+  if (!enable) x->drop_graphs();
+  return TH_OK;
+}
+
 th_status th_cycle_host(th_ctx* x, const double* f_host, double* u_host, int nrhs, void* stream) {
   th_status st = check_nrhs(x, nrhs);
   if (st != TH_OK) return st;
@@ -1146,7 +1252,7 @@ th_status th_cycle_host(th_ctx* x, const double* f_host, double* u_host, int nrh
   const size_t nb = sizeof(double2) * x->g.N * (size_t)nrhs;
   TH_CU(cudaMemcpyAsync(x->fin, f_host, nb, cudaMemcpyHostToDevice, s));
   TH_CU(cudaMemcpyAsync(x->uin, u_host, nb, cudaMemcpyHostToDevice, s));
-  if ((st = th_cycle(x, (const double*)x->fin, (double*)x->uin, nrhs, stream)) != TH_OK) return st;
+  if ((st = th_cycle_graph(x, (const double*)x->fin, (double*)x->uin, nrhs, stream)) != TH_OK) return st;
   TH_CU(cudaMemcpyAsync(u_host, x->uin, nb, cudaMemcpyDeviceToHost, s));
   TH_CU(cudaStreamSynchronize(s));
   return TH_OK;
@@ -1204,7 +1310,13 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
     for (int j = 0; j < m; ++j) {
       double2* Vj = x->Vk + (size_t)j * vstride;
       double2* Zj = x->Zk + (size_t)j * vstride;
-      if ((st = precondition(*x, Vj, Zj, nrhs, s)) != TH_OK) return st;
+      if (x->use_graphs && !x->prof_on) {
+        st = graph_run(*x, 1, Vj, Zj, nrhs, s,
+                       [&](cudaStream_t gs) { return precondition(*x, Vj, Zj, nrhs, gs); });
+      } else {
+        st = precondition(*x, Vj, Zj, nrhs, s);
+      }
+      if (st != TH_OK) return st;
       if ((st = fine_apply<double>(*x, TH_OP_A, Zj, nullptr, x->w, nrhs, s)) != TH_OK) return st;
       // classical Gram-Schmidt, twice
       x->launches += 6;

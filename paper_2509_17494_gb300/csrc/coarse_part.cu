@@ -8,12 +8,15 @@
 //      LU sweep of its chunk alone, y = A_cc^{-1} b_c, writing y into the
 //      output.  The chunks run concurrently, so the dependent chain is the
 //      chunk length (about sqrt(m_c)) instead of m_c.
-//   2. k_reduced_rhs + k_reduced_gemv: the separator rows satisfy a small
-//      dense system (P - 1 block rows); its right-hand side is formed from y
-//      and its FP64-set-up explicit inverse is applied as one row-parallel
-//      GEMV, writing the separator values into the output.
-//   3. k_spike_correct: every chunk row gets x_j = y_j - L_j x_left - R_j x_right
-//      (dense spike blocks, all rows in parallel).
+//   2. k_reduced_rhs + k_coarse_tsgemm<MODE 0>: the separator rows satisfy a
+//      small dense system (P - 1 block rows); its right-hand side is formed
+//      from y and its FP64-set-up explicit inverse is applied as one
+//      row-parallel product, writing the separator values into the output.
+//   3. k_coarse_tsgemm<MODE 1>: every chunk row gets
+//      x_j = y_j - L_j x_left - R_j x_right (dense spike blocks, all rows in
+//      parallel).
+// With several right-hand sides, k_chunk_sweep_mr and the NB-column
+// k_coarse_tsgemm take tiles of them (below).
 // Inside a cluster, CTA c owns rows [c rpc, (c+1) rpc) of every block vector.
 // After computing its rows of a block vector a CTA writes them into every
 // CTA's shared memory of the cluster (distributed shared memory), then all
@@ -222,58 +225,355 @@ __global__ void __launch_bounds__(256) k_reduced_rhs(const CoarsePartArgs<T> a) 
   a.rhat[(size_t)blockIdx.y * a.nred + i] = t;
 }
 
-// xhat = Sinv rhat, one warp per row, written into the separator rows of x
-template <typename T>
-__global__ void __launch_bounds__(256) k_reduced_gemv(const CoarsePartArgs<T> a) {
+// ------------------------------------------------------------- many right-hand sides
+// The same three stages for a tile of NB right-hand sides per cluster / warp:
+// every block of G, of the spikes and of the reduced inverse is read once per
+// tile instead of once per right-hand side, and the tile index varies fastest
+// in the grid so that the clusters running at the same time read the same
+// blocks (through L2).  The tile's vectors are stored [row][rhs] in shared
+// memory.  Each CTA splits the columns of its G_j rows over its warps; a lane
+// owns one row and NB accumulators, reads its row's entry of the transposed
+// G_j (consecutive across lanes) and the column's NB vector entries (the same
+// address for the whole warp); the warps' partial sums are then added in a
+// fixed order, so the result is bitwise deterministic.
+template <typename T, int NB, bool PREFETCH>
+__global__ void __launch_bounds__(512, 1) k_chunk_sweep_mr(const CoarsePartArgs<T> a) {
   using C = typename Cx<T>::t;
-  const int lane = threadIdx.x & 31;
-  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (row >= a.nred) return;
-  const C* srow = a.Sinv + (size_t)row * a.nred;
-  const C* r = a.rhat + (size_t)blockIdx.y * a.nred;
-  C acc;
-  acc.x = 0;
-  acc.y = 0;
-  for (int c = lane; c < a.nred; c += 32) cmac(acc, srow[c], r[c]);
-  acc = warp_sum<T>(acc);
-  if (lane == 0) {
-    const int k = (int)(row / a.mc), e = (int)(row - (long long)k * a.mc);
-    a.x[(size_t)blockIdx.y * a.Nc + (size_t)a.sep[k] * a.mc + e] = acc;
+  constexpr int NW = 16;  // warps per CTA
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank(), csz = (int)cl.num_blocks();
+  const int cid = blockIdx.x / csz;
+  const int ntiles = (a.nrhs + NB - 1) / NB;
+  const int tile = cid % ntiles, chunk = cid / ntiles;
+  const int r0 = tile * NB, nb = min(NB, a.nrhs - r0);
+  const int mc = a.mc, rpc = a.rpcm, mcr = a.mcr;
+  const int A = a.ca[chunk], L = a.cb[chunk] - A + 1;
+  const int nsteps = 2 * L - 1;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int row0 = crank * rpc, nrow = max(0, min(rpc, mc - row0));
+  const int cs = (mc + NW - 1) / NW, c0 = min(mc, warp * cs), c1 = min(mc, c0 + cs);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* gbuf = reinterpret_cast<C*>(smraw);                      // [2][mc][rpc] (PREFETCH)
+  C* bops = gbuf + (PREFETCH ? (size_t)2 * mc * rpc : 0);     // [2][mc][NB]
+  C* cops = bops + (size_t)2 * mc * NB;                       // [2][3][mc]
+  C* full = cops + (size_t)6 * mc;                            // [2][mc][NB]
+  C* tv = full + (size_t)2 * mc * NB;                         // [mc][NB]
+  C* red = tv + (size_t)mc * NB;                              // [NW][rpc][NB + 1]
+  C* zs = red + (size_t)NW * rpc * (NB + 1);                  // [Lmax][rpc][NB]: z, then y
+  auto block_of = [&](int q) { return q < L ? A + q : A + (2 * L - 2 - q); };
+  auto prefetch = [&](int q, int buf) {
+    if (q < nsteps) {
+      const int j = block_of(q);
+      if (PREFETCH && nrow > 0) {
+        const char* src = reinterpret_cast<const char*>(a.Gt + (size_t)j * mc * mcr + row0);
+        char* dst = reinterpret_cast<char*>(gbuf + (size_t)buf * mc * rpc);
+        const int units = (int)(rpc * sizeof(C) / 16);  // per column: this CTA's rows (padded)
+        for (int u = tid; u < mc * units; u += nth) {
+          const int c = u / units, w = u - c * units;
+          cp_async16(dst + ((size_t)c * rpc * sizeof(C) + (size_t)w * 16),
+                     src + ((size_t)c * mcr * sizeof(C) + (size_t)w * 16));
+        }
+      }
+      const bool f = q < L;
+      C* o = cops + (size_t)buf * 3 * mc;
+      const size_t oc = (size_t)(f ? j - 1 : j) * mc;
+      const C* r1 = f ? a.cu : a.cl;
+      const C* r2 = f ? a.cl : a.cu;
+      if (!f || q > 0) {
+        for (int k = tid; k < mc; k += nth) {
+          cp_async_elem(o + k, a.cd + oc + k);
+          cp_async_elem(o + mc + k, r1 + oc + k);
+          cp_async_elem(o + 2 * mc + k, r2 + oc + k);
+        }
+      }
+      if (f) {  // b_j of the tile's right-hand sides (a ragged tile repeats its last one)
+        C* bo = bops + (size_t)buf * mc * NB;
+        for (int i = tid; i < NB * mc; i += nth) {
+          const int r = i / mc, k = i - r * mc;
+          const C* src = a.b + (size_t)(r0 + min(r, nb - 1)) * a.Nc + (size_t)j * mc + k;
+          cp_async_elem(bo + (size_t)k * NB + r, src);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  prefetch(0, 0);
+  prefetch(1, 1);
+  for (int q = 0; q < nsteps; ++q) {
+    const bool fwd = q < L;
+    const int j = block_of(q);
+    const C* prev = full + (size_t)((q - 1) & 1) * mc * NB;
+    const C* o = cops + (size_t)(q & 1) * 3 * mc;
+    const C* bo = bops + (size_t)(q & 1) * mc * NB;
+    cp_async_wait<1>();
+    __syncthreads();
+    for (int i = tid; i < mc * NB; i += nth) {
+      const int k = i / NB;
+      C v;
+      v.x = 0;
+      v.y = 0;
+      if (!fwd || q > 0) {
+        cmac(v, o[k], prev[i]);
+        if (fwd) {  // C_{j-1}^T
+          if (k > 0) cmac(v, o[mc + k - 1], prev[i - NB]);
+          if (k + 1 < mc) cmac(v, o[2 * mc + k + 1], prev[i + NB]);
+        } else {    // C_j
+          if (k > 0) cmac(v, o[mc + k], prev[i - NB]);
+          if (k + 1 < mc) cmac(v, o[2 * mc + k], prev[i + NB]);
+        }
+      }
+      if (fwd) {
+        C tt = bo[i];
+        tt.x -= v.x;
+        tt.y -= v.y;
+        tv[i] = tt;
+      } else {
+        tv[i] = v;
+      }
+    }
+    __syncthreads();
+    // partial products over this warp's columns
+    const C* Gs = PREFETCH ? gbuf + (size_t)(q & 1) * mc * rpc : nullptr;
+    const C* Gg = a.Gt + (size_t)j * mc * mcr + row0;
+    for (int rr = lane; rr < nrow; rr += 32) {
+      C acc[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        acc[r].x = 0;
+        acc[r].y = 0;
+      }
+#pragma unroll 4
+      for (int c = c0; c < c1; ++c) {
+        const C g = PREFETCH ? Gs[(size_t)c * rpc + rr] : Gg[(size_t)c * mcr + rr];
+        const C* tc = tv + (size_t)c * NB;
+#pragma unroll
+        for (int r = 0; r < NB; ++r) cmac(acc[r], g, tc[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < NB; ++r) red[((size_t)warp * rpc + rr) * (NB + 1) + r] = acc[r];
+    }
+    __syncthreads();
+    C* dst = full + (size_t)(q & 1) * mc * NB;
+    for (int i = tid; i < nrow * NB; i += nth) {
+      const int rr = i / NB, r = i - rr * NB;
+      C s;
+      s.x = 0;
+      s.y = 0;
+      for (int w = 0; w < NW; ++w) {
+        if (w * cs >= mc) break;
+        const C v = red[((size_t)w * rpc + rr) * (NB + 1) + r];
+        s.x += v.x;
+        s.y += v.y;
+      }
+      const size_t zi = ((size_t)(j - A) * rpc + rr) * NB + r;
+      C val = s;
+      if (!fwd) {
+        const C z = zs[zi];
+        val.x = z.x - s.x;
+        val.y = z.y - s.y;
+      }
+      zs[zi] = val;  // z_j forward, y_j backward (y_{A+L-1} = z_{A+L-1})
+      for (int d = 0; d < csz; ++d) {
+        C* remote = cl.map_shared_rank(dst, d);
+        remote[(size_t)(row0 + rr) * NB + r] = val;
+      }
+    }
+    cluster_arrive_release();
+    cluster_wait_acquire();
+    prefetch(q + 2, q & 1);
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int i = tid; i < nb * L * nrow; i += nth) {
+    const int r = i / (L * nrow), rem = i - r * (L * nrow);
+    const int jj = rem / nrow, rr = rem - jj * nrow;
+    a.x[(size_t)(r0 + r) * a.Nc + (size_t)(A + jj) * mc + row0 + rr] = zs[((size_t)jj * rpc + rr) * NB + r];
   }
 }
 
-// ------------------------------------------------------------- spike correction
-template <typename T>
-__global__ void __launch_bounds__(256) k_spike_correct(const CoarsePartArgs<T> a) {
+// Tall-skinny products of the reduced solve and of the spike correction, for
+// one right-hand side or a tile of NB:
+//   MODE 0: xhat = Sinv rhat, written into the separator rows of x (one CTA per
+//           16 rows of Sinv, whose rows are padded to an even length ldS);
+//   MODE 1: x_j -= [L_j | R_j] [x_left; x_right] on every chunk row j (one CTA
+//           per quarter (one rhs) or half (tiles) of a block row; a CTA of a
+//           separator row returns at once).
+// The CTA stages the tile's right-hand-side columns in shared memory ([rhs]
+// [column]); each warp streams R matrix rows two complex values per lane and
+// load (16-byte loads for FP32, consecutive across lanes), reads the matching
+// column pair of every right-hand side with one shared load, and keeps R x NB
+// accumulators; row sums are warp reductions in a fixed order.  The tile index
+// varies fastest in the grid, so concurrent CTAs of different tiles read the
+// same matrix rows through L2.
+__device__ __forceinline__ void ld_pair(const float2* p, float2& u, float2& v) {
+  const float4 w = *reinterpret_cast<const float4*>(p);
+  u = make_float2(w.x, w.y);
+  v = make_float2(w.z, w.w);
+}
+__device__ __forceinline__ void ld_pair(const double2* p, double2& u, double2& v) {
+  u = p[0];
+  v = p[1];
+}
+
+template <typename T, int NB, int MODE>
+__global__ void __launch_bounds__(512) k_coarse_tsgemm(const CoarsePartArgs<T> a) {
   using C = typename Cx<T>::t;
+  constexpr int R = MODE == 0 ? 1 : 2, WARPS = 16;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* Xs = reinterpret_cast<C*>(smraw);  // [NB][kc]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ntiles = (a.nrhs + NB - 1) / NB;
+  const int tile = blockIdx.x % ntiles, blk = blockIdx.x / ntiles;
+  const int r0 = tile * NB, nb = min(NB, a.nrhs - r0);
   const int mc = a.mc, mcp = a.mcp;
-  const int lane = threadIdx.x & 31;
-  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nrows = (long long)mc * mc;
-  if (wid >= nrows) return;
-  const int j = (int)(wid / mc), e = (int)(wid - (long long)j * mc);
-  const int c = a.chunk_of[j];
-  if (c < 0) return;  // separator row
-  C* x = a.x + (size_t)blockIdx.y * a.Nc;
-  const C* row = a.LR + ((size_t)j * mc + e) * 2 * mcp;
-  C acc;
-  acc.x = 0;
-  acc.y = 0;
-  if (c > 0) {
-    const C* xl = x + (size_t)a.sep[c - 1] * mc;
-    for (int r = lane; r < mc; r += 32) cmac(acc, row[r], xl[r]);
+  int K, kc, rbeg, rend, j = 0, chunk = 0;
+  if (MODE == 0) {
+    K = a.ldS;
+    kc = NB == 1 ? K : 1024;
+    rbeg = blk * WARPS * R;
+    rend = min(a.nred, rbeg + WARPS * R);
+  } else {
+    constexpr int PARTS = NB == 1 ? 4 : 2;  // CTAs per block row
+    j = blk / PARTS;
+    chunk = a.chunk_of[j];
+    if (chunk < 0) return;  // separator block row (uniform over the CTA)
+    const int hr = (mc + PARTS - 1) / PARTS;
+    K = 2 * mcp;
+    kc = K;
+    rbeg = (blk - j * PARTS) * hr;
+    rend = min(mc, rbeg + hr);
   }
-  if (c < a.P - 1) {
-    const C* xr = x + (size_t)a.sep[c] * mc;
-    for (int r = lane; r < mc; r += 32) cmac(acc, row[mcp + r], xr[r]);
+  auto stage = [&](int k0, int kn) {
+    for (int i = tid; i < NB * kn; i += blockDim.x) {
+      const int r = i / kn, c = i - r * kn;
+      C v;
+      v.x = 0;
+      v.y = 0;
+      if (r < nb) {
+        if (MODE == 0) {
+          if (k0 + c < a.nred) v = a.rhat[(size_t)(r0 + r) * a.nred + k0 + c];
+        } else {
+          const int side = c >= mcp ? 1 : 0, k = c - side * mcp;
+          const bool has = k < mc && (side == 0 ? chunk > 0 : chunk < a.P - 1);
+          if (has) v = a.x[(size_t)(r0 + r) * a.Nc + (size_t)a.sep[side == 0 ? chunk - 1 : chunk] * mc + k];
+        }
+      }
+      Xs[(size_t)r * kc + c] = v;
+    }
+  };
+  auto rowptr = [&](int row) -> const C* {
+    return MODE == 0 ? a.Sinv + (size_t)row * a.ldS : a.LR + ((size_t)j * mc + row) * 2 * mcp;
+  };
+  // acc[q][r] += sum over the column pairs [k0, k0 + kn) of A[row_q] X_r
+  auto dot = [&](C (&acc)[R][NB], const C* const (&rows)[R], int k0, int kn) {
+#pragma unroll(NB == 1 ? 4 : 2)
+    for (int c = 2 * lane; c < kn; c += 64) {
+      C u[R], v[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) ld_pair(rows[q] + k0 + c, u[q], v[q]);
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        C xu, xv;
+        ld_pair(Xs + (size_t)r * kc + c, xu, xv);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          cmac(acc[q][r], u[q], xu);
+          cmac(acc[q][r], v[q], xv);
+        }
+      }
+    }
+  };
+  // lane r < nb ends with the sums of right-hand side r; MODE 1 subtracts them
+  // from y values the lane loaded before the products (yv), so no load waits
+  // behind a store
+  auto finish = [&](C (&acc)[R][NB], int row_first, const C (&yv)[R]) {
+    C out[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      out[q].x = 0;
+      out[q].y = 0;
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        const C s = warp_sum<T>(acc[q][r]);
+        if (lane == r) out[q] = s;
+      }
+    }
+    if (lane >= nb) return;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int row = row_first + q;
+      if (row >= rend) continue;
+      if (MODE == 0) {
+        const int k = row / mc, e = row - k * mc;
+        a.x[(size_t)(r0 + lane) * a.Nc + (size_t)a.sep[k] * mc + e] = out[q];
+      } else {
+        C v = yv[q];
+        v.x -= out[q].x;
+        v.y -= out[q].y;
+        a.x[(size_t)(r0 + lane) * a.Nc + (size_t)j * mc + row] = v;
+      }
+    }
+  };
+  auto zero = [&](C (&acc)[R][NB]) {
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        acc[q][r].x = 0;
+        acc[q][r].y = 0;
+      }
+  };
+  C acc[R][NB];
+  if (MODE == 0) {
+    const int row = rbeg + warp;
+    const C* rows[R] = {rowptr(row < rend ? row : rbeg)};
+    const C none[R] = {};
+    zero(acc);
+    for (int k0 = 0; k0 < K; k0 += kc) {
+      const int kn = min(kc, K - k0);
+      __syncthreads();
+      stage(k0, kn);
+      __syncthreads();
+      dot(acc, rows, k0, kn);
+    }
+    finish(acc, row, none);
+  } else {
+    stage(0, K);
+    __syncthreads();
+    for (int e0 = rbeg + warp * R; e0 < rend; e0 += WARPS * R) {
+      const C* rows[R];
+      C yv[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        rows[q] = rowptr(e0 + q < rend ? e0 + q : e0);
+        yv[q].x = 0;
+        yv[q].y = 0;
+        if (lane < nb && e0 + q < rend) yv[q] = a.x[(size_t)(r0 + lane) * a.Nc + (size_t)j * mc + e0 + q];
+      }
+      zero(acc);
+      dot(acc, rows, 0, K);
+      finish(acc, e0, yv);
+    }
   }
-  acc = warp_sum<T>(acc);
-  if (lane == 0) {
-    C v = x[(size_t)j * mc + e];
-    v.x -= acc.x;
-    v.y -= acc.y;
-    x[(size_t)j * mc + e] = v;
-  }
+}
+
+template <typename T, int NB>
+static cudaError_t launch_tsgemm(const CoarsePartArgs<T>& a, cudaStream_t s) {
+  using C = typename Cx<T>::t;
+  const int ntiles = (a.nrhs + NB - 1) / NB;
+  const size_t sm0 = sizeof(C) * (size_t)NB * (NB == 1 ? a.ldS : 1024), sm1 = sizeof(C) * (size_t)NB * 2 * a.mcp;
+  cudaError_t e = cudaFuncSetAttribute(k_coarse_tsgemm<T, NB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm0);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_coarse_tsgemm<T, NB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+  if (e != cudaSuccess) return e;
+  const unsigned g0 = (unsigned)((a.nred + 15) / 16) * ntiles;
+  k_coarse_tsgemm<T, NB, 0><<<g0, 512, sm0, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const unsigned g1 = (unsigned)((NB == 1 ? 4 : 2) * a.mc) * ntiles;
+  k_coarse_tsgemm<T, NB, 1><<<g1, 512, sm1, s>>>(a);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------- launcher
@@ -311,26 +611,56 @@ static cudaError_t launch_cluster(K kern, const Args& a, int grid, int cluster, 
 }
 
 template <typename T>
+constexpr int mr_tile() { return sizeof(T) == 8 ? 4 : 8; }
+
+template <typename T>
+size_t chunk_sweep_mr_smem(const CoarsePartArgs<T>& a, bool prefetch) {
+  using C = typename Cx<T>::t;
+  constexpr int NB = mr_tile<T>();
+  size_t s = (size_t)2 * a.mc * NB + (size_t)6 * a.mc + (size_t)2 * a.mc * NB + (size_t)a.mc * NB +
+             (size_t)16 * a.rpcm * (NB + 1) + (size_t)a.Lmax * a.rpcm * NB;
+  if (prefetch) s += (size_t)2 * a.mc * a.rpcm;
+  return s * sizeof(C);
+}
+
+// many right-hand sides: tiles of mr_tile<T>() per cluster / warp
+template <typename T>
+static cudaError_t launch_coarse_part_mr(const CoarsePartArgs<T>& a, int cluster, cudaStream_t s) {
+  constexpr int NB = mr_tile<T>();
+  const int ntiles = (a.nrhs + NB - 1) / NB;
+  const bool pf = chunk_sweep_mr_smem(a, true) <= 220 * 1024;
+  const size_t sm1 = chunk_sweep_mr_smem(a, pf);
+  if (sm1 > 227 * 1024) return cudaErrorInvalidValue;
+  const int grid = cluster * a.P * ntiles;
+  cudaError_t e = pf ? launch_cluster(k_chunk_sweep_mr<T, NB, true>, a, grid, cluster, sm1, s)
+                     : launch_cluster(k_chunk_sweep_mr<T, NB, false>, a, grid, cluster, sm1, s);
+  if (e != cudaSuccess || a.P < 2) return e;
+  dim3 g1((unsigned)((a.nred + 255) / 256), a.nrhs);
+  k_reduced_rhs<T><<<g1, 256, 0, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_tsgemm<T, NB>(a, s);
+}
+
+template <typename T>
 cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster, cudaStream_t s) {
+  if (nrhs >= 2 && a.Gt) {
+    CoarsePartArgs<T> b = a;
+    b.nrhs = nrhs;
+    return launch_coarse_part_mr<T>(b, cluster, s);
+  }
   const bool pf = chunk_sweep_smem(a, true) <= 220 * 1024;
   const size_t sm1 = chunk_sweep_smem(a, pf);
   cudaError_t e = pf ? launch_cluster(k_chunk_sweep<T, true>, a, cluster * a.P * nrhs, cluster, sm1, s)
                      : launch_cluster(k_chunk_sweep<T, false>, a, cluster * a.P * nrhs, cluster, sm1, s);
   if (e != cudaSuccess || a.P < 2) return e;
-  {
-    dim3 g1((unsigned)((a.nred + 255) / 256), nrhs);
-    k_reduced_rhs<T><<<g1, 256, 0, s>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    dim3 g2((unsigned)(((long long)a.nred * 32 + 255) / 256), nrhs);
-    k_reduced_gemv<T><<<g2, 256, 0, s>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  const long long warps = (long long)a.mc * a.mc;
-  dim3 grid((unsigned)((warps * 32 + 255) / 256), nrhs);
-  k_spike_correct<T><<<grid, 256, 0, s>>>(a);
-  return cudaGetLastError();
+  dim3 g1((unsigned)((a.nred + 255) / 256), nrhs);
+  k_reduced_rhs<T><<<g1, 256, 0, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CoarsePartArgs<T> b = a;
+  b.nrhs = nrhs;
+  return launch_tsgemm<T, 1>(b, s);
 }
 
 template cudaError_t launch_coarse_part<double>(const CoarsePartArgs<double>&, int, int, cudaStream_t);

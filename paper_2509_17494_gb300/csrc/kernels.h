@@ -128,7 +128,7 @@ struct CoarsePartArgs {
   typename Cx<T>::t* x;          // [rhs][Nc]
   const typename Cx<T>::t* G;    // chunk-row block inverses, mc blocks of mc x mcp
   const typename Cx<T>::t* LR;   // spikes [L_j | R_j], mc blocks of mc x 2 mcp
-  const typename Cx<T>::t* Sinv; // explicit inverse of the reduced separator system, nred x nred
+  const typename Cx<T>::t* Sinv; // explicit inverse of the reduced separator system, nred x ldS
   typename Cx<T>::t* rhat;       // scratch: reduced right-hand sides, [rhs][nred]
   const typename Cx<T>::t* cl;   // C_j diagonals
   const typename Cx<T>::t* cd;
@@ -137,8 +137,12 @@ struct CoarsePartArgs {
   const int* cb;                 // chunk last rows
   const int* sep;                // separator rows
   const int* chunk_of;           // per row: chunk index, or -1 for a separator
+  // multi-right-hand-side sweep: G_j transposed, [j][column][mcr] (rows padded to mcr = cluster * rpcm)
+  const typename Cx<T>::t* Gt;
   long long Nc;
   int mc, mcp, P, rpc, Lmax, nred;
+  int mcr, rpcm, nrhs;           // rpcm: rows per CTA of the multi-rhs sweep (even)
+  int ldS;                       // row stride of Sinv (nred rounded up to even)
 };
 template <typename T>
 cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster, cudaStream_t s);

@@ -122,6 +122,28 @@ def test_coarse_solve_fp64(th, c):
     assert relerr(got, want) < 1e-9
 
 
+@pytest.mark.parametrize("c", [CASES[0], CASES[2], CASES[5]])
+@pytest.mark.parametrize("nrhs", [2, 11])
+def test_coarse_solve_many_rhs(th, c, nrhs):
+    """Tiles of right-hand sides (ragged: 2 and 8 + 3) in FP64 against the
+    oracle, and in FP32 (the mixed cycle's coarse solve) against FP64 and
+    against the FP32 one-right-hand-side sweep (same products, other
+    summation order: a few FP32 roundings times the coarse condition number)."""
+    S, P = build(th, c, nrhs=nrhs, prec="fp64", extra_prec=("fp32",))
+    rc = synth.random_complex((nrhs, P.Nc), 31)
+    B = twogrid.BandedSolver(P.Aq)
+    want = np.stack([B.solve(rc[i]) for i in range(nrhs)])
+    got64 = host(S.coarse_solve(dev(rc)))
+    assert relerr(got64, want) < 1e-9
+    S.set_precision("fp32")
+    got32 = host(S.coarse_solve(dev(rc)))
+    one32 = np.stack([host(S.coarse_solve(dev(rc[i]))) for i in range(nrhs)])
+    assert relerr(got32, want) < 1e-4
+    assert relerr(got32, one32) < 1e-5
+    again = host(S.coarse_solve(dev(rc)))
+    assert np.array_equal(again, got32)
+
+
 @pytest.mark.parametrize("c", CASES)
 @pytest.mark.parametrize("n_s,omega_c", [(1, 1.0), (2, 0.8)])
 def test_cycle_fp64(th, c, n_s, omega_c):
