@@ -104,6 +104,8 @@ typedef struct {
   double relres_max;    /* max over rhs of the true ||f - A u|| / ||f|| at exit */
   double ms_total;      /* wall time of th_solve (host clock, includes syncs) */
   int iters_per_rhs[64];/* iterations of the first min(nrhs, 64) right-hand sides */
+  int fallbacks;        /* learned coarse corrector: restarts with the direct
+                         * coarse solve (see th_set_coarse), else 0 */
 } th_solve_info;
 
 typedef struct th_ctx th_ctx;
@@ -234,6 +236,70 @@ th_status th_solve(th_ctx* ctx, const double* f_dev, double* u_dev, int nrhs,
 /* th_solve on host buffers (copies in and out inside the call). */
 th_status th_solve_host(th_ctx* ctx, const double* f_host, double* u_host, int nrhs,
                         th_solve_info* info, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned coarse corrector (no counterpart in the paper).
+ *
+ * A small convolutional U-Net on the coarse node grid that stands in for the
+ * coarse solve "u_c = A_c^{-1} r_c" of Algorithm 1:
+ *     u_c ~= s * UNet([Re r_c / s, Im r_c / s, eta]),  s = RMS(r_c),
+ * eta = k h_c averaged from the coarse cells to the nodes (2-D only).  With L
+ * levels and C_l = base * 2^l channels on the node grid zero-padded to a
+ * multiple of 2^(L-1): per encoder level two 3x3 convolutions with SiLU and
+ * 2x2 average pooling, per decoder level nearest doubling, concatenation
+ * [skip, doubled] and two 3x3 convolutions with SiLU, then a 1x1 head to the
+ * 2 output channels.  BF16 weights and activations, FP32 accumulation on the
+ * tensor cores; FP32 master weights, gradients and Adam moments.
+ * Parameters are FP32 arrays in this order, per convolution weights
+ * [c_out][3][3][c_in] then bias [c_out]: encoder levels 0..L-1 (a, b), decoder
+ * levels L-2..0 (a, b), head weights [2][base] and bias [2].
+ * The network's buffers are allocated with cudaMalloc by th_unet_init (for
+ * batch_max right-hand sides) and freed by th_destroy.
+ * --------------------------------------------------------------------------- */
+
+/* Number of FP32 parameters; TH_ERR_ARG unless levels in [2, 6], base a
+ * multiple of 16, base 2^(L-1) <= 256 and 3 base 2^(L-2) <= 256. */
+th_status th_unet_param_count(int levels, int base, size_t* n);
+
+/* Creates (or replaces) the context's corrector with the given initial
+ * parameters (host, n = th_unet_param_count).  Synchronous.
+ * TH_ERR_UNSUPPORTED for a 3-D context, TH_ERR_NOMEM if allocation fails. */
+th_status th_unet_init(th_ctx* ctx, int levels, int base, int batch_max, const float* params_host,
+                       size_t n, void* stream);
+
+/* Copies the FP32 master parameters to / from the host (synchronous); a set
+ * also resets the Adam state. */
+th_status th_unet_get_params(th_ctx* ctx, float* params_host, size_t n, void* stream);
+th_status th_unet_set_params(th_ctx* ctx, const float* params_host, size_t n, void* stream);
+
+/* The network alone (for checks): in [batch][mp][mp][3] FP32 (padded node
+ * grid, mp = the node count rounded up to a multiple of 2^(L-1)) ->
+ * out [batch][mp][mp][2] FP32; batch <= batch_max. */
+th_status th_unet_forward(th_ctx* ctx, const float* in_dev, float* out_dev, int batch, void* stream);
+
+/* Gradients of sum(out * gout) with respect to every parameter (FP32, the
+ * parameter order above) for the activations of the last th_unet_forward. */
+th_status th_unet_backward(th_ctx* ctx, const float* gout_dev, float* grads_dev, int batch,
+                           void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
+ * loss mean_b ||out_b - u_b / s_b||^2 / ||u_b / s_b||^2 over the unpadded
+ * nodes for pairs (r_c, u_c) in FP64 complex [batch][N_c] on the device;
+ * *loss (may be NULL) receives the loss before the step (synchronous then). */
+th_status th_unet_train_step(th_ctx* ctx, const double* rc_dev, const double* uc_dev, int batch,
+                             double lr, double* loss, void* stream);
+
+/* u_c = s UNet(r_c / s) for nrhs coarse residuals (FP64 complex [nrhs][N_c]). */
+th_status th_unet_correct(th_ctx* ctx, const double* rc_dev, double* uc_dev, int nrhs, void* stream);
+
+/* Coarse correction inside th_cycle / th_solve: TH_COARSE_DIRECT (default),
+ * TH_COARSE_LEARNED (needs th_unet_init) or TH_COARSE_NONE (u_c = 0: the
+ * smoother alone, for comparison).  With TH_COARSE_LEARNED and plain_iters >
+ * 0, th_solve switches to the direct solve (restarting from its current
+ * iterate) once its iteration count reaches ceil(1.5 plain_iters), and counts
+ * that in th_solve_info.fallbacks; plain_iters = 0 disables the fallback. */
+enum { TH_COARSE_DIRECT = 0, TH_COARSE_LEARNED = 1, TH_COARSE_NONE = 2 };
+th_status th_set_coarse(th_ctx* ctx, int mode, int plain_iters);
 
 /* Number of kernel launches the library issued since the context was built
  * (all entry points), for accounting. */

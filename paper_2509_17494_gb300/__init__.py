@@ -48,7 +48,7 @@ class Params(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("relres_max", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("iters_per_rhs", ctypes.c_int * 64)]
+                ("ms_total", ctypes.c_double), ("iters_per_rhs", ctypes.c_int * 64), ("fallbacks", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -83,6 +83,15 @@ def lib() -> ctypes.CDLL:
         "th_coarse_solve": ([P, P, P, I, P], I),
         "th_cycle": ([P, P, P, I, P], I),
         "th_cycle_graph": ([P, P, P, I, P], I),
+        "th_unet_param_count": ([I, I, ctypes.POINTER(ctypes.c_size_t)], I),
+        "th_unet_init": ([P, I, I, I, P, ctypes.c_size_t, P], I),
+        "th_unet_get_params": ([P, P, ctypes.c_size_t, P], I),
+        "th_unet_set_params": ([P, P, ctypes.c_size_t, P], I),
+        "th_unet_forward": ([P, P, P, I, P], I),
+        "th_unet_backward": ([P, P, P, I, P], I),
+        "th_unet_train_step": ([P, P, P, I, D, ctypes.POINTER(ctypes.c_double), P], I),
+        "th_unet_correct": ([P, P, P, I, P], I),
+        "th_set_coarse": ([P, I, I], I),
         "th_set_graphs": ([P, I], I),
         "th_cycle_host": ([P, P, P, I, P], I),
         "th_solve": ([P, P, P, I, ctypes.POINTER(SolveInfo), P], I),
@@ -131,6 +140,27 @@ def _params(alpha_s=0.5, l_dd=2, n_dd=1, n_s=1, omega_c=1.0, prec="fp64", extra_
     q.prec_mask = mask
     q.restart, q.maxit, q.tol, q.nrhs_max = int(restart), int(maxit), float(tol), int(nrhs_max)
     return q
+
+
+def unet_param_shapes(levels=4, base=16):
+    """(name, shape) of the corrector's parameters in the library's order (see th.h)."""
+    C = [base << l for l in range(levels)]
+    out, prev = [], 3
+    for l in range(levels):
+        out += [(f"e{l}a.w", (C[l], 3, 3, prev)), (f"e{l}a.b", (C[l],)),
+                (f"e{l}b.w", (C[l], 3, 3, C[l])), (f"e{l}b.b", (C[l],))]
+        prev = C[l]
+    for l in range(levels - 2, -1, -1):
+        out += [(f"d{l}a.w", (C[l], 3, 3, C[l] + C[l + 1])), (f"d{l}a.b", (C[l],)),
+                (f"d{l}b.w", (C[l], 3, 3, C[l])), (f"d{l}b.b", (C[l],))]
+    return out + [("head.w", (2, C[0])), ("head.b", (2,))]
+
+
+def unet_param_count(levels=4, base=16) -> int:
+    """FP32 parameter count of the learned coarse corrector (th_unet_param_count)."""
+    n = ctypes.c_size_t(0)
+    _check(lib().th_unet_param_count(int(levels), int(base), ctypes.byref(n)), "th_unet_param_count")
+    return n.value
 
 
 def workspace_size(n, p, bc="robin", **params) -> int:
@@ -338,6 +368,62 @@ class TwoGridSolver:
                "th_cycle_graph")
         return u
 
+    # ------------------------------------------------------- learned coarse corrector
+    def unet_init(self, params, levels=4, base=16, batch_max=8):
+        """params: FP32 array in the library's parameter order (th_unet_param_count entries)."""
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self.unet_levels = int(levels)
+        _check(lib().th_unet_init(self._ctx, int(levels), int(base), int(batch_max), p.ctypes.data, p.size,
+                                  self._stream()), "th_unet_init")
+        self._unet_count = p.size
+        mc = self.n * self.p // 2 + 1
+        q = 1 << (int(levels) - 1)
+        self.unet_mp = (mc + q - 1) // q * q
+
+    def unet_params(self):
+        out = np.zeros(self._unet_n(), dtype=np.float32)
+        _check(lib().th_unet_get_params(self._ctx, out.ctypes.data, out.size, self._stream()), "th_unet_get_params")
+        return out
+
+    def unet_set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().th_unet_set_params(self._ctx, p.ctypes.data, p.size, self._stream()), "th_unet_set_params")
+
+    def unet_forward(self, x, out=None):
+        """x: float32 CUDA tensor [B, mp, mp, 3] -> [B, mp, mp, 2]."""
+        B = int(x.shape[0])
+        if out is None:
+            out = self.torch.empty((B, x.shape[1], x.shape[2], 2), dtype=self.torch.float32, device=x.device)
+        _check(lib().th_unet_forward(self._ctx, x.data_ptr(), out.data_ptr(), B, self._stream()), "th_unet_forward")
+        return out
+
+    def unet_backward(self, gout):
+        g = self.torch.empty(self._unet_n(), dtype=self.torch.float32, device=gout.device)
+        _check(lib().th_unet_backward(self._ctx, gout.data_ptr(), g.data_ptr(), int(gout.shape[0]), self._stream()),
+               "th_unet_backward")
+        return g
+
+    def unet_train_step(self, rc, uc, lr=1e-3):
+        B = self._vec(rc, self.Nc, "rc")
+        self._vec(uc, self.Nc, "uc")
+        loss = ctypes.c_double(0)
+        _check(lib().th_unet_train_step(self._ctx, rc.data_ptr(), uc.data_ptr(), B, float(lr), ctypes.byref(loss),
+                                        self._stream()), "th_unet_train_step")
+        return loss.value
+
+    def unet_correct(self, rc, out=None):
+        nrhs = self._vec(rc, self.Nc, "rc")
+        uc = out if out is not None else self.torch.empty_like(rc)
+        _check(lib().th_unet_correct(self._ctx, rc.data_ptr(), uc.data_ptr(), nrhs, self._stream()), "th_unet_correct")
+        return uc
+
+    def set_coarse(self, mode="direct", plain_iters=0):
+        m = {"direct": 0, "learned": 1, "none": 2}[mode]
+        _check(lib().th_set_coarse(self._ctx, m, int(plain_iters)), "th_set_coarse")
+
+    def _unet_n(self):
+        return self._unet_count
+
     def set_graphs(self, enable=True):
         _check(lib().th_set_graphs(self._ctx, 1 if enable else 0), "th_set_graphs")
 
@@ -374,4 +460,5 @@ class TwoGridSolver:
 
 def _info(info, nrhs, st):
     return dict(iters=info.iters, converged=info.converged, relres_max=info.relres_max,
-                ms_total=info.ms_total, iters_per_rhs=list(info.iters_per_rhs[:min(nrhs, 64)]), status=st)
+                ms_total=info.ms_total, iters_per_rhs=list(info.iters_per_rhs[:min(nrhs, 64)]),
+                fallbacks=info.fallbacks, status=st)

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "unet_net.h"
 #include "th_internal.h"
 
 using th::cplx;
@@ -112,11 +113,16 @@ struct th_ctx {
   cudaStream_t gstream = nullptr;  // private capture stream (the legacy stream cannot be captured)
   bool use_graphs = true;
   long long epoch = 0;  // bumped whenever a setting that changes the launch sequence changes
+  // coarse correction: 0 direct solve, 1 learned corrector, 2 none; fallback count for th_solve
+  int coarse_mode = 0, plain_iters = 0;
+  th::UNet* unet = nullptr;
+  std::vector<double> k_host;  // k per fine cell (inputs of the learned corrector)
   void drop_graphs() {
     for (Graph& gr : graphs) cudaGraphExecDestroy(gr.exec);
     graphs.clear();
   }
   ~th_ctx() {
+    delete unet;
     drop_graphs();
     if (gstream) cudaStreamDestroy(gstream);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
@@ -561,6 +567,18 @@ th_status coarse_apply_(th_ctx& x, const typename th::Cx<T>::t* in, typename th:
   return cuda_status(th::launch_coarse_apply<T>(a, nrhs, s));
 }
 
+// u_c from r_c: the direct coarse solve, the learned corrector or nothing (th_set_coarse)
+template <typename T>
+th_status coarse_correct_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th::Cx<T>::t* uc, int nrhs,
+                          cudaStream_t s) {
+  if (x.coarse_mode == 0 || !x.unet) return coarse_solve_<T>(x, rc, uc, nrhs, s);
+  x.launches += x.unet->launches_per_forward();
+  Prof prof(x, TH_K_COARSE_SOLVE, s);
+  if (x.coarse_mode == 2)
+    return cuda_status(cudaMemsetAsync(uc, 0, sizeof(typename th::Cx<T>::t) * x.g.Nc * (size_t)nrhs, s));
+  return cuda_status(x.unet->correct<typename th::Cx<T>::t>(rc, uc, x.g.Nc, nrhs, s));
+}
+
 // TwoGridStep(u, f) of Algorithm 1 in precision T.
 template <typename T>
 th_status cycle(th_ctx& x, int wkind, const typename th::Cx<T>::t* f, typename th::Cx<T>::t* u, bool u_zero,
@@ -571,7 +589,7 @@ th_status cycle(th_ctx& x, int wkind, const typename th::Cx<T>::t* f, typename t
     if ((st = smooth<T>(x, wkind, f, u, u_zero && i == 0, nrhs, s)) != TH_OK) return st;
   if ((st = fine_apply<T>(x, TH_OP_A, u, f, B::r(x), nrhs, s)) != TH_OK) return st;
   if ((st = restrict_<T>(x, B::r(x), B::rc(x), nrhs, s)) != TH_OK) return st;
-  if ((st = coarse_solve_<T>(x, B::rc(x), B::uc(x), nrhs, s)) != TH_OK) return st;
+  if ((st = coarse_correct_<T>(x, B::rc(x), B::uc(x), nrhs, s)) != TH_OK) return st;
   if ((st = prolong_<T>(x, B::uc(x), u, (T)x.prm.omega_c, nrhs, s)) != TH_OK) return st;
   for (int i = 0; i < x.prm.n_s; ++i)
     if ((st = smooth<T>(x, wkind, f, u, false, nrhs, s)) != TH_OK) return st;
@@ -607,6 +625,7 @@ th_status precondition(th_ctx& x, const double2* v, double2* z, int nrhs, cudaSt
 constexpr size_t kMaxGraphs = 256;
 template <typename F>
 th_status graph_run(th_ctx& x, int kind, const void* a, const void* b, int nrhs, cudaStream_t s, F&& body) {
+  if (!x.graphs.empty() && x.graphs.front().epoch != x.epoch) x.drop_graphs();  // settings changed
   for (const th_ctx::Graph& gr : x.graphs)
     if (gr.kind == kind && gr.a == a && gr.b == b && gr.nrhs == nrhs && gr.active == x.active &&
         gr.epoch == x.epoch) {
@@ -797,6 +816,7 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
   if (st != TH_OK) return st;
   const th::Geometry& g = x->g;
   const size_t n2 = (size_t)g.n * g.n;
+  x->k_host.assign(k_host, k_host + n2);
   for (size_t i = 0; i < n2; ++i) {
     if (!std::isfinite(k_host[i]) || k_host[i] <= 0.0) return TH_ERR_ARG;
     if (eps_host && (!std::isfinite(eps_host[i]) || eps_host[i] < 0.0)) return TH_ERR_ARG;
@@ -1244,6 +1264,101 @@ th_status th_set_graphs(th_ctx* x, int enable) {
   return TH_OK;
 }
 
+// ------------------------------------------------------------ learned coarse corrector
+th_status th_unet_param_count(int levels, int base, size_t* n) {
+  if (!n || !th::UNet::check(levels, base)) return TH_ERR_ARG;
+  *n = th::UNet::param_count(levels, base);
+  return TH_OK;
+}
+
+th_status th_unet_init(th_ctx* x, int levels, int base, int batch_max, const float* params, size_t n,
+                       void* stream) {
+  if (!x || !params || batch_max < 1 || !th::UNet::check(levels, base)) return TH_ERR_ARG;
+  if (n != th::UNet::param_count(levels, base)) return TH_ERR_ARG;
+  if (x->mesh.dim != 2) return TH_ERR_UNSUPPORTED;
+  const th::Geometry& g = x->g;
+  // eta = k h_c at the coarse nodes: mean over the adjacent coarse cells, each
+  // of which takes the k of the fine cell containing it
+  const int nc = g.nc, m = g.mc;
+  std::vector<float> eta((size_t)m * m);
+  for (int y = 0; y < m; ++y)
+    for (int xx = 0; xx < m; ++xx) {
+      double acc = 0;
+      int cnt = 0;
+      for (int cy = y - 1; cy <= y; ++cy)
+        for (int cx = xx - 1; cx <= xx; ++cx) {
+          if (cy < 0 || cy >= nc || cx < 0 || cx >= nc) continue;
+          acc += x->k_host[(size_t)(cy / g.q) * g.n + cx / g.q] * g.hc;
+          ++cnt;
+        }
+      eta[(size_t)y * m + xx] = (float)(acc / cnt);
+    }
+  delete x->unet;
+  x->unet = new (std::nothrow) th::UNet(levels, base, batch_max, m, eta, x->derr);
+  if (!x->unet || !x->unet->ok()) {
+    delete x->unet;
+    x->unet = nullptr;
+    return TH_ERR_NOMEM;
+  }
+  if (x->unet->set_params(params, S(stream)) != cudaSuccess) return TH_ERR_CUDA;
+  ++x->epoch;
+  return TH_OK;
+}
+
+th_status th_unet_get_params(th_ctx* x, float* params, size_t n, void* stream) {
+  if (!x || !params) return TH_ERR_ARG;
+  if (!x->unet) return TH_ERR_UNSUPPORTED;
+  if (n != x->unet->nparams()) return TH_ERR_ARG;
+  return cuda_status(x->unet->get_params(params, S(stream)));
+}
+
+th_status th_unet_set_params(th_ctx* x, const float* params, size_t n, void* stream) {
+  if (!x || !params) return TH_ERR_ARG;
+  if (!x->unet) return TH_ERR_UNSUPPORTED;
+  if (n != x->unet->nparams()) return TH_ERR_ARG;
+  return cuda_status(x->unet->set_params(params, S(stream)));
+}
+
+th_status th_unet_forward(th_ctx* x, const float* in_dev, float* out_dev, int batch, void* stream) {
+  if (!x || !in_dev || !out_dev) return TH_ERR_ARG;
+  if (!x->unet) return TH_ERR_UNSUPPORTED;
+  if (batch < 1 || batch > x->unet->batch_max()) return TH_ERR_ARG;
+  return cuda_status(x->unet->forward_from(in_dev, out_dev, batch, S(stream)));
+}
+
+th_status th_unet_backward(th_ctx* x, const float* gout_dev, float* grads_dev, int batch, void* stream) {
+  if (!x || !gout_dev || !grads_dev) return TH_ERR_ARG;
+  if (!x->unet) return TH_ERR_UNSUPPORTED;
+  if (batch < 1 || batch > x->unet->batch_max()) return TH_ERR_ARG;
+  return cuda_status(x->unet->backward_to(gout_dev, grads_dev, batch, S(stream)));
+}
+
+th_status th_unet_train_step(th_ctx* x, const double* rc_dev, const double* uc_dev, int batch, double lr,
+                             double* loss, void* stream) {
+  if (!x || !rc_dev || !uc_dev || !(lr > 0)) return TH_ERR_ARG;
+  if (!x->unet) return TH_ERR_UNSUPPORTED;
+  if (batch < 1 || batch > x->unet->batch_max()) return TH_ERR_ARG;
+  return cuda_status(x->unet->train_step(reinterpret_cast<const double2*>(rc_dev),
+                                         reinterpret_cast<const double2*>(uc_dev), batch, lr, loss, S(stream)));
+}
+
+th_status th_unet_correct(th_ctx* x, const double* rc_dev, double* uc_dev, int nrhs, void* stream) {
+  if (!x || !rc_dev || !uc_dev || nrhs < 1) return TH_ERR_ARG;
+  if (!x->unet) return TH_ERR_UNSUPPORTED;
+  x->launches += x->unet->launches_per_forward() * ((nrhs + x->unet->batch_max() - 1) / x->unet->batch_max());
+  return cuda_status(x->unet->correct<double2>(reinterpret_cast<const double2*>(rc_dev),
+                                               reinterpret_cast<double2*>(uc_dev), x->g.Nc, nrhs, S(stream)));
+}
+
+th_status th_set_coarse(th_ctx* x, int mode, int plain_iters) {
+  if (!x || mode < 0 || mode > 2 || plain_iters < 0) return TH_ERR_ARG;
+  if (mode == 1 && !x->unet) return TH_ERR_UNSUPPORTED;
+  x->coarse_mode = mode;
+  x->plain_iters = plain_iters;
+  ++x->epoch;
+  return TH_OK;
+}
+
 th_status th_cycle_host(th_ctx* x, const double* f_host, double* u_host, int nrhs, void* stream) {
   th_status st = check_nrhs(x, nrhs);
   if (st != TH_OK) return st;
@@ -1285,6 +1400,22 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
   std::vector<double2> yv;
   int it = 0;
   th_status result = TH_OK;
+  // learned corrector: fall back to the direct coarse solve once the iteration
+  // count reaches 1.5 x the plain count (restart from the current iterate)
+  const int saved_mode = x->coarse_mode;
+  const int limit = (saved_mode == 1 && x->plain_iters > 0) ? (int)std::ceil(1.5 * x->plain_iters) : INT32_MAX;
+  int fallbacks = 0;
+  bool switch_now = false;
+  struct Restore {
+    th_ctx* x;
+    int mode;
+    ~Restore() {
+      if (x->coarse_mode != mode) {
+        x->coarse_mode = mode;
+        ++x->epoch;
+      }
+    }
+  } restore{x, saved_mode};
   for (;;) {
     // r = f - A x  -> V_0
     if ((st = fine_apply<double>(*x, TH_OP_A, u2, f2, x->Vk, nrhs, s)) != TH_OK) return st;
@@ -1373,6 +1504,10 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
         }
       }
       if (!any || it >= x->prm.maxit) break;
+      if (x->coarse_mode == 1 && it >= limit) {
+        switch_now = true;
+        break;
+      }
     }
     // x += Z y per right-hand side (y = 0 beyond its own last step)
     yv.assign((size_t)nrhs * jdone, make_double2(0, 0));
@@ -1395,6 +1530,12 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
     x->launches += 1;
     TH_CU(th::launch_maxpy(x->Zk, vstride, x->ybuf, jdone, u2, N, jdone, nrhs, 1.0, s));
     TH_CU(cudaStreamSynchronize(s));
+    if (switch_now) {
+      switch_now = false;
+      x->coarse_mode = 0;
+      ++x->epoch;
+      ++fallbacks;
+    }
   }
   // final true residuals
   if ((st = fine_apply<double>(*x, TH_OP_A, u2, f2, x->w, nrhs, s)) != TH_OK) return st;
@@ -1414,6 +1555,7 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
     info->converged = nconv;
     info->relres_max = rmax;
     for (int r = 0; r < nrhs && r < 64; ++r) info->iters_per_rhs[r] = its[r];
+    info->fallbacks = fallbacks;
     info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return result;

@@ -142,3 +142,32 @@ def workload(name: str):
         return dict(name=name, dim=2, n=n, p=p, k=k, eps=eps, bc="robin",
                     f=random_sources(n, p, 2, 64, seed=100), alpha_s=0.5, l_dd=2)
     raise KeyError(name)
+
+
+def he_normal(shapes, seed: int) -> np.ndarray:
+    """Initial parameters of the learned coarse corrector: for each (name, shape)
+    in order, weights (names ending in ".w") drawn N(0, 2 / fan_in) with fan_in the
+    product of the trailing dimensions, biases zero; flattened to one float32 array."""
+    r = rng(seed)
+    out = []
+    for name, shape in shapes:
+        n = int(np.prod(shape))
+        if name.endswith(".w"):
+            fan_in = int(np.prod(shape[1:]))
+            out.append(r.standard_normal(n) * np.sqrt(2.0 / fan_in))
+        else:
+            out.append(np.zeros(n))
+    return np.concatenate(out).astype(np.float32)
+
+
+def smooth_coarse_noise(m: int, count: int, seed: int, passes: int = 4) -> np.ndarray:
+    """Complex white noise on an m x m node grid, averaged `passes` times with its
+    4 neighbours (zero outside): smooth random coarse residuals, [count, m*m]."""
+    r = rng(seed)
+    z = r.standard_normal((count, m, m)) + 1j * r.standard_normal((count, m, m))
+    for _ in range(passes):
+        zp = np.zeros((count, m + 2, m + 2), dtype=complex)
+        zp[:, 1:-1, 1:-1] = z
+        z = (zp[:, 1:-1, 1:-1] * 2 + zp[:, :-2, 1:-1] + zp[:, 2:, 1:-1] + zp[:, 1:-1, :-2] + zp[:, 1:-1, 2:]) / 6.0
+    return z.reshape(count, m * m)
+
