@@ -36,10 +36,11 @@ if ROOT not in sys.path:
 METRIC = "fine-level two-grid cycle GDOF/s and time-to-1e-8 residual vs plain FP64 form"
 WORKLOAD = "square40_q4_n100"
 HBM_FALLBACK_GBS = 6800.0
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_dd_apply (BF16 rows,
-# 1 rhs) launch on this workload, from the ncu capture summarised in
-# profiles/k_dd_apply_bf16_square40_q4_n100.md; None once the kernel changes.
-DD_TRAFFIC_BYTES = {0: 241.1e6, 1: None}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32-cycle
+# subdomain kernel (BF16 rows, 1 rhs) on this workload, by kernel variant: an
+# ncu capture of two launches of this script's timed region (variant 1, the
+# streamed kernel); None for a variant without a current capture.
+DD_TRAFFIC_BYTES = {0: None, 1: 240.4e6}
 
 
 def parse():
@@ -51,6 +52,14 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cycles", type=int, default=15, help="oracle cycles in the CPU-baseline sample")
+    ap.add_argument("--batch-rhs", type=int, default=64, help="right-hand sides of the batched section (0: skip)")
+    ap.add_argument("--dd-variant", choices=["auto", "0", "1"], default="auto",
+                    help="FP32 subdomain kernel: auto (set-up autotuner), 0 k_dd_apply, 1 k_dd_stream "
+                         "(pin it when the same command runs under a profiler, whose serialised launches "
+                         "change the autotuner's timings)")
+    ap.add_argument("--fine-variant", choices=["auto", "0", "1"], default="auto",
+                    help="FP32 and FP64 fine-apply tile variant: auto, 0 (large tiles), 1 (small tiles)")
+    ap.add_argument("--learned-steps", type=int, default=400, help="training steps of the learned section (0: skip)")
     return ap.parse_args()
 
 
@@ -187,6 +196,11 @@ def run_native(args):
     S = th.TwoGridSolver(n, p, w["k"], w["eps"], alpha_s=w["alpha_s"], l_dd=w["l_dd"], prec="bf16",
                          extra_prec=("fp64",), restart=30, maxit=300, tol=1e-8, nrhs_max=1, device=dev)
     setup_s = time.time() - t0
+    if args.dd_variant != "auto":
+        S.set_variant("dd", "fp32", int(args.dd_variant))
+    if args.fine_variant != "auto":
+        S.set_variant("fine", "fp32", int(args.fine_variant))
+        S.set_variant("fine", "fp64", int(args.fine_variant))
     N = S.N
     f = torch.from_numpy(np.ascontiguousarray(w["f"] if w["f"].ndim == 1 else w["f"][0])).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -207,10 +221,13 @@ def run_native(args):
             clocks.start()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        tag = f"cycle_{prec}_{'graph' if graph else 'launches'}{'_prof' if profile else ''}"
+        torch.cuda.nvtx.range_push(tag)   # ncu --nvtx-include "<tag>/" selects this region
         e0.record(stream)
         for _ in range(steps):
             step(f, u)
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize(dev)
         barrier(world)
         torch.cuda.synchronize(dev)
@@ -321,6 +338,12 @@ def run_native(args):
         "gpu_launches": int(launches),
         "clocks": ck,
     }
+    S.close()
+    del S
+    if args.batch_rhs > 0:
+        line["batched"] = batched_section(args, w, dev, world)
+    if args.learned_steps > 0:
+        line["learned"] = learned_section(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_cycles)
     if rank == 0:
@@ -329,6 +352,141 @@ def run_native(args):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# many sources at once, and the learned coarse corrector
+# ----------------------------------------------------------------------------
+def batched_section(args, w, dev, world):
+    """nrhs seeded point sources on the same workload in one graph-replayed cycle:
+    the subdomain products run on the tensor cores (k_dd_umma), the coarse solve
+    on tiles of right-hand sides."""
+    import numpy as np
+    import torch
+
+    import paper_2509_17494_gb300 as th
+    import synth
+
+    nr = args.batch_rhs
+    S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=w["alpha_s"], l_dd=w["l_dd"], prec="bf16",
+                         restart=30, maxit=300, tol=1e-8, nrhs_max=nr, device=dev)
+    F = torch.from_numpy(np.ascontiguousarray(synth.random_sources(w["n"], w["p"], 2, nr, 100))).to(dev)
+    U = torch.zeros_like(F)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        S.cycle_graph(F, U)
+    torch.cuda.synchronize(dev)
+    steps = max(3, args.steps // 2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("batched_cycle")
+    e0.record(stream)
+    for _ in range(steps):
+        S.cycle_graph(F, U)
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    ms = max_over_ranks(ms, world, dev)
+    S.profile(True)
+    for _ in range(3):
+        S.cycle(F, U)
+    torch.cuda.synchronize(dev)
+    prof = S.profile_read()
+    S.profile(False)
+    dd_ms, dd_cnt = prof["dd"]
+    dd_avg = dd_ms / max(dd_cnt, 1)
+    alg_bytes, _ = dd_algorithmic_bytes(w["n"], w["p"], w["l_dd"], 4, 8)
+    NR, NC = 81, 289
+    nsub = (w["n"] // w["l_dd"]) ** 2
+    flops = 8.0 * NR * NC * nsub * nr
+    _, info = S.solve(F)
+    hbm, src = peaks()
+    out = {"nrhs": nr, "sources": "seeded Gaussian point sources (synth.random_sources, seed 100)",
+           "value": round(S.N * nr * world / (ms * 1e-3) / 1e9, 4), "unit": "GDOF/s", "ms_per_cycle": round(ms, 4),
+           "time_to_tol_ms": round(info["ms_total"], 2), "iters": info["iters"], "relres_max": info["relres_max"],
+           "dd_tensor_core": {"kernel": "k_dd_umma (tcgen05, BF16 x BF16 -> FP32 in tensor memory)",
+                              "avg_launch_ms": round(dd_avg, 5),
+                              "achieved_tflops": round(flops / (dd_avg * 1e-3) / 1e12, 1),
+                              "achieved_gbs": round(alg_bytes / (dd_avg * 1e-3) / 1e9, 1),
+                              "hbm_peak_gbs": hbm, "peak_source": src},
+           "per_kernel_ms_per_cycle": {k: round(v[0] / 3, 4) for k, v in prof.items() if v[1] > 0}}
+    S.close()
+    return out
+
+
+def learned_section(args, dev):
+    """The learned coarse corrector on the 25 x 25 Q4 workload: trained on the GPU
+    (own kernels) for a few seconds, then FGMRES iterations with the direct
+    coarse solve, with no coarse correction, and with the corrector (alone and
+    with the fallback to the direct solve at 1.5x the plain count)."""
+    import numpy as np
+    import torch
+
+    import paper_2509_17494_gb300 as th
+    import synth
+
+    w = synth.workload("square10_q4_n25")
+    S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=0.5, l_dd=2, prec="bf16", extra_prec=("fp64",),
+                         nrhs_max=8, restart=40, maxit=400, device=dev)
+    levels, base = 4, 16
+    S.unet_init(synth.he_normal(th.unet_param_shapes(levels, base), 77), levels=levels, base=base, batch_max=8)
+    m = S.n * S.p // 2 + 1
+
+    def pairs(count, seed):
+        half = count // 2
+        f = torch.from_numpy(synth.random_complex((half, S.N), seed)).to(dev)
+        S.set_precision("fp64")
+        u = torch.zeros_like(f)
+        S.smooth(f, u)
+        rc1 = S.restrict(S.residual(f, u))
+        rc2 = torch.from_numpy(synth.smooth_coarse_noise(m, count - half, seed + 1)).to(dev)
+        rc = torch.cat([rc1, rc2]).contiguous()
+        uc = S.coarse_solve(rc)
+        S.set_precision("bf16")
+        return rc, uc
+
+    t0 = time.time()
+    losses = []
+    for it in range(args.learned_steps):
+        if it % 5 == 0:
+            rc, uc = pairs(8, 1000 + it)
+        losses.append(S.unet_train_step(rc, uc, lr=2e-3 if it < 0.7 * args.learned_steps else 5e-4))
+    torch.cuda.synchronize(dev)
+    train_s = time.time() - t0
+    rc, uc = pairs(8, 99999)
+    uh = S.unet_correct(rc)
+    held = float((torch.linalg.vector_norm(uh - uc, dim=1) / torch.linalg.vector_norm(uc, dim=1)).mean())
+    f = torch.from_numpy(np.ascontiguousarray(w["f"])).to(dev)
+    res = {}
+    S.set_coarse("direct")
+    res["direct"] = S.solve(f)[1]
+    S.set_coarse("none")
+    res["none"] = S.solve(f, check=False)[1]
+    S.set_coarse("learned", 0)
+    res["learned"] = S.solve(f, check=False)[1]
+    S.set_coarse("learned", res["direct"]["iters"])
+    res["learned_with_fallback"] = S.solve(f, check=False)[1]
+    S.set_coarse("direct")
+    r1 = rc[:1].contiguous()
+    for _ in range(3):
+        S.unet_correct(r1)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        S.unet_correct(r1)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    out = {"workload": "square10_q4_n25", "network": f"U-Net {levels} levels, base {base} channels, BF16",
+           "params": th.unet_param_count(levels, base), "train_steps": args.learned_steps,
+           "train_s": round(train_s, 2), "loss_first10": round(float(np.mean(losses[:10])), 4),
+           "loss_last10": round(float(np.mean(losses[-10:])), 4), "heldout_relerr": round(held, 4),
+           "correct_ms_1rhs": round(e0.elapsed_time(e1) / 20, 4),
+           "iters": {k: v["iters"] for k, v in res.items()},
+           "converged": {k: v["converged"] for k, v in res.items()},
+           "fallbacks": res["learned_with_fallback"]["fallbacks"]}
+    S.close()
+    return out
 
 
 # ----------------------------------------------------------------------------
