@@ -115,10 +115,143 @@ def coarse_cell_fields(k_cell: np.ndarray, eps_cell: np.ndarray, p: int):
     return kc, ec
 
 
+# ----------------------------------------------------------------------------
+# Three dimensions: a fitted 27-point stencil.  The paper only cites a 3-D
+# dispersion-minimising scheme; this one is the project's own construction on
+# the pattern of Eq. P_QSFEM (a reading, not the cited scheme):
+#   sigma_P(xi) = P0 + 2 P1 sum_a cos xi_a + 4 P2 sum_{a<b} cos xi_a cos xi_b
+#                 + 8 P3 cos xi_1 cos xi_2 cos xi_3,
+# P0 = 8 and P1, P2, P3 chosen so that sigma_P vanishes at |xi| = eta along the
+# three directions DIRS3 (the 2-D construction's exact zeros at pi/16 and
+# 3 pi/16 are the midpoints of the halves of the symmetry-reduced arc [0, pi/4];
+# here the directions are the images of the interior 3-point rule
+# (2/3, 1/6, 1/6) of the symmetry-reduced spherical triangle with corners
+# (0,0,1), (0,1,1)/sqrt2, (1,1,1)/sqrt3, normalised).  N = -eta^2 / sigma_P(0)
+# as in Eq. scaling_factor_QSFEM.  The operator is h_c N P (the 3-D finite
+# element forms scale with h), minus i eps h_c^3 times the Q1 mass and minus
+# i k h_c^2 times the Q1 face mass on absorbing faces; per coarse cell the pair
+# weights are N P0/8, N P1/4, N P2/2, N P3 by the number of coordinates in
+# which the two vertices differ.
+# ----------------------------------------------------------------------------
+
+def _dirs3():
+    V = np.array([[0.0, 0.0, 1.0], [0.0, 1.0, 1.0] / np.sqrt(2.0), [1.0, 1.0, 1.0] / np.sqrt(3.0)])
+    out = []
+    for w in ([2 / 3, 1 / 6, 1 / 6], [1 / 6, 2 / 3, 1 / 6], [1 / 6, 1 / 6, 2 / 3]):
+        d = np.asarray(w) @ V
+        out.append(d / np.linalg.norm(d))
+    return np.array(out)
+
+
+DIRS3 = _dirs3()
+
+
+def _stencil27_scalar(eta: float):
+    """(P0, P1, P2, P3, N) at one eta: the three zero conditions solved in 50 digits."""
+    if _mp is not None:
+        with _mp.workdps(50):
+            e = _mp.mpf(eta)
+            rows, rhs = [], []
+            for d in DIRS3:
+                c = [_mp.cos(e * _mp.mpf(float(x))) for x in d]
+                rows.append([2 * (c[0] + c[1] + c[2]), 4 * (c[0] * c[1] + c[0] * c[2] + c[1] * c[2]),
+                             8 * c[0] * c[1] * c[2]])
+                rhs.append(-8)
+            sol = _mp.lu_solve(_mp.matrix(rows), _mp.matrix(rhs))
+            P1, P2, P3 = sol[0], sol[1], sol[2]
+            s0 = 8 + 6 * P1 + 12 * P2 + 8 * P3
+            return 8.0, float(P1), float(P2), float(P3), float(-e * e / s0)
+    e = np.longdouble(eta)
+    rows, rhs = [], []
+    for d in DIRS3:
+        c = np.cos(e * d.astype(np.longdouble))
+        rows.append([2 * c.sum(), 4 * (c[0] * c[1] + c[0] * c[2] + c[1] * c[2]), 8 * c.prod()])
+        rhs.append(-8.0)
+    P1, P2, P3 = np.linalg.solve(np.array(rows, dtype=float), np.array(rhs))
+    return 8.0, P1, P2, P3, -eta * eta / (8 + 6 * P1 + 12 * P2 + 8 * P3)
+
+
+@functools.lru_cache(maxsize=1 << 16)
+def _stencil27_cached(eta: float):
+    return _stencil27_scalar(eta)
+
+
+def stencil27(eta: float):
+    """(P0, P1, P2, P3, N) of the fitted 27-point scheme at eta."""
+    return _stencil27_cached(float(eta))
+
+
+def symbol27(eta, xi):
+    """N sigma_P(xi) of the fitted 27-point scheme (xi: 3 normalised wave-vector components)."""
+    P0, P1, P2, P3, N = stencil27(eta)
+    c = np.cos(np.asarray(xi, dtype=float))
+    return N * (P0 + 2 * P1 * c.sum() + 4 * P2 * (c[0] * c[1] + c[0] * c[2] + c[1] * c[2]) + 8 * P3 * c.prod())
+
+
+def cell_q27(eta):
+    """(q_0, q_1, q_2, q_3) = (N P0/8, N P1/4, N P2/2, N P3) for one coarse cell."""
+    P0, P1, P2, P3, N = stencil27(eta)
+    return N * P0 / 8.0, N * P1 / 4.0, N * P2 / 2.0, N * P3
+
+
+def assemble_coarse3(n: int, p: int, k_cell: np.ndarray, eps_cell: np.ndarray,
+                     robin_sides=(), periodic: bool = False) -> sp.csr_matrix:
+    """A_q on the (n p/2)^3 coarse cells with spacing h_c = 2/(n p)  (3-D, fitted 27-point)."""
+    nc = n * p // 2
+    hc = 1.0 / nc
+    kc, ec = coarse_cell_fields(k_cell, eps_cell, p)
+    m = nc + (0 if periodic else 1)
+    Mq = np.array([[1.0 / 3.0, 1.0 / 6.0], [1.0 / 6.0, 1.0 / 3.0]])
+    verts = [(a, b, c) for a in (0, 1) for b in (0, 1) for c in (0, 1)]
+    rows, cols, vals = [], [], []
+    gid = lambda z, y, x: ((z % m) * m + (y % m)) * m + (x % m)
+    for cz in range(nc):
+        for cy in range(nc):
+            for cx in range(nc):
+                q = cell_q27(hc * kc[cz, cy, cx])
+                for va in verts:
+                    ga = gid(cz + va[0], cy + va[1], cx + va[2])
+                    for vb in verts:
+                        gb = gid(cz + vb[0], cy + vb[1], cx + vb[2])
+                        nd = sum(int(va[i] != vb[i]) for i in range(3))
+                        mass = hc ** 3 * Mq[va[0], vb[0]] * Mq[va[1], vb[1]] * Mq[va[2], vb[2]]
+                        rows.append(ga)
+                        cols.append(gb)
+                        vals.append(hc * q[nd] - 1j * ec[cz, cy, cx] * mass)
+    for (axis, end) in robin_sides:
+        j = 0 if end == 0 else 1
+        c_axis = 0 if end == 0 else nc - 1
+        for c1 in range(nc):
+            for c2 in range(nc):
+                cell = [0, 0, 0]
+                others = [a for a in range(3) if a != axis]
+                cell[axis] = c_axis
+                cell[others[0]], cell[others[1]] = c1, c2
+                kk = kc[tuple(cell)]
+                face = []
+                for a in (0, 1):
+                    for b in (0, 1):
+                        v = list(cell)
+                        v[axis] += j
+                        v[others[0]] += a
+                        v[others[1]] += b
+                        face.append((gid(*v), a, b))
+                for (ga, a1, b1) in face:
+                    for (gb, a2, b2) in face:
+                        rows.append(ga)
+                        cols.append(gb)
+                        vals.append(-1j * kk * hc * hc * Mq[a1, a2] * Mq[b1, b2])
+    A = sp.coo_matrix((np.array(vals), (np.array(rows), np.array(cols))), shape=(m ** 3, m ** 3)).tocsr()
+    A.sum_duplicates()
+    return A
+
+
 def assemble_coarse(n: int, p: int, k_cell: np.ndarray, eps_cell: np.ndarray,
                     robin_sides=(), periodic: bool = False) -> sp.csr_matrix:
-    """A_q on the (n p/2)^2 coarse cells with spacing h_c = 2/(n p)  (2-D)."""
-    assert k_cell.ndim == 2, "the 9-point scheme is two-dimensional"
+    """A_q on the (n p/2)^d coarse cells with spacing h_c = 2/(n p)."""
+    if k_cell.ndim == 3:
+        return assemble_coarse3(n, p, k_cell, eps_cell, robin_sides, periodic)
+    assert k_cell.ndim == 2, "the coarse schemes are two- or three-dimensional"
     nc = n * p // 2
     hc = 1.0 / nc
     kc, ec = coarse_cell_fields(k_cell, eps_cell, p)

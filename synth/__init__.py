@@ -141,6 +141,18 @@ def workload(name: str):
         eps = absorbing_layer(n, 2, p, k, 10.0)
         return dict(name=name, dim=2, n=n, p=p, k=k, eps=eps, bc="robin",
                     f=random_sources(n, p, 2, 64, seed=100), alpha_s=0.5, l_dd=2)
+    if name == "cube10_q2_n40":         # 3-D, 10 wavelengths, Q2, 40^3 cells, 81^3 dofs, 8 sources
+        n, p, W = 40, 2, 10.0
+        k = random_wavenumber(n, 3, W, seed=1)
+        eps = absorbing_layer(n, 3, p, k, 10.0)
+        return dict(name=name, dim=3, n=n, p=p, k=k, eps=eps, bc="robin",
+                    f=random_sources(n, p, 3, 8, seed=100, margin_dofs=12), alpha_s=0.5, l_dd=2)
+    if name == "cube2_q2_n8":           # small 3-D case: 2 wavelengths, Q2, 8^3 cells, 17^3 dofs
+        n, p, W = 8, 2, 2.0
+        k = random_wavenumber(n, 3, W, seed=3)
+        eps = absorbing_layer(n, 3, p, k, 3.0)
+        return dict(name=name, dim=3, n=n, p=p, k=k, eps=eps, bc="robin",
+                    f=gaussian_source(n, p, 3), alpha_s=0.5, l_dd=2)
     raise KeyError(name)
 
 
