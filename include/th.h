@@ -77,10 +77,11 @@ enum {
 };
 
 typedef struct {
-  int dim;      /* 2 */
+  int dim;      /* 2 (unit square) or 3 (unit cube; element order 2 only) */
   int n;        /* cells per direction, >= 1 */
-  int p;        /* element order: 2, 4, 6 or 8 */
-  int bc[4];    /* TH_BC_* per side: x low, x high, y low, y high */
+  int p;        /* element order: 2, 4, 6 or 8 (2-D); 2 (3-D) */
+  int bc[6];    /* TH_BC_* per side: x low, x high, y low, y high, z low, z high
+                   (the z entries are ignored in 2-D) */
 } th_mesh;
 
 typedef struct {
@@ -363,7 +364,16 @@ th_status th_host_qsfem_cell(double k, double eps, double hc, double* out);
  * block order; out receives rows x cols complex values (interleaved FP64),
  * row r = U-box dof r (lexicographic in the U box), column c = Omega-box dof
  * c, scaled by 1/L_j, where the boxes are given as
- * box[8] = (ox, oy, wx, wy, ux, uy, vx, vy) in global dof coordinates. */
+ * box[12] = (ox, oy, wx, wy, ux, uy, vx, vy, oz, wz, uz, vz) in global dof
+ * coordinates (Omega origin and widths, U origin and widths; in 2-D oz = uz
+ * = 0 and wz = vz = 1).  out receives Lu^d x Lw^d complex values. */
+/* The four pair weights of one coarse cell of the 3-D coarse operator (the
+ * project's fitted 27-point scheme, the 3-D counterpart of Eq. P_QSFEM and
+ * Eq. element_wise_qsfem): out[2 i], out[2 i + 1] = Re, Im of
+ * h_c N P_i w_i - i eps h_c^3 (1/3)^(3-i) (1/6)^i, i = number of coordinates
+ * in which the two vertices differ, w = (1/8, 1/4, 1/2, 1).  Host only. */
+th_status th_host_qsfem27_cell(double k, double eps, double hc, double* out);
+
 th_status th_host_inverse_rows(const th_mesh* mesh, const double* k_host, const double* eps_host,
                                const th_params* prm, int sub, int* box, double* out,
                                size_t out_len);

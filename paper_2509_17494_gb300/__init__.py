@@ -26,7 +26,7 @@ _LIB = None
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
 OPS = {"A": 0, "As": 1, "Aq": 2}
 BC = {"neumann": 0, "robin": 1, "dirichlet": 2}
-SIDES = ("xlo", "xhi", "ylo", "yhi")
+SIDES = ("xlo", "xhi", "ylo", "yhi", "zlo", "zhi")
 
 
 class ThError(RuntimeError):
@@ -36,7 +36,7 @@ class ThError(RuntimeError):
 
 
 class Mesh(ctypes.Structure):
-    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("p", ctypes.c_int), ("bc", ctypes.c_int * 4)]
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("p", ctypes.c_int), ("bc", ctypes.c_int * 6)]
 
 
 class Params(ctypes.Structure):
@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
         "th_profile_read": ([P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)], I),
         "th_host_reference_1d": ([I, P, P, P], I),
         "th_host_qsfem_cell": ([D, D, D, P], I),
+        "th_host_qsfem27_cell": ([D, D, D, P], I),
         "th_host_inverse_rows": ([ctypes.POINTER(Mesh), P, P, ctypes.POINTER(Params), I, P, P,
                                   ctypes.c_size_t], I),
     }
@@ -117,11 +118,11 @@ def _check(code, what):
         raise ThError(code, what)
 
 
-def _mesh(n, p, bc):
+def _mesh(n, p, bc, dim=2):
     m = Mesh()
-    m.dim, m.n, m.p = 2, int(n), int(p)
+    m.dim, m.n, m.p = int(dim), int(n), int(p)
     if isinstance(bc, str):
-        vals = [BC[bc]] * 4
+        vals = [BC[bc]] * 6
     else:
         vals = [BC[bc.get(s, "neumann")] for s in SIDES]
     for i, v in enumerate(vals):
@@ -165,7 +166,8 @@ def unet_param_count(levels=4, base=16) -> int:
 
 def workspace_size(n, p, bc="robin", **params) -> int:
     out = ctypes.c_size_t(0)
-    m, q = _mesh(n, p, bc), _params(**params)
+    dim = params.pop("dim", 2)
+    m, q = _mesh(n, p, bc, dim), _params(**params)
     _check(lib().th_workspace_size(ctypes.byref(m), ctypes.byref(q), ctypes.byref(out)), "th_workspace_size")
     return out.value
 
@@ -187,9 +189,17 @@ def host_qsfem_cell(k, eps, hc):
     return out[0::2] + 1j * out[1::2]
 
 
+def host_qsfem27_cell(k, eps, hc):
+    """The 4 complex pair weights of one coarse cell of the 3-D coarse operator."""
+    out = np.zeros(8)
+    _check(lib().th_host_qsfem27_cell(float(k), float(eps), float(hc), out.ctypes.data), "th_host_qsfem27_cell")
+    return out[0::2] + 1j * out[1::2]
+
+
 def host_inverse_rows(n, p, k_cell, eps_cell, sub, bc="robin", **params):
     """(box, W) of subdomain `sub` as the set-up computes it on the host."""
-    m, q = _mesh(n, p, bc), _params(**params)
+    dim = params.pop("dim", 2)
+    m, q = _mesh(n, p, bc, dim), _params(**params)
     k, kp = _f64(k_cell)
     e, ep = _f64(eps_cell if eps_cell is not None else np.zeros_like(k))
     l_dd = max(1, min(int(params.get("l_dd", 2)), n))
@@ -198,11 +208,11 @@ def host_inverse_rows(n, p, k_cell, eps_cell, sub, bc="robin", **params):
     lmax = -(-n // nb)
     Lu = lmax * p + 1
     Lw = min(lmax + 2, n) * p + 1
-    out = np.zeros(2 * Lu * Lu * Lw * Lw)
-    box = (ctypes.c_int * 8)()
+    out = np.zeros(2 * Lu ** dim * Lw ** dim)
+    box = (ctypes.c_int * 12)()
     _check(lib().th_host_inverse_rows(ctypes.byref(m), kp, ep, ctypes.byref(q), int(sub), box, out.ctypes.data,
                                       out.size), "th_host_inverse_rows")
-    W = (out[0::2] + 1j * out[1::2]).reshape(Lu * Lu, Lw * Lw)
+    W = (out[0::2] + 1j * out[1::2]).reshape(Lu ** dim, Lw ** dim)
     return list(box), W, Lu, Lw
 
 
@@ -211,7 +221,7 @@ class TwoGridSolver:
 
     def __init__(self, n, p, k_cell, eps_cell=None, bc="robin", alpha_s=0.5, l_dd=2, n_dd=1, n_s=1,
                  omega_c=1.0, prec="fp64", extra_prec=(), restart=30, maxit=200, tol=1e-8, nrhs_max=1,
-                 device=None):
+                 device=None, dim=None):
         import torch
 
         self.torch = torch
@@ -219,10 +229,12 @@ class TwoGridSolver:
             raise RuntimeError("TwoGridSolver needs a CUDA device (no CPU fallback)")
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.n, self.p = int(n), int(p)
-        self.N = (self.n * self.p + 1) ** 2
-        self.Nc = (self.n * self.p // 2 + 1) ** 2
+        kshape = np.shape(k_cell)
+        self.dim = int(dim) if dim is not None else (3 if len(kshape) == 3 else 2)
+        self.N = (self.n * self.p + 1) ** self.dim
+        self.Nc = (self.n * self.p // 2 + 1) ** self.dim
         self.nrhs_max = int(nrhs_max)
-        self._mesh = _mesh(n, p, bc)
+        self._mesh = _mesh(n, p, bc, self.dim)
         self._params = _params(alpha_s, l_dd, n_dd, n_s, omega_c, prec, extra_prec, restart, maxit, tol, nrhs_max)
         L = lib()
         nb = ctypes.c_size_t(0)

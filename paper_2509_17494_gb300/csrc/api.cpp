@@ -82,6 +82,9 @@ struct th_ctx {
   int nred = 0;  // (P - 1) mc separator unknowns
   double2 *Gp64 = nullptr, *LR64 = nullptr, *Si64 = nullptr, *rh64 = nullptr;
   float2 *Gp32 = nullptr, *LR32 = nullptr, *Si32 = nullptr, *rh32 = nullptr;
+  // 3-D coarse blocks (z-slices), sweep scratch and the fine apply's per-cell outputs
+  double2 *G3_64 = nullptr, *dn64 = nullptr, *up64 = nullptr, *tsw64 = nullptr, *ycell64 = nullptr;
+  float2 *G3_32 = nullptr, *dn32 = nullptr, *up32 = nullptr, *tsw32 = nullptr, *ycell32 = nullptr;
   // G_j transposed with rows padded to mcr, for the many-right-hand-side sweep (nrhs_max >= 2)
   int rpcm = 0, mcr = 0;
   double2* Gt64 = nullptr;
@@ -165,19 +168,23 @@ struct Prof {
 void carve_all(th_ctx& x, Carve& c) {
   const th::Geometry& g = x.g;
   const th_params& prm = x.prm;
-  const size_t n2 = (size_t)g.n * g.n;
+  const bool d3 = g.dim == 3;
+  const size_t n2 = (size_t)g.n * g.n * (d3 ? g.n : 1);  // cells
   const int nr = prm.nrhs_max;
   x.derr = c.take<int>(64);
   x.kc64 = c.take<double>(n2);
   x.ec64 = c.take<double>(n2);
-  x.box = c.take<int>((size_t)g.nsub * 8);
+  x.box = c.take<int>((size_t)g.nsub * th::kBox);
   x.ctab = c.take<int4>((size_t)g.m);
   x.pj0 = c.take<int>(g.m);
   x.pw64 = c.take<double>((size_t)g.m * (g.q + 1));
   x.ridx = c.take<int>((size_t)g.mc * x.rmax);
   x.rw64 = c.take<double>((size_t)g.mc * x.rmax);
-  x.ccell64 = c.take<double2>((size_t)g.nc * g.nc * 3);
-  x.crho64 = c.take<double2>((size_t)4 * g.nc);
+  const size_t ncell_c = d3 ? (size_t)g.nc * g.nc * g.nc * 4 : (size_t)g.nc * g.nc * 3;
+  const size_t nrho_c = d3 ? (size_t)6 * g.nc * g.nc : (size_t)4 * g.nc;
+  const size_t mb = (size_t)g.mc * g.mc;  // 3-D: nodes per z-slice
+  x.ccell64 = c.take<double2>(ncell_c);
+  x.crho64 = c.take<double2>(nrho_c);
   const size_t mm = (size_t)g.mc * g.mc;
   x.cl64 = c.take<double2>(mm);
   x.cd64 = c.take<double2>(mm);
@@ -188,11 +195,25 @@ void carve_all(th_ctx& x, Carve& c) {
     x.W[k] = has_prec(x.avail, k) ? (void*)c.take<uint4>((size_t)g.nsub * x.wchunks[k] * g.NR) : nullptr;
   }
   x.wscale16 = has_prec(x.avail, TH_PREC_FP16) ? c.take<float>(g.nsub) : nullptr;
-  x.Wu = (has_prec(x.avail, TH_PREC_BF16) && g.NR <= 128)
+  x.Wu = (!d3 && has_prec(x.avail, TH_PREC_BF16) && g.NR <= 128)
              ? c.take<unsigned char>((size_t)g.nsub * th::dd_umma_bytes_per_sub(g.NR, g.NC))
              : nullptr;
   const bool fp64 = has_prec(x.avail, TH_PREC_FP64);
-  x.G64 = fp64 ? c.take<double2>(mm * g.mc) : nullptr;
+  x.G64 = (fp64 && !d3) ? c.take<double2>(mm * g.mc) : nullptr;
+  if (d3) {
+    x.dn64 = c.take<double2>((size_t)g.mc * mb * 9);
+    x.up64 = c.take<double2>((size_t)g.mc * mb * 9);
+    x.G3_64 = fp64 ? c.take<double2>((size_t)g.mc * mb * mb) : nullptr;
+    x.tsw64 = c.take<double2>((size_t)nr * mb);
+    x.ycell64 = c.take<double2>((size_t)nr * n2 * 32);
+    if (x.mixed) {
+      x.dn32 = c.take<float2>((size_t)g.mc * mb * 9);
+      x.up32 = c.take<float2>((size_t)g.mc * mb * 9);
+      x.G3_32 = c.take<float2>((size_t)g.mc * mb * mb);
+      x.tsw32 = c.take<float2>((size_t)nr * mb);
+      x.ycell32 = c.take<float2>((size_t)nr * n2 * 32);
+    }
+  }
   const size_t blk = (size_t)g.mc * x.mcp;  // one padded dense block
   const int K = std::max(x.P - 1, 1);
   x.ca = c.take<int>(x.P);
@@ -200,7 +221,7 @@ void carve_all(th_ctx& x, Carve& c) {
   x.sep = c.take<int>(K);
   x.chunk_of = c.take<int>(g.mc);
   const size_t nred = std::max(x.nred, 1);
-  if (fp64) {
+  if (fp64 && !d3) {
     x.Gp64 = c.take<double2>(blk * g.mc);
     x.LR64 = c.take<double2>(2 * blk * g.mc);
     x.Si64 = c.take<double2>(nred * (nred + (nred & 1)));
@@ -221,16 +242,18 @@ void carve_all(th_ctx& x, Carve& c) {
     x.ec32 = c.take<float>(n2);
     x.pw32 = c.take<float>((size_t)g.m * (g.q + 1));
     x.rw32 = c.take<float>((size_t)g.mc * x.rmax);
-    x.ccell32 = c.take<float2>((size_t)g.nc * g.nc * 3);
-    x.crho32 = c.take<float2>((size_t)4 * g.nc);
+    x.ccell32 = c.take<float2>(ncell_c);
+    x.crho32 = c.take<float2>(nrho_c);
     x.cl32 = c.take<float2>(mm);
     x.cd32 = c.take<float2>(mm);
     x.cu32 = c.take<float2>(mm);
-    x.Gp32 = c.take<float2>(blk * g.mc);
-    x.LR32 = c.take<float2>(2 * blk * g.mc);
-    x.Si32 = c.take<float2>(nred * (nred + (nred & 1)));
-    x.rh32 = c.take<float2>(nred * nr);
-    if (nr >= 2) x.Gt32 = c.take<float2>(mm * x.mcr);
+    if (!d3) {
+      x.Gp32 = c.take<float2>(blk * g.mc);
+      x.LR32 = c.take<float2>(2 * blk * g.mc);
+      x.Si32 = c.take<float2>(nred * (nred + (nred & 1)));
+      x.rh32 = c.take<float2>(nred * nr);
+      if (nr >= 2) x.Gt32 = c.take<float2>(mm * x.mcr);
+    }
     x.f32 = c.take<float2>((size_t)nr * g.N);
     x.u32 = c.take<float2>((size_t)nr * g.N);
     x.r32 = c.take<float2>((size_t)nr * g.N);
@@ -262,7 +285,8 @@ th_status prepare(const th_mesh* mesh, const th_params* prm, th_ctx& x) {
   x.prm = *prm;
   th_status st = th::make_geometry(*mesh, *prm, x.g);
   if (st != TH_OK) return st;
-  if (x.g.mc > 1024) return TH_ERR_UNSUPPORTED;  // coarse kernels hold two coarse rows per thread
+  if (x.g.dim == 2 && x.g.mc > 1024) return TH_ERR_UNSUPPORTED;  // coarse kernels hold two coarse rows per thread
+  if (x.g.dim == 3 && (long long)x.g.mc * x.g.mc > 4096) return TH_ERR_UNSUPPORTED;  // z-slice blocks of mc^2 <= 4096
   x.avail = (prm->prec_mask & 0xFu) | (1u << prm->prec);
   x.active = prm->prec;
   x.mixed = (x.avail & ~1u) != 0;
@@ -274,7 +298,7 @@ th_status prepare(const th_mesh* mesh, const th_params* prm, th_ctx& x) {
   x.ref = ref;
   x.cluster = 8;
   x.rpc = (x.g.mc + x.cluster - 1) / x.cluster;
-  x.P = th::coarse_chunks(x.g.mc);
+  x.P = x.g.dim == 2 ? th::coarse_chunks(x.g.mc) : 1;
   x.mcp = x.g.mc + (x.g.mc & 1);
   x.rpcm = x.rpc + (x.rpc & 1);
   x.mcr = x.cluster * x.rpcm;
@@ -326,8 +350,45 @@ th::FineArgs<T> fine_args(const th_ctx& x, int op) {
 
 // y = OP u or y = f - OP u, in precision T, on nrhs right-hand sides
 template <typename T>
+th_status fine_apply3(th_ctx& x, int op, const typename th::Cx<T>::t* u, const typename th::Cx<T>::t* f,
+                      typename th::Cx<T>::t* y, int nrhs, cudaStream_t s) {
+  const th::Geometry& g = x.g;
+  th::Fine3Args<T> a{};
+  a.u = u;
+  a.f = f;
+  a.y = y;
+  a.residual = f ? 1 : 0;
+  a.N = g.N;
+  a.ncell = (long long)g.n * g.n * g.n;
+  a.n = g.n;
+  a.m = g.m;
+  a.robin = 0;
+  for (int s6 = 0; s6 < 6; ++s6) a.robin |= g.robin[s6] << s6;
+  a.h = (T)g.h;
+  a.alpha = (op == TH_OP_AS) ? (T)x.prm.alpha_s : (T)0;
+  for (int i = 0; i < 9; ++i) {
+    a.M[i] = (T)x.ref.M[i];
+    a.K[i] = (T)x.ref.K[i];
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    a.kc = x.kc64;
+    a.ec = x.ec64;
+    a.ycell = x.ycell64;
+  } else {
+    a.kc = x.kc32;
+    a.ec = x.ec32;
+    a.ycell = x.ycell32;
+  }
+  if (!a.ycell) return TH_ERR_UNSUPPORTED;
+  x.launches += 2;
+  Prof prof(x, TH_K_FINE, s);
+  return cuda_status(th::launch_fine3<T>(a, nrhs, s));
+}
+
+template <typename T>
 th_status fine_apply(th_ctx& x, int op, const typename th::Cx<T>::t* u, const typename th::Cx<T>::t* f,
                      typename th::Cx<T>::t* y, int nrhs, cudaStream_t s) {
+  if (x.g.dim == 3) return fine_apply3<T>(x, op, u, f, y, nrhs, s);
   th::FineArgs<T> a = fine_args<T>(x, op);
   a.u = u;
   a.f = f;
@@ -358,6 +419,11 @@ template <> struct PrecBufs<double> {
   static const double2* cu(th_ctx& x) { return x.cu64; }
   static const double2* cell(th_ctx& x) { return x.ccell64; }
   static const double2* rho(th_ctx& x) { return x.crho64; }
+  static const double2* G3(th_ctx& x) { return x.G3_64; }
+  static const double2* dn(th_ctx& x) { return x.dn64; }
+  static const double2* up(th_ctx& x) { return x.up64; }
+  static double2* tsw(th_ctx& x) { return x.tsw64; }
+  static double2* ycell(th_ctx& x) { return x.ycell64; }
 };
 template <> struct PrecBufs<float> {
   static float2* r(th_ctx& x) { return x.r32; }
@@ -378,6 +444,11 @@ template <> struct PrecBufs<float> {
   static const float2* cu(th_ctx& x) { return x.cu32; }
   static const float2* cell(th_ctx& x) { return x.ccell32; }
   static const float2* rho(th_ctx& x) { return x.crho32; }
+  static const float2* G3(th_ctx& x) { return x.G3_32; }
+  static const float2* dn(th_ctx& x) { return x.dn32; }
+  static const float2* up(th_ctx& x) { return x.up32; }
+  static float2* tsw(th_ctx& x) { return x.tsw32; }
+  static float2* ycell(th_ctx& x) { return x.ycell32; }
 };
 
 template <typename T>
@@ -442,6 +513,7 @@ th_status dd_combine(th_ctx& x, typename th::Cx<T>::t* u, int accumulate, int nr
   a.accumulate = accumulate;
   x.launches += 1;
   Prof prof(x, TH_K_COMBINE, s);
+  if (g.dim == 3) return cuda_status(th::launch_dd_combine3<T>(a, nrhs, s));
   return cuda_status(th::launch_dd_combine<T>(a, nrhs, s));
 }
 
@@ -491,6 +563,7 @@ th_status restrict_(th_ctx& x, const typename th::Cx<T>::t* r, typename th::Cx<T
   a.q = x.g.q;
   x.launches += 1;
   Prof prof(x, TH_K_RESTRICT, s);
+  if (x.g.dim == 3) return cuda_status(th::launch_restrict3<T>(a, nrhs, s));
   return cuda_status(th::launch_restrict<T>(a, nrhs, s));
 }
 
@@ -511,12 +584,35 @@ th_status prolong_(th_ctx& x, const typename th::Cx<T>::t* uc, typename th::Cx<T
   a.omega = omega;
   x.launches += 1;
   Prof prof(x, TH_K_PROLONG, s);
+  if (x.g.dim == 3) return cuda_status(th::launch_prolong3<T>(a, nrhs, s));
   return cuda_status(th::launch_prolong<T>(a, nrhs, s));
+}
+
+template <typename T>
+th_status coarse_solve3_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th::Cx<T>::t* uc, int nrhs,
+                         cudaStream_t s) {
+  using B = PrecBufs<T>;
+  th::Sweep3Args<T> a{};
+  a.b = rc;
+  a.x = uc;
+  a.t = B::tsw(x);
+  a.G = B::G3(x);
+  a.dn = B::dn(x);
+  a.up = B::up(x);
+  a.Nc = x.g.Nc;
+  a.mc = x.g.mc;
+  a.mb = x.g.mc * x.g.mc;
+  a.nrhs = nrhs;
+  if (!a.G || !a.t) return TH_ERR_UNSUPPORTED;
+  x.launches += 4 * x.g.mc - 2;
+  Prof prof(x, TH_K_COARSE_SOLVE, s);
+  return cuda_status(th::launch_sweep3<T>(a, s));
 }
 
 template <typename T>
 th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th::Cx<T>::t* uc, int nrhs,
                         cudaStream_t s) {
+  if (x.g.dim == 3) return coarse_solve3_<T>(x, rc, uc, nrhs, s);
   using B = PrecBufs<T>;
   th::CoarsePartArgs<T> a{};
   a.b = rc;
@@ -564,6 +660,7 @@ th_status coarse_apply_(th_ctx& x, const typename th::Cx<T>::t* in, typename th:
   a.mc = x.g.mc;
   x.launches += 1;
   Prof prof(x, TH_K_COARSE_APPLY, s);
+  if (x.g.dim == 3) return cuda_status(th::launch_coarse_apply3<T>(a, nrhs, s));
   return cuda_status(th::launch_coarse_apply<T>(a, nrhs, s));
 }
 
@@ -815,7 +912,8 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
   th_status st = prepare(mesh, prm, *x);
   if (st != TH_OK) return st;
   const th::Geometry& g = x->g;
-  const size_t n2 = (size_t)g.n * g.n;
+  const bool d3 = g.dim == 3;
+  const size_t n2 = (size_t)g.n * g.n * (d3 ? g.n : 1);  // cells
   x->k_host.assign(k_host, k_host + n2);
   for (size_t i = 0; i < n2; ++i) {
     if (!std::isfinite(k_host[i]) || k_host[i] <= 0.0) return TH_ERR_ARG;
@@ -839,9 +937,14 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
   th::TransferTables tt;
   th::transfer_tables(g, x->ref, tt);
   th::CoarseBlocks cb;
-  if ((st = th::coarse_setup(g, k_host, eps, cb)) != TH_OK) return st;
   th::CoarsePart cpart;
-  if ((st = th::coarse_partition(g, cb, x->P, cpart)) != TH_OK) return st;
+  th::CoarseBlocks3 cb3;
+  if (!d3) {
+    if ((st = th::coarse_setup(g, k_host, eps, cb)) != TH_OK) return st;
+    if ((st = th::coarse_partition(g, cb, x->P, cpart)) != TH_OK) return st;
+  } else {
+    if ((st = th::coarse_setup3(g, k_host, eps, cb3)) != TH_OK) return st;
+  }
   std::vector<cplx> Wh;
   if ((st = th::all_inverse_rows(g, x->ref, k_host, eps, x->prm.alpha_s, Wh)) != TH_OK) return st;
 
@@ -857,9 +960,15 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
   for (size_t i = 0; i < n2; ++i) { kf[i] = (float)k_host[i]; ef[i] = (float)eps[i]; }
   for (size_t i = 0; i < tt.pw.size(); ++i) pwf[i] = (float)tt.pw[i];
   for (size_t i = 0; i < tt.rw.size(); ++i) rwf[i] = (float)tt.rw[i];
-  std::vector<double2> rho64(4 * (size_t)g.nc);
-  for (int sd = 0; sd < 4; ++sd)
-    for (int t = 0; t < g.nc; ++t) rho64[(size_t)sd * g.nc + t] = make_double2(cb.rho[sd][t].real(), cb.rho[sd][t].imag());
+  std::vector<double2> rho64;
+  if (!d3) {
+    rho64.resize(4 * (size_t)g.nc);
+    for (int sd = 0; sd < 4; ++sd)
+      for (int t = 0; t < g.nc; ++t) rho64[(size_t)sd * g.nc + t] = make_double2(cb.rho[sd][t].real(), cb.rho[sd][t].imag());
+  } else {
+    rho64.resize(cb3.rho.size());
+    for (size_t i = 0; i < cb3.rho.size(); ++i) rho64[i] = make_double2(cb3.rho[i].real(), cb3.rho[i].imag());
+  }
   const size_t mm = (size_t)g.mc * g.mc;
   auto to2 = [](const std::vector<cplx>& v) {
     std::vector<double2> o(v.size());
@@ -871,7 +980,8 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].real(), (float)v[i].imag());
     return o;
   };
-  std::vector<double2> cell64 = to2(cb.cell), cl64 = to2(cb.cl), cd64 = to2(cb.cd), cu64 = to2(cb.cu);
+  std::vector<double2> cell64 = to2(d3 ? cb3.cell : cb.cell), cl64 = to2(cb.cl), cd64 = to2(cb.cd),
+                       cu64 = to2(cb.cu);
   if ((st = up(x->kc64, k_host, n2 * 8)) != TH_OK) return st;
   if ((st = up(x->ec64, eps, n2 * 8)) != TH_OK) return st;
   if ((st = up(x->box, g.box.data(), g.box.size() * 4)) != TH_OK) return st;
@@ -882,15 +992,17 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
   if ((st = up(x->rw64, tt.rw.data(), tt.rw.size() * 8)) != TH_OK) return st;
   if ((st = up(x->ccell64, cell64.data(), cell64.size() * 16)) != TH_OK) return st;
   if ((st = up(x->crho64, rho64.data(), rho64.size() * 16)) != TH_OK) return st;
-  if ((st = up(x->cl64, cl64.data(), mm * 16)) != TH_OK) return st;
-  if ((st = up(x->cd64, cd64.data(), mm * 16)) != TH_OK) return st;
-  if ((st = up(x->cu64, cu64.data(), mm * 16)) != TH_OK) return st;
+  if (!d3) {
+    if ((st = up(x->cl64, cl64.data(), mm * 16)) != TH_OK) return st;
+    if ((st = up(x->cd64, cd64.data(), mm * 16)) != TH_OK) return st;
+    if ((st = up(x->cu64, cu64.data(), mm * 16)) != TH_OK) return st;
+  }
   std::vector<double2> G64h;
   if (x->G64) {
     G64h = to2(cb.G);
     if ((st = up(x->G64, G64h.data(), G64h.size() * 16)) != TH_OK) return st;
   }
-  {
+  if (!d3) {
     std::vector<int> chunk_of(g.mc, -1);
     for (int c = 0; c < x->P; ++c)
       for (int j = cpart.ca[c]; j <= cpart.cb[c]; ++j) chunk_of[j] = c;
@@ -918,6 +1030,11 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     }
     return TH_OK;
   };
+  if (d3) {
+    if ((st = upload_c(x->G3_64, x->G3_32, cb3.G)) != TH_OK) return st;
+    if ((st = upload_c(x->dn64, x->dn32, cb3.dn)) != TH_OK) return st;
+    if ((st = upload_c(x->up64, x->up32, cb3.up)) != TH_OK) return st;
+  }
   if ((st = upload_c(x->Gp64, x->Gp32, cpart.G)) != TH_OK) return st;
   if (x->Gt64 || x->Gt32) {
     // G_j^T with rows padded to mcr: Gt[j][c][row] = G[j][row][c]
@@ -940,7 +1057,7 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
   }
   std::vector<float2> cell32, rho32, cl32, cd32, cu32;
   if (x->mixed) {
-    cell32 = to2f(cb.cell);
+    cell32 = to2f(d3 ? cb3.cell : cb.cell);
     cl32 = to2f(cb.cl);
     cd32 = to2f(cb.cd);
     cu32 = to2f(cb.cu);
@@ -952,9 +1069,11 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     if ((st = up(x->rw32, rwf.data(), rwf.size() * 4)) != TH_OK) return st;
     if ((st = up(x->ccell32, cell32.data(), cell32.size() * 8)) != TH_OK) return st;
     if ((st = up(x->crho32, rho32.data(), rho32.size() * 8)) != TH_OK) return st;
-    if ((st = up(x->cl32, cl32.data(), mm * 8)) != TH_OK) return st;
-    if ((st = up(x->cd32, cd32.data(), mm * 8)) != TH_OK) return st;
-    if ((st = up(x->cu32, cu32.data(), mm * 8)) != TH_OK) return st;
+    if (!d3) {
+      if ((st = up(x->cl32, cl32.data(), mm * 8)) != TH_OK) return st;
+      if ((st = up(x->cd32, cd32.data(), mm * 8)) != TH_OK) return st;
+      if ((st = up(x->cu32, cu32.data(), mm * 8)) != TH_OK) return st;
+    }
   }
   // inverse rows in the chunk-major layouts
   const size_t blk = (size_t)g.NR * g.NC;
@@ -1054,8 +1173,8 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     TH_CU(cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, dev));
     TH_CU(cudaMemsetAsync(x->derr, 0, 64 * sizeof(int), s));
   }
-  if ((st = tune_fine<double>(*x, s, x->tc64)) != TH_OK) return st;
-  if (x->mixed && (st = tune_fine<float>(*x, s, x->tc32)) != TH_OK) return st;
+  if (!d3 && (st = tune_fine<double>(*x, s, x->tc64)) != TH_OK) return st;  // the 3-D apply has one variant
+  if (!d3 && x->mixed && (st = tune_fine<float>(*x, s, x->tc32)) != TH_OK) return st;
   if (x->W[TH_PREC_FP64] && (st = tune_dd<double>(*x, TH_PREC_FP64, s, x->dds64)) != TH_OK) return st;
   if (x->mixed) {
     const int wk = (x->active != TH_PREC_FP64) ? x->active : (x->W[TH_PREC_BF16] ? TH_PREC_BF16 : TH_PREC_FP32);
@@ -1599,6 +1718,17 @@ th_status th_host_qsfem_cell(double k, double eps, double hc, double* out) {
   return TH_OK;
 }
 
+th_status th_host_qsfem27_cell(double k, double eps, double hc, double* out) {
+  if (!out || !(hc > 0) || !(k > 0) || !(eps >= 0)) return TH_ERR_ARG;
+  cplx d[4];
+  th::qsfem27_cell(k, eps, hc, d);
+  for (int i = 0; i < 4; ++i) {
+    out[2 * i] = d[i].real();
+    out[2 * i + 1] = d[i].imag();
+  }
+  return TH_OK;
+}
+
 th_status th_host_inverse_rows(const th_mesh* mesh, const double* k_host, const double* eps_host,
                                const th_params* prm, int sub, int* box, double* out, size_t out_len) {
   if (!mesh || !prm || !k_host || !box || !out) return TH_ERR_ARG;
@@ -1607,7 +1737,7 @@ th_status th_host_inverse_rows(const th_mesh* mesh, const double* k_host, const 
   if (st != TH_OK) return st;
   if (sub < 0 || sub >= g.nsub) return TH_ERR_ARG;
   if (out_len < (size_t)g.NR * g.NC * 2) return TH_ERR_NOMEM;
-  std::copy(&g.box[(size_t)sub * 8], &g.box[(size_t)sub * 8] + 8, box);
+  std::copy(&g.box[(size_t)sub * th::kBox], &g.box[(size_t)sub * th::kBox] + th::kBox, box);
   th::Ref1D ref = th::reference_1d(mesh->p);
   std::vector<cplx> o((size_t)g.NR * g.NC);
   if ((st = th::subdomain_inverse_rows(g, ref, k_host, eps_host, prm->alpha_s, sub, o.data())) != TH_OK) return st;

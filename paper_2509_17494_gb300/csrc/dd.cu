@@ -105,16 +105,18 @@ __global__ void __launch_bounds__(512) k_dd_apply(const DDArgs<T> a) {
   const int r0 = blockIdx.y * NRHS;
   const int nr = min(NRHS, a.nrhs - r0);
   for (int sub = blockIdx.x; sub < a.nsub; sub += gridDim.x) {
-    const int* bb = a.box + (size_t)sub * 8;
-    const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3];
+    const int* bb = a.box + (size_t)sub * 12;
+    const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3], oz = bb[8], wz = bb[9];
+    const int L2 = a.Lw * a.Lw;
     for (int i = tid; i < NRHS * XL; i += nth) {
       const int k = i / XL, c = i - k * XL;
-      const int cy = c / a.Lw, cx = c - cy * a.Lw;
+      const int cz = c / L2, cr = c - cz * L2;
+      const int cy = cr / a.Lw, cx = cr - cy * a.Lw;
       C v;
       v.x = 0;
       v.y = 0;
-      if (k < nr && c < a.NC && cx < wx && cy < wy)
-        v = a.r[(size_t)(r0 + k) * a.N + (size_t)(oy + cy) * a.m + (ox + cx)];
+      if (k < nr && c < a.NC && cx < wx && cy < wy && cz < wz)
+        v = a.r[(size_t)(r0 + k) * a.N + ((size_t)(oz + cz) * a.m + (oy + cy)) * a.m + (ox + cx)];
       xs[i] = v;
     }
     __syncthreads();
@@ -344,14 +346,16 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
   auto gather = [&](int i, int buf) {
     if (i < nmine) {
       const int sub = blockIdx.x + i * gridDim.x;
-      const int* bb = a.box + (size_t)sub * 8;
-      const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3];
+      const int* bb = a.box + (size_t)sub * 12;
+      const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3], oz = bb[8], wz = bb[9];
+      const int L2 = a.Lw * a.Lw;
       C* dst = xs + (size_t)buf * NRHS * XL;
       for (int idx = tid; idx < NRHS * XL; idx += nth) {
         const int k = idx / XL, c = idx - k * XL;
-        const int cy = c / a.Lw, cx = c - cy * a.Lw;
-        if (k < nr && c < a.NC && cx < wx && cy < wy) {
-          cp_async_c(dst + idx, a.r + (size_t)(r0 + k) * a.N + (size_t)(oy + cy) * a.m + (ox + cx));
+        const int cz = c / L2, cr = c - cz * L2;
+        const int cy = cr / a.Lw, cx = cr - cy * a.Lw;
+        if (k < nr && c < a.NC && cx < wx && cy < wy && cz < wz) {
+          cp_async_c(dst + idx, a.r + (size_t)(r0 + k) * a.N + ((size_t)(oz + cz) * a.m + (oy + cy)) * a.m + (ox + cx));
         } else {
           C z;
           z.x = 0;

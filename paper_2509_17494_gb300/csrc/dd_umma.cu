@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dd_umma(const DDUmmaArgs a) {
       const int xb = i & 1, ux = i >> 1;
       const int sub = blockIdx.x + i * gridDim.x;
       if (!failed) mbar_wait(xempty + xb, (unsigned)((ux & 1) ^ 1), &failed);
-      const int* bb = a.box + (size_t)sub * 8;
+      const int* bb = a.box + (size_t)sub * 12;  // 2-D boxes only (the 3-D rows exceed the tile)
       const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3];
       __nv_bfloat16* xr = reinterpret_cast<__nv_bfloat16*>(xbuf + (size_t)xb * xbuf_bytes);
       __nv_bfloat16* xi = xr + xbuf_bytes / 4;

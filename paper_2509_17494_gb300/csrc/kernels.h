@@ -37,7 +37,7 @@ struct DDArgs {
   const typename Cx<T>::t* r;   // residual, [rhs][N]
   typename Cx<T>::t* V;         // per-subdomain results, [rhs][nsub][NR]
   const void* W;                // inverse rows, [sub][chunk][NR] 16-byte chunks
-  const int* box;               // 8 ints per subdomain
+  const int* box;               // kBox = 12 ints per subdomain (see th_internal.h)
   const float* wscale;          // per-subdomain scale (FP16 rows), or null
   long long N;
   int nsub, m, Lw, NC, NCH, NR, G, nrhs;
@@ -55,7 +55,7 @@ struct DDUmmaArgs {
   const float2* r;        // residual, [rhs][N], FP32 complex
   float2* V;              // [rhs][nsub][NR]
   const unsigned char* W; // BF16 rows in the UMMA core-matrix layout (see setup)
-  const int* box;         // 8 ints per subdomain
+  const int* box;         // 12 ints per subdomain
   int* err;               // set to 1 when a bounded wait gives up
   long long N;
   int nsub, m, Lw, NC, NR, nrhs;
@@ -146,6 +146,47 @@ struct CoarsePartArgs {
 };
 template <typename T>
 cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster, cudaStream_t s);
+
+// ------------------------------------------------------- 3-D (unit cube, Q2)
+template <typename T>
+struct Fine3Args {
+  const typename Cx<T>::t* u;
+  const typename Cx<T>::t* f;  // used when residual != 0
+  typename Cx<T>::t* y;
+  typename Cx<T>::t* ycell;    // scratch [rhs][n^3][32]: per-cell local outputs
+  const T* kc;                 // k per cell
+  const T* ec;                 // eps per cell
+  long long N, ncell;          // m^3, n^3
+  int n, m;
+  int robin;                   // bit s = side s absorbing (x lo, x hi, y lo, y hi, z lo, z hi)
+  int residual;
+  T h, alpha;
+  T M[9], K[9];                // 1-D reference mass / stiffness (p = 2)
+};
+template <typename T>
+cudaError_t launch_fine3(const Fine3Args<T>& a, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_dd_combine3(const CombineArgs<T>& a, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict3(const TransferArgs<T>& a, int nrhs, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong3(const TransferArgs<T>& a, int nrhs, cudaStream_t s);
+// (CoarseApplyArgs: cell = nc^3 x 4 pair weights, rho = 6 x nc^2 face terms)
+template <typename T>
+cudaError_t launch_coarse_apply3(const CoarseApplyArgs<T>& a, int nrhs, cudaStream_t s);
+template <typename T>
+struct Sweep3Args {
+  const typename Cx<T>::t* b;    // [rhs][Nc]
+  typename Cx<T>::t* x;          // [rhs][Nc]
+  typename Cx<T>::t* t;          // scratch [rhs][mb]
+  const typename Cx<T>::t* G;    // mc blocks of mb x mb
+  const typename Cx<T>::t* dn;   // mc x mb x 9 couplings to the slice below
+  const typename Cx<T>::t* up;   // mc x mb x 9 couplings to the slice above
+  long long Nc;
+  int mc, mb, nrhs;
+};
+template <typename T>
+cudaError_t launch_sweep3(const Sweep3Args<T>& a, cudaStream_t s);
 
 // ------------------------------------------------------- vectors (K9/K10)
 cudaError_t launch_d2f(const double* in, float* out, long long n, cudaStream_t s);

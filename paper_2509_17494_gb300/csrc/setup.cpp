@@ -13,6 +13,8 @@
 //    by coarse grid rows.
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -184,10 +186,12 @@ Block1D partition_1d(int n, int l_dd) {
 }
 
 th_status make_geometry(const th_mesh& mesh, const th_params& prm, Geometry& g) {
-  if (mesh.dim != 2) return TH_ERR_UNSUPPORTED;
-  if (mesh.n < 1 || mesh.n > 4096) return TH_ERR_ARG;
+  if (mesh.dim != 2 && mesh.dim != 3) return TH_ERR_UNSUPPORTED;
+  if (mesh.n < 1 || mesh.n > (mesh.dim == 3 ? 256 : 4096)) return TH_ERR_ARG;
   if (mesh.p < 2 || mesh.p > kMaxP || (mesh.p % 2) != 0) return TH_ERR_ARG;
-  for (int s = 0; s < 4; ++s) {
+  if (mesh.dim == 3 && mesh.p != 2) return TH_ERR_UNSUPPORTED;  // the 3-D kernels are Q2
+  const int nsides = 2 * mesh.dim;
+  for (int s = 0; s < nsides; ++s) {
     if (mesh.bc[s] == TH_BC_DIRICHLET) return TH_ERR_UNSUPPORTED;
     if (mesh.bc[s] != TH_BC_ROBIN && mesh.bc[s] != TH_BC_NEUMANN) return TH_ERR_ARG;
   }
@@ -195,45 +199,62 @@ th_status make_geometry(const th_mesh& mesh, const th_params& prm, Geometry& g) 
   if (prm.restart < 1 || prm.maxit < 0 || prm.nrhs_max < 1 || prm.nrhs_max > 4096) return TH_ERR_ARG;
   if (prm.prec < TH_PREC_FP64 || prm.prec > TH_PREC_FP16) return TH_ERR_ARG;
   if (!(prm.tol >= 0.0) || !std::isfinite(prm.alpha_s) || !std::isfinite(prm.omega_c)) return TH_ERR_ARG;
+  g.dim = mesh.dim;
   g.n = mesh.n;
   g.p = mesh.p;
   g.q = mesh.p / 2;
   g.m = g.n * g.p + 1;
-  g.N = (long long)g.m * g.m;
   g.nc = g.n * g.q;
   g.mc = g.nc + 1;
-  g.Nc = (long long)g.mc * g.mc;
+  g.N = g.Nc = 1;
+  for (int d = 0; d < g.dim; ++d) {
+    g.N *= g.m;
+    g.Nc *= g.mc;
+  }
   g.h = 1.0 / g.n;
   g.hc = 1.0 / g.nc;
-  for (int s = 0; s < 4; ++s) g.robin[s] = (mesh.bc[s] == TH_BC_ROBIN);
+  for (int s = 0; s < 6; ++s) g.robin[s] = (s < nsides && mesh.bc[s] == TH_BC_ROBIN) ? 1 : 0;
   g.l_dd = std::min(prm.l_dd, g.n);
   g.blk = partition_1d(g.n, g.l_dd);
   g.nb = (int)g.blk.start.size();
-  g.nsub = g.nb * g.nb;
+  const int nbz = g.dim == 3 ? g.nb : 1;
+  g.nsub = g.nb * g.nb * nbz;
   int lmax = *std::max_element(g.blk.size.begin(), g.blk.size.end());
   g.Lu = lmax * g.p + 1;
   g.Lw = std::min(lmax + 2, g.n) * g.p + 1;
-  g.NR = g.Lu * g.Lu;
-  g.NC = g.Lw * g.Lw;
+  g.NR = g.Lu * g.Lu * (g.dim == 3 ? g.Lu : 1);
+  g.NC = g.Lw * g.Lw * (g.dim == 3 ? g.Lw : 1);
   // boxes
   std::vector<int> o0(g.nb), o1(g.nb);
   for (int b = 0; b < g.nb; ++b) {
     o0[b] = std::max(g.blk.start[b] - 1, 0);
     o1[b] = std::min(g.blk.start[b] + g.blk.size[b] + 1, g.n);
   }
-  g.box.resize((size_t)g.nsub * 8);
-  for (int by = 0; by < g.nb; ++by)
-    for (int bx = 0; bx < g.nb; ++bx) {
-      int* bb = &g.box[((size_t)by * g.nb + bx) * 8];
-      bb[0] = o0[bx] * g.p;
-      bb[1] = o0[by] * g.p;
-      bb[2] = (o1[bx] - o0[bx]) * g.p + 1;
-      bb[3] = (o1[by] - o0[by]) * g.p + 1;
-      bb[4] = g.blk.start[bx] * g.p;
-      bb[5] = g.blk.start[by] * g.p;
-      bb[6] = g.blk.size[bx] * g.p + 1;
-      bb[7] = g.blk.size[by] * g.p + 1;
-    }
+  g.box.resize((size_t)g.nsub * kBox);
+  for (int bz = 0; bz < nbz; ++bz)
+    for (int by = 0; by < g.nb; ++by)
+      for (int bx = 0; bx < g.nb; ++bx) {
+        int* bb = &g.box[(((size_t)bz * g.nb + by) * g.nb + bx) * kBox];
+        bb[0] = o0[bx] * g.p;
+        bb[1] = o0[by] * g.p;
+        bb[2] = (o1[bx] - o0[bx]) * g.p + 1;
+        bb[3] = (o1[by] - o0[by]) * g.p + 1;
+        bb[4] = g.blk.start[bx] * g.p;
+        bb[5] = g.blk.start[by] * g.p;
+        bb[6] = g.blk.size[bx] * g.p + 1;
+        bb[7] = g.blk.size[by] * g.p + 1;
+        if (g.dim == 3) {
+          bb[8] = o0[bz] * g.p;
+          bb[9] = (o1[bz] - o0[bz]) * g.p + 1;
+          bb[10] = g.blk.start[bz] * g.p;
+          bb[11] = g.blk.size[bz] * g.p + 1;
+        } else {
+          bb[8] = 0;
+          bb[9] = 1;
+          bb[10] = 0;
+          bb[11] = 1;
+        }
+      }
   // 1-D combine table and multiplicity
   g.ctab.assign((size_t)g.m * 4, -1);
   g.mult1d.assign(g.m, 0);
@@ -296,9 +317,102 @@ static void band_solve(const cplx* A, int n, int kl, int ku, const std::vector<i
   }
 }
 
+// 3-D: Omega^(i) box of wx x wy x wz dofs; element matrices
+// h (K M M + M K M + M M K) - (k^2 (1 + i a) + i eps) h^3 M M M, and
+// -i k h^2 M M on every absorbing face (internal faces of Omega^(i) and the
+// domain's Robin faces), lexicographic local numbering, x fastest.
+static th_status subdomain_inverse_rows3(const Geometry& g, const Ref1D& ref, const double* k,
+                                         const double* eps, double alpha_s, int sub, cplx* out) {
+  const int* bb = &g.box[(size_t)sub * kBox];
+  const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3];
+  const int ux = bb[4], uy = bb[5], vx = bb[6], vy = bb[7];
+  const int oz = bb[8], wz = bb[9], uz = bb[10], vz = bb[11];
+  const int p = g.p, np = p + 1;
+  const int nx = (wx - 1) / p, ny = (wy - 1) / p, nz = (wz - 1) / p;
+  const int c0x = ox / p, c0y = oy / p, c0z = oz / p;
+  const int nd = wx * wy * wz;
+  std::vector<cplx> A((size_t)nd * nd, 0.0);
+  const double h = g.h;
+  const double* M = ref.M.data();
+  const double* K = ref.K.data();
+  auto lid = [&](int lz, int ly, int lx) { return (lz * wy + ly) * wx + lx; };
+  for (int cz = 0; cz < nz; ++cz)
+    for (int cy = 0; cy < ny; ++cy)
+      for (int cx = 0; cx < nx; ++cx) {
+        const size_t cell = ((size_t)(c0z + cz) * g.n + (c0y + cy)) * g.n + (c0x + cx);
+        const double kk = k[cell], ee = eps ? eps[cell] : 0.0;
+        const cplx me = -cplx(kk * kk, alpha_s * kk * kk + ee) * (h * h * h);
+        for (int az = 0; az < np; ++az)
+          for (int ay = 0; ay < np; ++ay)
+            for (int ax = 0; ax < np; ++ax) {
+              const int row = lid(cz * p + az, cy * p + ay, cx * p + ax);
+              for (int bz = 0; bz < np; ++bz)
+                for (int by = 0; by < np; ++by)
+                  for (int bx = 0; bx < np; ++bx) {
+                    const int col = lid(cz * p + bz, cy * p + by, cx * p + bx);
+                    const double Mz = M[az * np + bz], My = M[ay * np + by], Mx = M[ax * np + bx];
+                    const double st = K[az * np + bz] * My * Mx + Mz * K[ay * np + by] * Mx + Mz * My * K[ax * np + bx];
+                    A[(size_t)row * nd + col] += h * st + me * (Mz * My * Mx);
+                  }
+            }
+      }
+  // absorbing faces: side s = 2 axis + end, axis 0 = x, 1 = y, 2 = z
+  const int ncl[3] = {nx, ny, nz}, c0[3] = {c0x, c0y, c0z}, wl[3] = {wx, wy, wz};
+  for (int s = 0; s < 6; ++s) {
+    const int ax = s / 2, end = s % 2;
+    const bool at_domain = end == 0 ? (c0[ax] == 0) : (c0[ax] + ncl[ax] == g.n);
+    if (at_domain && !g.robin[s]) continue;
+    const int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;  // the face's two axes
+    const int layer = end == 0 ? 0 : wl[ax] - 1;
+    for (int f2 = 0; f2 < ncl[a2]; ++f2)
+      for (int f1 = 0; f1 < ncl[a1]; ++f1) {
+        int cc[3];
+        cc[ax] = end == 0 ? 0 : ncl[ax] - 1;
+        cc[a1] = f1;
+        cc[a2] = f2;
+        const size_t cell = ((size_t)(c0z + cc[2]) * g.n + (c0y + cc[1])) * g.n + (c0x + cc[0]);
+        const cplx rho(0.0, -k[cell] * h * h);  // -i k h^2
+        for (int i2 = 0; i2 < np; ++i2)
+          for (int i1 = 0; i1 < np; ++i1)
+            for (int j2 = 0; j2 < np; ++j2)
+              for (int j1 = 0; j1 < np; ++j1) {
+                int ra[3], rb[3];
+                ra[ax] = rb[ax] = layer;
+                ra[a1] = f1 * p + i1;
+                ra[a2] = f2 * p + i2;
+                rb[a1] = f1 * p + j1;
+                rb[a2] = f2 * p + j2;
+                A[(size_t)lid(ra[2], ra[1], ra[0]) * nd + lid(rb[2], rb[1], rb[0])] +=
+                    rho * (M[i1 * np + j1] * M[i2 * np + j2]);
+              }
+      }
+  }
+  const int bw = p * wx * wy + p * wx + p;
+  std::vector<int> piv;
+  if (!band_lu(A.data(), nd, bw, bw, piv)) return TH_ERR_SINGULAR;
+  std::vector<cplx> x(nd);
+  const int NC = g.NC, Lu = g.Lu, Lw = g.Lw;
+  std::fill(out, out + (size_t)g.NR * NC, cplx(0.0));
+  for (int rz = 0; rz < vz; ++rz)
+    for (int ry = 0; ry < vy; ++ry)
+      for (int rx = 0; rx < vx; ++rx) {
+        const int gx = ux + rx, gy = uy + ry, gz = uz + rz;
+        std::fill(x.begin(), x.end(), cplx(0.0));
+        x[lid(gz - oz, gy - oy, gx - ox)] = 1.0;
+        band_solve(A.data(), nd, bw, bw, piv, x.data());
+        const double Lj = (double)g.mult1d[gx] * g.mult1d[gy] * g.mult1d[gz];
+        cplx* orow = out + (size_t)((rz * Lu + ry) * Lu + rx) * NC;
+        for (int cz = 0; cz < wz; ++cz)
+          for (int cy = 0; cy < wy; ++cy)
+            for (int cx = 0; cx < wx; ++cx) orow[(cz * Lw + cy) * Lw + cx] = x[lid(cz, cy, cx)] / Lj;
+      }
+  return TH_OK;
+}
+
 th_status subdomain_inverse_rows(const Geometry& g, const Ref1D& ref, const double* k,
                                  const double* eps, double alpha_s, int sub, cplx* out) {
-  const int* bb = &g.box[(size_t)sub * 8];
+  if (g.dim == 3) return subdomain_inverse_rows3(g, ref, k, eps, alpha_s, sub, out);
+  const int* bb = &g.box[(size_t)sub * kBox];
   const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3];
   const int ux = bb[4], uy = bb[5], vx = bb[6], vy = bb[7];
   const int p = g.p, np = p + 1;
@@ -388,24 +502,29 @@ th_status all_inverse_rows(const Geometry& g, const Ref1D& ref, const double* k,
   std::vector<int> rep(g.nsub);
   std::map<std::string, int> seen;
   for (int s = 0; s < g.nsub; ++s) {
-    const int* bb = &g.box[(size_t)s * 8];
+    const int* bb = &g.box[(size_t)s * kBox];
     std::string key;
     auto put = [&](const void* d, size_t nbytes) { key.append((const char*)d, nbytes); };
-    const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3];
-    int rel[8] = {bb[2], bb[3], bb[4] - ox, bb[5] - oy, bb[6], bb[7],
-                  (ox == 0) ? 1 : 0, (oy == 0) ? 1 : 0};
+    const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3], oz = bb[8], wz = bb[9];
+    int rel[12] = {bb[2], bb[3], bb[4] - ox, bb[5] - oy, bb[6], bb[7],
+                   (ox == 0) ? 1 : 0, (oy == 0) ? 1 : 0, bb[9], bb[10] - oz, bb[11], (oz == 0) ? 1 : 0};
     put(rel, sizeof(rel));
-    int hi[2] = {(ox + wx - 1 == g.m - 1) ? 1 : 0, (oy + wy - 1 == g.m - 1) ? 1 : 0};
+    int hi[3] = {(ox + wx - 1 == g.m - 1) ? 1 : 0, (oy + wy - 1 == g.m - 1) ? 1 : 0,
+                 (g.dim == 3 && oz + wz - 1 == g.m - 1) ? 1 : 0};
     put(hi, sizeof(hi));
-    for (int cy = oy / g.p; cy < (oy + wy - 1) / g.p; ++cy)
-      for (int cx = ox / g.p; cx < (ox + wx - 1) / g.p; ++cx) {
-        const size_t c = (size_t)cy * g.n + cx;
-        put(&k[c], sizeof(double));
-        double e = eps ? eps[c] : 0.0;
-        put(&e, sizeof(double));
-      }
+    const int czb = g.dim == 3 ? oz / g.p : 0, cze = g.dim == 3 ? (oz + wz - 1) / g.p : 1;
+    for (int cz = czb; cz < cze; ++cz)
+      for (int cy = oy / g.p; cy < (oy + wy - 1) / g.p; ++cy)
+        for (int cx = ox / g.p; cx < (ox + wx - 1) / g.p; ++cx) {
+          const size_t c = ((size_t)cz * g.n + cy) * g.n + cx;
+          put(&k[c], sizeof(double));
+          double e = eps ? eps[c] : 0.0;
+          put(&e, sizeof(double));
+        }
     for (int i = bb[4]; i < bb[4] + bb[6]; ++i) put(&g.mult1d[i], sizeof(int));
     for (int i = bb[5]; i < bb[5] + bb[7]; ++i) put(&g.mult1d[i], sizeof(int));
+    if (g.dim == 3)
+      for (int i = bb[10]; i < bb[10] + bb[11]; ++i) put(&g.mult1d[i], sizeof(int));
     auto it = seen.find(key);
     if (it == seen.end()) {
       seen.emplace(key, s);
@@ -726,6 +845,289 @@ void store_padded(int n, int ld, const cplx* M, cplx* dst) {
 }
 
 }  // namespace
+
+
+// -------------------------------------------------------------- 3-D coarse
+// Fitted 27-point scheme (the paper only cites a 3-D dispersion-minimising
+// stencil; this is the construction of the 9-point one carried to 3-D):
+// sigma_P(xi) = P0 + 2 P1 sum cos xi_a + 4 P2 sum_{a<b} cos xi_a cos xi_b
+// + 8 P3 prod cos xi_a vanishes at |xi| = eta along three directions d^(i)
+// (images of the interior 3-point rule (2/3, 1/6, 1/6) of the symmetry-reduced
+// spherical triangle with corners (0,0,1), (0,1,1)/sqrt2, (1,1,1)/sqrt3), and
+// N = -eta^2 / sigma_P(0).  With s_a = 2 sin^2(eta d_a / 2) = 1 - cos(eta d_a)
+// and S1 = sum s_a, S2 = sum_{a<b} s_a s_b, S3 = prod s_a, the zero conditions
+// of the scaled weights read Q1 S1 - Q2 S2 + Q3 S3 = -eta^2, where
+// Q1 = N (2 P1 + 8 P2 + 8 P3), Q2 = N (4 P2 + 8 P3), Q3 = 8 N P3.  Since
+// S1 ~ eta^2, S2 ~ eta^4, S3 ~ eta^6, the system is solved for (Q1, eta^2 Q2,
+// eta^4 Q3) with the columns divided by eta^2, eta^4, eta^6; Q2 and Q3 are then
+// determined by the O(eta^4), O(eta^6) differences between the directions, so
+// they lose about eta^-2 and eta^-4 units of the working precision, and the
+// 3 x 3 solve runs in long double (the s_a are computed without cancellation).
+// Then N P3 = Q3/8, N P2 = (Q2 - Q3)/4, N P1 = (Q1 - 2 Q2 + Q3)/2,
+// N P0 = -eta^2 - 3 Q1 + 3 Q2 - Q3, and the cell's pair weights are
+// h_c (N P0/8, N P1/4, N P2/2, N P3) minus i eps h_c^3 times the Q1 mass of
+// the pair ((1/3)^(3 - nd) (1/6)^nd for nd differing coordinates).
+void qsfem27_cell(double k, double eps, double hc, cplx d[4]) {
+  static double dirs[3][3];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const double r2 = 1.0 / std::sqrt(2.0), r3 = 1.0 / std::sqrt(3.0);
+    const double V[3][3] = {{0, 0, 1}, {0, r2, r2}, {r3, r3, r3}};
+    const double W[3][3] = {{2.0 / 3, 1.0 / 6, 1.0 / 6}, {1.0 / 6, 2.0 / 3, 1.0 / 6}, {1.0 / 6, 1.0 / 6, 2.0 / 3}};
+    for (int i = 0; i < 3; ++i) {
+      double v[3] = {0, 0, 0};
+      for (int j = 0; j < 3; ++j)
+        for (int a = 0; a < 3; ++a) v[a] += W[i][j] * V[j][a];
+      const double nrm = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      for (int a = 0; a < 3; ++a) dirs[i][a] = v[a] / nrm;
+    }
+  });
+  using L = long double;
+  const L eta = (L)k * (L)hc, e2 = eta * eta;
+  L Mx[3][4];
+  for (int i = 0; i < 3; ++i) {
+    L s[3];
+    for (int a = 0; a < 3; ++a) {
+      const L t = std::sin((L)0.5 * eta * (L)dirs[i][a]);
+      s[a] = 2 * t * t;
+    }
+    const L S1 = s[0] + s[1] + s[2], S2 = s[0] * s[1] + s[0] * s[2] + s[1] * s[2], S3 = s[0] * s[1] * s[2];
+    Mx[i][0] = S1 / e2;
+    Mx[i][1] = -S2 / (e2 * e2);
+    Mx[i][2] = S3 / (e2 * e2 * e2);
+    Mx[i][3] = -1;  // right-hand side -eta^2 / eta^2
+  }
+  // Gaussian elimination with partial pivoting on the scaled 3 x 3 system
+  for (int c = 0; c < 3; ++c) {
+    int pr = c;
+    for (int r = c + 1; r < 3; ++r)
+      if (std::fabs(Mx[r][c]) > std::fabs(Mx[pr][c])) pr = r;
+    for (int j = 0; j < 4; ++j) std::swap(Mx[c][j], Mx[pr][j]);
+    for (int r = c + 1; r < 3; ++r) {
+      const L l = Mx[r][c] / Mx[c][c];
+      for (int j = c; j < 4; ++j) Mx[r][j] -= l * Mx[c][j];
+    }
+  }
+  L y[3];
+  for (int r = 2; r >= 0; --r) {
+    L acc = Mx[r][3];
+    for (int j = r + 1; j < 3; ++j) acc -= Mx[r][j] * y[j];
+    y[r] = acc / Mx[r][r];
+  }
+  // unknowns were (Q1, eta^2 Q2, eta^4 Q3)
+  const L Q1 = y[0], Q2 = y[1] / e2, Q3 = y[2] / (e2 * e2);
+  const L NP3 = Q3 / 8, NP2 = (Q2 - Q3) / 4, NP1 = (Q1 - 2 * Q2 + Q3) / 2;
+  const L NP0 = -e2 - 3 * Q1 + 3 * Q2 - Q3;
+  const double q[4] = {(double)(NP0 / 8), (double)(NP1 / 4), (double)(NP2 / 2), (double)NP3};
+  const double mass[4] = {1.0 / 27.0, 1.0 / 54.0, 1.0 / 108.0, 1.0 / 216.0};
+  const double h3 = hc * hc * hc;
+  for (int i = 0; i < 4; ++i) d[i] = cplx(hc * q[i], -eps * h3 * mass[i]);
+}
+
+namespace {
+// Fixed-size thread team with a reusable barrier (host set-up only).
+struct Team {
+  int nt;
+  std::mutex mu;
+  std::condition_variable cv;
+  int waiting = 0;
+  long long gen = 0;
+  explicit Team(int n) : nt(n) {}
+  void barrier() {
+    std::unique_lock<std::mutex> lk(mu);
+    const long long g0 = gen;
+    if (++waiting == nt) {
+      waiting = 0;
+      ++gen;
+      cv.notify_all();
+    } else {
+      cv.wait(lk, [&] { return gen != g0; });
+    }
+  }
+};
+}  // namespace
+
+// Inverse of a dense n x n matrix: right-looking LU with partial pivoting whose
+// trailing update is split row-wise over a thread team, then the columns of
+// the inverse solved in parallel.
+static bool dense_inverse_par(std::vector<cplx>& S, int n, cplx* out) {
+  unsigned hw = std::thread::hardware_concurrency();
+  const int nt = (int)std::max(1u, std::min(hw == 0 ? 4u : hw, 64u));
+  std::vector<int> piv(n);
+  Team team(nt);
+  std::atomic<bool> fail(false);
+  cplx inv_piv = 0.0;
+  auto worker = [&](int t) {
+    for (int k = 0; k < n; ++k) {
+      if (t == 0) {
+        int pr = k;
+        double best = std::abs(S[(size_t)k * n + k]);
+        for (int r = k + 1; r < n; ++r) {
+          const double v = std::abs(S[(size_t)r * n + k]);
+          if (v > best) { best = v; pr = r; }
+        }
+        piv[k] = pr;
+        if (best == 0.0) {
+          fail.store(true);
+        } else {
+          if (pr != k)
+            for (int c = 0; c < n; ++c) std::swap(S[(size_t)k * n + c], S[(size_t)pr * n + c]);
+          inv_piv = 1.0 / S[(size_t)k * n + k];
+        }
+      }
+      team.barrier();
+      if (fail.load()) return;
+      const cplx* rowk = S.data() + (size_t)k * n;
+      const cplx ip = inv_piv;
+      for (int r = k + 1 + t; r < n; r += nt) {
+        cplx* rowr = S.data() + (size_t)r * n;
+        const cplx l = rowr[k] * ip;
+        rowr[k] = l;
+        if (l == 0.0) continue;
+        for (int c = k + 1; c < n; ++c) rowr[c] -= l * rowk[c];
+      }
+      team.barrier();
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker, t);
+  worker(0);
+  for (auto& th : pool) th.join();
+  if (fail.load()) return false;
+  parallel_for(n, [&](int c) {
+    std::vector<cplx> x(n, cplx(0.0));
+    x[c] = 1.0;
+    band_solve(S.data(), n, n - 1, n - 1, piv, x.data());
+    for (int r = 0; r < n; ++r) out[(size_t)r * n + c] = x[r];
+  });
+  return true;
+}
+
+th_status coarse_setup3(const Geometry& g, const double* k, const double* eps, CoarseBlocks3& cb) {
+  const int nc = g.nc, mc = g.mc, q = g.q;
+  const int mb = mc * mc;
+  const double hc = g.hc;
+  cb.mc = mc;
+  cb.mb = mb;
+  cb.cell.assign((size_t)nc * nc * nc * 4, cplx(0.0));
+  cb.rho.assign((size_t)6 * nc * nc, cplx(0.0));
+  cb.dn.assign((size_t)mc * mb * 9, cplx(0.0));
+  cb.up.assign((size_t)mc * mb * 9, cplx(0.0));
+  auto field = [&](int cz, int cy, int cx, const double* f) {
+    return f ? f[((size_t)(cz / q) * g.n + cy / q) * g.n + cx / q] : 0.0;
+  };
+  for (int cz = 0; cz < nc; ++cz)
+    for (int cy = 0; cy < nc; ++cy)
+      for (int cx = 0; cx < nc; ++cx)
+        qsfem27_cell(field(cz, cy, cx, k), field(cz, cy, cx, eps), hc, &cb.cell[(((size_t)cz * nc + cy) * nc + cx) * 4]);
+  // face terms: side s = 2 axis + end (axis 0 = x, 1 = y, 2 = z); face cell (f1, f2) over axes (axis+1, axis+2) mod 3
+  for (int s = 0; s < 6; ++s) {
+    if (!g.robin[s]) continue;
+    const int ax = s / 2, end = s % 2;
+    const int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
+    for (int f2 = 0; f2 < nc; ++f2)
+      for (int f1 = 0; f1 < nc; ++f1) {
+        int c[3];
+        c[ax] = end == 0 ? 0 : nc - 1;
+        c[a1] = f1;
+        c[a2] = f2;
+        cb.rho[((size_t)s * nc + f2) * nc + f1] = cplx(0.0, -field(c[2], c[1], c[0], k) * hc * hc);
+      }
+  }
+  // block assembly into the pivot blocks D_z (dense, per slice) and the couplings dn / up
+  std::vector<std::vector<cplx>> D(mc);
+  for (int j = 0; j < mc; ++j) D[j].assign((size_t)mb * mb, cplx(0.0));
+  auto add = [&](cplx v, int za, int ya, int xa, int zb, int yb, int xb) {
+    const int a = ya * mc + xa;
+    if (za == zb) {
+      D[za][(size_t)a * mb + yb * mc + xb] += v;
+    } else {
+      const int dy = yb - ya + 1, dx = xb - xa + 1;
+      if (zb == za + 1) cb.up[((size_t)za * mb + a) * 9 + dy * 3 + dx] += v;
+      else cb.dn[((size_t)za * mb + a) * 9 + dy * 3 + dx] += v;
+    }
+  };
+  const double Mq[2][2] = {{1.0 / 3, 1.0 / 6}, {1.0 / 6, 1.0 / 3}};
+  for (int cz = 0; cz < nc; ++cz)
+    for (int cy = 0; cy < nc; ++cy)
+      for (int cx = 0; cx < nc; ++cx) {
+        const cplx* dc = &cb.cell[(((size_t)cz * nc + cy) * nc + cx) * 4];
+        for (int va = 0; va < 8; ++va)
+          for (int vb = 0; vb < 8; ++vb) {
+            const int az = va >> 2, ay = (va >> 1) & 1, axx = va & 1;
+            const int bz = vb >> 2, by = (vb >> 1) & 1, bx = vb & 1;
+            const int nd = (az != bz) + (ay != by) + (axx != bx);
+            add(dc[nd], cz + az, cy + ay, cx + axx, cz + bz, cy + by, cx + bx);
+          }
+      }
+  for (int s = 0; s < 6; ++s) {
+    if (!g.robin[s]) continue;
+    const int ax = s / 2, end = s % 2;
+    const int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
+    for (int f2 = 0; f2 < nc; ++f2)
+      for (int f1 = 0; f1 < nc; ++f1) {
+        const cplx rv = cb.rho[((size_t)s * nc + f2) * nc + f1];
+        for (int i2 = 0; i2 < 2; ++i2)
+          for (int i1 = 0; i1 < 2; ++i1)
+            for (int j2 = 0; j2 < 2; ++j2)
+              for (int j1 = 0; j1 < 2; ++j1) {
+                int va[3], vb[3];
+                va[ax] = vb[ax] = end == 0 ? 0 : nc;
+                va[a1] = f1 + i1;
+                va[a2] = f2 + i2;
+                vb[a1] = f1 + j1;
+                vb[a2] = f2 + j2;
+                add(rv * (Mq[i1][j1] * Mq[i2][j2]), va[2], va[1], va[0], vb[2], vb[1], vb[0]);
+              }
+      }
+  }
+  // block LU: S_0 = D_0, S_j = D_j - C_{j-1}^T G_{j-1} C_{j-1}, G_j = S_j^{-1},
+  // with C_{j-1}[a][b] = A[(j-1, a), (j, b)] = up_{j-1}[a][b - a]
+  cb.G.assign((size_t)mc * mb * mb, cplx(0.0));
+  std::vector<cplx> T((size_t)mb * mb);
+  for (int j = 0; j < mc; ++j) {
+    std::vector<cplx>& S = D[j];
+    if (j > 0) {
+      const cplx* Gp = &cb.G[(size_t)(j - 1) * mb * mb];
+      const cplx* Up = &cb.up[(size_t)(j - 1) * mb * 9];
+      // T = G_{j-1} C_{j-1}
+      parallel_for(mb, [&](int a) {
+        cplx* Ta = &T[(size_t)a * mb];
+        std::fill(Ta, Ta + mb, cplx(0.0));
+        const cplx* Ga = Gp + (size_t)a * mb;
+        for (int ap = 0; ap < mb; ++ap) {
+          const cplx gv = Ga[ap];
+          if (gv == 0.0) continue;
+          const int y = ap / mc, x = ap % mc;
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int yb = y + dy, xb = x + dx;
+              if (yb < 0 || yb >= mc || xb < 0 || xb >= mc) continue;
+              Ta[yb * mc + xb] += gv * Up[(size_t)ap * 9 + (dy + 1) * 3 + (dx + 1)];
+            }
+        }
+      });
+      // S -= C^T T: (C^T T)[b][b'] = sum_a C[a][b] T[a][b']
+      parallel_for(mb, [&](int b) {
+        const int y = b / mc, x = b % mc;
+        cplx* Sb = &S[(size_t)b * mb];
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int ya = y - dy, xa = x - dx;  // a with b - a = (dy, dx)
+            if (ya < 0 || ya >= mc || xa < 0 || xa >= mc) continue;
+            const int a = ya * mc + xa;
+            const cplx c = Up[(size_t)a * 9 + (dy + 1) * 3 + (dx + 1)];
+            if (c == 0.0) continue;
+            const cplx* Ta = &T[(size_t)a * mb];
+            for (int bp = 0; bp < mb; ++bp) Sb[bp] -= c * Ta[bp];
+          }
+      });
+    }
+    if (!dense_inverse_par(S, mb, &cb.G[(size_t)j * mb * mb])) return TH_ERR_SINGULAR;
+    std::vector<cplx>().swap(S);
+  }
+  return TH_OK;
+}
 
 int coarse_chunks(int mc) {
   int P = (int)std::lround(std::sqrt((double)mc));

@@ -30,23 +30,27 @@ struct Block1D {
 Block1D partition_1d(int n, int l_dd);
 
 // Geometry of the fine mesh, the partition and the coarse mesh.
+constexpr int kBox = 12;  // ints per subdomain box
+
 struct Geometry {
+  int dim = 2;              // 2 or 3
   int n = 0, p = 0, q = 0;  // cells, order, p/2
   int m = 0;                // fine nodes per direction n p + 1
-  long long N = 0;          // fine dofs m^2
+  long long N = 0;          // fine dofs m^dim
   int nc = 0;               // coarse cells per direction n p / 2
   int mc = 0;               // coarse nodes per direction nc + 1
-  long long Nc = 0;         // coarse dofs
+  long long Nc = 0;         // coarse dofs mc^dim
   double h = 0, hc = 0;
-  int robin[4] = {0, 0, 0, 0};  // x lo, x hi, y lo, y hi
+  int robin[6] = {0, 0, 0, 0, 0, 0};  // x lo, x hi, y lo, y hi, z lo, z hi
   // partition
   int l_dd = 0;
   Block1D blk;              // same along x and y
   int nb = 0;               // blocks per direction
-  int nsub = 0;             // nb^2
+  int nsub = 0;             // nb^dim
   int Lw = 0, Lu = 0;       // max Omega / U box width in dofs
-  int NC = 0, NR = 0;       // Lw^2 columns, Lu^2 rows of an inverse-row block
-  // per-subdomain boxes (dof coordinates): ox, oy, wx, wy, ux, uy, vx, vy
+  int NC = 0, NR = 0;       // Lw^dim columns, Lu^dim rows of an inverse-row block
+  // per-subdomain boxes (dof coordinates), kBox ints each:
+  // ox, oy, wx, wy, ux, uy, vx, vy, oz, wz, uz, vz (2-D: oz = uz = 0, wz = vz = 1)
   std::vector<int> box;
   // 1-D combine table: per fine 1-D node i: (b0, r0, b1, r1), b1 = -1 if only one block
   std::vector<int> ctab;
@@ -76,6 +80,19 @@ struct CoarseBlocks {
   std::vector<cplx> G;            // mc blocks of mc x mc
 };
 th_status coarse_setup(const Geometry& g, const double* k, const double* eps, CoarseBlocks& cb);
+
+// 3-D coarse operator (fitted 27-point scheme) in z-slice block form: the
+// unknowns of slice j are the mb = mc^2 coarse nodes of that slice.
+struct CoarseBlocks3 {
+  int mc = 0, mb = 0;
+  std::vector<cplx> cell;  // nc^3 x 4: d_0..d_3 per coarse cell (pair weight by differing coordinates)
+  std::vector<cplx> rho;   // 6 x nc^2: -i k h_c^2 per face cell (0 where Neumann)
+  std::vector<cplx> dn;    // mc x mb x 9: A[(j, a), (j-1, a + (dy, dx))], dy, dx in -1..1 (slice 0: unused)
+  std::vector<cplx> up;    // mc x mb x 9: A[(j, a), (j+1, a + (dy, dx))] (last slice: unused)
+  std::vector<cplx> G;     // mc blocks of mb x mb: inverses of the block-LU pivots
+};
+void qsfem27_cell(double k, double eps, double hc, cplx d[4]);
+th_status coarse_setup3(const Geometry& g, const double* k, const double* eps, CoarseBlocks3& cb);
 
 // Partitioned form of the coarse block-tridiagonal system (see coarse_partition).
 struct CoarsePart {

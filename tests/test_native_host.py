@@ -5,6 +5,8 @@ import os
 import re
 
 import numpy as np
+
+import synth
 import pytest
 
 from oracle import dd, fem, qsfem, twogrid
@@ -62,7 +64,8 @@ def test_inverse_rows_match_oracle(th, n, l_dd, bc):
         box, W, Lu, Lw = th.host_inverse_rows(n, p, k, eps, sub, bc=bc, alpha_s=0.5, l_dd=l_dd)
         inv = np.linalg.inv(sd.As.toarray())
         rows = inv[sd.u_local, :] / S.L[sd.u_dofs][:, None]
-        ox, oy, wx, wy, ux, uy, vx, vy = box
+        ox, oy, wx, wy, ux, uy, vx, vy = box[:8]
+        assert box[8:] == [0, 1, 0, 1]
         Wr = np.zeros((vx * vy, wx * wy), complex)
         for ry in range(vy):
             for rx in range(vx):
@@ -72,6 +75,43 @@ def test_inverse_rows_match_oracle(th, n, l_dd, bc):
         Wfull = W.reshape(Lu, Lu, Lw, Lw)
         assert np.all(Wfull[vy:] == 0) and np.all(Wfull[:, vx:] == 0)
         assert np.all(Wfull[..., wy:, :] == 0) and np.all(Wfull[..., wx:] == 0)
+
+
+@pytest.mark.parametrize("n,l_dd", [(4, 2), (5, 2)])
+def test_inverse_rows_match_oracle_3d(th, n, l_dd):
+    p = 2
+    k = 2 * np.pi * 1.5 / synth.random_velocity(n, 3, 9)
+    eps = synth.absorbing_layer(n, 3, p, k, width_dofs=2)
+    P = twogrid.Problem(n, p, k, eps, dim=3, alpha_s=0.5, coarse=False)
+    S = dd.DDSmoother(P, l_dd)
+    for sub, sd in enumerate(S.subs):
+        box, W, Lu, Lw = th.host_inverse_rows(n, p, k, eps, sub, bc="robin", alpha_s=0.5, l_dd=l_dd, dim=3)
+        ox, oy, wx, wy, ux, uy, vx, vy, oz, wz, uz, vz = box
+        inv = np.linalg.inv(sd.As.toarray())
+        rows = inv[sd.u_local, :] / S.L[sd.u_dofs][:, None]
+        Wr = np.zeros((vx * vy * vz, wx * wy * wz), complex)
+        for rz in range(vz):
+            for ry in range(vy):
+                for rx in range(vx):
+                    Wr[(rz * vy + ry) * vx + rx] = W[(rz * Lu + ry) * Lu + rx].reshape(Lw, Lw, Lw)[:wz, :wy, :wx].reshape(-1)
+        assert np.abs(Wr - rows).max() <= 1e-12 * np.abs(rows).max(), sub
+
+
+@pytest.mark.parametrize("eta", [0.05, 0.1, 0.3, 1.0, 1.57, 2.2])
+def test_qsfem27_cell_matches_oracle(th, eta):
+    """The library's weights against the oracle's 50-digit solve of the zero
+    conditions.  The weight of the corner pairs is fixed by the O(eta^6)
+    differences between the fitted directions, so the library (a long double
+    solve: 64-bit significand on x86) loses about eta^-4 of its unit roundoff:
+    1e-13 from eta = 0.1 on, 2e-12 at eta = 0.05."""
+    from oracle import qsfem
+    hc, eps = 0.025, 3.0
+    d = th.host_qsfem27_cell(eta / hc, eps, hc)
+    q = np.array(qsfem.cell_q27(eta))
+    mass = np.array([1 / 27, 1 / 54, 1 / 108, 1 / 216]) * hc ** 3
+    want = hc * q - 1j * eps * mass
+    tol = 1e-13 if eta >= 0.1 else 2e-12
+    assert np.abs(d - want).max() <= tol * np.abs(want).max(), (d, want)
 
 
 def test_workspace_size_and_argument_errors(th):
