@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--fine-variant", choices=["auto", "0", "1"], default="auto",
                     help="FP32 and FP64 fine-apply tile variant: auto, 0 (large tiles), 1 (small tiles)")
     ap.add_argument("--learned-steps", type=int, default=400, help="training steps of the learned section (0: skip)")
+    ap.add_argument("--dim3", choices=["cube10_q2_n40", "cube2_q2_n8", "none"], default="cube10_q2_n40",
+                    help="3-D workload of the three-dimensional section")
     return ap.parse_args()
 
 
@@ -344,6 +346,8 @@ def run_native(args):
         line["batched"] = batched_section(args, w, dev, world)
     if args.learned_steps > 0:
         line["learned"] = learned_section(args, dev)
+    if args.dim3 != "none":
+        line["dim3"] = dim3_section(args, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_cycles)
     if rank == 0:
@@ -410,6 +414,59 @@ def batched_section(args, w, dev, world):
                               "achieved_gbs": round(alg_bytes / (dd_avg * 1e-3) / 1e9, 1),
                               "hbm_peak_gbs": hbm, "peak_source": src},
            "per_kernel_ms_per_cycle": {k: round(v[0] / 3, 4) for k, v in prof.items() if v[1] > 0}}
+    S.close()
+    return out
+
+
+def dim3_section(args, dev, world):
+    """The unit cube with Q2 elements and the fitted 27-point coarse operator:
+    all sources of the workload in one graph-replayed cycle, FP32 cycle (FP32
+    subdomain rows) against the plain FP64 form, and the time to 1e-8."""
+    import numpy as np
+    import torch
+
+    import paper_2509_17494_gb300 as th
+    import synth
+
+    w = synth.workload(args.dim3)
+    F = np.ascontiguousarray(w["f"].reshape(-1, (w["n"] * w["p"] + 1) ** 3))
+    nr = F.shape[0]
+    t0 = time.time()
+    S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=w["alpha_s"], l_dd=w["l_dd"], prec="fp32",
+                         extra_prec=("fp64",), restart=30, maxit=300, nrhs_max=nr, device=dev, dim=3)
+    setup_s = time.time() - t0
+    Fd = torch.from_numpy(F).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": args.dim3, "dofs": S.N, "coarse_dofs": S.Nc, "nrhs": nr, "setup_s": round(setup_s, 1),
+           "stencil": "fitted 27-point (project construction; the paper only cites a 3-D scheme)"}
+    for prec in ("fp32", "fp64"):
+        S.set_precision(prec)
+        U = torch.zeros_like(Fd)
+        for _ in range(3):
+            S.cycle_graph(Fd, U)
+        torch.cuda.synchronize(dev)
+        steps = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(f"dim3_cycle_{prec}")
+        e0.record(stream)
+        for _ in range(steps):
+            S.cycle_graph(Fd, U)
+        e1.record(stream)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize(dev)
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
+        S.profile(True)
+        S.cycle(Fd, U)
+        torch.cuda.synchronize(dev)
+        prof = S.profile_read()
+        S.profile(False)
+        _, info = S.solve(Fd, check=False)
+        out[prec] = {"value": round(S.N * nr * world / (ms * 1e-3) / 1e9, 4), "unit": "GDOF/s",
+                     "ms_per_cycle": round(ms, 3), "time_to_tol_ms": round(info["ms_total"], 1),
+                     "iters": info["iters"], "converged": info["converged"], "relres_max": info["relres_max"],
+                     "per_kernel_ms_per_cycle": {k: round(v[0], 3) for k, v in prof.items() if v[1] > 0}}
+    out["speedup_vs_fp64"] = {"cycle": round(out["fp64"]["ms_per_cycle"] / out["fp32"]["ms_per_cycle"], 2),
+                              "time_to_tol": round(out["fp64"]["time_to_tol_ms"] / out["fp32"]["time_to_tol_ms"], 2)}
     S.close()
     return out
 

@@ -183,8 +183,16 @@ static cudaError_t launch_dd_k(const DDArgs<T>& a, int grid_cap, cudaStream_t s)
   return cudaGetLastError();
 }
 
+// shared memory of k_dd_apply for NRHS right-hand sides per CTA
+template <typename T, int KIND>
+static size_t dd_apply_smem(const DDArgs<T>& a, int nrhs) {
+  using C = typename Cx<T>::t;
+  return sizeof(C) * ((size_t)nrhs * a.NCH * WTraits<KIND>::CPC + (size_t)a.G * a.NR * nrhs);
+}
+
 template <typename T, int KIND>
 static cudaError_t launch_dd_kind(const DDArgs<T>& a, int grid_cap, cudaStream_t s) {
+  if (a.nrhs >= 8 && dd_apply_smem<T, KIND>(a, 8) <= 227 * 1024) return launch_dd_k<T, KIND, 8>(a, grid_cap, s);
   if (a.nrhs >= 4) return launch_dd_k<T, KIND, 4>(a, grid_cap, s);
   if (a.nrhs >= 2) return launch_dd_k<T, KIND, 2>(a, grid_cap, s);
   return launch_dd_k<T, KIND, 1>(a, grid_cap, s);
@@ -476,7 +484,17 @@ static cudaError_t launch_dd_stream_k(const DDArgs<T>& a, int* err, int sms, cud
 }
 
 template <typename T, int KIND>
+static size_t dd_stream_smem(const DDArgs<T>& a, int nrhs) {
+  using C = typename Cx<T>::t;
+  const int cps = std::max(1, (int)((32 * 1024) / ((size_t)a.NR * 16)));
+  return 3 * (size_t)cps * a.NR * 16 + 8 * sizeof(uint64_t) +
+         sizeof(C) * ((size_t)2 * nrhs * a.NCH * WTraits<KIND>::CPC + (size_t)a.G * a.NR * nrhs);
+}
+
+template <typename T, int KIND>
 static cudaError_t launch_dd_stream_kind(const DDArgs<T>& a, int* err, int sms, cudaStream_t s) {
+  if (a.nrhs >= 8 && dd_stream_smem<T, KIND>(a, 8) <= 227 * 1024)
+    return launch_dd_stream_k<T, KIND, 8>(a, err, sms, s);
   if (a.nrhs >= 4) return launch_dd_stream_k<T, KIND, 4>(a, err, sms, s);
   if (a.nrhs >= 2) return launch_dd_stream_k<T, KIND, 2>(a, err, sms, s);
   return launch_dd_stream_k<T, KIND, 1>(a, err, sms, s);
