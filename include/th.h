@@ -339,7 +339,10 @@ th_status th_profile_read(th_ctx* ctx, int kind, double* ms, long long* launches
  *   TH_K_DD_BATCH: 1 (default when the BF16 rows fit, U box <= 128 nodes) runs
  *              the products of 8 or more right-hand sides on the tensor cores
  *              (tcgen05.mma, BF16 operands, FP32 accumulation; the residuals
- *              are rounded to BF16), 0 keeps them on the CUDA cores.
+ *              are rounded to BF16), 0 keeps them on the CUDA cores;
+ *   TH_K_COARSE_SOLVE: one-right-hand-side chunk sweep of the 2-D coarse
+ *              solve: 0 = two phases per block step (512 threads), 1 = one
+ *              cluster barrier per step (1024 threads, m_c <= 256).
  * prec selects the FP64 or the FP32-cycle kernels (TH_PREC_FP64 / TH_PREC_FP32).
  * Overriding is for testing and measurement; every variant computes the same
  * result up to summation order. */

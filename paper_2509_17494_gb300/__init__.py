@@ -286,11 +286,11 @@ class TwoGridSolver:
 
     def set_variant(self, kernel, prec, variant):
         """kernel: 'fine' | 'dd'; prec: 'fp64' | 'fp32'; variant 0 / 1 (see include/th.h)."""
-        k = {"fine": 0, "dd": 1, "dd_batch": 9}[kernel]
+        k = {"fine": 0, "dd": 1, "coarse": 6, "dd_batch": 9}[kernel]
         _check(lib().th_set_kernel_variant(self._ctx, k, PREC[prec], int(variant)), "th_set_kernel_variant")
 
     def get_variant(self, kernel, prec):
-        k = {"fine": 0, "dd": 1, "dd_batch": 9}[kernel]
+        k = {"fine": 0, "dd": 1, "coarse": 6, "dd_batch": 9}[kernel]
         v = ctypes.c_int(0)
         _check(lib().th_get_kernel_variant(self._ctx, k, PREC[prec], ctypes.byref(v)), "th_get_kernel_variant")
         return v.value

@@ -59,6 +59,7 @@ struct th_ctx {
   int tc64 = 0, tc32 = 0;  // fine-apply tile variant per precision (0 large, 1 small), autotuned
   int dds64 = 0, dds32 = 0;  // DD kernel per precision: 0 k_dd_apply, 1 k_dd_stream (autotuned)
   int dd_tc = 1;             // batched BF16 products on tensor cores (k_dd_umma) when available
+  int cs_variant = 1;        // one-rhs coarse chunk sweep: 0 two-phase, 1 one barrier per step (autotuned)
   unsigned char* Wu = nullptr;  // BF16 inverse rows in the tcgen05 operand layout (NR <= 128)
   int sms = 152;
   int* derr = nullptr;      // device flag: a bounded device wait gave up
@@ -338,6 +339,20 @@ th::FineArgs<T> fine_args(const th_ctx& x, int op) {
     a.M[i] = (T)x.ref.M[i];
     a.K[i] = (T)x.ref.K[i];
   }
+  const int H = g.p / 2, P = g.p;
+  const double* M = x.ref.M.data();
+  const double* K = x.ref.K.data();
+  for (int r = 0; r <= H; ++r)
+    for (int c = 0; c <= H; ++c) {
+      const bool mid = (c == H);
+      a.ME[r * (H + 1) + c] = (T)(mid ? M[r * np + c] : 0.5 * (M[r * np + c] + M[r * np + P - c]));
+      a.KE[r * (H + 1) + c] = (T)(mid ? K[r * np + c] : 0.5 * (K[r * np + c] + K[r * np + P - c]));
+    }
+  for (int r = 0; r < H; ++r)
+    for (int c = 0; c < H; ++c) {
+      a.MO[r * H + c] = (T)(0.5 * (M[r * np + c] - M[r * np + P - c]));
+      a.KO[r * H + c] = (T)(0.5 * (K[r * np + c] - K[r * np + P - c]));
+    }
   if constexpr (std::is_same<T, double>::value) {
     a.kc = x.kc64;
     a.ec = x.ec64;
@@ -640,6 +655,7 @@ th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th:
   a.mcr = x.mcr;
   a.rpcm = x.rpcm;
   a.nrhs = nrhs;
+  a.sweep_variant = x.cs_variant;
   if (!a.G || !a.LR) return TH_ERR_UNSUPPORTED;
   x.launches += (x.P > 1) ? 4 : 1;
   Prof prof(x, TH_K_COARSE_SOLVE, s);
@@ -812,6 +828,48 @@ th_status tune_fine(th_ctx& x, cudaStream_t s, int& choice) {
     float ms = 0;
     TH_CU(cudaEventElapsedTime(&ms, e0, e1));
     if (ms < best) { best = ms; arg = v; }
+  }
+  choice = arg;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return TH_OK;
+}
+
+// times the two one-rhs coarse sweeps (precision T) and keeps the faster
+template <typename T>
+th_status tune_coarse(th_ctx& x, cudaStream_t s, int& choice) {
+  using C = typename th::Cx<T>::t;
+  C *rc = nullptr, *uc = nullptr;
+  if constexpr (std::is_same<T, double>::value) {
+    rc = x.rc64;
+    uc = x.uc64;
+  } else {
+    rc = x.rc32;
+    uc = x.uc32;
+  }
+  if (!rc || !uc || x.g.dim != 2) return TH_OK;
+  TH_CU(cudaMemsetAsync(rc, 0, sizeof(C) * x.g.Nc, s));
+  cudaEvent_t e0, e1;
+  TH_CU(cudaEventCreate(&e0));
+  TH_CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int arg = choice;
+  for (int v = 0; v < 2; ++v) {
+    choice = v;
+    bool ok = true;
+    for (int w = 0; w < 2 && ok; ++w) ok = (coarse_solve_<T>(x, rc, uc, 1, s) == TH_OK);
+    if (!ok) {
+      cudaGetLastError();
+      continue;
+    }
+    TH_CU(cudaEventRecord(e0, s));
+    for (int k = 0; k < 4; ++k)
+      if (coarse_solve_<T>(x, rc, uc, 1, s) != TH_OK) ok = false;
+    TH_CU(cudaEventRecord(e1, s));
+    TH_CU(cudaEventSynchronize(e1));
+    float ms = 0;
+    TH_CU(cudaEventElapsedTime(&ms, e0, e1));
+    if (ok && ms < best) { best = ms; arg = v; }
   }
   choice = arg;
   cudaEventDestroy(e0);
@@ -1180,6 +1238,14 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     const int wk = (x->active != TH_PREC_FP64) ? x->active : (x->W[TH_PREC_BF16] ? TH_PREC_BF16 : TH_PREC_FP32);
     if (x->W[wk] && (st = tune_dd<float>(*x, wk, s, x->dds32)) != TH_OK) return st;
   }
+  if (!d3) {
+    // one sweep variant serves both precisions: time it where the cycle runs
+    if (x->mixed) {
+      if ((st = tune_coarse<float>(*x, s, x->cs_variant)) != TH_OK) return st;
+    } else if ((st = tune_coarse<double>(*x, s, x->cs_variant)) != TH_OK) {
+      return st;
+    }
+  }
   TH_CU(cudaStreamSynchronize(s));
   {
     int flag = 0;
@@ -1200,6 +1266,8 @@ th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
     (d ? x->dds64 : x->dds32) = variant;
   } else if (kernel == TH_K_DD_BATCH) {
     x->dd_tc = variant;
+  } else if (kernel == TH_K_COARSE_SOLVE) {
+    x->cs_variant = variant;
   } else {
     return TH_ERR_ARG;
   }
@@ -1213,6 +1281,7 @@ th_status th_get_kernel_variant(const th_ctx* x, int kernel, int prec, int* vari
   if (kernel == TH_K_FINE) *variant = d ? x->tc64 : x->tc32;
   else if (kernel == TH_K_DD) *variant = d ? x->dds64 : x->dds32;
   else if (kernel == TH_K_DD_BATCH) *variant = (x->Wu && x->dd_tc) ? 1 : 0;
+  else if (kernel == TH_K_COARSE_SOLVE) *variant = x->cs_variant;
   else return TH_ERR_ARG;
   return TH_OK;
 }

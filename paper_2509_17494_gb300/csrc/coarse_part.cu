@@ -195,6 +195,141 @@ __global__ void __launch_bounds__(512, 1) k_chunk_sweep(const CoarsePartArgs<T> 
   }
 }
 
+// Variant for m_c <= 256 with at most 32 rows per CTA: 32 warps, one row each,
+// and two barriers per block step instead of three: the vector G_j multiplies
+// is formed cooperatively (one entry per thread) and one CTA barrier separates
+// it from the products; each thread waits for its own prefetch copies before
+// the cluster barrier that ends the step, which then also makes every copy and
+// every pushed row visible to the next step.
+template <typename T, bool PREFETCH>
+__global__ void __launch_bounds__(1024, 1) k_chunk_sweep1(const CoarsePartArgs<T> a) {
+  using C = typename Cx<T>::t;
+  constexpr int NI = 8;
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank(), csz = (int)cl.num_blocks();
+  const int cid = blockIdx.x / csz;
+  const int chunk = cid % a.P, rhs = cid / a.P;
+  const int mc = a.mc, mcp = a.mcp, rpc = a.rpc;
+  const int A = a.ca[chunk], L = a.cb[chunk] - A + 1;
+  const int nsteps = 2 * L - 1;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int row0 = crank * rpc, nrow = max(0, min(rpc, mc - row0));
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* gbuf = reinterpret_cast<C*>(smraw);                    // [2][rpc * mcp] (PREFETCH)
+  C* ops = gbuf + (PREFETCH ? (size_t)2 * rpc * mcp : 0);   // [2][4][mc]: b, o0, o1, o2
+  C* full = ops + (size_t)8 * mc;                           // [2][mc]
+  C* tvs = full + 2 * mc;                                   // [mc]
+  C* zs = tvs + mc;                                         // [Lmax][rpc]: z, then y
+  const C* b = a.b + (size_t)rhs * a.Nc;
+  C* x = a.x + (size_t)rhs * a.Nc;
+  auto block_of = [&](int q) { return q < L ? A + q : A + (2 * L - 2 - q); };
+  auto prefetch = [&](int q, int buf) {
+    if (q < nsteps) {
+      const int j = block_of(q);
+      if (PREFETCH && nrow > 0) {
+        const char* src = reinterpret_cast<const char*>(a.G + ((size_t)j * mc + row0) * mcp);
+        char* dst = reinterpret_cast<char*>(gbuf + (size_t)buf * rpc * mcp);
+        const int units = (int)((size_t)nrow * mcp * sizeof(C) / 16);
+        for (int u = tid; u < units; u += nth) cp_async16(dst + (size_t)u * 16, src + (size_t)u * 16);
+      }
+      C* o = ops + (size_t)buf * 4 * mc;
+      const bool f = q < L;
+      const size_t oc = (size_t)(f ? j - 1 : j) * mc;
+      const C* r1 = f ? a.cu : a.cl;
+      const C* r2 = f ? a.cl : a.cu;
+      for (int k = tid; k < mc; k += nth) {
+        if (f) cp_async_elem(o + k, b + (size_t)j * mc + k);
+        if (!f || q > 0) {
+          cp_async_elem(o + mc + k, a.cd + oc + k);
+          cp_async_elem(o + 2 * mc + k, r1 + oc + k);
+          cp_async_elem(o + 3 * mc + k, r2 + oc + k);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  prefetch(0, 0);
+  prefetch(1, 1);
+  cp_async_wait<1>();
+  __syncthreads();
+  for (int q = 0; q < nsteps; ++q) {
+    const bool fwd = q < L;
+    const int j = block_of(q);
+    const C* prev = full + ((q - 1) & 1) * mc;
+    const C* o = ops + (size_t)(q & 1) * 4 * mc;
+    // the vector: forward b_j - C_{j-1}^T prev, backward C_j prev (one entry per thread)
+    for (int k = tid; k < mc; k += nth) {
+      C v;
+      v.x = 0;
+      v.y = 0;
+      if (!fwd || q > 0) {
+        cmac(v, o[mc + k], prev[k]);
+        if (fwd) {
+          if (k > 0) cmac(v, o[2 * mc + k - 1], prev[k - 1]);
+          if (k + 1 < mc) cmac(v, o[3 * mc + k + 1], prev[k + 1]);
+        } else {
+          if (k > 0) cmac(v, o[2 * mc + k], prev[k - 1]);
+          if (k + 1 < mc) cmac(v, o[3 * mc + k], prev[k + 1]);
+        }
+      }
+      if (fwd) {
+        const C bk = o[k];
+        v.x = bk.x - v.x;
+        v.y = bk.y - v.y;
+      }
+      tvs[k] = v;
+    }
+    __syncthreads();
+    C tv[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const int k = lane + 32 * i;
+      if (k < mc) {
+        tv[i] = tvs[k];
+      } else {
+        tv[i].x = 0;
+        tv[i].y = 0;
+      }
+    }
+    const int rr = warp;
+    if (rr < nrow) {
+      const C* g = PREFETCH ? gbuf + (size_t)(q & 1) * rpc * mcp + (size_t)rr * mcp
+                            : a.G + ((size_t)j * mc + row0 + rr) * mcp;
+      C acc;
+      acc.x = 0;
+      acc.y = 0;
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int k = lane + 32 * i;
+        if (k < mc) cmac(acc, g[k], tv[i]);
+      }
+      acc = warp_sum<T>(acc);
+      const size_t zi = (size_t)(j - A) * rpc + rr;
+      C val = acc;
+      if (!fwd) {
+        const C z = zs[zi];
+        val.x = z.x - acc.x;
+        val.y = z.y - acc.y;
+      }
+      if (lane == 0) zs[zi] = val;
+      if (lane < csz) {
+        C* remote = cl.map_shared_rank(full + (q & 1) * mc, lane);
+        remote[row0 + rr] = val;
+      }
+    }
+    cp_async_wait<0>();
+    cluster_arrive_release();
+    cluster_wait_acquire();
+    prefetch(q + 2, q & 1);
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int i = tid; i < L * nrow; i += nth) {
+    const int jj = i / nrow, rr = i - jj * nrow;
+    x[(size_t)(A + jj) * mc + row0 + rr] = zs[(size_t)jj * rpc + rr];
+  }
+}
+
 // ------------------------------------------------------------- reduced system
 // rhat_k = b_s - C_{s-1}^T y_{s-1} - C_s y_{s+1} for every separator row s = sep[k]
 template <typename T>
@@ -586,7 +721,8 @@ size_t chunk_sweep_smem(const CoarsePartArgs<T>& a, bool prefetch) {
 }
 
 template <typename K, typename Args>
-static cudaError_t launch_cluster(K kern, const Args& a, int grid, int cluster, size_t smem, cudaStream_t s) {
+static cudaError_t launch_cluster(K kern, const Args& a, int grid, int cluster, size_t smem, cudaStream_t s,
+                                  int threads = 512) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (cluster > 8) {
@@ -595,7 +731,7 @@ static cudaError_t launch_cluster(K kern, const Args& a, int grid, int cluster, 
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid, 1, 1);
-  cfg.blockDim = dim3(512, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -651,8 +787,14 @@ cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster
   }
   const bool pf = chunk_sweep_smem(a, true) <= 220 * 1024;
   const size_t sm1 = chunk_sweep_smem(a, pf);
-  cudaError_t e = pf ? launch_cluster(k_chunk_sweep<T, true>, a, cluster * a.P * nrhs, cluster, sm1, s)
-                     : launch_cluster(k_chunk_sweep<T, false>, a, cluster * a.P * nrhs, cluster, sm1, s);
+  cudaError_t e;
+  if (a.sweep_variant == 1 && a.mc <= 256 && a.rpc <= 32) {
+    e = pf ? launch_cluster(k_chunk_sweep1<T, true>, a, cluster * a.P * nrhs, cluster, sm1, s, 1024)
+           : launch_cluster(k_chunk_sweep1<T, false>, a, cluster * a.P * nrhs, cluster, sm1, s, 1024);
+  } else {
+    e = pf ? launch_cluster(k_chunk_sweep<T, true>, a, cluster * a.P * nrhs, cluster, sm1, s)
+           : launch_cluster(k_chunk_sweep<T, false>, a, cluster * a.P * nrhs, cluster, sm1, s);
+  }
   if (e != cudaSuccess || a.P < 2) return e;
   dim3 g1((unsigned)((a.nred + 255) / 256), nrhs);
   k_reduced_rhs<T><<<g1, 256, 0, s>>>(a);

@@ -49,32 +49,59 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
   }
   __syncthreads();
 
-  // phase 1: x-contractions of every row of every (extended) cell
+  // phase 1: x-contractions of every row of every (extended) cell.  M and K
+  // are centrosymmetric (GLL nodes are symmetric), so each contraction splits
+  // into an even part on s_b = u_b + u_{P-b} and an odd part on
+  // d_b = u_b - u_{P-b}: (H+1)^2 + H^2 products instead of (P+1)^2 (H = P/2).
+  constexpr int H = P / 2;
   for (int it = tid; it < CELLS * NP; it += nth) {
     const int e = it / NP, ay = it - e * NP;
     const int ecy = e / E, ecx = e - ecy * E;
     const int gcx = ex0 + ecx, gcy = ey0 + ecy;
     if (gcx < 0 || gcx >= a.n || gcy < 0 || gcy >= a.n) continue;
     const C* row = su + (ecy * P + ay) * UT + ecx * P;
-    C uv[NP];
+    C sv[H + 1], dv[H];
 #pragma unroll
-    for (int b = 0; b < NP; ++b) uv[b] = row[b];
+    for (int b = 0; b < H; ++b) {
+      const C lo = row[b], hi = row[P - b];
+      sv[b].x = lo.x + hi.x;
+      sv[b].y = lo.y + hi.y;
+      dv[b].x = lo.x - hi.x;
+      dv[b].y = lo.y - hi.y;
+    }
+    sv[H] = row[H];
+    C* o1 = s1 + (e * NP + ay) * NP;
+    C* o2 = s2 + (e * NP + ay) * NP;
 #pragma unroll
-    for (int ax = 0; ax < NP; ++ax) {
-      T mr = 0, mi = 0, kr = 0, ki = 0;
+    for (int ax = 0; ax <= H; ++ax) {
+      T pmr = 0, pmi = 0, pkr = 0, pki = 0, qmr = 0, qmi = 0, qkr = 0, qki = 0;
 #pragma unroll
-      for (int b = 0; b < NP; ++b) {
-        const T mm = a.M[ax * NP + b], kk = a.K[ax * NP + b];
-        mr += mm * uv[b].x;
-        mi += mm * uv[b].y;
-        kr += kk * uv[b].x;
-        ki += kk * uv[b].y;
+      for (int b = 0; b <= H; ++b) {
+        const T me = a.ME[ax * (H + 1) + b], ke = a.KE[ax * (H + 1) + b];
+        pmr += me * sv[b].x;
+        pmi += me * sv[b].y;
+        pkr += ke * sv[b].x;
+        pki += ke * sv[b].y;
       }
-      C t1, t2;
-      t1.x = mr; t1.y = mi;
-      t2.x = kr; t2.y = ki;
-      s1[(e * NP + ay) * NP + ax] = t1;
-      s2[(e * NP + ay) * NP + ax] = t2;
+      if (ax < H) {
+#pragma unroll
+        for (int b = 0; b < H; ++b) {
+          const T mo = a.MO[ax * H + b], ko = a.KO[ax * H + b];
+          qmr += mo * dv[b].x;
+          qmi += mo * dv[b].y;
+          qkr += ko * dv[b].x;
+          qki += ko * dv[b].y;
+        }
+        C t;
+        t.x = pmr + qmr; t.y = pmi + qmi; o1[ax] = t;
+        t.x = pmr - qmr; t.y = pmi - qmi; o1[P - ax] = t;
+        t.x = pkr + qkr; t.y = pki + qki; o2[ax] = t;
+        t.x = pkr - qkr; t.y = pki - qki; o2[P - ax] = t;
+      } else {
+        C t;
+        t.x = pmr; t.y = pmi; o1[ax] = t;
+        t.x = pkr; t.y = pki; o2[ax] = t;
+      }
     }
   }
   __syncthreads();
@@ -97,18 +124,46 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
       z[b].x = t2.x + mt.x;
       z[b].y = t2.y + mt.y;
     }
+    // y-contractions M z + K t1, split the same way
+    C zs_[H + 1], zd_[H], ts_[H + 1], td_[H];
+#pragma unroll
+    for (int b = 0; b < H; ++b) {
+      zs_[b].x = z[b].x + z[P - b].x;
+      zs_[b].y = z[b].y + z[P - b].y;
+      zd_[b].x = z[b].x - z[P - b].x;
+      zd_[b].y = z[b].y - z[P - b].y;
+      ts_[b].x = t1[b].x + t1[P - b].x;
+      ts_[b].y = t1[b].y + t1[P - b].y;
+      td_[b].x = t1[b].x - t1[P - b].x;
+      td_[b].y = t1[b].y - t1[P - b].y;
+    }
+    zs_[H] = z[H];
+    ts_[H] = t1[H];
     C yv[NP];
 #pragma unroll
-    for (int ay = 0; ay < NP; ++ay) {
-      T yr = 0, yi = 0;
+    for (int ay = 0; ay <= H; ++ay) {
+      T pr = 0, pi = 0, qr = 0, qi = 0;
 #pragma unroll
-      for (int b = 0; b < NP; ++b) {
-        const T mm = a.M[ay * NP + b], kq = a.K[ay * NP + b];
-        yr += mm * z[b].x + kq * t1[b].x;
-        yi += mm * z[b].y + kq * t1[b].y;
+      for (int b = 0; b <= H; ++b) {
+        const T me = a.ME[ay * (H + 1) + b], ke = a.KE[ay * (H + 1) + b];
+        pr += me * zs_[b].x + ke * ts_[b].x;
+        pi += me * zs_[b].y + ke * ts_[b].y;
       }
-      yv[ay].x = yr;
-      yv[ay].y = yi;
+      if (ay < H) {
+#pragma unroll
+        for (int b = 0; b < H; ++b) {
+          const T mo = a.MO[ay * H + b], ko = a.KO[ay * H + b];
+          qr += mo * zd_[b].x + ko * td_[b].x;
+          qi += mo * zd_[b].y + ko * td_[b].y;
+        }
+        yv[ay].x = pr + qr;
+        yv[ay].y = pi + qi;
+        yv[P - ay].x = pr - qr;
+        yv[P - ay].y = pi - qi;
+      } else {
+        yv[ay].x = pr;
+        yv[ay].y = pi;
+      }
     }
     // -i k h M on absorbing sides: rho * (x + i y) = k h y - i k h x
     const T kh = kk * a.h;

@@ -26,6 +26,9 @@ struct FineArgs {
   int tc;                      // tile edge in cells (0: default for p)
   T h, h2, alpha;              // alpha = shift (0 for A)
   T M[81], K[81];              // 1-D reference mass / stiffness, (p+1)^2
+  // even / odd halves (both matrices are centrosymmetric), H = p/2, 1/2 folded in:
+  // ME[a][b] = (M[a][b] + M[a][p-b]) / 2 (b < H), ME[a][H] = M[a][H]; MO[a][b] = (M[a][b] - M[a][p-b]) / 2
+  T ME[25], MO[16], KE[25], KO[16];
 };
 template <typename T>
 cudaError_t launch_fine_apply(const FineArgs<T>& a, int nrhs, cudaStream_t s);
@@ -143,6 +146,7 @@ struct CoarsePartArgs {
   int mc, mcp, P, rpc, Lmax, nred;
   int mcr, rpcm, nrhs;           // rpcm: rows per CTA of the multi-rhs sweep (even)
   int ldS;                       // row stride of Sinv (nred rounded up to even)
+  int sweep_variant;             // one-rhs chunk sweep: 0 two-phase (512 threads), 1 one barrier per step (1024)
 };
 template <typename T>
 cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster, cudaStream_t s);
