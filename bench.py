@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--learned-steps", type=int, default=400, help="training steps of the learned section (0: skip)")
     ap.add_argument("--dim3", choices=["cube10_q2_n40", "cube2_q2_n8", "none"], default="cube10_q2_n40",
                     help="3-D workload of the three-dimensional section")
+    ap.add_argument("--table1", action="store_true",
+                    help="add the parameter study of the paper's Table 1 (OPT coarsening) on the GPU")
     return ap.parse_args()
 
 
@@ -348,6 +350,8 @@ def run_native(args):
         line["learned"] = learned_section(args, dev)
     if args.dim3 != "none":
         line["dim3"] = dim3_section(args, dev, world)
+    if args.table1:
+        line["table1"] = table1_section(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_cycles)
     if rank == 0:
@@ -468,6 +472,52 @@ def dim3_section(args, dev, world):
     out["speedup_vs_fp64"] = {"cycle": round(out["fp64"]["ms_per_cycle"] / out["fp32"]["ms_per_cycle"], 2),
                               "time_to_tol": round(out["fp64"]["time_to_tol_ms"] / out["fp32"]["time_to_tol_ms"], 2)}
     S.close()
+    return out
+
+
+# The paper's Table 1 (OPT coarsening): (a) alpha_s x n_dd x subdomain size at
+# p = 4 (10 ppw) and p = 6 (8 ppw); (b) n_s x omega_c x ppw.  Its domain, Krylov
+# method and tolerance are not stated; here: unit square, constant k, Robin
+# sides, centred source, FGMRES(60) to 1e-6, p = 4 on 25^2 and p = 6 on 20^2 cells.
+TABLE1A_PAPER = {(4, 4, 1): [7, 7, 7, 7, 7], (4, 4, 2): [6, 6, 6, 6, 6], (4, 6, 1): [7, 6, 6, 6, 7],
+                 (4, 6, 2): [6, 5, 5, 6, 6], (6, 4, 1): [9, 8, 8, 8, 8], (6, 4, 2): [7, 7, 7, 7, 8],
+                 (6, 6, 1): [9, 8, 8, 8, 8], (6, 6, 2): [7, 7, 7, 7, 8]}
+TABLE1B_PAPER = {(4, 1, 1.0): [9, 7, 5], (4, 1, 0.8): [8, 6, 7], (4, 1, 0.6): [11, 11, 12],
+                 (4, 2, 1.0): [8, 6, 5], (4, 2, 0.8): [7, 6, 7], (4, 2, 0.6): [11, 11, 12],
+                 (6, 1, 1.0): [19, 8, 7, 5], (6, 1, 0.8): [16, 6, 5, 7], (6, 1, 0.6): [15, 8, 10, 11],
+                 (6, 2, 1.0): [16, 8, 7, 5], (6, 2, 0.8): [12, 5, 5, 7], (6, 2, 0.6): [11, 8, 10, 11]}
+
+
+def table1_section(dev):
+    import numpy as np
+    import torch
+
+    import paper_2509_17494_gb300 as th
+    import synth
+
+    cells = {4: 25, 6: 20}
+
+    def iters(p, ppw, **kw):
+        n = cells[p]
+        W = n * p / ppw
+        k = synth.constant_wavenumber(n, 2, W)
+        S = th.TwoGridSolver(n, p, k, None, restart=60, maxit=200, tol=1e-6, device=dev, **kw)
+        f = torch.from_numpy(synth.gaussian_source(n, p, 2)).to(dev)
+        _, info = S.solve(f, check=False)
+        S.close()
+        return info["iters"] if info["converged"] else -1
+
+    out = {"setup": "unit square, constant k, Robin sides, centred source, FGMRES(60) to 1e-6; "
+                    "p = 4 on 25^2 cells, p = 6 on 20^2 cells", "a": {}, "b": {}}
+    alphas = [0.1, 0.15, 0.2, 0.3, 0.4]
+    for (p, l_dd, n_dd), paper in TABLE1A_PAPER.items():
+        ppw = 10 if p == 4 else 8
+        got = [iters(p, ppw, alpha_s=a, l_dd=l_dd, n_dd=n_dd) for a in alphas]
+        out["a"][f"p{p}_ldd{l_dd}_ndd{n_dd}"] = {"alpha_s": alphas, "gpu": got, "paper": paper}
+    for (p, n_s, om), paper in TABLE1B_PAPER.items():
+        ppws = [8, 10, 14] if p == 4 else [6, 8, 10, 14]
+        got = [iters(p, q, alpha_s=0.2, l_dd=4, n_s=n_s, omega_c=om) for q in ppws]
+        out["b"][f"p{p}_ns{n_s}_omega{om}"] = {"ppw": ppws, "gpu": got, "paper": paper}
     return out
 
 

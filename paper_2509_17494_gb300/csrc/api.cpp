@@ -483,7 +483,7 @@ th_status dd_apply(th_ctx& x, int wkind, const typename th::Cx<T>::t* r, int nrh
   a.NC = g.NC;
   a.NCH = x.wchunks[wkind];
   a.NR = g.NR;
-  a.G = std::max(1, std::min(x.ddG, 512 / std::max(1, g.NR)));
+  a.G = std::max(1, std::min(x.ddG, 512 / std::max(1, g.NR)));  // boxes above 512 nodes: one group, 1024 threads
   a.nrhs = nrhs;
   x.launches += 1;
   Prof prof(x, TH_K_DD, s);

@@ -92,8 +92,8 @@ __device__ __forceinline__ void unpack_chunk_smem(const void* base, size_t idx, 
   }
 }
 
-template <typename T, int KIND, int NRHS>
-__global__ void __launch_bounds__(512) k_dd_apply(const DDArgs<T> a) {
+template <typename T, int KIND, int NRHS, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_dd_apply(const DDArgs<T> a) {
   using C = typename Cx<T>::t;
   constexpr int CPC = WTraits<KIND>::CPC;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -167,20 +167,28 @@ __global__ void __launch_bounds__(512) k_dd_apply(const DDArgs<T> a) {
   }
 }
 
+template <typename T, int KIND, int NRHS, int MAXT>
+static cudaError_t launch_dd_kt(const DDArgs<T>& a, int grid_cap, int threads, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_dd_apply<T, KIND, NRHS, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int gx = (grid_cap > 0 && grid_cap < a.nsub) ? grid_cap : a.nsub;
+  dim3 grid(gx, (a.nrhs + NRHS - 1) / NRHS);
+  k_dd_apply<T, KIND, NRHS, MAXT><<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// up to 512 threads (U boxes of at most 512 nodes, G column groups), or 1024
+// threads with one column group for larger boxes (e.g. 6 cells of order 6)
 template <typename T, int KIND, int NRHS>
 static cudaError_t launch_dd_k(const DDArgs<T>& a, int grid_cap, cudaStream_t s) {
   using C = typename Cx<T>::t;
   constexpr int CPC = WTraits<KIND>::CPC;
   const int threads = ((a.NR * a.G + 31) / 32) * 32;
-  if (threads > 512) return cudaErrorInvalidConfiguration;
+  if (threads > 1024) return cudaErrorInvalidConfiguration;
   const size_t smem = sizeof(C) * ((size_t)NRHS * a.NCH * CPC + (size_t)a.G * a.NR * NRHS);
-  cudaError_t e = cudaFuncSetAttribute(k_dd_apply<T, KIND, NRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  const int gx = (grid_cap > 0 && grid_cap < a.nsub) ? grid_cap : a.nsub;
-  dim3 grid(gx, (a.nrhs + NRHS - 1) / NRHS);
-  k_dd_apply<T, KIND, NRHS><<<grid, threads, smem, s>>>(a);
-  return cudaGetLastError();
+  if (threads > 512) return launch_dd_kt<T, KIND, NRHS, 1024>(a, grid_cap, threads, smem, s);
+  return launch_dd_kt<T, KIND, NRHS, 512>(a, grid_cap, threads, smem, s);
 }
 
 // shared memory of k_dd_apply for NRHS right-hand sides per CTA

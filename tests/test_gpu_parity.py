@@ -112,6 +112,20 @@ def test_smoother_fp64(th, c, n_dd, variant):
     S.device_status()
 
 
+def test_smoother_large_subdomains_fp64(th):
+    """U boxes above 512 nodes (4 cells of order 6: 25^2 = 625 rows) run the
+    1024-thread subdomain kernel."""
+    c = dict(n=9, p=6, l_dd=4, bc="robin")
+    S, P = build(th, c)
+    sm = dd.DDSmoother(P, c["l_dd"])
+    f = synth.random_complex((3, P.N), 61)
+    u = synth.random_complex((3, P.N), 62)
+    got = host(S.smooth(dev(f), dev(u.copy())))
+    want = np.stack([sm.smooth(u[i], f[i], 1) for i in range(3)])
+    assert relerr(got, want) < 1e-11
+    S.device_status()
+
+
 @pytest.mark.parametrize("c", CASES)
 @pytest.mark.parametrize("variant", [0, 1])
 def test_coarse_solve_fp64(th, c, variant):
