@@ -53,8 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cycles", type=int, default=15, help="oracle cycles in the CPU-baseline sample")
     ap.add_argument("--batch-rhs", type=int, default=64, help="right-hand sides of the batched section (0: skip)")
-    ap.add_argument("--dd-variant", choices=["auto", "0", "1"], default="auto",
-                    help="FP32 subdomain kernel: auto (set-up autotuner), 0 k_dd_apply, 1 k_dd_stream "
+    ap.add_argument("--dd-variant", choices=["auto", "0", "1", "2"], default="auto",
+                    help="FP32 subdomain kernel: auto (set-up autotuner), 0 k_dd_apply, 1 k_dd_stream, 2 k_dd_stream2 "
                          "(pin it when the same command runs under a profiler, whose serialised launches "
                          "change the autotuner's timings)")
     ap.add_argument("--fine-variant", choices=["auto", "0", "1"], default="auto",

@@ -335,7 +335,9 @@ th_status th_profile_read(th_ctx* ctx, int kind, double* ms, long long* launches
  * on the context's own problem with CUDA events):
  *   TH_K_FINE: 0 = large cell tile, 1 = small cell tile;
  *   TH_K_DD:   0 = per-subdomain CTAs with direct loads,
- *              1 = persistent CTAs streaming the rows through TMA bulk copies;
+ *              1 = persistent CTAs streaming the rows through TMA bulk copies,
+ *              2 = the same with a dedicated producer warp and per-slot
+ *                  mbarrier release (no CTA barrier per ring slot);
  *   TH_K_DD_BATCH: 1 (default when the BF16 rows fit, U box <= 128 nodes) runs
  *              the products of 8 or more right-hand sides on the tensor cores
  *              (tcgen05.mma, BF16 operands, FP32 accumulation; the residuals

@@ -320,6 +320,12 @@ __device__ __forceinline__ void cp_async_c(C* smem, const C* gmem) {
   }
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"((unsigned)__cvta_generic_to_shared(bar)) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -467,6 +473,185 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
   __syncthreads();
 }
 
+// Variant 2 of the streamed kernel: a dedicated producer warp issues the row
+// copies into a ring of `depth` slots and refills a slot when every compute
+// warp has released it (one mbarrier arrival per warp, no CTA barrier per
+// slot); the per-subdomain synchronisation uses a named barrier over the
+// compute warps only.  Smaller slots let three CTAs share an SM.
+template <typename T, int KIND, int NRHS>
+__global__ void __launch_bounds__(512, 2) k_dd_stream2(const DDArgs<T> a, int cps, int depth, int* err) {
+  using C = typename Cx<T>::t;
+  constexpr int CPC = WTraits<KIND>::CPC;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int NR = a.NR, NCH = a.NCH, G = a.G;
+  const size_t slot_bytes = (size_t)cps * NR * 16;
+  unsigned char* slots = smraw;                                              // [depth][slot_bytes]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smraw + depth * slot_bytes);  // [depth]
+  uint64_t* empty = full + 8;                                                // [depth]
+  const int XL = NCH * CPC;
+  C* xs = reinterpret_cast<C*>(full + 16);                                   // [2][NRHS][XL]
+  C* red = xs + 2 * NRHS * XL;                                               // [G][NR][NRHS]
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ncomp = blockDim.x - 32, nwc = ncomp / 32;
+  const bool producer = tid >= ncomp;
+  const int rr = tid % NR, g = tid / NR;
+  const int r0 = blockIdx.y * NRHS;
+  const int nr = min(NRHS, a.nrhs - r0);
+  const int NS = (NCH + cps - 1) / cps;
+  const int nmine = (a.nsub - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int total = nmine * NS;
+  __shared__ volatile int failed;
+  __shared__ int issued_hi;
+  if (tid == 0) {
+    failed = 0;
+    issued_hi = 0;
+    for (int d = 0; d < depth; ++d) {
+      mbar_init(full + d, 1);
+      mbar_init(empty + d, nwc);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (producer) {
+    if (lane == 0) {
+      for (int t = 0; t < total; ++t) {
+        if (t >= depth && !mbar_wait_bounded(empty + (t % depth), (unsigned)(((t / depth) - 1) & 1))) failed = 1;
+        if (failed) break;
+        const int sub = blockIdx.x + (t / NS) * gridDim.x;
+        const int s = t % NS;
+        const int ch0 = s * cps;
+        const int nch = min(cps, NCH - ch0);
+        const unsigned bytes = (unsigned)((size_t)nch * NR * 16);
+        const char* src = reinterpret_cast<const char*>(a.W) + ((size_t)sub * NCH + ch0) * NR * 16;
+        mbar_expect_tx_arrive(full + (t % depth), bytes);
+        bulk_g2s(slots + (size_t)(t % depth) * slot_bytes, src, bytes, full + (t % depth));
+        issued_hi = t + 1;
+      }
+    }
+    __syncwarp();
+  } else {
+    auto gather = [&](int i, int buf) {
+      if (i < nmine) {
+        const int sub = blockIdx.x + i * gridDim.x;
+        const int* bb = a.box + (size_t)sub * 12;
+        const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3], oz = bb[8], wz = bb[9];
+        const int L2 = a.Lw * a.Lw;
+        C* dst = xs + (size_t)buf * NRHS * XL;
+        for (int idx = tid; idx < NRHS * XL; idx += ncomp) {
+          const int k = idx / XL, c = idx - k * XL;
+          const int cz = c / L2, cr = c - cz * L2;
+          const int cy = cr / a.Lw, cx = cr - cy * a.Lw;
+          if (k < nr && c < a.NC && cx < wx && cy < wy && cz < wz) {
+            cp_async_c(dst + idx,
+                       a.r + (size_t)(r0 + k) * a.N + ((size_t)(oz + cz) * a.m + (oy + cy)) * a.m + (ox + cx));
+          } else {
+            C z;
+            z.x = 0;
+            z.y = 0;
+            dst[idx] = z;
+          }
+        }
+      }
+      cp_commit();
+    };
+    gather(0, 0);
+    int t = 0;
+    for (int i = 0; i < nmine; ++i) {
+      gather(i + 1, (i + 1) & 1);
+      cp_wait1();
+      named_sync(1, ncomp);
+      const C* xv = xs + (size_t)(i & 1) * NRHS * XL;
+      T acr[NRHS], aci[NRHS];
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) { acr[k] = 0; aci[k] = 0; }
+      for (int s = 0; s < NS; ++s, ++t) {
+        if (!failed && !mbar_wait_bounded(full + (t % depth), (unsigned)((t / depth) & 1))) failed = 1;
+        const int ch0 = s * cps, nch = min(cps, NCH - ch0);
+        const unsigned char* slot = slots + (size_t)(t % depth) * slot_bytes;
+        if (g < G && !failed) {
+          for (int ch = g; ch < nch; ch += G) {
+            T wr[CPC], wi[CPC];
+            unpack_chunk_smem<T, KIND>(slot, (size_t)ch * NR + rr, wr, wi);
+#pragma unroll
+            for (int j = 0; j < CPC; ++j) {
+              const int c = (ch0 + ch) * CPC + j;
+#pragma unroll
+              for (int k = 0; k < NRHS; ++k) {
+                const C x = xv[k * XL + c];
+                acr[k] += wr[j] * x.x - wi[j] * x.y;
+                aci[k] += wr[j] * x.y + wi[j] * x.x;
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive1(empty + (t % depth));
+      }
+      const int sub = blockIdx.x + i * gridDim.x;
+      if (g < G) {
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) {
+          C v;
+          v.x = acr[k];
+          v.y = aci[k];
+          red[((size_t)g * NR + rr) * NRHS + k] = v;
+        }
+      }
+      named_sync(1, ncomp);
+      if (tid < NR) {
+        const T sc = a.wscale ? (T)a.wscale[sub] : (T)1;
+        for (int k = 0; k < nr; ++k) {
+          T sr = 0, si = 0;
+          for (int gg = 0; gg < G; ++gg) {
+            const C v = red[((size_t)gg * NR + tid) * NRHS + k];
+            sr += v.x;
+            si += v.y;
+          }
+          C o;
+          o.x = sr * sc;
+          o.y = si * sc;
+          a.V[((size_t)(r0 + k) * a.nsub + sub) * NR + tid] = o;
+        }
+      }
+    }
+    cp_wait0();
+    __syncwarp();
+  }
+  __syncthreads();
+  if (tid == ncomp && failed) {
+    // record, then wait (bounded) for the copies that can still be in flight
+    atomicExch(err, 1);
+    for (int u = max(0, issued_hi - depth); u < issued_hi; ++u)
+      mbar_wait_bounded(full + (u % depth), (unsigned)((u / depth) & 1));
+  }
+  __syncthreads();
+}
+
+template <typename T, int KIND, int NRHS>
+static cudaError_t launch_dd_stream2_k(const DDArgs<T>& a0, int* err, int sms, cudaStream_t s) {
+  using C = typename Cx<T>::t;
+  constexpr int CPC = WTraits<KIND>::CPC;
+  if (a0.NR > 480) return cudaErrorInvalidConfiguration;
+  DDArgs<T> a = a0;  // the chunk groups shrink so that the producer warp fits in 512 threads
+  a.G = std::max(1, std::min(a0.G, (480 / 32 * 32) / a0.NR));
+  const int threads = ((a.NR * a.G + 31) / 32) * 32 + 32;
+  if (threads > 512) return cudaErrorInvalidConfiguration;
+  const int depth = 4;
+  const int cps = std::max(1, (int)((16 * 1024) / ((size_t)a.NR * 16)));
+  const size_t slot_bytes = (size_t)cps * a.NR * 16;
+  const size_t smem = depth * slot_bytes + 16 * sizeof(uint64_t) +
+                      sizeof(C) * ((size_t)2 * NRHS * a.NCH * CPC + (size_t)a.G * a.NR * NRHS);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  const int per_sm = std::max(1, std::min(3, (int)((228 * 1024) / (smem + 1024))));
+  cudaError_t e = cudaFuncSetAttribute(k_dd_stream2<T, KIND, NRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int gx = std::min(a.nsub, per_sm * sms);
+  dim3 grid(gx, (a.nrhs + NRHS - 1) / NRHS);
+  k_dd_stream2<T, KIND, NRHS><<<grid, threads, smem, s>>>(a, cps, depth, err);
+  return cudaGetLastError();
+}
+
 template <typename T, int KIND, int NRHS>
 static cudaError_t launch_dd_stream_k(const DDArgs<T>& a, int* err, int sms, cudaStream_t s) {
   using C = typename Cx<T>::t;
@@ -501,6 +686,11 @@ static size_t dd_stream_smem(const DDArgs<T>& a, int nrhs) {
 
 template <typename T, int KIND>
 static cudaError_t launch_dd_stream_kind(const DDArgs<T>& a, int* err, int sms, cudaStream_t s) {
+  if (a.stream_v2) {
+    if (a.nrhs >= 4) return launch_dd_stream2_k<T, KIND, 4>(a, err, sms, s);
+    if (a.nrhs >= 2) return launch_dd_stream2_k<T, KIND, 2>(a, err, sms, s);
+    return launch_dd_stream2_k<T, KIND, 1>(a, err, sms, s);
+  }
   if (a.nrhs >= 8 && dd_stream_smem<T, KIND>(a, 8) <= 227 * 1024)
     return launch_dd_stream_k<T, KIND, 8>(a, err, sms, s);
   if (a.nrhs >= 4) return launch_dd_stream_k<T, KIND, 4>(a, err, sms, s);

@@ -44,6 +44,7 @@ struct DDArgs {
   const float* wscale;          // per-subdomain scale (FP16 rows), or null
   long long N;
   int nsub, m, Lw, NC, NCH, NR, G, nrhs;
+  int stream_v2;                // launch_dd_stream: 1 = producer-warp variant (k_dd_stream2)
 };
 template <typename T>
 cudaError_t launch_dd_apply(const DDArgs<T>& a, int kind, int grid_cap, cudaStream_t s);
