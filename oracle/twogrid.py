@@ -6,8 +6,9 @@ Algorithm 1 (TwoGridStep): n_s smoother steps; r_c = I_P^* (f - A u);
 solve A_c u_c = r_c; u += omega_c I_P u_c; n_s smoother steps.  Used as a
 preconditioner with u = 0 on input (Section 4).  The restriction I_P^* is the
 transpose of the real prolongation (residuals are dual vectors).  The coarse
-operator is A_q of Section 3.3 and is solved directly (banded LU, LAPACK
-zgbtrf/zgbtrs, lexicographic ordering).
+operator is A_q of Section 3.3 ('opt'), or the Galerkin operator of standard
+p-type coarsening ('gal', oracle/galerkin.py), and is solved directly (banded
+LU, LAPACK zgbtrf/zgbtrs, lexicographic ordering).
 """
 from __future__ import annotations
 
@@ -16,14 +17,15 @@ import scipy.linalg.lapack as lapack
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from . import dd, fem, qsfem
+from . import dd, fem, galerkin, qsfem
 
 
 class Problem:
     """Discretised Helmholtz problem: A, A_s, A_q, I_P on the unit square."""
 
     def __init__(self, n: int, p: int, k_cell, eps_cell=None, bc="robin", dim: int = 2,
-                 alpha_s: float = 0.5, periodic: bool = False, coarse: bool = True):
+                 alpha_s: float = 0.5, periodic: bool = False, coarse: bool = True,
+                 coarse_kind: str = "qsfem", alpha_c: float = 0.0):
         self.dim, self.n, self.p = dim, n, p
         self.h = 1.0 / n
         self.k = np.asarray(k_cell, dtype=float).reshape((n,) * dim)
@@ -40,7 +42,13 @@ class Problem:
         self.N = self.A.shape[0]
         if coarse:
             self.IP = fem.prolongation(n, p, dim, periodic)
-            self.Aq = qsfem.assemble_coarse(n, p, self.k, self.eps, self.robin_sides, periodic)
+            self.coarse_kind = coarse_kind
+            if coarse_kind == "qsfem":
+                self.Aq = qsfem.assemble_coarse(n, p, self.k, self.eps, self.robin_sides, periodic)
+            elif coarse_kind == "gal":
+                self.Aq = galerkin.galerkin_coarse(self, alpha_c)
+            else:
+                raise ValueError(coarse_kind)
             self.Nc = self.Aq.shape[0]
 
 
