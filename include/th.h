@@ -97,7 +97,17 @@ typedef struct {
   int maxit;        /* FGMRES iteration limit */
   double tol;       /* relative residual target ||f - A u|| / ||f|| */
   int nrhs_max;     /* largest nrhs any later call will pass */
+  int coarse_kind;  /* TH_CK_QSFEM: the QSFEM coarse operator of Section 3.3 on the
+                       coarse grid of spacing 2h/p ('opt', the paper's method);
+                       TH_CK_GALERKIN: standard Galerkin p-type coarsening of
+                       Section 4 ('gal', the paper's comparison), A_c = I_P^T
+                       A_{alpha_c} I_P = the Q_{p/2} operator on the same mesh
+                       (2-D only; TH_ERR_UNSUPPORTED in 3-D) */
+  double alpha_c;   /* TH_CK_GALERKIN: complex shift of the coarse operator's volume
+                       term, k^2 (1 + i alpha_c) + i eps (Table 2); ignored for QSFEM */
 } th_params;
+
+enum { TH_CK_QSFEM = 0, TH_CK_GALERKIN = 1 };
 
 typedef struct {
   int iters;            /* FGMRES iterations (max over right-hand sides) */
@@ -382,6 +392,17 @@ th_status th_host_qsfem27_cell(double k, double eps, double hc, double* out);
 th_status th_host_inverse_rows(const th_mesh* mesh, const double* k_host, const double* eps_host,
                                const th_params* prm, int sub, int* box, double* out,
                                size_t out_len);
+
+/* Host-only probe of the Galerkin p-type coarse set-up (Section 4; 2-D,
+ * prm->coarse_kind ignored, prm->alpha_c used).  Writes the coarse operator as
+ * a (2q+1)^2-point stencil per coarse node, q = p/2, interleaved complex:
+ * stencil[((y mc + x) (2q+1) + dy + q) (2q+1) + dx + q] = A_c[(y, x), (y+dy, x+dx)]
+ * (stencil_len doubles, at least 2 mc^2 (2q+1)^2).  If b and x are non-NULL,
+ * also solves A_c x = b (mc^2 complex each) with the block sweep of the FP64
+ * block inverses the device solve uses.  TH_ERR_NOMEM if stencil_len is short. */
+th_status th_host_galerkin(const th_mesh* mesh, const double* k_host, const double* eps_host,
+                           const th_params* prm, double* stencil, size_t stencil_len,
+                           const double* b, double* x);
 
 #ifdef __cplusplus
 }

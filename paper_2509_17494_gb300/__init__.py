@@ -43,7 +43,11 @@ class Params(ctypes.Structure):
     _fields_ = [("alpha_s", ctypes.c_double), ("l_dd", ctypes.c_int), ("n_dd", ctypes.c_int),
                 ("n_s", ctypes.c_int), ("omega_c", ctypes.c_double), ("prec", ctypes.c_int),
                 ("prec_mask", ctypes.c_uint), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
-                ("tol", ctypes.c_double), ("nrhs_max", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("nrhs_max", ctypes.c_int), ("coarse_kind", ctypes.c_int),
+                ("alpha_c", ctypes.c_double)]
+
+
+COARSE_KIND = {"qsfem": 0, "gal": 1}   # TH_CK_QSFEM ('opt', Section 3.3), TH_CK_GALERKIN ('gal', Section 4)
 
 
 class SolveInfo(ctypes.Structure):
@@ -104,6 +108,7 @@ def lib() -> ctypes.CDLL:
         "th_host_qsfem27_cell": ([D, D, D, P], I),
         "th_host_inverse_rows": ([ctypes.POINTER(Mesh), P, P, ctypes.POINTER(Params), I, P, P,
                                   ctypes.c_size_t], I),
+        "th_host_galerkin": ([ctypes.POINTER(Mesh), P, P, ctypes.POINTER(Params), P, ctypes.c_size_t, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -131,7 +136,7 @@ def _mesh(n, p, bc, dim=2):
 
 
 def _params(alpha_s=0.5, l_dd=2, n_dd=1, n_s=1, omega_c=1.0, prec="fp64", extra_prec=(), restart=30,
-            maxit=200, tol=1e-8, nrhs_max=1):
+            maxit=200, tol=1e-8, nrhs_max=1, coarse="qsfem", alpha_c=0.0):
     q = Params()
     q.alpha_s, q.l_dd, q.n_dd, q.n_s, q.omega_c = float(alpha_s), int(l_dd), int(n_dd), int(n_s), float(omega_c)
     q.prec = PREC[prec]
@@ -140,6 +145,7 @@ def _params(alpha_s=0.5, l_dd=2, n_dd=1, n_s=1, omega_c=1.0, prec="fp64", extra_
         mask |= 1 << PREC[e]
     q.prec_mask = mask
     q.restart, q.maxit, q.tol, q.nrhs_max = int(restart), int(maxit), float(tol), int(nrhs_max)
+    q.coarse_kind, q.alpha_c = COARSE_KIND[coarse], float(alpha_c)
     return q
 
 
@@ -216,12 +222,35 @@ def host_inverse_rows(n, p, k_cell, eps_cell, sub, bc="robin", **params):
     return list(box), W, Lu, Lw
 
 
+def host_galerkin(n, p, k_cell, eps_cell=None, bc="robin", alpha_c=0.0, b=None):
+    """(stencil, x) of the host Galerkin coarse set-up: stencil[(y, x), dy + q, dx + q]
+    = A_c[(y, x), (y + dy, x + dx)], and x = A_c^{-1} b by the host block sweep if b is given."""
+    q = p // 2
+    mc = n * q + 1
+    S = 2 * q + 1
+    m, prm = _mesh(n, p, bc, 2), _params(alpha_c=alpha_c)
+    k, kp = _f64(k_cell)
+    e, ep = _f64(eps_cell if eps_cell is not None else np.zeros_like(k))
+    st = np.zeros(2 * mc * mc * S * S)
+    bp = xp = None
+    if b is not None:
+        bb = np.ascontiguousarray(np.asarray(b, dtype=np.complex128).reshape(-1))
+        xo = np.zeros(mc * mc, dtype=np.complex128)
+        bp, xp = bb.ctypes.data, xo.ctypes.data
+    _check(lib().th_host_galerkin(ctypes.byref(m), kp, ep, ctypes.byref(prm), st.ctypes.data, st.size, bp, xp),
+           "th_host_galerkin")
+    sten = (st[0::2] + 1j * st[1::2]).reshape(mc * mc, S, S)
+    return sten, (xo if b is not None else None)
+
+
 class TwoGridSolver:
     """A set-up context of the two-grid preconditioned FGMRES solver on one GPU."""
 
     def __init__(self, n, p, k_cell, eps_cell=None, bc="robin", alpha_s=0.5, l_dd=2, n_dd=1, n_s=1,
                  omega_c=1.0, prec="fp64", extra_prec=(), restart=30, maxit=200, tol=1e-8, nrhs_max=1,
-                 device=None, dim=None):
+                 device=None, dim=None, coarse="qsfem", alpha_c=0.0):
+        """coarse: 'qsfem' (the QSFEM coarse operator, the paper's 'opt') or 'gal'
+        (standard Galerkin p-type coarsening with coarse shift alpha_c, 2-D)."""
         import torch
 
         self.torch = torch
@@ -235,7 +264,9 @@ class TwoGridSolver:
         self.Nc = (self.n * self.p // 2 + 1) ** self.dim
         self.nrhs_max = int(nrhs_max)
         self._mesh = _mesh(n, p, bc, self.dim)
-        self._params = _params(alpha_s, l_dd, n_dd, n_s, omega_c, prec, extra_prec, restart, maxit, tol, nrhs_max)
+        self._params = _params(alpha_s, l_dd, n_dd, n_s, omega_c, prec, extra_prec, restart, maxit, tol, nrhs_max,
+                               coarse, alpha_c)
+        self.coarse_kind = coarse
         L = lib()
         nb = ctypes.c_size_t(0)
         _check(L.th_workspace_size(ctypes.byref(self._mesh), ctypes.byref(self._params), ctypes.byref(nb)),

@@ -117,6 +117,10 @@ struct th_ctx {
   cudaStream_t gstream = nullptr;  // private capture stream (the legacy stream cannot be captured)
   bool use_graphs = true;
   long long epoch = 0;  // bumped whenever a setting that changes the launch sequence changes
+  // Galerkin p-type coarsening (coarse_kind TH_CK_GALERKIN): stencil and block inverses
+  bool gal = false;
+  double2 *gst64 = nullptr, *gG64 = nullptr;
+  float2 *gst32 = nullptr, *gG32 = nullptr;
   // coarse correction: 0 direct solve, 1 learned corrector, 2 none; fallback count for th_solve
   int coarse_mode = 0, plain_iters = 0;
   th::UNet* unet = nullptr;
@@ -200,7 +204,18 @@ void carve_all(th_ctx& x, Carve& c) {
              ? c.take<unsigned char>((size_t)g.nsub * th::dd_umma_bytes_per_sub(g.NR, g.NC))
              : nullptr;
   const bool fp64 = has_prec(x.avail, TH_PREC_FP64);
-  x.G64 = (fp64 && !d3) ? c.take<double2>(mm * g.mc) : nullptr;
+  const bool qs = !x.gal;  // QSFEM coarse factors
+  x.G64 = (fp64 && !d3 && qs) ? c.take<double2>(mm * g.mc) : nullptr;
+  if (x.gal) {
+    const size_t S = 2 * g.q + 1;
+    const size_t gtot = (size_t)th::gal_goff(g.n, g.q, g.mc);
+    x.gst64 = c.take<double2>((size_t)g.Nc * S * S);
+    x.gG64 = fp64 ? c.take<double2>(gtot) : nullptr;
+    if (x.mixed) {
+      x.gst32 = c.take<float2>((size_t)g.Nc * S * S);
+      x.gG32 = c.take<float2>(gtot);
+    }
+  }
   if (d3) {
     x.dn64 = c.take<double2>((size_t)g.mc * mb * 9);
     x.up64 = c.take<double2>((size_t)g.mc * mb * 9);
@@ -222,7 +237,7 @@ void carve_all(th_ctx& x, Carve& c) {
   x.sep = c.take<int>(K);
   x.chunk_of = c.take<int>(g.mc);
   const size_t nred = std::max(x.nred, 1);
-  if (fp64 && !d3) {
+  if (fp64 && !d3 && qs) {
     x.Gp64 = c.take<double2>(blk * g.mc);
     x.LR64 = c.take<double2>(2 * blk * g.mc);
     x.Si64 = c.take<double2>(nred * (nred + (nred & 1)));
@@ -248,7 +263,7 @@ void carve_all(th_ctx& x, Carve& c) {
     x.cl32 = c.take<float2>(mm);
     x.cd32 = c.take<float2>(mm);
     x.cu32 = c.take<float2>(mm);
-    if (!d3) {
+    if (!d3 && qs) {
       x.Gp32 = c.take<float2>(blk * g.mc);
       x.LR32 = c.take<float2>(2 * blk * g.mc);
       x.Si32 = c.take<float2>(nred * (nred + (nred & 1)));
@@ -286,6 +301,12 @@ th_status prepare(const th_mesh* mesh, const th_params* prm, th_ctx& x) {
   x.prm = *prm;
   th_status st = th::make_geometry(*mesh, *prm, x.g);
   if (st != TH_OK) return st;
+  if (prm->coarse_kind != TH_CK_QSFEM && prm->coarse_kind != TH_CK_GALERKIN) return TH_ERR_ARG;
+  if (!std::isfinite(prm->alpha_c) || prm->alpha_c < 0.0) return TH_ERR_ARG;
+  x.gal = prm->coarse_kind == TH_CK_GALERKIN;
+  if (x.gal && x.g.dim != 2) return TH_ERR_UNSUPPORTED;
+  // block 0 of the Galerkin sweep holds its right-hand side in shared memory
+  if (x.gal && (size_t)(x.g.q + 1) * x.g.mc * 16 > 227 * 1024) return TH_ERR_UNSUPPORTED;
   if (x.g.dim == 2 && x.g.mc > 1024) return TH_ERR_UNSUPPORTED;  // coarse kernels hold two coarse rows per thread
   if (x.g.dim == 3 && (long long)x.g.mc * x.g.mc > 4096) return TH_ERR_UNSUPPORTED;  // z-slice blocks of mc^2 <= 4096
   x.avail = (prm->prec_mask & 0xFu) | (1u << prm->prec);
@@ -626,9 +647,41 @@ th_status coarse_solve3_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th
 }
 
 template <typename T>
+th::GalArgs<T> gal_args(th_ctx& x, const typename th::Cx<T>::t* in, typename th::Cx<T>::t* out, int nrhs) {
+  th::GalArgs<T> a{};
+  if constexpr (std::is_same<T, double>::value) {
+    a.st = x.gst64;
+    a.G = x.gG64;
+  } else {
+    a.st = x.gst32;
+    a.G = x.gG32;
+  }
+  a.b = in;
+  a.x = out;
+  a.Nc = x.g.Nc;
+  a.q = x.g.q;
+  a.mc = x.g.mc;
+  a.nblk = x.g.n;
+  a.nrhs = nrhs;
+  return a;
+}
+
+// Galerkin p-type coarsening: u_c = A_c^{-1} r_c by the block sweep
+template <typename T>
+th_status gal_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th::Cx<T>::t* uc, int nrhs,
+                     cudaStream_t s) {
+  const th::GalArgs<T> a = gal_args<T>(x, rc, uc, nrhs);
+  if (!a.st || !a.G) return TH_ERR_UNSUPPORTED;
+  x.launches += th::gal_solve_launches(a.nblk);
+  Prof prof(x, TH_K_COARSE_SOLVE, s);
+  return cuda_status(th::launch_gal_solve<T>(a, s));
+}
+
+template <typename T>
 th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th::Cx<T>::t* uc, int nrhs,
                         cudaStream_t s) {
   if (x.g.dim == 3) return coarse_solve3_<T>(x, rc, uc, nrhs, s);
+  if (x.gal) return gal_solve_<T>(x, rc, uc, nrhs, s);
   using B = PrecBufs<T>;
   th::CoarsePartArgs<T> a{};
   a.b = rc;
@@ -667,6 +720,13 @@ template <typename T>
 th_status coarse_apply_(th_ctx& x, const typename th::Cx<T>::t* in, typename th::Cx<T>::t* out, int nrhs,
                         cudaStream_t s) {
   using B = PrecBufs<T>;
+  if (x.gal) {
+    const th::GalArgs<T> ga = gal_args<T>(x, in, out, nrhs);
+    if (!ga.st) return TH_ERR_UNSUPPORTED;
+    x.launches += 1;
+    Prof prof(x, TH_K_COARSE_APPLY, s);
+    return cuda_status(th::launch_gal_apply<T>(ga, s));
+  }
   th::CoarseApplyArgs<T> a{};
   a.x = in;
   a.y = out;
@@ -998,7 +1058,11 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
   th::CoarseBlocks cb;
   th::CoarsePart cpart;
   th::CoarseBlocks3 cb3;
-  if (!d3) {
+  th::GalBlocks gb;
+  const bool qs2 = !d3 && !x->gal;  // 2-D QSFEM coarse level
+  if (x->gal) {
+    if ((st = th::galerkin_setup(g, k_host, eps, x->prm.alpha_c, gb)) != TH_OK) return st;
+  } else if (!d3) {
     if ((st = th::coarse_setup(g, k_host, eps, cb)) != TH_OK) return st;
     if ((st = th::coarse_partition(g, cb, x->P, cpart)) != TH_OK) return st;
   } else {
@@ -1020,11 +1084,11 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
   for (size_t i = 0; i < tt.pw.size(); ++i) pwf[i] = (float)tt.pw[i];
   for (size_t i = 0; i < tt.rw.size(); ++i) rwf[i] = (float)tt.rw[i];
   std::vector<double2> rho64;
-  if (!d3) {
+  if (qs2) {
     rho64.resize(4 * (size_t)g.nc);
     for (int sd = 0; sd < 4; ++sd)
       for (int t = 0; t < g.nc; ++t) rho64[(size_t)sd * g.nc + t] = make_double2(cb.rho[sd][t].real(), cb.rho[sd][t].imag());
-  } else {
+  } else if (d3) {
     rho64.resize(cb3.rho.size());
     for (size_t i = 0; i < cb3.rho.size(); ++i) rho64[i] = make_double2(cb3.rho[i].real(), cb3.rho[i].imag());
   }
@@ -1051,7 +1115,7 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
   if ((st = up(x->rw64, tt.rw.data(), tt.rw.size() * 8)) != TH_OK) return st;
   if ((st = up(x->ccell64, cell64.data(), cell64.size() * 16)) != TH_OK) return st;
   if ((st = up(x->crho64, rho64.data(), rho64.size() * 16)) != TH_OK) return st;
-  if (!d3) {
+  if (qs2) {
     if ((st = up(x->cl64, cl64.data(), mm * 16)) != TH_OK) return st;
     if ((st = up(x->cd64, cd64.data(), mm * 16)) != TH_OK) return st;
     if ((st = up(x->cu64, cu64.data(), mm * 16)) != TH_OK) return st;
@@ -1061,7 +1125,7 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     G64h = to2(cb.G);
     if ((st = up(x->G64, G64h.data(), G64h.size() * 16)) != TH_OK) return st;
   }
-  if (!d3) {
+  if (qs2) {
     std::vector<int> chunk_of(g.mc, -1);
     for (int c = 0; c < x->P; ++c)
       for (int j = cpart.ca[c]; j <= cpart.cb[c]; ++j) chunk_of[j] = c;
@@ -1094,6 +1158,11 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     if ((st = upload_c(x->dn64, x->dn32, cb3.dn)) != TH_OK) return st;
     if ((st = upload_c(x->up64, x->up32, cb3.up)) != TH_OK) return st;
   }
+  if (x->gal) {
+    if ((st = upload_c(x->gst64, x->gst32, gb.st)) != TH_OK) return st;
+    if ((st = upload_c(x->gG64, x->gG32, gb.G)) != TH_OK) return st;
+    std::vector<cplx>().swap(gb.G);
+  }
   if ((st = upload_c(x->Gp64, x->Gp32, cpart.G)) != TH_OK) return st;
   if (x->Gt64 || x->Gt32) {
     // G_j^T with rows padded to mcr: Gt[j][c][row] = G[j][row][c]
@@ -1107,7 +1176,7 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     if ((st = upload_c(x->Gt64, x->Gt32, gt)) != TH_OK) return st;
   }
   if ((st = upload_c(x->LR64, x->LR32, cpart.LR)) != TH_OK) return st;
-  if (x->P > 1) {
+  if (x->P > 1 && (x->Si64 || x->Si32)) {
     // rows padded to an even length (pairs of complex values per load)
     const size_t nr_ = (size_t)x->nred, ld = nr_ + (nr_ & 1);
     std::vector<cplx> sp(nr_ * ld, cplx(0.0));
@@ -1128,7 +1197,7 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     if ((st = up(x->rw32, rwf.data(), rwf.size() * 4)) != TH_OK) return st;
     if ((st = up(x->ccell32, cell32.data(), cell32.size() * 8)) != TH_OK) return st;
     if ((st = up(x->crho32, rho32.data(), rho32.size() * 8)) != TH_OK) return st;
-    if (!d3) {
+    if (qs2) {
       if ((st = up(x->cl32, cl32.data(), mm * 8)) != TH_OK) return st;
       if ((st = up(x->cd32, cd32.data(), mm * 8)) != TH_OK) return st;
       if ((st = up(x->cu32, cu32.data(), mm * 8)) != TH_OK) return st;
@@ -1239,7 +1308,7 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     const int wk = (x->active != TH_PREC_FP64) ? x->active : (x->W[TH_PREC_BF16] ? TH_PREC_BF16 : TH_PREC_FP32);
     if (x->W[wk] && (st = tune_dd<float>(*x, wk, s, x->dds32)) != TH_OK) return st;
   }
-  if (!d3) {
+  if (qs2) {
     // one sweep variant serves both precisions: time it where the cycle runs
     if (x->mixed) {
       if ((st = tune_coarse<float>(*x, s, x->cs_variant)) != TH_OK) return st;
@@ -1465,7 +1534,7 @@ th_status th_unet_init(th_ctx* x, int levels, int base, int batch_max, const flo
                        void* stream) {
   if (!x || !params || batch_max < 1 || !th::UNet::check(levels, base)) return TH_ERR_ARG;
   if (n != th::UNet::param_count(levels, base)) return TH_ERR_ARG;
-  if (x->mesh.dim != 2) return TH_ERR_UNSUPPORTED;
+  if (x->mesh.dim != 2 || x->gal) return TH_ERR_UNSUPPORTED;  // trained on the QSFEM coarse operator
   const th::Geometry& g = x->g;
   // eta = k h_c at the coarse nodes: mean over the adjacent coarse cells, each
   // of which takes the k of the fine cell containing it
@@ -1817,3 +1886,49 @@ th_status th_host_inverse_rows(const th_mesh* mesh, const double* k_host, const 
 }
 
 }  // extern "C"
+
+th_status th_host_galerkin(const th_mesh* mesh, const double* k_host, const double* eps_host,
+                           const th_params* prm, double* stencil, size_t stencil_len, const double* b, double* xo) {
+  if (!mesh || !prm || !k_host || !stencil) return TH_ERR_ARG;
+  if (mesh->dim != 2) return TH_ERR_UNSUPPORTED;
+  th::Geometry g;
+  th_status st = th::make_geometry(*mesh, *prm, g);
+  if (st != TH_OK) return st;
+  const int q = g.q, mc = g.mc, S = 2 * q + 1;
+  if (stencil_len < (size_t)2 * mc * mc * S * S) return TH_ERR_NOMEM;
+  th::GalBlocks gb;
+  if ((st = th::galerkin_setup(g, k_host, eps_host, prm->alpha_c, gb)) != TH_OK) return st;
+  std::memcpy(stencil, gb.st.data(), gb.st.size() * sizeof(cplx));
+  if (!b || !xo) return TH_OK;
+  // the device sweep's arithmetic on the host: forward x_j = G_j (b_j - L_j x_{j-1}),
+  // backward x_j -= G_j U_j x_{j+1}
+  const size_t Nc = (size_t)mc * mc;
+  std::vector<cplx> x(Nc, cplx(0.0)), t;
+  const cplx* B = reinterpret_cast<const cplx*>(b);
+  for (int dir = 0; dir < 2; ++dir)
+    for (int jj = 0; jj < g.n - dir; ++jj) {
+      const int j = dir ? g.n - 2 - jj : jj;
+      const int lo = th::gal_row_lo(j, q), hi = th::gal_row_hi(j, q), Sj = (hi - lo + 1) * mc;
+      int nlo = 0, nhi = -1;
+      if (!dir && j > 0) { nlo = th::gal_row_lo(j - 1, q); nhi = lo - 1; }
+      if (dir && j + 1 < g.n) { nlo = hi + 1; nhi = th::gal_row_hi(j + 1, q); }
+      t.assign(Sj, cplx(0.0));
+      for (int i = 0; i < Sj; ++i) {
+        const int y = lo + i / mc, xx = i % mc;
+        cplx acc = 0.0;
+        for (int dy = std::max(-q, nlo - y); dy <= std::min(q, nhi - y); ++dy)
+          for (int dx = std::max(-q, -xx); dx <= std::min(q, mc - 1 - xx); ++dx)
+            acc += gb.st[((size_t)y * mc + xx) * S * S + (dy + q) * S + dx + q] * x[(size_t)(y + dy) * mc + xx + dx];
+        t[i] = dir ? acc : B[(size_t)lo * mc + i] - acc;
+      }
+      const cplx* G = gb.G.data() + th::gal_goff(j, q, mc);
+      for (int r = 0; r < Sj; ++r) {
+        cplx v = 0.0;
+        for (int c = 0; c < Sj; ++c) v += G[(size_t)r * Sj + c] * t[c];
+        if (dir) x[(size_t)lo * mc + r] -= v;
+        else x[(size_t)lo * mc + r] = v;
+      }
+    }
+  std::memcpy(xo, x.data(), Nc * sizeof(cplx));
+  return TH_OK;
+}

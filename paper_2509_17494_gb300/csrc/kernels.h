@@ -193,6 +193,34 @@ struct Sweep3Args {
 template <typename T>
 cudaError_t launch_sweep3(const Sweep3Args<T>& a, cudaStream_t s);
 
+// ------------------------------------------ Galerkin p-type coarsening (2-D)
+// Row groups of the coarse node grid: [0, q], then [j q + 1, (j + 1) q] for
+// j = 1 .. n - 1, so that only the last row of group j couples to group j + 1.
+__host__ __device__ inline int gal_row_lo(int j, int q) { return j == 0 ? 0 : j * q + 1; }
+__host__ __device__ inline int gal_row_hi(int j, int q) { return (j + 1) * q; }
+__host__ __device__ inline int gal_group(int row, int q) { return row <= q ? 0 : (row - 1) / q; }
+// offset of block j in the concatenated inverses (block 0: ((q+1) mc)^2, the rest (q mc)^2)
+__host__ __device__ inline long long gal_goff(int j, int q, int mc) {
+  const long long s0 = (long long)(q + 1) * mc, s = (long long)q * mc;
+  return j == 0 ? 0 : s0 * s0 + (long long)(j - 1) * s * s;
+}
+template <typename T>
+struct GalArgs {
+  const typename Cx<T>::t* st;  // mc^2 x (2q+1)^2 stencil
+  const typename Cx<T>::t* G;   // block inverses
+  const typename Cx<T>::t* b;   // [rhs][Nc]
+  typename Cx<T>::t* x;         // [rhs][Nc]
+  long long Nc;
+  int q, mc, nblk, nrhs;
+};
+// y = A_c x (x = a.b, y = a.x)
+template <typename T>
+cudaError_t launch_gal_apply(const GalArgs<T>& a, cudaStream_t s);
+// x = A_c^{-1} b: block forward and backward sweeps, one launch per block step
+template <typename T>
+cudaError_t launch_gal_solve(const GalArgs<T>& a, cudaStream_t s);
+int gal_solve_launches(int nblk);
+
 // ------------------------------------------------------- vectors (K9/K10)
 cudaError_t launch_d2f(const double* in, float* out, long long n, cudaStream_t s);
 cudaError_t launch_f2d(const float* in, double* out, long long n, int accumulate, cudaStream_t s);

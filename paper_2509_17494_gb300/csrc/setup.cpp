@@ -970,8 +970,10 @@ static bool dense_inverse_par(std::vector<cplx>& S, int n, cplx* out) {
         if (best == 0.0) {
           fail.store(true);
         } else {
+          // interchange the trailing columns only: the multipliers of earlier steps
+          // stay in place, the convention band_solve applies (as LAPACK's gbtrf)
           if (pr != k)
-            for (int c = 0; c < n; ++c) std::swap(S[(size_t)k * n + c], S[(size_t)pr * n + c]);
+            for (int c = k; c < n; ++c) std::swap(S[(size_t)k * n + c], S[(size_t)pr * n + c]);
           inv_piv = 1.0 / S[(size_t)k * n + k];
         }
       }
@@ -1312,4 +1314,148 @@ th_status coarse_partition(const Geometry& g, const CoarseBlocks& cb, int P, Coa
   return TH_OK;
 }
 
+}  // namespace th
+
+namespace th {
+// ------------------------------------------------ Galerkin p-type coarsening
+// Section 4 ("Standard Galerkin p-type coarsening"): the coarse space is Q_q,
+// q = p/2, on the same mesh, in the nodal basis of the equispaced points of
+// each cell (the coarse-grid vertices, the basis the prolongation I_P of
+// Section 4.2 interpolates from), so I_P is the embedding and the coarse matrix
+// is the fine form restricted to Q_q.  With constant coefficients per cell and
+// exact integration this is, per cell e,
+//   Kq (x) Mq + Mq (x) Kq - (k_e^2 (1 + i alpha_c) + i eps_e) h^2 Mq (x) Mq
+// plus -i k_e h Mq on each Robin edge, Kq / Mq the 1-D stiffness / mass of the
+// degree-q equispaced Lagrange basis on [0, 1].
+th_status galerkin_setup(const Geometry& g, const double* k, const double* eps, double alpha_c, GalBlocks& gb) {
+  if (g.dim != 2) return TH_ERR_UNSUPPORTED;
+  const int q = g.q, mc = g.mc, n = g.n, S = 2 * q + 1, nq1 = q + 1;
+  gb.q = q;
+  gb.mc = mc;
+  gb.nblk = n;
+  // 1-D equispaced reference matrices, Gauss rule exact for degree 2q
+  std::vector<double> eq(nq1), xq, wq;
+  for (int b = 0; b <= q; ++b) eq[b] = (double)b / q;
+  gauss_rule(q + 2, xq, wq);
+  std::vector<double> Mq(nq1 * nq1, 0.0), Kq(nq1 * nq1, 0.0);
+  auto dlag = [&](int a, double x) {  // derivative of the a-th equispaced Lagrange polynomial
+    double s = 0.0;
+    for (int j = 0; j <= q; ++j) {
+      if (j == a) continue;
+      double t = 1.0 / (eq[a] - eq[j]);
+      for (int l = 0; l <= q; ++l)
+        if (l != a && l != j) t *= (x - eq[l]) / (eq[a] - eq[l]);
+      s += t;
+    }
+    return s;
+  };
+  for (int a = 0; a <= q; ++a)
+    for (int b = 0; b <= q; ++b)
+      for (size_t t = 0; t < xq.size(); ++t) {
+        Mq[a * nq1 + b] += wq[t] * lagrange_value(eq, a, xq[t]) * lagrange_value(eq, b, xq[t]);
+        Kq[a * nq1 + b] += wq[t] * dlag(a, xq[t]) * dlag(b, xq[t]);
+      }
+  // stencil: st[(y mc + x) S^2 + (dy + q) S + (dx + q)] = A_c[(y, x), (y + dy, x + dx)]
+  gb.st.assign((size_t)mc * mc * S * S, cplx(0.0));
+  auto add = [&](int ya, int xa, int yb, int xb, cplx v) {
+    gb.st[((size_t)ya * mc + xa) * S * S + (size_t)(yb - ya + q) * S + (xb - xa + q)] += v;
+  };
+  const double h = g.h;
+  for (int cy = 0; cy < n; ++cy)
+    for (int cx = 0; cx < n; ++cx) {
+      const size_t f = (size_t)cy * n + cx;
+      const double kk = k[f], ee = eps ? eps[f] : 0.0;
+      const cplx cvol(kk * kk, alpha_c * kk * kk + ee);
+      for (int ay = 0; ay <= q; ++ay)
+        for (int ax = 0; ax <= q; ++ax)
+          for (int by = 0; by <= q; ++by)
+            for (int bx = 0; bx <= q; ++bx) {
+              const double mx = Mq[ax * nq1 + bx], my = Mq[ay * nq1 + by];
+              const double kx = Kq[ax * nq1 + bx], ky = Kq[ay * nq1 + by];
+              const cplx v = cplx(kx * my + mx * ky, 0.0) - cvol * (h * h * mx * my);
+              add(cy * q + ay, cx * q + ax, cy * q + by, cx * q + bx, v);
+            }
+    }
+  for (int s = 0; s < 4; ++s) {
+    if (!g.robin[s]) continue;
+    for (int t = 0; t < n; ++t) {
+      // edge cell and the nodes along the edge: side s = 0/1 x lo/hi (nodes vary in y), 2/3 y lo/hi
+      const int cx = s < 2 ? (s == 0 ? 0 : n - 1) : t, cy = s < 2 ? t : (s == 2 ? 0 : n - 1);
+      const cplx rv(0.0, -k[(size_t)cy * n + cx] * h);
+      for (int a = 0; a <= q; ++a)
+        for (int b = 0; b <= q; ++b) {
+          const cplx v = rv * Mq[a * nq1 + b];
+          if (s < 2) {
+            const int x = s == 0 ? 0 : mc - 1;
+            add(t * q + a, x, t * q + b, x, v);
+          } else {
+            const int y = s == 2 ? 0 : mc - 1;
+            add(y, t * q + a, y, t * q + b, v);
+          }
+        }
+    }
+  }
+  // block LU over the row groups: G_j = (D_j - L_j G_{j-1} U_{j-1})^{-1}.  Only
+  // the last row of group j-1 couples to group j, so only that mc x mc corner of
+  // G_{j-1} enters the Schur complement.
+  const size_t gtot = (size_t)gal_goff(n, q, mc);
+  gb.G.assign(gtot, cplx(0.0));
+  for (int j = 0; j < n; ++j) {
+    const int lo = gal_row_lo(j, q), hi = gal_row_hi(j, q), Sj = (hi - lo + 1) * mc;
+    std::vector<cplx> D((size_t)Sj * Sj, cplx(0.0));
+    parallel_for(Sj, [&](int a) {
+      const int ya = lo + a / mc, xa = a % mc;
+      const cplx* sa = &gb.st[((size_t)ya * mc + xa) * S * S];
+      for (int dy = -q; dy <= q; ++dy) {
+        const int yb = ya + dy;
+        if (yb < lo || yb > hi) continue;
+        for (int dx = -q; dx <= q; ++dx) {
+          const int xb = xa + dx;
+          if (xb < 0 || xb >= mc) continue;
+          D[(size_t)a * Sj + (size_t)(yb - lo) * mc + xb] += sa[(dy + q) * S + dx + q];
+        }
+      }
+    });
+    if (j > 0) {
+      const int plo = gal_row_lo(j - 1, q), Sp = (gal_row_hi(j - 1, q) - plo + 1) * mc;
+      const int yl = lo - 1;  // the last row of group j-1
+      const cplx* Gp = &gb.G[(size_t)gal_goff(j - 1, q, mc)];
+      const size_t c0 = (size_t)Sp - mc;  // local index of (yl, 0) in group j-1
+      // T[a][d] = sum_c L[a][c] Gll[c][d], c, d on row yl
+      std::vector<cplx> T((size_t)Sj * mc, cplx(0.0));
+      parallel_for(Sj, [&](int a) {
+        const int ya = lo + a / mc, xa = a % mc, dy = yl - ya;
+        if (dy < -q) return;
+        const cplx* sa = &gb.st[((size_t)ya * mc + xa) * S * S];
+        for (int dx = -q; dx <= q; ++dx) {
+          const int xc = xa + dx;
+          if (xc < 0 || xc >= mc) continue;
+          const cplx l = sa[(dy + q) * S + dx + q];
+          if (l == 0.0) continue;
+          const cplx* grow = Gp + (c0 + xc) * Sp + c0;
+          for (int d = 0; d < mc; ++d) T[(size_t)a * mc + d] += l * grow[d];
+        }
+      });
+      // D[a][b] -= sum_d T[a][d] U[d][b], U[d][b] = A_c[(yl, d), b]
+      parallel_for(Sj, [&](int a) {
+        for (int d = 0; d < mc; ++d) {
+          const cplx t = T[(size_t)a * mc + d];
+          if (t == 0.0) continue;
+          const cplx* sd = &gb.st[((size_t)yl * mc + d) * S * S];
+          for (int dy = 1; dy <= q; ++dy) {
+            const int yb = yl + dy;
+            if (yb > hi) break;
+            for (int dx = -q; dx <= q; ++dx) {
+              const int xb = d + dx;
+              if (xb < 0 || xb >= mc) continue;
+              D[(size_t)a * Sj + (size_t)(yb - lo) * mc + xb] -= t * sd[(dy + q) * S + dx + q];
+            }
+          }
+        }
+      });
+    }
+    if (!dense_inverse_par(D, Sj, &gb.G[(size_t)gal_goff(j, q, mc)])) return TH_ERR_SINGULAR;
+  }
+  return TH_OK;
+}
 }  // namespace th

@@ -1,6 +1,8 @@
 // Internal declarations of the two-grid Helmholtz library (host + device).
 #pragma once
 
+#include "kernels.h"
+
 #include <complex>
 #include <cstddef>
 #include <cstdint>
@@ -93,6 +95,16 @@ struct CoarseBlocks3 {
 };
 void qsfem27_cell(double k, double eps, double hc, cplx d[4]);
 th_status coarse_setup3(const Geometry& g, const double* k, const double* eps, CoarseBlocks3& cb);
+
+// Galerkin p-type coarsening (2-D): the coarse operator as a (2q+1)^2-point
+// stencil per coarse node, and the FP64 block inverses of its block-tridiagonal
+// form over the row groups gal_row_lo(j)..gal_row_hi(j) (kernels.h).
+struct GalBlocks {
+  int q = 0, mc = 0, nblk = 0;
+  std::vector<cplx> st;  // mc^2 x (2q+1)^2
+  std::vector<cplx> G;   // block j at gal_goff(j), (rows_j mc)^2 row-major
+};
+th_status galerkin_setup(const Geometry& g, const double* k, const double* eps, double alpha_c, GalBlocks& gb);
 
 // Partitioned form of the coarse block-tridiagonal system (see coarse_partition).
 struct CoarsePart {

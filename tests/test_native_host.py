@@ -127,3 +127,40 @@ def test_workspace_size_and_argument_errors(th):
         th.workspace_size(10, 4, l_dd=0)
     with pytest.raises(th.ThError):
         th.workspace_size(10, 4, restart=0)
+
+
+def _stencil_matrix(sten, mc, q):
+    import scipy.sparse as sp
+    S = 2 * q + 1
+    rows, cols, vals = [], [], []
+    for node in range(mc * mc):
+        y, x = divmod(node, mc)
+        for a in range(S):
+            for b in range(S):
+                v = sten[node, a, b]
+                if v == 0:
+                    continue
+                yy, xx = y + a - q, x + b - q
+                assert 0 <= yy < mc and 0 <= xx < mc
+                rows.append(node)
+                cols.append(yy * mc + xx)
+                vals.append(v)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(mc * mc, mc * mc))
+
+
+@pytest.mark.parametrize("n,p,bc,alpha_c", [(5, 4, "robin", 0.0), (4, 6, {"xlo": "robin", "yhi": "robin"}, 0.05),
+                                            (3, 8, "neumann", 0.2), (6, 2, "robin", 0.02)])
+def test_galerkin_setup_matches_oracle(th, n, p, bc, alpha_c):
+    """Galerkin p-coarsening: the set-up's stencil equals I_P^T A_{alpha_c} I_P of
+    the oracle, and its block sweep solves A_c x = b."""
+    k, eps = small_case(n=n, p=p)
+    P = twogrid.Problem(n, p, k, eps, bc=oracle_bc(bc), coarse_kind="gal", alpha_c=alpha_c)
+    q = p // 2
+    mc = n * q + 1
+    b = synth.random_complex(mc * mc, 8)
+    sten, x = th.host_galerkin(n, p, k.reshape(-1), eps.reshape(-1), bc=bc, alpha_c=alpha_c, b=b)
+    A = _stencil_matrix(sten, mc, q)
+    assert abs(A - P.Aq).max() <= 1e-12 * abs(P.Aq).max()
+    import scipy.sparse.linalg as spla
+    want = spla.spsolve(P.Aq.tocsc(), b)
+    assert np.abs(x - want).max() <= 1e-9 * np.abs(want).max()
