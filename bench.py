@@ -64,6 +64,12 @@ def parse():
                     help="3-D workload of the three-dimensional section")
     ap.add_argument("--table1", action="store_true",
                     help="add the parameter study of the paper's Table 1 (OPT coarsening) on the GPU")
+    ap.add_argument("--gal", choices=["workload", "none"], default="workload",
+                    help="standard Galerkin p-coarsening ('gal') against QSFEM ('opt') on the bench workload")
+    ap.add_argument("--gal-sweep", action="store_true",
+                    help="add iterations vs problem size for opt and gal (the trend of the paper's Fig. 5)")
+    ap.add_argument("--table2", action="store_true",
+                    help="add the shift study of the paper's Table 2 (gal coarsening, p = 6) on the GPU")
     return ap.parse_args()
 
 
@@ -352,6 +358,12 @@ def run_native(args):
         line["dim3"] = dim3_section(args, dev, world)
     if args.table1:
         line["table1"] = table1_section(dev)
+    if args.gal != "none":
+        line["galerkin"] = galerkin_section(args, w, dev)
+    if args.gal_sweep:
+        line["gal_sweep"] = gal_sweep_section(dev)
+    if args.table2:
+        line["table2"] = table2_section(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_cycles)
     if rank == 0:
@@ -518,6 +530,133 @@ def table1_section(dev):
         ppws = [8, 10, 14] if p == 4 else [6, 8, 10, 14]
         got = [iters(p, q, alpha_s=0.2, l_dd=4, n_s=n_s, omega_c=om) for q in ppws]
         out["b"][f"p{p}_ns{n_s}_omega{om}"] = {"ppw": ppws, "gpu": got, "paper": paper}
+    return out
+
+
+def galerkin_section(args, w, dev):
+    """The paper's comparison method on the bench workload: standard Galerkin
+    p-type coarsening (coarse Q_{p/2} on the same mesh, its block-sweep solve),
+    with the shifts the paper uses for its size study (alpha_s = alpha_c = 0.02)
+    and without coarse correction, against the QSFEM coarse level ('opt'), all
+    in the mixed form (FP32 cycle, BF16 rows, FP64 FGMRES)."""
+    import numpy as np
+    import torch
+
+    import paper_2509_17494_gb300 as th
+
+    f = torch.from_numpy(np.ascontiguousarray(w["f"] if w["f"].ndim == 1 else w["f"][0])).to(dev)
+    out = {"setup": "bench workload, mixed precision, FGMRES(30) to 1e-8, at most 300 iterations"}
+
+    def run(label, coarse, alpha_s, alpha_c=0.0, none=False):
+        t0 = time.time()
+        S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=alpha_s, l_dd=w["l_dd"], prec="bf16",
+                             extra_prec=("fp64",), restart=30, maxit=300, tol=1e-8, device=dev, coarse=coarse,
+                             alpha_c=alpha_c)
+        setup = time.time() - t0
+        if none:
+            S.set_coarse("none")
+        u = torch.zeros_like(f)
+        for _ in range(3):
+            S.cycle_graph(f, u)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            S.cycle_graph(f, u)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / 10
+        best = None
+        for _ in range(2):
+            _, info = S.solve(f, check=False)
+            best = info if best is None or info["ms_total"] < best["ms_total"] else best
+        S.device_status()
+        S.close()
+        out[label] = {"alpha_s": alpha_s, "alpha_c": alpha_c if coarse == "gal" else None,
+                      "iters": best["iters"], "converged": best["converged"], "relres": best["relres_max"],
+                      "time_to_tol_ms": round(best["ms_total"], 2), "cycle_ms": round(ms, 4),
+                      "setup_s": round(setup, 2)}
+
+    run("opt", "qsfem", w["alpha_s"])
+    run("gal", "gal", 0.02, 0.02)
+    run("gal_noCGC", "gal", 0.02, 0.02, none=True)
+    return out
+
+
+def gal_sweep_section(dev):
+    """Iterations vs problem size at 8 points per wavelength (constant k, Robin
+    sides, centred source, FGMRES(60) to 1e-6, Q4, 4 x 4-cell subdomains): QSFEM
+    ('opt', alpha_s = 0.2) against Galerkin ('gal', alpha_s = alpha_c = 0.02)
+    and Galerkin without coarse correction."""
+    import torch
+
+    import paper_2509_17494_gb300 as th
+    import synth
+
+    p, ppw, l_dd = 4, 8, 4
+    out = {"setup": "unit square, constant k, Robin sides, centred source, Q4, 8 ppw, l_dd = 4, "
+                    "FGMRES(60) to 1e-6", "wavelengths": [], "opt": [], "gal": [], "gal_noCGC": []}
+    for W in (5, 10, 20, 40):
+        n = int(round(W * ppw / p))
+        k = synth.constant_wavenumber(n, 2, W)
+        f = torch.from_numpy(synth.gaussian_source(n, p, 2)).to(dev)
+        out["wavelengths"].append(W)
+        for label, kw, none in (("opt", dict(alpha_s=0.2), False),
+                                ("gal", dict(alpha_s=0.02, coarse="gal", alpha_c=0.02), False),
+                                ("gal_noCGC", dict(alpha_s=0.02, coarse="gal", alpha_c=0.02), True)):
+            S = th.TwoGridSolver(n, p, k, None, l_dd=l_dd, restart=60, maxit=400, tol=1e-6, device=dev, **kw)
+            if none:
+                S.set_coarse("none")
+            _, info = S.solve(f, check=False)
+            S.close()
+            out[label].append(info["iters"] if info["converged"] else -1)
+    return out
+
+
+# Table 2 of the paper: FGMRES iterations with 'gal' coarsening, p = 6, rows
+# alpha_c = 0, 0.01, 0.02, 0.05, 0.1, 0.2, 0.5 and no coarse correction, columns
+# alpha_s = 0.01, 0.02, 0.05, 0.1 (-1 stands for "> 200").
+TABLE2_PAPER = {
+    6: [[-1, -1, 110, -1], [-1, -1, 61, 102], [-1, 177, 46, 73], [-1, 30, 31, 47], [35, 21, 25, 35],
+        [21, 19, 21, 29], [21, 20, 22, 25], [23, 22, 24, 29]],
+    8: [[15, 15, 14, 15], [14, 14, 14, 14], [14, 13, 13, 14], [15, 15, 15, 16], [18, 18, 18, 19],
+        [22, 21, 21, 23], [25, 24, 25, 28], [29, 27, 28, 32]],
+}
+
+
+def table2_section(dev):
+    """The shift study of the paper's Table 2 with our kernels: 'gal' coarsening,
+    p = 6, 6 and 8 points per wavelength, alpha_s x alpha_c.  The paper does not
+    state the domain size; here 20 x 20 cells (121^2 dofs: 20 / 15 wavelengths),
+    constant k, Robin sides, centred source, 4 x 4-cell subdomains (the paper's
+    ~40-dof subdomains exceed the subdomain kernels' 1024-row limit at p = 6),
+    FGMRES(60) to 1e-6, at most 200 iterations (-1 = not converged)."""
+    import torch
+
+    import paper_2509_17494_gb300 as th
+    import synth
+
+    p, n, l_dd = 6, 20, 4
+    a_s = [0.01, 0.02, 0.05, 0.1]
+    a_c = [0.0, 0.01, 0.02, 0.05, 0.1, 0.2, 0.5, None]   # None: no coarse-grid correction
+    out = {"setup": "20^2 cells, p = 6, constant k, Robin sides, centred source, l_dd = 4, FGMRES(60) to 1e-6",
+           "alpha_s": a_s, "alpha_c": ["noCGC" if c is None else c for c in a_c]}
+    f = torch.from_numpy(synth.gaussian_source(n, p, 2)).to(dev)
+    for ppw in (6, 8):
+        k = synth.constant_wavenumber(n, 2, n * p / ppw)
+        rows = []
+        for c in a_c:
+            row = []
+            for s in a_s:
+                S = th.TwoGridSolver(n, p, k, None, alpha_s=s, l_dd=l_dd, restart=60, maxit=200, tol=1e-6, device=dev,
+                                     coarse="gal", alpha_c=0.0 if c is None else c)
+                if c is None:
+                    S.set_coarse("none")
+                _, info = S.solve(f, check=False)
+                S.close()
+                row.append(info["iters"] if info["converged"] else -1)
+            rows.append(row)
+        out[f"ppw{ppw}"] = {"gpu": rows, "paper": TABLE2_PAPER[ppw]}
     return out
 
 

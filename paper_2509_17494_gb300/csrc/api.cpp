@@ -745,11 +745,14 @@ th_status coarse_apply_(th_ctx& x, const typename th::Cx<T>::t* in, typename th:
 template <typename T>
 th_status coarse_correct_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th::Cx<T>::t* uc, int nrhs,
                           cudaStream_t s) {
-  if (x.coarse_mode == 0 || !x.unet) return coarse_solve_<T>(x, rc, uc, nrhs, s);
+  if (x.coarse_mode == 0) return coarse_solve_<T>(x, rc, uc, nrhs, s);
+  if (x.coarse_mode == 2) {  // no coarse-grid correction: u_c = 0
+    Prof prof(x, TH_K_COARSE_SOLVE, s);
+    return cuda_status(cudaMemsetAsync(uc, 0, sizeof(typename th::Cx<T>::t) * x.g.Nc * (size_t)nrhs, s));
+  }
+  if (!x.unet) return TH_ERR_UNSUPPORTED;
   x.launches += x.unet->launches_per_forward();
   Prof prof(x, TH_K_COARSE_SOLVE, s);
-  if (x.coarse_mode == 2)
-    return cuda_status(cudaMemsetAsync(uc, 0, sizeof(typename th::Cx<T>::t) * x.g.Nc * (size_t)nrhs, s));
   return cuda_status(x.unet->correct<typename th::Cx<T>::t>(rc, uc, x.g.Nc, nrhs, s));
 }
 
