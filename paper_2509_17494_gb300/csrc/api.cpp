@@ -1711,18 +1711,33 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
       }
       if (st != TH_OK) return st;
       if ((st = fine_apply<double>(*x, TH_OP_A, Zj, nullptr, x->w, nrhs, s)) != TH_OK) return st;
-      // classical Gram-Schmidt, twice
-      x->launches += 6;
+      // classical Gram-Schmidt, one pass, with a second pass only after severe
+      // cancellation, ||w - V h1|| < 1e-2 ||w|| for some rhs (the loss of
+      // orthogonality of one pass grows like eps (||w|| / ||w - V h1||)^2; with
+      // the two-grid preconditioner the ratio stays near 3).  FP64 arithmetic
+      // is scarce on this GPU: the single pass halves the Arnoldi step's work.
+      x->launches += 3;
       {
         Prof prof(*x, TH_K_KRYLOV, s);
-        TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, nrhs, x->dpart, x->h1, x->nblk, s));
-        TH_CU(th::launch_maxpy(x->Vk, vstride, x->h1, j + 1, x->w, N, j + 1, nrhs, -1.0, s));
-        TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, nrhs, x->dpart, x->h2, x->nblk, s));
-        TH_CU(th::launch_maxpy(x->Vk, vstride, x->h2, j + 1, x->w, N, j + 1, nrhs, -1.0, s));
+        TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, s));
+        TH_CU(th::launch_maxpy(x->Vk, vstride, x->h1, j + 2, x->w, N, j + 1, nrhs, -1.0, s));
       }
-      TH_CU(cudaMemcpyAsync(hh1.data(), x->h1, sizeof(double2) * (j + 1) * nrhs, cudaMemcpyDeviceToHost, s));
-      TH_CU(cudaMemcpyAsync(hh2.data(), x->h2, sizeof(double2) * (j + 1) * nrhs, cudaMemcpyDeviceToHost, s));
+      TH_CU(cudaMemcpyAsync(hh1.data(), x->h1, sizeof(double2) * (j + 2) * nrhs, cudaMemcpyDeviceToHost, s));
       if ((st = norms(*x, x->w, nrhs, hn, s)) != TH_OK) return st;
+      bool reorth = false;
+      for (int r = 0; r < nrhs; ++r)
+        if (active[r] && hn[r] * hn[r] < 1e-4 * hh1[(size_t)r * (j + 2) + j + 1].x) reorth = true;
+      std::fill(hh2.begin(), hh2.begin() + (size_t)(j + 1) * nrhs, make_double2(0.0, 0.0));
+      if (reorth) {
+        x->launches += 3;
+        {
+          Prof prof(*x, TH_K_KRYLOV, s);
+          TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, 0, nrhs, x->dpart, x->h2, x->nblk, s));
+          TH_CU(th::launch_maxpy(x->Vk, vstride, x->h2, j + 1, x->w, N, j + 1, nrhs, -1.0, s));
+        }
+        TH_CU(cudaMemcpyAsync(hh2.data(), x->h2, sizeof(double2) * (j + 1) * nrhs, cudaMemcpyDeviceToHost, s));
+        if ((st = norms(*x, x->w, nrhs, hn, s)) != TH_OK) return st;
+      }
       for (int r = 0; r < nrhs; ++r) {
         if (!std::isfinite(hn[r])) return TH_ERR_NONFINITE;
         scal[r] = (active[r] && hn[r] > 0.0) ? 1.0 / hn[r] : 0.0;
@@ -1737,7 +1752,7 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
         if (!active[r]) continue;
         cplx* Hc = &H[((size_t)r * (m + 1)) * m];  // column-major (m+1) x m: Hc[i + j (m+1)]
         for (int i = 0; i <= j; ++i) {
-          const double2 a1 = hh1[(size_t)r * (j + 1) + i], a2 = hh2[(size_t)r * (j + 1) + i];
+          const double2 a1 = hh1[(size_t)r * (j + 2) + i], a2 = hh2[(size_t)r * (j + 1) + i];
           Hc[i + (size_t)j * (m + 1)] = cplx(a1.x + a2.x, a1.y + a2.y);
         }
         Hc[j + 1 + (size_t)j * (m + 1)] = hn[r];

@@ -231,11 +231,12 @@ cudaError_t launch_zaxpy(const typename Cx<T>::t* x, typename Cx<T>::t* y, T alp
 template <typename T>
 cudaError_t launch_zero(typename Cx<T>::t* x, long long n, cudaStream_t s);
 
-// multi-dot: h[rhs][i] = sum_n conj(V_i[rhs][n]) w[rhs][n], i = 0..nv-1, V_i at Vbase + i*vstride.
-// partial sums in `part` ([rhs][nv][nblk]) then a fixed-order reduction.
+// multi-dot: h[rhs][i] = sum_n conj(V_i[rhs][n]) w[rhs][n], i = 0..nv-1, V_i at Vbase + i*vstride;
+// self = 1 appends h[rhs][nv] = ||w[rhs]||^2 (row stride nv + self).  Partial sums in `part`
+// ([rhs][nv + self][nblk]) then a fixed-order reduction.
 int mdot_blocks(long long N);
 cudaError_t launch_mdot(const double2* Vbase, long long vstride, const double2* w, long long N,
-                        int nv, int nrhs, double2* part, double2* h, int nblk, cudaStream_t s);
+                        int nv, int self, int nrhs, double2* part, double2* h, int nblk, cudaStream_t s);
 // w[rhs] -= sum_i h[rhs][i] V_i[rhs]  (sign = -1) or += (sign = +1)
 cudaError_t launch_maxpy(const double2* Vbase, long long vstride, const double2* h, int hstride,
                          double2* w, long long N, int nv, int nrhs, double sign, cudaStream_t s);

@@ -215,12 +215,14 @@ int mdot_blocks(long long N) {
   return (int)(b > 256 ? 256 : (b < 1 ? 1 : b));
 }
 
-// part[(rhs * nv + i) * nblk + blk] = sum over this block's range of conj(V_i) w
+// part[(rhs * nvt + i) * nblk + blk] = sum over this block's range of conj(V_i) w,
+// i < nvt = nv + self; index nv (self = 1) is w itself, giving ||w||^2.
 __global__ void __launch_bounds__(256) k_mdot_part(const double2* __restrict__ Vb, long long vstride,
-                                                   const double2* __restrict__ w, long long N, int nv,
+                                                   const double2* __restrict__ w, long long N, int nv, int self,
                                                    double2* __restrict__ part, int nblk) {
+  const int nvt = nv + self;
   const int rhs = blockIdx.z, i0 = blockIdx.y * kDotTile;
-  const int ni = min(kDotTile, nv - i0);
+  const int ni = min(kDotTile, nvt - i0);
   const long long chunk = (N + nblk - 1) / nblk;
   const long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
   const double2* wr = w + (size_t)rhs * N;
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(256) k_mdot_part(const double2* __restrict__ V
 #pragma unroll
     for (int t = 0; t < kDotTile; ++t) {
       if (t < ni) {
-        const double2 v = Vb[(size_t)(i0 + t) * vstride + (size_t)rhs * N + n];
+        const double2 v = (i0 + t < nv) ? Vb[(size_t)(i0 + t) * vstride + (size_t)rhs * N + n] : wv;
         ar[t] += v.x * wv.x + v.y * wv.y;
         ai[t] += v.x * wv.y - v.y * wv.x;
       }
@@ -259,34 +261,43 @@ __global__ void __launch_bounds__(256) k_mdot_part(const double2* __restrict__ V
     double2 o;
     o.x = sh[0][threadIdx.x][0];
     o.y = sh[1][threadIdx.x][0];
-    part[((size_t)rhs * nv + i0 + threadIdx.x) * nblk + blockIdx.x] = o;
+    part[((size_t)rhs * nvt + i0 + threadIdx.x) * nblk + blockIdx.x] = o;
   }
 }
 
-// h[rhs * nv + i] = sum over blocks (fixed order)
+// h[idx] = sum over blocks of part[idx][b]: one warp per output, lane l takes
+// blocks l, l + 32, ..., then a fixed shuffle tree (the same order every call)
 __global__ void k_mdot_final(const double2* __restrict__ part, int nblk, int total, double2* __restrict__ h) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (idx >= total) return;  // uniform over the warp
   double sr = 0, si = 0;
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = lane; b < nblk; b += 32) {
     const double2 v = part[(size_t)idx * nblk + b];
     sr += v.x;
     si += v.y;
   }
-  double2 o;
-  o.x = sr;
-  o.y = si;
-  h[idx] = o;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if (lane == 0) {
+    double2 o;
+    o.x = sr;
+    o.y = si;
+    h[idx] = o;
+  }
 }
 
-cudaError_t launch_mdot(const double2* Vbase, long long vstride, const double2* w, long long N, int nv, int nrhs,
-                        double2* part, double2* h, int nblk, cudaStream_t s) {
-  dim3 grid(nblk, (nv + kDotTile - 1) / kDotTile, nrhs);
-  k_mdot_part<<<grid, 256, 0, s>>>(Vbase, vstride, w, N, nv, part, nblk);
+cudaError_t launch_mdot(const double2* Vbase, long long vstride, const double2* w, long long N, int nv, int self,
+                        int nrhs, double2* part, double2* h, int nblk, cudaStream_t s) {
+  const int nvt = nv + (self ? 1 : 0);
+  dim3 grid(nblk, (nvt + kDotTile - 1) / kDotTile, nrhs);
+  k_mdot_part<<<grid, 256, 0, s>>>(Vbase, vstride, w, N, nv, self ? 1 : 0, part, nblk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int total = nv * nrhs;
-  k_mdot_final<<<(total + 127) / 128, 128, 0, s>>>(part, nblk, total, h);
+  const int total = nvt * nrhs;
+  k_mdot_final<<<(total + 3) / 4, 128, 0, s>>>(part, nblk, total, h);
   return cudaGetLastError();
 }
 
@@ -340,12 +351,15 @@ __global__ void __launch_bounds__(256) k_norm_part(const double2* __restrict__ w
   if (threadIdx.x == 0) part[(size_t)rhs * nblk + blockIdx.x] = sh[0];
 }
 
+// one warp per right-hand side, fixed lane / shuffle order (see k_mdot_final)
 __global__ void k_norm_final(const double* part, int nblk, int nrhs, double* out) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (r >= nrhs) return;
   double s = 0;
-  for (int b = 0; b < nblk; ++b) s += part[(size_t)r * nblk + b];
-  out[r] = s;
+  for (int b = lane; b < nblk; b += 32) s += part[(size_t)r * nblk + b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[r] = s;
 }
 
 cudaError_t launch_norm2(const double2* w, long long N, int nrhs, double* part, double* out, int nblk,
@@ -354,7 +368,7 @@ cudaError_t launch_norm2(const double2* w, long long N, int nrhs, double* part, 
   k_norm_part<<<grid, 256, 0, s>>>(w, N, part, nblk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_norm_final<<<(nrhs + 127) / 128, 128, 0, s>>>(part, nblk, nrhs, out);
+  k_norm_final<<<(nrhs + 3) / 4, 128, 0, s>>>(part, nblk, nrhs, out);
   return cudaGetLastError();
 }
 
