@@ -326,8 +326,9 @@ def run_native(args):
                    "coarse_dofs": S.Nc, "wavelengths": 40, "alpha_s": w["alpha_s"], "l_dd": w["l_dd"],
                    "n_s": 1, "n_dd": 1, "omega_c": 1.0, "nrhs": 1,
                    "precision": "FP32 cycle, BF16 inverse rows (FP32 accumulate), FP64 FGMRES",
-                   "step": "one TwoGridStep u <- TwoGridStep(u, f) replayed from a CUDA graph: FP64 residual, "
-                           "2 DD smoothers, FP32 residual, restriction, coarse block solve, prolongation",
+                   "step": "one TwoGridStep u <- TwoGridStep(u, f) replayed from a CUDA graph: outer residual of the "
+                           "FP64 iterate in double-single arithmetic (FP32 output), 2 DD smoothers, FP32 "
+                           "residual, restriction, coarse block solve, prolongation, FP64 update",
                    "l2": "inputs larger than L2: the BF16 inverse rows streamed every smoother step are "
                          f"{alg_bytes / 1e6:.0f} MB > 129 MB",
                    "setup_s": round(setup_s, 2), "parallelism": f"replicas x{world}"},

@@ -167,6 +167,16 @@ th_status th_apply(th_ctx* ctx, int op, const double* x_dev, double* y_dev,
 th_status th_residual(th_ctx* ctx, const double* f_dev, const double* u_dev,
                       double* r_dev, int nrhs, void* stream);
 
+/* The mixed form's outer residual (the first step of th_cycle and th_smooth
+ * when the active precision is not FP64): r = f - A u for FP64 f, u (layout as
+ * th_residual), delivered rounded to FP32 in r (nrhs x N complex floats,
+ * interleaved).  2-D: one kernel in double-single arithmetic (pairs of floats,
+ * 48 significant bits; FP64 arithmetic is the scarce unit on this GPU), so r
+ * carries the cancellation f - A u as the FP64 residual would; 3-D, or with
+ * th_set_kernel_variant(TH_K_RESID, ., 0): the FP64 apply, then rounding.
+ * TH_ERR_UNSUPPORTED when no FP32-cycle precision was prepared. */
+th_status th_residual_mixed(th_ctx* ctx, const double* f, const double* u, float* r, int nrhs, void* stream);
+
 /* One CSDDSmoother(u, f) step of Algorithm 2 in the active precision:
  * r = f - A u; v = 0; n_dd times DDStep(v, r; A_s); u += v.  Updates u. */
 th_status th_smooth(th_ctx* ctx, const double* f_dev, double* u_dev, int nrhs, void* stream);
@@ -328,7 +338,8 @@ enum {
   TH_K_VECTOR = 7,      /* precision conversions, axpy, zero fill (K10) */
   TH_K_KRYLOV = 8,      /* FGMRES dots, norms, updates (K9) */
   TH_K_COUNT = 9,
-  TH_K_DD_BATCH = 9     /* (variants only) batched BF16 subdomain products: 0 CUDA cores, 1 tensor cores */
+  TH_K_DD_BATCH = 9,    /* (variants only) batched BF16 subdomain products: 0 CUDA cores, 1 tensor cores */
+  TH_K_RESID = 10       /* (variants only) the mixed form's outer residual, see th_residual_mixed */
 };
 
 /* Per-kernel timing for measurement: with enable = 1 every later kernel
@@ -352,6 +363,8 @@ th_status th_profile_read(th_ctx* ctx, int kind, double* ms, long long* launches
  *              the products of 8 or more right-hand sides on the tensor cores
  *              (tcgen05.mma, BF16 operands, FP32 accumulation; the residuals
  *              are rounded to BF16), 0 keeps them on the CUDA cores;
+ *   TH_K_RESID: 1 (default) double-single residual kernel, 0 FP64 apply and
+ *              rounding (th_residual_mixed; prec is ignored);
  *   TH_K_COARSE_SOLVE: one-right-hand-side chunk sweep of the 2-D coarse
  *              solve: 0 = two phases per block step (512 threads), 1 = one
  *              cluster barrier per step (1024 threads, m_c <= 256).

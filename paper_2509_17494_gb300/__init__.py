@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
         "th_destroy": ([P], V),
         "th_apply": ([P, I, P, P, I, I, P], I),
         "th_residual": ([P, P, P, P, I, P], I),
+        "th_residual_mixed": ([P, P, P, P, I, P], I),
         "th_smooth": ([P, P, P, I, P], I),
         "th_restrict": ([P, P, P, I, P], I),
         "th_prolong": ([P, P, P, D, I, P], I),
@@ -317,11 +318,11 @@ class TwoGridSolver:
 
     def set_variant(self, kernel, prec, variant):
         """kernel: 'fine' | 'dd' | 'coarse' | 'dd_batch'; prec: 'fp64' | 'fp32'; variant 0 / 1 ('dd' also 2); see include/th.h."""
-        k = {"fine": 0, "dd": 1, "coarse": 6, "dd_batch": 9}[kernel]
+        k = {"fine": 0, "dd": 1, "coarse": 6, "dd_batch": 9, "resid": 10}[kernel]
         _check(lib().th_set_kernel_variant(self._ctx, k, PREC[prec], int(variant)), "th_set_kernel_variant")
 
     def get_variant(self, kernel, prec):
-        k = {"fine": 0, "dd": 1, "coarse": 6, "dd_batch": 9}[kernel]
+        k = {"fine": 0, "dd": 1, "coarse": 6, "dd_batch": 9, "resid": 10}[kernel]
         v = ctypes.c_int(0)
         _check(lib().th_get_kernel_variant(self._ctx, k, PREC[prec], ctypes.byref(v)), "th_get_kernel_variant")
         return v.value
@@ -365,6 +366,15 @@ class TwoGridSolver:
         r = out if out is not None else self.torch.empty_like(f)
         _check(lib().th_residual(self._ctx, f.data_ptr(), u.data_ptr(), r.data_ptr(), nrhs, self._stream()),
                "th_residual")
+        return r
+
+    def residual_mixed(self, f, u, out=None):
+        """The mixed form's outer residual f - A u, rounded to FP32 (complex64 tensor)."""
+        nrhs = self._vec(f, self.N, "f")
+        self._vec(u, self.N, "u")
+        r = out if out is not None else self.torch.empty(f.shape, dtype=self.torch.complex64, device=self.device)
+        _check(lib().th_residual_mixed(self._ctx, f.data_ptr(), u.data_ptr(), r.data_ptr(), nrhs, self._stream()),
+               "th_residual_mixed")
         return r
 
     def smooth(self, f, u):

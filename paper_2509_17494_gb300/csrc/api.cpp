@@ -66,6 +66,8 @@ struct th_ctx {
   // device arrays
   double *kc64 = nullptr, *ec64 = nullptr;
   float *kc32 = nullptr, *ec32 = nullptr;
+  th::ds *kcds = nullptr, *ecds = nullptr;  // k, eps per cell in double-single (mixed form, 2-D)
+  int resid_ds = 1;  // mixed form's outer residual: 1 double-single apply to FP32, 0 FP64 apply + rounding
   int* box = nullptr;
   int4* ctab = nullptr;
   void* W[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -256,6 +258,10 @@ void carve_all(th_ctx& x, Carve& c) {
   if (x.mixed) {
     x.kc32 = c.take<float>(n2);
     x.ec32 = c.take<float>(n2);
+    if (!d3) {
+      x.kcds = c.take<th::ds>(n2);
+      x.ecds = c.take<th::ds>(n2);
+    }
     x.pw32 = c.take<float>((size_t)g.m * (g.q + 1));
     x.rw32 = c.take<float>((size_t)g.mc * x.rmax);
     x.ccell32 = c.take<float2>(ncell_c);
@@ -343,6 +349,12 @@ uint16_t f2bf(float f) {
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 template <typename T>
+T cvt(double v) {
+  if constexpr (std::is_same<T, th::ds>::value) return th::ds_from_host(v);
+  else return (T)v;
+}
+
+template <typename T>
 th::FineArgs<T> fine_args(const th_ctx& x, int op) {
   th::FineArgs<T> a{};
   const th::Geometry& g = x.g;
@@ -351,14 +363,14 @@ th::FineArgs<T> fine_args(const th_ctx& x, int op) {
   a.m = g.m;
   a.p = g.p;
   a.robin = g.robin[0] | (g.robin[1] << 1) | (g.robin[2] << 2) | (g.robin[3] << 3);
-  a.h = (T)g.h;
-  a.h2 = (T)(g.h * g.h);
-  a.alpha = (op == TH_OP_AS) ? (T)x.prm.alpha_s : (T)0;
-  a.tc = std::is_same<T, double>::value ? x.tc64 : x.tc32;
+  a.h = cvt<T>(g.h);
+  a.h2 = cvt<T>(g.h * g.h);
+  a.alpha = cvt<T>(op == TH_OP_AS ? x.prm.alpha_s : 0.0);
+  a.tc = std::is_same<T, float>::value ? x.tc32 : x.tc64;
   const int np = g.p + 1;
   for (int i = 0; i < np * np; ++i) {
-    a.M[i] = (T)x.ref.M[i];
-    a.K[i] = (T)x.ref.K[i];
+    a.M[i] = cvt<T>(x.ref.M[i]);
+    a.K[i] = cvt<T>(x.ref.K[i]);
   }
   const int H = g.p / 2, P = g.p;
   const double* M = x.ref.M.data();
@@ -366,17 +378,20 @@ th::FineArgs<T> fine_args(const th_ctx& x, int op) {
   for (int r = 0; r <= H; ++r)
     for (int c = 0; c <= H; ++c) {
       const bool mid = (c == H);
-      a.ME[r * (H + 1) + c] = (T)(mid ? M[r * np + c] : 0.5 * (M[r * np + c] + M[r * np + P - c]));
-      a.KE[r * (H + 1) + c] = (T)(mid ? K[r * np + c] : 0.5 * (K[r * np + c] + K[r * np + P - c]));
+      a.ME[r * (H + 1) + c] = cvt<T>(mid ? M[r * np + c] : 0.5 * (M[r * np + c] + M[r * np + P - c]));
+      a.KE[r * (H + 1) + c] = cvt<T>(mid ? K[r * np + c] : 0.5 * (K[r * np + c] + K[r * np + P - c]));
     }
   for (int r = 0; r < H; ++r)
     for (int c = 0; c < H; ++c) {
-      a.MO[r * H + c] = (T)(0.5 * (M[r * np + c] - M[r * np + P - c]));
-      a.KO[r * H + c] = (T)(0.5 * (K[r * np + c] - K[r * np + P - c]));
+      a.MO[r * H + c] = cvt<T>(0.5 * (M[r * np + c] - M[r * np + P - c]));
+      a.KO[r * H + c] = cvt<T>(0.5 * (K[r * np + c] - K[r * np + P - c]));
     }
   if constexpr (std::is_same<T, double>::value) {
     a.kc = x.kc64;
     a.ec = x.ec64;
+  } else if constexpr (std::is_same<T, th::ds>::value) {
+    a.kc = x.kcds;
+    a.ec = x.ecds;
   } else {
     a.kc = x.kc32;
     a.ec = x.ec32;
@@ -433,6 +448,27 @@ th_status fine_apply(th_ctx& x, int op, const typename th::Cx<T>::t* u, const ty
   x.launches += 1;
   Prof prof(x, TH_K_FINE, s);
   return cuda_status(th::launch_fine_apply<T>(a, nrhs, s));
+}
+
+// The mixed form's outer residual r = f - A u from FP64 u, f, delivered in FP32
+// (the FP32 cycle's input): a double-single apply that writes FP32 (one launch),
+// or the FP64 apply followed by rounding (th_set_kernel_variant TH_K_RESID).
+th_status outer_residual(th_ctx& x, const double2* u, const double2* f, float2* r32, int nrhs, cudaStream_t s) {
+  if (x.g.dim == 2 && x.resid_ds && x.kcds) {
+    th::FineArgs<th::ds> a = fine_args<th::ds>(x, TH_OP_A);
+    a.u = reinterpret_cast<const th::cds*>(u);
+    a.f = reinterpret_cast<const th::cds*>(f);
+    a.y = reinterpret_cast<th::cds*>(r32);  // FP32 output (see NodeIO<ds>)
+    a.residual = 1;
+    x.launches += 1;
+    Prof prof(x, TH_K_FINE, s);
+    return cuda_status(th::launch_fine_apply<th::ds>(a, nrhs, s));
+  }
+  th_status st = fine_apply<double>(x, TH_OP_A, u, f, x.r64, nrhs, s);
+  if (st != TH_OK) return st;
+  x.launches += 1;
+  Prof prof(x, TH_K_VECTOR, s);
+  return cuda_status(th::launch_d2f((const double*)x.r64, (float*)r32, 2 * x.g.N * (long long)nrhs, s));
 }
 
 template <typename T> struct PrecBufs;
@@ -1196,6 +1232,16 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     for (size_t i = 0; i < rho64.size(); ++i) rho32[i] = make_float2((float)rho64[i].x, (float)rho64[i].y);
     if ((st = up(x->kc32, kf.data(), n2 * 4)) != TH_OK) return st;
     if ((st = up(x->ec32, ef.data(), n2 * 4)) != TH_OK) return st;
+    if (x->kcds) {
+      std::vector<th::ds> kd(n2), ed(n2);
+      for (size_t i = 0; i < n2; ++i) {
+        kd[i] = th::ds_from_host(k_host[i]);
+        ed[i] = th::ds_from_host(eps[i]);
+      }
+      if ((st = up(x->kcds, kd.data(), n2 * sizeof(th::ds))) != TH_OK) return st;
+      if ((st = up(x->ecds, ed.data(), n2 * sizeof(th::ds))) != TH_OK) return st;
+      TH_CU(cudaStreamSynchronize(s));
+    }
     if ((st = up(x->pw32, pwf.data(), pwf.size() * 4)) != TH_OK) return st;
     if ((st = up(x->rw32, rwf.data(), rwf.size() * 4)) != TH_OK) return st;
     if ((st = up(x->ccell32, cell32.data(), cell32.size() * 8)) != TH_OK) return st;
@@ -1342,6 +1388,8 @@ th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
     x->dd_tc = variant;
   } else if (kernel == TH_K_COARSE_SOLVE) {
     x->cs_variant = variant;
+  } else if (kernel == TH_K_RESID) {
+    x->resid_ds = variant;
   } else {
     return TH_ERR_ARG;
   }
@@ -1356,6 +1404,7 @@ th_status th_get_kernel_variant(const th_ctx* x, int kernel, int prec, int* vari
   else if (kernel == TH_K_DD) *variant = d ? x->dds64 : x->dds32;
   else if (kernel == TH_K_DD_BATCH) *variant = (x->Wu && x->dd_tc) ? 1 : 0;
   else if (kernel == TH_K_COARSE_SOLVE) *variant = x->cs_variant;
+  else if (kernel == TH_K_RESID) *variant = (x->resid_ds && x->kcds) ? 1 : 0;
   else return TH_ERR_ARG;
   return TH_OK;
 }
@@ -1449,6 +1498,15 @@ th_status th_residual(th_ctx* x, const double* f, const double* u, double* r, in
                             reinterpret_cast<double2*>(r), nrhs, S(stream));
 }
 
+th_status th_residual_mixed(th_ctx* x, const double* f, const double* u, float* r, int nrhs, void* stream) {
+  th_status st = check_nrhs(x, nrhs);
+  if (st != TH_OK) return st;
+  if (!f || !u || !r) return TH_ERR_ARG;
+  if (!x->mixed) return TH_ERR_UNSUPPORTED;
+  return outer_residual(*x, reinterpret_cast<const double2*>(u), reinterpret_cast<const double2*>(f),
+                        reinterpret_cast<float2*>(r), nrhs, S(stream));
+}
+
 th_status th_smooth(th_ctx* x, const double* f, double* u, int nrhs, void* stream) {
   th_status st = check_nrhs(x, nrhs);
   if (st != TH_OK) return st;
@@ -1459,8 +1517,7 @@ th_status th_smooth(th_ctx* x, const double* f, double* u, int nrhs, void* strea
   if (x->active == TH_PREC_FP64) return smooth<double>(*x, TH_PREC_FP64, f2, u2, false, nrhs, s);
   // mixed: u += S(0, f - A u) in FP32
   const long long n = x->g.N * (long long)nrhs;
-  if ((st = fine_apply<double>(*x, TH_OP_A, u2, f2, x->r64, nrhs, s)) != TH_OK) return st;
-  if ((st = narrow(*x, x->r64, x->f32, n, s)) != TH_OK) return st;
+  if ((st = outer_residual(*x, u2, f2, x->f32, nrhs, s)) != TH_OK) return st;
   if ((st = smooth<float>(*x, x->active, x->f32, x->u32, true, nrhs, s)) != TH_OK) return st;
   return widen(*x, x->u32, u2, n, 1, s);
 }
@@ -1504,8 +1561,7 @@ th_status th_cycle(th_ctx* x, const double* f, double* u, int nrhs, void* stream
   if (x->active == TH_PREC_FP64) return cycle<double>(*x, TH_PREC_FP64, f2, u2, false, nrhs, s);
   // mixed: TwoGridStep(u, f) = u + TwoGridStep(0, f - A u) (the step is affine in u and f)
   const long long n = x->g.N * (long long)nrhs;
-  if ((st = fine_apply<double>(*x, TH_OP_A, u2, f2, x->r64, nrhs, s)) != TH_OK) return st;
-  if ((st = narrow(*x, x->r64, x->f32, n, s)) != TH_OK) return st;
+  if ((st = outer_residual(*x, u2, f2, x->f32, nrhs, s)) != TH_OK) return st;
   if ((st = cycle<float>(*x, x->active, x->f32, x->u32, true, nrhs, s)) != TH_OK) return st;
   return widen(*x, x->u32, u2, n, 1, s);
 }

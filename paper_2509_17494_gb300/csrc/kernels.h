@@ -11,6 +11,27 @@ template <typename T> struct Cx;
 template <> struct Cx<double> { using t = double2; };
 template <> struct Cx<float> { using t = float2; };
 
+// Double-single number: the unevaluated sum h + l of two floats, |l| <= ulp(h) / 2
+// (Dekker 1971): 48 significant bits from FP32 arithmetic.  The device
+// operators are defined where they are used (fine.cu).  In the mixed form's
+// outer residual, global inputs are FP64 (split exactly into h + l on load) and
+// the output is FP32.
+struct ds {
+  float h, l;
+  ds() = default;
+  __host__ __device__ constexpr ds(float v) : h(v), l(0.f) {}
+  __host__ __device__ constexpr ds(int v) : h((float)v), l(0.f) {}
+  __host__ __device__ constexpr ds(float a, float b) : h(a), l(b) {}
+};
+struct cds {
+  ds x, y;
+};
+template <> struct Cx<ds> { using t = cds; };
+inline ds ds_from_host(double v) {
+  const float h = (float)v;
+  return ds(h, (float)(v - (double)h));
+}
+
 // ---------------------------------------------------------------- K1 fine apply
 template <typename T>
 struct FineArgs {

@@ -317,3 +317,32 @@ def test_batched_tensor_core_solve(th):
     X64, info64 = S.solve(dev(F))
     assert info["iters"] <= info64["iters"] + 2
     assert relerr(host(X), host(X64)) < 1e-6
+
+
+# ------------------------------------------------- the mixed form's outer residual
+@pytest.mark.parametrize("c", CASES)
+def test_mixed_outer_residual_double_single(th, c):
+    """r = f - A u in double-single arithmetic, rounded to FP32: against the FP64
+    oracle, within FP32 rounding of r plus 2^-40 of the terms' scale |A| |u|
+    (about 20 double-single operations of relative error 2^-46 on the longest
+    path); with u near the solution (r ~ 1e-9 |f|) that second term is what
+    remains, and a float-only apply (2^-24) would miss it by far."""
+    S, P = build(th, c, prec="fp32", extra_prec=("fp64",))
+    assert S.get_variant("resid", "fp32") == 1
+    import scipy.sparse.linalg as spla
+    f = synth.random_complex((3, P.N), 41)
+    u = synth.random_complex((3, P.N), 42)
+    uex = np.stack([spla.spsolve(P.A.tocsc(), f[i]) for i in range(3)])
+    Aabs = abs(P.A)
+    for uu in (u, uex * (1 + 1e-9 * synth.random_complex(P.N, 43).real)):
+        want = f - (P.A @ uu.T).T
+        got = host(S.residual_mixed(dev(f), dev(uu)))
+        scale = (Aabs @ np.abs(uu).T).T.max() + np.abs(f).max()
+        err = np.abs(got - want).max()
+        assert err <= 1.2e-7 * np.abs(want).max() + 2.0 ** -40 * scale, (err, np.abs(want).max(), scale)
+    # the FP64 variant of the same step agrees
+    S.set_variant("resid", "fp32", 0)
+    got0 = host(S.residual_mixed(dev(f), dev(u)))
+    S.set_variant("resid", "fp32", 1)
+    got1 = host(S.residual_mixed(dev(f), dev(u)))
+    assert relerr(got1, got0) < 2e-7
