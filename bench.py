@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cycles", type=int, default=15, help="oracle cycles in the CPU-baseline sample")
     ap.add_argument("--batch-rhs", type=int, default=64, help="right-hand sides of the batched section (0: skip)")
-    ap.add_argument("--dd-variant", choices=["auto", "0", "1", "2"], default="auto",
-                    help="FP32 subdomain kernel: auto (set-up autotuner), 0 k_dd_apply, 1 k_dd_stream, 2 k_dd_stream2 "
+    ap.add_argument("--dd-variant", choices=["auto", "0", "1", "2", "3"], default="auto",
+                    help="FP32 subdomain kernel: auto (set-up autotuner), 0 k_dd_apply, 1 k_dd_stream, 2 k_dd_stream2, "
+                         "3 k_dd_stream with three CTAs per SM "
                          "(pin it when the same command runs under a profiler, whose serialised launches "
                          "change the autotuner's timings)")
     ap.add_argument("--fine-variant", choices=["auto", "0", "1"], default="auto",
@@ -294,7 +295,8 @@ def run_native(args):
     dominant = max(per_step, key=lambda k: per_step[k][0])
     dd_ms, dd_cnt = prof["dd"]
     dd_avg_ms = dd_ms / max(dd_cnt, 1)
-    dd_kernel = "k_dd_stream (TMA bulk)" if S.get_variant("dd", "fp32") else "k_dd_apply"
+    dd_kernel = {0: "k_dd_apply", 1: "k_dd_stream (TMA bulk)", 2: "k_dd_stream2 (TMA bulk, producer warp)",
+                 3: "k_dd_stream (TMA bulk, three CTAs per SM)"}[S.get_variant("dd", "fp32")]
     alg_bytes, _ = dd_algorithmic_bytes(n, p, w["l_dd"], 4, 8)
     hbm, peak_src = peaks()
     achieved = alg_bytes / (dd_avg_ms * 1e-3) / 1e9

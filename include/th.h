@@ -358,7 +358,8 @@ th_status th_profile_read(th_ctx* ctx, int kind, double* ms, long long* launches
  *   TH_K_DD:   0 = per-subdomain CTAs with direct loads,
  *              1 = persistent CTAs streaming the rows through TMA bulk copies,
  *              2 = the same with a dedicated producer warp and per-slot
- *                  mbarrier release (no CTA barrier per ring slot);
+ *                  mbarrier release (no CTA barrier per ring slot),
+ *              3 = variant 1 with smaller ring stages, three CTAs per SM;
  *   TH_K_DD_BATCH: 1 (default when the BF16 rows fit, U box <= 128 nodes) runs
  *              the products of 8 or more right-hand sides on the tensor cores
  *              (tcgen05.mma, BF16 operands, FP32 accumulation; the residuals

@@ -566,6 +566,7 @@ th_status dd_apply(th_ctx& x, int wkind, const typename th::Cx<T>::t* r, int nrh
   }
   const int stream = std::is_same<T, double>::value ? x.dds64 : x.dds32;
   a.stream_v2 = stream == 2 ? 1 : 0;
+  a.stream_small = stream == 3 ? 1 : 0;
   if (stream) return cuda_status(th::launch_dd_stream<T>(a, wkind, x.derr, x.sms, s));
   return cuda_status(th::launch_dd_apply<T>(a, wkind, 0, s));
 }
@@ -989,7 +990,7 @@ th_status tune_dd(th_ctx& x, int wkind, cudaStream_t s, int& choice) {
   TH_CU(cudaEventCreate(&e1));
   float best = 1e30f;
   int arg = 0;
-  for (int v = 0; v < 3; ++v) {
+  for (int v = 0; v < 4; ++v) {
     choice = v;
     bool ok = true;
     for (int w = 0; w < 2 && ok; ++w) ok = (dd_apply<T>(x, wkind, r, 1, s) == TH_OK);
@@ -1377,7 +1378,7 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
 }
 
 th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
-  if (!x || variant < 0 || variant > (kernel == TH_K_DD ? 2 : 1) || (prec != TH_PREC_FP64 && prec != TH_PREC_FP32))
+  if (!x || variant < 0 || variant > (kernel == TH_K_DD ? 3 : 1) || (prec != TH_PREC_FP64 && prec != TH_PREC_FP32))
     return TH_ERR_ARG;
   const bool d = (prec == TH_PREC_FP64);
   if (kernel == TH_K_FINE) {

@@ -64,8 +64,10 @@ __global__ void __launch_bounds__(512) k_coarse_solve(const CoarseSolveArgs<T> a
     for (int c = lane; c < mc; c += 32) {
       const C g = grow[c];
       const C t = tv[c];
-      sr += g.x * t.x - g.y * t.y;
-      si += g.x * t.y + g.y * t.x;
+      sr = fmadd(g.x, t.x, sr);
+      sr = fmadd(-g.y, t.y, sr);
+      si = fmadd(g.x, t.y, si);
+      si = fmadd(g.y, t.x, si);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

@@ -41,8 +41,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 template <typename C>
 __device__ __forceinline__ void cmac(C& acc, C a, C b) {
-  acc.x += a.x * b.x - a.y * b.y;
-  acc.y += a.x * b.y + a.y * b.x;
+  cmadd(acc, a, b);
 }
 
 template <typename T>

@@ -134,8 +134,10 @@ __global__ void __launch_bounds__(MAXT) k_dd_apply(const DDArgs<T> a) {
 #pragma unroll
           for (int k = 0; k < NRHS; ++k) {
             const C xv = xs[k * XL + ch * CPC + j];
-            acr[k] += wr[j] * xv.x - wi[j] * xv.y;
-            aci[k] += wr[j] * xv.y + wi[j] * xv.x;
+            acr[k] = fmadd(wr[j], xv.x, acr[k]);
+            acr[k] = fmadd(-wi[j], xv.y, acr[k]);
+            aci[k] = fmadd(wr[j], xv.y, aci[k]);
+            aci[k] = fmadd(wi[j], xv.x, aci[k]);
           }
         }
       }
@@ -408,9 +410,10 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
     cp_wait1();
     __syncthreads();
     const C* xv = xs + (size_t)(i & 1) * NRHS * XL;
-    T acr[NRHS], aci[NRHS];
+    // two accumulator sets (even / odd column of a chunk) halve the FMA chains
+    T acr[2][NRHS], aci[2][NRHS];
 #pragma unroll
-    for (int k = 0; k < NRHS; ++k) { acr[k] = 0; aci[k] = 0; }
+    for (int k = 0; k < NRHS; ++k) { acr[0][k] = aci[0][k] = acr[1][k] = aci[1][k] = 0; }
     for (int s = 0; s < NS; ++s, ++t) {
       if (!failed && !mbar_wait_bounded(bars + (t % depth), (unsigned)((t / depth) & 1))) failed = 1;
       const int ch0 = s * cps, nch = min(cps, NCH - ch0);
@@ -419,14 +422,36 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
         for (int ch = g; ch < nch; ch += G) {
           T wr[CPC], wi[CPC];
           unpack_chunk_smem<T, KIND>(slot, (size_t)ch * NR + rr, wr, wi);
-#pragma unroll
-          for (int j = 0; j < CPC; ++j) {
-            const int c = (ch0 + ch) * CPC + j;
+          if constexpr (std::is_same<T, float>::value && CPC % 2 == 0) {
+            // two complex x per 16-byte load (x rows are 16-byte aligned, chunk starts even)
 #pragma unroll
             for (int k = 0; k < NRHS; ++k) {
-              const C x = xv[k * XL + c];
-              acr[k] += wr[j] * x.x - wi[j] * x.y;
-              aci[k] += wr[j] * x.y + wi[j] * x.x;
+              const float4* xq = reinterpret_cast<const float4*>(xv + (size_t)k * XL + (size_t)(ch0 + ch) * CPC);
+#pragma unroll
+              for (int j2 = 0; j2 < CPC / 2; ++j2) {
+                const float4 x = xq[j2];
+                acr[0][k] = fmadd(wr[2 * j2], x.x, acr[0][k]);
+                acr[0][k] = fmadd(-wi[2 * j2], x.y, acr[0][k]);
+                aci[0][k] = fmadd(wr[2 * j2], x.y, aci[0][k]);
+                aci[0][k] = fmadd(wi[2 * j2], x.x, aci[0][k]);
+                acr[1][k] = fmadd(wr[2 * j2 + 1], x.z, acr[1][k]);
+                acr[1][k] = fmadd(-wi[2 * j2 + 1], x.w, acr[1][k]);
+                aci[1][k] = fmadd(wr[2 * j2 + 1], x.w, aci[1][k]);
+                aci[1][k] = fmadd(wi[2 * j2 + 1], x.z, aci[1][k]);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < CPC; ++j) {
+              const int c = (ch0 + ch) * CPC + j;
+#pragma unroll
+              for (int k = 0; k < NRHS; ++k) {
+                const C x = xv[k * XL + c];
+                acr[j & 1][k] = fmadd(wr[j], x.x, acr[j & 1][k]);
+                acr[j & 1][k] = fmadd(-wi[j], x.y, acr[j & 1][k]);
+                aci[j & 1][k] = fmadd(wr[j], x.y, aci[j & 1][k]);
+                aci[j & 1][k] = fmadd(wi[j], x.x, aci[j & 1][k]);
+              }
             }
           }
         }
@@ -439,8 +464,8 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
 #pragma unroll
       for (int k = 0; k < NRHS; ++k) {
         C v;
-        v.x = acr[k];
-        v.y = aci[k];
+        v.x = acr[0][k] + acr[1][k];
+        v.y = aci[0][k] + aci[1][k];
         red[((size_t)g * NR + rr) * NRHS + k] = v;
       }
     }
@@ -578,8 +603,10 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream2(const DDArgs<T> a, int cp
 #pragma unroll
               for (int k = 0; k < NRHS; ++k) {
                 const C x = xv[k * XL + c];
-                acr[k] += wr[j] * x.x - wi[j] * x.y;
-                aci[k] += wr[j] * x.y + wi[j] * x.x;
+                acr[k] = fmadd(wr[j], x.x, acr[k]);
+                acr[k] = fmadd(-wi[j], x.y, acr[k]);
+                aci[k] = fmadd(wr[j], x.y, aci[k]);
+                aci[k] = fmadd(wi[j], x.x, aci[k]);
               }
             }
           }
@@ -658,15 +685,18 @@ static cudaError_t launch_dd_stream_k(const DDArgs<T>& a, int* err, int sms, cud
   constexpr int CPC = WTraits<KIND>::CPC;
   const int threads = ((a.NR * a.G + 31) / 32) * 32;
   if (threads > 512) return cudaErrorInvalidConfiguration;
-  // two CTAs per SM, each with a ring of three stages of up to 32 KB
-  const int cps = std::max(1, (int)((32 * 1024) / ((size_t)a.NR * 16)));
+  // a ring of three stages per CTA: up to 32 KB each for two CTAs per SM, or
+  // (stream_small) up to 20 KB each so that three CTAs share an SM
+  const int slot_target = a.stream_small ? 20 * 1024 : 32 * 1024;
+  const int cps = std::max(1, (int)(slot_target / ((size_t)a.NR * 16)));
   const size_t slot_bytes = (size_t)cps * a.NR * 16;
   const size_t fixed = 8 * sizeof(uint64_t) +
                        sizeof(C) * ((size_t)2 * NRHS * a.NCH * CPC + (size_t)a.G * a.NR * NRHS);
   const int depth = 3;
   const size_t smem = depth * slot_bytes + fixed;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  const int per_sm = (2 * (smem + 1024) <= 228 * 1024) ? 2 : 1;
+  const int fit = (int)((228 * 1024) / (smem + 1024));
+  const int per_sm = std::max(1, std::min(a.stream_small ? 3 : 2, fit));
   cudaError_t e = cudaFuncSetAttribute(k_dd_stream<T, KIND, NRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

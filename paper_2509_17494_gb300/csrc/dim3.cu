@@ -17,8 +17,7 @@ namespace th {
 
 template <typename C>
 __device__ __forceinline__ void c_fma(C& acc, C a, C b) {
-  acc.x += a.x * b.x - a.y * b.y;
-  acc.y += a.x * b.y + a.y * b.x;
+  cmadd(acc, a, b);
 }
 template <typename T>
 __device__ __forceinline__ typename Cx<T>::t shfl_c(typename Cx<T>::t v, int src) {
@@ -87,8 +86,10 @@ __global__ void __launch_bounds__(256) k_fine3_cells(const Fine3Args<T> a) {
   for (int b = 0; b < 3; ++b) {
     const C v1 = shfl_c<T>(W1, bz0 + 9 * b), v2 = shfl_c<T>(W2, bz0 + 9 * b);
     const T kz = a.K[az * 3 + b], mz = a.M[az * 3 + b];
-    Y.x += kz * v1.x + mz * v2.x;
-    Y.y += kz * v1.y + mz * v2.y;
+    Y.x = fmadd(kz, v1.x, Y.x);
+    Y.x = fmadd(mz, v2.x, Y.x);
+    Y.y = fmadd(kz, v1.y, Y.y);
+    Y.y = fmadd(mz, v2.y, Y.y);
   }
   // absorbing faces of the domain: -i k h^2 (M M) on the face's nodes
   const bool face[6] = {cx == 0, cx == n - 1, cy == 0, cy == n - 1, cz == 0, cz == n - 1};

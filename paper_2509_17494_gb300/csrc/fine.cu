@@ -44,6 +44,7 @@ __device__ __forceinline__ ds operator*(ds a, ds b) {
   return ds_fast_two_sum(p, e);
 }
 __device__ __forceinline__ ds& operator+=(ds& a, ds b) { return a = a + b; }
+__device__ __forceinline__ ds fmadd(ds a, ds b, ds c) { return c + a * b; }
 __device__ __forceinline__ ds& operator-=(ds& a, ds b) { return a = a - b; }
 
 // Exact split of a double into h (its leading 24 significant bits, truncated)
@@ -219,15 +220,19 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
 #pragma unroll
       for (int b = 0; b <= H; ++b) {
         const T me = a.ME[ay * (H + 1) + b], ke = a.KE[ay * (H + 1) + b];
-        pr += me * zs_[b].x + ke * ts_[b].x;
-        pi += me * zs_[b].y + ke * ts_[b].y;
+        pr = fmadd(me, zs_[b].x, pr);
+        pr = fmadd(ke, ts_[b].x, pr);
+        pi = fmadd(me, zs_[b].y, pi);
+        pi = fmadd(ke, ts_[b].y, pi);
       }
       if (ay < H) {
 #pragma unroll
         for (int b = 0; b < H; ++b) {
           const T mo = a.MO[ay * H + b], ko = a.KO[ay * H + b];
-          qr += mo * zd_[b].x + ko * td_[b].x;
-          qi += mo * zd_[b].y + ko * td_[b].y;
+          qr = fmadd(mo, zd_[b].x, qr);
+          qr = fmadd(ko, td_[b].x, qr);
+          qi = fmadd(mo, zd_[b].y, qi);
+          qi = fmadd(ko, td_[b].y, qi);
         }
         yv[ay].x = pr + qr;
         yv[ay].y = pi + qi;

@@ -15,8 +15,7 @@ namespace th {
 
 template <typename C>
 __device__ __forceinline__ void gal_fma(C& acc, C a, C b) {
-  acc.x += a.x * b.x - a.y * b.y;
-  acc.y += a.x * b.y + a.y * b.x;
+  cmadd(acc, a, b);
 }
 
 template <typename T>

@@ -27,6 +27,21 @@ struct cds {
   ds x, y;
 };
 template <> struct Cx<ds> { using t = cds; };
+
+#if defined(__CUDACC__)
+// c + a b as one fused multiply-add.  Accumulations are written as chains of
+// these: the compiler may not reassociate acc + (a b + c d) into two FMAs.
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+// acc += a b (complex)
+template <typename C>
+__device__ __forceinline__ void cmadd(C& acc, C a, C b) {
+  acc.x = fmadd(a.x, b.x, acc.x);
+  acc.x = fmadd(-a.y, b.y, acc.x);
+  acc.y = fmadd(a.x, b.y, acc.y);
+  acc.y = fmadd(a.y, b.x, acc.y);
+}
+#endif
 inline ds ds_from_host(double v) {
   const float h = (float)v;
   return ds(h, (float)(v - (double)h));
@@ -66,6 +81,7 @@ struct DDArgs {
   long long N;
   int nsub, m, Lw, NC, NCH, NR, G, nrhs;
   int stream_v2;                // launch_dd_stream: 1 = producer-warp variant (k_dd_stream2)
+  int stream_small;             // launch_dd_stream (k_dd_stream): 1 = 20 KB ring stages, three CTAs per SM
 };
 template <typename T>
 cudaError_t launch_dd_apply(const DDArgs<T>& a, int kind, int grid_cap, cudaStream_t s);

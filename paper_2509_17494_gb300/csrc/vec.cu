@@ -235,8 +235,10 @@ __global__ void __launch_bounds__(256) k_mdot_part(const double2* __restrict__ V
     for (int t = 0; t < kDotTile; ++t) {
       if (t < ni) {
         const double2 v = (i0 + t < nv) ? Vb[(size_t)(i0 + t) * vstride + (size_t)rhs * N + n] : wv;
-        ar[t] += v.x * wv.x + v.y * wv.y;
-        ai[t] += v.x * wv.y - v.y * wv.x;
+        ar[t] = fmadd(v.x, wv.x, ar[t]);
+        ar[t] = fmadd(v.y, wv.y, ar[t]);
+        ai[t] = fmadd(v.x, wv.y, ai[t]);
+        ai[t] = fmadd(-v.y, wv.x, ai[t]);
       }
     }
   }
@@ -313,8 +315,10 @@ __global__ void __launch_bounds__(256) k_maxpy(const double2* __restrict__ Vb, l
     for (int i = 0; i < nv; ++i) {
       const double2 c = hr[i];
       const double2 v = Vb[(size_t)i * vstride + (size_t)rhs * N + n];
-      sr += c.x * v.x - c.y * v.y;
-      si += c.x * v.y + c.y * v.x;
+      sr = fmadd(c.x, v.x, sr);
+      sr = fmadd(-c.y, v.y, sr);
+      si = fmadd(c.x, v.y, si);
+      si = fmadd(c.y, v.x, si);
     }
     double2 o = wr[n];
     o.x += sign * sr;
@@ -339,7 +343,8 @@ __global__ void __launch_bounds__(256) k_norm_part(const double2* __restrict__ w
   double s = 0;
   for (long long n = lo + threadIdx.x; n < hi; n += blockDim.x) {
     const double2 v = wr[n];
-    s += v.x * v.x + v.y * v.y;
+    s = fmadd(v.x, v.x, s);
+    s = fmadd(v.y, v.y, s);
   }
   __shared__ double sh[256];
   sh[threadIdx.x] = s;

@@ -89,7 +89,7 @@ def test_coarse_apply_transfers_and_solve_3d(th, c):
 
 
 @pytest.mark.parametrize("c", CASES3)
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_smoother_3d(th, c, variant):
     S, P = build(th, c)
     S.set_variant("dd", "fp64", variant)

@@ -99,7 +99,7 @@ def test_fine_apply_variants_fp64(th, c, variant):
 
 @pytest.mark.parametrize("c", CASES)
 @pytest.mark.parametrize("n_dd", [1, 2])
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_smoother_fp64(th, c, n_dd, variant):
     S, P = build(th, c, n_dd=n_dd)
     S.set_variant("dd", "fp64", variant)
@@ -223,7 +223,7 @@ def test_host_buffer_entry_points(th):
 
 # ------------------------------------------------------------ mixed precision
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 2e-3), ("bf16", 2e-2)])
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_mixed_smoother_close_to_fp64(th, prec, tol, variant):
     c = CASES[5]
     S, P = build(th, c, prec=prec, extra_prec=("fp64",))
