@@ -60,6 +60,9 @@ def parse():
                          "change the autotuner's timings)")
     ap.add_argument("--fine-variant", choices=["auto", "0", "1"], default="auto",
                     help="FP32 and FP64 fine-apply tile variant: auto, 0 (large tiles), 1 (small tiles)")
+    ap.add_argument("--coarse-variant", choices=["auto", "0", "1", "2"], default="auto",
+                    help="FP32 one-rhs coarse sweep: auto, 0 two phases, 1 one cluster barrier per step, "
+                         "2 st.async row exchange")
     ap.add_argument("--learned-steps", type=int, default=400, help="training steps of the learned section (0: skip)")
     ap.add_argument("--dim3", choices=["cube10_q2_n40", "cube2_q2_n8", "none"], default="cube10_q2_n40",
                     help="3-D workload of the three-dimensional section")
@@ -212,6 +215,8 @@ def run_native(args):
     if args.fine_variant != "auto":
         S.set_variant("fine", "fp32", int(args.fine_variant))
         S.set_variant("fine", "fp64", int(args.fine_variant))
+    if args.coarse_variant != "auto":
+        S.set_variant("coarse", "fp32", int(args.coarse_variant))
     N = S.N
     f = torch.from_numpy(np.ascontiguousarray(w["f"] if w["f"].ndim == 1 else w["f"][0])).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -308,7 +313,9 @@ def run_native(args):
                 "profiled_ms_per_step": round(ms_prof, 4),
                 "share_of_step": {k: round(v[0] / ms_prof, 3) for k, v in per_step.items() if v[1] > 0},
                 "variants": {"dd_fp32": S.get_variant("dd", "fp32"), "fine_fp32": S.get_variant("fine", "fp32"),
-                             "dd_fp64": S.get_variant("dd", "fp64"), "fine_fp64": S.get_variant("fine", "fp64")}}
+                             "dd_fp64": S.get_variant("dd", "fp64"), "fine_fp64": S.get_variant("fine", "fp64"),
+                             "coarse_sweep": S.get_variant("coarse", "fp32"),
+                             "outer_residual": "double-single" if S.get_variant("resid", "fp32") else "fp64"}}
 
     fine_ms = sum(v[0] for k, v in per_step.items() if k != "coarse_solve")
     line = {

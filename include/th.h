@@ -368,7 +368,10 @@ th_status th_profile_read(th_ctx* ctx, int kind, double* ms, long long* launches
  *              rounding (th_residual_mixed; prec is ignored);
  *   TH_K_COARSE_SOLVE: one-right-hand-side chunk sweep of the 2-D coarse
  *              solve: 0 = two phases per block step (512 threads), 1 = one
- *              cluster barrier per step (1024 threads, m_c <= 256).
+ *              cluster barrier per step (1024 threads, m_c <= 256), 2 = rows
+ *              exchanged by st.async on per-slot mbarriers, no cluster
+ *              barrier per step (1024 threads, m_c <= 256; bounded waits
+ *              report through th_device_status).
  * prec selects the FP64 or the FP32-cycle kernels (TH_PREC_FP64 / TH_PREC_FP32).
  * Overriding is for testing and measurement; every variant computes the same
  * result up to summation order. */

@@ -747,6 +747,7 @@ th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th:
   a.rpcm = x.rpcm;
   a.nrhs = nrhs;
   a.sweep_variant = x.cs_variant;
+  a.err = x.derr;
   if (!a.G || !a.LR) return TH_ERR_UNSUPPORTED;
   x.launches += (x.P > 1) ? 4 : 1;
   Prof prof(x, TH_K_COARSE_SOLVE, s);
@@ -955,7 +956,7 @@ th_status tune_coarse(th_ctx& x, cudaStream_t s, int& choice) {
   TH_CU(cudaEventCreate(&e1));
   float best = 1e30f;
   int arg = choice;
-  for (int v = 0; v < 2; ++v) {
+  for (int v = 0; v < 3; ++v) {
     choice = v;
     bool ok = true;
     for (int w = 0; w < 2 && ok; ++w) ok = (coarse_solve_<T>(x, rc, uc, 1, s) == TH_OK);
@@ -1378,7 +1379,8 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
 }
 
 th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
-  if (!x || variant < 0 || variant > (kernel == TH_K_DD ? 3 : 1) || (prec != TH_PREC_FP64 && prec != TH_PREC_FP32))
+  const int vmax = kernel == TH_K_DD ? 3 : kernel == TH_K_COARSE_SOLVE ? 2 : 1;
+  if (!x || variant < 0 || variant > vmax || (prec != TH_PREC_FP64 && prec != TH_PREC_FP32))
     return TH_ERR_ARG;
   const bool d = (prec == TH_PREC_FP64);
   if (kernel == TH_K_FINE) {

@@ -329,6 +329,200 @@ __global__ void __launch_bounds__(1024, 1) k_chunk_sweep1(const CoarsePartArgs<T
   }
 }
 
+// Variant 2: the rows a CTA computes reach the other CTAs of the cluster by
+// st.async stores that complete transactions on the receivers' mbarriers
+// (one per exchange slot), so a block step ends without a cluster barrier:
+// each CTA waits only for the mc values it needs.  The G rows of the coming
+// steps are prefetched into a ring of three buffers.  Slot reuse is safe
+// without further synchronisation: a CTA writes step q's rows into slot q&1
+// only after it received every row of step q-1, which every receiver sends
+// after it finished reading slot q&1 (its step q-1 input).  Waits are bounded;
+// on a timeout the CTA flags the error and finishes without waiting.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned mapa_u32(unsigned addr, int rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_async_c(unsigned raddr, float2 v, unsigned rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];\n"
+               ::"r"(raddr), "f"(v.x), "f"(v.y), "r"(rbar) : "memory");
+}
+__device__ __forceinline__ void st_async_c(unsigned raddr, double2 v, unsigned rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];\n"
+               ::"r"(raddr), "d"(v.x), "d"(v.y), "r"(rbar) : "memory");
+}
+__device__ __forceinline__ void cmbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void cmbar_expect(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool cmbar_try(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) k_chunk_sweep2(const CoarsePartArgs<T> a, int* err) {
+  using C = typename Cx<T>::t;
+  constexpr int NI = 8;
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank(), csz = (int)cl.num_blocks();
+  const int cid = blockIdx.x / csz;
+  const int chunk = cid % a.P, rhs = cid / a.P;
+  const int mc = a.mc, mcp = a.mcp, rpc = a.rpc;
+  const int A = a.ca[chunk], L = a.cb[chunk] - A + 1;
+  const int nsteps = 2 * L - 1;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int row0 = crank * rpc, nrow = max(0, min(rpc, mc - row0));
+  extern __shared__ __align__(16) unsigned char smraw[];
+  uint64_t* fbar = reinterpret_cast<uint64_t*>(smraw);          // [2] exchange-slot barriers
+  C* gbuf = reinterpret_cast<C*>(smraw + 16);                   // [3][rpc * mcp]
+  C* ops = gbuf + (size_t)3 * rpc * mcp;                        // [2][4][mc]: b, o0, o1, o2
+  C* full = ops + (size_t)8 * mc;                               // [2][mc]
+  C* tvs = full + 2 * mc;                                       // [mc]
+  C* zs = tvs + mc;                                             // [Lmax][rpc]: z, then y
+  __shared__ int failed;
+  const C* b = a.b + (size_t)rhs * a.Nc;
+  C* x = a.x + (size_t)rhs * a.Nc;
+  const unsigned slot_bytes = (unsigned)(mc * sizeof(C));
+  auto block_of = [&](int q) { return q < L ? A + q : A + (2 * L - 2 - q); };
+  auto prefetch = [&](int q) {
+    if (q < nsteps) {
+      const int j = block_of(q);
+      if (nrow > 0) {
+        const char* src = reinterpret_cast<const char*>(a.G + ((size_t)j * mc + row0) * mcp);
+        char* dst = reinterpret_cast<char*>(gbuf + (size_t)(q % 3) * rpc * mcp);
+        const int units = (int)((size_t)nrow * mcp * sizeof(C) / 16);
+        for (int u = tid; u < units; u += nth) cp_async16(dst + (size_t)u * 16, src + (size_t)u * 16);
+      }
+      // operands staged per entry k by the thread that later uses them, so the
+      // vector needs no CTA barrier after the copies: b_j[k], the diagonal
+      // coupling and the two off-diagonal ones, each at index k
+      C* o = ops + (size_t)(q & 1) * 4 * mc;
+      const bool f = q < L;
+      const size_t oc = (size_t)(f ? j - 1 : j) * mc;
+      for (int k = tid; k < mc; k += nth) {
+        if (f) cp_async_elem(o + k, b + (size_t)j * mc + k);
+        if (!f || q > 0) {
+          cp_async_elem(o + mc + k, a.cd + oc + k);
+          if (f) {  // C_{j-1}^T: cu[k-1] p[k-1] + cl[k+1] p[k+1]
+            if (k > 0) cp_async_elem(o + 2 * mc + k, a.cu + oc + k - 1);
+            if (k + 1 < mc) cp_async_elem(o + 3 * mc + k, a.cl + oc + k + 1);
+          } else {  // C_j: cl[k] p[k-1] + cu[k] p[k+1]
+            if (k > 0) cp_async_elem(o + 2 * mc + k, a.cl + oc + k);
+            if (k + 1 < mc) cp_async_elem(o + 3 * mc + k, a.cu + oc + k);
+          }
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  // rows are sent at steps 0 .. nsteps - 2 (the last step's rows stay local)
+  const int nsend = nsteps - 1;
+  if (tid == 0) {
+    failed = 0;
+    cmbar_init(fbar + 0, 1);
+    cmbar_init(fbar + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    if (nsend > 0) cmbar_expect(fbar + 0, slot_bytes);
+    if (nsend > 1) cmbar_expect(fbar + 1, slot_bytes);
+  }
+  // every barrier is initialised before any CTA of the cluster can send to it
+  cluster_arrive_release();
+  cluster_wait_acquire();
+  prefetch(0);
+  prefetch(1);
+  for (int q = 0; q < nsteps; ++q) {
+    const bool fwd = q < L;
+    const int j = block_of(q);
+    if (q > 0) {  // step q-1's rows, from every CTA of the cluster
+      uint64_t* bar = fbar + ((q - 1) & 1);
+      const unsigned par = (unsigned)(((q - 1) >> 1) & 1);
+      if (!failed) {
+        bool ok = false;
+        for (int it = 0; it < (1 << 20) && !ok; ++it) ok = cmbar_try(bar, par);
+        if (!ok) failed = 1;
+      }
+    }
+    cp_async_wait<1>();  // this thread's copies of this step (the next step's may be in flight)
+    const C* prev = full + ((q - 1) & 1) * mc;
+    const C* o = ops + (size_t)(q & 1) * 4 * mc;
+    for (int k = tid; k < mc; k += nth) {
+      C v;
+      v.x = 0;
+      v.y = 0;
+      if (!fwd || q > 0) {
+        cmac(v, o[mc + k], prev[k]);
+        if (k > 0) cmac(v, o[2 * mc + k], prev[k - 1]);
+        if (k + 1 < mc) cmac(v, o[3 * mc + k], prev[k + 1]);
+      }
+      if (fwd) {
+        const C bk = o[k];
+        v.x = bk.x - v.x;
+        v.y = bk.y - v.y;
+      }
+      tvs[k] = v;
+    }
+    __syncthreads();  // tvs and the G rows are visible; every thread is past its wait
+    // the slot just consumed takes the rows of step q + 1
+    if (tid == 0 && q > 0 && q + 1 <= nsend - 1 && !failed) cmbar_expect(fbar + ((q - 1) & 1), slot_bytes);
+    // step q + 2's copies: G into buffer (q + 2) % 3 (last read at step q - 1)
+    prefetch(q + 2);
+    const int rr = warp;
+    if (rr < nrow) {
+      C tv[NI];
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int k = lane + 32 * i;
+        if (k < mc) {
+          tv[i] = tvs[k];
+        } else {
+          tv[i].x = 0;
+          tv[i].y = 0;
+        }
+      }
+      const C* g = gbuf + (size_t)(q % 3) * rpc * mcp + (size_t)rr * mcp;
+      C acc;
+      acc.x = 0;
+      acc.y = 0;
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int k = lane + 32 * i;
+        if (k < mc) cmac(acc, g[k], tv[i]);
+      }
+      acc = warp_sum<T>(acc);
+      const size_t zi = (size_t)(j - A) * rpc + rr;
+      C val = acc;
+      if (!fwd) {
+        const C z = zs[zi];
+        val.x = z.x - acc.x;
+        val.y = z.y - acc.y;
+      }
+      if (lane == 0) zs[zi] = val;
+      if (q < nsend && lane < csz) {
+        const unsigned slot = smem_u32(full + (q & 1) * mc + row0 + rr);
+        st_async_c(mapa_u32(slot, lane), val, mapa_u32(smem_u32(fbar + (q & 1)), lane));
+      }
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int i = tid; i < L * nrow; i += nth) {
+    const int jj = i / nrow, rr = i - jj * nrow;
+    x[(size_t)(A + jj) * mc + row0 + rr] = zs[(size_t)jj * rpc + rr];
+  }
+  if (tid == 0 && failed) atomicExch(err, 1);
+  // no CTA leaves while another may still store into its shared memory
+  cluster_arrive_release();
+  cluster_wait_acquire();
+}
+
 // ------------------------------------------------------------- reduced system
 // rhat_k = b_s - C_{s-1}^T y_{s-1} - C_s y_{s+1} for every separator row s = sep[k]
 template <typename T>
@@ -712,6 +906,12 @@ static cudaError_t launch_tsgemm(const CoarsePartArgs<T>& a, cudaStream_t s) {
 
 // ------------------------------------------------------------- launcher
 template <typename T>
+size_t chunk_sweep2_smem(const CoarsePartArgs<T>& a) {
+  using C = typename Cx<T>::t;
+  return 16 + sizeof(C) * ((size_t)3 * a.rpc * a.mcp + (size_t)11 * a.mc + (size_t)a.Lmax * a.rpc);
+}
+
+template <typename T>
 size_t chunk_sweep_smem(const CoarsePartArgs<T>& a, bool prefetch) {
   using C = typename Cx<T>::t;
   size_t s = sizeof(C) * ((size_t)11 * a.mc + (size_t)a.Lmax * a.rpc);
@@ -787,7 +987,25 @@ cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster
   const bool pf = chunk_sweep_smem(a, true) <= 220 * 1024;
   const size_t sm1 = chunk_sweep_smem(a, pf);
   cudaError_t e;
-  if (a.sweep_variant == 1 && a.mc <= 256 && a.rpc <= 32) {
+  if (a.sweep_variant == 2 && a.mc <= 256 && a.rpc <= 32 && chunk_sweep2_smem(a) <= 220 * 1024 && a.err) {
+    cudaError_t e2 = cudaFuncSetAttribute(k_chunk_sweep2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)chunk_sweep2_smem(a));
+    if (e2 != cudaSuccess) return e2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster * a.P * nrhs, 1, 1);
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = chunk_sweep2_smem(a);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_chunk_sweep2<T>, a, a.err);
+    if (e == cudaSuccess) e = cudaGetLastError();
+  } else if (a.sweep_variant == 1 && a.mc <= 256 && a.rpc <= 32) {
     e = pf ? launch_cluster(k_chunk_sweep1<T, true>, a, cluster * a.P * nrhs, cluster, sm1, s, 1024)
            : launch_cluster(k_chunk_sweep1<T, false>, a, cluster * a.P * nrhs, cluster, sm1, s, 1024);
   } else {

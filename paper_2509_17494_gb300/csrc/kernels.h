@@ -184,7 +184,9 @@ struct CoarsePartArgs {
   int mc, mcp, P, rpc, Lmax, nred;
   int mcr, rpcm, nrhs;           // rpcm: rows per CTA of the multi-rhs sweep (even)
   int ldS;                       // row stride of Sinv (nred rounded up to even)
-  int sweep_variant;             // one-rhs chunk sweep: 0 two-phase (512 threads), 1 one barrier per step (1024)
+  int sweep_variant;             // one-rhs chunk sweep: 0 two-phase (512 threads), 1 one barrier per step (1024),
+                                 // 2 st.async row exchange on mbarriers (no cluster barrier per step)
+  int* err;                      // device flag set by a bounded wait that gave up (variant 2)
 };
 template <typename T>
 cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster, cudaStream_t s);

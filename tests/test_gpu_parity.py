@@ -138,6 +138,25 @@ def test_coarse_solve_fp64(th, c, variant):
         assert relerr(got, B.solve(rc)) < 1e-9
 
 
+@pytest.mark.parametrize("c", CASES)
+def test_coarse_solve_fp32_sweep_variants(th, c):
+    """The FP32 one-rhs coarse solve: the three chunk-sweep variants (two
+    phases, one cluster barrier per step, st.async row exchange on mbarriers)
+    do the same arithmetic in the same order, so they agree bitwise; against
+    the oracle within FP32 rounding of the explicit-inverse sweep."""
+    S, P = build(th, c, nrhs=1, prec="fp32", extra_prec=("fp64",))
+    B = twogrid.BandedSolver(P.Aq)
+    rc = dev(synth.random_complex(P.Nc, 8))
+    outs = []
+    for v in (0, 1, 2):
+        S.set_variant("coarse", "fp32", v)
+        outs.append(S.coarse_solve(rc))
+        S.device_status()
+    assert relerr(host(outs[0]), B.solve(host(rc))) < 1e-4
+    assert torch.equal(outs[1], outs[2])
+    assert relerr(host(outs[0]), host(outs[1])) < 1e-5
+
+
 @pytest.mark.parametrize("c", [CASES[0], CASES[2], CASES[5]])
 @pytest.mark.parametrize("nrhs", [2, 11])
 def test_coarse_solve_many_rhs(th, c, nrhs):
