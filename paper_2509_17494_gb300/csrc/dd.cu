@@ -96,7 +96,7 @@ template <typename T, int KIND, int NRHS, int MAXT>
 __global__ void __launch_bounds__(MAXT) k_dd_apply(const DDArgs<T> a) {
   using C = typename Cx<T>::t;
   constexpr int CPC = WTraits<KIND>::CPC;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   const int XL = a.NCH * CPC;
   C* xs = reinterpret_cast<C*>(smraw);        // [NRHS][XL]
   C* red = xs + NRHS * XL;                     // [G][NR][NRHS]
@@ -291,10 +291,12 @@ __device__ __forceinline__ void mbar_expect_tx_arrive(uint64_t* bar, unsigned by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
+// A waiting thread may be suspended for up to 10 us per call (it resumes when
+// the phase completes), so waiting warps do not spin on the issue slots.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   unsigned done;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 10000;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(done)
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
@@ -302,7 +304,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
 }
 // bounded wait: false after the iteration limit
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (int it = 0; it < (1 << 20); ++it)
+  for (int it = 0; it < (1 << 17); ++it)  // at most about 1.3 s
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
