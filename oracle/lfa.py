@@ -137,9 +137,13 @@ def _unit_cell_coarse(cell, p, mcells):
 
 
 class BlochOperators:
-    """Blocks P_{0,beta} of A, A_s, A_c, I_P, I_R for constant k, eps (2-D, Q_p, periodic)."""
+    """Blocks P_{0,beta} of A, A_s, A_c, I_P, I_R for constant k, eps (2-D, Q_p, periodic).
 
-    def __init__(self, p, kh, eps_over_k2, alpha_s):
+    coarse = 'qsfem': A_c is the QSFEM operator of Section 3.3 ('opt');
+    coarse = 'gal': A_c = I_R A_{alpha_c} I_P, standard Galerkin p-type coarsening
+    of Section 4 (the comparison of Fig. 3 (a)), alpha_c shifting k^2 in the volume term."""
+
+    def __init__(self, p, kh, eps_over_k2, alpha_s, coarse="qsfem", alpha_c=0.0):
         self.p = p
         mc = 3
         n = mc
@@ -149,9 +153,15 @@ class BlochOperators:
         ecell = np.full((n, n), eps_over_k2 * k * k)
         A = fem.assemble((n, n), p, h, fem.helmholtz_coefficient(kcell, ecell), kcell, (), True)
         As = fem.assemble((n, n), p, h, fem.shifted_coefficient(kcell, ecell, alpha_s), kcell, (), True)
-        Ac = qsfem.assemble_coarse(n, p, kcell, ecell, (), True)
         IP = fem.prolongation(n, p, 2, True)
         IR = IP.T.tocsr()
+        if coarse == "qsfem":
+            Ac = qsfem.assemble_coarse(n, p, kcell, ecell, (), True)
+        elif coarse == "gal":
+            Ash = fem.assemble((n, n), p, h, fem.shifted_coefficient(kcell, ecell, alpha_c), kcell, (), True)
+            Ac = (IR @ Ash @ IP).tocsr()
+        else:
+            raise ValueError(coarse)
         betas = list(itertools.product((-1, 0, 1), repeat=2))
         f0 = _unit_cell_fine((0, 0), p, mc)
         c0 = _unit_cell_coarse((0, 0), p, mc)
@@ -192,8 +202,8 @@ def theta_grid(npts):
     return [np.array([a, b]) for a in t for b in t]
 
 
-def lfa_rho(p, dofs_per_wavelength, D=0.01, alpha_s=0.2, n_s=1, omega_c=1.0, npts=48):
+def lfa_rho(p, dofs_per_wavelength, D=0.01, alpha_s=0.2, n_s=1, omega_c=1.0, npts=48, coarse="qsfem", alpha_c=0.0):
     """sup_theta rho(M(theta)) with eps = D k^2 / pi (Section 6, Eq. epsilon_ksquare_D)."""
     kh = 2 * math.pi * p / dofs_per_wavelength
-    ops = BlochOperators(p, kh, D / math.pi, alpha_s)
+    ops = BlochOperators(p, kh, D / math.pi, alpha_s, coarse, alpha_c)
     return ops.rho(theta_grid(npts), n_s, omega_c)

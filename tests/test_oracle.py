@@ -290,16 +290,19 @@ def test_banded_coarse_solve_matches_splu():
     assert np.linalg.norm(x1 - x2) < 1e-11 * np.linalg.norm(x2)
 
 
-@pytest.mark.parametrize("p,ppw,n_s,omega_c", [(4, 10, 1, 1.0), (4, 8, 2, 0.8), (2, 12, 1, 1.0)])
-def test_bruteforce_spectral_radius_equals_bloch_lfa(p, ppw, n_s, omega_c):
+@pytest.mark.parametrize("p,ppw,n_s,omega_c,coarse,alpha_c", [(4, 10, 1, 1.0, "qsfem", 0.0), (4, 8, 2, 0.8, "qsfem", 0.0),
+                                                               (2, 12, 1, 1.0, "qsfem", 0.0), (4, 8, 1, 1.0, "gal", 0.0),
+                                                               (6, 10, 1, 1.0, "gal", 0.05)])
+def test_bruteforce_spectral_radius_equals_bloch_lfa(p, ppw, n_s, omega_c, coarse, alpha_c):
     """rho of the oracle's own TwoGridStep on a periodic torus (one subdomain = exact
-    shifted smoother) equals sup over the torus' Bloch vectors of rho(M(theta))."""
+    shifted smoother) equals sup over the torus' Bloch vectors of rho(M(theta)),
+    for the QSFEM and the Galerkin coarse level."""
     mcells, D, alpha_s = 4, 0.01, 0.2
     kh = 2 * math.pi * p / ppw
     k = kh * mcells
     kc = np.full((mcells, mcells), k)
     ec = np.full((mcells, mcells), D * k * k / math.pi)
-    P = twogrid.Problem(mcells, p, kc, ec, alpha_s=alpha_s, periodic=True)
+    P = twogrid.Problem(mcells, p, kc, ec, alpha_s=alpha_s, periodic=True, coarse_kind=coarse, alpha_c=alpha_c)
     TG = twogrid.TwoGrid(P, l_dd=mcells, n_s=n_s, omega_c=omega_c, coarse_solver="splu")
     N = P.N
     M = np.zeros((N, N), dtype=complex)
@@ -309,7 +312,7 @@ def test_bruteforce_spectral_radius_equals_bloch_lfa(p, ppw, n_s, omega_c):
         e[j] = 1.0
         M[:, j] = TG.step(e, z)
     rho_brute = np.max(np.abs(np.linalg.eigvals(M)))
-    ops = lfa.BlochOperators(p, kh, D / math.pi, alpha_s)
+    ops = lfa.BlochOperators(p, kh, D / math.pi, alpha_s, coarse, alpha_c)
     ths = [2 * math.pi * np.array([a, b]) / mcells for a in range(mcells) for b in range(mcells)]
     rho_lfa = ops.rho(ths, n_s, omega_c)
     assert abs(rho_brute - rho_lfa) < 1e-9 * max(1.0, rho_lfa)
