@@ -74,6 +74,8 @@ def parse():
                     help="add iterations vs problem size for opt and gal (the trend of the paper's Fig. 5)")
     ap.add_argument("--table2", action="store_true",
                     help="add the shift study of the paper's Table 2 (gal coarsening, p = 6) on the GPU")
+    ap.add_argument("--lfa", choices=["sweep", "none"], default="sweep",
+                    help="Fourier-analysis rates against dofs per wavelength on the GPU (Figs. 3 and 4)")
     return ap.parse_args()
 
 
@@ -374,6 +376,8 @@ def run_native(args):
         line["gal_sweep"] = gal_sweep_section(dev)
     if args.table2:
         line["table2"] = table2_section(dev)
+    if args.lfa != "none":
+        line["lfa"] = lfa_section(rank == 0 and world == 1 and not args.no_cpu_baseline)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_cycles)
     if rank == 0:
@@ -667,6 +671,53 @@ def table2_section(dev):
                 row.append(info["iters"] if info["converged"] else -1)
             rows.append(row)
         out[f"ppw{ppw}"] = {"gpu": rows, "paper": TABLE2_PAPER[ppw]}
+    return out
+
+
+def lfa_section(with_oracle):
+    """Asymptotic two-grid rates sup_theta rho(M(theta)) from the GPU Fourier
+    analysis (Section 6) against dofs per wavelength, as in Figs. 3 and 4: QSFEM
+    ('opt') and Galerkin ('gal') coarse levels for p = 2, 4, 6 (exact shifted
+    smoother, alpha_s = 0.2, eps = 0.01 k^2 / pi, 48 x 48 theta grid), and for
+    opt the smoothing-step / relaxation variants of Fig. 4.  With the oracle the
+    same analysis of one parameter point on the host (numpy eigvals) gives the
+    CPU rate of theta points per second."""
+    import math
+
+    import numpy as np
+
+    import paper_2509_17494_gb300 as th
+
+    npts, D, a_s = 48, 0.01, 0.2
+    ppws = [4, 5, 6, 7, 8, 10, 12, 16, 20]
+    out = {"setup": "periodic plane, constant k, eps = 0.01 k^2 / pi, alpha_s = 0.2, exact shifted smoother, "
+                    f"{npts} x {npts} theta grid", "ppw": ppws, "opt": {}, "gal": {}, "opt_variants": {}}
+    n_theta = 0
+    t0 = time.perf_counter()
+    for p in (2, 4, 6):
+        params = [[2 * math.pi * p / q, D / math.pi, a_s, 1.0] for q in ppws]
+        out["opt"][f"p{p}"] = [round(float(v), 4) for v in th.lfa_rho(p, params, npts=npts)]
+        out["gal"][f"p{p}"] = [round(float(v), 4) for v in th.lfa_rho(p, params, npts=npts, coarse="gal")]
+        n_theta += 2 * len(params) * npts * npts
+    for p in (4, 6):
+        for n_s, om in ((1, 0.8), (2, 1.0), (2, 0.8)):
+            params = [[2 * math.pi * p / q, D / math.pi, a_s, om] for q in ppws]
+            out["opt_variants"][f"p{p}_ns{n_s}_omega{om}"] = [round(float(v), 4)
+                                                              for v in th.lfa_rho(p, params, n_s=n_s, npts=npts)]
+            n_theta += len(params) * npts * npts
+    gpu_s = time.perf_counter() - t0
+    out["gpu"] = {"theta_points": n_theta, "wall_s": round(gpu_s, 3),
+                  "theta_per_s": round(n_theta / gpu_s, 1)}
+    if with_oracle:
+        from oracle import lfa as olfa
+
+        t1 = time.perf_counter()
+        ops = olfa.BlochOperators(4, 2 * math.pi * 4 / 8, D / math.pi, a_s)
+        grid = olfa.theta_grid(16)
+        ops.rho(grid)
+        cpu_s = time.perf_counter() - t1
+        out["oracle"] = {"sample": "p = 4, 8 dofs per wavelength, 16 x 16 theta grid (numpy eigvals, one process)",
+                         "theta_per_s": round(len(grid) / cpu_s, 1)}
     return out
 
 

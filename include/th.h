@@ -421,6 +421,26 @@ th_status th_host_galerkin(const th_mesh* mesh, const double* k_host, const doub
                            const th_params* prm, double* stencil, size_t stencil_len,
                            const double* b, double* x);
 
+/* ---------------------------------------------------- Fourier analysis */
+
+/* Local Fourier analysis of the two-grid method (Section 6, Eq. symbol_sum):
+ * for nparam parameter points on the periodic plane with constant k and eps
+ * (Q_p, p in {2, 4, 6}; coarse level TH_CK_QSFEM, or TH_CK_GALERKIN with
+ * A_c = I_R A_{alpha_c} I_P (Section 4, Fig. 3 (a)); the exact shifted smoother
+ * S = I - A_s^{-1} A), the spectral radius of the Bloch symbol
+ * M(theta) = S^{n_s} K S^{n_s}, K = I - omega_c I_P A_c^{-1} I_R A, on the
+ * grid theta = (-pi + 2 pi i / npts, -pi + 2 pi j / npts), and its maximum.
+ *   params: host, nparam x 4 doubles (k h, eps / k^2, alpha_s, omega_c), k h > 0.
+ *   rho_max: host, nparam doubles (output): the maximum over the grid.
+ *   rho_theta: host, nparam x npts^2 doubles (output, index i npts + j), or NULL.
+ * The symbols' blocks are assembled on the host in FP64; one CTA per
+ * (parameter point, theta) forms the symbols, eliminates, and evaluates rho by
+ * Gelfand's formula with 40 normalised squarings (relative error ~1e-10).
+ * Allocates and frees its own device buffers; synchronous on `stream`.
+ * TH_ERR_ARG for invalid sizes or parameters, TH_ERR_UNSUPPORTED for other p. */
+th_status th_lfa_rho(int p, int n_s, int npts, int coarse_kind, double alpha_c, const double* params, int nparam,
+                     double* rho_max, double* rho_theta, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

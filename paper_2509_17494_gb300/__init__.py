@@ -110,6 +110,7 @@ def lib() -> ctypes.CDLL:
         "th_host_inverse_rows": ([ctypes.POINTER(Mesh), P, P, ctypes.POINTER(Params), I, P, P,
                                   ctypes.c_size_t], I),
         "th_host_galerkin": ([ctypes.POINTER(Mesh), P, P, ctypes.POINTER(Params), P, ctypes.c_size_t, P, P], I),
+        "th_lfa_rho": ([I, I, I, I, D, P, I, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -242,6 +243,23 @@ def host_galerkin(n, p, k_cell, eps_cell=None, bc="robin", alpha_c=0.0, b=None):
            "th_host_galerkin")
     sten = (st[0::2] + 1j * st[1::2]).reshape(mc * mc, S, S)
     return sten, (xo if b is not None else None)
+
+
+def lfa_rho(p, params, n_s=1, npts=48, per_theta=False, coarse="qsfem", alpha_c=0.0, stream=None):
+    """Fourier analysis of the two-grid method on the GPU (th_lfa_rho).
+
+    params: (nparam, 4) array of (k h, eps / k^2, alpha_s, omega_c).  Returns the
+    maximum of rho(M(theta)) over the npts x npts theta grid per parameter point,
+    and with per_theta also the (nparam, npts, npts) values."""
+    prm = np.ascontiguousarray(np.atleast_2d(np.asarray(params, dtype=np.float64)))
+    if prm.shape[1] != 4:
+        raise ValueError("params must have 4 columns (k h, eps / k^2, alpha_s, omega_c)")
+    nparam = prm.shape[0]
+    rmax = np.zeros(nparam)
+    rth = np.zeros((nparam, npts, npts)) if per_theta else None
+    _check(lib().th_lfa_rho(int(p), int(n_s), int(npts), COARSE_KIND[coarse], float(alpha_c), prm.ctypes.data, nparam,
+                            rmax.ctypes.data, rth.ctypes.data if per_theta else None, stream), "th_lfa_rho")
+    return (rmax, rth) if per_theta else rmax
 
 
 class TwoGridSolver:
