@@ -101,6 +101,11 @@ struct th_ctx {
   double2 *Vk = nullptr, *Zk = nullptr, *w = nullptr, *h1 = nullptr, *h2 = nullptr, *ybuf = nullptr,
           *dpart = nullptr;
   double *npart = nullptr, *nrm = nullptr, *scal = nullptr;
+  // device-side Arnoldi state (Hessenberg columns, rotations, g, ||f||, flags, status)
+  double2 *Hd = nullptr, *csd = nullptr, *snd = nullptr, *gd = nullptr;
+  double *fnd = nullptr, *statd = nullptr;
+  int* actd = nullptr;
+  double* pin = nullptr;  // pinned host ring for the lagged status reads (allocated by th_solve)
   double2 *fin = nullptr, *uin = nullptr;  // device staging for the host-buffer entry points
   // per-kernel event timing (th_profile)
   bool prof_on = false;
@@ -132,6 +137,7 @@ struct th_ctx {
     graphs.clear();
   }
   ~th_ctx() {
+    if (pin) cudaFreeHost(pin);
     delete unet;
     drop_graphs();
     if (gstream) cudaStreamDestroy(gstream);
@@ -297,6 +303,13 @@ void carve_all(th_ctx& x, Carve& c) {
   x.npart = c.take<double>((size_t)nr * x.nblk);
   x.nrm = c.take<double>((size_t)nr);
   x.scal = c.take<double>((size_t)nr);
+  x.Hd = c.take<double2>((size_t)nr * (m + 1) * m);
+  x.csd = c.take<double2>((size_t)nr * m);
+  x.snd = c.take<double2>((size_t)nr * m);
+  x.gd = c.take<double2>((size_t)nr * (m + 1));
+  x.fnd = c.take<double>((size_t)nr);
+  x.statd = c.take<double>((size_t)nr * 5);
+  x.actd = c.take<int>((size_t)nr);
   x.fin = c.take<double2>((size_t)nr * g.N);
   x.uin = c.take<double2>((size_t)nr * g.N);
 }
@@ -1703,11 +1716,13 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
   const th::Geometry& g = x->g;
   const long long N = g.N;
   const int m = x->prm.restart;
+  if (!x->pin && cudaHostAlloc(&x->pin, sizeof(double) * 2 * 5 * x->prm.nrhs_max, cudaHostAllocDefault) != cudaSuccess)
+    return TH_ERR_NOMEM;
   const long long vstride = N * (long long)nrhs;  // between basis vectors
   const double2* f2 = reinterpret_cast<const double2*>(f);
   double2* u2 = reinterpret_cast<double2*>(u);
   const double tol = x->prm.tol;
-  std::vector<double> fn, beta, hn;
+  std::vector<double> fn, beta;
   if ((st = norms(*x, f2, nrhs, fn, s)) != TH_OK) return st;
   for (double v : fn)
     if (!std::isfinite(v)) return TH_ERR_NONFINITE;
@@ -1716,7 +1731,6 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
     if (fn[r] == 0.0) done[r] = 1;
   std::vector<cplx> H((size_t)nrhs * (m + 1) * m), cs((size_t)nrhs * m), sn((size_t)nrhs * m),
       gg((size_t)nrhs * (m + 1));
-  std::vector<double2> hh1((size_t)nrhs * (m + 1)), hh2((size_t)nrhs * (m + 1));
   std::vector<double> scal(nrhs);
   std::vector<double2> yv;
   int it = 0;
@@ -1755,11 +1769,81 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
       std::fill(gg.begin() + (size_t)r * (m + 1), gg.begin() + (size_t)(r + 1) * (m + 1), cplx(0.0));
       gg[(size_t)r * (m + 1)] = beta[r];
     }
-    TH_CU(cudaMemcpyAsync(x->scal, scal.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    // device Arnoldi state for this restart cycle
+    {
+      std::vector<double2> g0((size_t)nrhs * (m + 1), make_double2(0.0, 0.0));
+      for (int r = 0; r < nrhs; ++r) g0[(size_t)r * (m + 1)] = make_double2(beta[r], 0.0);
+      TH_CU(cudaMemcpyAsync(x->gd, g0.data(), sizeof(double2) * g0.size(), cudaMemcpyHostToDevice, s));
+      TH_CU(cudaMemcpyAsync(x->actd, active.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+      TH_CU(cudaMemcpyAsync(x->fnd, fn.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+      TH_CU(cudaMemcpyAsync(x->scal, scal.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+      // the host buffers are read by the copies above: finish them before they change
+      TH_CU(cudaStreamSynchronize(s));
+    }
     x->launches += 1;
     TH_CU(th::launch_scale_rhs(x->Vk, x->Vk, x->scal, N, nrhs, s));
-    int jdone = 0;
-    for (int j = 0; j < m; ++j) {
+    th::ArnoldiArgs aa{x->h1, x->nrm, x->Hd, x->csd, x->snd, x->gd, x->fnd, x->actd, x->scal, x->statd, tol, nrhs, m};
+    // Arnoldi steps are enqueued one ahead of the host: after enqueueing step j the
+    // host reads the status of step j - 1 (pinned copy, event), so the GPU does not
+    // wait for the host between steps.  When the residual estimates predict that
+    // step j converges, the host reads its status before enqueueing step j + 1, so
+    // that no step is enqueued after the last one in the usual case.
+    cudaEvent_t evs[2];
+    TH_CU(cudaEventCreateWithFlags(&evs[0], cudaEventDisableTiming));
+    if (cudaEventCreateWithFlags(&evs[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventDestroy(evs[0]);
+      return TH_ERR_CUDA;
+    }
+    struct EvGuard {
+      cudaEvent_t* e;
+      ~EvGuard() {
+        cudaEventDestroy(e[0]);
+        cudaEventDestroy(e[1]);
+      }
+    } evguard{evs};
+    const int room = std::max(0, std::min(m, x->prm.maxit - it));
+    int jdone = 0, it_cycle = 0, last_read = -1;
+    bool stop = false, expect_conv = false;
+    std::vector<double> stj((size_t)nrhs * 5), rel_prev(nrhs, -1.0), rel_last(nrhs, -1.0);
+    auto read_status = [&](int jj) -> th_status {
+      TH_CU(cudaEventSynchronize(evs[jj & 1]));
+      std::memcpy(stj.data(), x->pin + (size_t)(jj & 1) * nrhs * 5, sizeof(double) * nrhs * 5);
+      last_read = jj;
+      bool any = false, cancel = false;
+      for (int r = 0; r < nrhs; ++r) {
+        const double* sr = &stj[(size_t)r * 5];
+        if (sr[3] != 0.0) return TH_ERR_NONFINITE;
+        if (active[r]) {
+          jr[r] = (int)sr[1];
+          its[r] = it + jj + 1;
+          if (sr[2] != 0.0) cancel = true;
+          if (sr[0] == 0.0) active[r] = 0;
+          rel_prev[r] = rel_last[r];
+          rel_last[r] = sr[4];
+        }
+        any = any || active[r];
+      }
+      jdone = jj + 1;
+      it_cycle = jj + 1;
+      if (!any || cancel || it + jj + 1 >= x->prm.maxit) stop = true;
+      if (x->coarse_mode == 1 && it + jj + 1 >= limit) {
+        switch_now = true;
+        stop = true;
+      }
+      // does the next step reach the tolerance for every active rhs (geometric extrapolation)?
+      expect_conv = any;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!active[r]) continue;
+        const double q = (rel_prev[r] > 0.0 && rel_last[r] > 0.0) ? std::min(1.0, rel_last[r] / rel_prev[r]) : 1.0;
+        if (!(rel_last[r] * q <= 3.0 * tol)) expect_conv = false;
+      }
+      return TH_OK;
+    };
+    for (int j = 0; j < room && !stop; ++j) {
+      if (expect_conv && last_read < j - 1) {  // the step before this one may have converged
+        if ((st = read_status(j - 1)) != TH_OK) return st;
+        if (stop) break;
+      }
       double2* Vj = x->Vk + (size_t)j * vstride;
       double2* Zj = x->Zk + (size_t)j * vstride;
       if (x->use_graphs && !x->prof_on) {
@@ -1770,82 +1854,40 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
       }
       if (st != TH_OK) return st;
       if ((st = fine_apply<double>(*x, TH_OP_A, Zj, nullptr, x->w, nrhs, s)) != TH_OK) return st;
-      // classical Gram-Schmidt, one pass, with a second pass only after severe
-      // cancellation, ||w - V h1|| < 1e-2 ||w|| for some rhs (the loss of
-      // orthogonality of one pass grows like eps (||w|| / ||w - V h1||)^2; with
-      // the two-grid preconditioner the ratio stays near 3).  FP64 arithmetic
-      // is scarce on this GPU: the single pass halves the Arnoldi step's work.
-      x->launches += 3;
+      // one classical Gram-Schmidt pass (the coefficients and ||w||^2 before it), then
+      // ||w||^2 after it; a pass that cancels more than 99.99 % of ||w||^2 makes the
+      // host restart (loss of orthogonality ~ eps ||w||^2 / ||w - V h||^2), which
+      // with the two-grid preconditioner does not occur in practice
+      x->launches += 6;
       {
         Prof prof(*x, TH_K_KRYLOV, s);
         TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, s));
         TH_CU(th::launch_maxpy(x->Vk, vstride, x->h1, j + 2, x->w, N, j + 1, nrhs, -1.0, s));
+        TH_CU(th::launch_norm2(x->w, N, nrhs, x->npart, x->nrm, x->nblk, s));
+        TH_CU(th::launch_arnoldi(aa, j, s));
+        TH_CU(th::launch_scale_rhs(x->w, x->Vk + (size_t)(j + 1) * vstride, x->scal, N, nrhs, s));
       }
-      TH_CU(cudaMemcpyAsync(hh1.data(), x->h1, sizeof(double2) * (j + 2) * nrhs, cudaMemcpyDeviceToHost, s));
-      if ((st = norms(*x, x->w, nrhs, hn, s)) != TH_OK) return st;
-      bool reorth = false;
-      for (int r = 0; r < nrhs; ++r)
-        if (active[r] && hn[r] * hn[r] < 1e-4 * hh1[(size_t)r * (j + 2) + j + 1].x) reorth = true;
-      std::fill(hh2.begin(), hh2.begin() + (size_t)(j + 1) * nrhs, make_double2(0.0, 0.0));
-      if (reorth) {
-        x->launches += 3;
-        {
-          Prof prof(*x, TH_K_KRYLOV, s);
-          TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, 0, nrhs, x->dpart, x->h2, x->nblk, s));
-          TH_CU(th::launch_maxpy(x->Vk, vstride, x->h2, j + 1, x->w, N, j + 1, nrhs, -1.0, s));
-        }
-        TH_CU(cudaMemcpyAsync(hh2.data(), x->h2, sizeof(double2) * (j + 1) * nrhs, cudaMemcpyDeviceToHost, s));
-        if ((st = norms(*x, x->w, nrhs, hn, s)) != TH_OK) return st;
-      }
-      for (int r = 0; r < nrhs; ++r) {
-        if (!std::isfinite(hn[r])) return TH_ERR_NONFINITE;
-        scal[r] = (active[r] && hn[r] > 0.0) ? 1.0 / hn[r] : 0.0;
-      }
-      TH_CU(cudaMemcpyAsync(x->scal, scal.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
-      x->launches += 1;
-      TH_CU(th::launch_scale_rhs(x->w, x->Vk + (size_t)(j + 1) * vstride, x->scal, N, nrhs, s));
-      ++it;
-      jdone = j + 1;
-      bool any = false;
-      for (int r = 0; r < nrhs; ++r) {
-        if (!active[r]) continue;
-        cplx* Hc = &H[((size_t)r * (m + 1)) * m];  // column-major (m+1) x m: Hc[i + j (m+1)]
-        for (int i = 0; i <= j; ++i) {
-          const double2 a1 = hh1[(size_t)r * (j + 2) + i], a2 = hh2[(size_t)r * (j + 1) + i];
-          Hc[i + (size_t)j * (m + 1)] = cplx(a1.x + a2.x, a1.y + a2.y);
-        }
-        Hc[j + 1 + (size_t)j * (m + 1)] = hn[r];
-        cplx* c_ = &cs[(size_t)r * m];
-        cplx* s_ = &sn[(size_t)r * m];
-        for (int i = 0; i < j; ++i) {
-          const cplx a = Hc[i + (size_t)j * (m + 1)], b = Hc[i + 1 + (size_t)j * (m + 1)];
-          Hc[i + (size_t)j * (m + 1)] = std::conj(c_[i]) * a + std::conj(s_[i]) * b;
-          Hc[i + 1 + (size_t)j * (m + 1)] = -s_[i] * a + c_[i] * b;
-        }
-        const cplx a = Hc[j + (size_t)j * (m + 1)], b = Hc[j + 1 + (size_t)j * (m + 1)];
-        const double den = std::sqrt(std::norm(a) + std::norm(b));
-        c_[j] = den > 0 ? a / den : cplx(1.0);
-        s_[j] = den > 0 ? b / den : cplx(0.0);
-        Hc[j + (size_t)j * (m + 1)] = den;
-        Hc[j + 1 + (size_t)j * (m + 1)] = 0.0;
-        cplx* gr = &gg[(size_t)r * (m + 1)];
-        gr[j + 1] = -s_[j] * gr[j];
-        gr[j] = std::conj(c_[j]) * gr[j];
-        its[r] = it;
-        jr[r] = j + 1;
-        if (std::abs(gr[j + 1]) <= tol * fn[r] || hn[r] == 0.0) {
-          active[r] = 0;
-        } else {
-          any = true;
-        }
-      }
-      if (!any || it >= x->prm.maxit) break;
-      if (x->coarse_mode == 1 && it >= limit) {
-        switch_now = true;
-        break;
-      }
+      TH_CU(cudaMemcpyAsync(x->pin + (size_t)(j & 1) * nrhs * 5, x->statd, sizeof(double) * nrhs * 5,
+                            cudaMemcpyDeviceToHost, s));
+      TH_CU(cudaEventRecord(evs[j & 1], s));
+      if (j >= 1 && last_read < j - 1 && (st = read_status(j - 1)) != TH_OK) return st;
     }
+    if (!stop && room > 0 && last_read < room - 1 && (st = read_status(room - 1)) != TH_OK) return st;
+    it += it_cycle;
+    // the Hessenberg columns and g of the valid steps (a discarded step touches neither)
+    const int jmax = jdone;
+    std::vector<double2> Hh((size_t)nrhs * (m + 1) * m), gh((size_t)nrhs * (m + 1));
+    if (jmax > 0) {
+      TH_CU(cudaMemcpyAsync(Hh.data(), x->Hd, sizeof(double2) * Hh.size(), cudaMemcpyDeviceToHost, s));
+      TH_CU(cudaMemcpyAsync(gh.data(), x->gd, sizeof(double2) * gh.size(), cudaMemcpyDeviceToHost, s));
+      TH_CU(cudaStreamSynchronize(s));
+    }
+    for (size_t q = 0; q < H.size(); ++q) H[q] = cplx(Hh[q].x, Hh[q].y);
+    for (size_t q = 0; q < gg.size(); ++q) gg[q] = cplx(gh[q].x, gh[q].y);
+    for (int r = 0; r < nrhs; ++r) jr[r] = std::min(jr[r], jmax);
+    const int jdone_all = jmax;
     // x += Z y per right-hand side (y = 0 beyond its own last step)
+    jdone = jdone_all;
     yv.assign((size_t)nrhs * jdone, make_double2(0, 0));
     for (int r = 0; r < nrhs; ++r) {
       const int jj = jr[r];

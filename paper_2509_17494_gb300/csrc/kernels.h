@@ -282,6 +282,22 @@ cudaError_t launch_maxpy(const double2* Vbase, long long vstride, const double2*
 // nrm2[rhs] = ||w[rhs]||^2 (fixed-order two-pass reduction into part/out)
 cudaError_t launch_norm2(const double2* w, long long N, int nrhs, double* part, double* out,
                          int nblk, cudaStream_t s);
+// FGMRES Arnoldi bookkeeping on the device (one thread per rhs), see vec.cu
+struct ArnoldiArgs {
+  const double2* h;   // [rhs][j + 2]: Gram-Schmidt coefficients, then ||w||^2 before the pass
+  const double* nrm;  // [rhs] ||w||^2 after the pass
+  double2* H;         // [rhs][m][m + 1] Hessenberg columns (column-major)
+  double2* cs;        // [rhs][m] Givens rotations
+  double2* sn;
+  double2* g;         // [rhs][m + 1] rotated residual vector
+  const double* fn;   // [rhs] ||f||
+  int* active;        // [rhs] 1 while the rhs iterates
+  double* scal;       // [rhs] out: 1 / h_{j+1,j} (0 if inactive)
+  double* stat;       // [rhs][5] out: active, steps, severe cancellation, non-finite, |g_{j+1}| / ||f||
+  double tol;
+  int nrhs, m;
+};
+cudaError_t launch_arnoldi(const ArnoldiArgs& a, int j, cudaStream_t s);
 // out[rhs] = in[rhs] * scale[rhs] (real scale per rhs from a device array; 0 if scale is not finite)
 cudaError_t launch_scale_rhs(const double2* in, double2* out, const double* inv, long long N, int nrhs,
                              cudaStream_t s);

@@ -399,3 +399,69 @@ cudaError_t launch_scale_rhs(const double2* in, double2* out, const double* inv,
 }
 
 }  // namespace th
+
+namespace th {
+// ------------------------------------------------- K9b Arnoldi bookkeeping
+// One thread per right-hand side: column j of the Hessenberg matrix from the
+// Gram-Schmidt coefficients and ||w||, the earlier Givens rotations applied, a
+// new rotation, the rotated residual vector g, the scale 1/h_{j+1,j} of the next
+// basis vector, and the status the host reads one iteration later.
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+
+__global__ void k_arnoldi(ArnoldiArgs a, int j) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.nrhs) return;
+  const int m = a.m;
+  double* st = a.stat + (size_t)r * 5;
+  if (!a.active[r]) {
+    a.scal[r] = 0.0;
+    st[0] = 0.0;
+    return;
+  }
+  const double2* h = a.h + (size_t)r * (j + 2);  // j + 1 coefficients, then ||w||^2 before the pass
+  const double hn2 = a.nrm[r], hn = sqrt(hn2);
+  double2* Hc = a.H + (size_t)r * (m + 1) * m + (size_t)j * (m + 1);
+  for (int i = 0; i <= j; ++i) Hc[i] = h[i];
+  Hc[j + 1] = make_double2(hn, 0.0);
+  a.scal[r] = (hn > 0.0 && isfinite(hn)) ? 1.0 / hn : 0.0;
+  double2* cs = a.cs + (size_t)r * m;
+  double2* sn = a.sn + (size_t)r * m;
+  for (int i = 0; i < j; ++i) {
+    const double2 x0 = Hc[i], x1 = Hc[i + 1];
+    const double2 t0 = zmul(zconj(cs[i]), x0), t1 = zmul(zconj(sn[i]), x1);
+    const double2 u0 = zmul(sn[i], x0), u1 = zmul(cs[i], x1);
+    Hc[i] = make_double2(t0.x + t1.x, t0.y + t1.y);
+    Hc[i + 1] = make_double2(u1.x - u0.x, u1.y - u0.y);
+  }
+  const double2 x0 = Hc[j], x1 = Hc[j + 1];
+  const double den = sqrt(x0.x * x0.x + x0.y * x0.y + x1.x * x1.x + x1.y * x1.y);
+  cs[j] = den > 0 ? make_double2(x0.x / den, x0.y / den) : make_double2(1.0, 0.0);
+  sn[j] = den > 0 ? make_double2(x1.x / den, x1.y / den) : make_double2(0.0, 0.0);
+  Hc[j] = make_double2(den, 0.0);
+  Hc[j + 1] = make_double2(0.0, 0.0);
+  double2* g = a.g + (size_t)r * (m + 1);
+  const double2 gj = g[j];
+  const double2 gn = zmul(sn[j], gj);
+  g[j + 1] = make_double2(-gn.x, -gn.y);
+  g[j] = zmul(zconj(cs[j]), gj);
+  const double res = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y);
+  const bool conv = res <= a.tol * a.fn[r] || hn == 0.0;
+  // status: [0] 1 while active after this step, [1] last step done (1-based), [2] 1 after severe
+  // cancellation in the single Gram-Schmidt pass, [3] 1 if ||w|| is not finite, [4] the
+  // residual estimate |g_{j+1}| / ||f||
+  st[0] = conv ? 0.0 : 1.0;
+  st[1] = (double)(j + 1);
+  st[2] = (hn2 < 1e-4 * h[j + 1].x) ? 1.0 : 0.0;
+  st[3] = isfinite(hn) ? 0.0 : 1.0;
+  st[4] = a.fn[r] > 0.0 ? res / a.fn[r] : 0.0;
+  if (conv) a.active[r] = 0;
+}
+
+cudaError_t launch_arnoldi(const ArnoldiArgs& a, int j, cudaStream_t s) {
+  k_arnoldi<<<(a.nrhs + 63) / 64, 64, 0, s>>>(a, j);
+  return cudaGetLastError();
+}
+}  // namespace th
