@@ -208,7 +208,7 @@ void carve_all(th_ctx& x, Carve& c) {
     x.W[k] = has_prec(x.avail, k) ? (void*)c.take<uint4>((size_t)g.nsub * x.wchunks[k] * g.NR) : nullptr;
   }
   x.wscale16 = has_prec(x.avail, TH_PREC_FP16) ? c.take<float>(g.nsub) : nullptr;
-  x.Wu = (!d3 && has_prec(x.avail, TH_PREC_BF16) && g.NR <= 128)
+  x.Wu = (has_prec(x.avail, TH_PREC_BF16) && g.NR <= 128 && prm.nrhs_max >= 8)
              ? c.take<unsigned char>((size_t)g.nsub * th::dd_umma_bytes_per_sub(g.NR, g.NC))
              : nullptr;
   const bool fp64 = has_prec(x.avail, TH_PREC_FP64);
@@ -574,6 +574,7 @@ th_status dd_apply(th_ctx& x, int wkind, const typename th::Cx<T>::t* r, int nrh
       u.nrhs = nrhs;
       u.M8 = (g.NR + 7) / 8;
       u.K8 = 2 * ((g.NC + 15) / 16);
+      u.dim3 = g.dim == 3 ? 1 : 0;
       return cuda_status(th::launch_dd_umma(u, x.sms, s));
     }
   }
@@ -998,7 +999,18 @@ th_status tune_dd(th_ctx& x, int wkind, cudaStream_t s, int& choice) {
   C* r = nullptr;
   if constexpr (std::is_same<T, double>::value) r = x.r64; else r = x.r32;
   if (!r || !x.W[wkind]) return TH_OK;
-  TH_CU(cudaMemsetAsync(r, 0, sizeof(C) * x.g.N, s));
+  // timed at the batch width the context was set up for (up to 8 right-hand sides):
+  // the best variant for one rhs is not the best for tiles of several
+  const int nt = std::max(1, std::min(x.prm.nrhs_max, 8));
+  TH_CU(cudaMemsetAsync(r, 0, sizeof(C) * x.g.N * nt, s));
+  // the CUDA-core variants are compared (the tensor-core path does not depend on them)
+  const int saved_tc = x.dd_tc;
+  x.dd_tc = 0;
+  struct TcRestore {
+    th_ctx& x;
+    int v;
+    ~TcRestore() { x.dd_tc = v; }
+  } tc_restore{x, saved_tc};
   cudaEvent_t e0, e1;
   TH_CU(cudaEventCreate(&e0));
   TH_CU(cudaEventCreate(&e1));
@@ -1007,14 +1019,14 @@ th_status tune_dd(th_ctx& x, int wkind, cudaStream_t s, int& choice) {
   for (int v = 0; v < 4; ++v) {
     choice = v;
     bool ok = true;
-    for (int w = 0; w < 2 && ok; ++w) ok = (dd_apply<T>(x, wkind, r, 1, s) == TH_OK);
+    for (int w = 0; w < 2 && ok; ++w) ok = (dd_apply<T>(x, wkind, r, nt, s) == TH_OK);
     if (!ok) {
       cudaGetLastError();
       continue;
     }
     TH_CU(cudaEventRecord(e0, s));
     for (int k = 0; k < 4; ++k)
-      if (dd_apply<T>(x, wkind, r, 1, s) != TH_OK) ok = false;
+      if (dd_apply<T>(x, wkind, r, nt, s) != TH_OK) ok = false;
     TH_CU(cudaEventRecord(e1, s));
     TH_CU(cudaEventSynchronize(e1));
     float ms = 0;

@@ -3,7 +3,9 @@
 // V_i = W_i R_i r for every right-hand side at once).
 //
 // Per subdomain the product is a complex GEMM V = W X^T, W: NR x NC rows
-// (NR <= 128), X: NB x NC gathered residuals (NB right-hand sides).  In real
+// (NR <= 128), X: NB x NC gathered residuals (NB = 32 or 16 right-hand sides per
+// tile; 16 when the doubled X buffer of 32 would not fit shared memory, e.g. the
+// 729-column rows of the 3-D Q2 subdomains).  In real
 // arithmetic, with A = W (M = 128 rows, K-major) and B = X (N = NB, K-major):
 //   D_re = W_re X_re^T - W_im X_im^T,   D_im = W_re X_im^T + W_im X_re^T,
 // four MMAs per K-step of 16 (the minus sign through the A-negate bit), with
@@ -35,7 +37,6 @@
 namespace th {
 namespace {
 
-constexpr int kNB = 32;      // right-hand sides per tile (MMA N)
 constexpr int kKC = 8;       // k/8 blocks per W chunk (64 columns)
 constexpr int kDepth = 4;    // W chunk slots
 constexpr int kSlotBytes = 2 * 16 * kKC * 128;  // re + im, 128 rows, 64 columns
@@ -112,6 +113,7 @@ size_t dd_umma_bytes_per_sub(int NR, int NC) {
   return (size_t)K8 * 2 * M8 * 128;
 }
 
+template <int kNB, bool D3>
 __global__ void __launch_bounds__(kThreads, 1) k_dd_umma(const DDUmmaArgs a) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   const int M8 = a.M8, K8 = a.K8;
@@ -257,20 +259,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_dd_umma(const DDUmmaArgs a) {
       const int xb = i & 1, ux = i >> 1;
       const int sub = blockIdx.x + i * gridDim.x;
       if (!failed) mbar_wait(xempty + xb, (unsigned)((ux & 1) ^ 1), &failed);
-      const int* bb = a.box + (size_t)sub * 12;  // 2-D boxes only (the 3-D rows exceed the tile)
-      const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3];
+      const int* bb = a.box + (size_t)sub * 12;
+      const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3], oz = D3 ? bb[8] : 0, wz = D3 ? bb[9] : 1;
+      const int L2 = a.Lw * a.Lw;
       __nv_bfloat16* xr = reinterpret_cast<__nv_bfloat16*>(xbuf + (size_t)xb * xbuf_bytes);
       __nv_bfloat16* xi = xr + xbuf_bytes / 4;
-      for (int idx = pidx; idx < kNB * KP; idx += nprod) {
-        const int n = idx / KP, c = idx - n * KP;
-        const int cy = c / a.Lw, cx = c - cy * a.Lw;
-        float2 v = make_float2(0.f, 0.f);
-        const int rhs = r0 + n;
-        if (rhs < a.nrhs && c < a.NC && cx < wx && cy < wy)
-          v = a.r[(size_t)rhs * a.N + (size_t)(oy + cy) * a.m + (ox + cx)];
-        const size_t off = ((size_t)(n >> 3) * K8 + (c >> 3)) * 64 + (n & 7) * 8 + (c & 7);
-        xr[off] = __float2bfloat16_rn(v.x);
-        xi[off] = __float2bfloat16_rn(v.y);
+      // one column c per producer thread at a time: its box coordinates once,
+      // then the kNB right-hand sides as independent loads
+      for (int c = pidx; c < KP; c += nprod) {
+        const int cz = D3 ? c / L2 : 0, cr = D3 ? c - cz * L2 : c;
+        const int cy = cr / a.Lw, cx = cr - cy * a.Lw;
+        const bool in = c < a.NC && cx < wx && cy < wy && cz < wz;
+        const size_t gidx = in ? ((size_t)(oz + cz) * a.m + (oy + cy)) * a.m + (ox + cx) : 0;
+        const size_t cbase = (size_t)(c >> 3) * 64 + (c & 7);
+#pragma unroll 8
+        for (int n = 0; n < kNB; ++n) {
+          const int rhs = r0 + n;
+          float2 v = make_float2(0.f, 0.f);
+          if (in && rhs < a.nrhs) v = a.r[(size_t)rhs * a.N + gidx];
+          const size_t off = (size_t)(n >> 3) * K8 * 64 + cbase + (n & 7) * 8;
+          xr[off] = __float2bfloat16_rn(v.x);
+          xi[off] = __float2bfloat16_rn(v.y);
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(xfull + xb);
@@ -285,16 +295,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_dd_umma(const DDUmmaArgs a) {
   }
 }
 
-cudaError_t launch_dd_umma(const DDUmmaArgs& a, int sms, cudaStream_t s) {
-  if (a.NR > 128 || (a.K8 & 1) || a.M8 * 8 > 128) return cudaErrorInvalidValue;
+template <int kNB>
+static size_t dd_umma_smem(const DDUmmaArgs& a) {
   const size_t xbuf_bytes = (size_t)2 * (kNB / 8) * a.K8 * 128;
-  const size_t smem = (size_t)kDepth * kSlotBytes + 2 * xbuf_bytes + 17 * sizeof(uint64_t);
-  if (smem > 225 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_dd_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return (size_t)kDepth * kSlotBytes + 2 * xbuf_bytes + 17 * sizeof(uint64_t);
+}
+
+template <int kNB, bool D3>
+static cudaError_t launch_dd_umma_k(const DDUmmaArgs& a, int sms, cudaStream_t s) {
+  const size_t smem = dd_umma_smem<kNB>(a);
+  cudaError_t e = cudaFuncSetAttribute(k_dd_umma<kNB, D3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(a.nsub < sms ? a.nsub : sms), (unsigned)((a.nrhs + kNB - 1) / kNB));
-  k_dd_umma<<<grid, kThreads, smem, s>>>(a);
+  k_dd_umma<kNB, D3><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+template <int kNB>
+static cudaError_t launch_dd_umma_nb(const DDUmmaArgs& a, int sms, cudaStream_t s) {
+  return a.dim3 ? launch_dd_umma_k<kNB, true>(a, sms, s) : launch_dd_umma_k<kNB, false>(a, sms, s);
+}
+
+cudaError_t launch_dd_umma(const DDUmmaArgs& a, int sms, cudaStream_t s) {
+  if (a.NR > 128 || (a.K8 & 1) || a.M8 * 8 > 128) return cudaErrorInvalidValue;
+  // 32 right-hand sides per tile when they fit, else 16 (MMA N >= 16 with M = 128)
+  if (a.nrhs > 16 && dd_umma_smem<32>(a) <= 225 * 1024) return launch_dd_umma_nb<32>(a, sms, s);
+  if (dd_umma_smem<16>(a) <= 225 * 1024) return launch_dd_umma_nb<16>(a, sms, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace th

@@ -101,6 +101,7 @@ struct DDUmmaArgs {
   long long N;
   int nsub, m, Lw, NC, NR, nrhs;
   int M8, K8;             // row and column core-matrix counts (rows <= 128, K8 even)
+  int dim3;               // 1: 3-D boxes (z origin and width used by the gather)
 };
 cudaError_t launch_dd_umma(const DDUmmaArgs& a, int sms, cudaStream_t s);
 size_t dd_umma_bytes_per_sub(int NR, int NC);

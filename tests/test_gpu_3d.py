@@ -143,3 +143,25 @@ def test_mixed_solve_3d(th, prec):
     assert info["converged"] == 2 and info["relres_max"] <= 1e-8
     assert info["iters"] <= info64["iters"] + 2
     assert relerr(host(U), host(U64)) < 1e-6
+
+
+@pytest.mark.parametrize("nrhs", [8, 13])
+def test_tensor_core_smoother_3d(th, nrhs):
+    """3-D subdomains (125 U-box rows x 729 columns) on the tensor cores: tiles
+    of 16 right-hand sides (the doubled operand buffer of 32 exceeds shared
+    memory), against the CUDA-core BF16 kernel and the FP64 smoother."""
+    c = CASES3[0]  # 2-cell blocks: 5^3 = 125 U-box rows, 9^3 = 729 columns
+    S, P = build(th, c, nrhs=nrhs, prec="bf16", extra_prec=("fp64",))
+    f = synth.random_complex((nrhs, P.N), 70)
+    u = synth.random_complex((nrhs, P.N), 71)
+    S.set_precision("fp64")
+    ref = host(S.smooth(dev(f), dev(u.copy()))) - u
+    S.set_precision("bf16")
+    S.set_variant("dd_batch", "fp32", 1)
+    assert S.get_variant("dd_batch", "fp32") == 1
+    tc = host(S.smooth(dev(f), dev(u.copy()))) - u
+    S.device_status()
+    S.set_variant("dd_batch", "fp32", 0)
+    cc = host(S.smooth(dev(f), dev(u.copy()))) - u
+    assert relerr(tc, cc) < 2e-2
+    assert relerr(tc, ref) < 3e-2
