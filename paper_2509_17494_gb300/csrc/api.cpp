@@ -264,10 +264,8 @@ void carve_all(th_ctx& x, Carve& c) {
   if (x.mixed) {
     x.kc32 = c.take<float>(n2);
     x.ec32 = c.take<float>(n2);
-    if (!d3) {
-      x.kcds = c.take<th::ds>(n2);
-      x.ecds = c.take<th::ds>(n2);
-    }
+    x.kcds = c.take<th::ds>(n2);
+    x.ecds = c.take<th::ds>(n2);
     x.pw32 = c.take<float>((size_t)g.m * (g.q + 1));
     x.rw32 = c.take<float>((size_t)g.mc * x.rmax);
     x.ccell32 = c.take<float2>(ncell_c);
@@ -428,16 +426,20 @@ th_status fine_apply3(th_ctx& x, int op, const typename th::Cx<T>::t* u, const t
   a.m = g.m;
   a.robin = 0;
   for (int s6 = 0; s6 < 6; ++s6) a.robin |= g.robin[s6] << s6;
-  a.h = (T)g.h;
-  a.alpha = (op == TH_OP_AS) ? (T)x.prm.alpha_s : (T)0;
+  a.h = cvt<T>(g.h);
+  a.alpha = cvt<T>(op == TH_OP_AS ? x.prm.alpha_s : 0.0);
   for (int i = 0; i < 9; ++i) {
-    a.M[i] = (T)x.ref.M[i];
-    a.K[i] = (T)x.ref.K[i];
+    a.M[i] = cvt<T>(x.ref.M[i]);
+    a.K[i] = cvt<T>(x.ref.K[i]);
   }
   if constexpr (std::is_same<T, double>::value) {
     a.kc = x.kc64;
     a.ec = x.ec64;
     a.ycell = x.ycell64;
+  } else if constexpr (std::is_same<T, th::ds>::value) {
+    a.kc = x.kcds;
+    a.ec = x.ecds;
+    a.ycell = reinterpret_cast<th::cds*>(x.ycell64);  // 16-byte entries, as FP64
   } else {
     a.kc = x.kc32;
     a.ec = x.ec32;
@@ -467,6 +469,9 @@ th_status fine_apply(th_ctx& x, int op, const typename th::Cx<T>::t* u, const ty
 // (the FP32 cycle's input): a double-single apply that writes FP32 (one launch),
 // or the FP64 apply followed by rounding (th_set_kernel_variant TH_K_RESID).
 th_status outer_residual(th_ctx& x, const double2* u, const double2* f, float2* r32, int nrhs, cudaStream_t s) {
+  if (x.g.dim == 3 && x.resid_ds && x.kcds)  // double-single 3-D apply, FP32 output (see NodeIO<ds>)
+    return fine_apply3<th::ds>(x, TH_OP_A, reinterpret_cast<const th::cds*>(u), reinterpret_cast<const th::cds*>(f),
+                               reinterpret_cast<th::cds*>(r32), nrhs, s);
   if (x.g.dim == 2 && x.resid_ds && x.kcds) {
     th::FineArgs<th::ds> a = fine_args<th::ds>(x, TH_OP_A);
     a.u = reinterpret_cast<const th::cds*>(u);

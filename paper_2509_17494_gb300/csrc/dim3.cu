@@ -11,6 +11,7 @@
 //   K7-3D  k_coarse_apply3: y_c = A_q x_c with 4 pair weights per coarse cell.
 //   K8-3D  k_sweep3_couple + k_sweep3_gemv: block forward / backward sweep over
 //          the z-slices of the coarse grid, one launch pair per slice.
+#include "ds_math.cuh"
 #include "kernels.h"
 
 namespace th {
@@ -22,8 +23,13 @@ __device__ __forceinline__ void c_fma(C& acc, C a, C b) {
 template <typename T>
 __device__ __forceinline__ typename Cx<T>::t shfl_c(typename Cx<T>::t v, int src) {
   typename Cx<T>::t o;
-  o.x = __shfl_sync(0xffffffffu, v.x, src);
-  o.y = __shfl_sync(0xffffffffu, v.y, src);
+  if constexpr (std::is_same<T, ds>::value) {
+    o.x = ds(__shfl_sync(0xffffffffu, v.x.h, src), __shfl_sync(0xffffffffu, v.x.l, src));
+    o.y = ds(__shfl_sync(0xffffffffu, v.y.h, src), __shfl_sync(0xffffffffu, v.y.l, src));
+  } else {
+    o.x = __shfl_sync(0xffffffffu, v.x, src);
+    o.y = __shfl_sync(0xffffffffu, v.y, src);
+  }
   return o;
 }
 
@@ -39,11 +45,10 @@ __global__ void __launch_bounds__(256) k_fine3_cells(const Fine3Args<T> a) {
   const bool act = lane < 27;
   const int l = act ? lane : 0;
   const int az = l / 9, ay = (l / 3) % 3, ax = l % 3;
-  const C* u = a.u + (size_t)blockIdx.y * a.N;
   C U;
   U.x = 0;
   U.y = 0;
-  if (act) U = u[((size_t)(2 * cz + az) * m + (2 * cy + ay)) * m + (2 * cx + ax)];
+  if (act) U = NodeIO<T>::ld(a.u, (size_t)blockIdx.y * a.N + ((size_t)(2 * cz + az) * m + (2 * cy + ay)) * m + (2 * cx + ax));
   // x: XM = M_x U, XK = K_x U
   C XM, XK;
   XM.x = XM.y = XK.x = XK.y = 0;
@@ -164,14 +169,14 @@ __global__ void __launch_bounds__(256) k_fine3_gather(const Fine3Args<T> a) {
       }
   C out;
   if (a.residual) {
-    const C f = a.f[(size_t)blockIdx.y * a.N + j];
+    const C f = NodeIO<T>::ld(a.f, (size_t)blockIdx.y * a.N + j);
     out.x = f.x - sr;
     out.y = f.y - si;
   } else {
     out.x = sr;
     out.y = si;
   }
-  a.y[(size_t)blockIdx.y * a.N + j] = out;
+  NodeIO<T>::st(a.y, (size_t)blockIdx.y * a.N + j, out);
 }
 
 template <typename T>
@@ -186,6 +191,7 @@ cudaError_t launch_fine3(const Fine3Args<T>& a, int nrhs, cudaStream_t s) {
 }
 template cudaError_t launch_fine3<double>(const Fine3Args<double>&, int, cudaStream_t);
 template cudaError_t launch_fine3<float>(const Fine3Args<float>&, int, cudaStream_t);
+template cudaError_t launch_fine3<ds>(const Fine3Args<ds>&, int, cudaStream_t);
 
 // ------------------------------------------------------------ K4-3D combine
 template <typename T>
@@ -476,9 +482,9 @@ __global__ void __launch_bounds__(256) k_sweep3_gemv(const Sweep3Args<T> a, int 
   }
 }
 
-template <typename T>
-cudaError_t launch_sweep3(const Sweep3Args<T>& a, cudaStream_t s) {
-  constexpr int NB = 4;
+// NB right-hand sides per warp: every pivot block is read once per tile of NB
+template <typename T, int NB>
+static cudaError_t launch_sweep3_nb(const Sweep3Args<T>& a, cudaStream_t s) {
   const dim3 gc((unsigned)((a.mb + 255) / 256), a.nrhs);
   const dim3 gg((unsigned)(((long long)a.mb * 32 + 255) / 256), (a.nrhs + NB - 1) / NB);
   for (int j = 0; j < a.mc; ++j) {
@@ -490,6 +496,13 @@ cudaError_t launch_sweep3(const Sweep3Args<T>& a, cudaStream_t s) {
     k_sweep3_gemv<T, NB><<<gg, 256, 0, s>>>(a, j, 1);
   }
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sweep3(const Sweep3Args<T>& a, cudaStream_t s) {
+  // the blocks stay in L2 across the rhs tiles of one step: narrower tiles give more warps
+  if (a.nrhs > 4) return launch_sweep3_nb<T, 2>(a, s);
+  return launch_sweep3_nb<T, 4>(a, s);
 }
 template cudaError_t launch_sweep3<double>(const Sweep3Args<double>&, cudaStream_t);
 template cudaError_t launch_sweep3<float>(const Sweep3Args<float>&, cudaStream_t);

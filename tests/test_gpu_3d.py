@@ -165,3 +165,23 @@ def test_tensor_core_smoother_3d(th, nrhs):
     cc = host(S.smooth(dev(f), dev(u.copy()))) - u
     assert relerr(tc, cc) < 2e-2
     assert relerr(tc, ref) < 3e-2
+
+
+@pytest.mark.parametrize("c", CASES3[:2])
+def test_mixed_outer_residual_double_single_3d(th, c):
+    """The 3-D outer residual in double-single arithmetic, FP32 output: against
+    the FP64 oracle within FP32 rounding plus 2^-40 of the terms' scale, also
+    with u within 1e-9 of the solution (where f - A u cancels)."""
+    import scipy.sparse.linalg as spla
+    S, P = build(th, c, prec="fp32", extra_prec=("fp64",))
+    assert S.get_variant("resid", "fp32") == 1
+    f = synth.random_complex((3, P.N), 41)
+    u = synth.random_complex((3, P.N), 42)
+    uex = np.stack([spla.spsolve(P.A.tocsc(), f[i]) for i in range(3)])
+    Aabs = abs(P.A)
+    for uu in (u, uex * (1 + 1e-9 * synth.random_complex(P.N, 43).real)):
+        want = f - (P.A @ uu.T).T
+        got = host(S.residual_mixed(dev(f), dev(uu)))
+        scale = (Aabs @ np.abs(uu).T).T.max() + np.abs(f).max()
+        err = np.abs(got - want).max()
+        assert err <= 1.2e-7 * np.abs(want).max() + 2.0 ** -40 * scale, (err, np.abs(want).max(), scale)
