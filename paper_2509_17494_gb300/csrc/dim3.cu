@@ -437,12 +437,23 @@ __global__ void __launch_bounds__(256) k_sweep3_couple(const Sweep3Args<T> a, in
 }
 
 template <typename T, int NB>
-__global__ void __launch_bounds__(256) k_sweep3_gemv(const Sweep3Args<T> a, int j, int backward) {
+__global__ void __launch_bounds__(512) k_sweep3_gemv(const Sweep3Args<T> a, int j, int backward) {
   using C = typename Cx<T>::t;
+  extern __shared__ __align__(16) unsigned char sw_sm[];
+  C* ts = reinterpret_cast<C*>(sw_sm);  // [NB][mb]: this tile's coupled right-hand sides
   const int lane = threadIdx.x & 31;
+  const int r0 = blockIdx.y * NB, nb = min(NB, a.nrhs - r0);
+  for (int i = threadIdx.x; i < NB * a.mb; i += blockDim.x) {
+    const int r = i / a.mb, c = i - r * a.mb;
+    C v;
+    v.x = 0;
+    v.y = 0;
+    if (r < nb) v = a.t[(size_t)(r0 + r) * a.mb + c];
+    ts[i] = v;
+  }
+  __syncthreads();
   const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (row >= a.mb) return;
-  const int r0 = blockIdx.y * NB, nb = min(NB, a.nrhs - r0);
   const C* g = a.G + ((size_t)j * a.mb + row) * a.mb;
   C acc[NB];
 #pragma unroll
@@ -454,8 +465,7 @@ __global__ void __launch_bounds__(256) k_sweep3_gemv(const Sweep3Args<T> a, int 
   for (int c = lane; c < a.mb; c += 32) {
     const C gv = g[c];
 #pragma unroll
-    for (int r = 0; r < NB; ++r)
-      if (r < nb) c_fma(acc[r], gv, a.t[(size_t)(r0 + r) * a.mb + c]);
+    for (int r = 0; r < NB; ++r) c_fma(acc[r], gv, ts[r * a.mb + c]);
   }
 #pragma unroll
   for (int r = 0; r < NB; ++r) {
@@ -485,15 +495,20 @@ __global__ void __launch_bounds__(256) k_sweep3_gemv(const Sweep3Args<T> a, int 
 // NB right-hand sides per warp: every pivot block is read once per tile of NB
 template <typename T, int NB>
 static cudaError_t launch_sweep3_nb(const Sweep3Args<T>& a, cudaStream_t s) {
+  using C = typename Cx<T>::t;
+  const size_t smem = sizeof(C) * (size_t)NB * a.mb;  // the tile's coupled vectors, staged per CTA
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_sweep3_gemv<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   const dim3 gc((unsigned)((a.mb + 255) / 256), a.nrhs);
-  const dim3 gg((unsigned)(((long long)a.mb * 32 + 255) / 256), (a.nrhs + NB - 1) / NB);
+  const dim3 gg((unsigned)(((long long)a.mb * 32 + 511) / 512), (a.nrhs + NB - 1) / NB);
   for (int j = 0; j < a.mc; ++j) {
     k_sweep3_couple<T><<<gc, 256, 0, s>>>(a, j, 0);
-    k_sweep3_gemv<T, NB><<<gg, 256, 0, s>>>(a, j, 0);
+    k_sweep3_gemv<T, NB><<<gg, 512, smem, s>>>(a, j, 0);
   }
   for (int j = a.mc - 2; j >= 0; --j) {
     k_sweep3_couple<T><<<gc, 256, 0, s>>>(a, j, 1);
-    k_sweep3_gemv<T, NB><<<gg, 256, 0, s>>>(a, j, 1);
+    k_sweep3_gemv<T, NB><<<gg, 512, smem, s>>>(a, j, 1);
   }
   return cudaGetLastError();
 }
