@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cycles", type=int, default=15, help="oracle cycles in the CPU-baseline sample")
     ap.add_argument("--batch-rhs", type=int, default=64, help="right-hand sides of the batched section (0: skip)")
+    ap.add_argument("--batch-workload", default="square80_q4_n200",
+                    help="workload of the batched section (default: 80 wavelengths, 801^2 dofs, its 64 sources)")
+    ap.add_argument("--mixed-batch", action="store_true",
+                    help="add 16 independent domains of 20..80 wavelengths, one cycle each, in one CUDA graph")
     ap.add_argument("--dd-variant", choices=["auto", "0", "1", "2", "3"], default="auto",
                     help="FP32 subdomain kernel: auto (set-up autotuner), 0 k_dd_apply, 1 k_dd_stream, 2 k_dd_stream2, "
                          "3 k_dd_stream with three CTAs per SM "
@@ -363,7 +367,9 @@ def run_native(args):
     S.close()
     del S
     if args.batch_rhs > 0:
-        line["batched"] = batched_section(args, w, dev, world)
+        line["batched"] = batched_section(args, synth.workload(args.batch_workload), dev, world)
+    if args.mixed_batch:
+        line["mixed_batch"] = mixed_batch_section(dev, world)
     if args.learned_steps > 0:
         line["learned"] = learned_section(args, dev)
     if args.dim3 != "none":
@@ -392,9 +398,10 @@ def run_native(args):
 # many sources at once, and the learned coarse corrector
 # ----------------------------------------------------------------------------
 def batched_section(args, w, dev, world):
-    """nrhs seeded point sources on the same workload in one graph-replayed cycle:
-    the subdomain products run on the tensor cores (k_dd_umma), the coarse solve
-    on tiles of right-hand sides."""
+    """nrhs seeded point sources on one workload (by default 80 wavelengths on
+    801^2 dofs with its 64 sources) in one graph-replayed cycle: the subdomain
+    products run on the tensor cores (k_dd_umma), the coarse solve on tiles of
+    right-hand sides."""
     import numpy as np
     import torch
 
@@ -402,9 +409,12 @@ def batched_section(args, w, dev, world):
     import synth
 
     nr = args.batch_rhs
+    t0 = time.time()
     S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=w["alpha_s"], l_dd=w["l_dd"], prec="bf16",
                          restart=30, maxit=300, tol=1e-8, nrhs_max=nr, device=dev)
-    F = torch.from_numpy(np.ascontiguousarray(synth.random_sources(w["n"], w["p"], 2, nr, 100))).to(dev)
+    setup_s = time.time() - t0
+    src = w["f"] if (w["f"].ndim == 2 and w["f"].shape[0] == nr) else synth.random_sources(w["n"], w["p"], 2, nr, 100)
+    F = torch.from_numpy(np.ascontiguousarray(src)).to(dev)
     U = torch.zeros_like(F)
     stream = torch.cuda.current_stream(dev)
     for _ in range(3):
@@ -435,7 +445,8 @@ def batched_section(args, w, dev, world):
     flops = 8.0 * NR * NC * nsub * nr
     _, info = S.solve(F)
     hbm, src = peaks()
-    out = {"nrhs": nr, "sources": "seeded Gaussian point sources (synth.random_sources, seed 100)",
+    out = {"workload": w["name"], "dofs": S.N, "setup_s": round(setup_s, 1),
+           "nrhs": nr, "sources": "seeded Gaussian point sources (synth.random_sources, seed 100)",
            "value": round(S.N * nr * world / (ms * 1e-3) / 1e9, 4), "unit": "GDOF/s", "ms_per_cycle": round(ms, 4),
            "time_to_tol_ms": round(info["ms_total"], 2), "iters": info["iters"], "relres_max": info["relres_max"],
            "dd_tensor_core": {"kernel": "k_dd_umma (tcgen05, BF16 x BF16 -> FP32 in tensor memory)",
@@ -446,6 +457,71 @@ def batched_section(args, w, dev, world):
            "per_kernel_ms_per_cycle": {k: round(v[0] / 3, 4) for k, v in prof.items() if v[1] > 0}}
     S.close()
     return out
+
+
+def mixed_batch_section(dev, world):
+    """16 independent domains of 20, 24, ..., 80 wavelengths (Q4, 2.5 W cells per
+    side, each its own random field and centred source, 10-dof layer), one
+    mixed-precision TwoGridStep each, all captured into one CUDA graph and
+    replayed: the cycle throughput of the whole batch; then each domain's solve
+    to 1e-8."""
+    import numpy as np
+    import torch
+
+    import paper_2509_17494_gb300 as th
+    import synth
+
+    Ws = list(range(20, 81, 4))
+    t0 = time.time()
+    solvers, Fs, Us = [], [], []
+    for i, W in enumerate(Ws):
+        n = int(round(2.5 * W))
+        k = synth.random_wavenumber(n, 2, float(W), seed=10 + i)
+        eps = synth.absorbing_layer(n, 2, 4, k, 10.0)
+        S = th.TwoGridSolver(n, 4, k, eps, alpha_s=0.5, l_dd=2, prec="bf16", extra_prec=("fp64",), restart=30,
+                             maxit=300, tol=1e-8, device=dev)
+        S.set_graphs(False)  # the batch is captured as a whole below
+        solvers.append(S)
+        Fs.append(torch.from_numpy(synth.gaussian_source(n, 4, 2)).to(dev))
+        Us.append(torch.zeros_like(Fs[-1]))
+    setup_s = time.time() - t0
+    dofs = sum(S.N for S in solvers)
+    cs = torch.cuda.Stream(dev)
+    cs.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(cs):
+        for S, F, U in zip(solvers, Fs, Us):  # first launches outside the capture
+            S.cycle(F, U)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cs):
+        for S, F, U in zip(solvers, Fs, Us):
+            S.cycle(F, U)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    steps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
+    iters, tts = [], []
+    for S, F in zip(solvers, Fs):
+        S.set_graphs(True)
+        _, info = S.solve(F, check=False)
+        iters.append(info["iters"] if info["converged"] else -1)
+        tts.append(info["ms_total"])
+        S.device_status()
+    del graph
+    for S in solvers:
+        S.close()
+    return {"domains": len(Ws), "wavelengths": Ws, "dofs_total": dofs, "setup_s": round(setup_s, 1),
+            "graph": "one CUDA graph holding one TwoGridStep of every domain (mixed precision)",
+            "value": round(dofs * world / (ms * 1e-3) / 1e9, 4), "unit": "GDOF/s", "ms_per_batch_cycle": round(ms, 3),
+            "iters": iters, "time_to_tol_ms_sum": round(sum(tts), 1)}
 
 
 def dim3_section(args, dev, world):

@@ -948,23 +948,21 @@ static cudaError_t launch_cluster(K kern, const Args& a, int grid, int cluster, 
 template <typename T>
 constexpr int mr_tile() { return sizeof(T) == 8 ? 4 : 8; }
 
-template <typename T>
+template <typename T, int NB>
 size_t chunk_sweep_mr_smem(const CoarsePartArgs<T>& a, bool prefetch) {
   using C = typename Cx<T>::t;
-  constexpr int NB = mr_tile<T>();
   size_t s = (size_t)2 * a.mc * NB + (size_t)6 * a.mc + (size_t)2 * a.mc * NB + (size_t)a.mc * NB +
              (size_t)16 * a.rpcm * (NB + 1) + (size_t)a.Lmax * a.rpcm * NB;
   if (prefetch) s += (size_t)2 * a.mc * a.rpcm;
   return s * sizeof(C);
 }
 
-// many right-hand sides: tiles of mr_tile<T>() per cluster / warp
-template <typename T>
-static cudaError_t launch_coarse_part_mr(const CoarsePartArgs<T>& a, int cluster, cudaStream_t s) {
-  constexpr int NB = mr_tile<T>();
+// many right-hand sides: tiles of NB per cluster / warp
+template <typename T, int NB>
+static cudaError_t launch_coarse_part_mr_nb(const CoarsePartArgs<T>& a, int cluster, cudaStream_t s) {
   const int ntiles = (a.nrhs + NB - 1) / NB;
-  const bool pf = chunk_sweep_mr_smem(a, true) <= 220 * 1024;
-  const size_t sm1 = chunk_sweep_mr_smem(a, pf);
+  const bool pf = chunk_sweep_mr_smem<T, NB>(a, true) <= 220 * 1024;
+  const size_t sm1 = chunk_sweep_mr_smem<T, NB>(a, pf);
   if (sm1 > 227 * 1024) return cudaErrorInvalidValue;
   const int grid = cluster * a.P * ntiles;
   cudaError_t e = pf ? launch_cluster(k_chunk_sweep_mr<T, NB, true>, a, grid, cluster, sm1, s)
@@ -975,6 +973,17 @@ static cudaError_t launch_coarse_part_mr(const CoarsePartArgs<T>& a, int cluster
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_tsgemm<T, NB>(a, s);
+}
+
+// the widest tile whose sweep buffers fit shared memory (large coarse grids,
+// e.g. 401 rows per block, take narrower tiles)
+template <typename T>
+static cudaError_t launch_coarse_part_mr(const CoarsePartArgs<T>& a, int cluster, cudaStream_t s) {
+  constexpr int NB = mr_tile<T>();
+  if (chunk_sweep_mr_smem<T, NB>(a, false) <= 227 * 1024) return launch_coarse_part_mr_nb<T, NB>(a, cluster, s);
+  if (chunk_sweep_mr_smem<T, NB / 2>(a, false) <= 227 * 1024) return launch_coarse_part_mr_nb<T, NB / 2>(a, cluster, s);
+  if (chunk_sweep_mr_smem<T, NB / 4>(a, false) <= 227 * 1024) return launch_coarse_part_mr_nb<T, NB / 4>(a, cluster, s);
+  return cudaErrorInvalidValue;
 }
 
 template <typename T>
