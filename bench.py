@@ -57,7 +57,7 @@ def parse():
                     help="workload of the batched section (default: 80 wavelengths, 801^2 dofs, its 64 sources)")
     ap.add_argument("--mixed-batch", action="store_true",
                     help="add 16 independent domains of 20..80 wavelengths, one cycle each, in one CUDA graph")
-    ap.add_argument("--dd-variant", choices=["auto", "0", "1", "2", "3"], default="auto",
+    ap.add_argument("--dd-variant", choices=["auto", "0", "1", "2", "3", "4", "5"], default="auto",
                     help="FP32 subdomain kernel: auto (set-up autotuner), 0 k_dd_apply, 1 k_dd_stream, 2 k_dd_stream2, "
                          "3 k_dd_stream with three CTAs per SM "
                          "(pin it when the same command runs under a profiler, whose serialised launches "
@@ -307,7 +307,8 @@ def run_native(args):
     dd_ms, dd_cnt = prof["dd"]
     dd_avg_ms = dd_ms / max(dd_cnt, 1)
     dd_kernel = {0: "k_dd_apply", 1: "k_dd_stream (TMA bulk)", 2: "k_dd_stream2 (TMA bulk, producer warp)",
-                 3: "k_dd_stream (TMA bulk, three CTAs per SM)"}[S.get_variant("dd", "fp32")]
+                 3: "k_dd_stream (TMA bulk, three CTAs per SM)", 4: "k_dd_stream (TMA bulk, paired FP32 FMAs)",
+                 5: "k_dd_stream (TMA bulk, paired FP32 FMAs, three CTAs per SM)"}[S.get_variant("dd", "fp32")]
     alg_bytes, _ = dd_algorithmic_bytes(n, p, w["l_dd"], 4, 8)
     hbm, peak_src = peaks()
     achieved = alg_bytes / (dd_avg_ms * 1e-3) / 1e9

@@ -359,7 +359,10 @@ th_status th_profile_read(th_ctx* ctx, int kind, double* ms, long long* launches
  *              1 = persistent CTAs streaming the rows through TMA bulk copies,
  *              2 = the same with a dedicated producer warp and per-slot
  *                  mbarrier release (no CTA barrier per ring slot),
- *              3 = variant 1 with smaller ring stages, three CTAs per SM;
+ *              3 = variant 1 with smaller ring stages, three CTAs per SM,
+ *              4, 5 = variants 1, 3 with paired FP32 FMAs (FP32 cycle on
+ *                  BF16 / FP16 rows only; prec must be TH_PREC_FP32; on FP32
+ *                  rows they run variants 1, 3);
  *   TH_K_DD_BATCH: 1 (default when the BF16 rows fit, U box <= 128 nodes) runs
  *              the products of 8 or more right-hand sides on the tensor cores
  *              (tcgen05.mma, BF16 operands, FP32 accumulation; the residuals

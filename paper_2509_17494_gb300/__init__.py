@@ -335,7 +335,7 @@ class TwoGridSolver:
         _check(lib().th_set_precision(self._ctx, PREC[prec]), "th_set_precision")
 
     def set_variant(self, kernel, prec, variant):
-        """kernel: 'fine' | 'dd' | 'coarse' | 'dd_batch'; prec: 'fp64' | 'fp32'; variant 0 / 1 ('dd' also 2); see include/th.h."""
+        """kernel: 'fine' | 'dd' | 'coarse' | 'dd_batch' | 'resid'; prec: 'fp64' | 'fp32'; the variant numbers are listed in include/th.h."""
         k = {"fine": 0, "dd": 1, "coarse": 6, "dd_batch": 9, "resid": 10}[kernel]
         _check(lib().th_set_kernel_variant(self._ctx, k, PREC[prec], int(variant)), "th_set_kernel_variant")
 

@@ -585,7 +585,8 @@ th_status dd_apply(th_ctx& x, int wkind, const typename th::Cx<T>::t* r, int nrh
   }
   const int stream = std::is_same<T, double>::value ? x.dds64 : x.dds32;
   a.stream_v2 = stream == 2 ? 1 : 0;
-  a.stream_small = stream == 3 ? 1 : 0;
+  a.stream_small = (stream == 3 || stream == 5) ? 1 : 0;
+  a.stream_pk = stream >= 4 ? 1 : 0;
   if (stream) return cuda_status(th::launch_dd_stream<T>(a, wkind, x.derr, x.sms, s));
   return cuda_status(th::launch_dd_apply<T>(a, wkind, 0, s));
 }
@@ -1021,7 +1022,9 @@ th_status tune_dd(th_ctx& x, int wkind, cudaStream_t s, int& choice) {
   TH_CU(cudaEventCreate(&e1));
   float best = 1e30f;
   int arg = 0;
-  for (int v = 0; v < 4; ++v) {
+  // 4 and 5 (paired FP32 FMAs) exist for FP32 arithmetic on BF16 / FP16 rows only
+  const int nv = (std::is_same<T, float>::value && (wkind == TH_PREC_BF16 || wkind == TH_PREC_FP16)) ? 6 : 4;
+  for (int v = 0; v < nv; ++v) {
     choice = v;
     bool ok = true;
     for (int w = 0; w < 2 && ok; ++w) ok = (dd_apply<T>(x, wkind, r, nt, s) == TH_OK);
@@ -1409,7 +1412,7 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
 }
 
 th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
-  const int vmax = kernel == TH_K_DD ? 3 : kernel == TH_K_COARSE_SOLVE ? 2 : 1;
+  const int vmax = kernel == TH_K_DD ? (prec == TH_PREC_FP32 ? 5 : 3) : kernel == TH_K_COARSE_SOLVE ? 2 : 1;
   if (!x || variant < 0 || variant > vmax || (prec != TH_PREC_FP64 && prec != TH_PREC_FP32))
     return TH_ERR_ARG;
   const bool d = (prec == TH_PREC_FP64);

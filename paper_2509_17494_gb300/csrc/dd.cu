@@ -335,10 +335,16 @@ __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0
 
 }  // namespace
 
-template <typename T, int KIND, int NRHS>
+// PK (FP32 arithmetic on 4-column BF16 / FP16 chunks, at most 4 right-hand
+// sides): the gathered x is stored per chunk as [re0..re3][im0..im3] and the
+// products run as paired FP32 FMAs (__ffma2_rn, two lanes per instruction):
+// (wr0, wr1) * (xr0, xr1) into a real sum, (wi0, wi1) * (xi0, xi1) into a sum
+// subtracted at the end, and both cross terms into the imaginary sum.
+template <typename T, int KIND, int NRHS, bool PK>
 __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps, int depth, int* err) {
   using C = typename Cx<T>::t;
   constexpr int CPC = WTraits<KIND>::CPC;
+  static_assert(!PK || (std::is_same<T, float>::value && CPC == 4 && NRHS <= 4), "paired-FMA form");
   extern __shared__ __align__(128) unsigned char smraw[];
   const int NR = a.NR, NCH = a.NCH, G = a.G;
   const size_t slot_bytes = (size_t)cps * NR * 16;
@@ -347,6 +353,7 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
   const int XL = NCH * CPC;
   C* xs = reinterpret_cast<C*>(bars + 8);                                   // [2][NRHS][XL]
   C* red = xs + 2 * NRHS * XL;                                              // [G][NR][NRHS]
+  int2* tab = reinterpret_cast<int2*>(red + (size_t)G * NR * NRHS);         // [XL]: box offset, packed (x, y, z)
   const int tid = threadIdx.x, nth = blockDim.x;
   const int rr = tid % NR, g = tid / NR;
   const int r0 = blockIdx.y * NRHS;
@@ -369,29 +376,55 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
     mbar_expect_tx_arrive(bar, bytes);
     bulk_g2s(slots + (size_t)(t % depth) * slot_bytes, src, bytes, bar);
   };
+  // box-relative offsets and coordinates of the gathered columns (the same for
+  // every subdomain): the per-subdomain gather does no integer division
+  {
+    const int L2 = a.Lw * a.Lw;
+    for (int c = tid; c < XL; c += nth) {
+      const int cz = c / L2, cr = c - cz * L2;
+      const int cy = cr / a.Lw, cx = cr - cy * a.Lw;
+      tab[c] = c < a.NC ? make_int2((cz * a.m + cy) * a.m + cx, cx | (cy << 10) | (cz << 20)) : make_int2(0, -1);
+    }
+  }
   auto gather = [&](int i, int buf) {
     if (i < nmine) {
       const int sub = blockIdx.x + i * gridDim.x;
       const int* bb = a.box + (size_t)sub * 12;
-      const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3], oz = bb[8], wz = bb[9];
-      const int L2 = a.Lw * a.Lw;
+      const int wx = bb[2], wy = bb[3], wz = bb[9];
+      const size_t base = ((size_t)bb[8] * a.m + bb[1]) * a.m + bb[0];
       C* dst = xs + (size_t)buf * NRHS * XL;
-      for (int idx = tid; idx < NRHS * XL; idx += nth) {
-        const int k = idx / XL, c = idx - k * XL;
-        const int cz = c / L2, cr = c - cz * L2;
-        const int cy = cr / a.Lw, cx = cr - cy * a.Lw;
-        if (k < nr && c < a.NC && cx < wx && cy < wy && cz < wz) {
-          cp_async_c(dst + idx, a.r + (size_t)(r0 + k) * a.N + ((size_t)(oz + cz) * a.m + (oy + cy)) * a.m + (ox + cx));
-        } else {
-          C z;
-          z.x = 0;
-          z.y = 0;
-          dst[idx] = z;
+#pragma unroll
+      for (int k = 0; k < NRHS; ++k) {
+        const C* src = a.r + (size_t)(r0 + k) * a.N + base;
+        for (int c = tid; c < XL; c += nth) {
+          const int2 e = tab[c];
+          const bool in = k < nr && e.y >= 0 && (e.y & 1023) < wx && ((e.y >> 10) & 1023) < wy && (e.y >> 20) < wz;
+          if constexpr (PK) {  // [chunk][re0..re3, im0..im3]
+            float* d = reinterpret_cast<float*>(dst + (size_t)k * XL) + (size_t)(c >> 2) * 8 + (c & 3);
+            if (in) {
+              const float* s2 = reinterpret_cast<const float*>(src + e.x);
+              asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(d)), "l"(s2) : "memory");
+              asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(d + 4)), "l"(s2 + 1) : "memory");
+            } else {
+              d[0] = 0.f;
+              d[4] = 0.f;
+            }
+          } else {
+            if (in) {
+              cp_async_c(dst + (size_t)k * XL + c, src + e.x);
+            } else {
+              C z;
+              z.x = 0;
+              z.y = 0;
+              dst[(size_t)k * XL + c] = z;
+            }
+          }
         }
       }
     }
     cp_commit();
   };
+  __syncthreads();  // tab
 
   if (tid == 0) {
     for (int d = 0; d < depth; ++d) mbar_init(bars + d, 1);
@@ -416,6 +449,15 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
     T acr[2][NRHS], aci[2][NRHS];
 #pragma unroll
     for (int k = 0; k < NRHS; ++k) { acr[0][k] = aci[0][k] = acr[1][k] = aci[1][k] = 0; }
+    // PK: real, subtracted and imaginary pair sums; with one right-hand side
+    // columns (0, 1) and (2, 3) of a chunk have their own (shorter chains),
+    // with several they share one set (registers)
+    constexpr int PS = NRHS == 1 ? 2 : 1;
+    float2 pR[PS][NRHS], pN[PS][NRHS], pI[PS][NRHS];
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k)
+#pragma unroll
+      for (int h = 0; h < PS; ++h) pR[h][k] = pN[h][k] = pI[h][k] = make_float2(0.f, 0.f);
     for (int s = 0; s < NS; ++s, ++t) {
       if (!failed && !mbar_wait_bounded(bars + (t % depth), (unsigned)((t / depth) & 1))) failed = 1;
       const int ch0 = s * cps, nch = min(cps, NCH - ch0);
@@ -424,7 +466,25 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
         for (int ch = g; ch < nch; ch += G) {
           T wr[CPC], wi[CPC];
           unpack_chunk_smem<T, KIND>(slot, (size_t)ch * NR + rr, wr, wi);
-          if constexpr (std::is_same<T, float>::value && CPC % 2 == 0) {
+          if constexpr (PK) {
+            const float2 WR[2] = {make_float2(wr[0], wr[1]), make_float2(wr[2], wr[3])};
+            const float2 WI[2] = {make_float2(wi[0], wi[1]), make_float2(wi[2], wi[3])};
+#pragma unroll
+            for (int k = 0; k < NRHS; ++k) {
+              const float4* xq = reinterpret_cast<const float4*>(xv + (size_t)k * XL) + (size_t)(ch0 + ch) * 2;
+              const float4 xr = xq[0], xi = xq[1];
+              const float2 XR[2] = {make_float2(xr.x, xr.y), make_float2(xr.z, xr.w)};
+              const float2 XI[2] = {make_float2(xi.x, xi.y), make_float2(xi.z, xi.w)};
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int q = h % PS;
+                pR[q][k] = __ffma2_rn(WR[h], XR[h], pR[q][k]);
+                pN[q][k] = __ffma2_rn(WI[h], XI[h], pN[q][k]);
+                pI[q][k] = __ffma2_rn(WR[h], XI[h], pI[q][k]);
+                pI[q][k] = __ffma2_rn(WI[h], XR[h], pI[q][k]);
+              }
+            }
+          } else if constexpr (std::is_same<T, float>::value && CPC % 2 == 0) {
             // two complex x per 16-byte load (x rows are 16-byte aligned, chunk starts even)
 #pragma unroll
             for (int k = 0; k < NRHS; ++k) {
@@ -466,8 +526,20 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
 #pragma unroll
       for (int k = 0; k < NRHS; ++k) {
         C v;
-        v.x = acr[0][k] + acr[1][k];
-        v.y = aci[0][k] + aci[1][k];
+        if constexpr (PK) {
+          float sr = 0.f, sn = 0.f, si = 0.f;
+#pragma unroll
+          for (int h = 0; h < PS; ++h) {
+            sr += pR[h][k].x + pR[h][k].y;
+            sn += pN[h][k].x + pN[h][k].y;
+            si += pI[h][k].x + pI[h][k].y;
+          }
+          v.x = sr - sn;
+          v.y = si;
+        } else {
+          v.x = acr[0][k] + acr[1][k];
+          v.y = aci[0][k] + aci[1][k];
+        }
         red[((size_t)g * NR + rr) * NRHS + k] = v;
       }
     }
@@ -681,30 +753,31 @@ static cudaError_t launch_dd_stream2_k(const DDArgs<T>& a0, int* err, int sms, c
   return cudaGetLastError();
 }
 
-template <typename T, int KIND, int NRHS>
+template <typename T, int KIND, int NRHS, bool PK>
 static cudaError_t launch_dd_stream_k(const DDArgs<T>& a, int* err, int sms, cudaStream_t s) {
   using C = typename Cx<T>::t;
   constexpr int CPC = WTraits<KIND>::CPC;
   const int threads = ((a.NR * a.G + 31) / 32) * 32;
-  if (threads > 512) return cudaErrorInvalidConfiguration;
+  if (threads > 512 || a.Lw > 1023) return cudaErrorInvalidConfiguration;
   // a ring of three stages per CTA: up to 32 KB each for two CTAs per SM, or
   // (stream_small) up to 20 KB each so that three CTAs share an SM
   const int slot_target = a.stream_small ? 20 * 1024 : 32 * 1024;
   const int cps = std::max(1, (int)(slot_target / ((size_t)a.NR * 16)));
   const size_t slot_bytes = (size_t)cps * a.NR * 16;
   const size_t fixed = 8 * sizeof(uint64_t) +
-                       sizeof(C) * ((size_t)2 * NRHS * a.NCH * CPC + (size_t)a.G * a.NR * NRHS);
+                       sizeof(C) * ((size_t)2 * NRHS * a.NCH * CPC + (size_t)a.G * a.NR * NRHS) +
+                       sizeof(int2) * (size_t)a.NCH * CPC;
   const int depth = 3;
   const size_t smem = depth * slot_bytes + fixed;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   const int fit = (int)((228 * 1024) / (smem + 1024));
   const int per_sm = std::max(1, std::min(a.stream_small ? 3 : 2, fit));
-  cudaError_t e = cudaFuncSetAttribute(k_dd_stream<T, KIND, NRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_dd_stream<T, KIND, NRHS, PK>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int gx = std::min(a.nsub, per_sm * sms);
   dim3 grid(gx, (a.nrhs + NRHS - 1) / NRHS);
-  k_dd_stream<T, KIND, NRHS><<<grid, threads, smem, s>>>(a, cps, depth, err);
+  k_dd_stream<T, KIND, NRHS, PK><<<grid, threads, smem, s>>>(a, cps, depth, err);
   return cudaGetLastError();
 }
 
@@ -713,7 +786,8 @@ static size_t dd_stream_smem(const DDArgs<T>& a, int nrhs) {
   using C = typename Cx<T>::t;
   const int cps = std::max(1, (int)((32 * 1024) / ((size_t)a.NR * 16)));
   return 3 * (size_t)cps * a.NR * 16 + 8 * sizeof(uint64_t) +
-         sizeof(C) * ((size_t)2 * nrhs * a.NCH * WTraits<KIND>::CPC + (size_t)a.G * a.NR * nrhs);
+         sizeof(C) * ((size_t)2 * nrhs * a.NCH * WTraits<KIND>::CPC + (size_t)a.G * a.NR * nrhs) +
+         sizeof(int2) * (size_t)a.NCH * WTraits<KIND>::CPC;
 }
 
 template <typename T, int KIND>
@@ -724,10 +798,16 @@ static cudaError_t launch_dd_stream_kind(const DDArgs<T>& a, int* err, int sms, 
     return launch_dd_stream2_k<T, KIND, 1>(a, err, sms, s);
   }
   if (a.nrhs >= 8 && dd_stream_smem<T, KIND>(a, 8) <= 227 * 1024)
-    return launch_dd_stream_k<T, KIND, 8>(a, err, sms, s);
-  if (a.nrhs >= 4) return launch_dd_stream_k<T, KIND, 4>(a, err, sms, s);
-  if (a.nrhs >= 2) return launch_dd_stream_k<T, KIND, 2>(a, err, sms, s);
-  return launch_dd_stream_k<T, KIND, 1>(a, err, sms, s);
+    return launch_dd_stream_k<T, KIND, 8, false>(a, err, sms, s);
+  constexpr bool pk = std::is_same<T, float>::value && WTraits<KIND>::CPC == 4;
+  if (pk && a.stream_pk) {
+    if (a.nrhs >= 4) return launch_dd_stream_k<T, KIND, 4, pk>(a, err, sms, s);
+    if (a.nrhs >= 2) return launch_dd_stream_k<T, KIND, 2, pk>(a, err, sms, s);
+    return launch_dd_stream_k<T, KIND, 1, pk>(a, err, sms, s);
+  }
+  if (a.nrhs >= 4) return launch_dd_stream_k<T, KIND, 4, false>(a, err, sms, s);
+  if (a.nrhs >= 2) return launch_dd_stream_k<T, KIND, 2, false>(a, err, sms, s);
+  return launch_dd_stream_k<T, KIND, 1, false>(a, err, sms, s);
 }
 
 template <>

@@ -82,6 +82,7 @@ struct DDArgs {
   int nsub, m, Lw, NC, NCH, NR, G, nrhs;
   int stream_v2;                // launch_dd_stream: 1 = producer-warp variant (k_dd_stream2)
   int stream_small;             // launch_dd_stream (k_dd_stream): 1 = 20 KB ring stages, three CTAs per SM
+  int stream_pk;                // launch_dd_stream (k_dd_stream, FP32 on BF16/FP16 rows): paired FP32 FMAs
 };
 template <typename T>
 cudaError_t launch_dd_apply(const DDArgs<T>& a, int kind, int grid_cap, cudaStream_t s);

@@ -167,6 +167,25 @@ def test_tensor_core_smoother_3d(th, nrhs):
     assert relerr(tc, ref) < 3e-2
 
 
+@pytest.mark.parametrize("variant", [0, 1, 3, 4, 5])
+def test_mixed_smoother_3d_stream_variants(th, variant):
+    """FP32 arithmetic on BF16 rows with 3-D gathers (z offsets in the column
+    table): the streamed kernels, with and without paired FP32 FMAs, on a tile of
+    four right-hand sides plus a ragged one, against the FP64 smoother."""
+    c = CASES3[0]
+    S, P = build(th, c, nrhs=5, prec="bf16", extra_prec=("fp64",))
+    f = synth.random_complex((5, P.N), 72)
+    u = synth.random_complex((5, P.N), 73)
+    S.set_precision("fp64")
+    ref = host(S.smooth(dev(f), dev(u.copy()))) - u
+    S.set_precision("bf16")
+    S.set_variant("dd_batch", "fp32", 0)
+    S.set_variant("dd", "fp32", variant)
+    got = host(S.smooth(dev(f), dev(u.copy()))) - u
+    S.device_status()
+    assert relerr(got, ref) < 2e-2
+
+
 @pytest.mark.parametrize("c", CASES3[:2])
 def test_mixed_outer_residual_double_single_3d(th, c):
     """The 3-D outer residual in double-single arithmetic, FP32 output: against

@@ -242,7 +242,7 @@ def test_host_buffer_entry_points(th):
 
 # ------------------------------------------------------------ mixed precision
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 2e-3), ("bf16", 2e-2)])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_mixed_smoother_close_to_fp64(th, prec, tol, variant):
     c = CASES[5]
     S, P = build(th, c, prec=prec, extra_prec=("fp64",))
