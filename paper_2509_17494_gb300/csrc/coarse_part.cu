@@ -392,14 +392,19 @@ __global__ void __launch_bounds__(1024, 1) k_chunk_sweep2(const CoarsePartArgs<T
   C* x = a.x + (size_t)rhs * a.Nc;
   const unsigned slot_bytes = (unsigned)(mc * sizeof(C));
   auto block_of = [&](int q) { return q < L ? A + q : A + (2 * L - 2 - q); };
+  // The G rows are copied by the warps that have no row of their own (warps
+  // rpc .. 31) when there are such warps, so the row warps start their
+  // products right after the step's barrier; otherwise by every thread.
+  const int cw0 = rpc < nth / 32 ? rpc : 0;
   auto prefetch = [&](int q) {
     if (q < nsteps) {
       const int j = block_of(q);
-      if (nrow > 0) {
+      if (nrow > 0 && warp >= cw0) {
         const char* src = reinterpret_cast<const char*>(a.G + ((size_t)j * mc + row0) * mcp);
         char* dst = reinterpret_cast<char*>(gbuf + (size_t)(q % 3) * rpc * mcp);
         const int units = (int)((size_t)nrow * mcp * sizeof(C) / 16);
-        for (int u = tid; u < units; u += nth) cp_async16(dst + (size_t)u * 16, src + (size_t)u * 16);
+        for (int u = tid - cw0 * 32; u < units; u += nth - cw0 * 32)
+          cp_async16(dst + (size_t)u * 16, src + (size_t)u * 16);
       }
       // operands staged per entry k by the thread that later uses them, so the
       // vector needs no CTA barrier after the copies: b_j[k], the diagonal
