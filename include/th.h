@@ -358,7 +358,8 @@ th_status th_profile_read(th_ctx* ctx, int kind, double* ms, long long* launches
  *   TH_K_DD:   0 = per-subdomain CTAs with direct loads,
  *              1 = persistent CTAs streaming the rows through TMA bulk copies,
  *              2 = the same with a dedicated producer warp and per-slot
- *                  mbarrier release (no CTA barrier per ring slot),
+ *                  mbarrier release (no CTA barrier per ring slot; the
+ *                  autotuner's usual choice for one rhs on BF16 rows),
  *              3 = variant 1 with smaller ring stages, three CTAs per SM,
  *              4, 5 = variants 1, 3 with paired FP32 FMAs (FP32 cycle on
  *                  BF16 / FP16 rows only; prec must be TH_PREC_FP32; on FP32

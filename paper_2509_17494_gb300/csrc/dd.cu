@@ -576,7 +576,10 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
 // copies into a ring of `depth` slots and refills a slot when every compute
 // warp has released it (one mbarrier arrival per warp, no CTA barrier per
 // slot); the per-subdomain synchronisation uses a named barrier over the
-// compute warps only.  Smaller slots let three CTAs share an SM.
+// compute warps only.  Three stages of up to 32 KB, two CTAs per SM: with
+// per-warp release a stage is back in flight as soon as its slowest warp is
+// done with it (four 24 KB stages, or 16 KB ones with three CTAs per SM, were
+// slower: more stage transitions per subdomain).
 template <typename T, int KIND, int NRHS>
 __global__ void __launch_bounds__(512, 2) k_dd_stream2(const DDArgs<T> a, int cps, int depth, int* err) {
   using C = typename Cx<T>::t;
@@ -737,8 +740,8 @@ static cudaError_t launch_dd_stream2_k(const DDArgs<T>& a0, int* err, int sms, c
   a.G = std::max(1, std::min(a0.G, (480 / 32 * 32) / a0.NR));
   const int threads = ((a.NR * a.G + 31) / 32) * 32 + 32;
   if (threads > 512) return cudaErrorInvalidConfiguration;
-  const int depth = 4;
-  const int cps = std::max(1, (int)((16 * 1024) / ((size_t)a.NR * 16)));
+  const int depth = 3;
+  const int cps = std::max(1, (int)((32 * 1024) / ((size_t)a.NR * 16)));
   const size_t slot_bytes = (size_t)cps * a.NR * 16;
   const size_t smem = depth * slot_bytes + 16 * sizeof(uint64_t) +
                       sizeof(C) * ((size_t)2 * NRHS * a.NCH * CPC + (size_t)a.G * a.NR * NRHS);
