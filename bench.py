@@ -37,10 +37,11 @@ METRIC = "fine-level two-grid cycle GDOF/s and time-to-1e-8 residual vs plain FP
 WORKLOAD = "square40_q4_n100"
 HBM_FALLBACK_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32-cycle
-# subdomain kernel (BF16 rows, 1 rhs) on this workload, by kernel variant: an
-# ncu capture of three launches of this script's timed region (variant 1, the
-# streamed kernel); None for a variant without a current capture.
-DD_TRAFFIC_BYTES = {0: None, 1: 239.9e6, 2: None, 3: None, 4: None, 5: None}
+# subdomain kernel (BF16 rows, 1 rhs) on this workload, by kernel variant: the
+# mean over ncu captures of three (variant 1, CTA-barrier ring) and five
+# (variant 2, producer warp) launches of this script's timed region; None for a
+# variant without a current capture.
+DD_TRAFFIC_BYTES = {0: None, 1: 239.9e6, 2: 239.5e6, 3: None, 4: None, 5: None}
 
 
 def parse():
