@@ -33,12 +33,23 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
   C* su = reinterpret_cast<C*>(smraw);
   C* s1 = su + UT * UT;
   C* s2 = s1 + CELLS * NP * NP;
+  constexpr int WO = TC * P + 1;                       // owned nodes per direction, at most
+  C* sf = s2 + CELLS * NP * NP;                        // [WO * WO] right-hand side at the owned nodes
+  T* skc = reinterpret_cast<T*>(sf + WO * WO);         // [CELLS] k, then eps, of the tile's cells
+  T* sec = skc + CELLS;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int cx0 = blockIdx.x * TC, cy0 = blockIdx.y * TC;
   const int ex0 = cx0 - 1, ey0 = cy0 - 1;
   const size_t roff = (size_t)blockIdx.z * a.N;
   const C* u = a.u + roff;
+  // owned nodes (phase 3)
+  const int ncx = min(TC, a.n - cx0), ncy = min(TC, a.n - cy0);
+  const int wx = ncx * P + ((cx0 + ncx == a.n) ? 1 : 0);
+  const int wy = ncy * P + ((cy0 + ncy == a.n) ? 1 : 0);
 
+  // Every global load of the tile is issued here, before the first barrier, so
+  // the CTA waits for memory once: its nodal values, its cells' coefficients
+  // and (residual form) the right-hand side at its owned nodes.
   for (int i = tid; i < UT * UT; i += nth) {
     const int iy = i / UT, ix = i - iy * UT;
     const int gx = ex0 * P + ix, gy = ey0 * P + iy;
@@ -48,6 +59,20 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
     if (gx >= 0 && gx < a.m && gy >= 0 && gy < a.m) v = NodeIO<T>::ld(u, (size_t)gy * a.m + gx);
     su[i] = v;
   }
+  for (int e = tid; e < CELLS; e += nth) {
+    const int ecy = e / E, ecx = e - ecy * E;
+    const int gcx = ex0 + ecx, gcy = ey0 + ecy;
+    if (gcx >= 0 && gcx < a.n && gcy >= 0 && gcy < a.n) {
+      const size_t cell = (size_t)gcy * a.n + gcx;
+      skc[e] = a.kc[cell];
+      sec[e] = a.ec[cell];
+    }
+  }
+  if (a.f)
+    for (int i = tid; i < wx * wy; i += nth) {
+      const int ly = i / wx, lx = i - ly * wx;
+      sf[i] = NodeIO<T>::ld(a.f, roff + (size_t)(cy0 * P + ly) * a.m + (cx0 * P + lx));
+    }
   __syncthreads();
 
   // phase 1: x-contractions of every row of every (extended) cell.  M and K
@@ -113,8 +138,7 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
     const int ecy = e / E, ecx = e - ecy * E;
     const int gcx = ex0 + ecx, gcy = ey0 + ecy;
     if (gcx < 0 || gcx >= a.n || gcy < 0 || gcy >= a.n) continue;
-    const size_t cell = (size_t)gcy * a.n + gcx;
-    const T kk = a.kc[cell], ee = a.ec[cell];
+    const T kk = skc[e], ee = sec[e];
     const T me_r = -kk * kk * a.h2, me_i = -(a.alpha * kk * kk + ee) * a.h2;
     C t1[NP], z[NP];
 #pragma unroll
@@ -195,9 +219,6 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
   __syncthreads();
 
   // phase 3: owned nodes sum their cells in a fixed order
-  const int ncx = min(TC, a.n - cx0), ncy = min(TC, a.n - cy0);
-  const int wx = ncx * P + ((cx0 + ncx == a.n) ? 1 : 0);
-  const int wy = ncy * P + ((cy0 + ncy == a.n) ? 1 : 0);
   // output and right-hand side addressed from their bases: the double-single
   // variant's output elements are narrower than C (see NodeIO<ds>)
   for (int i = tid; i < wx * wy; i += nth) {
@@ -232,9 +253,8 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
     const size_t g = (size_t)(cy0 * P + ly) * a.m + (cx0 * P + lx);
     C out;
     if (a.f) {
-      const C fv = NodeIO<T>::ld(a.f, roff + g);
-      out.x = fv.x - ar;
-      out.y = fv.y - ai;
+      out.x = sf[i].x - ar;
+      out.y = sf[i].y - ai;
     } else {
       out.x = ar;
       out.y = ai;
@@ -247,7 +267,8 @@ template <int P, int TC, typename T>
 static cudaError_t launch_fine_p(const FineArgs<T>& a, int nrhs, cudaStream_t s) {
   using C = typename Cx<T>::t;
   constexpr int NP = P + 1, E = TC + 1, UT = E * P + 1;
-  const size_t smem = sizeof(C) * (size_t)(UT * UT + 2 * E * E * NP * NP);
+  const size_t smem = sizeof(C) * (size_t)(UT * UT + 2 * E * E * NP * NP + (TC * P + 1) * (TC * P + 1)) +
+                      sizeof(T) * 2 * E * E;
   static bool attr_set = false;  // per instantiation
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_fine_apply<P, TC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
