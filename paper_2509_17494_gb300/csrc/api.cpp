@@ -1137,7 +1137,8 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
   if (x->gal) {
     if ((st = th::galerkin_setup(g, k_host, eps, x->prm.alpha_c, gb)) != TH_OK) return st;
   } else if (!d3) {
-    if ((st = th::coarse_setup(g, k_host, eps, cb)) != TH_OK) return st;
+    // the unpartitioned block inverses only for the FP64 no-alloc sweep
+    if ((st = th::coarse_setup(g, k_host, eps, cb, x->G64 != nullptr)) != TH_OK) return st;
     if ((st = th::coarse_partition(g, cb, x->P, cpart)) != TH_OK) return st;
   } else {
     if ((st = th::coarse_setup3(g, k_host, eps, cb3)) != TH_OK) return st;

@@ -608,9 +608,16 @@ void qsfem_cell(double k, double eps, double hc, cplx d[3]) {
   d[2] = cplx(s * num2, -eps * h2 / 36.0);
 }
 
+static bool dense_inverse_par(std::vector<cplx>& S, int n, cplx* out);
+
 // Inverse of a dense complex matrix (LU with partial pivoting, then one
-// triangular solve per unit column, columns in parallel).
+// triangular solve per unit column, columns in parallel); for n >= 1024 the
+// LU's trailing update is split over a thread team (dense_inverse_par: the same
+// operations in the same order, so the same result; for the 2-D coarse blocks,
+// n <= 1024, its two team barriers per pivot cost more than they save: 40 s
+// against 18 s for the 401 blocks of 401 rows).  Callers outside a parallel region.
 static bool dense_inverse(std::vector<cplx>& S, int n, cplx* out) {
+  if (n >= 1024) return dense_inverse_par(S, n, out);
   std::vector<int> piv;
   if (!band_lu(S.data(), n, n - 1, n - 1, piv)) return false;
   // column c of the inverse solves S x = e_c; write it as column c of out
@@ -623,7 +630,8 @@ static bool dense_inverse(std::vector<cplx>& S, int n, cplx* out) {
   return true;
 }
 
-th_status coarse_setup(const Geometry& g, const double* k, const double* eps, CoarseBlocks& cb) {
+th_status coarse_setup(const Geometry& g, const double* k, const double* eps, CoarseBlocks& cb,
+                       bool block_inverses) {
   const int nc = g.nc, mc = g.mc, q = g.q;
   cb.mc = mc;
   cb.cell.assign((size_t)nc * nc * 3, cplx(0.0));
@@ -681,6 +689,7 @@ th_status coarse_setup(const Geometry& g, const double* k, const double* eps, Co
     }
   }
   // block elimination: S_0 = D_0, S_j = D_j - B_j S_{j-1}^{-1} C_{j-1}, B_j = C_{j-1}^T
+  if (!block_inverses) return TH_OK;
   cb.G.assign((size_t)mc * mm, cplx(0.0));
   std::vector<cplx> S(mm), T(mm);
   for (int j = 0; j < mc; ++j) {
@@ -767,23 +776,29 @@ namespace {
 
 using Mat = std::vector<cplx>;
 
-// C = alpha A B (+ C when acc), n x n dense row-major, serial (i-k-j order)
-void zgemm(int n, const cplx* A, const cplx* B, cplx* C, cplx alpha, bool acc) {
-  if (!acc) std::fill(C, C + (size_t)n * n, cplx(0.0));
-  for (int i = 0; i < n; ++i) {
-    double* ci = reinterpret_cast<double*>(C + (size_t)i * n);
-    for (int k = 0; k < n; ++k) {
-      const cplx a = alpha * A[(size_t)i * n + k];
-      const double ar = a.real(), ai = a.imag();
-      if (ar == 0.0 && ai == 0.0) continue;
-      const double* bk = reinterpret_cast<const double*>(B + (size_t)k * n);
-      for (int j = 0; j < n; ++j) {
-        const double br = bk[2 * j], bi = bk[2 * j + 1];
-        ci[2 * j] += ar * br - ai * bi;
-        ci[2 * j + 1] += ar * bi + ai * br;
-      }
+// row i of C = alpha A B (+ C when acc), n x n dense row-major (k-j order)
+inline void zgemm_row(int n, int i, const cplx* A, const cplx* B, cplx* C, cplx alpha, bool acc) {
+  double* ci = reinterpret_cast<double*>(C + (size_t)i * n);
+  if (!acc) std::fill(C + (size_t)i * n, C + (size_t)(i + 1) * n, cplx(0.0));
+  for (int k = 0; k < n; ++k) {
+    const cplx a = alpha * A[(size_t)i * n + k];
+    const double ar = a.real(), ai = a.imag();
+    if (ar == 0.0 && ai == 0.0) continue;
+    const double* bk = reinterpret_cast<const double*>(B + (size_t)k * n);
+    for (int j = 0; j < n; ++j) {
+      const double br = bk[2 * j], bi = bk[2 * j + 1];
+      ci[2 * j] += ar * br - ai * bi;
+      ci[2 * j + 1] += ar * bi + ai * br;
     }
   }
+}
+// C = alpha A B (+ C when acc), serial
+void zgemm(int n, const cplx* A, const cplx* B, cplx* C, cplx alpha, bool acc) {
+  for (int i = 0; i < n; ++i) zgemm_row(n, i, A, B, C, alpha, acc);
+}
+// the same with the rows over threads (callers outside a parallel region)
+void zgemm_par(int n, const cplx* A, const cplx* B, cplx* C, cplx alpha, bool acc) {
+  parallel_for(n, [&](int i) { zgemm_row(n, i, A, B, C, alpha, acc); });
 }
 
 // Tridiagonal block helpers over the C_j diagonals (cl, cd, cu at row offset o = j mc):
@@ -1257,19 +1272,19 @@ th_status coarse_partition(const Geometry& g, const CoarseBlocks& cb, int P, Coa
       tri_CT_left(mc, cl + op, cd + op, cu + op, Lend[k].data(), W.data());
       for (auto& v : W) v = -v;
       // S -= What_k Ghat_{k-1} Ehat_{k-1}
-      zgemm(mc, Ghp.data(), Eprev.data(), T.data(), 1.0, false);
-      zgemm(mc, W.data(), T.data(), S.data(), -1.0, true);
+      zgemm_par(mc, Ghp.data(), Eprev.data(), T.data(), 1.0, false);
+      zgemm_par(mc, W.data(), T.data(), S.data(), -1.0, true);
     }
-    if (!zinverse_serial(mc, S, Gk.data())) return TH_ERR_SINGULAR;
+    if (!dense_inverse(S, mc, Gk.data())) return TH_ERR_SINGULAR;
     store_padded(mc, ld, Gk.data(), &cp.Gh[(size_t)k * mc * ld]);
     if (k > 0) {
-      zgemm(mc, Gk.data(), W.data(), T.data(), 1.0, false);
+      zgemm_par(mc, Gk.data(), W.data(), T.data(), 1.0, false);
       store_padded(mc, ld, T.data(), &cp.Fh[(size_t)k * mc * ld]);
     }
     if (k < K - 1) {
       tri_C_left(mc, cl + os, cd + os, cu + os, Rbeg[k + 1].data(), E.data());
       for (auto& v : E) v = -v;
-      zgemm(mc, Gk.data(), E.data(), T.data(), 1.0, false);
+      zgemm_par(mc, Gk.data(), E.data(), T.data(), 1.0, false);
       store_padded(mc, ld, T.data(), &cp.Hh[(size_t)k * mc * ld]);
       Eprev = E;
     }
@@ -1277,38 +1292,51 @@ th_status coarse_partition(const Geometry& g, const CoarseBlocks& cb, int P, Coa
   }
   // explicit inverse of the reduced system, one column per unit right-hand side
   // through its block factorisation (forward zhat_k = Ghat_k rhat_k - F_k zhat_{k-1},
-  // backward xhat_k = zhat_k - H_k xhat_{k+1}); columns in parallel
+  // backward xhat_k = zhat_k - H_k xhat_{k+1}); tasks of up to CB columns of one
+  // separator block share each matrix row they read (every column's sums keep
+  // their order), tasks in parallel
   if (K > 0) {
     const size_t nred = (size_t)K * mc;
     cp.Sinv.assign(nred * nred, cplx(0.0));
-    parallel_for((int)nred, [&](int col) {
-      const int k0 = col / mc, e0 = col % mc;
-      std::vector<cplx> z(nred, cplx(0.0)), xh(nred, cplx(0.0));
+    constexpr int CB = 16;
+    const int per_block = (mc + CB - 1) / CB;
+    parallel_for(K * per_block, [&](int task) {
+      const int k0 = task / per_block, e_begin = (task - k0 * per_block) * CB;
+      const int nb = std::min(CB, mc - e_begin);
+      std::vector<cplx> z((size_t)CB * nred, cplx(0.0)), xh((size_t)CB * nred, cplx(0.0));  // [column][nred]
+      cplx acc[CB];
       for (int k = k0; k < K; ++k) {
-        cplx* zk = &z[(size_t)k * mc];
-        if (k == k0) {
-          for (int r = 0; r < mc; ++r) zk[r] = cp.Gh[((size_t)k * mc + r) * ld + e0];
-        } else {
-          const cplx* zp = &z[(size_t)(k - 1) * mc];
-          for (int r = 0; r < mc; ++r) {
-            const cplx* f = &cp.Fh[((size_t)k * mc + r) * ld];
-            cplx acc = 0.0;
-            for (int c2 = 0; c2 < mc; ++c2) acc += f[c2] * zp[c2];
-            zk[r] = -acc;
+        for (int r = 0; r < mc; ++r) {
+          if (k == k0) {
+            for (int j = 0; j < nb; ++j) z[(size_t)j * nred + (size_t)k * mc + r] = cp.Gh[((size_t)k * mc + r) * ld + e_begin + j];
+            continue;
           }
+          const cplx* f = &cp.Fh[((size_t)k * mc + r) * ld];
+          for (int j = 0; j < nb; ++j) acc[j] = 0.0;
+          for (int c2 = 0; c2 < mc; ++c2) {
+            const cplx fv = f[c2];
+            for (int j = 0; j < nb; ++j) acc[j] += fv * z[(size_t)j * nred + (size_t)(k - 1) * mc + c2];
+          }
+          for (int j = 0; j < nb; ++j) z[(size_t)j * nred + (size_t)k * mc + r] = -acc[j];
         }
       }
-      for (int r = 0; r < mc; ++r) xh[(size_t)(K - 1) * mc + r] = z[(size_t)(K - 1) * mc + r];
+      for (int j = 0; j < nb; ++j)
+        for (int r = 0; r < mc; ++r)
+          xh[(size_t)j * nred + (size_t)(K - 1) * mc + r] = z[(size_t)j * nred + (size_t)(K - 1) * mc + r];
       for (int k = K - 2; k >= 0; --k) {
-        const cplx* xn = &xh[(size_t)(k + 1) * mc];
         for (int r = 0; r < mc; ++r) {
           const cplx* hrow = &cp.Hh[((size_t)k * mc + r) * ld];
-          cplx acc = 0.0;
-          for (int c2 = 0; c2 < mc; ++c2) acc += hrow[c2] * xn[c2];
-          xh[(size_t)k * mc + r] = z[(size_t)k * mc + r] - acc;
+          for (int j = 0; j < nb; ++j) acc[j] = 0.0;
+          for (int c2 = 0; c2 < mc; ++c2) {
+            const cplx hv = hrow[c2];
+            for (int j = 0; j < nb; ++j) acc[j] += hv * xh[(size_t)j * nred + (size_t)(k + 1) * mc + c2];
+          }
+          for (int j = 0; j < nb; ++j)
+            xh[(size_t)j * nred + (size_t)k * mc + r] = z[(size_t)j * nred + (size_t)k * mc + r] - acc[j];
         }
       }
-      for (size_t r = 0; r < nred; ++r) cp.Sinv[r * nred + col] = xh[r];
+      for (size_t r = 0; r < nred; ++r)
+        for (int j = 0; j < nb; ++j) cp.Sinv[r * nred + (size_t)k0 * mc + e_begin + j] = xh[(size_t)j * nred + r];
     });
   }
   return TH_OK;

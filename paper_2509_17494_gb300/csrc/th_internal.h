@@ -81,7 +81,10 @@ struct CoarseBlocks {
   std::vector<cplx> cl, cd, cu;   // C_j = A[row j, row j+1] tridiagonal, mc x mc (row mc-1 unused)
   std::vector<cplx> G;            // mc blocks of mc x mc
 };
-th_status coarse_setup(const Geometry& g, const double* k, const double* eps, CoarseBlocks& cb);
+// block_inverses = false leaves G empty (only the unpartitioned FP64 sweep of
+// th_coarse_solve_noalloc reads it).
+th_status coarse_setup(const Geometry& g, const double* k, const double* eps, CoarseBlocks& cb,
+                       bool block_inverses = true);
 
 // 3-D coarse operator (fitted 27-point scheme) in z-slice block form: the
 // unknowns of slice j are the mb = mc^2 coarse nodes of that slice.
