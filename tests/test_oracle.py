@@ -190,6 +190,47 @@ def test_coarse_mass_term_matches_q1_mass():
     assert abs(Mm[c, c + m + 1] / hc ** 2 - g["mass_corner_over_h2"]) < 1e-13
 
 
+@pytest.mark.parametrize("side", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_coarse_absorbing_term_is_minus_ik_boundary_integral(side):
+    """The Gamma_abs term of the 'quasi finite element' A_q (Section 3.3):
+    adding an absorbing side adds the bilinear form -i int_side k phi_a phi_b ds
+    with k constant per coarse cell.  Checked without the oracle's 1-D mass
+    matrix: for nodal vectors v, w on the side, the Q1 basis represents the
+    piecewise-linear interpolants I v, I w, whose product is quadratic on each
+    cell and is integrated exactly by Simpson's rule.  A wrong scale (h_c^2
+    for h_c), sign, mass entry or cell of k fails here."""
+    n, p = 3, 4
+    q = p // 2
+    nc = n * q
+    hc = 1.0 / nc
+    m = nc + 1
+    kf = synth.rng(17).uniform(3.0, 9.0, (n, n))           # k per fine cell [cy, cx]
+    B0 = qsfem.assemble_coarse(n, p, kf, 0 * kf, ())
+    B1 = qsfem.assemble_coarse(n, p, kf, 0 * kf, [side])
+    D = (B1 - B0).toarray()
+    axis, end = side
+    grid = np.arange(m * m).reshape(m, m)                    # [iy, ix]
+    j = 0 if end == 0 else m - 1
+    nodes = grid[j, :] if axis == 0 else grid[:, j]          # ordered along the side
+    fine_row = 0 if end == 0 else n - 1
+    # k of the coarse cell c along the side: the fine cell that contains it
+    ks = np.array([kf[fine_row, c // q] if axis == 0 else kf[c // q, fine_row] for c in range(nc)])
+    off = np.ones(m * m, bool)
+    off[nodes] = False
+    assert np.all(D[off, :] == 0) and np.all(D[:, off] == 0)
+    Ds = D[np.ix_(nodes, nodes)]
+    r = synth.rng(18)
+    for _ in range(4):
+        v = r.standard_normal(m) + 1j * r.standard_normal(m)
+        w = r.standard_normal(m) + 1j * r.standard_normal(m)
+        fl, fr = v[:-1] * w[:-1], v[1:] * w[1:]
+        fm = 0.25 * (v[:-1] + v[1:]) * (w[:-1] + w[1:])
+        want = -1j * np.sum(ks * hc / 6.0 * (fl + 4.0 * fm + fr))
+        assert abs(v @ Ds @ w - want) < 1e-13 * max(1.0, abs(want))
+    # v = w = 1: the side integral of k
+    assert abs(D.sum() + 1j * np.sum(ks) * hc) < 1e-13 * np.sum(ks)
+
+
 # --------------------------------------------------------------- prolongation
 @pytest.mark.parametrize("p", [2, 4, 6])
 def test_prolongation_reproduces_half_degree_polynomials(p):
