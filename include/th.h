@@ -233,13 +233,19 @@ th_status th_cycle_host(th_ctx* ctx, const double* f_host, double* u_host, int n
  * library, so the call uses only rc_dev (input), uc_dev (output) and the
  * context's factors, which it only reads.  It calls no cudaMalloc, cudaFree or
  * other allocating routine.
+ *   Scope: the 2-D dispersion-matched (QSFEM) coarse level of an FP64-prepared
+ *   context.  3-D contexts, Galerkin-coarsened contexts and contexts without
+ *   FP64 factors return TH_ERR_UNSUPPORTED.
  *   Limit: Nc * nrhs <= 262144 complex values (e.g. one right-hand side up to a
  *   401 x 401 coarse grid); larger requests return TH_ERR_ARG.  nrhs must not
- *   exceed the context's nrhs_max.  A context without FP64 factors returns
- *   TH_ERR_UNSUPPORTED.
- *   The array is per GPU and stays allocated until the process exits.  The
- *   first call on a device looks up the array's device address with that device
- *   current; make that first call before any CUDA stream capture.
+ *   exceed the context's nrhs_max.  The current device must be the one the
+ *   context was set up on (TH_ERR_ARG otherwise).
+ *   The array is per GPU and stays allocated until the process exits.  Every
+ *   call made outside a stream capture looks up the array's device address with
+ *   the current device (so a device reset or another current context cannot
+ *   leave a stale address); a call on a capturing stream reuses the address of
+ *   the last uncaptured call on that device, so make one call on each device
+ *   before capturing it, and none across a device reset inside a capture.
  *   All calls share the one array and it keeps the last call's contents (every
  *   entry is written before it is read, so nothing needs clearing); calls whose
  *   executions overlap on the GPU (other streams) race on it. */
@@ -424,6 +430,17 @@ th_status th_host_inverse_rows(const th_mesh* mesh, const double* k_host, const 
 th_status th_host_galerkin(const th_mesh* mesh, const double* k_host, const double* eps_host,
                            const th_params* prm, double* stencil, size_t stencil_len,
                            const double* b, double* x);
+
+/* Host-only probe of the partitioned coarse set-up (Algorithm 1's coarse solve,
+ * 2-D QSFEM coarse level): with the coarse node rows split into P chunks and
+ * P - 1 separator rows, writes the separator row indices (sep, P - 1 ints)
+ * and the explicit inverse of the reduced separator system that the device
+ * solve applies, sinv[((k mc + r) (P-1) mc + k' mc + r')] (interleaved
+ * complex, row-major, (P-1) mc square; sinv_len doubles, at least
+ * 2 ((P-1) mc)^2).  That matrix is the separator block of A_q^{-1}.
+ * TH_ERR_ARG unless 2 <= P and 2P - 1 <= mc; TH_ERR_NOMEM if sinv_len is short. */
+th_status th_host_coarse_separators(const th_mesh* mesh, const double* k_host, const double* eps_host,
+                                    const th_params* prm, int P, int* sep, double* sinv, size_t sinv_len);
 
 /* ---------------------------------------------------- Fourier analysis */
 

@@ -110,6 +110,8 @@ def lib() -> ctypes.CDLL:
         "th_host_inverse_rows": ([ctypes.POINTER(Mesh), P, P, ctypes.POINTER(Params), I, P, P,
                                   ctypes.c_size_t], I),
         "th_host_galerkin": ([ctypes.POINTER(Mesh), P, P, ctypes.POINTER(Params), P, ctypes.c_size_t, P, P], I),
+        "th_host_coarse_separators": ([ctypes.POINTER(Mesh), P, P, ctypes.POINTER(Params), I, P, P,
+                                       ctypes.c_size_t], I),
         "th_lfa_rho": ([I, I, I, I, D, P, I, P, P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -243,6 +245,21 @@ def host_galerkin(n, p, k_cell, eps_cell=None, bc="robin", alpha_c=0.0, b=None):
            "th_host_galerkin")
     sten = (st[0::2] + 1j * st[1::2]).reshape(mc * mc, S, S)
     return sten, (xo if b is not None else None)
+
+
+def host_coarse_separators(n, p, k_cell, eps_cell=None, bc="robin", P=3):
+    """(separator rows, explicit inverse of the reduced separator system) of the
+    host partitioned coarse set-up with P chunks (th_host_coarse_separators)."""
+    mc = n * p // 2 + 1
+    nred = (P - 1) * mc
+    m, prm = _mesh(n, p, bc, 2), _params()
+    k, kp = _f64(k_cell)
+    e, ep = _f64(eps_cell if eps_cell is not None else np.zeros_like(k))
+    sep = np.zeros(P - 1, dtype=np.int32)
+    out = np.zeros(2 * nred * nred)
+    _check(lib().th_host_coarse_separators(ctypes.byref(m), kp, ep, ctypes.byref(prm), int(P), sep.ctypes.data,
+                                           out.ctypes.data, out.size), "th_host_coarse_separators")
+    return sep, (out[0::2] + 1j * out[1::2]).reshape(nred, nred)
 
 
 def lfa_rho(p, params, n_s=1, npts=48, per_theta=False, coarse="qsfem", alpha_c=0.0, stream=None):

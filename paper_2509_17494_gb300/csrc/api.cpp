@@ -62,6 +62,7 @@ struct th_ctx {
   int cs_variant = 1;        // one-rhs coarse chunk sweep: 0 two-phase, 1 one barrier per step (autotuned)
   unsigned char* Wu = nullptr;  // BF16 inverse rows in the tcgen05 operand layout (NR <= 128)
   int sms = 152;
+  int device = -1;          // CUDA device the context was set up on
   int* derr = nullptr;      // device flag: a bounded device wait gave up
   // device arrays
   double *kc64 = nullptr, *ec64 = nullptr;
@@ -1051,8 +1052,9 @@ th_status tune_dd(th_ctx& x, int wkind, cudaStream_t s, int& choice) {
 
 namespace th {
 // Read-only view of the FP64 coarse factors of a context (for th_coarse_solve_noalloc).
-bool coarse_factors_fp64(const th_ctx* x, CoarseSolveArgs<double>* a, int* cluster, int* nrhs_max) {
+bool coarse_factors_fp64(const th_ctx* x, CoarseSolveArgs<double>* a, int* cluster, int* nrhs_max, int* device) {
   if (!x || !x->G64) return false;
+  *device = x->device;
   a->G = x->G64;
   a->cl = x->cl64;
   a->cd = x->cd64;
@@ -1383,6 +1385,7 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
   {
     int dev = 0;
     TH_CU(cudaGetDevice(&dev));
+    x->device = dev;
     TH_CU(cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, dev));
     TH_CU(cudaMemsetAsync(x->derr, 0, 64 * sizeof(int), s));
   }
@@ -2026,6 +2029,31 @@ th_status th_host_inverse_rows(const th_mesh* mesh, const double* k_host, const 
 }
 
 }  // extern "C"
+
+th_status th_host_coarse_separators(const th_mesh* mesh, const double* k_host, const double* eps_host,
+                                    const th_params* prm, int P, int* sep, double* sinv, size_t sinv_len) {
+  if (!mesh || !prm || !k_host || !sep || !sinv) return TH_ERR_ARG;
+  if (mesh->dim != 2) return TH_ERR_UNSUPPORTED;
+  th::Geometry g;
+  th_status st = th::make_geometry(*mesh, *prm, g);
+  if (st != TH_OK) return st;
+  if (P < 2 || 2 * P - 1 > g.mc) return TH_ERR_ARG;
+  const size_t nred = (size_t)(P - 1) * g.mc;
+  if (sinv_len < 2 * nred * nred) return TH_ERR_NOMEM;
+  std::vector<double> zero;
+  const double* eps = eps_host;
+  if (!eps) {
+    zero.assign((size_t)g.n * g.n, 0.0);
+    eps = zero.data();
+  }
+  th::CoarseBlocks cb;
+  if ((st = th::coarse_setup(g, k_host, eps, cb, false)) != TH_OK) return st;
+  th::CoarsePart cp;
+  if ((st = th::coarse_partition(g, cb, P, cp)) != TH_OK) return st;
+  for (int k = 0; k < P - 1; ++k) sep[k] = cp.sep[k];
+  std::memcpy(sinv, cp.Sinv.data(), nred * nred * sizeof(cplx));
+  return TH_OK;
+}
 
 th_status th_host_galerkin(const th_mesh* mesh, const double* k_host, const double* eps_host,
                            const th_params* prm, double* stencil, size_t stencil_len, const double* b, double* xo) {

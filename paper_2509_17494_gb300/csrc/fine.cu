@@ -269,13 +269,11 @@ static cudaError_t launch_fine_p(const FineArgs<T>& a, int nrhs, cudaStream_t s)
   constexpr int NP = P + 1, E = TC + 1, UT = E * P + 1;
   const size_t smem = sizeof(C) * (size_t)(UT * UT + 2 * E * E * NP * NP + (TC * P + 1) * (TC * P + 1)) +
                       sizeof(T) * 2 * E * E;
-  static bool attr_set = false;  // per instantiation
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_fine_apply<P, TC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // set on every launch (a cheap host call): the attribute is per device, and
+  // any device of the process may run this instantiation
+  cudaError_t e = cudaFuncSetAttribute(k_fine_apply<P, TC, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
   const int tiles = (a.n + TC - 1) / TC;
   dim3 grid(tiles, tiles, nrhs);
   k_fine_apply<P, TC, T><<<grid, TC >= 8 ? 256 : 128, smem, s>>>(a);

@@ -15,7 +15,7 @@
 #include "th_internal.h"
 
 namespace th {
-bool coarse_factors_fp64(const th_ctx* ctx, CoarseSolveArgs<double>* a, int* cluster, int* nrhs_max);
+bool coarse_factors_fp64(const th_ctx* ctx, CoarseSolveArgs<double>* a, int* cluster, int* nrhs_max, int* device);
 }
 
 namespace {
@@ -26,21 +26,29 @@ constexpr long long kNoallocComplex = 1LL << 18;
 
 static __device__ __align__(256) double2 g_noalloc_z[kNoallocComplex];
 
-// Device address of g_noalloc_z, looked up once per device with that device
-// current.  Host code must not use the symbol itself as a device pointer.
+// Device address of g_noalloc_z.  Host code must not use the symbol itself as
+// a device pointer.  The address is looked up with the caller's device current
+// on every call made outside a stream capture, so a module reload (after a
+// device reset, or with another context current) cannot leave a stale pointer
+// behind; the copy kept per device is used only while the caller's stream is
+// being captured, when a lookup could load the module and is not allowed.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double2* g_addr[kMaxDevices] = {};
 
-th_status scratch_address(double2** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TH_ERR_CUDA;
+th_status scratch_address(int dev, cudaStream_t stream, double2** out) {
+  if (dev < 0 || dev >= kMaxDevices) return TH_ERR_CUDA;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return TH_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_z) != cudaSuccess || !p) return TH_ERR_CUDA;
-    g_addr[dev] = static_cast<double2*>(p);
+  if (cap != cudaStreamCaptureStatusNone) {
+    if (!g_addr[dev]) return TH_ERR_CUDA;  // first call on this device inside a capture
+    *out = g_addr[dev];
+    return TH_OK;
   }
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_z) != cudaSuccess || !p) return TH_ERR_CUDA;
+  g_addr[dev] = static_cast<double2*>(p);
   *out = g_addr[dev];
   return TH_OK;
 }
@@ -51,16 +59,20 @@ extern "C" th_status th_coarse_solve_noalloc(const th_ctx* ctx, const double* rc
                                              void* stream) {
   if (!ctx || !rc_dev || !uc_dev || nrhs < 1) return TH_ERR_ARG;
   th::CoarseSolveArgs<double> a{};
-  int cluster = 0, nrhs_max = 0;
-  if (!th::coarse_factors_fp64(ctx, &a, &cluster, &nrhs_max)) return TH_ERR_UNSUPPORTED;
+  int cluster = 0, nrhs_max = 0, ctx_dev = -1;
+  if (!th::coarse_factors_fp64(ctx, &a, &cluster, &nrhs_max, &ctx_dev)) return TH_ERR_UNSUPPORTED;
   if (nrhs > nrhs_max) return TH_ERR_ARG;
   if (a.Nc * (long long)nrhs > kNoallocComplex) return TH_ERR_ARG;  // beyond the fixed scratch
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TH_ERR_CUDA;
+  if (dev != ctx_dev) return TH_ERR_ARG;  // the factors live on another device
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   double2* z = nullptr;
-  th_status st = scratch_address(&z);
+  th_status st = scratch_address(dev, s, &z);
   if (st != TH_OK) return st;
   a.rhs = reinterpret_cast<const double2*>(rc_dev);
   a.x = reinterpret_cast<double2*>(uc_dev);
   a.z = z;  // every z entry is written by the forward sweep before the backward sweep reads it
-  cudaError_t e = th::launch_coarse_solve<double>(a, nrhs, cluster, reinterpret_cast<cudaStream_t>(stream));
+  cudaError_t e = th::launch_coarse_solve<double>(a, nrhs, cluster, s);
   return e == cudaSuccess ? TH_OK : TH_ERR_CUDA;
 }

@@ -167,6 +167,23 @@ def test_tensor_core_smoother_3d(th, nrhs):
     assert relerr(tc, ref) < 3e-2
 
 
+def test_tensor_core_smoother_3d_64rhs_against_oracle(th):
+    """64 right-hand sides (four tiles of 16) of the 3-D tensor-core products
+    against the oracle's Algorithm 2 directly, per right-hand side."""
+    c = CASES3[1]  # ragged blocks, mixed sides
+    nrhs = 64
+    S, P = build(th, c, nrhs=nrhs, prec="bf16")
+    assert S.get_variant("dd_batch", "fp32") == 1
+    sm = dd.DDSmoother(P, c["l_dd"])
+    f = synth.random_complex((nrhs, P.N), 74)
+    u = synth.random_complex((nrhs, P.N), 75)
+    got = host(S.smooth(dev(f), dev(u.copy()))) - u
+    S.device_status()
+    want = np.stack([sm.smooth(u[i], f[i], 1) for i in range(nrhs)]) - u
+    for i in range(nrhs):
+        assert relerr(got[i], want[i]) < 3e-2, i
+
+
 @pytest.mark.parametrize("variant", [0, 1, 3, 4, 5])
 def test_mixed_smoother_3d_stream_variants(th, variant):
     """FP32 arithmetic on BF16 rows with 3-D gathers (z offsets in the column

@@ -1,0 +1,134 @@
+"""Parity at the sizes the benchmark reports, through the C ABI.
+
+* 40-wavelength 401^2 Q4 workload (random k-field, 10-dof layer, Robin
+  sides, centred source): the oracle's FGMRES with its own two-grid
+  preconditioner runs here (about a minute of CPU).  The FP64 GPU solve takes
+  the same number of iterations and lands within 1e-7 of the oracle's
+  solution (same arithmetic up to rounding order); the mixed form (FP32
+  cycle, BF16 inverse rows, FP64 FGMRES) reaches 1e-8 and lies within 1e-6 of
+  the oracle's solution, the target the mixed form is held to.
+* 80-wavelength 801^2 Q4 workload, 8 of its 64 seeded sources solved as one
+  batch (tensor-core subdomain products, coarse solve on tiles of
+  right-hand sides), and the 81^3 Q2 cube with its 8 sources: the oracle's
+  solutions of the first sources are too slow to recompute in a test (tens
+  of minutes of CPU), so they come from tests/golden/full_size_solutions.json,
+  written by tests/golden/make_full_size_solutions.py with the oracle alone,
+  to a residual of 1e-10.  Compared on the 1000 stored entries of each
+  (max-norm relative to the largest stored entry) and by the 2-norm.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import krylov, twogrid
+from tests.common import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "full_size_solutions.json")
+
+
+@pytest.fixture(scope="module")
+def th():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    import paper_2509_17494_gb300 as th
+    return th
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def rel2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def golden_cases(workload):
+    with open(GOLDEN) as fh:
+        doc = json.load(fh)
+    return [c for c in doc["cases"] if c["workload"] == workload]
+
+
+def check_against_samples(x, case, tol):
+    idx = np.asarray(case["index"])
+    want = np.asarray(case["re"]) + 1j * np.asarray(case["im"])
+    got = x[idx]
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < tol, (case["source"], err)
+    assert abs(np.linalg.norm(x) / case["norm2"] - 1.0) < tol, case["source"]
+    return err
+
+
+def test_square40_fp64_iterations_and_mixed_solution_match_oracle(th):
+    w = synth.workload("square40_q4_n100")
+    P = twogrid.Problem(w["n"], w["p"], w["k"], w["eps"], alpha_s=w["alpha_s"])
+    TG = twogrid.TwoGrid(P, l_dd=w["l_dd"])
+    f = w["f"]
+    xo, it, rr, _ = krylov.fgmres(lambda v: P.A @ v, TG.precondition, f, tol=1e-8, restart=60)
+    assert rr <= 1e-8
+    S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=w["alpha_s"], l_dd=w["l_dd"], prec="bf16",
+                         extra_prec=("fp64",), restart=60, maxit=300, tol=1e-8, device=DEV)
+    S.set_precision("fp64")
+    x64, info64 = S.solve(dev(f))
+    assert info64["iters"] == it
+    assert info64["relres_max"] <= 1e-8
+    x64 = x64.cpu().numpy()
+    assert rel2(x64, xo) < 1e-7
+    assert np.linalg.norm(f - P.A @ x64) / np.linalg.norm(f) <= 1.01e-8
+    S.set_precision("bf16")
+    xm, infom = S.solve(dev(f))
+    S.device_status()
+    assert infom["relres_max"] <= 1e-8
+    assert infom["iters"] <= it + 2
+    xm = xm.cpu().numpy()
+    # the true residual with the oracle's own matrix, and the distance to its solution
+    assert np.linalg.norm(f - P.A @ xm) / np.linalg.norm(f) <= 1.01e-8
+    assert rel2(xm, xo) < 1e-6
+    S.close()
+
+
+def test_square80_batched_sources_match_oracle(th):
+    """Eight sources of the 801^2 workload in one batched solve: the subdomain
+    products on the tensor cores (BF16 rows and residuals, FP32 accumulation),
+    the coarse solve on tiles of right-hand sides, FP64 FGMRES."""
+    w = synth.workload("square80_q4_n200")
+    nr = 8
+    S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=w["alpha_s"], l_dd=w["l_dd"], prec="bf16",
+                         restart=30, maxit=300, tol=1e-8, nrhs_max=nr, device=DEV)
+    assert S.get_variant("dd_batch", "fp32") == 1
+    F = np.ascontiguousarray(w["f"][:nr])
+    X, info = S.solve(dev(F))
+    S.device_status()
+    assert info["converged"] == nr and info["relres_max"] <= 1e-8
+    X = X.cpu().numpy()
+    cases = golden_cases("square80_q4_n200")
+    assert len(cases) >= 2
+    for c in cases:
+        check_against_samples(X[c["source"]], c, 1e-6)
+    S.close()
+
+
+def test_cube10_sources_match_oracle(th):
+    """The 81^3 Q2 cube with its 8 sources, BF16 rows on the tensor cores (tiles
+    of 16 sources), the fitted 27-point coarse level, FP64 FGMRES."""
+    w = synth.workload("cube10_q2_n40")
+    F = np.ascontiguousarray(w["f"].reshape(-1, (w["n"] * w["p"] + 1) ** 3))
+    nr = F.shape[0]
+    S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=w["alpha_s"], l_dd=w["l_dd"], prec="bf16",
+                         restart=30, maxit=300, nrhs_max=nr, device=DEV, dim=3)
+    X, info = S.solve(dev(F))
+    S.device_status()
+    assert info["converged"] == nr and info["relres_max"] <= 1e-8
+    X = X.cpu().numpy()
+    cases = golden_cases("cube10_q2_n40")
+    assert len(cases) >= 1
+    for c in cases:
+        check_against_samples(X[c["source"]], c, 1e-6)
+    S.close()

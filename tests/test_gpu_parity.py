@@ -323,6 +323,25 @@ def test_batched_tensor_core_smoother(th, nrhs):
     assert np.array_equal(tc, tc2)
 
 
+@pytest.mark.parametrize("c", [CASES[1], CASES[0]])
+def test_tensor_core_smoother_64rhs_against_oracle(th, c):
+    """64 right-hand sides (two full 32-wide tiles of the tcgen05 kernel) against
+    the oracle's Algorithm 2 (SuperLU subdomain solves) directly, per
+    right-hand side, at the BF16 tolerance of the smoother tests: rows and
+    residuals rounded to BF16 (2^-9 relative each), FP32 accumulation."""
+    nrhs = 64
+    S, P = build(th, c, nrhs=nrhs, prec="bf16")
+    assert S.get_variant("dd_batch", "fp32") == 1
+    sm = dd.DDSmoother(P, c["l_dd"])
+    f = synth.random_complex((nrhs, P.N), 52)
+    u = synth.random_complex((nrhs, P.N), 53)
+    got = host(S.smooth(dev(f), dev(u.copy()))) - u
+    S.device_status()
+    want = np.stack([sm.smooth(u[i], f[i], 1) for i in range(nrhs)]) - u
+    for i in range(nrhs):
+        assert relerr(got[i], want[i]) < 3e-2, i
+
+
 def test_batched_tensor_core_solve(th):
     w = synth.workload("square10_q4_n25")
     nrhs = 16

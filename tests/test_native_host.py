@@ -164,3 +164,22 @@ def test_galerkin_setup_matches_oracle(th, n, p, bc, alpha_c):
     import scipy.sparse.linalg as spla
     want = spla.spsolve(P.Aq.tocsc(), b)
     assert np.abs(x - want).max() <= 1e-9 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("n,P", [(25, 3), (13, 4)])
+def test_reduced_separator_inverse_is_block_of_coarse_inverse(th, n, P):
+    """The explicit inverse of the reduced separator system (the Schur complement
+    of A_q on the separator rows) equals the separator block of A_q^{-1}, here
+    the oracle's A_q inverted densely.  mc = 51 and 27 coarse rows: not multiples
+    of the 16-column tasks the set-up computes the inverse in, with K = 2 and 3
+    separator blocks."""
+    p = 4
+    k, eps = small_case(n=n, p=p, W=n / 5.0)
+    sep, Sinv = th.host_coarse_separators(n, p, k, eps, P=P)
+    mc = n * p // 2 + 1
+    assert len(sep) == P - 1 and np.all(np.diff(sep) > 1) and sep[0] > 0 and sep[-1] < mc - 1
+    Aq = qsfem.assemble_coarse(n, p, k, eps, fem.robin_set(2, "robin")).toarray()
+    Ainv = np.linalg.inv(Aq)
+    idx = np.concatenate([np.arange(s * mc, (s + 1) * mc) for s in sep])
+    want = Ainv[np.ix_(idx, idx)]
+    assert np.abs(Sinv - want).max() < 1e-10 * np.abs(want).max()

@@ -72,3 +72,23 @@ def test_noalloc_rejects_requests_beyond_the_array(th):
     assert fn(big._ctx, ctypes.c_void_p(rc1.data_ptr()), ctypes.c_void_p(out.data_ptr()), 1, stream) == 0
     torch.cuda.synchronize()
     assert relerr(out.cpu().numpy(), big.coarse_solve(rc1).cpu().numpy()) < 1e-12
+
+
+def test_noalloc_refuses_other_coarse_levels(th):
+    """The entry point covers the 2-D dispersion-matched coarse level only: a
+    3-D context and a Galerkin-coarsened context return TH_ERR_UNSUPPORTED (8)
+    and touch neither vector."""
+    fn = th.lib().th_coarse_solve_noalloc
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    n3 = 4
+    k3 = 2 * np.pi * 1.5 / synth.random_velocity(n3, 3, 5)
+    S3 = th.TwoGridSolver(n3, 2, k3, None, alpha_s=0.5, l_dd=2, device="cuda:0", dim=3)
+    k, eps = small_case(n=6, p=4)
+    Sg = th.TwoGridSolver(6, 4, k, eps, alpha_s=0.5, l_dd=2, device="cuda:0", coarse="gal", alpha_c=0.02)
+    for S in (S3, Sg):
+        rc = torch.from_numpy(synth.random_complex((1, S.Nc), 9)).to("cuda:0")
+        out = torch.full_like(rc, 3.0)
+        st = fn(S._ctx, ctypes.c_void_p(rc.data_ptr()), ctypes.c_void_p(out.data_ptr()), 1, stream)
+        assert st == 8, th.lib().th_status_str(st)
+        torch.cuda.synchronize()
+        assert torch.all(out == 3.0)
