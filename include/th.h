@@ -147,6 +147,18 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
  * the results of that launch are invalid. */
 th_status th_device_status(th_ctx* ctx, void* stream);
 
+/* Limit of every bounded device-side wait of the context's kernels (the
+ * mbarrier waits of the streamed and tensor-core subdomain products, the
+ * coarse chunk sweep's row exchange and the learned corrector's convolutions),
+ * in polls of the barrier: polls < 0 restores each kernel's default (about a
+ * second); polls > 0 sets that many; polls = 0 makes each such kernel record
+ * a timeout (reported by th_device_status as TH_ERR_TIMEOUT) and return before
+ * its first barrier, bulk copy or MMA, leaving its outputs unwritten.  The
+ * last form exists to exercise the error path without stalling a GPU.  A
+ * kernel that gives up still waits, with the default limit, for its own
+ * copies and MMAs in flight before it returns.  Synchronous on `stream`. */
+th_status th_set_wait_limit(th_ctx* ctx, long long polls, void* stream);
+
 /* Selects the active cycle precision (must have been prepared at set-up). */
 th_status th_set_precision(th_ctx* ctx, int prec);
 

@@ -102,6 +102,7 @@ def lib() -> ctypes.CDLL:
         "th_solve": ([P, P, P, I, ctypes.POINTER(SolveInfo), P], I),
         "th_solve_host": ([P, P, P, I, ctypes.POINTER(SolveInfo), P], I),
         "th_launch_count": ([P, ctypes.POINTER(ctypes.c_longlong)], I),
+        "th_set_wait_limit": ([P, ctypes.c_longlong, P], I),
         "th_profile": ([P, I], I),
         "th_profile_read": ([P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)], I),
         "th_host_reference_1d": ([I, P, P, P], I),
@@ -365,6 +366,11 @@ class TwoGridSolver:
     def device_status(self):
         """Raises ThError(TH_ERR_TIMEOUT) if a bounded device wait gave up since the last check."""
         _check(lib().th_device_status(self._ctx, self._stream()), "th_device_status")
+
+    def set_wait_limit(self, polls=-1):
+        """Polls of every bounded device wait: -1 the kernels' defaults, 0 none
+        (each such kernel reports a timeout and returns at once), > 0 that many."""
+        _check(lib().th_set_wait_limit(self._ctx, int(polls), self._stream()), "th_set_wait_limit")
 
     def launch_count(self) -> int:
         v = ctypes.c_longlong(0)

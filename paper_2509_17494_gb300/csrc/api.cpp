@@ -1461,6 +1461,16 @@ th_status th_device_status(th_ctx* x, void* stream) {
   return TH_ERR_TIMEOUT;
 }
 
+th_status th_set_wait_limit(th_ctx* x, long long polls, void* stream) {
+  if (!x) return TH_ERR_ARG;
+  // status word 63 (see ptx.cuh): 0 = each kernel's default, > 0 = polls, < 0 = none
+  const int word = polls < 0 ? 0 : (polls == 0 ? -1 : (int)std::min<long long>(polls, 1LL << 30));
+  cudaStream_t s = S(stream);
+  TH_CU(cudaMemcpyAsync(x->derr + 63, &word, sizeof(int), cudaMemcpyHostToDevice, s));
+  TH_CU(cudaStreamSynchronize(s));
+  return TH_OK;
+}
+
 th_status th_set_precision(th_ctx* x, int prec) {
   if (!x || prec < 0 || prec > 3) return TH_ERR_ARG;
   if (!has_prec(x->avail, prec)) return TH_ERR_UNSUPPORTED;

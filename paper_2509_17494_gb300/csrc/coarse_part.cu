@@ -26,6 +26,7 @@
 #include <cooperative_groups.h>
 
 #include "kernels.h"
+#include "ptx.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -352,21 +353,6 @@ __device__ __forceinline__ void st_async_c(unsigned raddr, double2 v, unsigned r
   asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];\n"
                ::"r"(raddr), "d"(v.x), "d"(v.y), "r"(rbar) : "memory");
 }
-__device__ __forceinline__ void cmbar_init(uint64_t* b, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void cmbar_expect(uint64_t* b, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool cmbar_try(uint64_t* b, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
-  return ok != 0;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(1024, 1) k_chunk_sweep2(const CoarsePartArgs<T> a, int* err) {
   using C = typename Cx<T>::t;
@@ -430,13 +416,18 @@ __global__ void __launch_bounds__(1024, 1) k_chunk_sweep2(const CoarsePartArgs<T
   };
   // rows are sent at steps 0 .. nsteps - 2 (the last step's rows stay local)
   const int nsend = nsteps - 1;
+  const int lim = ptx::wait_limit(err, 1 << 20);
+  if (lim == 0) {  // waits disabled (the same for every CTA of the cluster): no barrier, copy or store
+    if (tid == 0 && crank == 0) atomicExch(err, 1);
+    return;
+  }
   if (tid == 0) {
     failed = 0;
-    cmbar_init(fbar + 0, 1);
-    cmbar_init(fbar + 1, 1);
+    ptx::mbar_init(fbar + 0, 1);
+    ptx::mbar_init(fbar + 1, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    if (nsend > 0) cmbar_expect(fbar + 0, slot_bytes);
-    if (nsend > 1) cmbar_expect(fbar + 1, slot_bytes);
+    if (nsend > 0) ptx::mbar_arrive_expect_tx(fbar + 0, slot_bytes);
+    if (nsend > 1) ptx::mbar_arrive_expect_tx(fbar + 1, slot_bytes);
   }
   // every barrier is initialised before any CTA of the cluster can send to it
   cluster_arrive_release();
@@ -451,7 +442,7 @@ __global__ void __launch_bounds__(1024, 1) k_chunk_sweep2(const CoarsePartArgs<T
       const unsigned par = (unsigned)(((q - 1) >> 1) & 1);
       if (!failed) {
         bool ok = false;
-        for (int it = 0; it < (1 << 20) && !ok; ++it) ok = cmbar_try(bar, par);
+        for (int it = 0; it < lim && !ok; ++it) ok = ptx::mbar_try_wait_cluster(bar, par);
         if (!ok) failed = 1;
       }
     }
@@ -476,7 +467,7 @@ __global__ void __launch_bounds__(1024, 1) k_chunk_sweep2(const CoarsePartArgs<T
     }
     __syncthreads();  // tvs and the G rows are visible; every thread is past its wait
     // the slot just consumed takes the rows of step q + 1
-    if (tid == 0 && q > 0 && q + 1 <= nsend - 1 && !failed) cmbar_expect(fbar + ((q - 1) & 1), slot_bytes);
+    if (tid == 0 && q > 0 && q + 1 <= nsend - 1 && !failed) ptx::mbar_arrive_expect_tx(fbar + ((q - 1) & 1), slot_bytes);
     // step q + 2's copies: G into buffer (q + 2) % 3 (last read at step q - 1)
     prefetch(q + 2);
     const int rr = warp;

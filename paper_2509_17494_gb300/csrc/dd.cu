@@ -22,6 +22,7 @@
 #include <algorithm>
 
 #include "kernels.h"
+#include "ptx.cuh"
 
 namespace th {
 
@@ -282,39 +283,9 @@ template cudaError_t launch_dd_combine<float>(const CombineArgs<float>&, int, cu
 // drains its copies in flight (again bounded) and returns.
 namespace {
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx_arrive(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-// A waiting thread may be suspended for up to 10 us per call (it resumes when
-// the phase completes), so waiting warps do not spin on the issue slots.
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 10000;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-// bounded wait: false after the iteration limit
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (int it = 0; it < (1 << 17); ++it)  // at most about 1.3 s
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return ptx::smem_addr(p); }
+using ptx::bulk_g2s;
+using ptx::mbar_init;
 template <typename C>
 __device__ __forceinline__ void cp_async_c(C* smem, const C* gmem) {
   if constexpr (sizeof(C) == 16) {
@@ -324,9 +295,6 @@ __device__ __forceinline__ void cp_async_c(C* smem, const C* gmem) {
   }
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"((unsigned)__cvta_generic_to_shared(bar)) : "memory");
-}
 __device__ __forceinline__ void named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -361,6 +329,11 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
   const int NS = (NCH + cps - 1) / cps;
   const int nmine = (a.nsub - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const int total = nmine * NS;
+  const int lim = ptx::wait_limit(err, 1 << 17);  // about 1.3 s of suspending polls
+  if (lim == 0) {  // waits disabled: record a timeout before any barrier or copy
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
+  }
 
   int issued_hi = 0;         // thread 0: one past the last item issued
   auto issue = [&](int t) {  // thread 0 only
@@ -373,7 +346,7 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
     const unsigned bytes = (unsigned)((size_t)nch * NR * 16);
     const char* src = reinterpret_cast<const char*>(a.W) + ((size_t)sub * NCH + ch0) * NR * 16;
     uint64_t* bar = bars + (t % depth);
-    mbar_expect_tx_arrive(bar, bytes);
+    ptx::mbar_arrive_expect_tx(bar, bytes);
     bulk_g2s(slots + (size_t)(t % depth) * slot_bytes, src, bytes, bar);
   };
   // box-relative offsets and coordinates of the gathered columns (the same for
@@ -459,7 +432,7 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
 #pragma unroll
       for (int h = 0; h < PS; ++h) pR[h][k] = pN[h][k] = pI[h][k] = make_float2(0.f, 0.f);
     for (int s = 0; s < NS; ++s, ++t) {
-      if (!failed && !mbar_wait_bounded(bars + (t % depth), (unsigned)((t / depth) & 1))) failed = 1;
+      if (!failed && !ptx::mbar_wait_suspend(bars + (t % depth), (unsigned)((t / depth) & 1), lim)) failed = 1;
       const int ch0 = s * cps, nch = min(cps, NCH - ch0);
       const unsigned char* slot = slots + (size_t)(t % depth) * slot_bytes;
       if (g < G) {
@@ -567,7 +540,7 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
     // no item is issued before the one `depth` places earlier was consumed
     atomicExch(err, 1);
     for (int u = max(0, issued_hi - depth); u < issued_hi; ++u)
-      mbar_wait_bounded(bars + (u % depth), (unsigned)((u / depth) & 1));
+      ptx::mbar_wait_suspend(bars + (u % depth), (unsigned)((u / depth) & 1), ptx::kDrainPolls);
   }
   __syncthreads();
 }
@@ -602,6 +575,11 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream2(const DDArgs<T> a, int cp
   const int NS = (NCH + cps - 1) / cps;
   const int nmine = (a.nsub - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const int total = nmine * NS;
+  const int lim = ptx::wait_limit(err, 1 << 17);  // about 1.3 s of suspending polls
+  if (lim == 0) {  // waits disabled: record a timeout before any barrier or copy
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
+  }
   __shared__ volatile int failed;
   __shared__ int issued_hi;
   if (tid == 0) {
@@ -617,7 +595,7 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream2(const DDArgs<T> a, int cp
   if (producer) {
     if (lane == 0) {
       for (int t = 0; t < total; ++t) {
-        if (t >= depth && !mbar_wait_bounded(empty + (t % depth), (unsigned)(((t / depth) - 1) & 1))) failed = 1;
+        if (t >= depth && !ptx::mbar_wait_suspend(empty + (t % depth), (unsigned)(((t / depth) - 1) & 1), lim)) failed = 1;
         if (failed) break;
         const int sub = blockIdx.x + (t / NS) * gridDim.x;
         const int s = t % NS;
@@ -625,7 +603,7 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream2(const DDArgs<T> a, int cp
         const int nch = min(cps, NCH - ch0);
         const unsigned bytes = (unsigned)((size_t)nch * NR * 16);
         const char* src = reinterpret_cast<const char*>(a.W) + ((size_t)sub * NCH + ch0) * NR * 16;
-        mbar_expect_tx_arrive(full + (t % depth), bytes);
+        ptx::mbar_arrive_expect_tx(full + (t % depth), bytes);
         bulk_g2s(slots + (size_t)(t % depth) * slot_bytes, src, bytes, full + (t % depth));
         issued_hi = t + 1;
       }
@@ -667,7 +645,7 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream2(const DDArgs<T> a, int cp
 #pragma unroll
       for (int k = 0; k < NRHS; ++k) { acr[k] = 0; aci[k] = 0; }
       for (int s = 0; s < NS; ++s, ++t) {
-        if (!failed && !mbar_wait_bounded(full + (t % depth), (unsigned)((t / depth) & 1))) failed = 1;
+        if (!failed && !ptx::mbar_wait_suspend(full + (t % depth), (unsigned)((t / depth) & 1), lim)) failed = 1;
         const int ch0 = s * cps, nch = min(cps, NCH - ch0);
         const unsigned char* slot = slots + (size_t)(t % depth) * slot_bytes;
         if (g < G && !failed) {
@@ -689,7 +667,7 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream2(const DDArgs<T> a, int cp
           }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive1(empty + (t % depth));
+        if (lane == 0) ptx::mbar_arrive(empty + (t % depth));
       }
       const int sub = blockIdx.x + i * gridDim.x;
       if (g < G) {
@@ -726,7 +704,7 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream2(const DDArgs<T> a, int cp
     // record, then wait (bounded) for the copies that can still be in flight
     atomicExch(err, 1);
     for (int u = max(0, issued_hi - depth); u < issued_hi; ++u)
-      mbar_wait_bounded(full + (u % depth), (unsigned)((u / depth) & 1));
+      ptx::mbar_wait_suspend(full + (u % depth), (unsigned)((u / depth) & 1), ptx::kDrainPolls);
   }
   __syncthreads();
 }

@@ -33,6 +33,7 @@
 #include <cstdint>
 
 #include "kernels.h"
+#include "ptx.cuh"
 
 namespace th {
 namespace {
@@ -42,68 +43,13 @@ constexpr int kDepth = 4;    // W chunk slots
 constexpr int kSlotBytes = 2 * 16 * kKC * 128;  // re + im, 128 rows, 64 columns
 constexpr int kThreads = 512;
 
-__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t umma_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version
-  return d;                // no swizzle, base offset 0
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity) {
-  unsigned ok;
-  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-               : "=r"(ok)
-               : "r"(su32(b)), "r"(parity)
-               : "memory");
-  return ok != 0;
-}
-// bounded wait; false when the limit is reached or the CTA already failed
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* failed) {
-  for (int it = 0; it < (1 << 20); ++it) {
-    if (mbar_try(b, parity)) return true;
-    if ((it & 255) == 255 && *failed) return false;
-  }
-  *failed = 1;
-  return false;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   su32(dst)),
-               "l"(src), "r"(bytes), "r"(su32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void umma_bf16(unsigned d_tmem, uint64_t a, uint64_t b, unsigned idesc, unsigned acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(unsigned addr, unsigned* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
+__device__ __forceinline__ unsigned su32(const void* p) { return ptx::smem_addr(p); }
+using ptx::mbar_arrive;
+using ptx::mbar_init;
+using ptx::tmem_ld16;
+using ptx::umma_bf16;
+using ptx::umma_commit;
+using ptx::umma_desc;
 
 }  // namespace
 
@@ -137,6 +83,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dd_umma(const DDUmmaArgs a) {
   const bool producer = (warp >= 1 && warp <= 3) || warp >= 8;
   const int nprod = 11 * 32;
   const int pidx = (warp <= 3) ? tid - 32 : tid - 32 - 128;  // 0..351 among producers
+  const int lim = ptx::wait_limit(a.err, 1 << 20);
+  if (lim == 0) {  // waits disabled: record a timeout before any barrier, copy or MMA
+    if (tid == 0) atomicExch(a.err, 1);
+    return;
+  }
 
   if (tid == 0) {
     failed = 0;
@@ -174,12 +125,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_dd_umma(const DDUmmaArgs a) {
         const int kcs = min(kKC, K8 - kc * kKC);
         const unsigned part = (unsigned)(M8 * kcs * 128);
         const int slot = t % kDepth, use = t / kDepth;
-        if (!mbar_wait(wempty + slot, (unsigned)((use & 1) ^ 1), &failed)) return;
-        mbar_expect_tx(wfull + slot, 2 * part);
+        if (!ptx::mbar_wait_shared_flag(wempty + slot, (unsigned)((use & 1) ^ 1), &failed, lim)) return;
+        ptx::mbar_arrive_expect_tx(wfull + slot, 2 * part);
         const unsigned char* src = a.W + (size_t)sub * sub_bytes + (size_t)kc * kKC * 2 * M8 * 128;
         unsigned char* dst = wslot + (size_t)slot * kSlotBytes;
-        bulk_g2s(dst, src, part, wfull + slot);                          // real part
-        bulk_g2s(dst + kSlotBytes / 2, src + part, part, wfull + slot);  // imaginary part
+        ptx::bulk_g2s(dst, src, part, wfull + slot);                          // real part
+        ptx::bulk_g2s(dst + kSlotBytes / 2, src + part, part, wfull + slot);  // imaginary part
         issued = t + 1;
       };
       // instruction descriptors: D f32, A/B bf16, K-major, N = kNB, M = 128
@@ -189,14 +140,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_dd_umma(const DDUmmaArgs a) {
       int t = 0;
       for (int i = 0; i < nmine && !failed; ++i) {
         const int xb = i & 1, ux = i >> 1, ab = i & 1;
-        if (!mbar_wait(xfull + xb, (unsigned)(ux & 1), &failed)) break;
-        if (!mbar_wait(aempty + ab, (unsigned)((ux & 1) ^ 1), &failed)) break;
+        if (!ptx::mbar_wait_shared_flag(xfull + xb, (unsigned)(ux & 1), &failed, lim)) break;
+        if (!ptx::mbar_wait_shared_flag(aempty + ab, (unsigned)((ux & 1) ^ 1), &failed, lim)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const unsigned d_re = tmem + (unsigned)(ab * 2 * kNB), d_im = d_re + kNB;
         const unsigned xre = su32(xbuf + (size_t)xb * xbuf_bytes), xim = xre + (unsigned)(xbuf_bytes / 2);
         for (int kc = 0; kc < NKC; ++kc, ++t) {
           const int slot = t % kDepth, use = t / kDepth;
-          if (!mbar_wait(wfull + slot, (unsigned)(use & 1), &failed)) break;
+          if (!ptx::mbar_wait_shared_flag(wfull + slot, (unsigned)(use & 1), &failed, lim)) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const int kcs = min(kKC, K8 - kc * kKC);
           const unsigned wre = su32(wslot + (size_t)slot * kSlotBytes), wim = wre + kSlotBytes / 2;
@@ -222,9 +173,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dd_umma(const DDUmmaArgs a) {
       // every MMA issued above completes before tensor memory is released
       umma_commit(done);
       volatile int ignore = 0;
-      mbar_wait(done, 0u, &ignore);
+      ptx::mbar_wait_shared_flag(done, 0u, &ignore, ptx::kDrainPolls);
       // bulk copies issued but not consumed (only after a failure)
-      for (int u = t; u < issued; ++u) mbar_wait(wfull + (u % kDepth), (unsigned)((u / kDepth) & 1), &ignore);
+      for (int u = t; u < issued; ++u) ptx::mbar_wait_shared_flag(wfull + (u % kDepth), (unsigned)((u / kDepth) & 1), &ignore, ptx::kDrainPolls);
     }
   } else if (warp >= 4 && warp <= 7) {
     // ------------------------------------------------ epilogue: TMEM -> V
@@ -233,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dd_umma(const DDUmmaArgs a) {
     for (int i = 0; i < nmine; ++i) {
       const int ab = i & 1, ua = i >> 1;
       const int sub = blockIdx.x + i * gridDim.x;
-      if (!failed) mbar_wait(afull + ab, (unsigned)(ua & 1), &failed);
+      if (!failed) ptx::mbar_wait_shared_flag(afull + ab, (unsigned)(ua & 1), &failed, lim);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const unsigned base = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(ab * 2 * kNB);
       for (int c0 = 0; c0 < kNB; c0 += 16) {
@@ -258,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dd_umma(const DDUmmaArgs a) {
     for (int i = 0; i < nmine; ++i) {
       const int xb = i & 1, ux = i >> 1;
       const int sub = blockIdx.x + i * gridDim.x;
-      if (!failed) mbar_wait(xempty + xb, (unsigned)((ux & 1) ^ 1), &failed);
+      if (!failed) ptx::mbar_wait_shared_flag(xempty + xb, (unsigned)((ux & 1) ^ 1), &failed, lim);
       const int* bb = a.box + (size_t)sub * 12;
       const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3], oz = D3 ? bb[8] : 0, wz = D3 ? bb[9] : 1;
       const int L2 = a.Lw * a.Lw;

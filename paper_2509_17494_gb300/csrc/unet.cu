@@ -26,6 +26,7 @@
 
 #include <cstdint>
 
+#include "ptx.cuh"
 #include "unet.h"
 
 namespace th {
@@ -36,65 +37,13 @@ constexpr int kStages = 4;
 constexpr int kConvThreads = 384;
 constexpr int kProducers = 7 * 32;  // warps 1-3 and 8-11
 
-__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ uint64_t umma_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity) {
-  unsigned ok;
-  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-               : "=r"(ok)
-               : "r"(su32(b)), "r"(parity)
-               : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* failed) {
-  for (int it = 0; it < (1 << 20); ++it) {
-    if (mbar_try(b, parity)) return true;
-    if ((it & 255) == 255 && *failed) return false;
-  }
-  *failed = 1;
-  return false;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   su32(dst)),
-               "l"(src), "r"(bytes), "r"(su32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void umma_bf16(unsigned d_tmem, uint64_t a, uint64_t b, unsigned idesc, unsigned acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(unsigned addr, unsigned* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
+__device__ __forceinline__ unsigned su32(const void* p) { return ptx::smem_addr(p); }
+using ptx::mbar_arrive;
+using ptx::mbar_init;
+using ptx::tmem_ld16;
+using ptx::umma_bf16;
+using ptx::umma_commit;
+using ptx::umma_desc;
 __device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
 __device__ __forceinline__ float dsilu_f(float z) {
   const float s = 1.0f / (1.0f + __expf(-z));
@@ -119,6 +68,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_umma(const ConvArgs a)
   const long long p0 = (long long)blockIdx.x * 128;
   const unsigned ncols = cout <= 32 ? 32u : (cout <= 64 ? 64u : (cout <= 128 ? 128u : 256u));
   const int nchunk = a.nchunk;
+  const int lim = ptx::wait_limit(a.err, 1 << 20);
+  if (lim == 0) {  // waits disabled: record a timeout before any barrier, copy or MMA
+    if (tid == 0) atomicExch(a.err, 1);
+    return;
+  }
 
   if (tid == 0) {
     failed = 0;
@@ -147,9 +101,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_umma(const ConvArgs a)
       auto issue = [&](int t) {
         if (t >= nchunk || failed) return;
         const int s = t % kStages, use = t / kStages;
-        if (!mbar_wait(empty + s, (unsigned)((use & 1) ^ 1), &failed)) return;
-        mbar_expect_tx(full + s, b_bytes);
-        bulk_g2s(bbuf + (size_t)s * b_bytes, a.w + (size_t)t * b_bytes, b_bytes, full + s);
+        if (!ptx::mbar_wait_shared_flag(empty + s, (unsigned)((use & 1) ^ 1), &failed, lim)) return;
+        ptx::mbar_arrive_expect_tx(full + s, b_bytes);
+        ptx::bulk_g2s(bbuf + (size_t)s * b_bytes, a.w + (size_t)t * b_bytes, b_bytes, full + s);
         issued = t + 1;
       };
       // D f32, A/B bf16, both K-major, N = cout, M = 128
@@ -158,7 +112,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_umma(const ConvArgs a)
       int t = 0;
       for (; t < nchunk && !failed; ++t) {
         const int s = t % kStages, use = t / kStages;
-        if (!mbar_wait(full + s, (unsigned)(use & 1), &failed)) break;
+        if (!ptx::mbar_wait_shared_flag(full + s, (unsigned)(use & 1), &failed, lim)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const unsigned as = su32(abuf + (size_t)s * a_bytes), bs = su32(bbuf + (size_t)s * b_bytes);
         for (int j = 0; j < kUnits / 2; ++j) {
@@ -171,14 +125,14 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_umma(const ConvArgs a)
       }
       umma_commit(done);
       volatile int ignore = 0;
-      mbar_wait(done, 0u, &ignore);
-      for (int u = t; u < issued; ++u) mbar_wait(full + (u % kStages), (unsigned)((u / kStages) & 1), &ignore);
+      ptx::mbar_wait_shared_flag(done, 0u, &ignore, ptx::kDrainPolls);
+      for (int u = t; u < issued; ++u) ptx::mbar_wait_shared_flag(full + (u % kStages), (unsigned)((u / kStages) & 1), &ignore, ptx::kDrainPolls);
     }
   } else if (warp >= 4 && warp <= 7) {
     // ------------------------------------------------ epilogue
     const int q = warp - 4;
     const long long p = p0 + q * 32 + lane;
-    if (!failed) mbar_wait(done, 0u, &failed);
+    if (!failed) ptx::mbar_wait_shared_flag(done, 0u, &failed, lim);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     for (int c0 = 0; c0 < cout; c0 += 16) {
       unsigned r[16];
@@ -213,7 +167,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_umma(const ConvArgs a)
     const int C8 = a.C8, U = 9 * C8;
     for (int t = 0; t < nchunk; ++t) {
       const int s = t % kStages, use = t / kStages;
-      if (!failed) mbar_wait(empty + s, (unsigned)((use & 1) ^ 1), &failed);
+      if (!failed) ptx::mbar_wait_shared_flag(empty + s, (unsigned)((use & 1) ^ 1), &failed, lim);
       unsigned char* dst = abuf + (size_t)s * a_bytes;
       for (int idx = pidx; idx < 128 * kUnits; idx += kProducers) {
         const int row = idx / kUnits, uu = idx - row * kUnits;
