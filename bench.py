@@ -32,16 +32,38 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+# the CPU oracle legs state their core counts: no hidden BLAS threads
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
 
 METRIC = "fine-level two-grid cycle GDOF/s and time-to-1e-8 residual vs plain FP64 form"
 WORKLOAD = "square40_q4_n100"
 HBM_FALLBACK_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP32-cycle
-# subdomain kernel (BF16 rows, 1 rhs) on this workload, by kernel variant: the
-# mean over ncu captures of three (variant 1, CTA-barrier ring) and five
-# (variant 2, producer warp) launches of this script's timed region; None for a
-# variant without a current capture.
-DD_TRAFFIC_BYTES = {0: None, 1: 239.9e6, 2: 239.5e6, 3: None, 4: None, 5: None}
+# subdomain kernel (BF16 rows, 1 rhs) on this workload, by kernel variant, from
+# an ncu capture of this script's timed region (the profile summary named), with
+# the digest of the kernel sources at the time of that capture: the figure is
+# reported only while the sources are unchanged, else null.
+DD_TRAFFIC = {}
+DD_SOURCES = ("paper_2509_17494_gb300/csrc/dd.cu", "paper_2509_17494_gb300/csrc/ptx.cuh",
+              "paper_2509_17494_gb300/csrc/kernels.h")
+
+
+def dd_sources_digest():
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in DD_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dd_traffic(variant):
+    rec = DD_TRAFFIC.get(variant)
+    if not rec or rec["sources"] != dd_sources_digest():
+        return None
+    return rec["bytes"]
 
 
 def parse():
@@ -227,6 +249,9 @@ def run_native(args):
     N = S.N
     f = torch.from_numpy(np.ascontiguousarray(w["f"] if w["f"].ndim == 1 else w["f"][0])).to(dev)
     stream = torch.cuda.current_stream(dev)
+    # FP64 and FP32 pipe rates of this GPU (FMA chains, CUDA events): the
+    # denominators of the FP64 form's roofline
+    pipe = {pr: th.peak_fma(pr, stream=stream.cuda_stream) / 1e12 for pr in ("fp64", "fp32")}
 
     def timed_cycles(prec, steps, warmup, profile=False, clocks=None, graph=True):
         S.set_precision(prec)
@@ -315,7 +340,8 @@ def run_native(args):
     achieved = alg_bytes / (dd_avg_ms * 1e-3) / 1e9
     roofline = {"kernel": f"{dd_kernel}, BF16 inverse rows, 1 rhs", "bound": "hbm", "achieved": round(achieved, 1),
                 "peak": hbm, "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": DD_TRAFFIC_BYTES.get(S.get_variant("dd", "fp32")), "alg_bytes_per_launch": int(alg_bytes),
+                "traffic": dd_traffic(S.get_variant("dd", "fp32")), "alg_bytes_per_launch": int(alg_bytes),
+                "traffic_source": (DD_TRAFFIC.get(S.get_variant("dd", "fp32")) or {}).get("profile"),
                 "avg_launch_ms": round(dd_avg_ms, 5),
                 "dominant_by_time": dominant,
                 "profiled_ms_per_step": round(ms_prof, 4),
@@ -324,6 +350,18 @@ def run_native(args):
                              "dd_fp64": S.get_variant("dd", "fp64"), "fine_fp64": S.get_variant("fine", "fp64"),
                              "coarse_sweep": S.get_variant("coarse", "fp32"),
                              "outer_residual": "double-single" if S.get_variant("resid", "fp32") else "fp64"}}
+
+    # the FP64 form's subdomain products: 8 flop per complex row entry, FP64-pipe bound
+    _, w_entries = dd_algorithmic_bytes(n, p, w["l_dd"], 16, 16)
+    dd64_ms, dd64_cnt = prof64["dd"]
+    dd64_avg = dd64_ms / max(dd64_cnt, 1)
+    dd64_tf = 8.0 * w_entries / (dd64_avg * 1e-3) / 1e12
+    roofline64 = {"kernel": {0: "k_dd_apply", 1: "k_dd_stream", 2: "k_dd_stream2"}.get(S.get_variant("dd", "fp64"),
+                                                                                      "k_dd_stream"),
+                  "bound": "fp64", "achieved": round(dd64_tf, 3), "peak": round(pipe["fp64"], 3),
+                  "peak_source": "measured here (th_peak_fma: FP64 FMA chains, CUDA events)", "unit": "TFLOP/s",
+                  "frac": round(dd64_tf / pipe["fp64"], 4), "flop_per_launch": int(8 * w_entries),
+                  "avg_launch_ms": round(dd64_avg, 5)}
 
     fine_ms = sum(v[0] for k, v in per_step.items() if k != "coarse_solve")
     line = {
@@ -358,7 +396,9 @@ def run_native(args):
         "fp64": {"value": round(gdofs(ms_fp64), 4), "ms_per_step": round(ms_fp64, 4),
                  "time_to_tol_ms": round(tt_fp64, 3), "iters": info_fp64["iters"],
                  "relres": info_fp64["relres_max"],
-                 "share_of_step": {k: round(v[0] / steps64 / ms_fp64, 3) for k, v in prof64.items() if v[1] > 0}},
+                 "share_of_step": {k: round(v[0] / steps64 / ms_fp64, 3) for k, v in prof64.items() if v[1] > 0},
+                 "dd_roofline": roofline64},
+        "pipe_peaks_tflops": {k: round(v, 3) for k, v in pipe.items()},
         "speedup_vs_fp64": {"cycle": round(ms_fp64 / ms_mixed, 2), "time_to_tol": round(tt_fp64 / tt_mixed, 2)},
         "roofline": roofline,
         "e2e": {"value": round(gdofs(ms_e2e), 4), "unit": "GDOF/s", "ms_per_step": round(ms_e2e, 4),
@@ -890,7 +930,32 @@ def oracle_setup(name):
     return P, TG, f
 
 
+def _oracle_cycles_worker(name, cycles, bar, q):
+    """One process of the all-core oracle sample: its own set-up, then `cycles`
+    oracle cycles started together with every other process (single-threaded)."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    import numpy as np
+
+    try:
+        P, TG, f = oracle_setup(name)
+        u = TG.step(np.zeros_like(f), f)
+        bar.wait(timeout=900)
+        t = time.perf_counter()
+        for _ in range(cycles):
+            u = TG.step(u, f)
+        q.put(time.perf_counter() - t)
+    except Exception as e:  # reported by the parent as a missing sample
+        q.put(repr(e))
+
+
 def cpu_baseline(name, cycles):
+    """The FP64 oracle on the host: `cycles` cycles on one core, then the same
+    number in every one of the host's cores at once (one process per core, each
+    an independent replica of the problem with its own set-up; the processes are
+    started with spawn, so none inherits this process's CUDA state)."""
+    import multiprocessing as mp
+
     import numpy as np
 
     P, TG, f = oracle_setup(name)
@@ -900,10 +965,45 @@ def cpu_baseline(name, cycles):
     for _ in range(cycles):
         u = TG.step(u, f)
     dt = (time.perf_counter() - t) / cycles
-    return {"value": round(P.N / dt / 1e9, 6), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
-            "sample": f"{cycles} TwoGridStep cycles of the FP64 NumPy/SciPy oracle on the full {name} "
-                      f"workload (set-up excluded; SuperLU local solves, CSR applies and the banded coarse "
-                      f"solve are single-threaded), {dt * 1e3:.0f} ms per cycle"}
+    out = {"value": round(P.N / dt / 1e9, 6), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+           "sample": f"{cycles} TwoGridStep cycles of the FP64 NumPy/SciPy oracle on the full {name} "
+                     f"workload (set-up excluded; SuperLU local solves, CSR applies and the banded coarse "
+                     f"solve, one thread), {dt * 1e3:.0f} ms per cycle"}
+    ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    if ncores < 2:
+        return out
+    ctx = mp.get_context("spawn")
+    bar = ctx.Barrier(ncores)
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_cycles_worker, args=(name, cycles, bar, q), daemon=True)
+             for _ in range(ncores - 1)]
+    for pr in procs:
+        pr.start()
+    times = []
+    try:
+        bar.wait(timeout=900)
+        t = time.perf_counter()
+        for _ in range(cycles):
+            u = TG.step(u, f)
+        times.append(time.perf_counter() - t)
+        for _ in procs:
+            times.append(q.get(timeout=900))
+    except Exception as e:
+        times.append(repr(e))
+    for pr in procs:
+        pr.join(timeout=60)
+    ok = [x for x in times if isinstance(x, float)]
+    if len(ok) == ncores:
+        wall = max(ok)
+        out["all_cores"] = {"value": round(ncores * cycles * P.N / wall / 1e9, 6), "unit": "GDOF/s",
+                            "cores": ncores, "kind": "oracle",
+                            "sample": f"{ncores} single-threaded processes (one per host core), each an "
+                                      f"independent replica of the {name} oracle running {cycles} cycles at "
+                                      f"once; slowest process {wall * 1e3 / cycles:.0f} ms per cycle"}
+    else:
+        out["all_cores"] = {"unavailable": f"{len(ok)} of {ncores} processes reported: "
+                                           f"{[x for x in times if not isinstance(x, float)][:1]}"}
+    return out
 
 
 def run_reference(args):

@@ -370,6 +370,16 @@ th_status th_profile(th_ctx* ctx, int enable);
  * class `kind` since th_profile(ctx, 1).  Synchronises on the recorded events. */
 th_status th_profile_read(th_ctx* ctx, int kind, double* ms, long long* launches);
 
+/* Arithmetic peak probe (measurement only; no counterpart in the paper):
+ * the FMA rate of the FP64 (prec = TH_PREC_FP64) or FP32 (TH_PREC_FP32)
+ * pipe of the current device, in flop/s (2 per fused multiply-add), from
+ * 8 blocks of 256 threads per SM each running 8 independent chains of `iters`
+ * dependent FMAs, timed with CUDA events on `stream` after one shorter
+ * warm-up launch.  Synchronous.  The roofline of kernels bound by these pipes
+ * (the FP64 form's subdomain products, the double-single residual) is taken
+ * against this rate.  TH_ERR_ARG for another prec or iters < 1. */
+th_status th_peak_fma(int prec, int iters, double* flops_per_s, void* stream);
+
 /* Kernel variants chosen by the set-up autotuner (which times each candidate
  * on the context's own problem with CUDA events):
  *   TH_K_FINE: 0 = large cell tile, 1 = small cell tile;

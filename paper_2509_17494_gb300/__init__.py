@@ -103,6 +103,7 @@ def lib() -> ctypes.CDLL:
         "th_solve_host": ([P, P, P, I, ctypes.POINTER(SolveInfo), P], I),
         "th_launch_count": ([P, ctypes.POINTER(ctypes.c_longlong)], I),
         "th_set_wait_limit": ([P, ctypes.c_longlong, P], I),
+        "th_peak_fma": ([I, I, ctypes.POINTER(ctypes.c_double), P], I),
         "th_profile": ([P, I], I),
         "th_profile_read": ([P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)], I),
         "th_host_reference_1d": ([I, P, P, P], I),
@@ -246,6 +247,16 @@ def host_galerkin(n, p, k_cell, eps_cell=None, bc="robin", alpha_c=0.0, b=None):
            "th_host_galerkin")
     sten = (st[0::2] + 1j * st[1::2]).reshape(mc * mc, S, S)
     return sten, (xo if b is not None else None)
+
+
+def peak_fma(prec="fp64", iters=None, stream=None):
+    """Measured FMA rate of the FP64 or FP32 pipe of the current device, flop/s."""
+    if iters is None:
+        iters = 4096 if prec == "fp64" else 262144
+    v = ctypes.c_double(0)
+    st = ctypes.c_void_p(stream) if stream is not None else None
+    _check(lib().th_peak_fma(PREC[prec], int(iters), ctypes.byref(v), st), "th_peak_fma")
+    return v.value
 
 
 def host_coarse_separators(n, p, k_cell, eps_cell=None, bc="robin", P=3):
