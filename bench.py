@@ -87,6 +87,8 @@ def parse():
                          "change the autotuner's timings)")
     ap.add_argument("--fine-variant", choices=["auto", "0", "1"], default="auto",
                     help="FP32 and FP64 fine-apply tile variant: auto, 0 (large tiles), 1 (small tiles)")
+    ap.add_argument("--cycle-variant", choices=["auto", "0", "1", "2"], default="auto",
+                    help="launch structure of the cycle (th_set_kernel_variant TH_K_CYCLE)")
     ap.add_argument("--coarse-variant", choices=["auto", "0", "1", "2"], default="auto",
                     help="FP32 one-rhs coarse sweep: auto, 0 two phases, 1 one cluster barrier per step, "
                          "2 st.async row exchange")
@@ -246,6 +248,8 @@ def run_native(args):
         S.set_variant("fine", "fp64", int(args.fine_variant))
     if args.coarse_variant != "auto":
         S.set_variant("coarse", "fp32", int(args.coarse_variant))
+    if args.cycle_variant != "auto":
+        S.set_variant("cycle", "fp32", int(args.cycle_variant))
     N = S.N
     f = torch.from_numpy(np.ascontiguousarray(w["f"] if w["f"].ndim == 1 else w["f"][0])).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -291,6 +295,13 @@ def run_native(args):
     ms_mixed = max_over_ranks(ms_mixed, world, dev)
     # the same steps launched kernel by kernel (no graph), then with per-kernel CUDA events (th_profile)
     ms_nograph, _, _, _, _ = timed_cycles("bf16", args.steps, 2, graph=False)
+    # the same graph-replayed step with each launch structure of the cycle
+    cyc0 = S.get_variant("cycle", "fp32")
+    ms_by_cycle = {}
+    for v in (0, 1, 2):
+        S.set_variant("cycle", "fp32", v)
+        ms_by_cycle[v] = round(max_over_ranks(timed_cycles("bf16", args.steps, 3)[0], world, dev), 4)
+    S.set_variant("cycle", "fp32", cyc0)
     ms_prof, _, prof, _, _ = timed_cycles("bf16", args.steps, 1, profile=True, graph=False)
     steps64 = max(3, args.steps // 2)
     ms_fp64, _, _, _, _ = timed_cycles("fp64", steps64, max(3, args.warmup // 2))
@@ -387,7 +398,10 @@ def run_native(args):
                    "l2": "inputs larger than L2: the BF16 inverse rows streamed every smoother step are "
                          f"{alg_bytes / 1e6:.0f} MB > 129 MB",
                    "setup_s": round(setup_s, 2), "parallelism": f"replicas x{world}"},
-        "cycle_launch": {"graph_ms_per_step": round(ms_mixed, 4), "no_graph_ms_per_step": round(ms_nograph, 4)},
+        "cycle_launch": {"graph_ms_per_step": round(ms_mixed, 4), "no_graph_ms_per_step": round(ms_nograph, 4),
+                         "variant": cyc0,
+                         "graph_ms_by_variant": {"0 step by step": ms_by_cycle[0], "1 fused": ms_by_cycle[1],
+                                                 "2 fused, programmatic dependent launch": ms_by_cycle[2]}},
         "fine_level": {"value": round(gdofs(fine_ms), 4), "unit": "GDOF/s", "ms_per_step": round(fine_ms, 4),
                        "what": "sum of the per-kernel event times of every cycle kernel except the coarse solve"},
         "time_to_tol_ms": round(tt_mixed, 3),

@@ -357,7 +357,8 @@ enum {
   TH_K_KRYLOV = 8,      /* FGMRES dots, norms, updates (K9) */
   TH_K_COUNT = 9,
   TH_K_DD_BATCH = 9,    /* (variants only) batched BF16 subdomain products: 0 CUDA cores, 1 tensor cores */
-  TH_K_RESID = 10       /* (variants only) the mixed form's outer residual, see th_residual_mixed */
+  TH_K_RESID = 10,      /* (variants only) the mixed form's outer residual, see th_residual_mixed */
+  TH_K_CYCLE = 11       /* (variants only) launch structure of the cycle, see th_set_kernel_variant */
 };
 
 /* Per-kernel timing for measurement: with enable = 1 every later kernel
@@ -398,6 +399,17 @@ th_status th_peak_fma(int prec, int iters, double* flops_per_s, void* stream);
  *              are rounded to BF16), 0 keeps them on the CUDA cores;
  *   TH_K_RESID: 1 (default) double-single residual kernel, 0 FP64 apply and
  *              rounding (th_residual_mixed; prec is ignored);
+ *   TH_K_CYCLE: 1 (default) a TwoGridStep with u = 0 on entry (the
+ *              preconditioner, and the mixed form's inner step) of a 2-D
+ *              context with n_s = n_dd = 1 folds the RAS-like average into
+ *              the next fine apply, the prolongation and correction into the
+ *              post-smoother's fine apply, and the last average, the update
+ *              and (mixed form) the widening to FP64 into one kernel: the
+ *              same arithmetic in the same order as 0, the step-by-step
+ *              launches (prec is ignored); 2 = 1 with every launch after the
+ *              first issued with a programmatic dependency on the one before
+ *              (it may be scheduled while that one drains, and waits for it
+ *              before touching shared data; not while th_profile records);
  *   TH_K_COARSE_SOLVE: one-right-hand-side chunk sweep of the 2-D coarse
  *              solve: 0 = two phases per block step (512 threads), 1 = one
  *              cluster barrier per step (1024 threads, m_c <= 256), 2 = rows

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "launch.cuh"
 #include "unet_net.h"
 #include "th_internal.h"
 
@@ -60,6 +61,7 @@ struct th_ctx {
   int dds64 = 0, dds32 = 0;  // DD kernel per precision: 0 k_dd_apply, 1 k_dd_stream (autotuned)
   int dd_tc = 1;             // batched BF16 products on tensor cores (k_dd_umma) when available
   int cs_variant = 1;        // one-rhs coarse chunk sweep: 0 two-phase, 1 one barrier per step (autotuned)
+  int fuse = 1;              // cycle with u = 0 on entry: combine, prolongation and widening fused (TH_K_CYCLE)
   unsigned char* Wu = nullptr;  // BF16 inverse rows in the tcgen05 operand layout (NR <= 128)
   int sms = 152;
   int device = -1;          // CUDA device the context was set up on
@@ -815,12 +817,89 @@ th_status coarse_correct_(th_ctx& x, const typename th::Cx<T>::t* rc, typename t
   return cuda_status(x.unet->correct<typename th::Cx<T>::t>(rc, uc, x.g.Nc, nrhs, s));
 }
 
+// TwoGridStep(0, f) of Algorithm 1 in precision T (2-D, n_s = n_dd = 1) with
+// the vector passes folded into their neighbours, bitwise the same arithmetic
+// as the step-by-step form below:
+//   V = DD(f);  ua = avg V, r = f - A ua   (one fine apply reading V)
+//   r_c = I_P^T r;  u_c = coarse(r_c)
+//   ub = ua + omega_c I_P u_c, r = f - A ub   (one fine apply reading u_c)
+//   V = DD(r);  out = ub + avg V   (one combine; to `wide` in FP64 if given)
+template <typename T>
+th_status cycle_fused(th_ctx& x, int wkind, const typename th::Cx<T>::t* f, typename th::Cx<T>::t* u, int nrhs,
+                      double2* wide, int wide_acc, cudaStream_t s) {
+  using B = PrecBufs<T>;
+  using C = typename th::Cx<T>::t;
+  const th::Geometry& g = x.g;
+  th_status st;
+  C* ua = u;
+  C* ub = B::s(x);
+  if ((st = dd_apply<T>(x, wkind, f, nrhs, s)) != TH_OK) return st;
+  // variant 2: every later launch of the step may be scheduled while its
+  // predecessor drains (programmatic dependent launch; each kernel waits for
+  // it before touching its data); not with per-kernel events or a non-kernel
+  // step between two launches
+  th::PdlScope pdl(x.fuse == 2 && !x.prof_on && x.coarse_mode == 0);
+  auto fused_apply = [&](int src, C* uout) -> th_status {
+    th::FineArgs<T> a = fine_args<T>(x, TH_OP_A);
+    a.u = nullptr;
+    a.f = f;
+    a.y = B::r(x);
+    a.residual = 1;
+    a.src = src;
+    a.uout = uout;
+    a.V = B::V(x);
+    a.ctab = x.ctab;
+    a.nb = g.nb;
+    a.Lu = g.Lu;
+    a.NR = g.NR;
+    a.nsub = g.nsub;
+    a.uin = ua;
+    a.uc = B::uc(x);
+    a.pj0 = x.pj0;
+    a.pw = B::pw(x);
+    a.Nc = g.Nc;
+    a.mc = g.mc;
+    a.q = g.q;
+    a.omega = (T)x.prm.omega_c;
+    x.launches += 1;
+    Prof prof(x, TH_K_FINE, s);
+    return cuda_status(th::launch_fine_apply<T>(a, nrhs, s));
+  };
+  if ((st = fused_apply(1, ua)) != TH_OK) return st;
+  if ((st = restrict_<T>(x, B::r(x), B::rc(x), nrhs, s)) != TH_OK) return st;
+  if ((st = coarse_correct_<T>(x, B::rc(x), B::uc(x), nrhs, s)) != TH_OK) return st;
+  if ((st = fused_apply(2, ub)) != TH_OK) return st;
+  if ((st = dd_apply<T>(x, wkind, B::r(x), nrhs, s)) != TH_OK) return st;
+  th::CombineArgs<T> a{};
+  a.V = B::V(x);
+  a.u = u;
+  a.uin = ub;
+  a.wide = wide;
+  a.wide_acc = wide_acc;
+  a.ctab = x.ctab;
+  a.N = g.N;
+  a.m = g.m;
+  a.nb = g.nb;
+  a.Lu = g.Lu;
+  a.NR = g.NR;
+  a.nsub = g.nsub;
+  x.launches += 1;
+  Prof prof(x, TH_K_COMBINE, s);
+  return cuda_status(th::launch_dd_combine<T>(a, nrhs, s));
+}
+
+template <typename T>
+bool can_fuse(const th_ctx& x, bool u_zero) {
+  return x.fuse && u_zero && x.g.dim == 2 && x.prm.n_s == 1 && x.prm.n_dd == 1;
+}
+
 // TwoGridStep(u, f) of Algorithm 1 in precision T.
 template <typename T>
 th_status cycle(th_ctx& x, int wkind, const typename th::Cx<T>::t* f, typename th::Cx<T>::t* u, bool u_zero,
                 int nrhs, cudaStream_t s) {
   using B = PrecBufs<T>;
   th_status st;
+  if (can_fuse<T>(x, u_zero)) return cycle_fused<T>(x, wkind, f, u, nrhs, nullptr, 0, s);
   for (int i = 0; i < x.prm.n_s; ++i)
     if ((st = smooth<T>(x, wkind, f, u, u_zero && i == 0, nrhs, s)) != TH_OK) return st;
   if ((st = fine_apply<T>(x, TH_OP_A, u, f, B::r(x), nrhs, s)) != TH_OK) return st;
@@ -850,6 +929,7 @@ th_status precondition(th_ctx& x, const double2* v, double2* z, int nrhs, cudaSt
   if (x.active == TH_PREC_FP64) return cycle<double>(x, TH_PREC_FP64, v, z, true, nrhs, s);
   th_status st;
   if ((st = narrow(x, v, x.f32, n, s)) != TH_OK) return st;
+  if (can_fuse<float>(x, true)) return cycle_fused<float>(x, x.active, x.f32, x.u32, nrhs, z, 0, s);
   if ((st = cycle<float>(x, x.active, x.f32, x.u32, true, nrhs, s)) != TH_OK) return st;
   return widen(x, x.u32, z, n, 0, s);
 }
@@ -1416,7 +1496,8 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
 }
 
 th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
-  const int vmax = kernel == TH_K_DD ? (prec == TH_PREC_FP32 ? 5 : 3) : kernel == TH_K_COARSE_SOLVE ? 2 : 1;
+  const int vmax = kernel == TH_K_DD ? (prec == TH_PREC_FP32 ? 5 : 3)
+                   : (kernel == TH_K_COARSE_SOLVE || kernel == TH_K_CYCLE) ? 2 : 1;
   if (!x || variant < 0 || variant > vmax || (prec != TH_PREC_FP64 && prec != TH_PREC_FP32))
     return TH_ERR_ARG;
   const bool d = (prec == TH_PREC_FP64);
@@ -1430,6 +1511,8 @@ th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
     x->cs_variant = variant;
   } else if (kernel == TH_K_RESID) {
     x->resid_ds = variant;
+  } else if (kernel == TH_K_CYCLE) {
+    x->fuse = variant;
   } else {
     return TH_ERR_ARG;
   }
@@ -1445,6 +1528,7 @@ th_status th_get_kernel_variant(const th_ctx* x, int kernel, int prec, int* vari
   else if (kernel == TH_K_DD_BATCH) *variant = (x->Wu && x->dd_tc) ? 1 : 0;
   else if (kernel == TH_K_COARSE_SOLVE) *variant = x->cs_variant;
   else if (kernel == TH_K_RESID) *variant = (x->resid_ds && x->kcds) ? 1 : 0;
+  else if (kernel == TH_K_CYCLE) *variant = x->fuse;
   else return TH_ERR_ARG;
   return TH_OK;
 }
@@ -1612,6 +1696,7 @@ th_status th_cycle(th_ctx* x, const double* f, double* u, int nrhs, void* stream
   // mixed: TwoGridStep(u, f) = u + TwoGridStep(0, f - A u) (the step is affine in u and f)
   const long long n = x->g.N * (long long)nrhs;
   if ((st = outer_residual(*x, u2, f2, x->f32, nrhs, s)) != TH_OK) return st;
+  if (can_fuse<float>(*x, true)) return cycle_fused<float>(*x, x->active, x->f32, x->u32, nrhs, u2, 1, s);
   if ((st = cycle<float>(*x, x->active, x->f32, x->u32, true, nrhs, s)) != TH_OK) return st;
   return widen(*x, x->u32, u2, n, 1, s);
 }

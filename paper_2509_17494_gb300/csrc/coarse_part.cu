@@ -26,6 +26,7 @@
 #include <cooperative_groups.h>
 
 #include "kernels.h"
+#include "launch.cuh"
 #include "ptx.cuh"
 
 namespace cg = cooperative_groups;
@@ -432,6 +433,8 @@ __global__ void __launch_bounds__(1024, 1) k_chunk_sweep2(const CoarsePartArgs<T
   // every barrier is initialised before any CTA of the cluster can send to it
   cluster_arrive_release();
   cluster_wait_acquire();
+  ptx::grid_dep_wait();  // b is the previous kernel's output
+  ptx::grid_dep_launch();
   prefetch(0);
   prefetch(1);
   for (int q = 0; q < nsteps; ++q) {
@@ -524,6 +527,8 @@ __global__ void __launch_bounds__(1024, 1) k_chunk_sweep2(const CoarsePartArgs<T
 template <typename T>
 __global__ void __launch_bounds__(256) k_reduced_rhs(const CoarsePartArgs<T> a) {
   using C = typename Cx<T>::t;
+  ptx::grid_dep_wait();  // launched with a programmatic dependency inside the cycle
+  ptx::grid_dep_launch();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.nred) return;
   const int mc = a.mc;
@@ -742,6 +747,8 @@ __device__ __forceinline__ void ld_pair(const double2* p, double2& u, double2& v
 template <typename T, int NB, int MODE>
 __global__ void __launch_bounds__(512) k_coarse_tsgemm(const CoarsePartArgs<T> a) {
   using C = typename Cx<T>::t;
+  ptx::grid_dep_wait();  // launched with a programmatic dependency inside the cycle
+  ptx::grid_dep_launch();
   constexpr int R = MODE == 0 ? 1 : 2, WARPS = 16;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* Xs = reinterpret_cast<C*>(smraw);  // [NB][kc]
@@ -892,12 +899,10 @@ static cudaError_t launch_tsgemm(const CoarsePartArgs<T>& a, cudaStream_t s) {
   e = cudaFuncSetAttribute(k_coarse_tsgemm<T, NB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
   if (e != cudaSuccess) return e;
   const unsigned g0 = (unsigned)((a.nred + 15) / 16) * ntiles;
-  k_coarse_tsgemm<T, NB, 0><<<g0, 512, sm0, s>>>(a);
-  e = cudaGetLastError();
+  e = launch_pdl(k_coarse_tsgemm<T, NB, 0>, dim3(g0), dim3(512), sm0, s, 0, a);
   if (e != cudaSuccess) return e;
   const unsigned g1 = (unsigned)((NB == 1 ? 4 : 2) * a.mc) * ntiles;
-  k_coarse_tsgemm<T, NB, 1><<<g1, 512, sm1, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_coarse_tsgemm<T, NB, 1>, dim3(g1), dim3(512), sm1, s, 0, a);
 }
 
 // ------------------------------------------------------------- launcher
@@ -996,20 +1001,8 @@ cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster
     cudaError_t e2 = cudaFuncSetAttribute(k_chunk_sweep2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)chunk_sweep2_smem(a));
     if (e2 != cudaSuccess) return e2;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cluster * a.P * nrhs, 1, 1);
-    cfg.blockDim = dim3(1024, 1, 1);
-    cfg.dynamicSmemBytes = chunk_sweep2_smem(a);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_chunk_sweep2<T>, a, a.err);
-    if (e == cudaSuccess) e = cudaGetLastError();
+    e = launch_pdl(k_chunk_sweep2<T>, dim3(cluster * a.P * nrhs), dim3(1024), chunk_sweep2_smem(a), s, cluster, a,
+                   a.err);
   } else if (a.sweep_variant == 1 && a.mc <= 256 && a.rpc <= 32) {
     e = pf ? launch_cluster(k_chunk_sweep1<T, true>, a, cluster * a.P * nrhs, cluster, sm1, s, 1024)
            : launch_cluster(k_chunk_sweep1<T, false>, a, cluster * a.P * nrhs, cluster, sm1, s, 1024);
@@ -1019,8 +1012,7 @@ cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster
   }
   if (e != cudaSuccess || a.P < 2) return e;
   dim3 g1((unsigned)((a.nred + 255) / 256), nrhs);
-  k_reduced_rhs<T><<<g1, 256, 0, s>>>(a);
-  e = cudaGetLastError();
+  e = launch_pdl(k_reduced_rhs<T>, g1, dim3(256), 0, s, 0, a);
   if (e != cudaSuccess) return e;
   CoarsePartArgs<T> b = a;
   b.nrhs = nrhs;

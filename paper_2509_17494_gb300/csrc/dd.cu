@@ -22,6 +22,7 @@
 #include <algorithm>
 
 #include "kernels.h"
+#include "launch.cuh"
 #include "ptx.cuh"
 
 namespace th {
@@ -105,6 +106,8 @@ __global__ void __launch_bounds__(MAXT) k_dd_apply(const DDArgs<T> a) {
   const int rr = tid % a.NR, g = tid / a.NR;
   const int r0 = blockIdx.y * NRHS;
   const int nr = min(NRHS, a.nrhs - r0);
+  ptx::grid_dep_wait();  // launched with a programmatic dependency inside the cycle
+  ptx::grid_dep_launch();
   for (int sub = blockIdx.x; sub < a.nsub; sub += gridDim.x) {
     const int* bb = a.box + (size_t)sub * 12;
     const int ox = bb[0], oy = bb[1], wx = bb[2], wy = bb[3], oz = bb[8], wz = bb[9];
@@ -177,8 +180,7 @@ static cudaError_t launch_dd_kt(const DDArgs<T>& a, int grid_cap, int threads, s
   if (e != cudaSuccess) return e;
   const int gx = (grid_cap > 0 && grid_cap < a.nsub) ? grid_cap : a.nsub;
   dim3 grid(gx, (a.nrhs + NRHS - 1) / NRHS);
-  k_dd_apply<T, KIND, NRHS, MAXT><<<grid, threads, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_dd_apply<T, KIND, NRHS, MAXT>, grid, dim3(threads), smem, s, 0, a);
 }
 
 // up to 512 threads (U boxes of at most 512 nodes, G column groups), or 1024
@@ -229,6 +231,8 @@ cudaError_t launch_dd_apply<float>(const DDArgs<float>& a, int kind, int grid_ca
 template <typename T>
 __global__ void __launch_bounds__(256) k_dd_combine(const CombineArgs<T> a) {
   using C = typename Cx<T>::t;
+  ptx::grid_dep_wait();  // launched with a programmatic dependency inside the cycle
+  ptx::grid_dep_launch();
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= a.N) return;
   const int iy = (int)(j / a.m), ix = (int)(j - (long long)iy * a.m);
@@ -250,7 +254,11 @@ __global__ void __launch_bounds__(256) k_dd_combine(const CombineArgs<T> a) {
   }
   C* u = a.u + (size_t)blockIdx.y * a.N;
   C o;
-  if (a.accumulate) {
+  if (a.uin) {
+    o = a.uin[(size_t)blockIdx.y * a.N + j];
+    o.x += sr;
+    o.y += si;
+  } else if (a.accumulate) {
     o = u[j];
     o.x += sr;
     o.y += si;
@@ -258,14 +266,21 @@ __global__ void __launch_bounds__(256) k_dd_combine(const CombineArgs<T> a) {
     o.x = sr;
     o.y = si;
   }
-  u[j] = o;
+  if (a.wide) {
+    double2* w = a.wide + (size_t)blockIdx.y * a.N + j;
+    double2 d = a.wide_acc ? *w : make_double2(0.0, 0.0);
+    d.x = a.wide_acc ? d.x + (double)o.x : (double)o.x;
+    d.y = a.wide_acc ? d.y + (double)o.y : (double)o.y;
+    *w = d;
+  } else {
+    u[j] = o;
+  }
 }
 
 template <typename T>
 cudaError_t launch_dd_combine(const CombineArgs<T>& a, int nrhs, cudaStream_t s) {
   dim3 grid((unsigned)((a.N + 255) / 256), nrhs);
-  k_dd_combine<T><<<grid, 256, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_dd_combine<T>, grid, dim3(256), 0, s, 0, a);
 }
 
 template cudaError_t launch_dd_combine<double>(const CombineArgs<double>&, int, cudaStream_t);
@@ -406,6 +421,9 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream(const DDArgs<T> a, int cps
   __syncthreads();
   if (tid == 0)
     for (int t = 0; t < depth; ++t) issue(t);
+  // the rows above are set-up data; r is the previous kernel's output
+  ptx::grid_dep_wait();
+  ptx::grid_dep_launch();
   gather(0, 0);
   // A wait that gives up marks `failed` (shared); every thread keeps running the
   // same loop (on possibly stale data) so the barriers stay uniform, no new
@@ -634,6 +652,9 @@ __global__ void __launch_bounds__(512, 2) k_dd_stream2(const DDArgs<T> a, int cp
       }
       cp_commit();
     };
+    // r is the previous kernel's output (the producer streams set-up data only)
+    ptx::grid_dep_wait();
+    ptx::grid_dep_launch();
     gather(0, 0);
     int t = 0;
     for (int i = 0; i < nmine; ++i) {
@@ -730,8 +751,7 @@ static cudaError_t launch_dd_stream2_k(const DDArgs<T>& a0, int* err, int sms, c
   if (e != cudaSuccess) return e;
   const int gx = std::min(a.nsub, per_sm * sms);
   dim3 grid(gx, (a.nrhs + NRHS - 1) / NRHS);
-  k_dd_stream2<T, KIND, NRHS><<<grid, threads, smem, s>>>(a, cps, depth, err);
-  return cudaGetLastError();
+  return launch_pdl(k_dd_stream2<T, KIND, NRHS>, grid, dim3(threads), smem, s, 0, a, cps, depth, err);
 }
 
 template <typename T, int KIND, int NRHS, bool PK>
@@ -758,8 +778,7 @@ static cudaError_t launch_dd_stream_k(const DDArgs<T>& a, int* err, int sms, cud
   if (e != cudaSuccess) return e;
   const int gx = std::min(a.nsub, per_sm * sms);
   dim3 grid(gx, (a.nrhs + NRHS - 1) / NRHS);
-  k_dd_stream<T, KIND, NRHS, PK><<<grid, threads, smem, s>>>(a, cps, depth, err);
-  return cudaGetLastError();
+  return launch_pdl(k_dd_stream<T, KIND, NRHS, PK>, grid, dim3(threads), smem, s, 0, a, cps, depth, err);
 }
 
 template <typename T, int KIND>

@@ -12,8 +12,12 @@
 // memory, computes every cell matrix-vector product there, and sums the
 // contributions of the 1, 2 or 4 cells around each owned node in a fixed
 // order, so the result is bitwise deterministic.
+#include <type_traits>
+
 #include "ds_math.cuh"
 #include "kernels.h"
+#include "launch.cuh"
+#include "ptx.cuh"
 
 namespace th {
 
@@ -23,6 +27,60 @@ __device__ __forceinline__ C cmul(C a, T br, T bi) {
   r.x = a.x * br - a.y * bi;
   r.y = a.x * bi + a.y * br;
   return r;
+}
+
+// The RAS-like average at node (gx, gy) of this CTA's right-hand side: the sum
+// of the V entries of the (at most 2 x 2) U boxes holding the node, in the
+// order of k_dd_combine, so the fused cycle is bitwise the unfused one.
+template <typename T>
+__device__ __forceinline__ typename Cx<T>::t combine_at(const FineArgs<T>& a, int gx, int gy) {
+  using C = typename Cx<T>::t;
+  const int4 tx = a.ctab[gx], ty = a.ctab[gy];
+  const C* V = a.V + (size_t)blockIdx.z * a.nsub * a.NR;
+  T sr = 0, si = 0;
+  const int byl[2] = {ty.x, ty.z}, ryl[2] = {ty.y, ty.w};
+  const int bxl[2] = {tx.x, tx.z}, rxl[2] = {tx.y, tx.w};
+#pragma unroll
+  for (int jy = 0; jy < 2; ++jy) {
+    if (byl[jy] < 0) continue;
+#pragma unroll
+    for (int jx = 0; jx < 2; ++jx) {
+      if (bxl[jx] < 0) continue;
+      const C v = V[((size_t)byl[jy] * a.nb + bxl[jx]) * a.NR + ryl[jy] * a.Lu + rxl[jx]];
+      sr += v.x;
+      si += v.y;
+    }
+  }
+  C o;
+  o.x = sr;
+  o.y = si;
+  return o;
+}
+
+// uin + omega I_P uc at node (gx, gy), in the order of k_prolong
+template <typename T>
+__device__ __forceinline__ typename Cx<T>::t prolong_at(const FineArgs<T>& a, int gx, int gy) {
+  using C = typename Cx<T>::t;
+  const C* uc = a.uc + (size_t)blockIdx.z * a.Nc;
+  const int jx0 = a.pj0[gx], jy0 = a.pj0[gy];
+  T sr = 0, si = 0;
+  for (int by = 0; by <= a.q; ++by) {
+    const T wy = a.pw[(size_t)gy * (a.q + 1) + by];
+    if (wy == (T)0) continue;
+    T tr = 0, ti = 0;
+    for (int bx = 0; bx <= a.q; ++bx) {
+      const T wx = a.pw[(size_t)gx * (a.q + 1) + bx];
+      const C v = uc[(size_t)(jy0 + by) * a.mc + jx0 + bx];
+      tr = fma(wx, v.x, tr);
+      ti = fma(wx, v.y, ti);
+    }
+    sr = fma(wy, tr, sr);
+    si = fma(wy, ti, si);
+  }
+  C o = a.uin[(size_t)blockIdx.z * a.N + (size_t)gy * a.m + gx];
+  o.x = fma(a.omega, sr, o.x);
+  o.y = fma(a.omega, si, o.y);
+  return o;
 }
 
 template <int P, int TC, typename T>
@@ -46,6 +104,8 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
   const int ncx = min(TC, a.n - cx0), ncy = min(TC, a.n - cy0);
   const int wx = ncx * P + ((cx0 + ncx == a.n) ? 1 : 0);
   const int wy = ncy * P + ((cy0 + ncy == a.n) ? 1 : 0);
+  ptx::grid_dep_wait();  // launched with a programmatic dependency inside the cycle
+  ptx::grid_dep_launch();
 
   // Every global load of the tile is issued here, before the first barrier, so
   // the CTA waits for memory once: its nodal values, its cells' coefficients
@@ -56,7 +116,19 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
     C v;
     v.x = 0;
     v.y = 0;
-    if (gx >= 0 && gx < a.m && gy >= 0 && gy < a.m) v = NodeIO<T>::ld(u, (size_t)gy * a.m + gx);
+    if (gx >= 0 && gx < a.m && gy >= 0 && gy < a.m) {
+      if constexpr (std::is_same<T, ds>::value) {
+        v = NodeIO<T>::ld(u, (size_t)gy * a.m + gx);
+      } else {
+        if (a.src == 1) {
+          v = combine_at(a, gx, gy);
+        } else if (a.src == 2) {
+          v = prolong_at(a, gx, gy);
+        } else {
+          v = NodeIO<T>::ld(u, (size_t)gy * a.m + gx);
+        }
+      }
+    }
     su[i] = v;
   }
   for (int e = tid; e < CELLS; e += nth) {
@@ -251,6 +323,9 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
       }
     }
     const size_t g = (size_t)(cy0 * P + ly) * a.m + (cx0 * P + lx);
+    if constexpr (!std::is_same<T, ds>::value) {
+      if (a.src != 0) a.uout[roff + g] = su[(ly + P) * UT + lx + P];
+    }
     C out;
     if (a.f) {
       out.x = sf[i].x - ar;
@@ -276,8 +351,7 @@ static cudaError_t launch_fine_p(const FineArgs<T>& a, int nrhs, cudaStream_t s)
   if (e != cudaSuccess) return e;
   const int tiles = (a.n + TC - 1) / TC;
   dim3 grid(tiles, tiles, nrhs);
-  k_fine_apply<P, TC, T><<<grid, TC >= 8 ? 256 : 128, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_fine_apply<P, TC, T>, grid, dim3(TC >= 8 ? 256 : 128), smem, s, 0, a);
 }
 
 template <typename T>

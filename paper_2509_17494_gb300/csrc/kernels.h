@@ -65,6 +65,27 @@ struct FineArgs {
   // even / odd halves (both matrices are centrosymmetric), H = p/2, 1/2 folded in:
   // ME[a][b] = (M[a][b] + M[a][p-b]) / 2 (b < H), ME[a][H] = M[a][H]; MO[a][b] = (M[a][b] - M[a][p-b]) / 2
   T ME[25], MO[16], KE[25], KO[16];
+  // Where the operand comes from (FP32 / FP64 forms only; the fused cycle):
+  //   src 0: u;
+  //   src 1: the RAS-like average of the subdomain results, u_j = sum of the
+  //          V entries of the U boxes that hold node j (the weights 1/L_j are
+  //          in the rows), in the order of k_dd_combine;
+  //   src 2: uin + omega I_P uc (the prolonged coarse correction), in the
+  //          order of k_prolong.
+  // With src != 0 the operand at the owned nodes is also written to uout
+  // (which must not alias uin).
+  int src;
+  const typename Cx<T>::t* V;  // src 1: [rhs][nsub][NR]
+  const int4* ctab;            // src 1: per 1-D node (b0, r0, b1, r1)
+  int nb, Lu, NR, nsub;
+  const typename Cx<T>::t* uin;  // src 2
+  const typename Cx<T>::t* uc;   // src 2: coarse correction, [rhs][Nc]
+  const int* pj0;                // src 2: per fine 1-D node, first coarse node of its cell
+  const T* pw;                   // src 2: per fine 1-D node, q + 1 weights
+  long long Nc;
+  int mc, q;
+  T omega;
+  typename Cx<T>::t* uout;
 };
 template <typename T>
 cudaError_t launch_fine_apply(const FineArgs<T>& a, int nrhs, cudaStream_t s);
@@ -115,6 +136,12 @@ struct CombineArgs {
   const int4* ctab;             // per 1-D node: (b0, r0, b1, r1)
   long long N;
   int m, nb, Lu, NR, nsub, accumulate;
+  // fused cycle: with uin set the result is uin + average (u is not read);
+  // with wide set it goes, widened to FP64, to wide (added to it if
+  // wide_acc) instead of u
+  const typename Cx<T>::t* uin;
+  double2* wide;
+  int wide_acc;
 };
 template <typename T>
 cudaError_t launch_dd_combine(const CombineArgs<T>& a, int nrhs, cudaStream_t s);

@@ -97,6 +97,16 @@ __device__ __forceinline__ bool mbar_wait_shared_flag(uint64_t* b, unsigned pari
   return false;
 }
 
+// ------------------------------------------------- programmatic dependent launch
+// Wait until every grid this one depends on programmatically has completed and
+// its memory operations are visible; a no-op in a launch without such a
+// dependency.  A kernel launched with one must pass here before it touches
+// anything an earlier kernel of the stream writes or reads.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+// Let the next grid of the stream, if launched with a programmatic dependency,
+// be scheduled (it still waits in grid_dep_wait for this grid to complete).
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // ------------------------------------------------------------ bulk copies
 // one-dimensional bulk copy global -> shared (16-byte aligned addresses, size
 // a multiple of 16), completing `bytes` transactions on bar

@@ -8,6 +8,8 @@
 // coefficients (d0, d1, d2) for same-node, edge-neighbour and diagonal pairs,
 // plus -i k hc times the Q1 edge mass on absorbing sides.
 #include "kernels.h"
+#include "launch.cuh"
+#include "ptx.cuh"
 
 namespace th {
 
@@ -15,6 +17,8 @@ namespace th {
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict(const TransferArgs<T> a) {
   using C = typename Cx<T>::t;
+  ptx::grid_dep_wait();  // launched with a programmatic dependency inside the cycle
+  ptx::grid_dep_launch();
   const long long J = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= a.Nc) return;
   const int Jy = (int)(J / a.mc), Jx = (int)(J - (long long)Jy * a.mc);
@@ -28,11 +32,11 @@ __global__ void __launch_bounds__(256) k_restrict(const TransferArgs<T> a) {
     for (int kx = 0; kx < a.rmax; ++kx) {
       const T wx = a.rw[(size_t)Jx * a.rmax + kx];
       const C v = r[(size_t)iy * a.m + a.ridx[(size_t)Jx * a.rmax + kx]];
-      tr += wx * v.x;
-      ti += wx * v.y;
+      tr = fma(wx, v.x, tr);
+      ti = fma(wx, v.y, ti);
     }
-    sr += wy * tr;
-    si += wy * ti;
+    sr = fma(wy, tr, sr);
+    si = fma(wy, ti, si);
   }
   C o;
   o.x = sr;
@@ -57,24 +61,23 @@ __global__ void __launch_bounds__(256) k_prolong(const TransferArgs<T> a) {
     for (int bx = 0; bx <= a.q; ++bx) {
       const T wx = a.pw[(size_t)ix * (a.q + 1) + bx];
       const C v = uc[(size_t)(jy0 + by) * a.mc + jx0 + bx];
-      tr += wx * v.x;
-      ti += wx * v.y;
+      tr = fma(wx, v.x, tr);
+      ti = fma(wx, v.y, ti);
     }
-    sr += wy * tr;
-    si += wy * ti;
+    sr = fma(wy, tr, sr);
+    si = fma(wy, ti, si);
   }
   C* u = a.out + (size_t)blockIdx.y * a.N;
   C o = u[j];
-  o.x += a.omega * sr;
-  o.y += a.omega * si;
+  o.x = fma(a.omega, sr, o.x);
+  o.y = fma(a.omega, si, o.y);
   u[j] = o;
 }
 
 template <typename T>
 cudaError_t launch_restrict(const TransferArgs<T>& a, int nrhs, cudaStream_t s) {
   dim3 grid((unsigned)((a.Nc + 255) / 256), nrhs);
-  k_restrict<T><<<grid, 256, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_restrict<T>, grid, dim3(256), 0, s, 0, a);
 }
 template <typename T>
 cudaError_t launch_prolong(const TransferArgs<T>& a, int nrhs, cudaStream_t s) {

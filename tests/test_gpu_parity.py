@@ -191,6 +191,35 @@ def test_cycle_fp64(th, c, n_s, omega_c):
     assert relerr(got, want) < 1e-9
 
 
+@pytest.mark.parametrize("c", CASES)
+@pytest.mark.parametrize("prec,nrhs", [("bf16", 3), ("fp32", 2), ("bf16", 9)])
+def test_fused_cycle_bitwise_equals_step_by_step(th, c, prec, nrhs):
+    """The fused launch structure of the cycle (the average folded into the next
+    fine apply, the prolongation into the post-smoother's, the last average with
+    the update and the widening into one kernel) does the step-by-step
+    arithmetic in the same order: bitwise equal cycles (mixed form) and
+    preconditioned solves (FP64 form, whose preconditioner is the fused step)."""
+    S, P = build(th, c, nrhs=nrhs, prec=prec, extra_prec=("fp64",))
+    f = dev(synth.random_complex((nrhs, P.N), 90))
+    u0 = synth.random_complex((nrhs, P.N), 91)
+    outs = []
+    for v in (0, 1, 2):   # 2: the fused launches with programmatic dependencies
+        S.set_variant("cycle", "fp32", v)
+        outs.append(S.cycle(f, dev(u0.copy())))
+        outs.append(S.cycle_graph(f, dev(u0.copy())))
+        S.device_status()
+    for o in outs[1:]:
+        assert torch.equal(outs[0], o)
+    S.set_precision("fp64")
+    sols = []
+    for v in (0, 1, 2):
+        S.set_variant("cycle", "fp64", v)
+        x, info = S.solve(f)
+        sols.append((x, info["iters"]))
+    for x, it in sols[1:]:
+        assert it == sols[0][1] and torch.equal(x, sols[0][0])
+
+
 def test_cycle_is_deterministic(th):
     S, P = build(th, CASES[1])
     f = dev(synth.random_complex((3, P.N), 11))
