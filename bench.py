@@ -843,6 +843,15 @@ def lfa_section(with_oracle):
     gpu_s = time.perf_counter() - t0
     out["gpu"] = {"theta_points": n_theta, "wall_s": round(gpu_s, 3),
                   "theta_per_s": round(n_theta / gpu_s, 1)}
+    # coarse-level dispersion error D_P / k (Section 3.2) at the coarse spacing
+    # h_c = 2 h / p, i.e. half the fine dofs per wavelength: eta_c = 4 pi / ppw
+    ppw_d = [7, 8, 10, 12, 16, 20]
+    etas = [4 * math.pi / q for q in ppw_d]
+    t2 = time.perf_counter()
+    disp = {kind: [float("%.3e" % v) for v in th.dispersion(kind, etas, nt=256)] for kind in ("qsfem", "q1", "fd5")}
+    out["dispersion"] = {"what": "D_P / k of the coarse stencil at eta_c = 4 pi / (fine dofs per wavelength), "
+                                 "max over 256 directions (th_dispersion, FP64 on the GPU)",
+                         "ppw": ppw_d, **disp, "gpu_wall_s": round(time.perf_counter() - t2, 3)}
     if with_oracle:
         from oracle import lfa as olfa
 

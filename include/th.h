@@ -478,6 +478,24 @@ th_status th_host_coarse_separators(const th_mesh* mesh, const double* k_host, c
 
 /* ---------------------------------------------------- Fourier analysis */
 
+/* Dispersion error of a compact 2-D stencil (Section 3.2): for a symmetric
+ * 3 x 3 stencil P with symbol sigma_P(xi) (Eq. symbol_sigma_P) on the grid of
+ * spacing h and eta = k h, the distance of its zero set Z_P to the circle
+ * |xi| = k,
+ *     D_P = max_{t in [-pi, pi]} min_{xi in Z_P} |k (cos t, sin t) - xi| ,
+ * returned divided by k, over the directions t_j = -pi + 2 pi j / nt.
+ *   kind: TH_DISP_QSFEM (Eq. P_QSFEM, from the same cancellation-free weights as
+ *         the coarse operator), TH_DISP_Q1 (bilinear elements: stiffness minus
+ *         eta^2 times mass, Section 3.3), TH_DISP_FD5 (5-point differences).
+ *   eta: host, n values in (0, 2];  d_max: host, n values (output);
+ *   d_theta: host, n x nt values (output, index i nt + j) or NULL.
+ * One GPU thread per (eta, t_j), FP64: the zero along each ray by a sign-change
+ * scan and bisection, the nearest point by a scan over nearby rays and a
+ * golden-section search.  Allocates and frees its own device buffers;
+ * synchronous on `stream`.  TH_ERR_ARG for invalid arguments. */
+enum { TH_DISP_QSFEM = 0, TH_DISP_Q1 = 1, TH_DISP_FD5 = 2 };
+th_status th_dispersion(int kind, const double* eta, int n, int nt, double* d_max, double* d_theta, void* stream);
+
 /* Local Fourier analysis of the two-grid method (Section 6, Eq. symbol_sum):
  * for nparam parameter points on the periodic plane with constant k and eps
  * (Q_p, p in {2, 4, 6}; coarse level TH_CK_QSFEM, or TH_CK_GALERKIN with

@@ -104,6 +104,7 @@ def lib() -> ctypes.CDLL:
         "th_launch_count": ([P, ctypes.POINTER(ctypes.c_longlong)], I),
         "th_set_wait_limit": ([P, ctypes.c_longlong, P], I),
         "th_peak_fma": ([I, I, ctypes.POINTER(ctypes.c_double), P], I),
+        "th_dispersion": ([I, P, I, I, P, P, P], I),
         "th_profile": ([P, I], I),
         "th_profile_read": ([P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)], I),
         "th_host_reference_1d": ([I, P, P, P], I),
@@ -247,6 +248,19 @@ def host_galerkin(n, p, k_cell, eps_cell=None, bc="robin", alpha_c=0.0, b=None):
            "th_host_galerkin")
     sten = (st[0::2] + 1j * st[1::2]).reshape(mc * mc, S, S)
     return sten, (xo if b is not None else None)
+
+
+def dispersion(kind, eta, nt=64, per_theta=False, stream=None):
+    """D_P / k (Section 3.2) of the 'qsfem', 'q1' or 'fd5' stencil at each eta = k h, on the
+    GPU (th_dispersion): max over nt directions, and the per-direction values if asked."""
+    e = np.ascontiguousarray(np.atleast_1d(np.asarray(eta, dtype=np.float64)))
+    dmax = np.zeros(e.size)
+    dt = np.zeros((e.size, nt)) if per_theta else None
+    k = {"qsfem": 0, "q1": 1, "fd5": 2}[kind]
+    st = ctypes.c_void_p(stream) if stream is not None else None
+    _check(lib().th_dispersion(k, e.ctypes.data, e.size, int(nt), dmax.ctypes.data,
+                               dt.ctypes.data if per_theta else None, st), "th_dispersion")
+    return (dmax, dt) if per_theta else dmax
 
 
 def peak_fma(prec="fp64", iters=None, stream=None):

@@ -65,3 +65,26 @@ def test_lfa_argument_errors(th):
     assert e.value.code == 8
     with pytest.raises(th.ThError):
         th.lfa_rho(4, [[-1.0, 0.0, 0.2, 1.0]], npts=4)
+
+
+@pytest.mark.parametrize("kind", ["qsfem", "q1", "fd5"])
+def test_dispersion_error_matches_oracle(th, kind):
+    """D_P / k (Section 3.2) per direction on the GPU against the oracle's trace of
+    the zero set (scan + Brent on each ray, dense scan + bounded minimisation over
+    rays): within 1e-10 of k.  The QSFEM stencils come from the library's
+    cancellation-free weights and the oracle's 50-digit ones."""
+    from oracle import dispersion
+    etas = [0.4, 1.0, 2 * math.pi / 5, 1.6]
+    nt = 12
+    dmax, dth = th.dispersion(kind, etas, nt=nt, per_theta=True)
+    for i, eta in enumerate(etas):
+        want_max, want = dispersion.dispersion_error(kind, eta, nt=nt)
+        assert np.abs(dth[i] - want).max() < 1e-10, (eta, np.abs(dth[i] - want).max())
+        assert abs(dmax[i] - want_max) < 1e-10
+    if kind == "qsfem":
+        # the exact zeros: with nt = 32 the directions are the multiples of pi/16, the odd ones
+        # (pi/16, 3 pi/16 and their images under the stencil's symmetries) are zeros of sigma_P on |xi| = k
+        _, d32 = th.dispersion(kind, [1.0], nt=32, per_theta=True)
+        t = -math.pi + 2 * math.pi * np.arange(32) / 32
+        on = np.isclose(np.mod(t * 16 / math.pi, 2), 1.0)
+        assert np.all(d32[0][on] < 1e-11)
