@@ -358,7 +358,8 @@ enum {
   TH_K_COUNT = 9,
   TH_K_DD_BATCH = 9,    /* (variants only) batched BF16 subdomain products: 0 CUDA cores, 1 tensor cores */
   TH_K_RESID = 10,      /* (variants only) the mixed form's outer residual, see th_residual_mixed */
-  TH_K_CYCLE = 11       /* (variants only) launch structure of the cycle, see th_set_kernel_variant */
+  TH_K_CYCLE = 11,      /* (variants only) launch structure of the cycle, see th_set_kernel_variant */
+  TH_K_COARSE_MULTI = 12 /* (variants only) 2-D coarse sweep for 8 or more right-hand sides */
 };
 
 /* Per-kernel timing for measurement: with enable = 1 every later kernel
@@ -410,6 +411,11 @@ th_status th_peak_fma(int prec, int iters, double* flops_per_s, void* stream);
  *              first issued with a programmatic dependency on the one before
  *              (it may be scheduled while that one drains, and waits for it
  *              before touching shared data; not while th_profile records);
+ *   TH_K_COARSE_MULTI: the 2-D coarse chunk sweep for 8 or more right-hand
+ *              sides: 1 (default) one CTA per chunk and group of 8 right-hand
+ *              sides, each G_j streamed once for all groups through L2; 0 one
+ *              thread-block cluster per chunk and tile of 2-8 right-hand sides
+ *              (the tile count multiplies the G_j reads); prec is ignored;
  *   TH_K_COARSE_SOLVE: one-right-hand-side chunk sweep of the 2-D coarse
  *              solve: 0 = two phases per block step (512 threads), 1 = one
  *              cluster barrier per step (1024 threads, m_c <= 256), 2 = rows

@@ -62,6 +62,7 @@ struct th_ctx {
   int dd_tc = 1;             // batched BF16 products on tensor cores (k_dd_umma) when available
   int cs_variant = 1;        // one-rhs coarse chunk sweep: 0 two-phase, 1 one barrier per step (autotuned)
   int fuse = 1;              // cycle with u = 0 on entry: combine, prolongation and widening fused (TH_K_CYCLE)
+  int cs_multi = 1;          // 8 or more right-hand sides: 0 per-tile cluster sweep, 1 column groups (TH_K_COARSE_MULTI)
   unsigned char* Wu = nullptr;  // BF16 inverse rows in the tcgen05 operand layout (NR <= 128)
   int sms = 152;
   int device = -1;          // CUDA device the context was set up on
@@ -341,6 +342,10 @@ th_status prepare(const th_mesh* mesh, const th_params* prm, th_ctx& x) {
   x.cluster = 8;
   x.rpc = (x.g.mc + x.cluster - 1) / x.cluster;
   x.P = x.g.dim == 2 ? th::coarse_chunks(x.g.mc) : 1;
+  // large coarse grids: at most 19 chunks, so that the many-right-hand-side
+  // sweep's P x 8 CTAs (groups of 8 right-hand sides, 64 at once) fill the
+  // 152 SMs in one wave
+  if (x.g.dim == 2 && x.g.mc > 256) x.P = std::min(x.P, 19);
   x.mcp = x.g.mc + (x.g.mc & 1);
   x.rpcm = x.rpc + (x.rpc & 1);
   x.mcr = x.cluster * x.rpcm;
@@ -770,6 +775,7 @@ th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th:
   a.rpcm = x.rpcm;
   a.nrhs = nrhs;
   a.sweep_variant = x.cs_variant;
+  a.multi_variant = x.cs_multi;
   a.err = x.derr;
   if (!a.G || !a.LR) return TH_ERR_UNSUPPORTED;
   x.launches += (x.P > 1) ? 4 : 1;
@@ -1513,6 +1519,8 @@ th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
     x->resid_ds = variant;
   } else if (kernel == TH_K_CYCLE) {
     x->fuse = variant;
+  } else if (kernel == TH_K_COARSE_MULTI) {
+    x->cs_multi = variant;
   } else {
     return TH_ERR_ARG;
   }
@@ -1529,6 +1537,7 @@ th_status th_get_kernel_variant(const th_ctx* x, int kernel, int prec, int* vari
   else if (kernel == TH_K_COARSE_SOLVE) *variant = x->cs_variant;
   else if (kernel == TH_K_RESID) *variant = (x->resid_ds && x->kcds) ? 1 : 0;
   else if (kernel == TH_K_CYCLE) *variant = x->fuse;
+  else if (kernel == TH_K_COARSE_MULTI) *variant = x->cs_multi;
   else return TH_ERR_ARG;
   return TH_OK;
 }

@@ -720,6 +720,112 @@ __global__ void __launch_bounds__(512, 1) k_chunk_sweep_mr(const CoarsePartArgs<
   }
 }
 
+// ------------------------------------------------------------- wide tiles of right-hand sides
+// The chunk sweep for a group of NBW right-hand sides per CTA: one CTA per
+// (chunk, group), no cluster.  A thread owns rows of the block (row rr for
+// rr = tid, tid + blockDim, ...) and NBW accumulators; it streams its row's
+// entries of the transposed G_j (consecutive across lanes, through L2: the
+// CTAs of the other groups of the same chunk read the same G_j at about the
+// same time) and reads the step's vector block T_j[c][0..NBW-1] from shared
+// memory (the same address for the whole warp).  Per step
+//   forward  (q < L):  T = b_j - C_{j-1}^T z_{j-1},  z_j = G_j T,
+//   backward (q >= L): T = C_j y_{j+1},             y_j = z_j - G_j T,
+// with z_j kept in the output x between the passes (x[j] = z_j, then y_j)
+// and the previous step's block in shared memory.  Each G_j is read from
+// HBM about once per sweep for all right-hand sides (the per-tile sweep
+// above reads it once per tile), and the grid has P x groups CTAs.
+template <typename T, int NBW>
+__global__ void __launch_bounds__(512, 1) k_sweep_cols(const CoarsePartArgs<T> a) {
+  using C = typename Cx<T>::t;
+  const int chunk = blockIdx.x % a.P, grp = blockIdx.x / a.P;
+  const int r0 = grp * NBW, nb = min(NBW, a.nrhs - r0);
+  const int mc = a.mc, mcr = a.mcr;
+  const int A = a.ca[chunk], L = a.cb[chunk] - A + 1;
+  const int nsteps = 2 * L - 1;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* tv = reinterpret_cast<C*>(smraw);   // [mc][NBW]: T_j
+  C* yb = tv + (size_t)mc * NBW;         // [2][mc][NBW]: the blocks of the last two steps
+  auto block_of = [&](int q) { return q < L ? A + q : A + (2 * L - 2 - q); };
+  ptx::grid_dep_wait();
+  ptx::grid_dep_launch();
+  for (int q = 0; q < nsteps; ++q) {
+    const bool fwd = q < L;
+    const int j = block_of(q);
+    const C* prev = yb + (size_t)((q - 1) & 1) * mc * NBW;
+    C* cur = yb + (size_t)(q & 1) * mc * NBW;
+    const size_t oc = (size_t)(fwd ? j - 1 : j) * mc;
+    for (int i = tid; i < mc * NBW; i += nth) {
+      const int k = i / NBW, r = i - k * NBW;
+      C v;
+      v.x = 0;
+      v.y = 0;
+      if (!fwd || q > 0) {
+        cmac(v, a.cd[oc + k], prev[i]);
+        if (fwd) {  // C_{j-1}^T
+          if (k > 0) cmac(v, a.cu[oc + k - 1], prev[i - NBW]);
+          if (k + 1 < mc) cmac(v, a.cl[oc + k + 1], prev[i + NBW]);
+        } else {    // C_j
+          if (k > 0) cmac(v, a.cl[oc + k], prev[i - NBW]);
+          if (k + 1 < mc) cmac(v, a.cu[oc + k], prev[i + NBW]);
+        }
+      }
+      if (fwd) {  // a ragged group repeats its last right-hand side
+        C t = a.b[(size_t)(r0 + min(r, nb - 1)) * a.Nc + (size_t)j * mc + k];
+        t.x -= v.x;
+        t.y -= v.y;
+        tv[i] = t;
+      } else {
+        tv[i] = v;
+      }
+    }
+    __syncthreads();
+    const C* g = a.Gt + (size_t)j * mc * mcr;
+    for (int rr = tid; rr < mc; rr += nth) {
+      C acc[NBW];
+#pragma unroll
+      for (int r = 0; r < NBW; ++r) {
+        acc[r].x = 0;
+        acc[r].y = 0;
+      }
+      int c = 0;
+      for (; c + 8 <= mc; c += 8) {
+        C gv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) gv[u] = g[(size_t)(c + u) * mcr + rr];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const C* tc = tv + (size_t)(c + u) * NBW;
+#pragma unroll
+          for (int r = 0; r < NBW; ++r) cmac(acc[r], gv[u], tc[r]);
+        }
+      }
+      for (; c < mc; ++c) {
+        const C gc = g[(size_t)c * mcr + rr];
+        const C* tc = tv + (size_t)c * NBW;
+#pragma unroll
+        for (int r = 0; r < NBW; ++r) cmac(acc[r], gc, tc[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < NBW; ++r) {
+        C* xo = a.x + (size_t)(r0 + r) * a.Nc + (size_t)j * mc + rr;
+        C val = acc[r];
+        if (!fwd) {
+          C z;
+          z.x = 0;
+          z.y = 0;
+          if (r < nb) z = *xo;  // the padded columns of a ragged group are never stored
+          val.x = z.x - acc[r].x;
+          val.y = z.y - acc[r].y;
+        }
+        cur[(size_t)rr * NBW + r] = val;
+        if (r < nb) *xo = val;  // z_j forward, y_j backward (y_{A+L-1} = z_{A+L-1})
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Tall-skinny products of the reduced solve and of the spike correction, for
 // one right-hand side or a tile of NB:
 //   MODE 0: xhat = Sinv rhat, written into the separator rows of x (one CTA per
@@ -987,11 +1093,33 @@ static cudaError_t launch_coarse_part_mr(const CoarsePartArgs<T>& a, int cluster
   return cudaErrorInvalidValue;
 }
 
+// many right-hand sides in groups of NBW per CTA (one CTA per chunk and group),
+// then the reduced system and the spike correction on tiles of right-hand sides
+template <typename T, int NBW>
+static cudaError_t launch_coarse_part_cols(const CoarsePartArgs<T>& a, cudaStream_t s) {
+  using C = typename Cx<T>::t;
+  const size_t smem = sizeof(C) * (size_t)3 * a.mc * NBW;
+  if (smem > 227 * 1024 || a.mc > 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_cols<T, NBW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int groups = (a.nrhs + NBW - 1) / NBW;
+  e = launch_pdl(k_sweep_cols<T, NBW>, dim3(a.P * groups), dim3(512), smem, s, 0, a);
+  if (e != cudaSuccess || a.P < 2) return e;
+  dim3 g1((unsigned)((a.nred + 255) / 256), a.nrhs);
+  e = launch_pdl(k_reduced_rhs<T>, g1, dim3(256), 0, s, 0, a);
+  if (e != cudaSuccess) return e;
+  return launch_tsgemm<T, mr_tile<T>()>(a, s);
+}
+
 template <typename T>
 cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster, cudaStream_t s) {
   if (nrhs >= 2 && a.Gt) {
     CoarsePartArgs<T> b = a;
     b.nrhs = nrhs;
+    if (a.multi_variant == 1 && nrhs >= 8) {
+      const cudaError_t e = launch_coarse_part_cols<T, 8>(b, s);
+      if (e != cudaErrorInvalidValue) return e;
+    }
     return launch_coarse_part_mr<T>(b, cluster, s);
   }
   const bool pf = chunk_sweep_smem(a, true) <= 220 * 1024;

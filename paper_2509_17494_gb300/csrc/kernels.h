@@ -216,6 +216,7 @@ struct CoarsePartArgs {
   int sweep_variant;             // one-rhs chunk sweep: 0 two-phase (512 threads), 1 one barrier per step (1024),
                                  // 2 st.async row exchange on mbarriers (no cluster barrier per step)
   int* err;                      // device flag set by a bounded wait that gave up (variant 2)
+  int multi_variant;             // 8 or more right-hand sides: 0 per-tile cluster sweep, 1 column groups per CTA
 };
 template <typename T>
 cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster, cudaStream_t s);

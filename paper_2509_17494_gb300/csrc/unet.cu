@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "ptx.cuh"
@@ -103,7 +104,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_umma(const ConvArgs a)
         const int s = t % kStages, use = t / kStages;
         if (!ptx::mbar_wait_shared_flag(empty + s, (unsigned)((use & 1) ^ 1), &failed, lim)) return;
         ptx::mbar_arrive_expect_tx(full + s, b_bytes);
-        ptx::bulk_g2s(bbuf + (size_t)s * b_bytes, a.w + (size_t)t * b_bytes, b_bytes, full + s);
+        const size_t wchunk = (size_t)(a.wrows ? a.wrows : cout) * kUnits * 16u;  // bytes per packed chunk
+        ptx::bulk_g2s(bbuf + (size_t)s * b_bytes, a.w + (size_t)t * wchunk, b_bytes, full + s);
         issued = t + 1;
       };
       // D f32, A/B bf16, both K-major, N = cout, M = 128
@@ -550,15 +552,31 @@ size_t conv_smem_bytes(int cout) {
 int conv_chunks(int c8) { return (9 * c8 + kUnits - 1) / kUnits; }
 size_t packed_weight_elems(int rows, int c8) { return (size_t)conv_chunks(c8) * rows * kUnits * 8; }
 
+// One tcgen05 MMA has N <= 256: wider outputs (the input gradient of a decoder
+// convolution, whose output channels are the concatenation's 3 C) run as
+// launches over output-channel ranges of at most 256, each reading its rows of
+// every packed weight chunk and writing its channel range.
 cudaError_t launch_conv_umma(const ConvArgs& a, cudaStream_t s) {
-  if (a.cout < 16 || a.cout > 256 || (a.cout & 15)) return cudaErrorInvalidValue;
+  if (a.cout < 16 || (a.cout & 15) || a.cout > 1024) return cudaErrorInvalidValue;
   if ((a.xs & 7) || (a.xo & 7)) return cudaErrorInvalidValue;
-  const size_t smem = conv_smem_bytes(a.cout);
-  cudaError_t e = cudaFuncSetAttribute(k_conv_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const long long npix = (long long)a.B * a.H * a.W;
-  k_conv_umma<<<(unsigned)((npix + 127) / 128), kConvThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  for (int c0 = 0; c0 < a.cout; c0 += 256) {
+    ConvArgs b = a;
+    b.cout = std::min(256, a.cout - c0);
+    b.wrows = a.wrows ? a.wrows : a.cout;
+    b.w = a.w + (size_t)c0 * kUnits * 16u;  // rows c0.. of each chunk (rows are 8-row groups, row-group major)
+    if (a.bias) b.bias = a.bias + c0;
+    b.zo = a.zo + c0;
+    b.ao = a.ao + c0;
+    b.yo = a.yo + c0;
+    const size_t smem = conv_smem_bytes(b.cout);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_conv_umma<<<(unsigned)((npix + 127) / 128), kConvThreads, smem, s>>>(b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_pack_weights(const float* w, __nv_bfloat16* out, int cout, int cin, int c8, int transpose,

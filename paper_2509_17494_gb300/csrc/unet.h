@@ -15,7 +15,8 @@ struct ConvArgs {
   int B, H, W;             // batch and spatial size
   int C8;                  // input channel units of 8 (channels padded to 8 C8)
   int nchunk;              // conv_chunks(C8)
-  int cout;                // output channels, multiple of 16, <= 256
+  int cout;                // output channels, multiple of 16 (more than 256: several launches)
+  int wrows;               // rows of each packed weight chunk (0: cout); a launch reads rows [0, cout) of them
   int mode;                // 0: z = acc + bias and act = silu(z) as BF16; 1: y = acc as FP32
   __nv_bfloat16* z;        // mode 0 outputs: z[p * zs + zo + c], act[p * as + ao + c]
   int zs, zo;

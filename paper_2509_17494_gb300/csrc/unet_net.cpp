@@ -25,8 +25,10 @@ namespace {
 
 int UNet::check(int levels, int base) {
   if (levels < 2 || levels > 6 || base < 16 || (base & 15)) return 0;
+  // the widest forward output (the bottom level) must fit one MMA (N <= 256);
+  // input gradients wider than that (decoder concatenations) are split
   const int top = base << (levels - 1);
-  if (top > 256 || (base << (levels - 2)) * 3 > 256) return 0;
+  if (top > 256 || (base << (levels - 2)) * 3 > 1024) return 0;
   return 1;
 }
 

@@ -179,6 +179,31 @@ def test_coarse_solve_many_rhs(th, c, nrhs):
     assert np.array_equal(again, got32)
 
 
+@pytest.mark.parametrize("c", [CASES[0], CASES[2], CASES[5]])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_coarse_solve_column_groups(th, c, prec):
+    """Eight or more right-hand sides: the sweep in groups of 8 per CTA (variant
+    1, default) and the per-tile cluster sweep (variant 0), on two full groups
+    and a ragged one, against the oracle's banded LU (FP64 1e-9, FP32 1e-4)."""
+    nrhs = 20
+    extra = ("fp64",) if prec != "fp64" else ()
+    S, P = build(th, c, nrhs=nrhs, prec=prec, extra_prec=extra)
+    assert S.get_variant("coarse_multi", prec) == 1
+    rc = synth.random_complex((nrhs, P.Nc), 33)
+    B = twogrid.BandedSolver(P.Aq)
+    want = np.stack([B.solve(rc[i]) for i in range(nrhs)])
+    tol = 1e-9 if prec == "fp64" else 1e-4
+    outs = []
+    for v in (1, 0):
+        S.set_variant("coarse_multi", prec, v)
+        outs.append(host(S.coarse_solve(dev(rc))))
+        S.device_status()
+        for i in range(nrhs):
+            assert relerr(outs[-1][i], want[i]) < tol, (v, i)
+    again = host(S.coarse_solve(dev(rc)))
+    assert np.array_equal(again, outs[-1])
+
+
 @pytest.mark.parametrize("c", CASES)
 @pytest.mark.parametrize("n_s,omega_c", [(1, 1.0), (2, 0.8)])
 def test_cycle_fp64(th, c, n_s, omega_c):

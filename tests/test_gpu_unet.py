@@ -175,3 +175,35 @@ def test_learned_corrector_in_fgmres(case, th):
     _, free = S.solve(f, check=False)
     S.set_coarse("direct")
     assert free["fallbacks"] == 0
+
+
+def test_32_channel_network_matches_oracle(th):
+    """The configuration-4 width: 4 levels of 32 base channels.  The decoder's
+    widest concatenation (128 + 256 = 384 channels) makes its input gradient an
+    MMA of N = 384 > 256, run as two launches over output-channel ranges."""
+    w = synth.workload("square10_q4_n25")
+    S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=0.5, l_dd=2, prec="bf16",
+                         extra_prec=("fp64",), nrhs_max=2, device=DEV)
+    shapes = th.unet_param_shapes(4, 32)
+    assert shapes == ounet.param_shapes(4, 32)
+    params0 = synth.he_normal(shapes, 78)
+    S.unet_init(params0, levels=4, base=32, batch_max=2)
+    mp = S.unet_mp
+    r = synth.rng(5)
+    x = r.standard_normal((2, mp, mp, 3)).astype(np.float32)
+    gout = r.standard_normal((2, mp, mp, 2)).astype(np.float32)
+    got = S.unet_forward(torch.from_numpy(x).to(DEV)).cpu().numpy()
+    grads = S.unet_backward(torch.from_numpy(gout).to(DEV)).cpu().numpy()
+    S.device_status()
+    P = unflatten(bf16_round(params0), shapes)
+    for k in P:
+        if k.endswith(".b") or k.startswith("head"):
+            P[k] = unflatten(params0, shapes)[k]
+    want, cache = ounet.forward(P, bf16_round(x), 4)
+    assert np.abs(got - want).max() / np.abs(want).max() < 3e-2
+    gw = ounet.backward(P, cache, gout.astype(np.float64), 4)
+    G = unflatten(grads, shapes)
+    for name, _ in shapes:
+        e = np.linalg.norm(G[name] - gw[name]) / max(np.linalg.norm(gw[name]), 1e-30)
+        assert e < 5e-2, (name, e)
+    S.close()
