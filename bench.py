@@ -94,6 +94,8 @@ def parse():
                     help="FP32 one-rhs coarse sweep: auto, 0 two phases, 1 one cluster barrier per step, "
                          "2 st.async row exchange")
     ap.add_argument("--learned-steps", type=int, default=400, help="training steps of the learned section (0: skip)")
+    ap.add_argument("--learned-c4-pairs", type=int, default=0,
+                    help="training pairs of the corrector on the 401^2 coarse grid, 32 channels (0: skip)")
     ap.add_argument("--dim3", choices=["cube10_q2_n40", "cube2_q2_n8", "none"], default="cube10_q2_n40",
                     help="3-D workload of the three-dimensional section")
     ap.add_argument("--table1", action="store_true",
@@ -429,6 +431,8 @@ def run_native(args):
         line["mixed_batch"] = mixed_batch_section(dev, world)
     if args.learned_steps > 0:
         line["learned"] = learned_section(args, dev)
+    if args.learned_c4_pairs > 0:
+        line["learned_c4"] = learned_c4_section(args, dev)
     if args.dim3 != "none":
         line["dim3"] = dim3_section(args, dev, world)
     if args.table1:
@@ -934,6 +938,106 @@ def learned_section(args, dev):
            "loss_last10": round(float(np.mean(losses[-10:])), 4), "heldout_relerr": round(held, 4),
            "correct_ms_1rhs": round(e0.elapsed_time(e1) / 20, 4),
            "iters": {k: v["iters"] for k, v in res.items()},
+           "converged": {k: v["converged"] for k, v in res.items()},
+           "fallbacks": res["learned_with_fallback"]["fallbacks"]}
+    S.close()
+    return out
+
+
+def learned_c4_section(args, dev):
+    """The learned corrector at the size of its specification: the 401^2 coarse
+    grid of the 80-wavelength Q4 problem (801^2 fine dofs, random k-field), a
+    U-Net of 4 levels and 32 base channels, trained on the GPU on pairs (r_c,
+    A_q^{-1} r_c) from the FP64 direct coarse solve (half restricted residuals of
+    random fine right-hand sides after one smoothing step, half smooth random
+    coarse fields), 8 pairs per Adam step, each pair used once; then FGMRES
+    iterations and time to 1e-8 with the direct solve, with no correction, with
+    the corrector alone and with the fallback at 1.5x the plain count."""
+    import numpy as np
+    import torch
+
+    import paper_2509_17494_gb300 as th
+    import synth
+
+    w = synth.workload("square80_q4_n200")
+    t0 = time.time()
+    S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=0.5, l_dd=2, prec="bf16", extra_prec=("fp64",),
+                         nrhs_max=64, restart=60, maxit=400, device=dev)
+    setup_s = time.time() - t0
+    levels, base, B = 4, 32, 8
+    S.unet_init(synth.he_normal(th.unet_param_shapes(levels, base), 77), levels=levels, base=base, batch_max=16)
+    m = S.n * S.p // 2 + 1
+    npairs = args.learned_c4_pairs
+    gen = 64   # pairs per generation batch (one coarse solve of 64 right-hand sides)
+
+    def pairs(count, seed):
+        half = count // 2
+        f = torch.from_numpy(synth.random_complex((half, S.N), seed)).to(dev)
+        S.set_precision("fp64")
+        u = torch.zeros_like(f)
+        S.smooth(f, u)
+        rc1 = S.restrict(S.residual(f, u))
+        del f, u
+        rc2 = torch.from_numpy(synth.smooth_coarse_noise(m, count - half, seed + 1)).to(dev)
+        rc = torch.cat([rc1, rc2]).contiguous()
+        uc = S.coarse_solve(rc)
+        S.set_precision("bf16")
+        return rc, uc
+
+    t1 = time.time()
+    losses, gen_s, seen = [], 0.0, 0
+    steps = npairs // B
+    for it in range(steps):
+        if it % (gen // B) == 0:
+            tg = time.time()
+            rc, uc = pairs(gen, 5000 + it)
+            torch.cuda.synchronize(dev)
+            gen_s += time.time() - tg
+        k = (it % (gen // B)) * B
+        lr = 1e-3 if it < 0.7 * steps else 2.5e-4
+        losses.append(S.unet_train_step(rc[k:k + B].contiguous(), uc[k:k + B].contiguous(), lr=lr))
+        seen += B
+    torch.cuda.synchronize(dev)
+    train_s = time.time() - t1
+    rc, uc = pairs(16, 424242)
+    uh = S.unet_correct(rc)
+    held = float((torch.linalg.vector_norm(uh - uc, dim=1) / torch.linalg.vector_norm(uc, dim=1)).mean())
+    f = torch.from_numpy(np.ascontiguousarray(w["f"][0])).to(dev)
+    res = {}
+    S.set_coarse("direct")
+    res["direct"] = S.solve(f)[1]
+    S.set_coarse("none")
+    res["none"] = S.solve(f, check=False)[1]
+    S.set_coarse("learned", 0)
+    res["learned"] = S.solve(f, check=False)[1]
+    S.set_coarse("learned", res["direct"]["iters"])
+    res["learned_with_fallback"] = S.solve(f, check=False)[1]
+    S.set_coarse("direct")
+    r1 = rc[:1].contiguous()
+
+    def time_it(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    correct_ms = time_it(lambda: S.unet_correct(r1))
+    direct_ms = time_it(lambda: S.coarse_solve(r1))
+    out = {"workload": "square80_q4_n200 (coarse grid 401^2)",
+           "network": f"U-Net {levels} levels, base {base} channels, BF16 weights, FP32 accumulation",
+           "params": th.unet_param_count(levels, base), "setup_s": round(setup_s, 1),
+           "pairs": seen, "batch": B, "adam_steps": steps, "pair_generation_s": round(gen_s, 1),
+           "train_s_total": round(train_s, 1), "loss_first20": round(float(np.mean(losses[:20])), 4),
+           "loss_last20": round(float(np.mean(losses[-20:])), 4), "heldout_relerr": round(held, 4),
+           "correct_ms_1rhs": round(correct_ms, 3), "direct_coarse_solve_ms_1rhs": round(direct_ms, 3),
+           "iters": {k: v["iters"] for k, v in res.items()},
+           "time_to_tol_ms": {k: round(v["ms_total"], 2) for k, v in res.items()},
            "converged": {k: v["converged"] for k, v in res.items()},
            "fallbacks": res["learned_with_fallback"]["fallbacks"]}
     S.close()

@@ -412,8 +412,10 @@ th_status th_peak_fma(int prec, int iters, double* flops_per_s, void* stream);
  *              (it may be scheduled while that one drains, and waits for it
  *              before touching shared data; not while th_profile records);
  *   TH_K_COARSE_MULTI: the 2-D coarse chunk sweep for 8 or more right-hand
- *              sides: 1 (default) one CTA per chunk and group of 8 right-hand
- *              sides, each G_j streamed once for all groups through L2; 0 one
+ *              sides: 1 (default) one CTA per chunk and group of 8 to 16
+ *              right-hand sides (the narrowest group that keeps the chunks x
+ *              groups within one CTA per SM), each G_j streamed once for all
+ *              groups through L2; 0 one
  *              thread-block cluster per chunk and tile of 2-8 right-hand sides
  *              (the tile count multiplies the G_j reads); prec is ignored;
  *   TH_K_COARSE_SOLVE: one-right-hand-side chunk sweep of the 2-D coarse

@@ -342,10 +342,6 @@ th_status prepare(const th_mesh* mesh, const th_params* prm, th_ctx& x) {
   x.cluster = 8;
   x.rpc = (x.g.mc + x.cluster - 1) / x.cluster;
   x.P = x.g.dim == 2 ? th::coarse_chunks(x.g.mc) : 1;
-  // large coarse grids: at most 19 chunks, so that the many-right-hand-side
-  // sweep's P x 8 CTAs (groups of 8 right-hand sides, 64 at once) fill the
-  // 152 SMs in one wave
-  if (x.g.dim == 2 && x.g.mc > 256) x.P = std::min(x.P, 19);
   x.mcp = x.g.mc + (x.g.mc & 1);
   x.rpcm = x.rpc + (x.rpc & 1);
   x.mcr = x.cluster * x.rpcm;
@@ -776,6 +772,7 @@ th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th:
   a.nrhs = nrhs;
   a.sweep_variant = x.cs_variant;
   a.multi_variant = x.cs_multi;
+  a.nsm = x.sms;
   a.err = x.derr;
   if (!a.G || !a.LR) return TH_ERR_UNSUPPORTED;
   x.launches += (x.P > 1) ? 4 : 1;

@@ -721,7 +721,8 @@ __global__ void __launch_bounds__(512, 1) k_chunk_sweep_mr(const CoarsePartArgs<
 }
 
 // ------------------------------------------------------------- wide tiles of right-hand sides
-// The chunk sweep for a group of NBW right-hand sides per CTA: one CTA per
+// The chunk sweep for a group of NBW right-hand sides per CTA (NBW from 8 to 16,
+// the narrowest that keeps P x groups within one CTA per SM): one CTA per
 // (chunk, group), no cluster.  A thread owns rows of the block (row rr for
 // rr = tid, tid + blockDim, ...) and NBW accumulators; it streams its row's
 // entries of the transposed G_j (consecutive across lanes, through L2: the
@@ -1117,7 +1118,14 @@ cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster
     CoarsePartArgs<T> b = a;
     b.nrhs = nrhs;
     if (a.multi_variant == 1 && nrhs >= 8) {
-      const cudaError_t e = launch_coarse_part_cols<T, 8>(b, s);
+      // the narrowest group width with at most one CTA per SM: P * ceil(nrhs / NBW) <= SMs
+      const int per = std::max(1, (a.nsm > 0 ? a.nsm : 152) / std::max(1, a.P));
+      const int need = (nrhs + per - 1) / per;
+      cudaError_t e = cudaErrorInvalidValue;
+      if (need <= 8) e = launch_coarse_part_cols<T, 8>(b, s);
+      else if (need <= 10) e = launch_coarse_part_cols<T, 10>(b, s);
+      else if (need <= 12) e = launch_coarse_part_cols<T, 12>(b, s);
+      else if (need <= 16) e = launch_coarse_part_cols<T, 16>(b, s);
       if (e != cudaErrorInvalidValue) return e;
     }
     return launch_coarse_part_mr<T>(b, cluster, s);

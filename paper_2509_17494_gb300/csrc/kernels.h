@@ -217,6 +217,7 @@ struct CoarsePartArgs {
                                  // 2 st.async row exchange on mbarriers (no cluster barrier per step)
   int* err;                      // device flag set by a bounded wait that gave up (variant 2)
   int multi_variant;             // 8 or more right-hand sides: 0 per-tile cluster sweep, 1 column groups per CTA
+  int nsm;                       // SMs of the device (column groups are sized to fill them in one wave)
 };
 template <typename T>
 cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster, cudaStream_t s);

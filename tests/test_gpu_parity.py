@@ -440,6 +440,31 @@ def test_mixed_outer_residual_double_single(th, c):
     assert relerr(got1, got0) < 2e-7
 
 
+def test_coarse_solve_column_groups_large_grid(th):
+    """64 right-hand sides on a 401^2 coarse grid (20 chunks): groups of 10 per
+    CTA (7 groups, the last one ragged) so that 20 x 7 CTAs fit the SMs once;
+    FP64 against the FP64 one-right-hand-side solve, FP32 within its own
+    accuracy on this grid, and both by the coarse residual."""
+    n, p = 200, 4
+    k = synth.random_wavenumber(n, 2, 20.0, seed=5)
+    eps = synth.absorbing_layer(n, 2, p, k, 10.0)
+    S = th.TwoGridSolver(n, p, k, eps, alpha_s=0.5, l_dd=4, prec="fp32", extra_prec=("fp64",), nrhs_max=64,
+                         restart=2, device=DEV)
+    rc = dev(synth.random_complex((64, S.Nc), 82))
+    S.set_precision("fp64")
+    many = S.coarse_solve(rc)
+    S.device_status()
+    one = torch.stack([S.coarse_solve(rc[i].contiguous()) for i in (0, 37, 63)])
+    assert relerr(host(many)[[0, 37, 63]], host(one)) < 1e-10
+    res = S.apply(many, "Aq") - rc
+    assert float(torch.linalg.norm(res) / torch.linalg.norm(rc)) < 1e-9
+    S.set_precision("fp32")
+    m32 = S.coarse_solve(rc)
+    S.device_status()
+    for i in range(64):
+        assert relerr(host(m32[i]), host(many[i])) < 5e-3, i
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_coarse_solve_many_rhs_large_grid(th, prec):
     """A 401^2 coarse grid (200^2 Q4 cells): the multi-rhs sweep takes narrower
