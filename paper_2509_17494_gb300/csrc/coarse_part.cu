@@ -995,21 +995,22 @@ __global__ void __launch_bounds__(512) k_coarse_tsgemm(const CoarsePartArgs<T> a
   }
 }
 
-template <typename T, int NB>
+// separator product on tiles of NB0 right-hand sides, spike correction on tiles of NB1
+template <typename T, int NB0, int NB1 = NB0>
 static cudaError_t launch_tsgemm(const CoarsePartArgs<T>& a, cudaStream_t s) {
   using C = typename Cx<T>::t;
-  const int ntiles = (a.nrhs + NB - 1) / NB;
-  const size_t sm0 = sizeof(C) * (size_t)NB * (NB == 1 ? a.ldS : 1024), sm1 = sizeof(C) * (size_t)NB * 2 * a.mcp;
-  cudaError_t e = cudaFuncSetAttribute(k_coarse_tsgemm<T, NB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const int nt0 = (a.nrhs + NB0 - 1) / NB0, nt1 = (a.nrhs + NB1 - 1) / NB1;
+  const size_t sm0 = sizeof(C) * (size_t)NB0 * (NB0 == 1 ? a.ldS : 1024), sm1 = sizeof(C) * (size_t)NB1 * 2 * a.mcp;
+  cudaError_t e = cudaFuncSetAttribute(k_coarse_tsgemm<T, NB0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm0);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_coarse_tsgemm<T, NB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+  e = cudaFuncSetAttribute(k_coarse_tsgemm<T, NB1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
   if (e != cudaSuccess) return e;
-  const unsigned g0 = (unsigned)((a.nred + 15) / 16) * ntiles;
-  e = launch_pdl(k_coarse_tsgemm<T, NB, 0>, dim3(g0), dim3(512), sm0, s, 0, a);
+  const unsigned g0 = (unsigned)((a.nred + 15) / 16) * nt0;
+  e = launch_pdl(k_coarse_tsgemm<T, NB0, 0>, dim3(g0), dim3(512), sm0, s, 0, a);
   if (e != cudaSuccess) return e;
-  const unsigned g1 = (unsigned)((NB == 1 ? 4 : 2) * a.mc) * ntiles;
-  return launch_pdl(k_coarse_tsgemm<T, NB, 1>, dim3(g1), dim3(512), sm1, s, 0, a);
+  const unsigned g1 = (unsigned)((NB1 == 1 ? 4 : 2) * a.mc) * nt1;
+  return launch_pdl(k_coarse_tsgemm<T, NB1, 1>, dim3(g1), dim3(512), sm1, s, 0, a);
 }
 
 // ------------------------------------------------------------- launcher
@@ -1109,6 +1110,10 @@ static cudaError_t launch_coarse_part_cols(const CoarsePartArgs<T>& a, cudaStrea
   dim3 g1((unsigned)((a.nred + 255) / 256), a.nrhs);
   e = launch_pdl(k_reduced_rhs<T>, g1, dim3(256), 0, s, 0, a);
   if (e != cudaSuccess) return e;
+  // the separator product on tiles of 16 right-hand sides (FP32): each row of the
+  // reduced inverse serves 16 of them (the spike products keep tiles of 8, whose
+  // two rows x 8 accumulators per lane fit the registers)
+  if (sizeof(T) == 4 && a.nrhs >= 16) return launch_tsgemm<T, 16, mr_tile<T>()>(a, s);
   return launch_tsgemm<T, mr_tile<T>()>(a, s);
 }
 
