@@ -96,6 +96,7 @@ struct th_ctx {
   int rpcm = 0, mcr = 0;
   double2* Gt64 = nullptr;
   float2* Gt32 = nullptr;
+  float2* LRt32 = nullptr;  // spikes transposed ([j][col][mcr]) for the grouped FP32 spike correction (nrhs_max >= 8)
   // cycle work vectors
   double2 *r64 = nullptr, *s64 = nullptr, *v64 = nullptr, *V64 = nullptr, *rc64 = nullptr, *uc64 = nullptr,
           *zc64 = nullptr, *t64 = nullptr;
@@ -283,6 +284,7 @@ void carve_all(th_ctx& x, Carve& c) {
       x.Si32 = c.take<float2>(nred * (nred + (nred & 1)));
       x.rh32 = c.take<float2>(nred * nr);
       if (nr >= 2) x.Gt32 = c.take<float2>(mm * x.mcr);
+      if (nr >= 8) x.LRt32 = c.take<float2>((size_t)g.mc * 2 * x.mcp * x.mcr);
     }
     x.f32 = c.take<float2>((size_t)nr * g.N);
     x.u32 = c.take<float2>((size_t)nr * g.N);
@@ -767,6 +769,7 @@ th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th:
   a.rpc = x.rpc;
   a.Lmax = x.Lmax;
   a.Gt = B::Gt(x);
+  if constexpr (std::is_same<T, float>::value) a.LRt = x.LRt32;
   a.mcr = x.mcr;
   a.rpcm = x.rpcm;
   a.nrhs = nrhs;
@@ -1336,6 +1339,16 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     if ((st = upload_c(x->Gt64, x->Gt32, gt)) != TH_OK) return st;
   }
   if ((st = upload_c(x->LR64, x->LR32, cpart.LR)) != TH_OK) return st;
+  if (x->LRt32) {
+    // LRt[j][col][row] = LR[j][row][col], rows padded to mcr
+    const size_t mcr = (size_t)x->mcr, K = 2 * (size_t)x->mcp;
+    std::vector<cplx> lt((size_t)g.mc * K * mcr, cplx(0.0));
+    th::parallel_for(g.mc, [&](int j) {
+      for (int row = 0; row < g.mc; ++row)
+        for (size_t c = 0; c < K; ++c) lt[((size_t)j * K + c) * mcr + row] = cpart.LR[((size_t)j * g.mc + row) * K + c];
+    });
+    if ((st = upload_c(nullptr, x->LRt32, lt)) != TH_OK) return st;
+  }
   if (x->P > 1 && (x->Si64 || x->Si32)) {
     // rows padded to an even length (pairs of complex values per load)
     const size_t nr_ = (size_t)x->nred, ld = nr_ + (nr_ & 1);

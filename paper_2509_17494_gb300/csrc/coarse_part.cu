@@ -827,6 +827,76 @@ __global__ void __launch_bounds__(512, 1) k_sweep_cols(const CoarsePartArgs<T> a
   }
 }
 
+// The spike correction x_j -= [L_j | R_j] [x_left; x_right] for a group of NBW
+// right-hand sides per CTA, from the spikes stored transposed (LRt[j][col][row],
+// rows padded to mcr): one CTA per (chunk row j, group), the groups of one j
+// adjacent in the grid so that they read LRt[j] together through L2; a thread
+// owns a row and NBW accumulators and reads its row's entries (consecutive
+// across lanes) and the separator values of its group from shared memory.
+template <typename T, int NBW>
+__global__ void __launch_bounds__(512) k_spikes_cols(const CoarsePartArgs<T> a) {
+  using C = typename Cx<T>::t;
+  ptx::grid_dep_wait();  // launched with a programmatic dependency inside the cycle
+  ptx::grid_dep_launch();
+  const int groups = (a.nrhs + NBW - 1) / NBW;
+  const int j = blockIdx.x / groups, grp = blockIdx.x - j * groups;
+  const int chunk = a.chunk_of[j];
+  if (chunk < 0) return;  // a separator row (uniform over the CTA)
+  const int r0 = grp * NBW, nb = min(NBW, a.nrhs - r0);
+  const int mc = a.mc, mcp = a.mcp, K = 2 * mcp;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* xs = reinterpret_cast<C*>(smraw);  // [K][NBW]
+  for (int i = tid; i < K * NBW; i += nth) {
+    const int col = i / NBW, r = i - col * NBW;
+    const int side = col >= mcp ? 1 : 0, k = col - side * mcp;
+    const bool has = r < nb && k < mc && (side == 0 ? chunk > 0 : chunk < a.P - 1);
+    C v;
+    v.x = 0;
+    v.y = 0;
+    if (has) v = a.x[(size_t)(r0 + r) * a.Nc + (size_t)a.sep[side == 0 ? chunk - 1 : chunk] * mc + k];
+    xs[i] = v;
+  }
+  __syncthreads();
+  const C* lr = a.LRt + (size_t)j * K * a.mcr;
+  for (int rr = tid; rr < mc; rr += nth) {
+    C acc[NBW];
+#pragma unroll
+    for (int r = 0; r < NBW; ++r) {
+      acc[r].x = 0;
+      acc[r].y = 0;
+    }
+    int c = 0;
+    for (; c + 8 <= K; c += 8) {
+      C lv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) lv[u] = lr[(size_t)(c + u) * a.mcr + rr];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const C* xc = xs + (size_t)(c + u) * NBW;
+#pragma unroll
+        for (int r = 0; r < NBW; ++r) cmac(acc[r], lv[u], xc[r]);
+      }
+    }
+    for (; c < K; ++c) {
+      const C lc = lr[(size_t)c * a.mcr + rr];
+      const C* xc = xs + (size_t)c * NBW;
+#pragma unroll
+      for (int r = 0; r < NBW; ++r) cmac(acc[r], lc, xc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < NBW; ++r) {
+      if (r < nb) {
+        C* xo = a.x + (size_t)(r0 + r) * a.Nc + (size_t)j * mc + rr;
+        C v = *xo;
+        v.x -= acc[r].x;
+        v.y -= acc[r].y;
+        *xo = v;
+      }
+    }
+  }
+}
+
 // Tall-skinny products of the reduced solve and of the spike correction, for
 // one right-hand side or a tile of NB:
 //   MODE 0: xhat = Sinv rhat, written into the separator rows of x (one CTA per
@@ -1110,6 +1180,25 @@ static cudaError_t launch_coarse_part_cols(const CoarsePartArgs<T>& a, cudaStrea
   dim3 g1((unsigned)((a.nred + 255) / 256), a.nrhs);
   e = launch_pdl(k_reduced_rhs<T>, g1, dim3(256), 0, s, 0, a);
   if (e != cudaSuccess) return e;
+  // the spike correction in the same groups from the transposed spikes when the
+  // context keeps them; else the tiled products (below)
+  if (a.LRt) {
+    using C = typename Cx<T>::t;
+    constexpr int NB0 = sizeof(T) == 4 ? 16 : mr_tile<T>();
+    const int nt0 = (a.nrhs + NB0 - 1) / NB0;
+    const size_t sm0 = sizeof(C) * (size_t)NB0 * 1024, sm1 = sizeof(C) * (size_t)2 * a.mcp * NBW;
+    if (sm1 <= 220 * 1024) {
+      e = cudaFuncSetAttribute(k_coarse_tsgemm<T, NB0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0);
+      if (e != cudaSuccess) return e;
+      e = launch_pdl(k_coarse_tsgemm<T, NB0, 0>, dim3((unsigned)((a.nred + 15) / 16) * nt0), dim3(512), sm0, s, 0,
+                     a);
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(k_spikes_cols<T, NBW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+      if (e != cudaSuccess) return e;
+      const int groups = (a.nrhs + NBW - 1) / NBW;
+      return launch_pdl(k_spikes_cols<T, NBW>, dim3((unsigned)(a.mc * groups)), dim3(512), sm1, s, 0, a);
+    }
+  }
   // the separator product on tiles of 16 right-hand sides (FP32): each row of the
   // reduced inverse serves 16 of them (the spike products keep tiles of 8, whose
   // two rows x 8 accumulators per lane fit the registers)

@@ -209,6 +209,8 @@ struct CoarsePartArgs {
   const int* chunk_of;           // per row: chunk index, or -1 for a separator
   // multi-right-hand-side sweep: G_j transposed, [j][column][mcr] (rows padded to mcr = cluster * rpcm)
   const typename Cx<T>::t* Gt;
+  // spikes transposed, [j][col][mcr] (col < 2 mcp), for the grouped spike correction; or null
+  const typename Cx<T>::t* LRt;
   long long Nc;
   int mc, mcp, P, rpc, Lmax, nred;
   int mcr, rpcm, nrhs;           // rpcm: rows per CTA of the multi-rhs sweep (even)
