@@ -827,6 +827,73 @@ __global__ void __launch_bounds__(512, 1) k_sweep_cols(const CoarsePartArgs<T> a
   }
 }
 
+// The separator values xhat = Sinv rhat for a group of NBW right-hand sides per
+// CTA and a block of 256 separator unknowns.  The reduced system is the Schur
+// complement of the complex-symmetric A_q on the separator rows, so Sinv is
+// complex symmetric and its column rr is its row rr: a thread owns unknown rr
+// and reads Sinv[c][rr] over c (consecutive across lanes), with the group's
+// rhat[c][0..NBW-1] staged in shared memory in slices of 1024 columns.
+template <typename T, int NBW>
+__global__ void __launch_bounds__(256) k_sep_cols(const CoarsePartArgs<T> a) {
+  using C = typename Cx<T>::t;
+  constexpr int KS = 1024;
+  ptx::grid_dep_wait();  // launched with a programmatic dependency inside the cycle
+  ptx::grid_dep_launch();
+  const int groups = (a.nrhs + NBW - 1) / NBW;
+  const int blk = blockIdx.x / groups, grp = blockIdx.x - blk * groups;
+  const int r0 = grp * NBW, nb = min(NBW, a.nrhs - r0);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int rr = blk * 256 + tid;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* hs = reinterpret_cast<C*>(smraw);  // [KS][NBW]
+  C acc[NBW];
+#pragma unroll
+  for (int r = 0; r < NBW; ++r) {
+    acc[r].x = 0;
+    acc[r].y = 0;
+  }
+  for (int k0 = 0; k0 < a.nred; k0 += KS) {
+    const int kn = min(KS, a.nred - k0);
+    __syncthreads();
+    for (int i = tid; i < kn * NBW; i += nth) {
+      const int c = i / NBW, r = i - c * NBW;
+      C v;
+      v.x = 0;
+      v.y = 0;
+      if (r < nb) v = a.rhat[(size_t)(r0 + r) * a.nred + k0 + c];
+      hs[i] = v;
+    }
+    __syncthreads();
+    if (rr < a.nred) {
+      const C* sc = a.Sinv + (size_t)k0 * a.ldS + rr;
+      int c = 0;
+      for (; c + 8 <= kn; c += 8) {
+        C sv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sv[u] = sc[(size_t)(c + u) * a.ldS];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const C* hc = hs + (size_t)(c + u) * NBW;
+#pragma unroll
+          for (int r = 0; r < NBW; ++r) cmac(acc[r], sv[u], hc[r]);
+        }
+      }
+      for (; c < kn; ++c) {
+        const C sv = sc[(size_t)c * a.ldS];
+        const C* hc = hs + (size_t)c * NBW;
+#pragma unroll
+        for (int r = 0; r < NBW; ++r) cmac(acc[r], sv, hc[r]);
+      }
+    }
+  }
+  if (rr < a.nred) {
+    const int k = rr / a.mc, e = rr - k * a.mc;
+#pragma unroll
+    for (int r = 0; r < NBW; ++r)
+      if (r < nb) a.x[(size_t)(r0 + r) * a.Nc + (size_t)a.sep[k] * a.mc + e] = acc[r];
+  }
+}
+
 // The spike correction x_j -= [L_j | R_j] [x_left; x_right] for a group of NBW
 // right-hand sides per CTA, from the spikes stored transposed (LRt[j][col][row],
 // rows padded to mcr): one CTA per (chunk row j, group), the groups of one j
@@ -1184,25 +1251,18 @@ static cudaError_t launch_coarse_part_cols(const CoarsePartArgs<T>& a, cudaStrea
   // context keeps them; else the tiled products (below)
   if (a.LRt) {
     using C = typename Cx<T>::t;
-    constexpr int NB0 = sizeof(T) == 4 ? 16 : mr_tile<T>();
-    const int nt0 = (a.nrhs + NB0 - 1) / NB0;
-    const size_t sm0 = sizeof(C) * (size_t)NB0 * 1024, sm1 = sizeof(C) * (size_t)2 * a.mcp * NBW;
+    const int groups = (a.nrhs + NBW - 1) / NBW;
+    const size_t sm0 = sizeof(C) * (size_t)1024 * NBW, sm1 = sizeof(C) * (size_t)2 * a.mcp * NBW;
     if (sm1 <= 220 * 1024) {
-      e = cudaFuncSetAttribute(k_coarse_tsgemm<T, NB0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0);
+      e = cudaFuncSetAttribute(k_sep_cols<T, NBW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0);
       if (e != cudaSuccess) return e;
-      e = launch_pdl(k_coarse_tsgemm<T, NB0, 0>, dim3((unsigned)((a.nred + 15) / 16) * nt0), dim3(512), sm0, s, 0,
-                     a);
+      e = launch_pdl(k_sep_cols<T, NBW>, dim3((unsigned)((a.nred + 255) / 256 * groups)), dim3(256), sm0, s, 0, a);
       if (e != cudaSuccess) return e;
       e = cudaFuncSetAttribute(k_spikes_cols<T, NBW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
       if (e != cudaSuccess) return e;
-      const int groups = (a.nrhs + NBW - 1) / NBW;
       return launch_pdl(k_spikes_cols<T, NBW>, dim3((unsigned)(a.mc * groups)), dim3(512), sm1, s, 0, a);
     }
   }
-  // the separator product on tiles of 16 right-hand sides (FP32): each row of the
-  // reduced inverse serves 16 of them (the spike products keep tiles of 8, whose
-  // two rows x 8 accumulators per lane fit the registers)
-  if (sizeof(T) == 4 && a.nrhs >= 16) return launch_tsgemm<T, 16, mr_tile<T>()>(a, s);
   return launch_tsgemm<T, mr_tile<T>()>(a, s);
 }
 

@@ -112,3 +112,56 @@ def test_profiling_bypasses_graphs(th):
     p = S.profile_read()
     S.profile(False)
     assert p["dd"][1] >= 2 and p["coarse_solve"][1] >= 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_uneven_domains_concurrent_in_one_graph(th, prec):
+    """A mixed batch of independent domains of uneven size (6, 9 and 13 cells per
+    side, each its own random field, layer and source): one TwoGridStep of every
+    domain captured into one CUDA graph, each domain's launches on a stream of
+    its own (forked from and joined into the capture stream) so that they run
+    concurrently.  Every domain's result equals its own step launched alone,
+    bitwise, and (FP64) the oracle's TwoGridStep within 1e-9."""
+    from oracle import twogrid
+    from tests.common import small_case
+    doms = []
+    for i, n in enumerate((6, 9, 13)):
+        k, eps = small_case(n=n, p=4, W=n / 4.0, seed=20 + i)
+        extra = ("fp64",) if prec != "fp64" else ()
+        S = th.TwoGridSolver(n, 4, k, eps, alpha_s=0.5, l_dd=2, prec=prec, extra_prec=extra, device=DEV)
+        S.set_graphs(False)
+        f = synth.random_complex(S.N, 40 + i)
+        u = synth.random_complex(S.N, 50 + i)
+        doms.append((S, k, eps, f, u, n))
+    alone = []
+    for S, k, eps, f, u, n in doms:
+        alone.append(S.cycle(torch.from_numpy(f).to(DEV), torch.from_numpy(u.copy()).to(DEV)))
+    torch.cuda.synchronize()
+    main = torch.cuda.Stream()
+    sides = [torch.cuda.Stream() for _ in doms]
+    F = [torch.from_numpy(f).to(DEV) for (_, _, _, f, _, _) in doms]
+    U = [torch.from_numpy(u.copy()).to(DEV) for (_, _, _, _, u, _) in doms]
+    U0 = [x.clone() for x in U]
+    main.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=main):
+        for (S, *_), f, x, st in zip(doms, F, U, sides):
+            st.wait_stream(main)
+            with torch.cuda.stream(st):
+                S.cycle(f, x)
+        for st in sides:
+            main.wait_stream(st)
+    for x, x0 in zip(U, U0):   # the capture ran nothing: start from the initial iterates
+        x.copy_(x0)
+    graph.replay()
+    torch.cuda.synchronize()
+    for (S, k, eps, f, u, n), x, a in zip(doms, U, alone):
+        S.device_status()
+        assert torch.equal(x, a)
+        if prec == "fp64":
+            P = twogrid.Problem(n, 4, k, eps, alpha_s=0.5)
+            want = twogrid.TwoGrid(P, l_dd=2).step(u.copy(), f)
+            got = x.cpu().numpy()
+            assert np.abs(got - want).max() / np.abs(want).max() < 1e-9
+    for d in doms:
+        d[0].close()
