@@ -94,11 +94,14 @@ class DDSmoother:
             for ax in range(dim):
                 for end in (0, 1):
                     on_boundary = (ob[ax][0] == 0) if end == 0 else (ob[ax][1] == n)
-                    if (not on_boundary) or ((ax, end) in robin):
+                    if (not on_boundary) or ((ax, end) in robin):   # Dirichlet and Neumann sides: natural here
                         sides.append((ax, end))
             ncl = [hi - lo for (lo, hi) in ob]
             Asl = fem.assemble(ncl, p, prob.h, cs[sl], prob.k[sl], sides)
             odofs = _box_dofs(ob, p, m)
+            if getattr(prob, "dirichlet_sides", None):
+                # inherited Dirichlet condition on the parts of Gamma_0 in the subdomain's boundary
+                Asl = fem.impose_dirichlet(Asl, prob.dmask[odofs])
             udofs = _box_dofs(ub, p, m)
             pos = {g: i for i, g in enumerate(odofs.tolist())}
             uloc = np.array([pos[g] for g in udofs.tolist()])

@@ -180,10 +180,38 @@ def all_sides(dim):
 
 
 def robin_set(dim, bc):
-    """bc: 'robin' | 'neumann' | dict {(axis, end): 'robin'|'neumann'}."""
+    """bc: 'robin' | 'neumann' | 'dirichlet' | dict {(axis, end): 'robin'|'neumann'|'dirichlet'}."""
     if isinstance(bc, str):
         return [s for s in all_sides(dim)] if bc == "robin" else []
     return [s for s in all_sides(dim) if bc.get(s, "neumann") == "robin"]
+
+
+def dirichlet_set(dim, bc):
+    """The sides of Gamma_0 (Section 2: u = 0 there)."""
+    if isinstance(bc, str):
+        return [s for s in all_sides(dim)] if bc == "dirichlet" else []
+    return [s for s in all_sides(dim) if bc.get(s, "neumann") == "dirichlet"]
+
+
+def boundary_mask(m: int, dim: int, sides) -> np.ndarray:
+    """Boolean mask over the m^dim node grid (lexicographic, last axis fastest) of
+    the nodes on the given sides."""
+    mask = np.zeros((m,) * dim, dtype=bool)
+    for (axis, end) in sides:
+        sl = [slice(None)] * dim
+        sl[axis] = 0 if end == 0 else m - 1
+        mask[tuple(sl)] = True
+    return mask.reshape(-1)
+
+
+def impose_dirichlet(A: sp.spmatrix, mask: np.ndarray) -> sp.csr_matrix:
+    """The matrix of the space H^1_0(Omega; Gamma_0) (Section 2) kept on the full
+    node grid: rows and columns of the Dirichlet nodes removed and replaced by
+    the identity, so those unknowns are decoupled and equal their right-hand side."""
+    if not mask.any():
+        return A.tocsr()
+    keep = sp.diags((~mask).astype(float))
+    return (keep @ A @ keep + sp.diags(mask.astype(float))).tocsr()
 
 
 def shifted_coefficient(k, eps, alpha_s):

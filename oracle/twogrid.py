@@ -34,11 +34,18 @@ class Problem:
         self.periodic = periodic
         self.alpha_s = alpha_s
         self.robin_sides = [] if periodic else fem.robin_set(dim, bc)
+        # Dirichlet sides (Gamma_0): the unknowns there are kept on the node grid,
+        # decoupled by identity rows and columns (fem.impose_dirichlet)
+        self.dirichlet_sides = [] if periodic else fem.dirichlet_set(dim, bc)
         nc = (n,) * dim
+        self.dmask = fem.boundary_mask(n * p + 1, dim, self.dirichlet_sides) if not periodic else None
         self.A = fem.assemble(nc, p, self.h, fem.helmholtz_coefficient(self.k, self.eps),
                               self.k, self.robin_sides, periodic)
         self.As = fem.assemble(nc, p, self.h, fem.shifted_coefficient(self.k, self.eps, alpha_s),
                                self.k, self.robin_sides, periodic)
+        if self.dirichlet_sides:
+            self.A = fem.impose_dirichlet(self.A, self.dmask)
+            self.As = fem.impose_dirichlet(self.As, self.dmask)
         self.N = self.A.shape[0]
         if coarse:
             self.IP = fem.prolongation(n, p, dim, periodic)
@@ -46,9 +53,17 @@ class Problem:
             if coarse_kind == "qsfem":
                 self.Aq = qsfem.assemble_coarse(n, p, self.k, self.eps, self.robin_sides, periodic)
             elif coarse_kind == "gal":
+                if self.dirichlet_sides:
+                    raise ValueError("Galerkin coarsening with Dirichlet sides is not built")
                 self.Aq = galerkin.galerkin_coarse(self, alpha_c)
             else:
                 raise ValueError(coarse_kind)
+            if self.dirichlet_sides:
+                # the coarse space vanishes on Gamma_0 as well: I_P maps only the
+                # coarse nodes off it, and A_q is decoupled there
+                cmask = fem.boundary_mask(n * p // 2 + 1, dim, self.dirichlet_sides)
+                self.IP = (self.IP @ sp.diags((~cmask).astype(float))).tocsr()
+                self.Aq = fem.impose_dirichlet(self.Aq, cmask)
             self.Nc = self.Aq.shape[0]
 
 
