@@ -51,12 +51,19 @@ typedef enum {
   TH_ERR_BREAKDOWN = 5,    /* Krylov breakdown (zero new direction before convergence) */
   TH_ERR_NONFINITE = 6,    /* NaN/Inf met in a residual norm */
   TH_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
-  TH_ERR_UNSUPPORTED = 8,  /* valid but not implemented (e.g. Dirichlet sides) */
+  TH_ERR_UNSUPPORTED = 8,  /* valid but not implemented (e.g. Dirichlet sides in 3-D) */
   TH_ERR_SINGULAR = 9      /* a zero pivot during the FP64 set-up factorisations */
 } th_status;
 
 /* Boundary condition of one side (Section 2). */
-enum { TH_BC_NEUMANN = 0, TH_BC_ROBIN = 1, TH_BC_DIRICHLET = 2 /* not supported */ };
+/* Boundary condition per side (Section 2): Neumann (natural), absorbing
+ * (Robin, -i k u), or Dirichlet (u = 0 on Gamma_0; 2-D, QSFEM coarse level):
+ * the unknowns on Gamma_0 stay on the node grid and are decoupled by identity
+ * rows and columns of the fine, subdomain and coarse operators, the coarse
+ * space vanishes there too (the restriction gives 0 there and the
+ * prolongation ignores those coarse values), so a right-hand side that is
+ * zero on Gamma_0 gives a solution that is zero there. */
+enum { TH_BC_NEUMANN = 0, TH_BC_ROBIN = 1, TH_BC_DIRICHLET = 2 };
 /* Side index in th_mesh.bc: 0 = x low, 1 = x high, 2 = y low, 3 = y high. */
 
 /* Storage / arithmetic precision of the two-grid cycle.

@@ -328,6 +328,8 @@ th_status prepare(const th_mesh* mesh, const th_params* prm, th_ctx& x) {
   if (!std::isfinite(prm->alpha_c) || prm->alpha_c < 0.0) return TH_ERR_ARG;
   x.gal = prm->coarse_kind == TH_CK_GALERKIN;
   if (x.gal && x.g.dim != 2) return TH_ERR_UNSUPPORTED;
+  if (x.gal && (x.g.dirichlet[0] | x.g.dirichlet[1] | x.g.dirichlet[2] | x.g.dirichlet[3]))
+    return TH_ERR_UNSUPPORTED;  // Galerkin coarsening with Dirichlet sides is not built
   // block 0 of the Galerkin sweep holds its right-hand side in shared memory
   if (x.gal && (size_t)(x.g.q + 1) * x.g.mc * 16 > 227 * 1024) return TH_ERR_UNSUPPORTED;
   if (x.g.dim == 2 && x.g.mc > 1024) return TH_ERR_UNSUPPORTED;  // coarse kernels hold two coarse rows per thread
@@ -380,6 +382,7 @@ th::FineArgs<T> fine_args(const th_ctx& x, int op) {
   a.m = g.m;
   a.p = g.p;
   a.robin = g.robin[0] | (g.robin[1] << 1) | (g.robin[2] << 2) | (g.robin[3] << 3);
+  a.dirichlet = g.dirichlet[0] | (g.dirichlet[1] << 1) | (g.dirichlet[2] << 2) | (g.dirichlet[3] << 3);
   a.h = cvt<T>(g.h);
   a.h2 = cvt<T>(g.h * g.h);
   a.alpha = cvt<T>(op == TH_OP_AS ? x.prm.alpha_s : 0.0);
@@ -656,6 +659,7 @@ th_status restrict_(th_ctx& x, const typename th::Cx<T>::t* r, typename th::Cx<T
   a.ridx = x.ridx;
   a.rw = B::rw(x);
   a.rmax = x.rmax;
+  a.dirichlet = x.g.dirichlet[0] | (x.g.dirichlet[1] << 1) | (x.g.dirichlet[2] << 2) | (x.g.dirichlet[3] << 3);
   a.N = x.g.N;
   a.Nc = x.g.Nc;
   a.m = x.g.m;
@@ -682,6 +686,7 @@ th_status prolong_(th_ctx& x, const typename th::Cx<T>::t* uc, typename th::Cx<T
   a.mc = x.g.mc;
   a.q = x.g.q;
   a.omega = omega;
+  a.dirichlet = x.g.dirichlet[0] | (x.g.dirichlet[1] << 1) | (x.g.dirichlet[2] << 2) | (x.g.dirichlet[3] << 3);
   x.launches += 1;
   Prof prof(x, TH_K_PROLONG, s);
   if (x.g.dim == 3) return cuda_status(th::launch_prolong3<T>(a, nrhs, s));
@@ -802,6 +807,7 @@ th_status coarse_apply_(th_ctx& x, const typename th::Cx<T>::t* in, typename th:
   a.Nc = x.g.Nc;
   a.nc = x.g.nc;
   a.mc = x.g.mc;
+  a.dirichlet = x.g.dirichlet[0] | (x.g.dirichlet[1] << 1) | (x.g.dirichlet[2] << 2) | (x.g.dirichlet[3] << 3);
   x.launches += 1;
   Prof prof(x, TH_K_COARSE_APPLY, s);
   if (x.g.dim == 3) return cuda_status(th::launch_coarse_apply3<T>(a, nrhs, s));

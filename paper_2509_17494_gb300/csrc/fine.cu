@@ -70,7 +70,11 @@ __device__ __forceinline__ typename Cx<T>::t prolong_at(const FineArgs<T>& a, in
     T tr = 0, ti = 0;
     for (int bx = 0; bx <= a.q; ++bx) {
       const T wx = a.pw[(size_t)gx * (a.q + 1) + bx];
-      const C v = uc[(size_t)(jy0 + by) * a.mc + jx0 + bx];
+      C v = uc[(size_t)(jy0 + by) * a.mc + jx0 + bx];
+      if (a.dirichlet && coarse_on_gamma0(a.dirichlet, jx0 + bx, jy0 + by, a.mc)) {
+        v.x = 0;   // the coarse space vanishes on Gamma_0
+        v.y = 0;
+      }
       tr = fma(wx, v.x, tr);
       ti = fma(wx, v.y, ti);
     }
@@ -116,7 +120,9 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
     C v;
     v.x = 0;
     v.y = 0;
-    if (gx >= 0 && gx < a.m && gy >= 0 && gy < a.m) {
+    const bool on_d = ((a.dirichlet & 1) && gx == 0) || ((a.dirichlet & 2) && gx == a.m - 1) ||
+                      ((a.dirichlet & 4) && gy == 0) || ((a.dirichlet & 8) && gy == a.m - 1);
+    if (gx >= 0 && gx < a.m && gy >= 0 && gy < a.m && !on_d) {  // Gamma_0 nodes: zero columns
       if constexpr (std::is_same<T, ds>::value) {
         v = NodeIO<T>::ld(u, (size_t)gy * a.m + gx);
       } else {
@@ -323,8 +329,21 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
       }
     }
     const size_t g = (size_t)(cy0 * P + ly) * a.m + (cx0 * P + lx);
+    const int gx = cx0 * P + lx, gy = cy0 * P + ly;
+    C uo = su[(ly + P) * UT + lx + P];
+    if (a.dirichlet && (((a.dirichlet & 1) && gx == 0) || ((a.dirichlet & 2) && gx == a.m - 1) ||
+                        ((a.dirichlet & 4) && gy == 0) || ((a.dirichlet & 8) && gy == a.m - 1))) {
+      // identity row on Gamma_0: (A u)_j = u_j, with the operand's own value
+      if constexpr (std::is_same<T, ds>::value) {
+        uo = NodeIO<T>::ld(u, g);
+      } else {
+        uo = a.src == 1 ? combine_at(a, gx, gy) : a.src == 2 ? prolong_at(a, gx, gy) : NodeIO<T>::ld(u, g);
+      }
+      ar = uo.x;
+      ai = uo.y;
+    }
     if constexpr (!std::is_same<T, ds>::value) {
-      if (a.src != 0) a.uout[roff + g] = su[(ly + P) * UT + lx + P];
+      if (a.src != 0) a.uout[roff + g] = uo;
     }
     C out;
     if (a.f) {

@@ -58,6 +58,7 @@ struct FineArgs {
   long long N;                 // stride between right-hand sides
   int n, m, p;
   int robin;                   // bit s set = side s absorbing (x lo, x hi, y lo, y hi)
+  int dirichlet;               // bit s set = side s on Gamma_0: identity rows and columns there
   int residual;                // 0: y = OP u;  1: y = f - OP u
   int tc;                      // tile edge in cells (0: default for p)
   T h, h2, alpha;              // alpha = shift (0 for A)
@@ -146,6 +147,12 @@ struct CombineArgs {
 template <typename T>
 cudaError_t launch_dd_combine(const CombineArgs<T>& a, int nrhs, cudaStream_t s);
 
+// coarse node (ix, iy) of an mc x mc grid on a side of Gamma_0 (bits: x lo, x hi, y lo, y hi)
+__host__ __device__ inline bool coarse_on_gamma0(int bits, int ix, int iy, int mc) {
+  return ((bits & 1) && ix == 0) || ((bits & 2) && ix == mc - 1) || ((bits & 4) && iy == 0) ||
+         ((bits & 8) && iy == mc - 1);
+}
+
 // ------------------------------------------------------- K5/K6 transfers
 template <typename T>
 struct TransferArgs {
@@ -156,6 +163,7 @@ struct TransferArgs {
   long long N, Nc;
   int m, mc, q;
   T omega;
+  int dirichlet;               // restriction: bit s set = coarse nodes of side s get 0 (x lo, x hi, y lo, y hi)
 };
 template <typename T>
 cudaError_t launch_restrict(const TransferArgs<T>& a, int nrhs, cudaStream_t s);
@@ -171,6 +179,7 @@ struct CoarseApplyArgs {
   const typename Cx<T>::t* rho;    // 4 x nc (per side), zero where Neumann
   long long Nc;
   int nc, mc;
+  int dirichlet;                   // bit s set = side s on Gamma_0: identity rows, zero columns
 };
 template <typename T>
 cudaError_t launch_coarse_apply(const CoarseApplyArgs<T>& a, int nrhs, cudaStream_t s);

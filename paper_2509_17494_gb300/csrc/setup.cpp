@@ -192,8 +192,9 @@ th_status make_geometry(const th_mesh& mesh, const th_params& prm, Geometry& g) 
   if (mesh.dim == 3 && mesh.p != 2) return TH_ERR_UNSUPPORTED;  // the 3-D kernels are Q2
   const int nsides = 2 * mesh.dim;
   for (int s = 0; s < nsides; ++s) {
-    if (mesh.bc[s] == TH_BC_DIRICHLET) return TH_ERR_UNSUPPORTED;
-    if (mesh.bc[s] != TH_BC_ROBIN && mesh.bc[s] != TH_BC_NEUMANN) return TH_ERR_ARG;
+    if (mesh.bc[s] == TH_BC_DIRICHLET && mesh.dim == 3) return TH_ERR_UNSUPPORTED;  // 2-D only
+    if (mesh.bc[s] != TH_BC_ROBIN && mesh.bc[s] != TH_BC_NEUMANN && mesh.bc[s] != TH_BC_DIRICHLET)
+      return TH_ERR_ARG;
   }
   if (prm.l_dd < 1 || prm.n_dd < 1 || prm.n_s < 1) return TH_ERR_ARG;
   if (prm.restart < 1 || prm.maxit < 0 || prm.nrhs_max < 1 || prm.nrhs_max > 4096) return TH_ERR_ARG;
@@ -214,6 +215,7 @@ th_status make_geometry(const th_mesh& mesh, const th_params& prm, Geometry& g) 
   g.h = 1.0 / g.n;
   g.hc = 1.0 / g.nc;
   for (int s = 0; s < 6; ++s) g.robin[s] = (s < nsides && mesh.bc[s] == TH_BC_ROBIN) ? 1 : 0;
+  for (int s = 0; s < 6; ++s) g.dirichlet[s] = (s < nsides && mesh.bc[s] == TH_BC_DIRICHLET) ? 1 : 0;
   g.l_dd = std::min(prm.l_dd, g.n);
   g.blk = partition_1d(g.n, g.l_dd);
   g.nb = (int)g.blk.start.size();
@@ -470,6 +472,28 @@ th_status subdomain_inverse_rows(const Geometry& g, const Ref1D& ref, const doub
         }
     }
   }
+  // Dirichlet sides of the domain in this subdomain's boundary (Gamma_0, inherited):
+  // the unknowns there are decoupled, identity rows and columns
+  {
+    const bool dside[4] = {at_lo_x && g.dirichlet[0], at_hi_x && g.dirichlet[1], at_lo_y && g.dirichlet[2],
+                           at_hi_y && g.dirichlet[3]};
+    if (dside[0] || dside[1] || dside[2] || dside[3]) {
+      std::vector<char> dn(nd, 0);
+      for (int ly = 0; ly < wy; ++ly)
+        for (int lx = 0; lx < wx; ++lx)
+          if ((dside[0] && lx == 0) || (dside[1] && lx == wx - 1) || (dside[2] && ly == 0) ||
+              (dside[3] && ly == wy - 1))
+            dn[(size_t)ly * wx + lx] = 1;
+      for (int i = 0; i < nd; ++i) {
+        if (!dn[i]) continue;
+        for (int j = 0; j < nd; ++j) {
+          A[(size_t)i * nd + j] = 0.0;
+          A[(size_t)j * nd + i] = 0.0;
+        }
+        A[(size_t)i * nd + i] = 1.0;
+      }
+    }
+  }
   // banded LU: coupling within a cell reaches p rows and p columns
   const int bw = p * wx + p;
   std::vector<int> piv;
@@ -688,6 +712,26 @@ th_status coarse_setup(const Geometry& g, const double* k, const double* eps, Co
       add(x1, y1, x0, y0, r / 6.0);
     }
   }
+  // Dirichlet sides (Gamma_0): the coarse space vanishes there as well; the
+  // coarse nodes on them are decoupled (identity rows, zero columns)
+  for (int ay = 0; ay < mc; ++ay)
+    for (int ax = 0; ax < mc; ++ax) {
+      const bool dn = (g.dirichlet[0] && ax == 0) || (g.dirichlet[1] && ax == mc - 1) ||
+                      (g.dirichlet[2] && ay == 0) || (g.dirichlet[3] && ay == mc - 1);
+      if (!dn) continue;
+      const size_t r = (size_t)ay * mc + ax;
+      cb.dl[r] = cb.du[r] = 0.0;
+      cb.dd[r] = 1.0;
+      cb.cl[r] = cb.cd[r] = cb.cu[r] = 0.0;          // row r's couplings to block row ay + 1
+      if (ax > 0) cb.du[r - 1] = 0.0;                  // column r in block row ay
+      if (ax + 1 < mc) cb.dl[r + 1] = 0.0;
+      if (ay > 0) {                                    // column r in C_{ay-1} (and so in B_ay)
+        const size_t o = (size_t)(ay - 1) * mc;
+        cb.cd[o + ax] = 0.0;
+        if (ax > 0) cb.cu[o + ax - 1] = 0.0;
+        if (ax + 1 < mc) cb.cl[o + ax + 1] = 0.0;
+      }
+    }
   // block elimination: S_0 = D_0, S_j = D_j - B_j S_{j-1}^{-1} C_{j-1}, B_j = C_{j-1}^T
   if (!block_inverses) return TH_OK;
   cb.G.assign((size_t)mc * mm, cplx(0.0));

@@ -44,6 +44,7 @@ struct Geometry {
   long long Nc = 0;         // coarse dofs mc^dim
   double h = 0, hc = 0;
   int robin[6] = {0, 0, 0, 0, 0, 0};  // x lo, x hi, y lo, y hi, z lo, z hi
+  int dirichlet[6] = {0, 0, 0, 0, 0, 0};  // sides of Gamma_0 (u = 0), same order (2-D only)
   // partition
   int l_dd = 0;
   Block1D blk;              // same along x and y

@@ -41,6 +41,12 @@ __global__ void __launch_bounds__(256) k_restrict(const TransferArgs<T> a) {
   C o;
   o.x = sr;
   o.y = si;
+  // the coarse space vanishes on Gamma_0: no restricted residual there
+  if (((a.dirichlet & 1) && Jx == 0) || ((a.dirichlet & 2) && Jx == a.mc - 1) || ((a.dirichlet & 4) && Jy == 0) ||
+      ((a.dirichlet & 8) && Jy == a.mc - 1)) {
+    o.x = 0;
+    o.y = 0;
+  }
   a.out[(size_t)blockIdx.y * a.Nc + J] = o;
 }
 
@@ -60,7 +66,11 @@ __global__ void __launch_bounds__(256) k_prolong(const TransferArgs<T> a) {
     T tr = 0, ti = 0;
     for (int bx = 0; bx <= a.q; ++bx) {
       const T wx = a.pw[(size_t)ix * (a.q + 1) + bx];
-      const C v = uc[(size_t)(jy0 + by) * a.mc + jx0 + bx];
+      C v = uc[(size_t)(jy0 + by) * a.mc + jx0 + bx];
+      if (a.dirichlet && coarse_on_gamma0(a.dirichlet, jx0 + bx, jy0 + by, a.mc)) {
+        v.x = 0;   // the coarse space vanishes on Gamma_0
+        v.y = 0;
+      }
       tr = fma(wx, v.x, tr);
       ti = fma(wx, v.y, ti);
     }
@@ -104,6 +114,23 @@ __global__ void __launch_bounds__(256) k_coarse_apply(const CoarseApplyArgs<T> a
   if (J >= a.Nc) return;
   const int Jy = (int)(J / a.mc), Jx = (int)(J - (long long)Jy * a.mc);
   const C* x = a.x + (size_t)blockIdx.y * a.Nc;
+  auto dnode = [&](int ix, int iy) {
+    return ((a.dirichlet & 1) && ix == 0) || ((a.dirichlet & 2) && ix == a.mc - 1) ||
+           ((a.dirichlet & 4) && iy == 0) || ((a.dirichlet & 8) && iy == a.mc - 1);
+  };
+  if (a.dirichlet && dnode(Jx, Jy)) {  // identity row on Gamma_0
+    a.y[(size_t)blockIdx.y * a.Nc + J] = x[J];
+    return;
+  }
+  // with Gamma_0 present the values of its nodes are left out (zero columns)
+  auto xv = [&](int ix, int iy) {
+    C v = x[(size_t)iy * a.mc + ix];
+    if (a.dirichlet && dnode(ix, iy)) {
+      v.x = 0;
+      v.y = 0;
+    }
+    return v;
+  };
   C acc;
   acc.x = 0;
   acc.y = 0;
@@ -114,10 +141,10 @@ __global__ void __launch_bounds__(256) k_coarse_apply(const CoarseApplyArgs<T> a
       if (cx < 0 || cx >= a.nc) continue;
       const C* d = a.cell + ((size_t)cy * a.nc + cx) * 3;
       const int ox = (cx == Jx) ? 1 : -1, oy = (cy == Jy) ? 1 : -1;  // direction of the other nodes
-      cfma(acc, d[0], x[(size_t)Jy * a.mc + Jx]);
-      cfma(acc, d[1], x[(size_t)Jy * a.mc + Jx + ox]);
-      cfma(acc, d[1], x[(size_t)(Jy + oy) * a.mc + Jx]);
-      cfma(acc, d[2], x[(size_t)(Jy + oy) * a.mc + Jx + ox]);
+      cfma(acc, d[0], xv(Jx, Jy));
+      cfma(acc, d[1], xv(Jx + ox, Jy));
+      cfma(acc, d[1], xv(Jx, Jy + oy));
+      cfma(acc, d[2], xv(Jx + ox, Jy + oy));
     }
   }
   // absorbing sides: rho_e (1/3 x_J + 1/6 x_neighbour) per boundary edge at J
@@ -132,8 +159,7 @@ __global__ void __launch_bounds__(256) k_coarse_apply(const CoarseApplyArgs<T> a
       if (t < 0 || t >= a.nc) continue;
       const C r = rho[t];
       const int other = (t == along) ? along + 1 : along - 1;
-      const size_t jo = xside ? (size_t)other * a.mc + Jx : (size_t)Jy * a.mc + other;
-      C xj = x[J], xo = x[jo];
+      C xj = x[J], xo = xside ? xv(Jx, other) : xv(other, Jy);
       C v;
       v.x = third * xj.x + sixth * xo.x;
       v.y = third * xj.y + sixth * xo.y;

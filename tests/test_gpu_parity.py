@@ -52,6 +52,8 @@ CASES = [
     dict(n=5, p=6, l_dd=2, bc="neumann"),                            # p = 6, Neumann (layer absorbs)
     dict(n=5, p=8, l_dd=2, bc={"ylo": "robin", "xhi": "robin"}),     # p = 8
     dict(n=25, p=4, l_dd=4, bc="robin"),                             # 4/3 block sizes
+    dict(n=9, p=4, l_dd=2, bc={"xlo": "dirichlet", "ylo": "dirichlet", "xhi": "robin", "yhi": "robin"}),
+    dict(n=10, p=2, l_dd=3, bc="dirichlet"),                         # Gamma_0 all round, damping layer only
 ]
 
 
@@ -266,6 +268,32 @@ def test_solve_matches_oracle_iterations(th, name, alpha_s, l_dd):
     assert info["iters"] == it
     assert info["relres_max"] <= 1e-8
     assert relerr(host(x), xo) < 1e-7
+
+
+@pytest.mark.parametrize("bc", [{"xlo": "dirichlet", "ylo": "dirichlet", "xhi": "robin", "yhi": "robin"},
+                                {"xlo": "dirichlet", "xhi": "dirichlet", "ylo": "robin", "yhi": "robin"}])
+def test_dirichlet_solve_matches_oracle(th, bc):
+    """Dirichlet sides (Section 2, u = 0 on Gamma_0): the FP64 solve takes the
+    oracle's FGMRES iterations and lands within 1e-7 of its solution; the mixed
+    form reaches 1e-8 and the exact solution within 1e-6; u is zero on Gamma_0."""
+    import scipy.sparse.linalg as spla
+    n, p = 16, 4
+    k, eps = small_case(n=n, p=p, W=4.0, seed=11)
+    S = th.TwoGridSolver(n, p, k, eps, bc=bc, alpha_s=0.5, l_dd=2, prec="bf16", extra_prec=("fp64",), restart=40,
+                         device=DEV)
+    P = twogrid.Problem(n, p, k, eps, bc=oracle_bc(bc), alpha_s=0.5)
+    TG = twogrid.TwoGrid(P, l_dd=2)
+    f = synth.gaussian_source(n, p, 2)
+    xo, it, rr, _ = krylov.fgmres(lambda v: P.A @ v, TG.precondition, f, tol=1e-8, restart=40)
+    S.set_precision("fp64")
+    x, info = S.solve(dev(f))
+    assert info["iters"] == it and relerr(host(x), xo) < 1e-7
+    assert np.all(host(x)[P.dmask] == 0)
+    S.set_precision("bf16")
+    xm, infom = S.solve(dev(f))
+    assert infom["relres_max"] <= 1e-8 and infom["iters"] <= it + 2
+    xs = spla.spsolve(P.A.tocsc(), f)
+    assert np.linalg.norm(host(xm) - xs) / np.linalg.norm(xs) < 1e-6
 
 
 def test_solve_multiple_rhs_and_restart(th):

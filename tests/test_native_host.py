@@ -54,7 +54,9 @@ def test_qsfem_cell_matches_oracle(th, eta):
 
 
 @pytest.mark.parametrize("n,l_dd,bc", [(6, 2, "robin"), (7, 3, "neumann"),
-                                        (5, 2, {"xlo": "robin", "yhi": "robin"})])
+                                        (5, 2, {"xlo": "robin", "yhi": "robin"}),
+                                        (6, 2, {"xlo": "dirichlet", "ylo": "dirichlet", "xhi": "robin", "yhi": "robin"}),
+                                        (5, 3, "dirichlet")])
 def test_inverse_rows_match_oracle(th, n, l_dd, bc):
     p = 4
     k, eps = small_case(n=n, p=p)
@@ -166,8 +168,9 @@ def test_galerkin_setup_matches_oracle(th, n, p, bc, alpha_c):
     assert np.abs(x - want).max() <= 1e-9 * np.abs(want).max()
 
 
-@pytest.mark.parametrize("n,P", [(25, 3), (13, 4)])
-def test_reduced_separator_inverse_is_block_of_coarse_inverse(th, n, P):
+@pytest.mark.parametrize("n,P,bc", [(25, 3, "robin"), (13, 4, "robin"),
+                                    (13, 3, {"xlo": "dirichlet", "ylo": "dirichlet", "xhi": "robin", "yhi": "robin"})])
+def test_reduced_separator_inverse_is_block_of_coarse_inverse(th, n, P, bc):
     """The explicit inverse of the reduced separator system (the Schur complement
     of A_q on the separator rows) equals the separator block of A_q^{-1}, here
     the oracle's A_q inverted densely.  mc = 51 and 27 coarse rows: not multiples
@@ -175,10 +178,10 @@ def test_reduced_separator_inverse_is_block_of_coarse_inverse(th, n, P):
     separator blocks."""
     p = 4
     k, eps = small_case(n=n, p=p, W=n / 5.0)
-    sep, Sinv = th.host_coarse_separators(n, p, k, eps, P=P)
+    sep, Sinv = th.host_coarse_separators(n, p, k, eps, bc=bc, P=P)
     mc = n * p // 2 + 1
     assert len(sep) == P - 1 and np.all(np.diff(sep) > 1) and sep[0] > 0 and sep[-1] < mc - 1
-    Aq = qsfem.assemble_coarse(n, p, k, eps, fem.robin_set(2, "robin")).toarray()
+    Aq = twogrid.Problem(n, p, k, eps, bc=oracle_bc(bc), alpha_s=0.5).Aq.toarray()
     Ainv = np.linalg.inv(Aq)
     idx = np.concatenate([np.arange(s * mc, (s + 1) * mc) for s in sep])
     want = Ainv[np.ix_(idx, idx)]
