@@ -94,6 +94,8 @@ def parse():
                     help="FP32 one-rhs coarse sweep: auto, 0 two phases, 1 one cluster barrier per step, "
                          "2 st.async row exchange")
     ap.add_argument("--learned-steps", type=int, default=400, help="training steps of the learned section (0: skip)")
+    ap.add_argument("--bc-sweep", action="store_true",
+                    help="iterations vs size for Robin / Dirichlet / Neumann sides (Fig. 6 (a))")
     ap.add_argument("--learned-c4-pairs", type=int, default=0,
                     help="training pairs of the corrector on the 401^2 coarse grid, 32 channels (0: skip)")
     ap.add_argument("--dim3", choices=["cube10_q2_n40", "cube2_q2_n8", "none"], default="cube10_q2_n40",
@@ -441,6 +443,8 @@ def run_native(args):
         line["galerkin"] = galerkin_section(args, w, dev)
     if args.gal_sweep:
         line["gal_sweep"] = gal_sweep_section(dev)
+    if args.bc_sweep:
+        line["bc_sweep"] = bc_sweep_section(dev)
     if args.table2:
         line["table2"] = table2_section(dev)
     if args.lfa != "none":
@@ -769,6 +773,39 @@ def gal_sweep_section(dev):
             S = th.TwoGridSolver(n, p, k, None, l_dd=l_dd, restart=60, maxit=400, tol=1e-6, device=dev, **kw)
             if none:
                 S.set_coarse("none")
+            _, info = S.solve(f, check=False)
+            S.close()
+            out[label].append(info["iters"] if info["converged"] else -1)
+    return out
+
+
+def bc_sweep_section(dev):
+    """Fig. 6 (a): iterations of the QSFEM ('opt') method against problem size for
+    different boundary conditions (constant k, 8 points per wavelength, Q4,
+    4 x 4-cell subdomains, alpha_s = 0.2, centred source, FGMRES(60) to 1e-6):
+    Robin on every side; Dirichlet on two non-opposite sides (x low, y low) and
+    Robin on the others; Neumann there instead.  A thin damping layer (10 dofs)
+    keeps the Dirichlet / Neumann problems away from resonance."""
+    import torch
+
+    import paper_2509_17494_gb300 as th
+    import synth
+
+    p, ppw, l_dd = 4, 8, 4
+    variants = {"robin": "robin",
+                "dirichlet_2_sides": {"xlo": "dirichlet", "ylo": "dirichlet", "xhi": "robin", "yhi": "robin"},
+                "neumann_2_sides": {"xlo": "neumann", "ylo": "neumann", "xhi": "robin", "yhi": "robin"}}
+    out = {"setup": "unit square, constant k, Q4, 8 ppw, l_dd = 4, alpha_s = 0.2, 10-dof damping layer, "
+                    "centred source, FGMRES(60) to 1e-6", "wavelengths": [], **{v: [] for v in variants}}
+    for W in (5, 10, 20, 40):
+        n = int(round(W * ppw / p))
+        k = synth.constant_wavenumber(n, 2, W)
+        eps = synth.absorbing_layer(n, 2, p, k, 10.0)
+        f = torch.from_numpy(synth.gaussian_source(n, p, 2)).to(dev)
+        out["wavelengths"].append(W)
+        for label, bc in variants.items():
+            S = th.TwoGridSolver(n, p, k, eps, bc=bc, alpha_s=0.2, l_dd=l_dd, restart=60, maxit=400, tol=1e-6,
+                                 device=dev)
             _, info = S.solve(f, check=False)
             S.close()
             out[label].append(info["iters"] if info["converged"] else -1)
