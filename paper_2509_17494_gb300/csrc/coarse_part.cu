@@ -789,19 +789,29 @@ __global__ void __launch_bounds__(512, 1) k_sweep_cols(const CoarsePartArgs<T> a
         acc[r].x = 0;
         acc[r].y = 0;
       }
-      int c = 0;
-      for (; c + 8 <= mc; c += 8) {
-        C gv[8];
+      // blocks of 8 columns; the next block's entries are loaded before the
+      // current block's products, so the L2 latency overlaps them
+      const int c8 = mc & ~7;
+      C gv[8], gn[8];
+      if (c8 > 0) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) gv[u] = g[(size_t)(c + u) * mcr + rr];
+        for (int u = 0; u < 8; ++u) gv[u] = g[(size_t)u * mcr + rr];
+      }
+      for (int c = 0; c < c8; c += 8) {
+        if (c + 8 < c8) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) gn[u] = g[(size_t)(c + 8 + u) * mcr + rr];
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const C* tc = tv + (size_t)(c + u) * NBW;
 #pragma unroll
           for (int r = 0; r < NBW; ++r) cmac(acc[r], gv[u], tc[r]);
         }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) gv[u] = gn[u];
       }
-      for (; c < mc; ++c) {
+      for (int c = c8; c < mc; ++c) {
         const C gc = g[(size_t)c * mcr + rr];
         const C* tc = tv + (size_t)c * NBW;
 #pragma unroll
@@ -866,19 +876,27 @@ __global__ void __launch_bounds__(256) k_sep_cols(const CoarsePartArgs<T> a) {
     __syncthreads();
     if (rr < a.nred) {
       const C* sc = a.Sinv + (size_t)k0 * a.ldS + rr;
-      int c = 0;
-      for (; c + 8 <= kn; c += 8) {
-        C sv[8];
+      const int c8 = kn & ~7;
+      C sv[8], sn[8];
+      if (c8 > 0) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) sv[u] = sc[(size_t)(c + u) * a.ldS];
+        for (int u = 0; u < 8; ++u) sv[u] = sc[(size_t)u * a.ldS];
+      }
+      for (int c = 0; c < c8; c += 8) {
+        if (c + 8 < c8) {  // the next block's entries ahead of this block's products
+#pragma unroll
+          for (int u = 0; u < 8; ++u) sn[u] = sc[(size_t)(c + 8 + u) * a.ldS];
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const C* hc = hs + (size_t)(c + u) * NBW;
 #pragma unroll
           for (int r = 0; r < NBW; ++r) cmac(acc[r], sv[u], hc[r]);
         }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sv[u] = sn[u];
       }
-      for (; c < kn; ++c) {
+      for (int c = c8; c < kn; ++c) {
         const C sv = sc[(size_t)c * a.ldS];
         const C* hc = hs + (size_t)c * NBW;
 #pragma unroll
@@ -933,19 +951,27 @@ __global__ void __launch_bounds__(512) k_spikes_cols(const CoarsePartArgs<T> a) 
       acc[r].x = 0;
       acc[r].y = 0;
     }
-    int c = 0;
-    for (; c + 8 <= K; c += 8) {
-      C lv[8];
+    const int c8 = K & ~7;
+    C lv[8], ln[8];
+    if (c8 > 0) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) lv[u] = lr[(size_t)(c + u) * a.mcr + rr];
+      for (int u = 0; u < 8; ++u) lv[u] = lr[(size_t)u * a.mcr + rr];
+    }
+    for (int c = 0; c < c8; c += 8) {
+      if (c + 8 < c8) {  // the next block's entries ahead of this block's products
+#pragma unroll
+        for (int u = 0; u < 8; ++u) ln[u] = lr[(size_t)(c + 8 + u) * a.mcr + rr];
+      }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const C* xc = xs + (size_t)(c + u) * NBW;
 #pragma unroll
         for (int r = 0; r < NBW; ++r) cmac(acc[r], lv[u], xc[r]);
       }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) lv[u] = ln[u];
     }
-    for (; c < K; ++c) {
+    for (int c = c8; c < K; ++c) {
       const C lc = lr[(size_t)c * a.mcr + rr];
       const C* xc = xs + (size_t)c * NBW;
 #pragma unroll
