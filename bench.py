@@ -1040,7 +1040,7 @@ def learned_c4_section(args, dev):
             torch.cuda.synchronize(dev)
             gen_s += time.time() - tg
         k = (it % (gen // B)) * B
-        lr = 1e-3 if it < 0.7 * steps else 2.5e-4
+        lr = 2e-3 if it < 0.7 * steps else 5e-4
         losses.append(S.unet_train_step(rc[k:k + B].contiguous(), uc[k:k + B].contiguous(), lr=lr))
         seen += B
     torch.cuda.synchronize(dev)
