@@ -366,7 +366,8 @@ enum {
   TH_K_DD_BATCH = 9,    /* (variants only) batched BF16 subdomain products: 0 CUDA cores, 1 tensor cores */
   TH_K_RESID = 10,      /* (variants only) the mixed form's outer residual, see th_residual_mixed */
   TH_K_CYCLE = 11,      /* (variants only) launch structure of the cycle, see th_set_kernel_variant */
-  TH_K_COARSE_MULTI = 12 /* (variants only) 2-D coarse sweep for 8 or more right-hand sides */
+  TH_K_COARSE_MULTI = 12, /* (variants only) 2-D coarse sweep for 8 or more right-hand sides */
+  TH_K_AZ = 13          /* (variants only) the FGMRES product A z of the mixed forms */
 };
 
 /* Per-kernel timing for measurement: with enable = 1 every later kernel
@@ -418,6 +419,10 @@ th_status th_peak_fma(int prec, int iters, double* flops_per_s, void* stream);
  *              first issued with a programmatic dependency on the one before
  *              (it may be scheduled while that one drains, and waits for it
  *              before touching shared data; not while th_profile records);
+ *   TH_K_AZ:   the product w = A z of each FGMRES step in the mixed forms
+ *              (2-D): 1 (default) the double-single apply with FP64 output
+ *              (48-bit significands; the final residual is still recomputed
+ *              with the FP64 apply), 0 the FP64 apply; prec is ignored;
  *   TH_K_COARSE_MULTI: the 2-D coarse chunk sweep for 8 or more right-hand
  *              sides: 1 (default) one CTA per chunk and group of 8 to 16
  *              right-hand sides (the narrowest group that keeps the chunks x

@@ -72,6 +72,7 @@ struct th_ctx {
   float *kc32 = nullptr, *ec32 = nullptr;
   th::ds *kcds = nullptr, *ecds = nullptr;  // k, eps per cell in double-single (mixed form, 2-D)
   int resid_ds = 1;  // mixed form's outer residual: 1 double-single apply to FP32, 0 FP64 apply + rounding
+  int az_ds = 1;     // mixed form's FGMRES product A z: 1 double-single apply with FP64 output, 0 FP64 apply
   int* box = nullptr;
   int4* ctab = nullptr;
   void* W[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -496,6 +497,26 @@ th_status outer_residual(th_ctx& x, const double2* u, const double2* f, float2* 
   x.launches += 1;
   Prof prof(x, TH_K_VECTOR, s);
   return cuda_status(th::launch_d2f((const double*)x.r64, (float*)r32, 2 * x.g.N * (long long)nrhs, s));
+}
+
+// The FGMRES product w = A z.  In the mixed forms (2-D) it runs in double-single
+// arithmetic (48-bit significands, 64-bit exponent range of FP32 pairs) with
+// FP64 output, TH_K_AZ 1: GB300's FP64 rate is 1/64 of its FP32 rate; the
+// Arnoldi relation then holds to ~1e-14 relative, far below the 1e-8
+// tolerance, and the final residual is recomputed in FP64.
+th_status az_apply(th_ctx& x, const double2* z, double2* w, int nrhs, cudaStream_t s) {
+  if (x.active != TH_PREC_FP64 && x.az_ds && x.kcds && x.g.dim == 2) {
+    th::FineArgs<th::ds> a = fine_args<th::ds>(x, TH_OP_A);
+    a.u = reinterpret_cast<const th::cds*>(z);
+    a.f = nullptr;
+    a.y = reinterpret_cast<th::cds*>(w);
+    a.residual = 0;
+    a.out64 = 1;
+    x.launches += 1;
+    Prof prof(x, TH_K_FINE, s);
+    return cuda_status(th::launch_fine_apply<th::ds>(a, nrhs, s));
+  }
+  return fine_apply<double>(x, TH_OP_A, z, nullptr, w, nrhs, s);
 }
 
 template <typename T> struct PrecBufs;
@@ -1537,6 +1558,8 @@ th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
     x->fuse = variant;
   } else if (kernel == TH_K_COARSE_MULTI) {
     x->cs_multi = variant;
+  } else if (kernel == TH_K_AZ) {
+    x->az_ds = variant;
   } else {
     return TH_ERR_ARG;
   }
@@ -1554,6 +1577,7 @@ th_status th_get_kernel_variant(const th_ctx* x, int kernel, int prec, int* vari
   else if (kernel == TH_K_RESID) *variant = (x->resid_ds && x->kcds) ? 1 : 0;
   else if (kernel == TH_K_CYCLE) *variant = x->fuse;
   else if (kernel == TH_K_COARSE_MULTI) *variant = x->cs_multi;
+  else if (kernel == TH_K_AZ) *variant = (x->az_ds && x->kcds && x->g.dim == 2) ? 1 : 0;
   else return TH_ERR_ARG;
   return TH_OK;
 }
@@ -1997,7 +2021,7 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
         st = precondition(*x, Vj, Zj, nrhs, s);
       }
       if (st != TH_OK) return st;
-      if ((st = fine_apply<double>(*x, TH_OP_A, Zj, nullptr, x->w, nrhs, s)) != TH_OK) return st;
+      if ((st = az_apply(*x, Zj, x->w, nrhs, s)) != TH_OK) return st;
       // one classical Gram-Schmidt pass (the coefficients and ||w||^2 before it), then
       // ||w||^2 after it; a pass that cancels more than 99.99 % of ||w||^2 makes the
       // host restart (loss of orthogonality ~ eps ||w||^2 / ||w - V h||^2), which

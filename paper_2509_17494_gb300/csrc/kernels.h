@@ -60,6 +60,7 @@ struct FineArgs {
   int robin;                   // bit s set = side s absorbing (x lo, x hi, y lo, y hi)
   int dirichlet;               // bit s set = side s on Gamma_0: identity rows and columns there
   int residual;                // 0: y = OP u;  1: y = f - OP u
+  int out64;                   // double-single apply only: y in FP64 (the rounded sum of each pair) instead of FP32
   int tc;                      // tile edge in cells (0: default for p)
   T h, h2, alpha;              // alpha = shift (0 for A)
   T M[81], K[81];              // 1-D reference mass / stiffness, (p+1)^2

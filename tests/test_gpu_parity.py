@@ -360,6 +360,23 @@ def test_mixed_solve_reaches_tolerance(th, prec):
     assert relerr(host(x), xs) < 1e-6
 
 
+@pytest.mark.parametrize("c", [CASES[5], CASES[6]])
+def test_mixed_solve_double_single_products(th, c):
+    """The mixed form's FGMRES products A z in double-single arithmetic with FP64
+    output (variant 1, default) against the FP64 apply (variant 0): the same
+    iterations (within one), the same 1e-8 true residual, solutions within
+    1e-9 of each other (the products differ by ~1e-14 relative)."""
+    S, P = build(th, c, nrhs=2, prec="bf16", extra_prec=("fp64",), restart=40)
+    F = dev(synth.random_complex((2, P.N), 95))
+    assert S.get_variant("az", "fp32") == 1
+    X1, i1 = S.solve(F)
+    S.set_variant("az", "fp32", 0)
+    X0, i0 = S.solve(F)
+    assert i1["relres_max"] <= 1e-8 and i0["relres_max"] <= 1e-8
+    assert abs(i1["iters"] - i0["iters"]) <= 1
+    assert relerr(host(X1), host(X0)) < 1e-8
+
+
 # ------------------------------------------------------------ full-size, sampled
 def test_full_size_apply_and_cycle(th):
     """40-wavelength 401^2 workload: the apply at full size and one cycle compared on sampled nodes."""
