@@ -736,7 +736,7 @@ __global__ void __launch_bounds__(512, 1) k_chunk_sweep_mr(const CoarsePartArgs<
 // HBM about once per sweep for all right-hand sides (the per-tile sweep
 // above reads it once per tile), and the grid has P x groups CTAs.
 template <typename T, int NBW>
-__global__ void __launch_bounds__(256, 1) k_sweep_cols(const CoarsePartArgs<T> a) {
+__global__ void __launch_bounds__(512, 1) k_sweep_cols(const CoarsePartArgs<T> a) {
   using C = typename Cx<T>::t;
   const int chunk = blockIdx.x % a.P, grp = blockIdx.x / a.P;
   const int r0 = grp * NBW, nb = min(NBW, a.nrhs - r0);
@@ -782,69 +782,55 @@ __global__ void __launch_bounds__(256, 1) k_sweep_cols(const CoarsePartArgs<T> a
     }
     __syncthreads();
     const C* g = a.Gt + (size_t)j * mc * mcr;
-    // two rows per thread (rows ra and rb = ra + blockDim): every vector entry
-    // read from shared memory serves both
-    for (int base = 0; base < mc; base += 2 * nth) {
-      const int ra = base + tid, rb = base + nth + tid;
-      const bool va = ra < mc, vb = rb < mc;
-      C acc0[NBW], acc1[NBW];
+    for (int rr = tid; rr < mc; rr += nth) {
+      C acc[NBW];
 #pragma unroll
       for (int r = 0; r < NBW; ++r) {
-        acc0[r].x = 0;
-        acc0[r].y = 0;
-        acc1[r].x = 0;
-        acc1[r].y = 0;
+        acc[r].x = 0;
+        acc[r].y = 0;
       }
-      C zero;
-      zero.x = 0;
-      zero.y = 0;
-      int c = 0;
-      for (; c + 4 <= mc; c += 4) {
-        C ga[4], gb[4];
+      // blocks of 8 columns; the next block's entries are loaded before the
+      // current block's products, so the L2 latency overlaps them
+      const int c8 = mc & ~7;
+      C gv[8], gn[8];
+      if (c8 > 0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          ga[u] = va ? g[(size_t)(c + u) * mcr + ra] : zero;
-          gb[u] = vb ? g[(size_t)(c + u) * mcr + rb] : zero;
+        for (int u = 0; u < 8; ++u) gv[u] = g[(size_t)u * mcr + rr];
+      }
+      for (int c = 0; c < c8; c += 8) {
+        if (c + 8 < c8) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) gn[u] = g[(size_t)(c + 8 + u) * mcr + rr];
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
           const C* tc = tv + (size_t)(c + u) * NBW;
 #pragma unroll
-          for (int r = 0; r < NBW; ++r) {
-            const C t = tc[r];
-            cmac(acc0[r], ga[u], t);
-            cmac(acc1[r], gb[u], t);
-          }
+          for (int r = 0; r < NBW; ++r) cmac(acc[r], gv[u], tc[r]);
         }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) gv[u] = gn[u];
       }
-      for (; c < mc; ++c) {
-        const C ga = va ? g[(size_t)c * mcr + ra] : zero, gb = vb ? g[(size_t)c * mcr + rb] : zero;
+      for (int c = c8; c < mc; ++c) {
+        const C gc = g[(size_t)c * mcr + rr];
         const C* tc = tv + (size_t)c * NBW;
 #pragma unroll
-        for (int r = 0; r < NBW; ++r) {
-          const C t = tc[r];
-          cmac(acc0[r], ga, t);
-          cmac(acc1[r], gb, t);
-        }
+        for (int r = 0; r < NBW; ++r) cmac(acc[r], gc, tc[r]);
       }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int rr = h ? rb : ra;
-        if (!(h ? vb : va)) continue;
-#pragma unroll
-        for (int r = 0; r < NBW; ++r) {
-          const C av = h ? acc1[r] : acc0[r];
-          C* xo = a.x + (size_t)(r0 + r) * a.Nc + (size_t)j * mc + rr;
-          C val = av;
-          if (!fwd) {
-            C z = zero;
-            if (r < nb) z = *xo;  // the padded columns of a ragged group are never stored
-            val.x = z.x - av.x;
-            val.y = z.y - av.y;
-          }
-          cur[(size_t)rr * NBW + r] = val;
-          if (r < nb) *xo = val;  // z_j forward, y_j backward (y_{A+L-1} = z_{A+L-1})
+      for (int r = 0; r < NBW; ++r) {
+        C* xo = a.x + (size_t)(r0 + r) * a.Nc + (size_t)j * mc + rr;
+        C val = acc[r];
+        if (!fwd) {
+          C z;
+          z.x = 0;
+          z.y = 0;
+          if (r < nb) z = *xo;  // the padded columns of a ragged group are never stored
+          val.x = z.x - acc[r].x;
+          val.y = z.y - acc[r].y;
         }
+        cur[(size_t)rr * NBW + r] = val;
+        if (r < nb) *xo = val;  // z_j forward, y_j backward (y_{A+L-1} = z_{A+L-1})
       }
     }
     __syncthreads();
@@ -933,7 +919,7 @@ __global__ void __launch_bounds__(256) k_sep_cols(const CoarsePartArgs<T> a) {
 // owns a row and NBW accumulators and reads its row's entries (consecutive
 // across lanes) and the separator values of its group from shared memory.
 template <typename T, int NBW>
-__global__ void __launch_bounds__(256) k_spikes_cols(const CoarsePartArgs<T> a) {
+__global__ void __launch_bounds__(512) k_spikes_cols(const CoarsePartArgs<T> a) {
   using C = typename Cx<T>::t;
   ptx::grid_dep_wait();  // launched with a programmatic dependency inside the cycle
   ptx::grid_dep_launch();
@@ -958,62 +944,47 @@ __global__ void __launch_bounds__(256) k_spikes_cols(const CoarsePartArgs<T> a) 
   }
   __syncthreads();
   const C* lr = a.LRt + (size_t)j * K * a.mcr;
-  C zero;
-  zero.x = 0;
-  zero.y = 0;
-  // two rows per thread (ra and rb = ra + blockDim): each staged value serves both
-  for (int base = 0; base < mc; base += 2 * nth) {
-    const int ra = base + tid, rb = base + nth + tid;
-    const bool va = ra < mc, vb = rb < mc;
-    C acc0[NBW], acc1[NBW];
+  for (int rr = tid; rr < mc; rr += nth) {
+    C acc[NBW];
 #pragma unroll
     for (int r = 0; r < NBW; ++r) {
-      acc0[r] = zero;
-      acc1[r] = zero;
+      acc[r].x = 0;
+      acc[r].y = 0;
     }
-    int c = 0;
-    for (; c + 4 <= K; c += 4) {
-      C la[4], lb[4];
+    const int c8 = K & ~7;
+    C lv[8], ln[8];
+    if (c8 > 0) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        la[u] = va ? lr[(size_t)(c + u) * a.mcr + ra] : zero;
-        lb[u] = vb ? lr[(size_t)(c + u) * a.mcr + rb] : zero;
+      for (int u = 0; u < 8; ++u) lv[u] = lr[(size_t)u * a.mcr + rr];
+    }
+    for (int c = 0; c < c8; c += 8) {
+      if (c + 8 < c8) {  // the next block's entries ahead of this block's products
+#pragma unroll
+        for (int u = 0; u < 8; ++u) ln[u] = lr[(size_t)(c + 8 + u) * a.mcr + rr];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const C* xc = xs + (size_t)(c + u) * NBW;
 #pragma unroll
-        for (int r = 0; r < NBW; ++r) {
-          const C t = xc[r];
-          cmac(acc0[r], la[u], t);
-          cmac(acc1[r], lb[u], t);
-        }
+        for (int r = 0; r < NBW; ++r) cmac(acc[r], lv[u], xc[r]);
       }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) lv[u] = ln[u];
     }
-    for (; c < K; ++c) {
-      const C la = va ? lr[(size_t)c * a.mcr + ra] : zero, lb = vb ? lr[(size_t)c * a.mcr + rb] : zero;
+    for (int c = c8; c < K; ++c) {
+      const C lc = lr[(size_t)c * a.mcr + rr];
       const C* xc = xs + (size_t)c * NBW;
 #pragma unroll
-      for (int r = 0; r < NBW; ++r) {
-        const C t = xc[r];
-        cmac(acc0[r], la, t);
-        cmac(acc1[r], lb, t);
-      }
+      for (int r = 0; r < NBW; ++r) cmac(acc[r], lc, xc[r]);
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int rr = h ? rb : ra;
-      if (!(h ? vb : va)) continue;
-#pragma unroll
-      for (int r = 0; r < NBW; ++r) {
-        if (r < nb) {
-          const C av = h ? acc1[r] : acc0[r];
-          C* xo = a.x + (size_t)(r0 + r) * a.Nc + (size_t)j * mc + rr;
-          C v = *xo;
-          v.x -= av.x;
-          v.y -= av.y;
-          *xo = v;
-        }
+    for (int r = 0; r < NBW; ++r) {
+      if (r < nb) {
+        C* xo = a.x + (size_t)(r0 + r) * a.Nc + (size_t)j * mc + rr;
+        C v = *xo;
+        v.x -= acc[r].x;
+        v.y -= acc[r].y;
+        *xo = v;
       }
     }
   }
@@ -1297,7 +1268,7 @@ static cudaError_t launch_coarse_part_cols(const CoarsePartArgs<T>& a, cudaStrea
   cudaError_t e = cudaFuncSetAttribute(k_sweep_cols<T, NBW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int groups = (a.nrhs + NBW - 1) / NBW;
-  e = launch_pdl(k_sweep_cols<T, NBW>, dim3(a.P * groups), dim3(256), smem, s, 0, a);
+  e = launch_pdl(k_sweep_cols<T, NBW>, dim3(a.P * groups), dim3(512), smem, s, 0, a);
   if (e != cudaSuccess || a.P < 2) return e;
   dim3 g1((unsigned)((a.nred + 255) / 256), a.nrhs);
   e = launch_pdl(k_reduced_rhs<T>, g1, dim3(256), 0, s, 0, a);
@@ -1315,7 +1286,7 @@ static cudaError_t launch_coarse_part_cols(const CoarsePartArgs<T>& a, cudaStrea
       if (e != cudaSuccess) return e;
       e = cudaFuncSetAttribute(k_spikes_cols<T, NBW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
       if (e != cudaSuccess) return e;
-      return launch_pdl(k_spikes_cols<T, NBW>, dim3((unsigned)(a.mc * groups)), dim3(256), sm1, s, 0, a);
+      return launch_pdl(k_spikes_cols<T, NBW>, dim3((unsigned)(a.mc * groups)), dim3(512), sm1, s, 0, a);
     }
   }
   return launch_tsgemm<T, mr_tile<T>()>(a, s);
