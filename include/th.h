@@ -367,7 +367,8 @@ enum {
   TH_K_RESID = 10,      /* (variants only) the mixed form's outer residual, see th_residual_mixed */
   TH_K_CYCLE = 11,      /* (variants only) launch structure of the cycle, see th_set_kernel_variant */
   TH_K_COARSE_MULTI = 12, /* (variants only) 2-D coarse sweep for 8 or more right-hand sides */
-  TH_K_AZ = 13          /* (variants only) the FGMRES product A z of the mixed forms */
+  TH_K_AZ = 13,         /* (variants only) the FGMRES product A z of the mixed forms */
+  TH_K_COARSE_REFINE = 14 /* (variants only) refinement steps of the mixed 2-D coarse solve */
 };
 
 /* Per-kernel timing for measurement: with enable = 1 every later kernel
@@ -429,7 +430,18 @@ th_status th_peak_fma(int prec, int iters, double* flops_per_s, void* stream);
  *              groups within one CTA per SM), each G_j streamed once for all
  *              groups through L2; 0 one
  *              thread-block cluster per chunk and tile of 2-8 right-hand sides
- *              (the tile count multiplies the G_j reads); prec is ignored;
+ *              (the tile count multiplies the G_j reads); 2 the column-group
+ *              sweep of variant 1, then the separator product and the spike
+ *              correction on the tensor cores for groups of up to 64
+ *              right-hand sides, with the reduced inverse, the spikes and
+ *              their operands each held as two BF16 numbers (hi + lo, 16
+ *              significant bits; mixed contexts with nrhs_max >= 8, else as
+ *              variant 1); prec is ignored;
+ *   TH_K_COARSE_REFINE: steps (0 to 3) of iterative refinement after the
+ *              mixed form's 2-D coarse solve: z = r_c - A_q u_c in FP32, the
+ *              same solve of z, u_c += its solution.  The set-up chooses the
+ *              default from the FP32 solve's residual on a seeded right-hand
+ *              side; prec is ignored;
  *   TH_K_COARSE_SOLVE: one-right-hand-side chunk sweep of the 2-D coarse
  *              solve: 0 = two phases per block step (512 threads), 1 = one
  *              cluster barrier per step (1024 threads, m_c <= 256), 2 = rows

@@ -63,6 +63,7 @@ struct th_ctx {
   int cs_variant = 1;        // one-rhs coarse chunk sweep: 0 two-phase, 1 one barrier per step (autotuned)
   int fuse = 1;              // cycle with u = 0 on entry: combine, prolongation and widening fused (TH_K_CYCLE)
   int cs_multi = 1;          // 8 or more right-hand sides: 0 per-tile cluster sweep, 1 column groups (TH_K_COARSE_MULTI)
+  int coarse_refine = 0;     // mixed 2-D coarse solve: refinement steps on its FP32 residual (TH_K_COARSE_REFINE)
   unsigned char* Wu = nullptr;  // BF16 inverse rows in the tcgen05 operand layout (NR <= 128)
   int sms = 152;
   int device = -1;          // CUDA device the context was set up on
@@ -98,11 +99,19 @@ struct th_ctx {
   double2* Gt64 = nullptr;
   float2* Gt32 = nullptr;
   float2* LRt32 = nullptr;  // spikes transposed ([j][col][mcr]) for the grouped FP32 spike correction (nrhs_max >= 8)
+  // tensor-core separator product and spike correction (mixed 2-D, nrhs_max >= 8, P > 1): BF16 reduced
+  // inverse and spikes in 128-row tiles of 64-column operand chunks, their tile tables and the BF16
+  // operand staging of the reduced right-hand sides and separator values (coarse_umma.cu)
+  unsigned char *Sb16 = nullptr, *LRb16 = nullptr, *rst16 = nullptr, *xst16 = nullptr;
+  th::CoarseTile *tiles_s = nullptr, *tiles_l = nullptr;
+  int ntiles_s = 0, ntiles_l = 0, nkc_s = 0, nkc_m = 0;
+  long long lrb_chunks = 0;  // A chunks of the spikes over all tiles
+  th::CoarseUmmaArgs umma{};
   // cycle work vectors
   double2 *r64 = nullptr, *s64 = nullptr, *v64 = nullptr, *V64 = nullptr, *rc64 = nullptr, *uc64 = nullptr,
           *zc64 = nullptr, *t64 = nullptr;
   float2 *f32 = nullptr, *u32 = nullptr, *r32 = nullptr, *s32 = nullptr, *v32 = nullptr, *V32 = nullptr,
-         *rc32 = nullptr, *uc32 = nullptr, *zc32 = nullptr;
+         *rc32 = nullptr, *uc32 = nullptr, *zc32 = nullptr, *wc32 = nullptr;
   // FGMRES
   double2 *Vk = nullptr, *Zk = nullptr, *w = nullptr, *h1 = nullptr, *h2 = nullptr, *ybuf = nullptr,
           *dpart = nullptr;
@@ -286,6 +295,29 @@ void carve_all(th_ctx& x, Carve& c) {
       x.rh32 = c.take<float2>(nred * nr);
       if (nr >= 2) x.Gt32 = c.take<float2>(mm * x.mcr);
       if (nr >= 8) x.LRt32 = c.take<float2>((size_t)g.mc * 2 * x.mcp * x.mcr);
+      if (nr >= 8 && x.P > 1) {
+        // chunk lengths of coarse_partition (P - 1 separator rows between P chunks)
+        const int rows = g.mc - (x.P - 1), base = rows / x.P, rem = rows % x.P;
+        x.nkc_s = (x.nred + 31) / 32;
+        x.nkc_m = (g.mc + 31) / 32;
+        x.ntiles_s = (x.nred + 127) / 128;
+        x.ntiles_l = 0;
+        x.lrb_chunks = 0;
+        for (int ch = 0; ch < x.P; ++ch) {
+          const long long L = base + (ch < rem ? 1 : 0);
+          const int t = (int)((L * g.mc + 127) / 128);
+          const int sides = (ch > 0 ? 1 : 0) + (ch < x.P - 1 ? 1 : 0);
+          x.ntiles_l += t;
+          x.lrb_chunks += (long long)t * sides * x.nkc_m;
+        }
+        const size_t groups = (size_t)(nr + 63) / 64;
+        x.Sb16 = c.take<unsigned char>((size_t)x.ntiles_s * x.nkc_s * 32768);
+        x.LRb16 = c.take<unsigned char>((size_t)x.lrb_chunks * 32768);
+        x.rst16 = c.take<unsigned char>(groups * x.nkc_s * 16384);
+        x.xst16 = c.take<unsigned char>(groups * (x.P - 1) * x.nkc_m * 16384);
+        x.tiles_s = c.take<th::CoarseTile>(x.ntiles_s);
+        x.tiles_l = c.take<th::CoarseTile>(x.ntiles_l);
+      }
     }
     x.f32 = c.take<float2>((size_t)nr * g.N);
     x.u32 = c.take<float2>((size_t)nr * g.N);
@@ -295,6 +327,10 @@ void carve_all(th_ctx& x, Carve& c) {
     x.V32 = c.take<float2>((size_t)nr * g.nsub * g.NR);
     x.rc32 = c.take<float2>((size_t)nr * g.Nc);
     x.uc32 = c.take<float2>((size_t)nr * g.Nc);
+    if (!d3 && qs) {  // coarse residual and correction of the refinement steps
+      x.zc32 = c.take<float2>((size_t)nr * g.Nc);
+      x.wc32 = c.take<float2>((size_t)nr * g.Nc);
+    }
   }
   const int m = prm.restart;
   x.Vk = c.take<double2>((size_t)(m + 1) * nr * g.N);
@@ -364,6 +400,23 @@ uint16_t f2bf(float f) {
   if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);  // inf / nan
   u += 0x7fffu + ((u >> 16) & 1u);
   return (uint16_t)(u >> 16);
+}
+
+// a complex value as four BF16 parts (re hi, im hi, re lo, im lo), `part` entries apart:
+// v = hi + lo with hi = bf16(v), lo = bf16(v - hi), both rounded to nearest
+void put_split(uint16_t* dst, int off, int part, cplx v) {
+  const double re = v.real(), im = v.imag();
+  const uint16_t hr = f2bf((float)re), hi = f2bf((float)im);
+  auto up = [](uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+  };
+  dst[off] = hr;
+  dst[part + off] = hi;
+  dst[2 * part + off] = f2bf((float)(re - up(hr)));
+  dst[3 * part + off] = f2bf((float)(im - up(hi)));
 }
 
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -767,8 +820,8 @@ th_status gal_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th::Cx
 }
 
 template <typename T>
-th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th::Cx<T>::t* uc, int nrhs,
-                        cudaStream_t s) {
+th_status coarse_solve_once_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th::Cx<T>::t* uc, int nrhs,
+                             cudaStream_t s) {
   if (x.g.dim == 3) return coarse_solve3_<T>(x, rc, uc, nrhs, s);
   if (x.gal) return gal_solve_<T>(x, rc, uc, nrhs, s);
   using B = PrecBufs<T>;
@@ -795,7 +848,14 @@ th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th:
   a.rpc = x.rpc;
   a.Lmax = x.Lmax;
   a.Gt = B::Gt(x);
-  if constexpr (std::is_same<T, float>::value) a.LRt = x.LRt32;
+  if constexpr (std::is_same<T, float>::value) {
+    a.LRt = x.LRt32;
+    if (x.Sb16) {
+      a.rst = x.rst16;
+      a.nkc_s = x.nkc_s;
+      a.umma = &x.umma;
+    }
+  }
   a.mcr = x.mcr;
   a.rpcm = x.rpcm;
   a.nrhs = nrhs;
@@ -807,6 +867,44 @@ th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th:
   x.launches += (x.P > 1) ? 4 : 1;
   Prof prof(x, TH_K_COARSE_SOLVE, s);
   return cuda_status(th::launch_coarse_part<T>(a, nrhs, x.cluster, s));
+}
+
+// FP32 coarse residual z = r_c - A_q u_c (2-D QSFEM coarse level)
+th_status coarse_residual32(th_ctx& x, const float2* rc, const float2* uc, float2* z, int nrhs, cudaStream_t s) {
+  th::CoarseApplyArgs<float> a{};
+  a.x = uc;
+  a.y = z;
+  a.f = rc;
+  a.cell = x.ccell32;
+  a.rho = x.crho32;
+  a.Nc = x.g.Nc;
+  a.nc = x.g.nc;
+  a.mc = x.g.mc;
+  a.dirichlet = x.g.dirichlet[0] | (x.g.dirichlet[1] << 1) | (x.g.dirichlet[2] << 2) | (x.g.dirichlet[3] << 3);
+  x.launches += 1;
+  Prof prof(x, TH_K_COARSE_APPLY, s);
+  return cuda_status(th::launch_coarse_apply<float>(a, nrhs, s));
+}
+
+// The coarse solve of the cycle.  In FP32 the partitioned solve can lose
+// several digits on large coarse grids (its chunk systems amplify rounding
+// errors); there `coarse_refine` steps of iterative refinement follow it:
+// z = r_c - A_q u_c in FP32, w = the same solve of z, u_c += w.
+template <typename T>
+th_status coarse_solve_(th_ctx& x, const typename th::Cx<T>::t* rc, typename th::Cx<T>::t* uc, int nrhs,
+                        cudaStream_t s) {
+  th_status st = coarse_solve_once_<T>(x, rc, uc, nrhs, s);
+  if constexpr (std::is_same<T, float>::value) {
+    if (st != TH_OK || x.coarse_refine <= 0 || x.g.dim != 2 || x.gal || !x.zc32 || !x.wc32) return st;
+    for (int it = 0; it < x.coarse_refine; ++it) {
+      if ((st = coarse_residual32(x, rc, uc, x.zc32, nrhs, s)) != TH_OK) return st;
+      if ((st = coarse_solve_once_<T>(x, x.zc32, x.wc32, nrhs, s)) != TH_OK) return st;
+      x.launches += 1;
+      Prof prof(x, TH_K_VECTOR, s);
+      if ((st = cuda_status(th::launch_cadd32(uc, x.wc32, x.g.Nc * (long long)nrhs, s))) != TH_OK) return st;
+    }
+  }
+  return st;
 }
 
 template <typename T>
@@ -1113,6 +1211,61 @@ th_status tune_coarse(th_ctx& x, cudaStream_t s, int& choice) {
   return TH_OK;
 }
 
+// Accuracy check of the mixed form's 2-D coarse solve: on seeded right-hand
+// sides (1 and, with nrhs_max >= 8, 8 of them: the grouped path), refinement
+// steps are added, at most 2, while the FP32 coarse residual
+// max_i ||r_i - A_q u_i|| / ||r_i|| exceeds 1e-3.  On large coarse grids the
+// partitioned FP32 solve loses several digits (its chunk systems amplify the
+// rounding errors) and the outer iteration then needs more steps; one
+// refinement step restores the FP64 solve's accuracy to about 1e-5.
+th_status tune_coarse_refine(th_ctx& x, cudaStream_t s) {
+  x.coarse_refine = 0;
+  if (!x.zc32 || !x.wc32 || !x.rc32 || !x.uc32 || x.g.dim != 2 || x.gal) return TH_OK;
+  const long long Nc = x.g.Nc;
+  const int nmax = x.prm.nrhs_max >= 8 ? 8 : 1;
+  std::vector<float2> h((size_t)nmax * Nc), z(h.size());
+  uint64_t st = 0x2545F4914F6CDD1Dull;  // xorshift64, values uniform in [-1, 1)
+  auto next = [&]() {
+    st ^= st << 13;
+    st ^= st >> 7;
+    st ^= st << 17;
+    return (float)((double)(st >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+  };
+  for (float2& v : h) {
+    v.x = next();
+    v.y = next();
+  }
+  TH_CU(cudaMemcpyAsync(x.rc32, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+  TH_CU(cudaStreamSynchronize(s));
+  int need = 0;
+  for (int nrhs : {1, nmax}) {
+    for (int r = 0; r <= 2; ++r) {
+      x.coarse_refine = r;
+      th_status e = coarse_solve_<float>(x, x.rc32, x.uc32, nrhs, s);
+      if (e == TH_OK) e = coarse_residual32(x, x.rc32, x.uc32, x.zc32, nrhs, s);
+      if (e != TH_OK) return e;
+      TH_CU(cudaMemcpyAsync(z.data(), x.zc32, (size_t)nrhs * Nc * sizeof(float2), cudaMemcpyDeviceToHost, s));
+      TH_CU(cudaStreamSynchronize(s));
+      double worst = 0.0;
+      for (int i = 0; i < nrhs; ++i) {
+        double zz = 0.0, rr = 0.0;
+        for (long long j = 0; j < Nc; ++j) {
+          const float2 a = z[(size_t)i * Nc + j], b = h[(size_t)i * Nc + j];
+          zz += (double)a.x * a.x + (double)a.y * a.y;
+          rr += (double)b.x * b.x + (double)b.y * b.y;
+        }
+        worst = std::max(worst, std::sqrt(zz / rr));
+      }
+      if (!(worst > 1e-3) || r == 2) {
+        need = std::max(need, r);
+        break;
+      }
+    }
+  }
+  x.coarse_refine = need;
+  return TH_OK;
+}
+
 template <typename T>
 th_status tune_dd(th_ctx& x, int wkind, cudaStream_t s, int& choice) {
   using C = typename th::Cx<T>::t;
@@ -1376,6 +1529,92 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     });
     if ((st = upload_c(nullptr, x->LRt32, lt)) != TH_OK) return st;
   }
+  if (x->Sb16 && x->LRb16) {
+    // split-BF16 operands of the tensor-core separator product and spike
+    // correction: 128-row tiles, 32-column chunks of four parts (re hi, im hi,
+    // re lo, im lo; v = hi + lo, hi = bf16(v), lo = bf16(v - hi)) in the K-major
+    // core-matrix layout (umma_off32); padding rows and columns are zero
+    const int mc = g.mc, nred = x->nred, nkc_s = x->nkc_s, nkc_m = x->nkc_m;
+    const size_t K = 2 * (size_t)x->mcp;  // row length of cpart.LR
+    std::vector<th::CoarseTile> ts(x->ntiles_s), tl;
+    {
+      std::vector<uint16_t> sb((size_t)x->ntiles_s * nkc_s * 16384, 0);
+      th::parallel_for(x->ntiles_s, [&](int t) {
+        for (int kc = 0; kc < nkc_s; ++kc) {
+          uint16_t* ch = sb.data() + ((size_t)t * nkc_s + kc) * 16384;
+          for (int r = 0; r < 128; ++r) {
+            const int row = t * 128 + r;
+            if (row >= nred) break;
+            for (int k = 0; k < 32; ++k) {
+              const int col = kc * 32 + k;
+              if (col >= nred) break;
+              put_split(ch, th::umma_off32(r, k), 4096, cpart.Sinv[(size_t)row * nred + col]);
+            }
+          }
+        }
+      });
+      for (int t = 0; t < x->ntiles_s; ++t)
+        ts[t] = th::CoarseTile{(long long)t * nkc_s * 32768, nkc_s, t * 128, std::min(128, nred - t * 128), -1, -1};
+      if ((st = up(x->Sb16, sb.data(), sb.size() * 2)) != TH_OK) return st;
+      TH_CU(cudaStreamSynchronize(s));
+    }
+    {
+      long long chunk0 = 0;
+      std::vector<int> tch;  // chunk of each tile
+      for (int ch = 0; ch < x->P; ++ch) {
+        const int L = cpart.cb[ch] - cpart.ca[ch] + 1, nrow = L * mc;
+        // separators: chunk 0 has only its right one (index 0), the last chunk only its left one
+        const int b0 = ch > 0 ? ch - 1 : ch, b1 = (ch > 0 && ch < x->P - 1) ? ch : -1;
+        const int nkc = (b1 >= 0 ? 2 : 1) * nkc_m;
+        for (int r0 = 0; r0 < nrow; r0 += 128) {
+          tl.push_back(th::CoarseTile{chunk0 * 32768, nkc, cpart.ca[ch] * mc + r0, std::min(128, nrow - r0), b0, b1});
+          tch.push_back(ch);
+          chunk0 += nkc;
+        }
+      }
+      if ((int)tl.size() != x->ntiles_l || chunk0 != x->lrb_chunks) return TH_ERR_ARG;  // partition mismatch
+      std::vector<uint16_t> lb((size_t)x->lrb_chunks * 16384, 0);
+      th::parallel_for(x->ntiles_l, [&](int t) {
+        const th::CoarseTile& tt = tl[t];
+        for (int kc = 0; kc < tt.nkc; ++kc) {
+          // column block of [L | R]: 0 = the left separator's coupling, 1 = the right one's
+          const int side = tt.b1 >= 0 ? kc / nkc_m : (tch[t] == 0 ? 1 : 0);
+          uint16_t* chp = lb.data() + ((size_t)(tt.a_off / 32768) + kc) * 16384;
+          for (int r = 0; r < tt.rows; ++r) {
+            const size_t xi = (size_t)tt.row0 + r;  // coarse index: block row j, entry rr
+            const size_t j = xi / mc, rr = xi % mc;
+            for (int k = 0; k < 32; ++k) {
+              const int col = (kc % nkc_m) * 32 + k;
+              if (col >= mc) break;
+              put_split(chp, th::umma_off32(r, k), 4096, cpart.LR[(j * mc + rr) * K + (size_t)side * x->mcp + col]);
+            }
+          }
+        }
+      });
+      if ((st = up(x->LRb16, lb.data(), lb.size() * 2)) != TH_OK) return st;
+      if ((st = up(x->tiles_s, ts.data(), ts.size() * sizeof(th::CoarseTile))) != TH_OK) return st;
+      if ((st = up(x->tiles_l, tl.data(), tl.size() * sizeof(th::CoarseTile))) != TH_OK) return st;
+      TH_CU(cudaStreamSynchronize(s));
+    }
+    const size_t groups = (size_t)(x->prm.nrhs_max + 63) / 64;
+    TH_CU(cudaMemsetAsync(x->rst16, 0, groups * nkc_s * 16384, s));
+    TH_CU(cudaMemsetAsync(x->xst16, 0, groups * (x->P - 1) * nkc_m * 16384, s));
+    th::CoarseUmmaArgs& u = x->umma;
+    u.As = x->Sb16;
+    u.Al = x->LRb16;
+    u.tiles_s = x->tiles_s;
+    u.tiles_l = x->tiles_l;
+    u.ntiles_s = x->ntiles_s;
+    u.ntiles_l = x->ntiles_l;
+    u.rst = x->rst16;
+    u.xst = x->xst16;
+    u.sep = x->sep;
+    u.Nc = g.Nc;
+    u.mc = mc;
+    u.nsep = x->P - 1;
+    u.nkc_s = nkc_s;
+    u.nkc_m = nkc_m;
+  }
   if (x->P > 1 && (x->Si64 || x->Si32)) {
     // rows padded to an even length (pairs of complex values per load)
     const size_t nr_ = (size_t)x->nred, ld = nr_ + (nr_ & 1);
@@ -1523,6 +1762,9 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     // one sweep variant serves both precisions: time it where the cycle runs
     if (x->mixed) {
       if ((st = tune_coarse<float>(*x, s, x->cs_variant)) != TH_OK) return st;
+      // the tensor-core separator and spike products for 8 or more right-hand sides where built
+      if (x->Sb16) x->cs_multi = 2;
+      if ((st = tune_coarse_refine(*x, s)) != TH_OK) return st;
     } else if ((st = tune_coarse<double>(*x, s, x->cs_variant)) != TH_OK) {
       return st;
     }
@@ -1540,7 +1782,8 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
 
 th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
   const int vmax = kernel == TH_K_DD ? (prec == TH_PREC_FP32 ? 5 : 3)
-                   : (kernel == TH_K_COARSE_SOLVE || kernel == TH_K_CYCLE) ? 2 : 1;
+                   : kernel == TH_K_COARSE_REFINE ? 3
+                   : (kernel == TH_K_COARSE_SOLVE || kernel == TH_K_CYCLE || kernel == TH_K_COARSE_MULTI) ? 2 : 1;
   if (!x || variant < 0 || variant > vmax || (prec != TH_PREC_FP64 && prec != TH_PREC_FP32))
     return TH_ERR_ARG;
   const bool d = (prec == TH_PREC_FP64);
@@ -1560,6 +1803,8 @@ th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
     x->cs_multi = variant;
   } else if (kernel == TH_K_AZ) {
     x->az_ds = variant;
+  } else if (kernel == TH_K_COARSE_REFINE) {
+    x->coarse_refine = variant;
   } else {
     return TH_ERR_ARG;
   }
@@ -1578,6 +1823,7 @@ th_status th_get_kernel_variant(const th_ctx* x, int kernel, int prec, int* vari
   else if (kernel == TH_K_CYCLE) *variant = x->fuse;
   else if (kernel == TH_K_COARSE_MULTI) *variant = x->cs_multi;
   else if (kernel == TH_K_AZ) *variant = (x->az_ds && x->kcds && x->g.dim == 2) ? 1 : 0;
+  else if (kernel == TH_K_COARSE_REFINE) *variant = (x->zc32 && x->wc32) ? x->coarse_refine : 0;
   else return TH_ERR_ARG;
   return TH_OK;
 }

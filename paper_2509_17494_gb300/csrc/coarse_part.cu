@@ -24,6 +24,10 @@
 // prefetched with cp.async into a double buffer one step ahead.  There are no
 // spin waits: every CTA of a cluster executes the same number of barriers.
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <type_traits>
 
 #include "kernels.h"
 #include "launch.cuh"
@@ -551,6 +555,19 @@ __global__ void __launch_bounds__(256) k_reduced_rhs(const CoarsePartArgs<T> a) 
   if (e + 1 < mc) cmac(v, a.cu[os + e], yp[e + 1]);
   t.x -= v.x;
   t.y -= v.y;
+  if (a.rst) {  // split-BF16 operand chunks of the tensor-core separator product (coarse_umma.cu)
+    const int rhs = blockIdx.y, n = rhs & 63;
+    __nv_bfloat16* st =
+        reinterpret_cast<__nv_bfloat16*>(a.rst + ((size_t)(rhs >> 6) * a.nkc_s + (i >> 5)) * (4 * 64 * 32 * 2));
+    const int off = umma_off32(n, i & 31);
+    const float vr = (float)t.x, vi = (float)t.y;
+    const __nv_bfloat16 hr = __float2bfloat16_rn(vr), hi = __float2bfloat16_rn(vi);
+    st[off] = hr;
+    st[64 * 32 + off] = hi;
+    st[2 * 64 * 32 + off] = __float2bfloat16_rn(vr - __bfloat162float(hr));
+    st[3 * 64 * 32 + off] = __float2bfloat16_rn(vi - __bfloat162float(hi));
+    return;
+  }
   a.rhat[(size_t)blockIdx.y * a.nred + i] = t;
 }
 
@@ -1271,7 +1288,27 @@ static cudaError_t launch_coarse_part_cols(const CoarsePartArgs<T>& a, cudaStrea
   e = launch_pdl(k_sweep_cols<T, NBW>, dim3(a.P * groups), dim3(512), smem, s, 0, a);
   if (e != cudaSuccess || a.P < 2) return e;
   dim3 g1((unsigned)((a.nred + 255) / 256), a.nrhs);
-  e = launch_pdl(k_reduced_rhs<T>, g1, dim3(256), 0, s, 0, a);
+  if constexpr (std::is_same<T, float>::value) {
+    if (a.multi_variant == 2 && a.umma && a.rst) {
+      // the separator product and the spike correction on the tensor cores
+      // (BF16 reduced inverse and spikes, coarse_umma.cu)
+      e = launch_pdl(k_reduced_rhs<T>, g1, dim3(256), 0, s, 0, a);
+      if (e != cudaSuccess) return e;
+      CoarseUmmaArgs u = *a.umma;
+      u.x = a.x;
+      u.nrhs = a.nrhs;
+      u.err = a.err;
+      const int sms = a.nsm > 0 ? a.nsm : 152;
+      e = launch_coarse_umma(u, 0, sms, s);
+      if (e != cudaSuccess) return e;
+      return launch_coarse_umma(u, 1, sms, s);
+    }
+  }
+  {
+    CoarsePartArgs<T> b = a;
+    b.rst = nullptr;
+    e = launch_pdl(k_reduced_rhs<T>, g1, dim3(256), 0, s, 0, b);
+  }
   if (e != cudaSuccess) return e;
   // the spike correction in the same groups from the transposed spikes when the
   // context keeps them; else the tiled products (below)
@@ -1293,11 +1330,15 @@ static cudaError_t launch_coarse_part_cols(const CoarsePartArgs<T>& a, cudaStrea
 }
 
 template <typename T>
-cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster, cudaStream_t s) {
+cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a0, int nrhs, int cluster, cudaStream_t s) {
+  // the BF16 staging of the reduced right-hand sides serves the tensor-core path only
+  CoarsePartArgs<T> a = a0;
+  const bool tc = a.multi_variant == 2 && nrhs >= 8 && a.umma && a.rst;
+  if (!tc) a.rst = nullptr;
   if (nrhs >= 2 && a.Gt) {
     CoarsePartArgs<T> b = a;
     b.nrhs = nrhs;
-    if (a.multi_variant == 1 && nrhs >= 8) {
+    if (a.multi_variant >= 1 && nrhs >= 8) {
       // the narrowest group width with at most one CTA per SM: P * ceil(nrhs / NBW) <= SMs
       const int per = std::max(1, (a.nsm > 0 ? a.nsm : 152) / std::max(1, a.P));
       const int need = (nrhs + per - 1) / per;
@@ -1308,6 +1349,7 @@ cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster
       else if (need <= 16) e = launch_coarse_part_cols<T, 16>(b, s);
       if (e != cudaErrorInvalidValue) return e;
     }
+    b.rst = nullptr;
     return launch_coarse_part_mr<T>(b, cluster, s);
   }
   const bool pf = chunk_sweep_smem(a, true) <= 220 * 1024;

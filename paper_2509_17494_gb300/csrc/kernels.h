@@ -181,9 +181,12 @@ struct CoarseApplyArgs {
   long long Nc;
   int nc, mc;
   int dirichlet;                   // bit s set = side s on Gamma_0: identity rows, zero columns
+  const typename Cx<T>::t* f;      // non-null: y = f - A_q x (the residual) instead of A_q x
 };
 template <typename T>
 cudaError_t launch_coarse_apply(const CoarseApplyArgs<T>& a, int nrhs, cudaStream_t s);
+// u += w, n complex FP32 entries
+cudaError_t launch_cadd32(float2* u, const float2* w, long long n, cudaStream_t s);
 
 // ------------------------------------------------------- K8 coarse solve
 template <typename T>
@@ -228,11 +231,48 @@ struct CoarsePartArgs {
   int sweep_variant;             // one-rhs chunk sweep: 0 two-phase (512 threads), 1 one barrier per step (1024),
                                  // 2 st.async row exchange on mbarriers (no cluster barrier per step)
   int* err;                      // device flag set by a bounded wait that gave up (variant 2)
-  int multi_variant;             // 8 or more right-hand sides: 0 per-tile cluster sweep, 1 column groups per CTA
+  int multi_variant;             // 8 or more right-hand sides: 0 per-tile cluster sweep, 1 column groups per CTA,
+                                 // 2 column groups + tensor-core separator and spike products (umma below)
   int nsm;                       // SMs of the device (column groups are sized to fill them in one wave)
+  // reduced right-hand sides as split-BF16 operand chunks (tensor-core path), else null:
+  // [rhs / 64][nkc_s][re hi | im hi | re lo | im lo][umma_off32(rhs % 64, k % 32)]
+  unsigned char* rst;
+  int nkc_s;
+  const struct CoarseUmmaArgs* umma;  // host-side description of the tensor-core products, or null
 };
 template <typename T>
 cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster, cudaStream_t s);
+
+// Offset (in elements) of entry (r, k) of a 32-column chunk in the tensor
+// cores' no-swizzle K-major operand layout: core matrices of 8 rows x 8
+// 16-bit entries (128 bytes), arranged [r / 8][k / 8] with k / 8 fastest.
+__host__ __device__ inline int umma_off32(int r, int k) {
+  return (((r >> 3) * 4 + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+// K8c: one 128-row tile of a tensor-core coarse product (coarse_umma.cu)
+struct CoarseTile {
+  long long a_off;  // byte offset of the tile's A chunks (nkc x 32 KB)
+  int nkc;          // chunks of 32 columns
+  int row0;         // separator product: first reduced index; spikes: x index of the first row
+  int rows;         // valid rows (<= 128)
+  int b0, b1;       // spikes: separator of the first and second column block (b1 = -1: one block)
+};
+struct CoarseUmmaArgs {
+  const unsigned char* As;  // split-BF16 reduced inverse, ntiles_s tiles
+  const unsigned char* Al;  // split-BF16 spikes, ntiles_l tiles
+  const CoarseTile* tiles_s;
+  const CoarseTile* tiles_l;
+  int ntiles_s, ntiles_l;
+  const unsigned char* rst;  // reduced right-hand sides, 16 KB chunks [rhs / 64][nkc_s]
+  unsigned char* xst;        // separator values, 16 KB chunks [rhs / 64][nsep][nkc_m] (written by MODE 0)
+  float2* x;                 // [rhs][Nc]
+  const int* sep;            // separator rows
+  long long Nc;
+  int mc, nsep, nkc_s, nkc_m, nrhs;
+  int* err;
+};
+cudaError_t launch_coarse_umma(const CoarseUmmaArgs& a, int mode, int sms, cudaStream_t s);
 
 // ------------------------------------------------------- 3-D (unit cube, Q2)
 template <typename T>

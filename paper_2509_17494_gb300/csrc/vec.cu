@@ -119,7 +119,13 @@ __global__ void __launch_bounds__(256) k_coarse_apply(const CoarseApplyArgs<T> a
            ((a.dirichlet & 4) && iy == 0) || ((a.dirichlet & 8) && iy == a.mc - 1);
   };
   if (a.dirichlet && dnode(Jx, Jy)) {  // identity row on Gamma_0
-    a.y[(size_t)blockIdx.y * a.Nc + J] = x[J];
+    C v = x[J];
+    if (a.f) {
+      const C fv = a.f[(size_t)blockIdx.y * a.Nc + J];
+      v.x = fv.x - v.x;
+      v.y = fv.y - v.y;
+    }
+    a.y[(size_t)blockIdx.y * a.Nc + J] = v;
     return;
   }
   // with Gamma_0 present the values of its nodes are left out (zero columns)
@@ -166,6 +172,11 @@ __global__ void __launch_bounds__(256) k_coarse_apply(const CoarseApplyArgs<T> a
       cfma(acc, r, v);
     }
   }
+  if (a.f) {
+    const C fv = a.f[(size_t)blockIdx.y * a.Nc + J];
+    acc.x = fv.x - acc.x;
+    acc.y = fv.y - acc.y;
+  }
   a.y[(size_t)blockIdx.y * a.Nc + J] = acc;
 }
 
@@ -190,6 +201,19 @@ __global__ void k_f2d(const float* __restrict__ in, double* __restrict__ out, lo
 static unsigned vgrid(long long n) {
   long long b = (n + 255) / 256;
   return (unsigned)(b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b));
+}
+__global__ void k_cadd32(float2* __restrict__ u, const float2* __restrict__ w, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float2 a = u[i];
+    const float2 b = w[i];
+    a.x += b.x;
+    a.y += b.y;
+    u[i] = a;
+  }
+}
+cudaError_t launch_cadd32(float2* u, const float2* w, long long n, cudaStream_t s) {
+  k_cadd32<<<vgrid(n), 256, 0, s>>>(u, w, n);
+  return cudaGetLastError();
 }
 cudaError_t launch_d2f(const double* in, float* out, long long n, cudaStream_t s) {
   k_d2f<<<vgrid(n), 256, 0, s>>>(in, out, n);

@@ -131,6 +131,24 @@ def test_zero_wait_limit_coarse_row_exchange(th):
     assert relerr(got, B.solve(rc)) < 1e-4
 
 
+def test_zero_wait_limit_tensor_core_coarse_products(th):
+    """The tensor-core separator and spike products of the grouped coarse solve
+    (8 right-hand sides, split-BF16 operands)."""
+    nrhs = 8
+    S, P = _case(th, n=25, nrhs=nrhs, prec="bf16", extra_prec=("fp64",))
+    assert S.get_variant("coarse_multi", "fp32") == 2
+    B = twogrid.BandedSolver(P.Aq)
+    rc = synth.random_complex((nrhs, P.Nc), 10)
+    S.set_wait_limit(0)
+    S.coarse_solve(dev(rc))
+    _expect_timeout(th, S)
+    S.set_wait_limit(-1)
+    got = host(S.coarse_solve(dev(rc)))
+    S.device_status()
+    for i in range(nrhs):
+        assert relerr(got[i], B.solve(rc[i])) < 2e-4, i
+
+
 def test_zero_wait_limit_corrector_convolutions(th):
     w = synth.workload("square10_q4_n25")
     S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=0.5, l_dd=2, prec="bf16",

@@ -8,6 +8,8 @@ Tolerances (relative, max-norm over the output):
   * FP64 coarse solve and two-grid cycle: 1e-9 (explicit block inverses vs
     banded LU on the coarse Helmholtz matrix, condition numbers up to ~1e6);
   * FP64 FGMRES: identical iteration count, solutions within 1e-7;
+  * FP32 coarse solve: 1e-4; with the tensor-core separator and spike
+    products (operands as two BF16 numbers, 2^-17 relative each): 2e-4;
   * FP32 applies: 2e-6; FP32 / FP16 / BF16 smoothers against the FP64
     smoother: 1e-5 / 2e-3 / 2e-2 (unit roundoff of the stored rows times the
     growth of a few-hundred-term sums); mixed-precision solves reach the same
@@ -167,6 +169,7 @@ def test_coarse_solve_many_rhs(th, c, nrhs):
     against the FP32 one-right-hand-side sweep (same products, other
     summation order: a few FP32 roundings times the coarse condition number)."""
     S, P = build(th, c, nrhs=nrhs, prec="fp64", extra_prec=("fp32",))
+    S.set_variant("coarse_multi", "fp32", 1)  # FP32 products (the tensor-core ones: test below)
     rc = synth.random_complex((nrhs, P.Nc), 31)
     B = twogrid.BandedSolver(P.Aq)
     want = np.stack([B.solve(rc[i]) for i in range(nrhs)])
@@ -185,18 +188,21 @@ def test_coarse_solve_many_rhs(th, c, nrhs):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_coarse_solve_column_groups(th, c, prec):
     """Eight or more right-hand sides: the sweep in groups of 8 per CTA (variant
-    1, default) and the per-tile cluster sweep (variant 0), on two full groups
-    and a ragged one, against the oracle's banded LU (FP64 1e-9, FP32 1e-4)."""
+    1, the FP64 default), the per-tile cluster sweep (variant 0) and, in the
+    mixed form, the column-group sweep with the tensor-core separator and spike
+    products (variant 2, its default), on two full groups and a ragged one,
+    against the oracle's banded LU (FP64 1e-9, FP32 1e-4, split BF16 2e-4)."""
     nrhs = 20
     extra = ("fp64",) if prec != "fp64" else ()
     S, P = build(th, c, nrhs=nrhs, prec=prec, extra_prec=extra)
-    assert S.get_variant("coarse_multi", prec) == 1
+    assert S.get_variant("coarse_multi", prec) == (1 if prec == "fp64" else 2)
+    assert S.get_variant("coarse_refine", prec) == 0  # small grids: the FP32 solve is accurate
     rc = synth.random_complex((nrhs, P.Nc), 33)
     B = twogrid.BandedSolver(P.Aq)
     want = np.stack([B.solve(rc[i]) for i in range(nrhs)])
-    tol = 1e-9 if prec == "fp64" else 1e-4
     outs = []
-    for v in (1, 0):
+    for v in ((1, 0) if prec == "fp64" else (2, 1, 0)):
+        tol = 1e-9 if prec == "fp64" else (2e-4 if v == 2 else 1e-4)
         S.set_variant("coarse_multi", prec, v)
         outs.append(host(S.coarse_solve(dev(rc))))
         S.device_status()
@@ -204,6 +210,62 @@ def test_coarse_solve_column_groups(th, c, prec):
             assert relerr(outs[-1][i], want[i]) < tol, (v, i)
     again = host(S.coarse_solve(dev(rc)))
     assert np.array_equal(again, outs[-1])
+
+
+@pytest.mark.parametrize("c", CASES)
+def test_coarse_solve_tensor_core_products(th, c):
+    """Variant 2 of the grouped coarse solve on 70 right-hand sides (a full group
+    of 64 and a ragged one of 6): the FP32 column-group sweep, then the separator
+    product and the spike correction on the tensor cores with every operand as
+    two BF16 numbers (hi + lo: 2^-17 relative each, sums over at most a few
+    hundred terms, amplified about tenfold by the chunk systems of these grids:
+    2e-4), against the oracle's banded LU; bitwise repeatable; and the FGMRES
+    solve on 12 right-hand sides takes the iterations of variant 1."""
+    nrhs = 70
+    S, P = build(th, c, nrhs=nrhs, prec="bf16", extra_prec=("fp64",))
+    assert S.get_variant("coarse_multi", "fp32") == 2
+    rc = synth.random_complex((nrhs, P.Nc), 34)
+    B = twogrid.BandedSolver(P.Aq)
+    want = np.stack([B.solve(rc[i]) for i in range(nrhs)])
+    got = host(S.coarse_solve(dev(rc)))
+    S.device_status()
+    for i in range(nrhs):
+        assert relerr(got[i], want[i]) < 2e-4, i
+    assert np.array_equal(host(S.coarse_solve(dev(rc))), got)
+    F = dev(synth.random_complex((12, P.N), 35))
+    X2, i2 = S.solve(F)
+    S.set_variant("coarse_multi", "fp32", 1)
+    X1, i1 = S.solve(F)
+    assert i2["relres_max"] <= 1e-8 and i1["relres_max"] <= 1e-8
+    assert i2["iters"] == i1["iters"]
+    assert relerr(host(X2), host(X1)) < 1e-7
+
+
+@pytest.mark.parametrize("c", [CASES[1], CASES[6]])
+@pytest.mark.parametrize("nrhs", [1, 9])
+def test_coarse_refinement_steps(th, c, nrhs):
+    """Iterative refinement of the mixed form's coarse solve (TH_K_COARSE_REFINE):
+    each step z = r_c - A_q u_c (FP32), the same solve of z, u_c += its solution,
+    contracts the error of the FP32 solve (here about 1e-6 relative, so the
+    refined solve reaches the FP32 residual's level, 1e-6), for one right-hand
+    side and for the grouped tensor-core path."""
+    S, P = build(th, c, nrhs=nrhs, prec="bf16", extra_prec=("fp64",))
+    rc = synth.random_complex((nrhs, P.Nc), 36)
+    B = twogrid.BandedSolver(P.Aq)
+    want = np.stack([B.solve(rc[i]) for i in range(nrhs)])
+    errs = []
+    for r in (0, 1, 2):
+        S.set_variant("coarse_refine", "fp32", r)
+        assert S.get_variant("coarse_refine", "fp32") == r
+        got = host(S.coarse_solve(dev(rc)))
+        S.device_status()
+        errs.append(max(relerr(got[i], want[i]) for i in range(nrhs)))
+    assert errs[0] < 2e-4
+    assert errs[1] < 2e-6 and errs[2] < 2e-6, errs
+    F = dev(synth.random_complex((nrhs, P.N), 37))
+    S.set_variant("coarse_refine", "fp32", 1)
+    X, info = S.solve(F)
+    assert info["relres_max"] <= 1e-8
 
 
 @pytest.mark.parametrize("c", CASES)
@@ -489,8 +551,9 @@ def test_mixed_outer_residual_double_single(th, c):
 def test_coarse_solve_column_groups_large_grid(th):
     """64 right-hand sides on a 401^2 coarse grid (20 chunks): groups of 10 per
     CTA (7 groups, the last one ragged) so that 20 x 7 CTAs fit the SMs once;
-    FP64 against the FP64 one-right-hand-side solve, FP32 within its own
-    accuracy on this grid, and both by the coarse residual."""
+    FP64 against the FP64 one-right-hand-side solve, FP32 (FP32 or split-BF16
+    tensor-core products) within its own accuracy on this grid, one
+    refinement step within 2e-5, and FP64 by the coarse residual."""
     n, p = 200, 4
     k = synth.random_wavenumber(n, 2, 20.0, seed=5)
     eps = synth.absorbing_layer(n, 2, p, k, 10.0)
@@ -505,10 +568,19 @@ def test_coarse_solve_column_groups_large_grid(th):
     res = S.apply(many, "Aq") - rc
     assert float(torch.linalg.norm(res) / torch.linalg.norm(rc)) < 1e-9
     S.set_precision("fp32")
+    S.set_variant("coarse_refine", "fp32", 0)
+    for v in (1, 2):  # FP32 products, then the split-BF16 tensor-core products
+        S.set_variant("coarse_multi", "fp32", v)
+        m32 = S.coarse_solve(rc)
+        S.device_status()
+        for i in range(64):
+            assert relerr(host(m32[i]), host(many[i])) < 5e-3, (v, i)
+    # one refinement step on the FP32 residual: about the FP32 residual's level
+    S.set_variant("coarse_refine", "fp32", 1)
     m32 = S.coarse_solve(rc)
     S.device_status()
     for i in range(64):
-        assert relerr(host(m32[i]), host(many[i])) < 5e-3, i
+        assert relerr(host(m32[i]), host(many[i])) < 2e-5, i
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])

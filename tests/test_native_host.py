@@ -121,7 +121,9 @@ def test_workspace_size_and_argument_errors(th):
     b = th.workspace_size(25, 4, l_dd=2, nrhs_max=4)
     c = th.workspace_size(25, 4, l_dd=2, prec="bf16", extra_prec=("fp64",))
     assert 0 < a < b and a < c
-    for kw, code in [(dict(n=25, p=3), 1), (dict(n=0, p=4), 1), (dict(n=10, p=4, bc="dirichlet"), 8)]:
+    # Dirichlet sides are built in 2-D only
+    assert th.workspace_size(10, 4, bc="dirichlet") > 0
+    for kw, code in [(dict(n=25, p=3), 1), (dict(n=0, p=4), 1), (dict(n=4, p=2, bc="dirichlet", dim=3), 8)]:
         with pytest.raises(th.ThError) as e:
             th.workspace_size(**kw)
         assert e.value.code == code
