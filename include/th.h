@@ -437,6 +437,11 @@ th_status th_peak_fma(int prec, int iters, double* flops_per_s, void* stream);
  *              their operands each held as two BF16 numbers (hi + lo, 16
  *              significant bits; mixed contexts with nrhs_max >= 8, else as
  *              variant 1); prec is ignored;
+ *   TH_K_KRYLOV: the FGMRES Gram-Schmidt dots, norms and updates of the
+ *              mixed forms: 1 (default) double-single arithmetic on the FP64
+ *              vectors (exact two-float splits, products with their exact
+ *              rounding errors, compensated sums: about 2^-44 relative),
+ *              0 FP64; the FP64 form always uses FP64; prec is ignored;
  *   TH_K_COARSE_REFINE: steps (0 to 3) of iterative refinement after the
  *              mixed form's 2-D coarse solve: z = r_c - A_q u_c in FP32, the
  *              same solve of z, u_c += its solution.  The set-up chooses the

@@ -64,6 +64,7 @@ struct th_ctx {
   int fuse = 1;              // cycle with u = 0 on entry: combine, prolongation and widening fused (TH_K_CYCLE)
   int cs_multi = 1;          // 8 or more right-hand sides: 0 per-tile cluster sweep, 1 column groups (TH_K_COARSE_MULTI)
   int coarse_refine = 0;     // mixed 2-D coarse solve: refinement steps on its FP32 residual (TH_K_COARSE_REFINE)
+  int krylov_ds = 1;         // mixed forms' FGMRES dots, norms and updates: 1 double-single arithmetic, 0 FP64 (TH_K_KRYLOV)
   unsigned char* Wu = nullptr;  // BF16 inverse rows in the tcgen05 operand layout (NR <= 128)
   int sms = 152;
   int device = -1;          // CUDA device the context was set up on
@@ -1805,6 +1806,8 @@ th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
     x->az_ds = variant;
   } else if (kernel == TH_K_COARSE_REFINE) {
     x->coarse_refine = variant;
+  } else if (kernel == TH_K_KRYLOV) {
+    x->krylov_ds = variant;
   } else {
     return TH_ERR_ARG;
   }
@@ -1824,6 +1827,7 @@ th_status th_get_kernel_variant(const th_ctx* x, int kernel, int prec, int* vari
   else if (kernel == TH_K_COARSE_MULTI) *variant = x->cs_multi;
   else if (kernel == TH_K_AZ) *variant = (x->az_ds && x->kcds && x->g.dim == 2) ? 1 : 0;
   else if (kernel == TH_K_COARSE_REFINE) *variant = (x->zc32 && x->wc32) ? x->coarse_refine : 0;
+  else if (kernel == TH_K_KRYLOV) *variant = x->krylov_ds;
   else return TH_ERR_ARG;
   return TH_OK;
 }
@@ -2136,6 +2140,8 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
   const double2* f2 = reinterpret_cast<const double2*>(f);
   double2* u2 = reinterpret_cast<double2*>(u);
   const double tol = x->prm.tol;
+  // the mixed forms' Gram-Schmidt products in double-single arithmetic (the FP64 form stays FP64)
+  const bool kds = x->krylov_ds && x->active != TH_PREC_FP64;
   std::vector<double> fn, beta;
   if ((st = norms(*x, f2, nrhs, fn, s)) != TH_OK) return st;
   for (double v : fn)
@@ -2275,9 +2281,15 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
       x->launches += 6;
       {
         Prof prof(*x, TH_K_KRYLOV, s);
-        TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, s));
-        TH_CU(th::launch_maxpy(x->Vk, vstride, x->h1, j + 2, x->w, N, j + 1, nrhs, -1.0, s));
-        TH_CU(th::launch_norm2(x->w, N, nrhs, x->npart, x->nrm, x->nblk, s));
+        if (kds) {
+          TH_CU(th::launch_mdot_ds(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, s));
+          TH_CU(th::launch_maxpy_ds(x->Vk, vstride, x->h1, j + 2, x->w, N, j + 1, nrhs, -1.0, s));
+          TH_CU(th::launch_norm2_ds(x->w, N, nrhs, x->npart, x->nrm, x->nblk, s));
+        } else {
+          TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, s));
+          TH_CU(th::launch_maxpy(x->Vk, vstride, x->h1, j + 2, x->w, N, j + 1, nrhs, -1.0, s));
+          TH_CU(th::launch_norm2(x->w, N, nrhs, x->npart, x->nrm, x->nblk, s));
+        }
         TH_CU(th::launch_arnoldi(aa, j, s));
         TH_CU(th::launch_scale_rhs(x->w, x->Vk + (size_t)(j + 1) * vstride, x->scal, N, nrhs, s));
       }
@@ -2320,7 +2332,11 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
     }
     TH_CU(cudaMemcpyAsync(x->ybuf, yv.data(), sizeof(double2) * yv.size(), cudaMemcpyHostToDevice, s));
     x->launches += 1;
-    TH_CU(th::launch_maxpy(x->Zk, vstride, x->ybuf, jdone, u2, N, jdone, nrhs, 1.0, s));
+    if (kds) {
+      TH_CU(th::launch_maxpy_ds(x->Zk, vstride, x->ybuf, jdone, u2, N, jdone, nrhs, 1.0, s));
+    } else {
+      TH_CU(th::launch_maxpy(x->Zk, vstride, x->ybuf, jdone, u2, N, jdone, nrhs, 1.0, s));
+    }
     TH_CU(cudaStreamSynchronize(s));
     if (switch_now) {
       switch_now = false;

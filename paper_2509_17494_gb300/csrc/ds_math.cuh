@@ -58,6 +58,14 @@ __device__ __forceinline__ ds ds_from_double(double d) {
   return ds(h, l);
 }
 
+// float -> double by its bit pattern (integer operations only: the FP64 pipe
+// of this GPU is 1/64 of the FP32 rate); subnormal floats become zero
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f), e = (u >> 23) & 0xffu, m = e == 0u ? 0u : (u & 0x7fffffu);
+  const unsigned ed = e == 0u ? 0u : (e == 255u ? 2047u : e + 896u);
+  return __hiloint2double((int)((u & 0x80000000u) | (ed << 20) | (m >> 3)), (int)((m & 7u) << 29));
+}
+
 // Global loads and stores of nodal values: FP64 / FP32 as stored; for the
 // double-single apply the inputs are FP64 vectors and the output is FP32.
 template <typename T>

@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
     if constexpr (std::is_same<T, ds>::value) {
       if (a.out64) {  // FP64 output (the FGMRES product A z of the mixed form)
         reinterpret_cast<double2*>(a.y)[roff + g] =
-            make_double2((double)out.x.h + (double)out.x.l, (double)out.y.h + (double)out.y.l);
+            make_double2(f2d_bits(out.x.h) + f2d_bits(out.x.l), f2d_bits(out.y.h) + f2d_bits(out.y.l));
         continue;
       }
     }

@@ -365,6 +365,13 @@ cudaError_t launch_maxpy(const double2* Vbase, long long vstride, const double2*
 // nrm2[rhs] = ||w[rhs]||^2 (fixed-order two-pass reduction into part/out)
 cudaError_t launch_norm2(const double2* w, long long N, int nrhs, double* part, double* out,
                          int nblk, cudaStream_t s);
+// the same three in double-single arithmetic (the mixed form's FGMRES; vec.cu)
+cudaError_t launch_mdot_ds(const double2* Vbase, long long vstride, const double2* w, long long N, int nv, int self,
+                           int nrhs, double2* part, double2* h, int nblk, cudaStream_t s);
+cudaError_t launch_maxpy_ds(const double2* Vbase, long long vstride, const double2* h, int hstride, double2* w,
+                            long long N, int nv, int nrhs, double sign, cudaStream_t s);
+cudaError_t launch_norm2_ds(const double2* w, long long N, int nrhs, double* part, double* out, int nblk,
+                            cudaStream_t s);
 // FGMRES Arnoldi bookkeeping on the device (one thread per rhs), see vec.cu
 struct ArnoldiArgs {
   const double2* h;   // [rhs][j + 2]: Gram-Schmidt coefficients, then ||w||^2 before the pass

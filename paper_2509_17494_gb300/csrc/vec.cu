@@ -7,6 +7,7 @@
 // K7: A_q of Section 3.3 applied cell by cell: per coarse cell c the
 // coefficients (d0, d1, d2) for same-node, edge-neighbour and diagonal pairs,
 // plus -i k hc times the Q1 edge mass on absorbing sides.
+#include "ds_math.cuh"
 #include "kernels.h"
 #include "launch.cuh"
 #include "ptx.cuh"
@@ -424,6 +425,231 @@ cudaError_t launch_norm2(const double2* w, long long N, int nrhs, double* part, 
                          cudaStream_t s) {
   dim3 grid(nblk, nrhs);
   k_norm_part<<<grid, 256, 0, s>>>(w, N, part, nblk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_norm_final<<<(nrhs + 3) / 4, 128, 0, s>>>(part, nblk, nrhs, out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ K9 in double-single arithmetic
+// The same three Gram-Schmidt kernels for the mixed form.  This GPU issues
+// FP64 FMAs at 1/64 of the FP32 rate, which holds the FP64 kernels above to
+// about 2.5 TB/s of vector traffic (four FMAs per complex entry and basis
+// vector).  Here every FP64 operand is split exactly into two floats
+// (ds_from_double: its leading 24 and next 24 significant bits); a product
+// x y is formed as p = fl(x_h y_h) with its exact rounding error
+// fma(x_h, y_h, -p) plus the cross terms x_h y_l + x_l y_h (Dekker; the dropped
+// x_l y_l is below 2^-46 relative); a thread's running sum is a float pair
+// (s, c) in which s takes the products and c the exact rounding errors of the
+// additions (Knuth's two-sum) and of the products.  Each thread sums a few
+// dozen products; its pair goes to FP64 for the fixed-order block and grid
+// reductions of the FP64 kernels.  Relative error about 2^-44 of the sum of
+// the terms' magnitudes.
+struct dsacc {
+  float s, c;
+};
+__device__ __forceinline__ void acc_prod(dsacc& a, ds x, ds y) {
+  const float p = __fmul_rn(x.h, y.h);
+  float e = __fmaf_rn(x.h, y.h, -p);
+  e = __fmaf_rn(x.h, y.l, e);
+  e = __fmaf_rn(x.l, y.h, e);
+  const float t = __fadd_rn(a.s, p);
+  const float z = __fsub_rn(t, a.s);
+  const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  a.c = __fadd_rn(a.c, __fadd_rn(err, e));
+  a.s = t;
+}
+// s + c in FP64 (exact while c is within 2^-29 of s's exponent range, as here)
+__device__ __forceinline__ double acc_value(const dsacc& a) { return f2d_bits(a.s) + f2d_bits(a.c); }
+__device__ __forceinline__ ds dneg(ds x) { return ds(-x.h, -x.l); }
+// a += (s2, c2): two-sum of the leading parts, the error and c2 into the second
+__device__ __forceinline__ void acc_add(dsacc& a, float s2, float c2) {
+  const float t = __fadd_rn(a.s, s2);
+  const float z = __fsub_rn(t, a.s);
+  const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, z)), __fsub_rn(s2, z));
+  a.c = __fadd_rn(a.c, __fadd_rn(c2, err));
+  a.s = t;
+}
+// butterfly sum over the warp (every lane ends with the same pair: each step
+// adds the same two pairs, and two-sum's error term is exact in either order)
+__device__ __forceinline__ void acc_warp_sum(dsacc& a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, a.s, o), c2 = __shfl_xor_sync(0xffffffffu, a.c, o);
+    acc_add(a, s2, c2);
+  }
+}
+
+template <int TILE, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_mdot_part_ds(const double2* __restrict__ Vb, long long vstride,
+                                                            const double2* __restrict__ w, long long N, int nv,
+                                                            int self, double2* __restrict__ part, int nblk) {
+  const int nvt = nv + self;
+  const int rhs = blockIdx.z, i0 = blockIdx.y * TILE;
+  const int ni = min(TILE, nvt - i0);
+  const long long chunk = (N + nblk - 1) / nblk;
+  const long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
+  const double2* wr = w + (size_t)rhs * N;
+  dsacc ar[TILE], ai[TILE];
+#pragma unroll
+  for (int t = 0; t < TILE; ++t) {
+    ar[t] = dsacc{0.f, 0.f};
+    ai[t] = dsacc{0.f, 0.f};
+  }
+  for (long long n = lo + threadIdx.x; n < hi; n += blockDim.x) {
+    const double2 wv = wr[n];
+    const ds wx = ds_from_double(wv.x), wy = ds_from_double(wv.y);
+#pragma unroll
+    for (int t = 0; t < TILE; ++t) {
+      if (t < ni) {
+        ds vx = wx, vy = wy;
+        if (i0 + t < nv) {
+          const double2 v = Vb[(size_t)(i0 + t) * vstride + (size_t)rhs * N + n];
+          vx = ds_from_double(v.x);
+          vy = ds_from_double(v.y);
+        }
+        // conj(v) w = (vx wx + vy wy) + i (vx wy - vy wx)
+        acc_prod(ar[t], vx, wx);
+        acc_prod(ar[t], vy, wy);
+        acc_prod(ai[t], vx, wy);
+        acc_prod(ai[t], dneg(vy), wx);
+      }
+    }
+  }
+  // warp sums of the pairs, then the 8 warps' values in FP64 in a fixed order
+  __shared__ double sh[2][TILE][8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int t = 0; t < TILE; ++t) {
+    acc_warp_sum(ar[t]);
+    acc_warp_sum(ai[t]);
+    if (lane == 0) {
+      sh[0][t][warp] = acc_value(ar[t]);
+      sh[1][t][warp] = acc_value(ai[t]);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < (unsigned)ni) {
+    double2 o;
+    o.x = sh[0][threadIdx.x][0];
+    o.y = sh[1][threadIdx.x][0];
+    for (int q = 1; q < 8; ++q) {
+      o.x += sh[0][threadIdx.x][q];
+      o.y += sh[1][threadIdx.x][q];
+    }
+    part[((size_t)rhs * nvt + i0 + threadIdx.x) * nblk + blockIdx.x] = o;
+  }
+}
+
+cudaError_t launch_mdot_ds(const double2* Vbase, long long vstride, const double2* w, long long N, int nv, int self,
+                           int nrhs, double2* part, double2* h, int nblk, cudaStream_t s) {
+  const int nvt = nv + (self ? 1 : 0);
+  dim3 grid(nblk, (nvt + kDotTile - 1) / kDotTile, nrhs);
+  // four CTAs per SM (at most 64 registers a thread): the loads of more warps in
+  // flight (measured: 0.72 of the time with the compiler's 93 registers)
+  k_mdot_part_ds<kDotTile, 4><<<grid, 256, 0, s>>>(Vbase, vstride, w, N, nv, self ? 1 : 0, part, nblk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int total = nvt * nrhs;
+  k_mdot_final<<<(total + 3) / 4, 128, 0, s>>>(part, nblk, total, h);
+  return cudaGetLastError();
+}
+
+// w[rhs] += sign * sum_i h[rhs * hstride + i] V_i[rhs]; the coefficients are
+// split once per block into shared memory ([nv][re h, re l, im h, im l])
+__global__ void __launch_bounds__(256) k_maxpy_ds(const double2* __restrict__ Vb, long long vstride,
+                                                  const double2* __restrict__ h, int hstride, double2* __restrict__ w,
+                                                  long long N, int nv, double sign) {
+  extern __shared__ float hsm[];
+  const int rhs = blockIdx.y;
+  const double2* hr = h + (size_t)rhs * hstride;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const double2 c = hr[i];
+    const ds cr = ds_from_double(c.x), ci = ds_from_double(c.y);
+    hsm[4 * i] = cr.h;
+    hsm[4 * i + 1] = cr.l;
+    hsm[4 * i + 2] = ci.h;
+    hsm[4 * i + 3] = ci.l;
+  }
+  __syncthreads();
+  double2* wr = w + (size_t)rhs * N;
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    // c v = (cr vx - ci vy) + i (cr vy + ci vx); two independent sums per
+    // component (even and odd i) shorten the dependent chains
+    dsacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
+    int i = 0;
+    for (; i + 1 < nv; i += 2) {
+      const double2 v0 = Vb[(size_t)i * vstride + (size_t)rhs * N + n];
+      const double2 v1 = Vb[(size_t)(i + 1) * vstride + (size_t)rhs * N + n];
+      const ds c0r(hsm[4 * i], hsm[4 * i + 1]), c0i(hsm[4 * i + 2], hsm[4 * i + 3]);
+      const ds c1r(hsm[4 * i + 4], hsm[4 * i + 5]), c1i(hsm[4 * i + 6], hsm[4 * i + 7]);
+      const ds v0x = ds_from_double(v0.x), v0y = ds_from_double(v0.y);
+      const ds v1x = ds_from_double(v1.x), v1y = ds_from_double(v1.y);
+      acc_prod(sr, c0r, v0x);
+      acc_prod(tr, c1r, v1x);
+      acc_prod(si, c0r, v0y);
+      acc_prod(ti, c1r, v1y);
+      acc_prod(sr, dneg(c0i), v0y);
+      acc_prod(tr, dneg(c1i), v1y);
+      acc_prod(si, c0i, v0x);
+      acc_prod(ti, c1i, v1x);
+    }
+    if (i < nv) {
+      const double2 v = Vb[(size_t)i * vstride + (size_t)rhs * N + n];
+      const ds cr(hsm[4 * i], hsm[4 * i + 1]), ci(hsm[4 * i + 2], hsm[4 * i + 3]);
+      const ds vx = ds_from_double(v.x), vy = ds_from_double(v.y);
+      acc_prod(sr, cr, vx);
+      acc_prod(sr, dneg(ci), vy);
+      acc_prod(si, cr, vy);
+      acc_prod(si, ci, vx);
+    }
+    acc_add(sr, tr.s, tr.c);
+    acc_add(si, ti.s, ti.c);
+    double2 o = wr[n];
+    o.x = fmadd(sign, acc_value(sr), o.x);
+    o.y = fmadd(sign, acc_value(si), o.y);
+    wr[n] = o;
+  }
+}
+
+cudaError_t launch_maxpy_ds(const double2* Vbase, long long vstride, const double2* h, int hstride, double2* w,
+                            long long N, int nv, int nrhs, double sign, cudaStream_t s) {
+  long long b = (N + 255) / 256;
+  dim3 grid((unsigned)(b > 1216 ? 1216 : b), nrhs);
+  const size_t smem = sizeof(float) * 4 * (size_t)(nv > 0 ? nv : 1);
+  if (smem > 48 * 1024) return cudaErrorInvalidValue;
+  k_maxpy_ds<<<grid, 256, smem, s>>>(Vbase, vstride, h, hstride, w, N, nv, sign);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_norm_part_ds(const double2* __restrict__ w, long long N, double* part,
+                                                      int nblk) {
+  const int rhs = blockIdx.y;
+  const long long chunk = (N + nblk - 1) / nblk;
+  const long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
+  const double2* wr = w + (size_t)rhs * N;
+  dsacc a{0.f, 0.f};
+  for (long long n = lo + threadIdx.x; n < hi; n += blockDim.x) {
+    const double2 v = wr[n];
+    const ds vx = ds_from_double(v.x), vy = ds_from_double(v.y);
+    acc_prod(a, vx, vx);
+    acc_prod(a, vy, vy);
+  }
+  __shared__ double sh[8];
+  acc_warp_sum(a);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc_value(a);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = sh[0];
+    for (int q = 1; q < 8; ++q) v += sh[q];
+    part[(size_t)rhs * nblk + blockIdx.x] = v;
+  }
+}
+
+cudaError_t launch_norm2_ds(const double2* w, long long N, int nrhs, double* part, double* out, int nblk,
+                            cudaStream_t s) {
+  dim3 grid(nblk, nrhs);
+  k_norm_part_ds<<<grid, 256, 0, s>>>(w, N, part, nblk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_norm_final<<<(nrhs + 3) / 4, 128, 0, s>>>(part, nblk, nrhs, out);

@@ -439,6 +439,27 @@ def test_mixed_solve_double_single_products(th, c):
     assert relerr(host(X1), host(X0)) < 1e-8
 
 
+@pytest.mark.parametrize("c", [CASES[0], CASES[4], CASES[6]])
+def test_mixed_solve_double_single_krylov(th, c):
+    """The mixed forms' Gram-Schmidt dots, norms and updates in double-single
+    arithmetic (TH_K_KRYLOV 1, default; about 2^-44 relative) against FP64
+    (variant 0): the same iterations and residuals, solutions within 1e-9,
+    over a restart (restart 4)."""
+    S, P = build(th, c, nrhs=3, prec="bf16", extra_prec=("fp64",), restart=4, maxit=200)
+    F = dev(synth.random_complex((3, P.N), 96))
+    assert S.get_variant("krylov", "fp32") == 1
+    X1, i1 = S.solve(F)
+    S.set_variant("krylov", "fp32", 0)
+    X0, i0 = S.solve(F)
+    assert i1["relres_max"] <= 1e-8 and i0["relres_max"] <= 1e-8
+    assert i1["iters"] == i0["iters"]
+    assert relerr(host(X1), host(X0)) < 1e-9
+    x = host(X1)
+    f = host(F)
+    for r in range(3):
+        assert np.linalg.norm(f[r] - P.A @ x[r]) / np.linalg.norm(f[r]) <= 1.01e-8
+
+
 # ------------------------------------------------------------ full-size, sampled
 def test_full_size_apply_and_cycle(th):
     """40-wavelength 401^2 workload: the apply at full size and one cycle compared on sampled nodes."""
