@@ -37,6 +37,54 @@ __device__ __forceinline__ ds& operator+=(ds& a, ds b) { return a = a + b; }
 __device__ __forceinline__ ds fmadd(ds a, ds b, ds c) { return c + a * b; }
 __device__ __forceinline__ ds& operator-=(ds& a, ds b) { return a = a - b; }
 
+// Unnormalised double-single accumulator: s takes the rounded products and
+// sums, c the exact rounding errors (Knuth's two-sum for the additions,
+// Dekker's product through FMA for the multiplications).  A term costs 12
+// FP32 operations against 18 for a normalised ds multiply-add; the pair is
+// normalised once, at the end (ds_of).
+struct dsacc {
+  float s, c;
+};
+__device__ __forceinline__ void acc_prod(dsacc& a, ds x, ds y) {
+  const float p = __fmul_rn(x.h, y.h);
+  float e = __fmaf_rn(x.h, y.h, -p);
+  e = __fmaf_rn(x.h, y.l, e);
+  e = __fmaf_rn(x.l, y.h, e);
+  const float t = __fadd_rn(a.s, p);
+  const float z = __fsub_rn(t, a.s);
+  const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  a.c = __fadd_rn(a.c, __fadd_rn(err, e));
+  a.s = t;
+}
+// the accumulated value as a normalised ds number
+__device__ __forceinline__ ds ds_of(const dsacc& a) { return ds_two_sum(a.s, a.c); }
+
+// Multiply-accumulate chains of the apply kernels: plain T for FP32 / FP64
+// (the expressions of those kernels unchanged), the unnormalised pair for ds.
+template <typename T>
+struct MacAcc {
+  using type = T;
+};
+template <>
+struct MacAcc<ds> {
+  using type = dsacc;
+};
+template <typename T>
+__device__ __forceinline__ void mac(T& acc, T a, T b) {  // acc += a b
+  acc += a * b;
+}
+__device__ __forceinline__ void mac(dsacc& acc, ds a, ds b) { acc_prod(acc, a, b); }
+template <typename T>
+__device__ __forceinline__ void mac_fma(T& acc, T a, T b) {  // acc = fma(a, b, acc)
+  acc = fmadd(a, b, acc);
+}
+__device__ __forceinline__ void mac_fma(dsacc& acc, ds a, ds b) { acc_prod(acc, a, b); }
+template <typename T>
+__device__ __forceinline__ T mac_val(const T& a) {
+  return a;
+}
+__device__ __forceinline__ ds mac_val(const dsacc& a) { return ds_of(a); }
+
 // Exact split of a double into h (its leading 24 significant bits, truncated)
 // and l (the remaining 29 bits rounded to 24) with integer operations only;
 // magnitudes below 2^-126 (and l below the float range) flush to zero.

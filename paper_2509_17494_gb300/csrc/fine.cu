@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
   // into an even part on s_b = u_b + u_{P-b} and an odd part on
   // d_b = u_b - u_{P-b}: (H+1)^2 + H^2 products instead of (P+1)^2 (H = P/2).
   constexpr int H = P / 2;
+  using Acc = typename MacAcc<T>::type;  // multiply-accumulate chains (ds: unnormalised pairs)
   for (int it = tid; it < CELLS * NP; it += nth) {
     const int e = it / NP, ay = it - e * NP;
     const int ecy = e / E, ecx = e - ecy * E;
@@ -178,24 +179,26 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
     C* o2 = s2 + (e * NP + ay) * NP;
 #pragma unroll
     for (int ax = 0; ax <= H; ++ax) {
-      T pmr = 0, pmi = 0, pkr = 0, pki = 0, qmr = 0, qmi = 0, qkr = 0, qki = 0;
+      Acc pmr_{}, pmi_{}, pkr_{}, pki_{}, qmr_{}, qmi_{}, qkr_{}, qki_{};
 #pragma unroll
       for (int b = 0; b <= H; ++b) {
         const T me = a.ME[ax * (H + 1) + b], ke = a.KE[ax * (H + 1) + b];
-        pmr += me * sv[b].x;
-        pmi += me * sv[b].y;
-        pkr += ke * sv[b].x;
-        pki += ke * sv[b].y;
+        mac(pmr_, me, sv[b].x);
+        mac(pmi_, me, sv[b].y);
+        mac(pkr_, ke, sv[b].x);
+        mac(pki_, ke, sv[b].y);
       }
+      const T pmr = mac_val(pmr_), pmi = mac_val(pmi_), pkr = mac_val(pkr_), pki = mac_val(pki_);
       if (ax < H) {
 #pragma unroll
         for (int b = 0; b < H; ++b) {
           const T mo = a.MO[ax * H + b], ko = a.KO[ax * H + b];
-          qmr += mo * dv[b].x;
-          qmi += mo * dv[b].y;
-          qkr += ko * dv[b].x;
-          qki += ko * dv[b].y;
+          mac(qmr_, mo, dv[b].x);
+          mac(qmi_, mo, dv[b].y);
+          mac(qkr_, ko, dv[b].x);
+          mac(qki_, ko, dv[b].y);
         }
+        const T qmr = mac_val(qmr_), qmi = mac_val(qmi_), qkr = mac_val(qkr_), qki = mac_val(qki_);
         C t;
         t.x = pmr + qmr; t.y = pmi + qmi; o1[ax] = t;
         t.x = pmr - qmr; t.y = pmi - qmi; o1[P - ax] = t;
@@ -245,24 +248,26 @@ __global__ void __launch_bounds__(TC >= 8 ? 256 : 128) k_fine_apply(const FineAr
     C yv[NP];
 #pragma unroll
     for (int ay = 0; ay <= H; ++ay) {
-      T pr = 0, pi = 0, qr = 0, qi = 0;
+      Acc pr_{}, pi_{}, qr_{}, qi_{};
 #pragma unroll
       for (int b = 0; b <= H; ++b) {
         const T me = a.ME[ay * (H + 1) + b], ke = a.KE[ay * (H + 1) + b];
-        pr = fmadd(me, zs_[b].x, pr);
-        pr = fmadd(ke, ts_[b].x, pr);
-        pi = fmadd(me, zs_[b].y, pi);
-        pi = fmadd(ke, ts_[b].y, pi);
+        mac_fma(pr_, me, zs_[b].x);
+        mac_fma(pr_, ke, ts_[b].x);
+        mac_fma(pi_, me, zs_[b].y);
+        mac_fma(pi_, ke, ts_[b].y);
       }
+      const T pr = mac_val(pr_), pi = mac_val(pi_);
       if (ay < H) {
 #pragma unroll
         for (int b = 0; b < H; ++b) {
           const T mo = a.MO[ay * H + b], ko = a.KO[ay * H + b];
-          qr = fmadd(mo, zd_[b].x, qr);
-          qr = fmadd(ko, td_[b].x, qr);
-          qi = fmadd(mo, zd_[b].y, qi);
-          qi = fmadd(ko, td_[b].y, qi);
+          mac_fma(qr_, mo, zd_[b].x);
+          mac_fma(qr_, ko, td_[b].x);
+          mac_fma(qi_, mo, zd_[b].y);
+          mac_fma(qi_, ko, td_[b].y);
         }
+        const T qr = mac_val(qr_), qi = mac_val(qi_);
         yv[ay].x = pr + qr;
         yv[ay].y = pi + qi;
         yv[P - ay].x = pr - qr;

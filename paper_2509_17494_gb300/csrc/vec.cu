@@ -445,20 +445,6 @@ cudaError_t launch_norm2(const double2* w, long long N, int nrhs, double* part, 
 // dozen products; its pair goes to FP64 for the fixed-order block and grid
 // reductions of the FP64 kernels.  Relative error about 2^-44 of the sum of
 // the terms' magnitudes.
-struct dsacc {
-  float s, c;
-};
-__device__ __forceinline__ void acc_prod(dsacc& a, ds x, ds y) {
-  const float p = __fmul_rn(x.h, y.h);
-  float e = __fmaf_rn(x.h, y.h, -p);
-  e = __fmaf_rn(x.h, y.l, e);
-  e = __fmaf_rn(x.l, y.h, e);
-  const float t = __fadd_rn(a.s, p);
-  const float z = __fsub_rn(t, a.s);
-  const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, z)), __fsub_rn(p, z));
-  a.c = __fadd_rn(a.c, __fadd_rn(err, e));
-  a.s = t;
-}
 // s + c in FP64 (exact while c is within 2^-29 of s's exponent range, as here)
 __device__ __forceinline__ double acc_value(const dsacc& a) { return f2d_bits(a.s) + f2d_bits(a.c); }
 __device__ __forceinline__ ds dneg(ds x) { return ds(-x.h, -x.l); }
