@@ -3,9 +3,10 @@
 // V_i = W_i R_i r for every right-hand side at once).
 //
 // Per subdomain the product is a complex GEMM V = W X^T, W: NR x NC rows
-// (NR <= 128), X: NB x NC gathered residuals (NB = 32 or 16 right-hand sides per
-// tile; 16 when the doubled X buffer of 32 would not fit shared memory, e.g. the
-// 729-column rows of the 3-D Q2 subdomains).  In real
+// (NR <= 128), X: NB x NC gathered residuals (NB = 64, 32 or 16 right-hand sides
+// per tile, the widest whose doubled X buffer fits shared memory: 64 for the
+// 289-column rows of the 2-D Q4 subdomains, so that every row crosses HBM once
+// for 64 sources; 16 for the 729-column rows of the 3-D Q2 subdomains).  In real
 // arithmetic, with A = W (M = 128 rows, K-major) and B = X (N = NB, K-major):
 //   D_re = W_re X_re^T - W_im X_im^T,   D_im = W_re X_im^T + W_im X_re^T,
 // four MMAs per K-step of 16 (the minus sign through the A-negate bit), with
@@ -22,7 +23,8 @@
 //
 // Roles in a persistent CTA (one per SM): warp 0 lane 0 issues the bulk copies
 // and the MMAs; warps 4-7 move the accumulators from tensor memory to global
-// memory; all other warps gather X.  W chunks go through a ring of 4 slots,
+// memory; all other warps gather X.  W chunks go through a ring of 3 (NB = 64)
+// or 4 slots,
 // X and the accumulators are double-buffered; everything is ordered by
 // mbarriers.  Every wait has an iteration limit; when one gives up the CTA
 // raises `failed`, stops issuing work, drains what it issued (bounded) and
@@ -39,8 +41,9 @@ namespace th {
 namespace {
 
 constexpr int kKC = 8;       // k/8 blocks per W chunk (64 columns)
-constexpr int kDepth = 4;    // W chunk slots
-constexpr int kSlotBytes = 2 * 16 * kKC * 128;  // re + im, 128 rows, 64 columns
+constexpr int kMaxDepth = 4;  // W chunk slots at most (barrier arrays)
+// one W chunk slot: re + im parts of M8 row groups x 64 columns
+__host__ __device__ inline size_t w_slot_bytes(int M8) { return (size_t)2 * M8 * kKC * 128; }
 constexpr int kThreads = 512;
 
 __device__ __forceinline__ unsigned su32(const void* p) { return ptx::smem_addr(p); }
@@ -59,12 +62,13 @@ size_t dd_umma_bytes_per_sub(int NR, int NC) {
   return (size_t)K8 * 2 * M8 * 128;
 }
 
-template <int kNB, bool D3>
+template <int kNB, int kDepth, bool D3>
 __global__ void __launch_bounds__(kThreads, 1) k_dd_umma(const DDUmmaArgs a) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   const int M8 = a.M8, K8 = a.K8;
   const int NKC = (K8 + kKC - 1) / kKC;
   const size_t xbuf_bytes = (size_t)2 * (kNB / 8) * K8 * 128;  // re + im
+  const size_t kSlotBytes = w_slot_bytes(M8);                  // a multiple of 1024 bytes
   unsigned char* wslot = smraw;                                 // [kDepth][kSlotBytes]
   unsigned char* xbuf = smraw + (size_t)kDepth * kSlotBytes;    // [2][xbuf_bytes]
   uint64_t* bars = reinterpret_cast<uint64_t*>(xbuf + 2 * xbuf_bytes);
@@ -246,31 +250,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_dd_umma(const DDUmmaArgs a) {
   }
 }
 
-template <int kNB>
+template <int kNB, int kDepth>
 static size_t dd_umma_smem(const DDUmmaArgs& a) {
   const size_t xbuf_bytes = (size_t)2 * (kNB / 8) * a.K8 * 128;
-  return (size_t)kDepth * kSlotBytes + 2 * xbuf_bytes + 17 * sizeof(uint64_t);
+  return (size_t)kDepth * w_slot_bytes(a.M8) + 2 * xbuf_bytes + 17 * sizeof(uint64_t);
 }
 
-template <int kNB, bool D3>
+template <int kNB, int kDepth, bool D3>
 static cudaError_t launch_dd_umma_k(const DDUmmaArgs& a, int sms, cudaStream_t s) {
-  const size_t smem = dd_umma_smem<kNB>(a);
-  cudaError_t e = cudaFuncSetAttribute(k_dd_umma<kNB, D3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = dd_umma_smem<kNB, kDepth>(a);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_dd_umma<kNB, kDepth, D3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(a.nsub < sms ? a.nsub : sms), (unsigned)((a.nrhs + kNB - 1) / kNB));
-  k_dd_umma<kNB, D3><<<grid, kThreads, smem, s>>>(a);
+  k_dd_umma<kNB, kDepth, D3><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
-template <int kNB>
+template <int kNB, int kDepth>
 static cudaError_t launch_dd_umma_nb(const DDUmmaArgs& a, int sms, cudaStream_t s) {
-  return a.dim3 ? launch_dd_umma_k<kNB, true>(a, sms, s) : launch_dd_umma_k<kNB, false>(a, sms, s);
+  return a.dim3 ? launch_dd_umma_k<kNB, kDepth, true>(a, sms, s) : launch_dd_umma_k<kNB, kDepth, false>(a, sms, s);
 }
 
 cudaError_t launch_dd_umma(const DDUmmaArgs& a, int sms, cudaStream_t s) {
   if (a.NR > 128 || (a.K8 & 1) || a.M8 * 8 > 128) return cudaErrorInvalidValue;
-  // 32 right-hand sides per tile when they fit, else 16 (MMA N >= 16 with M = 128)
-  if (a.nrhs > 16 && dd_umma_smem<32>(a) <= 225 * 1024) return launch_dd_umma_nb<32>(a, sms, s);
-  if (dd_umma_smem<16>(a) <= 225 * 1024) return launch_dd_umma_nb<16>(a, sms, s);
+  // 64 right-hand sides per tile when they fit (the rows then cross HBM once for
+  // all 64; a ring of three W slots), else 32 or 16 (MMA N >= 16 with M = 128)
+  if (a.nrhs > 32 && dd_umma_smem<64, 3>(a) <= 225 * 1024) return launch_dd_umma_nb<64, 3>(a, sms, s);
+  if (a.nrhs > 16 && dd_umma_smem<32, 4>(a) <= 225 * 1024) return launch_dd_umma_nb<32, 4>(a, sms, s);
+  if (dd_umma_smem<16, 4>(a) <= 225 * 1024) return launch_dd_umma_nb<16, 4>(a, sms, s);
   return cudaErrorInvalidValue;
 }
 
