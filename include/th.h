@@ -393,7 +393,10 @@ th_status th_peak_fma(int prec, int iters, double* flops_per_s, void* stream);
 
 /* Kernel variants chosen by the set-up autotuner (which times each candidate
  * on the context's own problem with CUDA events):
- *   TH_K_FINE: 0 = large cell tile, 1 = small cell tile;
+ *   TH_K_FINE: 0 = large cell tile, 1 = small cell tile (the set-up times both
+ *              for one right-hand side and, with nrhs_max >= 8, for nrhs_max, per
+ *              precision; setting a variant sets it for every right-hand-side count,
+ *              and prec FP32 also sets the double-single apply's);
  *   TH_K_DD:   0 = per-subdomain CTAs with direct loads,
  *              1 = persistent CTAs streaming the rows through TMA bulk copies,
  *              2 = the same with a dedicated producer warp and per-slot

@@ -57,7 +57,9 @@ struct th_ctx {
   int rmax = 0;
   int wchunks[4] = {0, 0, 0, 0};
   int ddG = 4;  // column groups per subdomain in K3
-  int tc64 = 0, tc32 = 0;  // fine-apply tile variant per precision (0 large, 1 small), autotuned
+  int tc64 = 0, tc32 = 0;  // fine-apply tile variant per precision (0 large, 1 small), autotuned at 1 rhs
+  int tcds = 0;            // the same for the double-single apply
+  int tc64m = 0, tc32m = 0, tcdsm = 0;  // ... and at nrhs_max (>= 8) right-hand sides
   int dds64 = 0, dds32 = 0;  // DD kernel per precision: 0 k_dd_apply, 1 k_dd_stream (autotuned)
   int dd_tc = 1;             // batched BF16 products on tensor cores (k_dd_umma) when available
   int cs_variant = 1;        // one-rhs coarse chunk sweep: 0 two-phase, 1 one barrier per step (autotuned)
@@ -428,8 +430,17 @@ T cvt(double v) {
   else return (T)v;
 }
 
+// the autotuned tile variant of the fine apply for precision T and nrhs right-hand sides
 template <typename T>
-th::FineArgs<T> fine_args(const th_ctx& x, int op) {
+int fine_tile(const th_ctx& x, int nrhs) {
+  const bool many = nrhs >= 8;
+  if constexpr (std::is_same<T, float>::value) return many ? x.tc32m : x.tc32;
+  else if constexpr (std::is_same<T, th::ds>::value) return many ? x.tcdsm : x.tcds;
+  else return many ? x.tc64m : x.tc64;
+}
+
+template <typename T>
+th::FineArgs<T> fine_args(const th_ctx& x, int op, int nrhs) {
   th::FineArgs<T> a{};
   const th::Geometry& g = x.g;
   a.N = g.N;
@@ -441,7 +452,7 @@ th::FineArgs<T> fine_args(const th_ctx& x, int op) {
   a.h = cvt<T>(g.h);
   a.h2 = cvt<T>(g.h * g.h);
   a.alpha = cvt<T>(op == TH_OP_AS ? x.prm.alpha_s : 0.0);
-  a.tc = std::is_same<T, float>::value ? x.tc32 : x.tc64;
+  a.tc = fine_tile<T>(x, nrhs);
   const int np = g.p + 1;
   for (int i = 0; i < np * np; ++i) {
     a.M[i] = cvt<T>(x.ref.M[i]);
@@ -519,7 +530,7 @@ template <typename T>
 th_status fine_apply(th_ctx& x, int op, const typename th::Cx<T>::t* u, const typename th::Cx<T>::t* f,
                      typename th::Cx<T>::t* y, int nrhs, cudaStream_t s) {
   if (x.g.dim == 3) return fine_apply3<T>(x, op, u, f, y, nrhs, s);
-  th::FineArgs<T> a = fine_args<T>(x, op);
+  th::FineArgs<T> a = fine_args<T>(x, op, nrhs);
   a.u = u;
   a.f = f;
   a.y = y;
@@ -537,7 +548,7 @@ th_status outer_residual(th_ctx& x, const double2* u, const double2* f, float2* 
     return fine_apply3<th::ds>(x, TH_OP_A, reinterpret_cast<const th::cds*>(u), reinterpret_cast<const th::cds*>(f),
                                reinterpret_cast<th::cds*>(r32), nrhs, s);
   if (x.g.dim == 2 && x.resid_ds && x.kcds) {
-    th::FineArgs<th::ds> a = fine_args<th::ds>(x, TH_OP_A);
+    th::FineArgs<th::ds> a = fine_args<th::ds>(x, TH_OP_A, nrhs);
     a.u = reinterpret_cast<const th::cds*>(u);
     a.f = reinterpret_cast<const th::cds*>(f);
     a.y = reinterpret_cast<th::cds*>(r32);  // FP32 output (see NodeIO<ds>)
@@ -560,7 +571,7 @@ th_status outer_residual(th_ctx& x, const double2* u, const double2* f, float2* 
 // tolerance, and the final residual is recomputed in FP64.
 th_status az_apply(th_ctx& x, const double2* z, double2* w, int nrhs, cudaStream_t s) {
   if (x.active != TH_PREC_FP64 && x.az_ds && x.kcds && x.g.dim == 2) {
-    th::FineArgs<th::ds> a = fine_args<th::ds>(x, TH_OP_A);
+    th::FineArgs<th::ds> a = fine_args<th::ds>(x, TH_OP_A, nrhs);
     a.u = reinterpret_cast<const th::cds*>(z);
     a.f = nullptr;
     a.y = reinterpret_cast<th::cds*>(w);
@@ -972,7 +983,7 @@ th_status cycle_fused(th_ctx& x, int wkind, const typename th::Cx<T>::t* f, type
   // step between two launches
   th::PdlScope pdl(x.fuse == 2 && !x.prof_on && x.coarse_mode == 0);
   auto fused_apply = [&](int src, C* uout) -> th_status {
-    th::FineArgs<T> a = fine_args<T>(x, TH_OP_A);
+    th::FineArgs<T> a = fine_args<T>(x, TH_OP_A, nrhs);
     a.u = nullptr;
     a.f = f;
     a.y = B::r(x);
@@ -1128,36 +1139,45 @@ th_status norms(th_ctx& x, const double2* w, int nrhs, std::vector<double>& out,
 
 namespace {
 // Set-up autotuner: times the fine-apply tile variants on this problem with
-// CUDA events and keeps the faster one per precision.
+// CUDA events, for nrhs right-hand sides, and keeps the faster one (T = ds:
+// the double-single apply, FP64 input and FP32 output).
 template <typename T>
-th_status tune_fine(th_ctx& x, cudaStream_t s, int& choice) {
+th_status tune_fine(th_ctx& x, cudaStream_t s, int nrhs, int& choice) {
   using C = typename th::Cx<T>::t;
   C* u = nullptr;
   C* y = nullptr;
+  size_t ubytes = 0;
   if constexpr (std::is_same<T, double>::value) {
     u = x.r64;
     y = x.t64;
+    ubytes = sizeof(double2);
+  } else if constexpr (std::is_same<T, th::ds>::value) {
+    u = reinterpret_cast<C*>(x.r64);
+    y = reinterpret_cast<C*>(x.r32);
+    ubytes = sizeof(double2);
+    if (!x.kcds) return TH_OK;
   } else {
     u = x.f32;
     y = x.r32;
+    ubytes = sizeof(float2);
   }
   if (!u || !y) return TH_OK;
-  TH_CU(cudaMemsetAsync(u, 0, sizeof(C) * x.g.N, s));
+  TH_CU(cudaMemsetAsync(u, 0, ubytes * x.g.N * (size_t)nrhs, s));
   cudaEvent_t e0, e1;
   TH_CU(cudaEventCreate(&e0));
   TH_CU(cudaEventCreate(&e1));
   float best = 1e30f;
   int arg = 0;
   for (int v = 0; v < 2; ++v) {
-    choice = v;
-    th::FineArgs<T> a = fine_args<T>(x, TH_OP_A);
+    th::FineArgs<T> a = fine_args<T>(x, TH_OP_A, 1);
+    a.tc = v;
     a.u = u;
     a.y = y;
     a.f = nullptr;
     a.residual = 0;
-    for (int w = 0; w < 2; ++w) TH_CU(th::launch_fine_apply<T>(a, 1, s));
+    for (int w = 0; w < 2; ++w) TH_CU(th::launch_fine_apply<T>(a, nrhs, s));
     TH_CU(cudaEventRecord(e0, s));
-    for (int r = 0; r < 5; ++r) TH_CU(th::launch_fine_apply<T>(a, 1, s));
+    for (int r = 0; r < 5; ++r) TH_CU(th::launch_fine_apply<T>(a, nrhs, s));
     TH_CU(cudaEventRecord(e1, s));
     TH_CU(cudaEventSynchronize(e1));
     float ms = 0;
@@ -1752,8 +1772,20 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     TH_CU(cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, dev));
     TH_CU(cudaMemsetAsync(x->derr, 0, 64 * sizeof(int), s));
   }
-  if (!d3 && (st = tune_fine<double>(*x, s, x->tc64)) != TH_OK) return st;  // the 3-D apply has one variant
-  if (!d3 && x->mixed && (st = tune_fine<float>(*x, s, x->tc32)) != TH_OK) return st;
+  if (!d3) {  // the 3-D apply has one variant
+    const int nm = x->prm.nrhs_max;
+    if ((st = tune_fine<double>(*x, s, 1, x->tc64)) != TH_OK) return st;
+    x->tc64m = x->tc64;
+    if (nm >= 8 && (st = tune_fine<double>(*x, s, nm, x->tc64m)) != TH_OK) return st;
+    if (x->mixed) {
+      if ((st = tune_fine<float>(*x, s, 1, x->tc32)) != TH_OK) return st;
+      if ((st = tune_fine<th::ds>(*x, s, 1, x->tcds)) != TH_OK) return st;
+      x->tc32m = x->tc32;
+      x->tcdsm = x->tcds;
+      if (nm >= 8 && (st = tune_fine<float>(*x, s, nm, x->tc32m)) != TH_OK) return st;
+      if (nm >= 8 && (st = tune_fine<th::ds>(*x, s, nm, x->tcdsm)) != TH_OK) return st;
+    }
+  }
   if (x->W[TH_PREC_FP64] && (st = tune_dd<double>(*x, TH_PREC_FP64, s, x->dds64)) != TH_OK) return st;
   if (x->mixed) {
     const int wk = (x->active != TH_PREC_FP64) ? x->active : (x->W[TH_PREC_BF16] ? TH_PREC_BF16 : TH_PREC_FP32);
@@ -1788,8 +1820,13 @@ th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
   if (!x || variant < 0 || variant > vmax || (prec != TH_PREC_FP64 && prec != TH_PREC_FP32))
     return TH_ERR_ARG;
   const bool d = (prec == TH_PREC_FP64);
-  if (kernel == TH_K_FINE) {
-    (d ? x->tc64 : x->tc32) = variant;
+  if (kernel == TH_K_FINE) {  // every right-hand-side count; FP32 also sets the double-single apply's
+    if (d) {
+      x->tc64 = x->tc64m = variant;
+    } else {
+      x->tc32 = x->tc32m = variant;
+      x->tcds = x->tcdsm = variant;
+    }
   } else if (kernel == TH_K_DD) {
     (d ? x->dds64 : x->dds32) = variant;
   } else if (kernel == TH_K_DD_BATCH) {

@@ -221,22 +221,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_umma(const CoarseUmmaArg
         ptx::tmem_ld16(base + (unsigned)c0, re);
         ptx::tmem_ld16(base + (unsigned)(64 + c0), im);
         if (!live) continue;
+        const int nb = min(16, a.nrhs - (grp * 64 + c0));  // right-hand sides of this slice
+        if (MODE == 0) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = c0 + j, rhs = grp * 64 + n;
-          if (rhs >= a.nrhs) break;
-          const float vr = __uint_as_float(re[j]), vi = __uint_as_float(im[j]);
-          if (MODE == 0) {
+          for (int j = 0; j < 16; ++j) {
+            if (j >= nb) break;
+            const int n = c0 + j, rhs = grp * 64 + n;
+            const float vr = __uint_as_float(re[j]), vi = __uint_as_float(im[j]);
             a.x[(size_t)rhs * a.Nc + (size_t)a.sep[k] * a.mc + e] = make_float2(vr, vi);
             __nv_bfloat16* st = reinterpret_cast<__nv_bfloat16*>(
                 a.xst + (((size_t)grp * a.nsep + k) * a.nkc_m + (e >> 5)) * kBChunk);
             store_split(st, kBPart / 2, umma_off32(n, e & 31), vr, vi);
-          } else {
-            float2* p = a.x + (size_t)rhs * a.Nc + tl.row0 + row;
-            float2 v = *p;
-            v.x -= vr;
-            v.y -= vi;
-            *p = v;
+          }
+        } else {
+          // every load of the slice before the first store (they are independent)
+          float2* p0 = a.x + (size_t)(grp * 64 + c0) * a.Nc + tl.row0 + row;
+          float2 v[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (j < nb) v[j] = p0[(size_t)j * a.Nc];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (j < nb) {
+              v[j].x -= __uint_as_float(re[j]);
+              v[j].y -= __uint_as_float(im[j]);
+              p0[(size_t)j * a.Nc] = v[j];
+            }
           }
         }
       }
