@@ -323,8 +323,9 @@ def run_native(args):
             out.append(info)
         return min(i["ms_total"] for i in out), out[-1]
 
+    # the first solve of a context captures its per-step CUDA graphs: best of several
     tt_mixed, info_mixed = solve_time("bf16", 3)
-    tt_fp64, info_fp64 = solve_time("fp64", 1)
+    tt_fp64, info_fp64 = solve_time("fp64", 2)
 
     # end to end through the host-buffer entry point (pinned host memory)
     S.set_precision("bf16")
@@ -508,6 +509,7 @@ def batched_section(args, w, dev, world):
     NR, NC = 81, 289
     nsub = (w["n"] // w["l_dd"]) ** 2
     flops = 8.0 * NR * NC * nsub * nr
+    S.solve(F)  # captures the per-step CUDA graphs
     _, info = S.solve(F)
     hbm, src = peaks()
     out = {"workload": w["name"], "dofs": S.N, "setup_s": round(setup_s, 1),

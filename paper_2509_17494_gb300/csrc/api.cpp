@@ -2303,35 +2303,39 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
       }
       double2* Vj = x->Vk + (size_t)j * vstride;
       double2* Zj = x->Zk + (size_t)j * vstride;
-      if (x->use_graphs && !x->prof_on) {
-        st = graph_run(*x, 1, Vj, Zj, nrhs, s,
-                       [&](cudaStream_t gs) { return precondition(*x, Vj, Zj, nrhs, gs); });
-      } else {
-        st = precondition(*x, Vj, Zj, nrhs, s);
-      }
-      if (st != TH_OK) return st;
-      if ((st = az_apply(*x, Zj, x->w, nrhs, s)) != TH_OK) return st;
-      // one classical Gram-Schmidt pass (the coefficients and ||w||^2 before it), then
-      // ||w||^2 after it; a pass that cancels more than 99.99 % of ||w||^2 makes the
-      // host restart (loss of orthogonality ~ eps ||w||^2 / ||w - V h||^2), which
-      // with the two-grid preconditioner does not occur in practice
-      x->launches += 6;
-      {
-        Prof prof(*x, TH_K_KRYLOV, s);
-        if (kds) {
-          TH_CU(th::launch_mdot_ds(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, s));
-          TH_CU(th::launch_maxpy_ds(x->Vk, vstride, x->h1, j + 2, x->w, N, j + 1, nrhs, -1.0, s));
-          TH_CU(th::launch_norm2_ds(x->w, N, nrhs, x->npart, x->nrm, x->nblk, s));
-        } else {
-          TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, s));
-          TH_CU(th::launch_maxpy(x->Vk, vstride, x->h1, j + 2, x->w, N, j + 1, nrhs, -1.0, s));
-          TH_CU(th::launch_norm2(x->w, N, nrhs, x->npart, x->nrm, x->nblk, s));
+      // one Arnoldi step: z_j = B v_j, w = A z_j, one classical Gram-Schmidt pass
+      // (the coefficients and ||w||^2 before it), then ||w||^2 after it, the
+      // Hessenberg column and rotations, v_{j+1}, and the step's status copied to
+      // pinned host memory.  A pass that cancels more than 99.99 % of ||w||^2 makes
+      // the host restart (loss of orthogonality ~ eps ||w||^2 / ||w - V h||^2),
+      // which with the two-grid preconditioner does not occur in practice.
+      auto step = [&](cudaStream_t ss) -> th_status {
+        th_status e;
+        if ((e = precondition(*x, Vj, Zj, nrhs, ss)) != TH_OK) return e;
+        if ((e = az_apply(*x, Zj, x->w, nrhs, ss)) != TH_OK) return e;
+        x->launches += 6;
+        {
+          Prof prof(*x, TH_K_KRYLOV, ss);
+          if (kds) {
+            TH_CU(th::launch_mdot_ds(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, ss));
+            TH_CU(th::launch_maxpy_ds(x->Vk, vstride, x->h1, j + 2, x->w, N, j + 1, nrhs, -1.0, ss));
+            TH_CU(th::launch_norm2_ds(x->w, N, nrhs, x->npart, x->nrm, x->nblk, ss));
+          } else {
+            TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, ss));
+            TH_CU(th::launch_maxpy(x->Vk, vstride, x->h1, j + 2, x->w, N, j + 1, nrhs, -1.0, ss));
+            TH_CU(th::launch_norm2(x->w, N, nrhs, x->npart, x->nrm, x->nblk, ss));
+          }
+          TH_CU(th::launch_arnoldi(aa, j, ss));
+          TH_CU(th::launch_scale_rhs(x->w, x->Vk + (size_t)(j + 1) * vstride, x->scal, N, nrhs, ss));
         }
-        TH_CU(th::launch_arnoldi(aa, j, s));
-        TH_CU(th::launch_scale_rhs(x->w, x->Vk + (size_t)(j + 1) * vstride, x->scal, N, nrhs, s));
-      }
-      TH_CU(cudaMemcpyAsync(x->pin + (size_t)(j & 1) * nrhs * 5, x->statd, sizeof(double) * nrhs * 5,
-                            cudaMemcpyDeviceToHost, s));
+        TH_CU(cudaMemcpyAsync(x->pin + (size_t)(j & 1) * nrhs * 5, x->statd, sizeof(double) * nrhs * 5,
+                              cudaMemcpyDeviceToHost, ss));
+        return TH_OK;
+      };
+      // the whole step from one CUDA graph per (j, buffers): a launch instead of a
+      // dozen, and no launch gaps between its small Krylov kernels
+      st = (x->use_graphs && !x->prof_on) ? graph_run(*x, 3 + 2 * j, Vj, Zj, nrhs, s, step) : step(s);
+      if (st != TH_OK) return st;
       TH_CU(cudaEventRecord(evs[j & 1], s));
       if (j >= 1 && last_read < j - 1 && (st = read_status(j - 1)) != TH_OK) return st;
     }
