@@ -110,7 +110,49 @@ def parse():
                     help="add the shift study of the paper's Table 2 (gal coarsening, p = 6) on the GPU")
     ap.add_argument("--lfa", choices=["sweep", "none"], default="sweep",
                     help="Fourier-analysis rates against dofs per wavelength on the GPU (Figs. 3 and 4)")
+    ap.add_argument("--kernel-case", choices=["dd64", "coarse64", "krylov64"], default=None,
+                    help="only run one small-footprint kernel workload for a profiler (64 sources on the 401^2 "
+                         "workload: the smoother, the coarse solve, or 8 FGMRES steps) and print one JSON line")
     return ap.parse_args()
+
+
+def kernel_case(args):
+    """A profiler's workload: one operation of the batched path, 64 right-hand
+    sides on the 401^2 grid, a few GB on the device (FGMRES restart 8), inside
+    the NVTX range 'kernel_case' after two untimed repetitions."""
+    import numpy as np
+    import torch
+
+    import paper_2509_17494_gb300 as th
+    import synth
+
+    dev = "cuda:0"
+    w = synth.workload("square40_q4_n100")
+    nr = 64
+    S = th.TwoGridSolver(w["n"], w["p"], w["k"], w["eps"], alpha_s=w["alpha_s"], l_dd=w["l_dd"], prec="bf16",
+                         restart=8, maxit=8, tol=1e-8, nrhs_max=nr, device=dev)
+    F = torch.from_numpy(np.ascontiguousarray(synth.random_sources(w["n"], w["p"], 2, nr, 100))).to(dev)
+    U = torch.from_numpy(np.ascontiguousarray(synth.random_complex((nr, S.N), 5))).to(dev)
+    rc = torch.from_numpy(np.ascontiguousarray(synth.random_complex((nr, S.Nc), 6))).to(dev)
+
+    def once():
+        if args.kernel_case == "dd64":
+            S.smooth(F, U)
+        elif args.kernel_case == "coarse64":
+            S.coarse_solve(rc)
+        else:
+            S.solve(F, check=False)
+
+    for _ in range(2):
+        once()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("kernel_case")
+    once()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    S.device_status()
+    print(json.dumps({"kernel_case": args.kernel_case, "workload": w["name"], "nrhs": nr, "ok": True}), flush=True)
+    S.close()
 
 
 # ----------------------------------------------------------------------------
@@ -1211,7 +1253,12 @@ def main():
     args = parse()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.kernel_case:
+        from paper_2509_17494_gb300 import _build
+
+        _build.build()
+        kernel_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_native(args)
