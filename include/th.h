@@ -368,7 +368,8 @@ enum {
   TH_K_CYCLE = 11,      /* (variants only) launch structure of the cycle, see th_set_kernel_variant */
   TH_K_COARSE_MULTI = 12, /* (variants only) 2-D coarse sweep for 8 or more right-hand sides */
   TH_K_AZ = 13,         /* (variants only) the FGMRES product A z of the mixed forms */
-  TH_K_COARSE_REFINE = 14 /* (variants only) refinement steps of the mixed 2-D coarse solve */
+  TH_K_COARSE_REFINE = 14, /* (variants only) refinement steps of the mixed 2-D coarse solve */
+  TH_K_SEP_SYM = 15     /* (variants only) one-rhs FP32 separator product from Sinv's upper triangle */
 };
 
 /* Per-kernel timing for measurement: with enable = 1 every later kernel
@@ -445,6 +446,11 @@ th_status th_peak_fma(int prec, int iters, double* flops_per_s, void* stream);
  *              vectors (exact two-float splits, products with their exact
  *              rounding errors, compensated sums: about 2^-44 relative),
  *              0 FP64; the FP64 form always uses FP64; prec is ignored;
+ *   TH_K_SEP_SYM: the one-right-hand-side FP32 separator product of the 2-D
+ *              coarse solve: 1 (default) from the upper triangle of the
+ *              complex-symmetric reduced inverse only (64 x 64 blocks, each
+ *              serving S_IJ x_J and S_IJ^T x_I; half the bytes), 0 the full
+ *              GEMV; prec is ignored;
  *   TH_K_COARSE_REFINE: steps (0 to 3) of iterative refinement after the
  *              mixed form's 2-D coarse solve: z = r_c - A_q u_c in FP32, the
  *              same solve of z, u_c += its solution.  The set-up chooses the

@@ -378,13 +378,13 @@ class TwoGridSolver:
         _check(lib().th_set_precision(self._ctx, PREC[prec]), "th_set_precision")
 
     def set_variant(self, kernel, prec, variant):
-        """kernel: 'fine' | 'dd' | 'coarse' | 'dd_batch' | 'resid' | 'cycle' | 'coarse_multi' | 'az' | 'coarse_refine' | 'krylov';
+        """kernel: 'fine' | 'dd' | 'coarse' | 'dd_batch' | 'resid' | 'cycle' | 'coarse_multi' | 'az' | 'coarse_refine' | 'krylov' | 'sep_sym';
         prec: 'fp64' | 'fp32'; the variant numbers are listed in include/th.h."""
-        k = {"fine": 0, "dd": 1, "coarse": 6, "dd_batch": 9, "resid": 10, "cycle": 11, "coarse_multi": 12, "az": 13, "coarse_refine": 14, "krylov": 8}[kernel]
+        k = {"fine": 0, "dd": 1, "coarse": 6, "dd_batch": 9, "resid": 10, "cycle": 11, "coarse_multi": 12, "az": 13, "coarse_refine": 14, "krylov": 8, "sep_sym": 15}[kernel]
         _check(lib().th_set_kernel_variant(self._ctx, k, PREC[prec], int(variant)), "th_set_kernel_variant")
 
     def get_variant(self, kernel, prec):
-        k = {"fine": 0, "dd": 1, "coarse": 6, "dd_batch": 9, "resid": 10, "cycle": 11, "coarse_multi": 12, "az": 13, "coarse_refine": 14, "krylov": 8}[kernel]
+        k = {"fine": 0, "dd": 1, "coarse": 6, "dd_batch": 9, "resid": 10, "cycle": 11, "coarse_multi": 12, "az": 13, "coarse_refine": 14, "krylov": 8, "sep_sym": 15}[kernel]
         v = ctypes.c_int(0)
         _check(lib().th_get_kernel_variant(self._ctx, k, PREC[prec], ctypes.byref(v)), "th_get_kernel_variant")
         return v.value

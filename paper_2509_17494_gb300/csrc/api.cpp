@@ -67,6 +67,7 @@ struct th_ctx {
   int cs_multi = 1;          // 8 or more right-hand sides: 0 per-tile cluster sweep, 1 column groups (TH_K_COARSE_MULTI)
   int coarse_refine = 0;     // mixed 2-D coarse solve: refinement steps on its FP32 residual (TH_K_COARSE_REFINE)
   int krylov_ds = 1;         // mixed forms' FGMRES dots, norms and updates: 1 double-single arithmetic, 0 FP64 (TH_K_KRYLOV)
+  int sep_sym = 1;           // one-rhs FP32 separator product from Sinv's upper triangle (TH_K_SEP_SYM)
   unsigned char* Wu = nullptr;  // BF16 inverse rows in the tcgen05 operand layout (NR <= 128)
   int sms = 152;
   int device = -1;          // CUDA device the context was set up on
@@ -109,6 +110,11 @@ struct th_ctx {
   th::CoarseTile *tiles_s = nullptr, *tiles_l = nullptr;
   int ntiles_s = 0, ntiles_l = 0, nkc_s = 0, nkc_m = 0;
   long long lrb_chunks = 0;  // A chunks of the spikes over all tiles
+  // one right-hand side (mixed 2-D): the upper-triangle 64 x 64 blocks of the reduced inverse, their
+  // tile pairs and the partial products (k_sep_sym)
+  float2 *Ssym32 = nullptr, *spart32 = nullptr;
+  int2* sym_ij = nullptr;
+  int Tsym = 0, nsym = 0;
   th::CoarseUmmaArgs umma{};
   // cycle work vectors
   double2 *r64 = nullptr, *s64 = nullptr, *v64 = nullptr, *V64 = nullptr, *rc64 = nullptr, *uc64 = nullptr,
@@ -298,6 +304,13 @@ void carve_all(th_ctx& x, Carve& c) {
       x.rh32 = c.take<float2>(nred * nr);
       if (nr >= 2) x.Gt32 = c.take<float2>(mm * x.mcr);
       if (nr >= 8) x.LRt32 = c.take<float2>((size_t)g.mc * 2 * x.mcp * x.mcr);
+      if (x.P > 1) {
+        x.Tsym = (x.nred + 63) / 64;
+        x.nsym = x.Tsym * (x.Tsym + 1) / 2;
+        x.Ssym32 = c.take<float2>((size_t)x.nsym * 64 * 64);
+        x.sym_ij = c.take<int2>((size_t)x.nsym);
+        x.spart32 = c.take<float2>((size_t)x.Tsym * x.Tsym * 64);
+      }
       if (nr >= 8 && x.P > 1) {
         // chunk lengths of coarse_partition (P - 1 separator rows between P chunks)
         const int rows = g.mc - (x.P - 1), base = rows / x.P, rem = rows % x.P;
@@ -867,6 +880,13 @@ th_status coarse_solve_once_(th_ctx& x, const typename th::Cx<T>::t* rc, typenam
       a.nkc_s = x.nkc_s;
       a.umma = &x.umma;
     }
+    if (x.sep_sym) {
+      a.Ssym = x.Ssym32;
+      a.sym_ij = x.sym_ij;
+      a.spart = x.spart32;
+      a.Tsym = x.Tsym;
+      a.nsym = x.nsym;
+    }
   }
   a.mcr = x.mcr;
   a.rpcm = x.rpcm;
@@ -876,7 +896,7 @@ th_status coarse_solve_once_(th_ctx& x, const typename th::Cx<T>::t* rc, typenam
   a.nsm = x.sms;
   a.err = x.derr;
   if (!a.G || !a.LR) return TH_ERR_UNSUPPORTED;
-  x.launches += (x.P > 1) ? 4 : 1;
+  x.launches += (x.P > 1) ? ((nrhs == 1 && a.Ssym) ? 5 : 4) : 1;
   Prof prof(x, TH_K_COARSE_SOLVE, s);
   return cuda_status(th::launch_coarse_part<T>(a, nrhs, x.cluster, s));
 }
@@ -1643,6 +1663,31 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     for (size_t r = 0; r < nr_; ++r) std::copy(&cpart.Sinv[r * nr_], &cpart.Sinv[r * nr_] + nr_, &sp[r * ld]);
     if ((st = upload_c(x->Si64, x->Si32, sp)) != TH_OK) return st;
   }
+  if (x->Ssym32 && x->sym_ij) {
+    // Sinv's upper-triangle 64 x 64 blocks (I <= J), row-major, zero padded
+    const int T = x->Tsym, nred = x->nred;
+    std::vector<int2> ij;
+    for (int I = 0; I < T; ++I)
+      for (int J = I; J < T; ++J) ij.push_back(make_int2(I, J));
+    if ((int)ij.size() != x->nsym) return TH_ERR_ARG;
+    std::vector<float2> sb((size_t)x->nsym * 64 * 64, make_float2(0.f, 0.f));
+    th::parallel_for(x->nsym, [&](int b) {
+      const int I = ij[b].x, J = ij[b].y;
+      for (int r = 0; r < 64; ++r) {
+        const int row = I * 64 + r;
+        if (row >= nred) break;
+        for (int c = 0; c < 64; ++c) {
+          const int col = J * 64 + c;
+          if (col >= nred) break;
+          const cplx v = cpart.Sinv[(size_t)row * nred + col];
+          sb[((size_t)b * 64 + r) * 64 + c] = make_float2((float)v.real(), (float)v.imag());
+        }
+      }
+    });
+    if ((st = up(x->Ssym32, sb.data(), sb.size() * sizeof(float2))) != TH_OK) return st;
+    if ((st = up(x->sym_ij, ij.data(), ij.size() * sizeof(int2))) != TH_OK) return st;
+    TH_CU(cudaStreamSynchronize(s));
+  }
   std::vector<float2> cell32, rho32, cl32, cd32, cu32;
   if (x->mixed) {
     cell32 = to2f(d3 ? cb3.cell : cb.cell);
@@ -1845,6 +1890,8 @@ th_status th_set_kernel_variant(th_ctx* x, int kernel, int prec, int variant) {
     x->coarse_refine = variant;
   } else if (kernel == TH_K_KRYLOV) {
     x->krylov_ds = variant;
+  } else if (kernel == TH_K_SEP_SYM) {
+    x->sep_sym = variant;
   } else {
     return TH_ERR_ARG;
   }
@@ -1865,6 +1912,7 @@ th_status th_get_kernel_variant(const th_ctx* x, int kernel, int prec, int* vari
   else if (kernel == TH_K_AZ) *variant = (x->az_ds && x->kcds && x->g.dim == 2) ? 1 : 0;
   else if (kernel == TH_K_COARSE_REFINE) *variant = (x->zc32 && x->wc32) ? x->coarse_refine : 0;
   else if (kernel == TH_K_KRYLOV) *variant = x->krylov_ds;
+  else if (kernel == TH_K_SEP_SYM) *variant = (x->sep_sym && x->Ssym32) ? 1 : 0;
   else return TH_ERR_ARG;
   return TH_OK;
 }

@@ -1193,6 +1193,99 @@ static cudaError_t launch_tsgemm(const CoarsePartArgs<T>& a, cudaStream_t s) {
   return launch_pdl(k_coarse_tsgemm<T, NB1, 1>, dim3(g1), dim3(512), sm1, s, 0, a);
 }
 
+// The separator values xhat = Sinv rhat for one right-hand side from the upper
+// triangle of Sinv only.  Sinv is complex symmetric (Sinv^T = Sinv: the inverse
+// of the Schur complement of the complex-symmetric A_q), so a stored block
+// S_IJ (J > I) of 64 x 64 serves both y_I += S_IJ x_J and y_J += S_IJ^T x_I:
+// half the bytes of the full GEMV.  One CTA per stored block stages it in
+// shared memory (rows padded to 65 entries, so that neither the row-wise nor
+// the column-wise pass has more than the minimum two wavefronts per warp),
+// forms both products and writes them as partials part[(I T + J) 64 + r] (for
+// row tile I); k_sep_sym_sum adds the T partials of every unknown in a fixed
+// order and writes it into the separator rows of x.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sep_sym(const CoarsePartArgs<T> a) {
+  using C = typename Cx<T>::t;
+  constexpr int R = 64, RS = 65;
+  __shared__ C sb[R * RS];
+  __shared__ C xi[R], xj[R];
+  __shared__ C red[4][R];
+  ptx::grid_dep_wait();  // launched with a programmatic dependency inside the cycle
+  ptx::grid_dep_launch();
+  const int2 ij = a.sym_ij[blockIdx.x];
+  const int I = ij.x, J = ij.y, tid = threadIdx.x;
+  const C* blk = a.Ssym + (size_t)blockIdx.x * R * R;
+  for (int e = tid; e < R * R / 2; e += 256) {  // two complex values per 16-byte load
+    const int r = e / (R / 2), c2 = e - r * (R / 2);
+    const C* p = blk + (size_t)r * R + 2 * c2;
+    sb[r * RS + 2 * c2] = p[0];
+    sb[r * RS + 2 * c2 + 1] = p[1];
+  }
+  if (tid < R) {
+    C v;
+    v.x = 0;
+    v.y = 0;
+    const int gi = I * R + tid, gj = J * R + tid;
+    xi[tid] = gi < a.nred ? a.rhat[gi] : v;
+    xj[tid] = gj < a.nred ? a.rhat[gj] : v;
+  }
+  __syncthreads();
+  const int r = tid & (R - 1), q = tid >> 6;  // row (or column) and quarter of the 64
+  C acc;
+  acc.x = 0;
+  acc.y = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) cmac(acc, sb[r * RS + q * 16 + k], xj[q * 16 + k]);  // (S_IJ x_J)_r
+  red[q][r] = acc;
+  __syncthreads();
+  if (tid < R) {
+    C y = red[0][tid];
+#pragma unroll
+    for (int u = 1; u < 4; ++u) {
+      y.x += red[u][tid].x;
+      y.y += red[u][tid].y;
+    }
+    a.spart[((size_t)I * a.Tsym + J) * R + tid] = y;
+  }
+  if (J == I) return;  // uniform over the CTA
+  __syncthreads();
+  acc.x = 0;
+  acc.y = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) cmac(acc, sb[(q * 16 + k) * RS + r], xi[q * 16 + k]);  // (S_IJ^T x_I)_c, c = r
+  red[q][r] = acc;
+  __syncthreads();
+  if (tid < R) {
+    C y = red[0][tid];
+#pragma unroll
+    for (int u = 1; u < 4; ++u) {
+      y.x += red[u][tid].x;
+      y.y += red[u][tid].y;
+    }
+    a.spart[((size_t)J * a.Tsym + I) * R + tid] = y;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sep_sym_sum(const CoarsePartArgs<T> a) {
+  using C = typename Cx<T>::t;
+  ptx::grid_dep_wait();
+  ptx::grid_dep_launch();
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= a.nred) return;
+  const int I = idx >> 6, r = idx & 63;
+  C y;
+  y.x = 0;
+  y.y = 0;
+  for (int J = 0; J < a.Tsym; ++J) {
+    const C v = a.spart[((size_t)I * a.Tsym + J) * 64 + r];
+    y.x += v.x;
+    y.y += v.y;
+  }
+  const int k = idx / a.mc, e = idx - k * a.mc;
+  a.x[(size_t)a.sep[k] * a.mc + e] = y;
+}
+
 // ------------------------------------------------------------- launcher
 template <typename T>
 size_t chunk_sweep2_smem(const CoarsePartArgs<T>& a) {
@@ -1374,6 +1467,20 @@ cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a0, int nrhs, int cluste
   if (e != cudaSuccess) return e;
   CoarsePartArgs<T> b = a;
   b.nrhs = nrhs;
+  if constexpr (std::is_same<T, float>::value) {
+    if (nrhs == 1 && a.Ssym && a.spart && a.sym_ij) {
+      // the separator values from Sinv's upper triangle, then the spike correction
+      e = launch_pdl(k_sep_sym<T>, dim3((unsigned)a.nsym), dim3(256), 0, s, 0, b);
+      if (e != cudaSuccess) return e;
+      e = launch_pdl(k_sep_sym_sum<T>, dim3((unsigned)((a.nred + 255) / 256)), dim3(256), 0, s, 0, b);
+      if (e != cudaSuccess) return e;
+      using C = typename Cx<T>::t;
+      const size_t sm1 = sizeof(C) * (size_t)2 * a.mcp;
+      e = cudaFuncSetAttribute(k_coarse_tsgemm<T, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+      if (e != cudaSuccess) return e;
+      return launch_pdl(k_coarse_tsgemm<T, 1, 1>, dim3((unsigned)(4 * a.mc)), dim3(512), sm1, s, 0, b);
+    }
+  }
   return launch_tsgemm<T, 1>(b, s);
 }
 

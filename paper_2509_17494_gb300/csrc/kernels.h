@@ -239,6 +239,12 @@ struct CoarsePartArgs {
   unsigned char* rst;
   int nkc_s;
   const struct CoarseUmmaArgs* umma;  // host-side description of the tensor-core products, or null
+  // one right-hand side (FP32): the upper-triangle 64 x 64 blocks of the complex-symmetric Sinv
+  // (row-major, zero padded), their (I, J) tile pairs, and the partial products [T][T][64]; or null
+  const typename Cx<T>::t* Ssym;
+  const int2* sym_ij;
+  typename Cx<T>::t* spart;
+  int Tsym, nsym;
 };
 template <typename T>
 cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a, int nrhs, int cluster, cudaStream_t s);

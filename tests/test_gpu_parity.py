@@ -161,6 +161,26 @@ def test_coarse_solve_fp32_sweep_variants(th, c):
     assert relerr(host(outs[0]), host(outs[1])) < 1e-5
 
 
+@pytest.mark.parametrize("c", CASES)
+def test_coarse_solve_symmetric_separator_product(th, c):
+    """One right-hand side in FP32: the separator values from the upper triangle
+    of the complex-symmetric reduced inverse (TH_K_SEP_SYM 1, default; 64 x 64
+    blocks serving S_IJ x_J and S_IJ^T x_I) against the full GEMV (0): the same
+    products in another summation order, FP32 rounding apart (1e-5), and both
+    against the oracle's banded LU (1e-4)."""
+    S, P = build(th, c, nrhs=1, prec="fp32", extra_prec=("fp64",))
+    assert S.get_variant("sep_sym", "fp32") == 1
+    B = twogrid.BandedSolver(P.Aq)
+    rc = synth.random_complex(P.Nc, 12)
+    want = B.solve(rc)
+    sym = host(S.coarse_solve(dev(rc)))
+    S.device_status()
+    S.set_variant("sep_sym", "fp32", 0)
+    full = host(S.coarse_solve(dev(rc)))
+    assert relerr(sym, full) < 1e-5
+    assert relerr(sym, want) < 1e-4 and relerr(full, want) < 1e-4
+
+
 @pytest.mark.parametrize("c", [CASES[0], CASES[2], CASES[5]])
 @pytest.mark.parametrize("nrhs", [2, 11])
 def test_coarse_solve_many_rhs(th, c, nrhs):
