@@ -112,6 +112,8 @@ typedef struct {
                        (2-D only; TH_ERR_UNSUPPORTED in 3-D) */
   double alpha_c;   /* TH_CK_GALERKIN: complex shift of the coarse operator's volume
                        term, k^2 (1 + i alpha_c) + i eps (Table 2); ignored for QSFEM */
+  int coarse_chunks; /* 2-D QSFEM coarse solve: the number P of row chunks of its
+                        partition (2 P - 1 <= m_c); 0 (the default) = round(sqrt(m_c)) */
 } th_params;
 
 enum { TH_CK_QSFEM = 0, TH_CK_GALERKIN = 1 };

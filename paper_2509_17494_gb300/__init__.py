@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
                 ("n_s", ctypes.c_int), ("omega_c", ctypes.c_double), ("prec", ctypes.c_int),
                 ("prec_mask", ctypes.c_uint), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("tol", ctypes.c_double), ("nrhs_max", ctypes.c_int), ("coarse_kind", ctypes.c_int),
-                ("alpha_c", ctypes.c_double)]
+                ("alpha_c", ctypes.c_double), ("coarse_chunks", ctypes.c_int)]
 
 
 COARSE_KIND = {"qsfem": 0, "gal": 1}   # TH_CK_QSFEM ('opt', Section 3.3), TH_CK_GALERKIN ('gal', Section 4)
@@ -143,7 +143,7 @@ def _mesh(n, p, bc, dim=2):
 
 
 def _params(alpha_s=0.5, l_dd=2, n_dd=1, n_s=1, omega_c=1.0, prec="fp64", extra_prec=(), restart=30,
-            maxit=200, tol=1e-8, nrhs_max=1, coarse="qsfem", alpha_c=0.0):
+            maxit=200, tol=1e-8, nrhs_max=1, coarse="qsfem", alpha_c=0.0, coarse_chunks=0):
     q = Params()
     q.alpha_s, q.l_dd, q.n_dd, q.n_s, q.omega_c = float(alpha_s), int(l_dd), int(n_dd), int(n_s), float(omega_c)
     q.prec = PREC[prec]
@@ -153,6 +153,7 @@ def _params(alpha_s=0.5, l_dd=2, n_dd=1, n_s=1, omega_c=1.0, prec="fp64", extra_
     q.prec_mask = mask
     q.restart, q.maxit, q.tol, q.nrhs_max = int(restart), int(maxit), float(tol), int(nrhs_max)
     q.coarse_kind, q.alpha_c = COARSE_KIND[coarse], float(alpha_c)
+    q.coarse_chunks = int(coarse_chunks)
     return q
 
 
@@ -310,9 +311,10 @@ class TwoGridSolver:
 
     def __init__(self, n, p, k_cell, eps_cell=None, bc="robin", alpha_s=0.5, l_dd=2, n_dd=1, n_s=1,
                  omega_c=1.0, prec="fp64", extra_prec=(), restart=30, maxit=200, tol=1e-8, nrhs_max=1,
-                 device=None, dim=None, coarse="qsfem", alpha_c=0.0):
+                 device=None, dim=None, coarse="qsfem", alpha_c=0.0, coarse_chunks=0):
         """coarse: 'qsfem' (the QSFEM coarse operator, the paper's 'opt') or 'gal'
-        (standard Galerkin p-type coarsening with coarse shift alpha_c, 2-D)."""
+        (standard Galerkin p-type coarsening with coarse shift alpha_c, 2-D);
+        coarse_chunks: row chunks of the 2-D coarse partition (0: round(sqrt(m_c)))."""
         import torch
 
         self.torch = torch
@@ -327,7 +329,7 @@ class TwoGridSolver:
         self.nrhs_max = int(nrhs_max)
         self._mesh = _mesh(n, p, bc, self.dim)
         self._params = _params(alpha_s, l_dd, n_dd, n_s, omega_c, prec, extra_prec, restart, maxit, tol, nrhs_max,
-                               coarse, alpha_c)
+                               coarse, alpha_c, coarse_chunks)
         self.coarse_kind = coarse
         L = lib()
         nb = ctypes.c_size_t(0)

@@ -398,7 +398,8 @@ th_status prepare(const th_mesh* mesh, const th_params* prm, th_ctx& x) {
   x.ref = ref;
   x.cluster = 8;
   x.rpc = (x.g.mc + x.cluster - 1) / x.cluster;
-  x.P = x.g.dim == 2 ? th::coarse_chunks(x.g.mc) : 1;
+  if (prm->coarse_chunks < 0 || (prm->coarse_chunks > 0 && 2 * prm->coarse_chunks - 1 > x.g.mc)) return TH_ERR_ARG;
+  x.P = x.g.dim == 2 ? (prm->coarse_chunks > 0 ? prm->coarse_chunks : th::coarse_chunks(x.g.mc)) : 1;
   x.mcp = x.g.mc + (x.g.mc & 1);
   x.rpcm = x.rpc + (x.rpc & 1);
   x.mcr = x.cluster * x.rpcm;

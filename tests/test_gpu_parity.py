@@ -181,6 +181,19 @@ def test_coarse_solve_symmetric_separator_product(th, c):
     assert relerr(sym, want) < 1e-4 and relerr(full, want) < 1e-4
 
 
+@pytest.mark.parametrize("chunks", [2, 5])
+def test_coarse_solve_chunk_count(th, chunks):
+    """th_params.coarse_chunks sets the partition's chunk count P (2 P - 1 <= m_c):
+    FP64 against the oracle's banded LU (1e-9) and the solve to 1e-8."""
+    c = CASES[5]
+    S, P = build(th, c, nrhs=1, coarse_chunks=chunks)
+    B = twogrid.BandedSolver(P.Aq)
+    rc = synth.random_complex(P.Nc, 13)
+    assert relerr(host(S.coarse_solve(dev(rc))), B.solve(rc)) < 1e-9
+    X, info = S.solve(dev(synth.random_complex(P.N, 14)))
+    assert info["relres_max"] <= 1e-8
+
+
 @pytest.mark.parametrize("c", [CASES[0], CASES[2], CASES[5]])
 @pytest.mark.parametrize("nrhs", [2, 11])
 def test_coarse_solve_many_rhs(th, c, nrhs):

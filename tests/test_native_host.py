@@ -131,6 +131,12 @@ def test_workspace_size_and_argument_errors(th):
         th.workspace_size(10, 4, l_dd=0)
     with pytest.raises(th.ThError):
         th.workspace_size(10, 4, restart=0)
+    # the coarse partition's chunk count: 2 P - 1 <= m_c (m_c = 21 here)
+    assert th.workspace_size(10, 4, coarse_chunks=11) > 0
+    for bad in (12, -1):
+        with pytest.raises(th.ThError) as e:
+            th.workspace_size(10, 4, coarse_chunks=bad)
+        assert e.value.code == 1
 
 
 def _stencil_matrix(sten, mc, q):
