@@ -1088,11 +1088,18 @@ th_status widen(th_ctx& x, const float2* in, double2* out, long long n, int acc,
 }
 
 // z = B v: the two-grid preconditioner (TwoGridStep with u = 0) in the active precision.
-th_status precondition(th_ctx& x, const double2* v, double2* z, int nrhs, cudaStream_t s) {
+// vsplit (mixed forms): v is in the split form of the double-single FGMRES basis.
+th_status precondition(th_ctx& x, const double2* v, double2* z, int nrhs, cudaStream_t s, bool vsplit = false) {
   const long long n = x.g.N * (long long)nrhs;
   if (x.active == TH_PREC_FP64) return cycle<double>(x, TH_PREC_FP64, v, z, true, nrhs, s);
   th_status st;
-  if ((st = narrow(x, v, x.f32, n, s)) != TH_OK) return st;
+  if (vsplit) {
+    x.launches += 1;
+    Prof prof(x, TH_K_VECTOR, s);
+    if ((st = cuda_status(th::launch_split_to_f32(v, x.f32, n, s))) != TH_OK) return st;
+  } else if ((st = narrow(x, v, x.f32, n, s)) != TH_OK) {
+    return st;
+  }
   if (can_fuse<float>(x, true)) return cycle_fused<float>(x, x.active, x.f32, x.u32, nrhs, z, 0, s);
   if ((st = cycle<float>(x, x.active, x.f32, x.u32, true, nrhs, s)) != TH_OK) return st;
   return widen(x, x.u32, z, n, 0, s);
@@ -2287,7 +2294,12 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
       TH_CU(cudaStreamSynchronize(s));
     }
     x->launches += 1;
-    TH_CU(th::launch_scale_rhs(x->Vk, x->Vk, x->scal, N, nrhs, s));
+    // the basis in the split form of the double-single Gram-Schmidt kernels (mixed forms)
+    if (kds) {
+      TH_CU(th::launch_scale_split(x->Vk, x->Vk, x->scal, N, nrhs, s));
+    } else {
+      TH_CU(th::launch_scale_rhs(x->Vk, x->Vk, x->scal, N, nrhs, s));
+    }
     th::ArnoldiArgs aa{x->h1, x->nrm, x->Hd, x->csd, x->snd, x->gd, x->fnd, x->actd, x->scal, x->statd, tol, nrhs, m};
     // Arnoldi steps are enqueued one ahead of the host: after enqueueing step j the
     // host reads the status of step j - 1 (pinned copy, event), so the GPU does not
@@ -2360,14 +2372,14 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
       // which with the two-grid preconditioner does not occur in practice.
       auto step = [&](cudaStream_t ss) -> th_status {
         th_status e;
-        if ((e = precondition(*x, Vj, Zj, nrhs, ss)) != TH_OK) return e;
+        if ((e = precondition(*x, Vj, Zj, nrhs, ss, kds)) != TH_OK) return e;
         if ((e = az_apply(*x, Zj, x->w, nrhs, ss)) != TH_OK) return e;
         x->launches += 6;
         {
           Prof prof(*x, TH_K_KRYLOV, ss);
           if (kds) {
-            TH_CU(th::launch_mdot_ds(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, ss));
-            TH_CU(th::launch_maxpy_ds(x->Vk, vstride, x->h1, j + 2, x->w, N, j + 1, nrhs, -1.0, ss));
+            TH_CU(th::launch_mdot_ds(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, 1, ss));
+            TH_CU(th::launch_maxpy_ds(x->Vk, vstride, x->h1, j + 2, x->w, N, j + 1, nrhs, -1.0, 1, ss));
             TH_CU(th::launch_norm2_ds(x->w, N, nrhs, x->npart, x->nrm, x->nblk, ss));
           } else {
             TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, ss));
@@ -2375,7 +2387,11 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
             TH_CU(th::launch_norm2(x->w, N, nrhs, x->npart, x->nrm, x->nblk, ss));
           }
           TH_CU(th::launch_arnoldi(aa, j, ss));
-          TH_CU(th::launch_scale_rhs(x->w, x->Vk + (size_t)(j + 1) * vstride, x->scal, N, nrhs, ss));
+          if (kds) {
+            TH_CU(th::launch_scale_split(x->w, x->Vk + (size_t)(j + 1) * vstride, x->scal, N, nrhs, ss));
+          } else {
+            TH_CU(th::launch_scale_rhs(x->w, x->Vk + (size_t)(j + 1) * vstride, x->scal, N, nrhs, ss));
+          }
         }
         TH_CU(cudaMemcpyAsync(x->pin + (size_t)(j & 1) * nrhs * 5, x->statd, sizeof(double) * nrhs * 5,
                               cudaMemcpyDeviceToHost, ss));
@@ -2423,7 +2439,7 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
     TH_CU(cudaMemcpyAsync(x->ybuf, yv.data(), sizeof(double2) * yv.size(), cudaMemcpyHostToDevice, s));
     x->launches += 1;
     if (kds) {
-      TH_CU(th::launch_maxpy_ds(x->Zk, vstride, x->ybuf, jdone, u2, N, jdone, nrhs, 1.0, s));
+      TH_CU(th::launch_maxpy_ds(x->Zk, vstride, x->ybuf, jdone, u2, N, jdone, nrhs, 1.0, 0, s));
     } else {
       TH_CU(th::launch_maxpy(x->Zk, vstride, x->ybuf, jdone, u2, N, jdone, nrhs, 1.0, s));
     }

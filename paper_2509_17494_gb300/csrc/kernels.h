@@ -372,10 +372,15 @@ cudaError_t launch_maxpy(const double2* Vbase, long long vstride, const double2*
 cudaError_t launch_norm2(const double2* w, long long N, int nrhs, double* part, double* out,
                          int nblk, cudaStream_t s);
 // the same three in double-single arithmetic (the mixed form's FGMRES; vec.cu)
+// split != 0: the basis vectors V_i stored as (re h, re l, im h, im l) floats (launch_scale_split)
 cudaError_t launch_mdot_ds(const double2* Vbase, long long vstride, const double2* w, long long N, int nv, int self,
-                           int nrhs, double2* part, double2* h, int nblk, cudaStream_t s);
+                           int nrhs, double2* part, double2* h, int nblk, int split, cudaStream_t s);
 cudaError_t launch_maxpy_ds(const double2* Vbase, long long vstride, const double2* h, int hstride, double2* w,
-                            long long N, int nv, int nrhs, double sign, cudaStream_t s);
+                            long long N, int nv, int nrhs, double sign, int split, cudaStream_t s);
+// out = in * scale[rhs] written in the split form; the split form's FP32 rounding (h + l)
+cudaError_t launch_scale_split(const double2* in, double2* out, const double* inv, long long N, int nrhs,
+                               cudaStream_t s);
+cudaError_t launch_split_to_f32(const double2* in, float2* out, long long n, cudaStream_t s);
 cudaError_t launch_norm2_ds(const double2* w, long long N, int nrhs, double* part, double* out, int nblk,
                             cudaStream_t s);
 // FGMRES Arnoldi bookkeeping on the device (one thread per rhs), see vec.cu

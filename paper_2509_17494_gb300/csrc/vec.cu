@@ -466,7 +466,22 @@ __device__ __forceinline__ void acc_warp_sum(dsacc& a) {
   }
 }
 
-template <int TILE, int MINB>
+// The basis vector i of a right-hand side at entry n: FP64 (split on load) or,
+// SPLIT, stored already split as (re h, re l, im h, im l) in the same 16 bytes
+template <bool SPLIT>
+__device__ __forceinline__ void basis_entry(const double2* __restrict__ Vb, size_t idx, ds& x, ds& y) {
+  if constexpr (SPLIT) {
+    const float4 q = reinterpret_cast<const float4*>(Vb)[idx];
+    x = ds(q.x, q.y);
+    y = ds(q.z, q.w);
+  } else {
+    const double2 v = Vb[idx];
+    x = ds_from_double(v.x);
+    y = ds_from_double(v.y);
+  }
+}
+
+template <int TILE, int MINB, bool SPLIT>
 __global__ void __launch_bounds__(256, MINB) k_mdot_part_ds(const double2* __restrict__ Vb, long long vstride,
                                                             const double2* __restrict__ w, long long N, int nv,
                                                             int self, double2* __restrict__ part, int nblk) {
@@ -489,11 +504,7 @@ __global__ void __launch_bounds__(256, MINB) k_mdot_part_ds(const double2* __res
     for (int t = 0; t < TILE; ++t) {
       if (t < ni) {
         ds vx = wx, vy = wy;
-        if (i0 + t < nv) {
-          const double2 v = Vb[(size_t)(i0 + t) * vstride + (size_t)rhs * N + n];
-          vx = ds_from_double(v.x);
-          vy = ds_from_double(v.y);
-        }
+        if (i0 + t < nv) basis_entry<SPLIT>(Vb, (size_t)(i0 + t) * vstride + (size_t)rhs * N + n, vx, vy);
         // conj(v) w = (vx wx + vy wy) + i (vx wy - vy wx)
         acc_prod(ar[t], vx, wx);
         acc_prod(ar[t], vy, wy);
@@ -528,12 +539,15 @@ __global__ void __launch_bounds__(256, MINB) k_mdot_part_ds(const double2* __res
 }
 
 cudaError_t launch_mdot_ds(const double2* Vbase, long long vstride, const double2* w, long long N, int nv, int self,
-                           int nrhs, double2* part, double2* h, int nblk, cudaStream_t s) {
+                           int nrhs, double2* part, double2* h, int nblk, int split, cudaStream_t s) {
   const int nvt = nv + (self ? 1 : 0);
   dim3 grid(nblk, (nvt + kDotTile - 1) / kDotTile, nrhs);
   // four CTAs per SM (at most 64 registers a thread): the loads of more warps in
   // flight (measured: 0.72 of the time with the compiler's 93 registers)
-  k_mdot_part_ds<kDotTile, 4><<<grid, 256, 0, s>>>(Vbase, vstride, w, N, nv, self ? 1 : 0, part, nblk);
+  if (split)
+    k_mdot_part_ds<kDotTile, 4, true><<<grid, 256, 0, s>>>(Vbase, vstride, w, N, nv, self ? 1 : 0, part, nblk);
+  else
+    k_mdot_part_ds<kDotTile, 4, false><<<grid, 256, 0, s>>>(Vbase, vstride, w, N, nv, self ? 1 : 0, part, nblk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int total = nvt * nrhs;
@@ -543,6 +557,7 @@ cudaError_t launch_mdot_ds(const double2* Vbase, long long vstride, const double
 
 // w[rhs] += sign * sum_i h[rhs * hstride + i] V_i[rhs]; the coefficients are
 // split once per block into shared memory ([nv][re h, re l, im h, im l])
+template <bool SPLIT>
 __global__ void __launch_bounds__(256) k_maxpy_ds(const double2* __restrict__ Vb, long long vstride,
                                                   const double2* __restrict__ h, int hstride, double2* __restrict__ w,
                                                   long long N, int nv, double sign) {
@@ -565,12 +580,11 @@ __global__ void __launch_bounds__(256) k_maxpy_ds(const double2* __restrict__ Vb
     dsacc sr{0.f, 0.f}, si{0.f, 0.f}, tr{0.f, 0.f}, ti{0.f, 0.f};
     int i = 0;
     for (; i + 1 < nv; i += 2) {
-      const double2 v0 = Vb[(size_t)i * vstride + (size_t)rhs * N + n];
-      const double2 v1 = Vb[(size_t)(i + 1) * vstride + (size_t)rhs * N + n];
+      ds v0x, v0y, v1x, v1y;
+      basis_entry<SPLIT>(Vb, (size_t)i * vstride + (size_t)rhs * N + n, v0x, v0y);
+      basis_entry<SPLIT>(Vb, (size_t)(i + 1) * vstride + (size_t)rhs * N + n, v1x, v1y);
       const ds c0r(hsm[4 * i], hsm[4 * i + 1]), c0i(hsm[4 * i + 2], hsm[4 * i + 3]);
       const ds c1r(hsm[4 * i + 4], hsm[4 * i + 5]), c1i(hsm[4 * i + 6], hsm[4 * i + 7]);
-      const ds v0x = ds_from_double(v0.x), v0y = ds_from_double(v0.y);
-      const ds v1x = ds_from_double(v1.x), v1y = ds_from_double(v1.y);
       acc_prod(sr, c0r, v0x);
       acc_prod(tr, c1r, v1x);
       acc_prod(si, c0r, v0y);
@@ -581,9 +595,9 @@ __global__ void __launch_bounds__(256) k_maxpy_ds(const double2* __restrict__ Vb
       acc_prod(ti, c1i, v1x);
     }
     if (i < nv) {
-      const double2 v = Vb[(size_t)i * vstride + (size_t)rhs * N + n];
+      ds vx, vy;
+      basis_entry<SPLIT>(Vb, (size_t)i * vstride + (size_t)rhs * N + n, vx, vy);
       const ds cr(hsm[4 * i], hsm[4 * i + 1]), ci(hsm[4 * i + 2], hsm[4 * i + 3]);
-      const ds vx = ds_from_double(v.x), vy = ds_from_double(v.y);
       acc_prod(sr, cr, vx);
       acc_prod(sr, dneg(ci), vy);
       acc_prod(si, cr, vy);
@@ -599,12 +613,49 @@ __global__ void __launch_bounds__(256) k_maxpy_ds(const double2* __restrict__ Vb
 }
 
 cudaError_t launch_maxpy_ds(const double2* Vbase, long long vstride, const double2* h, int hstride, double2* w,
-                            long long N, int nv, int nrhs, double sign, cudaStream_t s) {
+                            long long N, int nv, int nrhs, double sign, int split, cudaStream_t s) {
   long long b = (N + 255) / 256;
   dim3 grid((unsigned)(b > 1216 ? 1216 : b), nrhs);
   const size_t smem = sizeof(float) * 4 * (size_t)(nv > 0 ? nv : 1);
   if (smem > 48 * 1024) return cudaErrorInvalidValue;
-  k_maxpy_ds<<<grid, 256, smem, s>>>(Vbase, vstride, h, hstride, w, N, nv, sign);
+  if (split)
+    k_maxpy_ds<true><<<grid, 256, smem, s>>>(Vbase, vstride, h, hstride, w, N, nv, sign);
+  else
+    k_maxpy_ds<false><<<grid, 256, smem, s>>>(Vbase, vstride, h, hstride, w, N, nv, sign);
+  return cudaGetLastError();
+}
+
+// out[rhs] = split(in[rhs] * scale[rhs]) as (re h, re l, im h, im l) (0 if the
+// scale is not finite); the product in FP64, the split by ds_from_double, so
+// the Gram-Schmidt kernels read exactly the numbers they would split on load.
+// in and out may be the same vector.
+__global__ void k_scale_split(const double2* in, float4* out, const double* __restrict__ sc, long long N) {
+  const int rhs = blockIdx.y;
+  const double c = sc[rhs];
+  const double f = isfinite(c) ? c : 0.0;
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    const double2 v = in[(size_t)rhs * N + n];
+    const ds x = ds_from_double(v.x * f), y = ds_from_double(v.y * f);
+    out[(size_t)rhs * N + n] = make_float4(x.h, x.l, y.h, y.l);
+  }
+}
+cudaError_t launch_scale_split(const double2* in, double2* out, const double* inv, long long N, int nrhs,
+                               cudaStream_t s) {
+  long long b = (N + 255) / 256;
+  dim3 grid((unsigned)(b > 1216 ? 1216 : b), nrhs);
+  k_scale_split<<<grid, 256, 0, s>>>(in, reinterpret_cast<float4*>(out), inv, N);
+  return cudaGetLastError();
+}
+// FP32 complex from the split form: h + l rounded to FP32
+__global__ void k_split_to_f32(const float4* __restrict__ in, float2* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float4 q = in[i];
+    out[i] = make_float2(__fadd_rn(q.x, q.y), __fadd_rn(q.z, q.w));
+  }
+}
+cudaError_t launch_split_to_f32(const double2* in, float2* out, long long n, cudaStream_t s) {
+  long long b = (n + 255) / 256;
+  k_split_to_f32<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(reinterpret_cast<const float4*>(in), out, n);
   return cudaGetLastError();
 }
 
