@@ -1012,8 +1012,8 @@ __global__ void __launch_bounds__(512) k_spikes_cols(const CoarsePartArgs<T> a) 
 //   MODE 0: xhat = Sinv rhat, written into the separator rows of x (one CTA per
 //           16 rows of Sinv, whose rows are padded to an even length ldS);
 //   MODE 1: x_j -= [L_j | R_j] [x_left; x_right] on every chunk row j (one CTA
-//           per quarter (one rhs) or half (tiles) of a block row; a CTA of a
-//           separator row returns at once).
+//           per 32 rows (one rhs: 16 warps of two rows, a single pass) or per
+//           half (tiles) of a block row; a CTA of a separator row returns at once).
 // The CTA stages the tile's right-hand-side columns in shared memory ([rhs]
 // [column]); each warp streams R matrix rows two complex values per lane and
 // load (16-byte loads for FP32, consecutive across lanes), reads the matching
@@ -1051,7 +1051,8 @@ __global__ void __launch_bounds__(512) k_coarse_tsgemm(const CoarsePartArgs<T> a
     rbeg = blk * WARPS * R;
     rend = min(a.nred, rbeg + WARPS * R);
   } else {
-    constexpr int PARTS = NB == 1 ? 4 : 2;  // CTAs per block row
+    // CTAs per block row: one right-hand side, 32 rows each (16 warps of two rows, one pass)
+    const int PARTS = NB == 1 ? (mc + 31) / 32 : 2;
     j = blk / PARTS;
     chunk = a.chunk_of[j];
     if (chunk < 0) return;  // separator block row (uniform over the CTA)
@@ -1189,7 +1190,7 @@ static cudaError_t launch_tsgemm(const CoarsePartArgs<T>& a, cudaStream_t s) {
   const unsigned g0 = (unsigned)((a.nred + 15) / 16) * nt0;
   e = launch_pdl(k_coarse_tsgemm<T, NB0, 0>, dim3(g0), dim3(512), sm0, s, 0, a);
   if (e != cudaSuccess) return e;
-  const unsigned g1 = (unsigned)((NB1 == 1 ? 4 : 2) * a.mc) * nt1;
+  const unsigned g1 = (unsigned)((NB1 == 1 ? (a.mc + 31) / 32 : 2) * a.mc) * nt1;
   return launch_pdl(k_coarse_tsgemm<T, NB1, 1>, dim3(g1), dim3(512), sm1, s, 0, a);
 }
 
@@ -1478,7 +1479,8 @@ cudaError_t launch_coarse_part(const CoarsePartArgs<T>& a0, int nrhs, int cluste
       const size_t sm1 = sizeof(C) * (size_t)2 * a.mcp;
       e = cudaFuncSetAttribute(k_coarse_tsgemm<T, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
       if (e != cudaSuccess) return e;
-      return launch_pdl(k_coarse_tsgemm<T, 1, 1>, dim3((unsigned)(4 * a.mc)), dim3(512), sm1, s, 0, b);
+      return launch_pdl(k_coarse_tsgemm<T, 1, 1>, dim3((unsigned)((a.mc + 31) / 32 * a.mc)), dim3(512), sm1, s, 0,
+                        b);
     }
   }
   return launch_tsgemm<T, 1>(b, s);
