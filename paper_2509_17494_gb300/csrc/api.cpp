@@ -598,6 +598,25 @@ th_status az_apply(th_ctx& x, const double2* z, double2* w, int nrhs, cudaStream
   return fine_apply<double>(x, TH_OP_A, z, nullptr, w, nrhs, s);
 }
 
+// r = f - A u into an FP64 vector: in double-single arithmetic where the mixed
+// form's double-single apply exists (exact = false), else FP64.  th_solve takes
+// its restart residuals this way and confirms convergence with the FP64 apply.
+th_status fgmres_residual(th_ctx& x, const double2* u, const double2* f, double2* r, int nrhs, cudaStream_t s,
+                          bool exact) {
+  if (!exact && x.active != TH_PREC_FP64 && x.az_ds && x.kcds && x.g.dim == 2) {
+    th::FineArgs<th::ds> a = fine_args<th::ds>(x, TH_OP_A, nrhs);
+    a.u = reinterpret_cast<const th::cds*>(u);
+    a.f = reinterpret_cast<const th::cds*>(f);
+    a.y = reinterpret_cast<th::cds*>(r);
+    a.residual = 1;
+    a.out64 = 1;
+    x.launches += 1;
+    Prof prof(x, TH_K_FINE, s);
+    return cuda_status(th::launch_fine_apply<th::ds>(a, nrhs, s));
+  }
+  return fine_apply<double>(x, TH_OP_A, u, f, r, nrhs, s);
+}
+
 template <typename T> struct PrecBufs;
 template <> struct PrecBufs<double> {
   static double2* r(th_ctx& x) { return x.r64; }
@@ -2264,15 +2283,27 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
       }
     }
   } restore{x, saved_mode};
+  // the residual at the loop's exit, FP64 (reused as the final true residual)
+  bool exact_exit = false;
   for (;;) {
-    // r = f - A x  -> V_0
-    if ((st = fine_apply<double>(*x, TH_OP_A, u2, f2, x->Vk, nrhs, s)) != TH_OK) return st;
-    if ((st = norms(*x, x->Vk, nrhs, beta, s)) != TH_OK) return st;
+    // r = f - A x -> V_0: in double-single arithmetic in the mixed forms (about
+    // 2^-44 of |A||x|); when that shows convergence or the iteration limit, again
+    // in FP64, which decides
+    const std::vector<int> done_before = done;
     bool all = true;
-    for (int r = 0; r < nrhs; ++r) {
-      if (!std::isfinite(beta[r])) return TH_ERR_NONFINITE;
-      if (!done[r] && beta[r] <= tol * fn[r]) done[r] = 1;
-      all = all && done[r];
+    for (int pass = 0; pass < 2; ++pass) {
+      const bool exact = pass == 1 || !kds;
+      if ((st = fgmres_residual(*x, u2, f2, x->Vk, nrhs, s, exact)) != TH_OK) return st;
+      if ((st = norms(*x, x->Vk, nrhs, beta, s)) != TH_OK) return st;
+      done = done_before;
+      all = true;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!std::isfinite(beta[r])) return TH_ERR_NONFINITE;
+        if (!done[r] && beta[r] <= tol * fn[r]) done[r] = 1;
+        all = all && done[r];
+      }
+      exact_exit = exact;
+      if (exact || !(all || it >= x->prm.maxit)) break;
     }
     if (all || it >= x->prm.maxit) break;
     std::vector<int> active(nrhs), jr(nrhs, 0);
@@ -2451,10 +2482,12 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
       ++fallbacks;
     }
   }
-  // final true residuals
-  if ((st = fine_apply<double>(*x, TH_OP_A, u2, f2, x->w, nrhs, s)) != TH_OK) return st;
-  std::vector<double> rn;
-  if ((st = norms(*x, x->w, nrhs, rn, s)) != TH_OK) return st;
+  // final true residuals (FP64): those of the loop's exit
+  std::vector<double> rn = beta;
+  if (!exact_exit) {
+    if ((st = fine_apply<double>(*x, TH_OP_A, u2, f2, x->w, nrhs, s)) != TH_OK) return st;
+    if ((st = norms(*x, x->w, nrhs, rn, s)) != TH_OK) return st;
+  }
   double rmax = 0.0;
   int nconv = 0;
   for (int r = 0; r < nrhs; ++r) {
