@@ -109,6 +109,8 @@ struct th_ctx {
   unsigned char *Sb16 = nullptr, *LRb16 = nullptr, *rst16 = nullptr, *xst16 = nullptr;
   th::CoarseTile *tiles_s = nullptr, *tiles_l = nullptr;
   int ntiles_s = 0, ntiles_l = 0, nkc_s = 0, nkc_m = 0;
+  int nsplit_s = 1;          // K splits of the separator product (to fill the SMs), partials in spart_s
+  float2* spart_s = nullptr;
   long long lrb_chunks = 0;  // A chunks of the spikes over all tiles
   // one right-hand side (mixed 2-D): the upper-triangle 64 x 64 blocks of the reduced inverse, their
   // tile pairs and the partial products (k_sep_sym)
@@ -331,7 +333,11 @@ void carve_all(th_ctx& x, Carve& c) {
         x.LRb16 = c.take<unsigned char>((size_t)x.lrb_chunks * 32768);
         x.rst16 = c.take<unsigned char>(groups * x.nkc_s * 16384);
         x.xst16 = c.take<unsigned char>(groups * (x.P - 1) * x.nkc_m * 16384);
-        x.tiles_s = c.take<th::CoarseTile>(x.ntiles_s);
+        // split the separator product over K so that its tiles fill the 152 SMs (the tiles of
+        // the 401-row grid: 60), at least 8 chunks a split
+        x.nsplit_s = std::max(1, std::min(std::min(8, 152 / std::max(1, x.ntiles_s)), x.nkc_s / 8));
+        x.tiles_s = c.take<th::CoarseTile>((size_t)x.ntiles_s * x.nsplit_s);
+        x.spart_s = x.nsplit_s > 1 ? c.take<float2>((size_t)x.nsplit_s * groups * 64 * x.nred) : nullptr;
         x.tiles_l = c.take<th::CoarseTile>(x.ntiles_l);
       }
     }
@@ -1604,7 +1610,7 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     // core-matrix layout (umma_off32); padding rows and columns are zero
     const int mc = g.mc, nred = x->nred, nkc_s = x->nkc_s, nkc_m = x->nkc_m;
     const size_t K = 2 * (size_t)x->mcp;  // row length of cpart.LR
-    std::vector<th::CoarseTile> ts(x->ntiles_s), tl;
+    std::vector<th::CoarseTile> ts, tl;
     {
       std::vector<uint16_t> sb((size_t)x->ntiles_s * nkc_s * 16384, 0);
       th::parallel_for(x->ntiles_s, [&](int t) {
@@ -1621,8 +1627,14 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
           }
         }
       });
+      // per tile and K split: the split's first chunk (b0) and index (b1)
+      const int ns = x->nsplit_s;
       for (int t = 0; t < x->ntiles_s; ++t)
-        ts[t] = th::CoarseTile{(long long)t * nkc_s * 32768, nkc_s, t * 128, std::min(128, nred - t * 128), -1, -1};
+        for (int sp = 0; sp < ns; ++sp) {
+          const int k0 = (int)((long long)sp * nkc_s / ns), k1 = (int)((long long)(sp + 1) * nkc_s / ns);
+          ts.push_back(th::CoarseTile{((long long)t * nkc_s + k0) * 32768, k1 - k0, t * 128,
+                                      std::min(128, nred - t * 128), k0, sp});
+        }
       if ((st = up(x->Sb16, sb.data(), sb.size() * 2)) != TH_OK) return st;
       TH_CU(cudaStreamSynchronize(s));
     }
@@ -1672,7 +1684,11 @@ th_status th_setup(const th_mesh* mesh, const double* k_host, const double* eps_
     u.Al = x->LRb16;
     u.tiles_s = x->tiles_s;
     u.tiles_l = x->tiles_l;
-    u.ntiles_s = x->ntiles_s;
+    u.ntiles_s = x->ntiles_s * x->nsplit_s;
+    u.nsplit = x->nsplit_s;
+    u.spart = x->spart_s;
+    u.nrhs_cap = (int)groups * 64;
+    u.nred = nred;
     u.ntiles_l = x->ntiles_l;
     u.rst = x->rst16;
     u.xst = x->xst16;

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_umma(const CoarseUmmaArg
         const unsigned char* asrc = Ag + tl.a_off + (size_t)pkc * kAChunk;
         const unsigned char* bsrc;
         if (MODE == 0) {
-          bsrc = Bg + (size_t)pkc * kBChunk;
+          bsrc = Bg + (size_t)(tl.b0 + pkc) * kBChunk;
         } else {
           const int side = pkc < a.nkc_m ? 0 : 1;
           const int sp = side ? tl.b1 : tl.b0;
@@ -222,7 +222,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_umma(const CoarseUmmaArg
         ptx::tmem_ld16(base + (unsigned)(64 + c0), im);
         if (!live) continue;
         const int nb = min(16, a.nrhs - (grp * 64 + c0));  // right-hand sides of this slice
-        if (MODE == 0) {
+        if (MODE == 0 && a.nsplit > 1) {  // a partial product of one K split
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (j >= nb) break;
+            const int rhs = grp * 64 + c0 + j;
+            a.spart[((size_t)tl.b1 * a.nrhs_cap + rhs) * a.nred + tl.row0 + row] =
+                make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+          }
+        } else if (MODE == 0) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             if (j >= nb) break;
@@ -263,6 +271,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_umma(const CoarseUmmaArg
   }
 }
 
+// The separator values from the K splits' partial products, added in split
+// order: into the separator rows of x and the split-BF16 copy for MODE 1.
+__global__ void __launch_bounds__(256) k_sep_split_sum(const CoarseUmmaArgs a) {
+  ptx::grid_dep_wait();
+  ptx::grid_dep_launch();
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x, rhs = blockIdx.y;
+  if (idx >= a.nred || rhs >= a.nrhs) return;
+  float vr = 0.f, vi = 0.f;
+  for (int sp = 0; sp < a.nsplit; ++sp) {
+    const float2 v = a.spart[((size_t)sp * a.nrhs_cap + rhs) * a.nred + idx];
+    vr += v.x;
+    vi += v.y;
+  }
+  const int k = idx / a.mc, e = idx - k * a.mc, grp = rhs >> 6, n = rhs & 63;
+  a.x[(size_t)rhs * a.Nc + (size_t)a.sep[k] * a.mc + e] = make_float2(vr, vi);
+  __nv_bfloat16* st =
+      reinterpret_cast<__nv_bfloat16*>(a.xst + (((size_t)grp * a.nsep + k) * a.nkc_m + (e >> 5)) * kBChunk);
+  store_split(st, kBPart / 2, umma_off32(n, e & 31), vr, vi);
+}
+
 cudaError_t launch_coarse_umma(const CoarseUmmaArgs& a, int mode, int sms, cudaStream_t s) {
   if (a.nrhs < 1 || a.mc < 1 || (mode != 0 && mode != 1)) return cudaErrorInvalidValue;
   const int ntiles = mode == 0 ? a.ntiles_s : a.ntiles_l;
@@ -274,7 +302,10 @@ cudaError_t launch_coarse_umma(const CoarseUmmaArgs& a, int mode, int sms, cudaS
   if (mode == 0) {
     e = cudaFuncSetAttribute(k_coarse_umma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_coarse_umma<0>, grid, dim3(kThreads), smem, s, 0, a);
+    e = launch_pdl(k_coarse_umma<0>, grid, dim3(kThreads), smem, s, 0, a);
+    if (e != cudaSuccess || a.nsplit <= 1) return e;
+    return launch_pdl(k_sep_split_sum, dim3((unsigned)((a.nred + 255) / 256), (unsigned)a.nrhs), dim3(256), 0, s, 0,
+                      a);
   }
   e = cudaFuncSetAttribute(k_coarse_umma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -262,7 +262,8 @@ struct CoarseTile {
   int nkc;          // chunks of 32 columns
   int row0;         // separator product: first reduced index; spikes: x index of the first row
   int rows;         // valid rows (<= 128)
-  int b0, b1;       // spikes: separator of the first and second column block (b1 = -1: one block)
+  int b0, b1;       // spikes: separator of the first and second column block (b1 = -1: one block);
+                    // separator product split over K: first chunk and split index
 };
 struct CoarseUmmaArgs {
   const unsigned char* As;  // split-BF16 reduced inverse, ntiles_s tiles
@@ -277,6 +278,11 @@ struct CoarseUmmaArgs {
   long long Nc;
   int mc, nsep, nkc_s, nkc_m, nrhs;
   int* err;
+  // MODE 0 split over K (nsplit > 1): tile entries carry their first chunk (b0) and split
+  // index (b1); partial products go to spart [nsplit][nrhs_cap][nred] and k_sep_split_sum
+  // adds them in a fixed order
+  float2* spart;
+  int nsplit, nrhs_cap, nred;
 };
 cudaError_t launch_coarse_umma(const CoarseUmmaArgs& a, int mode, int sms, cudaStream_t s);
 
