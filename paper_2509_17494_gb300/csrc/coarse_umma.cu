@@ -10,12 +10,14 @@
 // FP64 set-up and the FP32 chunk sweep are those of the other forms.
 //
 //   MODE 0: xhat = Sinv rhat.  A = Sinv (nred x nred), B = rhat (nred values
-//           per right-hand side, written in BF16 by k_reduced_rhs).  The
+//           per right-hand side, written as split BF16 by k_reduced_rhs).  The
 //           epilogue stores xhat into the separator rows of x (FP32) and a
-//           BF16 copy of every separator's values for MODE 1.
+//           split-BF16 copy of every separator's values for MODE 1; with the
+//           K range split over CTAs (nsplit > 1, to fill the SMs) it stores
+//           partial products instead, which k_sep_split_sum adds in split order.
 //   MODE 1: x_c -= [L | R]_c [x_left; x_right] on every chunk c.  A = the
 //           chunk's spikes (L_c mc rows; one column block per adjacent
-//           separator), B = the BF16 copies of those separators' values.
+//           separator), B = the split-BF16 copies of those separators' values.
 //
 // Both operands lie in global memory already in the tensor cores' K-major
 // layout without swizzle, cut into chunks of 32 columns: an A chunk is 128
