@@ -2417,6 +2417,10 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
       // pinned host memory.  A pass that cancels more than 99.99 % of ||w||^2 makes
       // the host restart (loss of orthogonality ~ eps ||w||^2 / ||w - V h||^2),
       // which with the two-grid preconditioner does not occur in practice.
+      // blocks per right-hand side of the double-single dots and norms: with
+      // many right-hand sides a quarter as many, so each thread sums about four
+      // times the entries before the block reduction (its fixed cost)
+      const int nbk = nrhs >= 8 ? std::max(1, x->nblk / 4) : x->nblk;
       auto step = [&](cudaStream_t ss) -> th_status {
         th_status e;
         if ((e = precondition(*x, Vj, Zj, nrhs, ss, kds)) != TH_OK) return e;
@@ -2425,9 +2429,9 @@ th_status th_solve(th_ctx* x, const double* f, double* u, int nrhs, th_solve_inf
         {
           Prof prof(*x, TH_K_KRYLOV, ss);
           if (kds) {
-            TH_CU(th::launch_mdot_ds(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, 1, ss));
+            TH_CU(th::launch_mdot_ds(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, nbk, 1, ss));
             TH_CU(th::launch_maxpy_ds(x->Vk, vstride, x->h1, j + 2, x->w, N, j + 1, nrhs, -1.0, 1, ss));
-            TH_CU(th::launch_norm2_ds(x->w, N, nrhs, x->npart, x->nrm, x->nblk, ss));
+            TH_CU(th::launch_norm2_ds(x->w, N, nrhs, x->npart, x->nrm, nbk, ss));
           } else {
             TH_CU(th::launch_mdot(x->Vk, vstride, x->w, N, j + 1, 1, nrhs, x->dpart, x->h1, x->nblk, ss));
             TH_CU(th::launch_maxpy(x->Vk, vstride, x->h1, j + 2, x->w, N, j + 1, nrhs, -1.0, ss));

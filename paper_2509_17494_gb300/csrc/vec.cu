@@ -514,15 +514,18 @@ __global__ void __launch_bounds__(256, MINB) k_mdot_part_ds(const double2* __res
     }
   }
   // warp sums of the pairs, then the 8 warps' values in FP64 in a fixed order
+  // (only the block's ni live pairs: ni is uniform over the block)
   __shared__ double sh[2][TILE][8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int t = 0; t < TILE; ++t) {
-    acc_warp_sum(ar[t]);
-    acc_warp_sum(ai[t]);
-    if (lane == 0) {
-      sh[0][t][warp] = acc_value(ar[t]);
-      sh[1][t][warp] = acc_value(ai[t]);
+    if (t < ni) {
+      acc_warp_sum(ar[t]);
+      acc_warp_sum(ai[t]);
+      if (lane == 0) {
+        sh[0][t][warp] = acc_value(ar[t]);
+        sh[1][t][warp] = acc_value(ai[t]);
+      }
     }
   }
   __syncthreads();
